@@ -1,0 +1,245 @@
+"""Plain FP64 CPU oracle for the two-terminal KNIT problem -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  It shares
+no code with the CUDA library in ``paper_1010_2627_gb300`` and imports nothing
+from it; both sides only read inputs produced by
+``paper_1010_2627_gb300.inputs``, which holds no arithmetic of the method.
+
+The arithmetic lives in ``knit_oracle.c`` (plain C, FP64, own complex LU, no
+BLAS).  This module compiles it with gcc on first use and calls it through
+ctypes:
+
+* ``sigma_square``   closed-form lead self-energy of a clean square lead
+                     (KNIT user guide Sec. 5.3 B lead construction; textbook
+                     transverse modes)
+* ``decimation``     Sancho-Rubio surface Green function and self-energy of
+                     a general lead (Sec. 5.3 B)
+* ``dense``          the plain definition, Eq. (2) and the Sec. 2.3
+                     transmission formula, by dense LU of the whole system
+* ``dense_general``  the same for an arbitrary site graph with two leads
+                     (the Sec. 2.2 worked example)
+* ``rgf``            the slice form of the method (Sec. 5.3 D knitting and
+                     sewing), plain loops
+* ``rgf_batch``      ``rgf`` over many instances on all host cores (the CPU
+                     baseline)
+* ``onsite``         counter-based Anderson disorder (Sec. 6.1)
+
+Parity status: every function here is pinned by ``tests/test_oracle.py``
+(closed forms, the paper's printed Fig. 3 values, brute force, identities).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "knit_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID, ERR_OOM, ERR_SINGULAR, ERR_NOCONVERGE = 0, 1, 2, 4, 5
+
+
+def build(force: bool = False) -> str:
+    """Compile knit_oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i32, f64, u64 = ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+            lib.orc_splitmix64.restype = u64
+            lib.orc_splitmix64.argtypes = [u64]
+            lib.orc_onsite.restype = f64
+            lib.orc_onsite.argtypes = [u64, i32, i32, f64]
+            lib.orc_onsite_fill.argtypes = [u64, i32, i32, i32, P, f64, P]
+            lib.orc_sigma_square.argtypes = [i32, f64, f64, P]
+            lib.orc_lead_decimation.restype = i32
+            lib.orc_lead_decimation.argtypes = [i32, P, P, f64, f64, i32, f64, i32, P, P, P]
+            lib.orc_dense_flat.restype = i32
+            lib.orc_dense_flat.argtypes = [i32, i32, P, P, P, i32, f64, P, P, P, P, P, P, P]
+            lib.orc_rgf_flat.restype = i32
+            lib.orc_rgf_flat.argtypes = [i32, i32, P, P, P, i32, f64, P, P, P, P, P]
+            lib.orc_dense_general.restype = i32
+            lib.orc_dense_general.argtypes = [i32, P, f64, i32, P, P, i32, P, P, P]
+            lib.orc_rgf_batch.restype = i32
+            lib.orc_rgf_batch.argtypes = [i32, i32, P, P, i32, i32, P, i32, P, P, P, P, P, P,
+                                          i32, P, P]
+            lib.orc_max_threads.restype = i32
+            lib.orc_lu_factor.restype = i32
+            lib.orc_lu_factor.argtypes = [i32, P, P]
+            lib.orc_lu_solve.argtypes = [i32, P, P, P, i32]
+            _lib = lib
+    return _lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"oracle {what} failed with status {code}")
+        self.code = code
+
+
+def splitmix64(z: int) -> int:
+    return int(_load().orc_splitmix64(ctypes.c_uint64(z & 0xFFFFFFFFFFFFFFFF)))
+
+
+def onsite(seed: int, L: int, M: int, W: float, block: int = 1, sign=None) -> np.ndarray:
+    """(L, M) on-site energies W (r - 1/2), r from the (seed, n, site) counter."""
+    sign = _c([1.0] * block if sign is None else sign, np.float64)
+    out = np.empty((L, M), dtype=np.float64)
+    _load().orc_onsite_fill(ctypes.c_uint64(seed), L, M, block, _p(sign), W, _p(out))
+    return out
+
+
+def sigma_square(M: int, t: float, E: float) -> np.ndarray:
+    """Closed-form self-energy (M x M) of a clean square lead of width M, hopping t."""
+    out = np.empty((M, M), dtype=np.complex128)
+    _load().orc_sigma_square(M, t, E, _p(out))
+    return out
+
+
+def decimation(H0, V, E: float, side: int, eta: float = 1e-12, tol: float = 1e-15,
+               maxit: int = 200):
+    """Sancho-Rubio surface g and self-energy of a lead (side 0 left, 1 right).
+
+    Returns (g, Sigma, iterations)."""
+    H0 = _c(H0, np.complex128)
+    V = _c(V, np.complex128)
+    M = H0.shape[0]
+    g = np.empty((M, M), dtype=np.complex128)
+    S = np.empty((M, M), dtype=np.complex128)
+    it = ctypes.c_int(0)
+    rc = _load().orc_lead_decimation(M, _p(H0), _p(V), E, eta, side, tol, maxit, _p(g), _p(S),
+                                     ctypes.byref(it))
+    if rc != OK:
+        raise OracleError(rc, "decimation")
+    return g, S, it.value
+
+
+def _sys_arrays(H0, V, eps, L):
+    H0 = _c(H0, np.complex128)
+    M = H0.shape[0]
+    V = _c(V, np.complex128)
+    if V.ndim == 2:
+        V = V[None]
+    eps = None if eps is None else _c(eps, np.float64).reshape(L, M)
+    return H0, V, eps, M
+
+
+def dense(H0, V, eps, L: int, E: float, SigL, SigR, want_ldos: bool = False):
+    """Dense-LU solution of Eq. (2) for a slice system.
+
+    V is (M, M) or (P, M, M) with H_{n,n-1} = V[n % P]; eps is (L, M) or None.
+    Returns dict(T_LR, T_RL, G11, G1L, GL1, ldos)."""
+    H0, V, eps, M = _sys_arrays(H0, V, eps, L)
+    SigL = _c(SigL, np.complex128)
+    SigR = _c(SigR, np.complex128)
+    T = np.empty(2)
+    G11 = np.empty((M, M), np.complex128)
+    G1L = np.empty((M, M), np.complex128)
+    GL1 = np.empty((M, M), np.complex128)
+    ldos = np.empty((L, M)) if want_ldos else None
+    rc = _load().orc_dense_flat(M, L, _p(H0), _p(eps), _p(V), V.shape[0], E, _p(SigL), _p(SigR),
+                                _p(T), _p(G11), _p(G1L), _p(GL1), _p(ldos))
+    if rc != OK:
+        raise OracleError(rc, "dense")
+    return dict(T_LR=float(T[0]), T_RL=float(T[1]), G11=G11, G1L=G1L, GL1=GL1, ldos=ldos)
+
+
+def dense_general(H, E: float, idx0, Sig0, idx1, Sig1):
+    """Two-lead transmission of an arbitrary site graph: (T_{1<-0}, T_{0<-1})."""
+    H = _c(H, np.complex128)
+    idx0 = _c(idx0, np.int32)
+    idx1 = _c(idx1, np.int32)
+    Sig0 = _c(Sig0, np.complex128)
+    Sig1 = _c(Sig1, np.complex128)
+    T = np.empty(2)
+    rc = _load().orc_dense_general(H.shape[0], _p(H), E, len(idx0), _p(idx0), _p(Sig0),
+                                   len(idx1), _p(idx1), _p(Sig1), _p(T))
+    if rc != OK:
+        raise OracleError(rc, "dense_general")
+    return float(T[0]), float(T[1])
+
+
+def rgf(H0, V, eps, L: int, E: float, SigL, SigR, want_ldos: bool = False):
+    """The slice-by-slice method: returns dict(T, ldos, G11)."""
+    H0, V, eps, M = _sys_arrays(H0, V, eps, L)
+    SigL = _c(SigL, np.complex128)
+    SigR = _c(SigR, np.complex128)
+    T = np.empty(1)
+    ldos = np.empty((L, M)) if want_ldos else None
+    G11 = np.empty((M, M), np.complex128) if want_ldos else None
+    rc = _load().orc_rgf_flat(M, L, _p(H0), _p(eps), _p(V), V.shape[0], E, _p(SigL), _p(SigR),
+                              _p(T), _p(ldos), _p(G11))
+    if rc != OK:
+        raise OracleError(rc, "rgf")
+    return dict(T=float(T[0]), ldos=ldos, G11=G11)
+
+
+def rgf_batch(H0, V, L: int, E, seeds, W, SigL, SigR, sig_index, block: int = 1, sign=None,
+              nthreads: int = 0):
+    """``rgf`` over instances i with energy E[i], disorder (seeds[i], W[i]) and
+    self-energies SigL[sig_index[i]], SigR[sig_index[i]].  Returns (T, status)."""
+    H0 = _c(H0, np.complex128)
+    M = H0.shape[0]
+    V = _c(V, np.complex128)
+    if V.ndim == 2:
+        V = V[None]
+    E = _c(E, np.float64)
+    n = E.shape[0]
+    seeds = _c(seeds, np.uint64)
+    W = _c(np.broadcast_to(W, (n,)), np.float64)
+    SigL = _c(SigL, np.complex128)
+    SigR = _c(SigR, np.complex128)
+    sig_index = _c(sig_index, np.int32)
+    sign = _c([1.0] * block if sign is None else sign, np.float64)
+    T = np.empty(n)
+    st = np.zeros(n, np.int32)
+    _load().orc_rgf_batch(M, L, _p(H0), _p(V), V.shape[0], block, _p(sign), n, _p(E), _p(seeds),
+                          _p(W), _p(SigL), _p(SigR), _p(sig_index), nthreads, _p(T), _p(st))
+    return T, st
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def lu_solve(A, B):
+    """Solve A X = B with the oracle's own pivoted LU (for tests of the LU)."""
+    A = np.array(A, dtype=np.complex128, order="C")
+    B = np.array(B, dtype=np.complex128, order="C")
+    if B.ndim == 1:
+        B = B[:, None]
+    N = A.shape[0]
+    perm = np.empty(N, np.int32)
+    rc = _load().orc_lu_factor(N, _p(A), _p(perm))
+    if rc != 0:
+        raise OracleError(ERR_SINGULAR, "lu_factor")
+    _load().orc_lu_solve(N, _p(A), _p(perm), _p(B), B.shape[1])
+    return B, perm

@@ -1,0 +1,303 @@
+"""Pins for the CPU oracle: values the paper prints, closed forms, identities
+and brute force -- none of them re-runs the oracle's own formula.
+
+Every test here is CPU-only (``-m "not gpu"``)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1010_2627_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def gamma(S):
+    return 1j * (S - S.conj().T)
+
+
+# --------------------------------------------------------------------------
+# LU with partial pivoting
+
+def test_lu_matches_library_solve():
+    rng = np.random.default_rng(1)
+    for N in (1, 2, 7, 33):
+        A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+        B = rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3))
+        X, _ = oracle.lu_solve(A, B)
+        assert np.allclose(X, np.linalg.solve(A, B), atol=1e-11, rtol=1e-11)
+
+
+def test_lu_pivot_rule_and_ties():
+    # column 0: |1+0i| = |0+1i| (|Re|+|Im| equal) -> lowest row kept; |2| wins below.
+    A = np.array([[1, 5, 0], [1j, 2, 1], [0, 1, 3]], np.complex128)
+    _, perm = oracle.lu_solve(A, np.eye(3))
+    assert perm[0] == 0
+    A = np.array([[1, 5, 0], [2, 2, 1], [0, 1, 3]], np.complex128)
+    _, perm = oracle.lu_solve(A, np.eye(3))
+    assert perm[0] == 1
+    # a singular matrix must be reported, not divided through
+    with pytest.raises(oracle.OracleError):
+        oracle.lu_solve(np.array([[1, 2], [2, 4]], np.complex128), np.eye(2))
+
+
+# --------------------------------------------------------------------------
+# Disorder generator (Sec. 6.1 Anderson disorder, SplitMix64 counter)
+
+def test_splitmix64_published_vector():
+    gamma_ = 0x9E3779B97F4A7C15
+    want = [int(r[0]) for r in _golden("splitmix64_seed1234567.txt")]
+    x = 1234567
+    got = []
+    for _ in range(5):
+        got.append(oracle.splitmix64(x))
+        x = (x + gamma_) & 0xFFFFFFFFFFFFFFFF
+    assert got == want
+
+
+def test_onsite_distribution_and_structure():
+    W = 2.0
+    eps = oracle.onsite(7, 400, 50, W)
+    assert eps.shape == (400, 50)
+    assert eps.min() >= -W / 2 and eps.max() < W / 2
+    assert abs(eps.mean()) < 0.02
+    assert abs(eps.var() - W * W / 12) < 0.01
+    # keyed by (seed, n, site): reproducible, different seeds differ, and a
+    # 4-orbital block repeats the site value with the component signs
+    assert np.array_equal(eps, oracle.onsite(7, 400, 50, W))
+    assert not np.allclose(eps, oracle.onsite(8, 400, 50, W))
+    e4 = oracle.onsite(7, 10, 20, W, block=4, sign=[1, 1, -1, -1])
+    e1 = oracle.onsite(7, 10, 5, W)
+    assert np.array_equal(e4[:, 0::4], e1) and np.array_equal(e4[:, 1::4], e1)
+    assert np.array_equal(e4[:, 2::4], -e1) and np.array_equal(e4[:, 3::4], -e1)
+
+
+# --------------------------------------------------------------------------
+# Leads (Sec. 5.3 B): closed form, fixed point, decimation
+
+@pytest.mark.parametrize("E", [-2.5, -1.3, 0.0, 0.7, 1.99, 3.2])
+def test_sigma_1d_chain_closed_form(E):
+    # the 1D lead: Sigma = (E - i sqrt(4 t^2 - E^2))/2 in band (t = 1), real outside
+    S = oracle.sigma_square(1, 1.0, E)[0, 0]
+    if abs(E) < 2:
+        want = (E - 1j * np.sqrt(4 - E * E)) / 2
+    else:
+        want = (E - np.sign(E) * np.sqrt(E * E - 4)) / 2
+    assert abs(S - want) < 1e-14
+
+
+@pytest.mark.parametrize("M,t,E", [(8, 1.0, -3.1), (8, 1.0, 0.3), (13, 0.7, 1.1), (5, -1.0, 0.45)])
+def test_sigma_square_is_retarded_fixed_point(M, t, E):
+    sys_ = inputs.square(M, 4, t)
+    S = oracle.sigma_square(M, t, E)
+    g = S / (t * t)
+    H0, V = sys_.H0, sys_.V[0]
+    resid = g - np.linalg.inv(E * np.eye(M) - H0 - V @ g @ V.conj().T)
+    assert np.abs(resid).max() < 1e-12
+    # retarded branch: i (g - g^dagger) positive semi-definite
+    assert np.linalg.eigvalsh(1j * (g - g.conj().T)).min() > -1e-12
+    assert np.allclose(S, S.T)                  # symmetric real H0, V -> symmetric
+
+
+@pytest.mark.parametrize("E", [-2.9, -0.8, 0.05, 2.2])
+def test_decimation_matches_closed_form(E):
+    M, t = 6, 1.0
+    s = inputs.square(M, 4, t)
+    Sc = oracle.sigma_square(M, t, E)
+    for side in (0, 1):
+        g, S, it = oracle.decimation(s.H0, s.V[0], E, side, eta=1e-13)
+        assert np.abs(S - Sc).max() < 1e-9, (side, it)
+
+
+def test_decimation_general_lead_fixed_point():
+    rng = np.random.default_rng(3)
+    M = 5
+    A = rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))
+    H0 = (A + A.conj().T) / 2
+    V = 0.8 * (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M)))
+    eta = 1e-3   # finite eta: residual of the fixed point at E + i eta
+    for side, E in ((0, 0.4), (1, -1.1)):
+        g, S, it = oracle.decimation(H0, V, E, side, eta=eta)
+        Vin, Vout = (V, V.conj().T) if side == 0 else (V.conj().T, V)
+        z = E + 1j * eta
+        assert np.abs(g - np.linalg.inv(z * np.eye(M) - H0 - Vin @ g @ Vout)).max() < 1e-11
+        assert np.abs(S - Vin @ g @ Vout).max() < 1e-11
+        assert np.linalg.eigvalsh(1j * (g - g.conj().T)).min() > -1e-12
+
+
+# --------------------------------------------------------------------------
+# Transmission pins
+
+def _square_T(M, L, E, eps=None, method="dense"):
+    s = inputs.square(M, L)
+    S = oracle.sigma_square(M, 1.0, E)
+    f = oracle.dense if method == "dense" else oracle.rgf
+    return f(s.H0, s.V, eps, L, E, S, S)
+
+
+@pytest.mark.parametrize("E", [-3.0, -1.9, -0.4, 0.0, 1.2, 2.5])
+def test_clean_chain_T_is_one_in_band(E):
+    for L in (1, 2, 9):
+        r = _square_T(1, L, E)
+        want = 1.0 if abs(E) < 2 else 0.0
+        assert abs(r["T_LR"] - want) < 1e-12
+        assert abs(_square_T(1, L, E, method="rgf")["T"] - want) < 1e-12
+
+
+@pytest.mark.parametrize("M", [3, 8])
+def test_clean_ribbon_plateaus(M):
+    ek = 2 * np.cos(np.arange(1, M + 1) * np.pi / (M + 1))
+    for E in inputs.energy_grid(-3.9, 3.9, 23):
+        nopen = int(np.sum(np.abs(E - ek) < 2))
+        if np.min(np.abs(np.abs(E - ek) - 2)) < 1e-3:
+            continue                        # too close to a channel threshold
+        assert abs(_square_T(M, 5, E, method="rgf")["T"] - nopen) < 1e-10
+        assert abs(_square_T(M, 5, E)["T_LR"] - nopen) < 1e-10
+
+
+def test_clean_ribbon_ldos_closed_form():
+    M, L, E = 6, 7, 0.37
+    y = np.arange(1, M + 1)
+    phi = np.sqrt(2 / (M + 1)) * np.sin(np.outer(y, y) * np.pi / (M + 1))
+    ek = 2 * np.cos(y * np.pi / (M + 1))
+    open_ = np.abs(E - ek) < 2
+    rho = (phi[:, open_] ** 2 / (np.pi * np.sqrt(4 - (E - ek[open_]) ** 2))).sum(axis=1)
+    for method in ("dense", "rgf"):
+        s = inputs.square(M, L)
+        S = oracle.sigma_square(M, 1.0, E)
+        f = oracle.dense if method == "dense" else oracle.rgf
+        ldos = f(s.H0, s.V, None, L, E, S, S, want_ldos=True)["ldos"]
+        assert np.abs(ldos - rho[None, :]).max() < 1e-11
+
+
+def test_fig3_worked_example():
+    """The only numbers the paper prints: Fig. 3, T_{1<-0} of the L-shaped system."""
+    H, idx0, idx1, w0, w1 = inputs.lshape_example()
+    for Es, Ts in _golden("fig3_conductance.txt"):
+        E, Tp = float(Es), float(Ts)
+        S0 = oracle.sigma_square(w0, 1.0, E)
+        S1 = oracle.sigma_square(w1, 1.0, E)
+        T10, T01 = oracle.dense_general(H, E, idx0, S0, idx1, S1)
+        assert abs(T10 - Tp) < 6e-12, (E, T10, Tp)
+        assert abs(T01 - T10) < 1e-11
+
+
+def test_reciprocity_bounds_and_ward_identity():
+    M, L = 6, 9
+    for seed, E in ((0, -1.7), (1, 0.2), (2, 2.6)):
+        eps = oracle.onsite(seed, L, M, 2.0)
+        s = inputs.square(M, L)
+        S = oracle.sigma_square(M, 1.0, E)
+        r = oracle.dense(s.H0, s.V, eps, L, E, S, S)
+        ek = 2 * np.cos(np.arange(1, M + 1) * np.pi / (M + 1))
+        nch = int(np.sum(np.abs(E - ek) < 2))
+        assert abs(r["T_LR"] - r["T_RL"]) < 1e-11
+        assert -1e-12 <= r["T_LR"] <= nch + 1e-12
+        # unitarity of the scattering matrix (Ward identity, textbook):
+        # T = Tr[Gamma_L i(G11 - G11^dag)] - Tr[Gamma_L G11 Gamma_L G11^dag]
+        G, Gl = r["G11"], gamma(S)
+        ward = np.real(np.trace(Gl @ (1j * (G - G.conj().T))) - np.trace(Gl @ G @ Gl @ G.conj().T))
+        assert abs(ward - r["T_LR"]) < 1e-11
+
+
+@pytest.mark.parametrize("M,L,P", [(1, 1, 1), (2, 3, 1), (3, 6, 2), (4, 5, 1), (4, 6, 2)])
+def test_rgf_equals_dense_brute_force(M, L, P):
+    rng = np.random.default_rng(100 + 10 * M + L)
+    s = inputs.random_slice_system(rng, M, L, P)
+    eps = rng.uniform(-1, 1, (L, M))
+    SL = inputs.random_retarded_sigma(rng, M)
+    SR = inputs.random_retarded_sigma(rng, M)
+    E = 0.3
+    d = oracle.dense(s.H0, s.V, eps, L, E, SL, SR, want_ldos=True)
+    r = oracle.rgf(s.H0, s.V, eps, L, E, SL, SR, want_ldos=True)
+    assert abs(d["T_LR"] - r["T"]) < 1e-10 * max(1, abs(d["T_LR"]))
+    assert np.abs(d["ldos"] - r["ldos"]).max() < 1e-10
+    assert np.abs(d["G11"] - r["G11"]).max() < 1e-10
+    # the dense oracle against a library inverse of an independently assembled matrix
+    N = M * L
+    A = np.zeros((N, N), np.complex128)
+    for n in range(L):
+        A[n * M:(n + 1) * M, n * M:(n + 1) * M] = E * np.eye(M) - s.H0 - np.diag(eps[n])
+        if n:
+            Vn = s.V[n % P]
+            A[n * M:(n + 1) * M, (n - 1) * M:n * M] = -Vn
+            A[(n - 1) * M:n * M, n * M:(n + 1) * M] = -Vn.conj().T
+    A[:M, :M] -= SL
+    A[-M:, -M:] -= SR
+    G = np.linalg.inv(A)
+    assert np.abs(G[:M, -M:] - d["G1L"]).max() < 1e-10
+    assert np.abs(G[-M:, :M] - d["GL1"]).max() < 1e-10
+    assert np.abs(-np.diag(G).imag / np.pi - d["ldos"].ravel()).max() < 1e-10
+
+
+def test_rgf_batch_matches_single():
+    M, L = 5, 8
+    s = inputs.square(M, L)
+    E = np.array([-1.0, 0.5, 2.1])
+    SL = np.stack([oracle.sigma_square(M, 1.0, e) for e in E])
+    T, st = oracle.rgf_batch(s.H0, s.V, L, E, np.array([3, 4, 5], np.uint64), 1.5, SL, SL,
+                             np.arange(3), nthreads=2)
+    assert (st == 0).all()
+    for i in range(3):
+        eps = oracle.onsite(3 + i, L, M, 1.5)
+        assert abs(T[i] - oracle.rgf(s.H0, s.V, eps, L, E[i], SL[i], SL[i])["T"]) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Spin x Nambu (BdG) blocks
+
+def _bdg_T(sysb, E, eps, part=None):
+    Ns = sysb.M // 4
+    gs = []
+    for side in (0, 1):
+        g, S, _ = oracle.decimation(sysb.lead_H0[side], sysb.lead_V[side], E, side, eta=1e-12)
+        gs.append(S)
+    r = oracle.dense(sysb.H0, sysb.V, eps, sysb.L, E, gs[0], gs[1])
+    if part is None:
+        return r["T_LR"]
+    P = np.zeros(sysb.M)
+    for s in range(Ns):
+        P[4 * s + (0 if part == "e" else 2):4 * s + (2 if part == "e" else 4)] = 1
+    Pm = np.diag(P)
+    G = r["G1L"]
+    return np.real(np.trace(Pm @ gamma(gs[0]) @ Pm @ G @ Pm @ gamma(gs[1]) @ Pm @ G.conj().T))
+
+
+def test_bdg_without_pairing_is_two_spinless_copies():
+    Ns, L, mu, E = 3, 4, -1.0, 0.23
+    b = inputs.bdg(Ns, L, mu=mu, delta=0.0, alpha=0.0)
+    eps_site = oracle.onsite(5, L, Ns, 1.0)
+    eps = oracle.onsite(5, L, 4 * Ns, 1.0, block=4, sign=b.sign)
+    sq = inputs.square(Ns, L)
+    Se = oracle.sigma_square(Ns, 1.0, E + mu)
+    Te1 = oracle.dense(sq.H0, sq.V, eps_site, L, E + mu, Se, Se)["T_LR"]
+    Sh = oracle.sigma_square(Ns, 1.0, E - mu)
+    # hole block: on-site mu - eps and hopping -t at energy E, i.e. the spinless
+    # system with on-site -eps and hopping -t at energy E - mu
+    sqm = inputs.square(Ns, L, t=-1.0)
+    Shm = oracle.sigma_square(Ns, -1.0, E - mu)
+    Th1 = oracle.dense(sqm.H0, sqm.V, -eps_site, L, E - mu, Shm, Shm)["T_LR"]
+    assert abs(_bdg_T(b, E, eps, "e") - 2 * Te1) < 1e-9
+    assert abs(_bdg_T(b, E, eps, "h") - 2 * Th1) < 1e-9
+    del Sh
+
+
+def test_bdg_particle_hole_symmetry():
+    Ns, L = 3, 5
+    b = inputs.bdg(Ns, L, mu=-1.0, delta=0.1, alpha=0.2)
+    eps = oracle.onsite(2, L, 4 * Ns, 1.0, block=4, sign=b.sign)
+    for E in (0.03, 0.11):
+        Tee = _bdg_T(b, E, eps, "e")
+        Thh = _bdg_T(b, -E, eps, "h")
+        assert abs(Tee - Thh) < 1e-9, (E, Tee, Thh)
