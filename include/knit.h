@@ -1,0 +1,172 @@
+/*
+ * knit.h -- C-ABI of the GB300 recursive Green-function (KNIT slice sweep)
+ * transport library.  Plain pointers and sizes only; no C++ or framework types.
+ *
+ * The problem (KNIT user guide, Sec. 2.3, Eq. 1 and Eq. 2): a tight-binding
+ * system of L slices with M orbitals each, block-tridiagonal Hamiltonian
+ *     H_{n,n}   = H0 + diag(eps_n)                (M x M, Hermitian)
+ *     H_{n,n-1} = V[n % Vperiod],  H_{n-1,n} = V[n % Vperiod]^dagger,
+ * coupled at slice 0 and slice L-1 to two semi-infinite clean leads.  Each
+ * lead repeats one cell (lead_H0, lead_V) and couples to the system with its
+ * own inter-cell hopping (Sec. 5.3 B, "the hopping matrix elements from the
+ * lead to the system are exactly the same as those inside lead itself"):
+ *     left:  g_L = (E - H0_L - V_L g_L V_L^dagger)^{-1},  Sigma_L = V_L g_L V_L^dagger
+ *     right: g_R = (E - H0_R - V_R^dagger g_R V_R)^{-1},  Sigma_R = V_R^dagger g_R V_R
+ * The retarded Green function is G = (E - H - Sigma_L - Sigma_R)^{-1} (Eq. 2,
+ * read with the textbook sign Im Sigma <= 0), the transmission
+ *     T = Re Tr[Gamma_L G_{0,L-1} Gamma_R G_{0,L-1}^dagger],  Gamma = i(Sigma - Sigma^dagger)
+ * (Sec. 2.3 transmission formula) and the local density of states
+ *     LDOS[n][x] = -Im G_{(n,x),(n,x)} / pi  (Sec. 2.1 b, on-site density).
+ * The slice sweep ("knitting", Sec. 5.3 D) is block Gaussian elimination of
+ * (E - H - Sigma); the backward pass ("sewing") gives the diagonal blocks.
+ *
+ * Disorder (Sec. 6.1): orbital c of site s = x / block in slice n receives
+ *     eps = onsite_sign[c] * W * (r - 1/2),
+ *     r = (splitmix64(splitmix64(seed) ^ (n << 32 | s)) >> 11) * 2^-53,
+ * with SplitMix64 as published by Steele, Lea & Flood (OOPSLA 2014).
+ *
+ * Conventions for every call:
+ *  - complex numbers are knit_c128 (re, im) pairs; matrices are row-major;
+ *  - input and output arrays may be host or device memory (the library asks
+ *    the CUDA runtime which); the caller owns them;
+ *  - calls are ordered on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream); a call whose outputs include host memory returns after the
+ *    results are in host memory, otherwise it returns after enqueueing;
+ *  - the return value reports invalid arguments, out-of-memory and CUDA
+ *    errors; per-instance numerical failures (singular pivot, non-finite
+ *    result, non-converged lead) go to the optional `status` array and do
+ *    not fail the batch;
+ *  - knit_last_error() returns a thread-local message for the last failure.
+ *  - Only one call per system may run at a time: a system owns its device
+ *    workspace.
+ */
+#ifndef KNIT_H
+#define KNIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct knit_system_s *knit_system;   /* opaque; owned by the library */
+
+typedef struct {
+    double re, im;
+} knit_c128;
+
+typedef enum {
+    KNIT_OK = 0,
+    KNIT_ERR_INVALID = 1,    /* bad argument or unsupported structure */
+    KNIT_ERR_OOM = 2,        /* device or host allocation failed */
+    KNIT_ERR_CUDA = 3,       /* CUDA runtime error (message in knit_last_error) */
+    KNIT_ERR_SINGULAR = 4,   /* per instance: exactly zero pivot in an inversion */
+    KNIT_ERR_NOCONVERGE = 5, /* per energy: lead fixed point did not converge */
+    KNIT_ERR_TIMEOUT = 6,    /* a bounded device wait ran out */
+    KNIT_ERR_NONFINITE = 7   /* per instance: NaN or Inf in the result */
+} knit_status;
+
+/* Arithmetic of the slice sweep. */
+enum {
+    KNIT_FP64 = 0,  /* complex128 throughout */
+    KNIT_MIXED = 1  /* complex64 inversion + one refinement step against a
+                       residual accumulated in double-float (hi + lo float)
+                       arithmetic; the state g_n is carried as hi + lo */
+};
+
+/* Lead solver. */
+enum {
+    KNIT_LEAD_AUTO = 0,       /* MODES when the lead hopping is a multiple of
+                                 the identity, else DECIMATION */
+    KNIT_LEAD_MODES = 1,      /* transverse modes of lead_H0 (FP64 Jacobi
+                                 eigensolver once per system) and the retarded
+                                 1D surface function per mode; exact for
+                                 lead_V = t * I */
+    KNIT_LEAD_DECIMATION = 2  /* Sancho-Rubio decimation in FP64 at E + i eta */
+};
+
+typedef struct {
+    int32_t M;                   /* orbitals per slice, 1 <= M <= 256 */
+    int32_t L;                   /* slices, L >= 1 */
+    int32_t block;               /* orbitals per site (1, 2 or 4); M % block == 0 */
+    const double *onsite_sign;   /* `block` signs for the site's disorder draw, NULL = all +1 */
+    const knit_c128 *H0;         /* M*M clean slice Hamiltonian (Hermitian) */
+    const double *onsite;        /* L*M explicit diagonal shifts added to H0, or NULL;
+                                    when given, W and seeds are ignored */
+    const knit_c128 *V;          /* Vperiod*M*M, H_{n,n-1} = V[n % Vperiod]; each V must be
+                                    block-diagonal with `block` x `block` blocks */
+    int32_t Vperiod;             /* 1 or 2 */
+    const knit_c128 *lead_H0[2]; /* left/right lead cell (M*M); NULL = H0 */
+    const knit_c128 *lead_V[2];  /* left/right lead inter-cell hopping (M*M); NULL = V[0] */
+} knit_system_desc;
+
+/* Copy the description into a new system (all pointers are read during the
+ * call only; host or device memory).  Returns KNIT_ERR_INVALID for sizes out
+ * of range, a non-block-diagonal V, or a lead_V whose structure the lead
+ * solvers do not support. */
+knit_status knit_system_create(const knit_system_desc *desc, knit_system *out);
+
+/* Free a system and its device workspace (NULL is accepted). */
+knit_status knit_system_destroy(knit_system sys);
+
+typedef struct {
+    int32_t method;    /* KNIT_LEAD_* */
+    double eta;        /* decimation broadening (default 1e-12 when <= 0) */
+    double tol;        /* decimation stop: max|alpha| + max|beta| < tol (default 1e-14) */
+    int32_t maxit;     /* decimation iteration cap (default 200) */
+} knit_lead_opts;
+
+/* Lead self-energy Sigma_lead(E[e]) for nE energies (Sec. 5.3 B selfE(E)).
+ * lead: 0 = left, 1 = right.  sigma: nE*M*M outputs (caller-owned).
+ * iters (nE, optional): decimation iterations (0 for MODES); residual (nE,
+ * optional): max-norm of g - (E - H0 - V g V^dagger)^{-1} at eta = 0, computed
+ * in FP64 on the device.  opts may be NULL (AUTO). */
+knit_status knit_lead_selfenergy(knit_system sys, int32_t lead, const double *E, int32_t nE,
+                                 const knit_lead_opts *opts, knit_c128 *sigma, int32_t *iters,
+                                 double *residual, void *stream);
+
+/* Instances form an energy x seed grid: instance i = e * nS + s has energy
+ * E[e] and disorder seed seeds[s] (seeds may be NULL: seed 0 for all), all
+ * with disorder strength W (ignored when the system has explicit `onsite`).
+ * Per-instance outputs are indexed the same way. */
+
+/* Two-terminal transmission T_i (Sec. 2.3) for nE * nS instances.  The lead
+ * self-energies are computed once per energy on the device (opts may be
+ * NULL: AUTO).  precision: KNIT_FP64 or KNIT_MIXED (KNIT_MIXED needs
+ * diagonal inter-slice couplings and M <= 64).  T: nE*nS outputs; status
+ * (optional): nE*nS knit_status values. */
+knit_status knit_transmission(knit_system sys, const double *E, int32_t nE,
+                              const uint64_t *seeds, int32_t nS, double W, int32_t precision,
+                              const knit_lead_opts *opts, double *T, int32_t *status,
+                              void *stream);
+
+/* The sweep alone (Sec. 5.3 D knitting) with caller-supplied self-energies:
+ * energy e uses sigmaL/sigmaR + e*M*M (complex128, nE*M*M each). */
+knit_status knit_transmission_sigma(knit_system sys, const double *E, int32_t nE,
+                                    const uint64_t *seeds, int32_t nS, double W,
+                                    const knit_c128 *sigmaL, const knit_c128 *sigmaR,
+                                    int32_t precision, double *T, int32_t *status, void *stream);
+
+/* Local density of states (Sec. 5.3 D knitting followed by sewing), FP64:
+ * ldos (nE*nS*L*M, row-major [i][n][x]) receives -Im G_nn[x][x]/pi; T
+ * (optional) the transmission; status (optional) per instance (ldos of an
+ * instance with non-zero status is unspecified).  saving_level follows
+ * knitANDsew (Sec. 7.3): -1 keeps every forward g_n; k >= 1 keeps every k-th
+ * and recomputes the slices in between during the backward pass; 0 (keep
+ * nothing) is rejected because the backward pass needs the forward g_n. */
+knit_status knit_ldos(knit_system sys, const double *E, int32_t nE, const uint64_t *seeds,
+                      int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
+                      double *ldos, double *T, int32_t *status, void *stream);
+
+/* Thread-local description of the last error (never NULL). */
+const char *knit_last_error(void);
+
+/* Library version string. */
+const char *knit_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNIT_H */

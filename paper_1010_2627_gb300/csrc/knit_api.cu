@@ -1,0 +1,672 @@
+// knit_api.cu -- implementation of the C-ABI declared in include/knit.h:
+// argument validation, host/device staging, workspace management and kernel
+// launches.  No arithmetic of the method runs here; every step of the path
+// is a kernel in sweep_fp64.cu, sweep_mixed.cu or lead_kernels.cu.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/knit.h"
+#include "knit_common.cuh"
+
+extern "C" cudaError_t knit_launch_sweep_fp64(const SysDev *, const InstDev *, int, double2 *, int,
+                                              cudaStream_t);
+extern "C" cudaError_t knit_launch_ldos_fp64(const SysDev *, const InstDev *, int, double2 *, int,
+                                             double2 *, int, double *, cudaStream_t);
+extern "C" size_t knit_fp64_smem_bytes(int, int, int);
+extern "C" cudaError_t knit_launch_mixed(const SysDev *, const InstDev *, int, cudaStream_t);
+extern "C" int knit_mixed_max_M(void);
+extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
+extern "C" cudaError_t knit_launch_modes_sigma(const double2 *, const double2 *, int, double,
+                                               const double *, int, double2 *, double2 *, int,
+                                               cudaStream_t);
+extern "C" cudaError_t knit_launch_decimation(const double2 *, const double2 *, int, int, int,
+                                              const double *, int, double, double, int, double2 *,
+                                              double2 *, double2 *, int *, int *, int,
+                                              cudaStream_t);
+extern "C" cudaError_t knit_launch_lead_residual(const double2 *, const double2 *, int, int, int,
+                                                 const double *, int, const double2 *, double2 *,
+                                                 double *, int, cudaStream_t);
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+knit_status fail(knit_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+knit_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(KNIT_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(KNIT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= n) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 256));
+        if (e == cudaSuccess) n = std::max<size_t>(bytes, 256);
+        else p = nullptr;
+        return e;
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct Lead {
+    double2 *H0 = nullptr, *V = nullptr;   // device copies
+    int vb = 1;
+    int scalar = 0;     // V = t * identity
+    double t2 = 0.0;    // |t|^2
+    double2 *U = nullptr, *A = nullptr;    // modes: eigenvectors and diagonalised cell
+    int modes_ready = 0;
+    std::vector<double2> hH0, hV;          // host copies (structure checks)
+};
+
+}  // namespace
+
+struct knit_system_s {
+    int M = 0, L = 0, block = 1, Vperiod = 1, vb = 1;
+    int device = 0, nsm = 1;
+    double2 *H0 = nullptr, *V = nullptr, *h0_val = nullptr;
+    double *sign = nullptr, *onsite = nullptr;
+    int *h0_rowptr = nullptr, *h0_col = nullptr;
+    Lead lead[2];
+    int leads_same = 0;
+    // grow-only workspaces
+    DevBuf E, seeds, T, status, queue, sigL, sigR, gL, gR, lst, lit, lres, work, ckpt, decw, ldos;
+
+    SysDev dev() const
+    {
+        SysDev s;
+        s.M = M;
+        s.L = L;
+        s.block = block;
+        s.Vperiod = Vperiod;
+        s.vdiag = vb == 1;
+        s.vb = vb;
+        s.H0 = H0;
+        s.V = V;
+        s.sign = sign;
+        s.onsite = onsite;
+        s.h0_rowptr = h0_rowptr;
+        s.h0_col = h0_col;
+        s.h0_val = h0_val;
+        return s;
+    }
+};
+
+namespace {
+
+template <typename T>
+knit_status to_host(std::vector<T> &dst, const void *src, size_t count, const char *what)
+{
+    dst.resize(count);
+    if (count == 0) return KNIT_OK;
+    if (!src) return fail(KNIT_ERR_INVALID, "%s is NULL", what);
+    CK(cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDefault), what);
+    return KNIT_OK;
+}
+
+template <typename T>
+knit_status to_device(T **dst, const T *src, size_t count, const char *what)
+{
+    CK(cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(count, 1)), what);
+    if (count) CK(cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice), what);
+    return KNIT_OK;
+}
+
+// block size of a block-diagonal M x M matrix whose blocks are at most `block`
+// wide: 1 if diagonal, `block` if block-diagonal, 0 otherwise
+int block_structure(const double2 *A, int M, int block)
+{
+    bool diag = true, bdiag = true;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double2 v = A[(size_t)i * M + j];
+            if (v.x == 0.0 && v.y == 0.0) continue;
+            if (i != j) diag = false;
+            if (i / block != j / block) bdiag = false;
+        }
+    return diag ? 1 : (bdiag ? block : 0);
+}
+
+bool hermitian(const double2 *A, int M)
+{
+    double mx = 0.0;
+    for (int q = 0; q < M * M; ++q) mx = std::max(mx, std::fabs(A[q].x) + std::fabs(A[q].y));
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double2 a = A[(size_t)i * M + j], b = A[(size_t)j * M + i];
+            if (std::fabs(a.x - b.x) + std::fabs(a.y + b.y) > 1e-12 * std::max(mx, 1.0)) return false;
+        }
+    return true;
+}
+
+bool scalar_identity(const double2 *A, int M, double *t2)
+{
+    double2 d = A[0];
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double2 v = A[(size_t)i * M + j];
+            if (i == j) {
+                if (v.x != d.x || v.y != d.y) return false;
+            } else if (v.x != 0.0 || v.y != 0.0) {
+                return false;
+            }
+        }
+    *t2 = d.x * d.x + d.y * d.y;
+    return *t2 > 0.0;
+}
+
+// stage an input array on the device (no copy if it already is device memory)
+template <typename T>
+knit_status stage_in(DevBuf &buf, const T *src, size_t count, cudaStream_t st, const T **out,
+                     const char *what)
+{
+    if (!src) {
+        *out = nullptr;
+        return KNIT_OK;
+    }
+    if (is_device_ptr(src)) {
+        *out = src;
+        return KNIT_OK;
+    }
+    CK(buf.ensure(sizeof(T) * count), what);
+    CK(cudaMemcpyAsync(buf.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, st), what);
+    *out = buf.as<T>();
+    return KNIT_OK;
+}
+
+template <typename T>
+knit_status stage_out(DevBuf &buf, T *dst, size_t count, T **out, bool *host, const char *what)
+{
+    *host = false;
+    if (!dst) {
+        *out = nullptr;
+        return KNIT_OK;
+    }
+    if (is_device_ptr(dst)) {
+        *out = dst;
+        return KNIT_OK;
+    }
+    *host = true;
+    CK(buf.ensure(sizeof(T) * count), what);
+    *out = buf.as<T>();
+    return KNIT_OK;
+}
+
+knit_status ensure_modes(knit_system s, int p)
+{
+    Lead &ld = s->lead[p];
+    if (ld.modes_ready) return KNIT_OK;
+    const size_t MM = (size_t)s->M * s->M;
+    CK(cudaMalloc((void **)&ld.U, sizeof(double2) * MM), "modes U");
+    CK(cudaMalloc((void **)&ld.A, sizeof(double2) * MM), "modes A");
+    CK(cudaMemcpy(ld.A, ld.H0, sizeof(double2) * MM, cudaMemcpyDeviceToDevice), "modes copy");
+    CK(knit_launch_jacobi(ld.A, ld.U, s->M, nullptr, 0), "jacobi launch");
+    CK(cudaStreamSynchronize(0), "jacobi");
+    ld.modes_ready = 1;
+    return KNIT_OK;
+}
+
+int resolve_method(const knit_system s, int p, const knit_lead_opts *o)
+{
+    int m = o ? o->method : KNIT_LEAD_AUTO;
+    if (m == KNIT_LEAD_AUTO) m = s->lead[p].scalar ? KNIT_LEAD_MODES : KNIT_LEAD_DECIMATION;
+    return m;
+}
+
+// Sigma_p at nE device energies into sig (and g into gout), per-energy status into lst
+knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
+                          const knit_lead_opts *o, double2 *sig, double2 *gout, int *lst,
+                          int *lit, cudaStream_t st)
+{
+    const int M = s->M;
+    const int method = resolve_method(s, p, o);
+    const int grid = std::min(nE, s->nsm * 4);
+    if (method == KNIT_LEAD_MODES) {
+        if (!s->lead[p].scalar)
+            return fail(KNIT_ERR_INVALID, "lead %d: MODES needs lead_V = t * identity", p);
+        knit_status r = ensure_modes(s, p);
+        if (r != KNIT_OK) return r;
+        CK(knit_launch_modes_sigma(s->lead[p].U, s->lead[p].A, M, s->lead[p].t2, dE, nE, sig,
+                                   gout, grid, st),
+           "modes sigma");
+        if (lst) CK(cudaMemsetAsync(lst, 0, sizeof(int) * nE, st), "lead status");
+        if (lit) CK(cudaMemsetAsync(lit, 0, sizeof(int) * nE, st), "lead iters");
+        return KNIT_OK;
+    }
+    if (method != KNIT_LEAD_DECIMATION) return fail(KNIT_ERR_INVALID, "unknown lead method %d", method);
+    double eta = (o && o->eta > 0) ? o->eta : 1e-12;
+    double tol = (o && o->tol > 0) ? o->tol : 1e-14;
+    int maxit = (o && o->maxit > 0) ? o->maxit : 200;
+    const size_t MM = (size_t)M * M;
+    CK(s->decw.ensure(sizeof(double2) * 8 * MM * grid), "decimation workspace");
+    CK(knit_launch_decimation(s->lead[p].H0, s->lead[p].V, M, s->lead[p].vb, p, dE, nE, eta, tol,
+                              maxit, s->decw.as<double2>(), sig, gout, lit, lst, grid, st),
+       "decimation");
+    return KNIT_OK;
+}
+
+knit_status check_system(knit_system s)
+{
+    if (!s) return fail(KNIT_ERR_INVALID, "NULL system");
+    CK(cudaSetDevice(s->device), "cudaSetDevice");
+    return KNIT_OK;
+}
+
+// Sigma_L / Sigma_R for the energies in dE; combined per-energy status in s->lst
+knit_status both_sigmas(knit_system s, const double *dE, int nE, const knit_lead_opts *o,
+                        cudaStream_t st, const double2 **sL, const double2 **sR, const int **lst)
+{
+    const size_t MM = (size_t)s->M * s->M;
+    CK(s->sigL.ensure(sizeof(double2) * MM * nE), "sigma workspace");
+    CK(s->gL.ensure(sizeof(double2) * MM * nE), "g workspace");
+    CK(s->lst.ensure(sizeof(int) * 2 * nE), "lead status");
+    int *st0 = s->lst.as<int>(), *st1 = st0 + nE;
+    knit_status r = compute_sigma(s, 0, dE, nE, o, s->sigL.as<double2>(), s->gL.as<double2>(),
+                                  st0, nullptr, st);
+    if (r != KNIT_OK) return r;
+    *sL = s->sigL.as<double2>();
+    if (s->leads_same && s->lead[0].scalar && resolve_method(s, 1, o) == KNIT_LEAD_MODES) {
+        *sR = *sL;    // V = t I and identical cells: Sigma_R = Sigma_L
+        CK(cudaMemsetAsync(st1, 0, sizeof(int) * nE, st), "lead status");
+    } else {
+        CK(s->sigR.ensure(sizeof(double2) * MM * nE), "sigma workspace");
+        CK(s->gR.ensure(sizeof(double2) * MM * nE), "g workspace");
+        r = compute_sigma(s, 1, dE, nE, o, s->sigR.as<double2>(), s->gR.as<double2>(), st1,
+                          nullptr, st);
+        if (r != KNIT_OK) return r;
+        *sR = s->sigR.as<double2>();
+    }
+    *lst = st0;   // the sweep reads st0[e] | st1[e] through the combined array below
+    return KNIT_OK;
+}
+
+__global__ void combine_status(int *a, const int *b, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && a[i] == 0) a[i] = b[i];
+}
+
+knit_status run_sweep(knit_system s, InstDev in, int precision, cudaStream_t st)
+{
+    SysDev sd = s->dev();
+    CK(s->queue.ensure(sizeof(int)), "queue");
+    in.queue = s->queue.as<int>();
+    CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
+    const int grid = std::max(1, std::min(in.n, s->nsm));
+    if (precision == KNIT_MIXED) {
+        CK(knit_launch_mixed(&sd, &in, grid, st), "mixed sweep launch");
+        return KNIT_OK;
+    }
+    const size_t MM = (size_t)s->M * s->M;
+    int use_smem = knit_fp64_smem_bytes(s->M, 1, 3) <= 220 * 1024;
+    if (!use_smem) CK(s->work.ensure(sizeof(double2) * 3 * MM * grid), "sweep workspace");
+    CK(knit_launch_sweep_fp64(&sd, &in, grid, s->work.as<double2>(), use_smem, st),
+       "fp64 sweep launch");
+    return KNIT_OK;
+}
+
+knit_status check_batch(knit_system s, const double *E, int nE, int nS, int precision, double W)
+{
+    if (!E) return fail(KNIT_ERR_INVALID, "E is NULL");
+    if (nE <= 0 || nS <= 0) return fail(KNIT_ERR_INVALID, "nE and nS must be positive");
+    if ((long long)nE * nS > 0x7fffffffLL) return fail(KNIT_ERR_INVALID, "nE * nS too large");
+    if (!std::isfinite(W)) return fail(KNIT_ERR_INVALID, "W is not finite");
+    if (precision != KNIT_FP64 && precision != KNIT_MIXED)
+        return fail(KNIT_ERR_INVALID, "unknown precision %d", precision);
+    if (precision == KNIT_MIXED) {
+        if (s->M > knit_mixed_max_M())
+            return fail(KNIT_ERR_INVALID, "KNIT_MIXED supports M <= %d (M = %d)", knit_mixed_max_M(),
+                        s->M);
+        if (s->vb != 1) return fail(KNIT_ERR_INVALID, "KNIT_MIXED needs diagonal inter-slice V");
+    }
+    return KNIT_OK;
+}
+
+knit_status finish(cudaStream_t st, bool sync, const char *what)
+{
+    CK(cudaGetLastError(), what);
+    if (sync) CK(cudaStreamSynchronize(st), what);
+    return KNIT_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *knit_last_error(void) { return g_err.c_str(); }
+
+const char *knit_version(void) { return "knit-gb300 0.1 (sm_103a)"; }
+
+knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
+{
+    if (!d || !out) return fail(KNIT_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    const int M = d->M, L = d->L, B = d->block, P = d->Vperiod;
+    if (M < 1 || M > 256) return fail(KNIT_ERR_INVALID, "M = %d out of range [1, 256]", M);
+    if (L < 1) return fail(KNIT_ERR_INVALID, "L = %d must be >= 1", L);
+    if (B != 1 && B != 2 && B != 4) return fail(KNIT_ERR_INVALID, "block must be 1, 2 or 4");
+    if (M % B) return fail(KNIT_ERR_INVALID, "M must be a multiple of block");
+    if (P != 1 && P != 2) return fail(KNIT_ERR_INVALID, "Vperiod must be 1 or 2");
+    if (!d->H0 || !d->V) return fail(KNIT_ERR_INVALID, "H0 and V are required");
+    const size_t MM = (size_t)M * M;
+    std::vector<double2> H0, V, sign, onsite_dummy;
+    std::vector<double> hs, hon;
+    knit_status r;
+    if ((r = to_host(H0, d->H0, MM, "H0")) != KNIT_OK) return r;
+    if ((r = to_host(V, d->V, MM * P, "V")) != KNIT_OK) return r;
+    if (!hermitian(H0.data(), M)) return fail(KNIT_ERR_INVALID, "H0 is not Hermitian");
+    int vb = 1;
+    for (int q = 0; q < P; ++q) {
+        int b = block_structure(V.data() + q * MM, M, B);
+        if (b == 0) return fail(KNIT_ERR_INVALID, "V[%d] is not block-diagonal with %dx%d blocks", q, B, B);
+        vb = std::max(vb, b);
+    }
+    hs.assign(B, 1.0);
+    if (d->onsite_sign && (r = to_host(hs, d->onsite_sign, B, "onsite_sign")) != KNIT_OK) return r;
+    if (d->onsite && (r = to_host(hon, d->onsite, (size_t)L * M, "onsite")) != KNIT_OK) return r;
+    for (double v : hon)
+        if (!std::isfinite(v)) return fail(KNIT_ERR_INVALID, "onsite has non-finite values");
+
+    knit_system s = new (std::nothrow) knit_system_s;
+    if (!s) return fail(KNIT_ERR_OOM, "host allocation");
+    s->M = M;
+    s->L = L;
+    s->block = B;
+    s->Vperiod = P;
+    s->vb = vb;
+    cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
+    // sparse rows of H0 for the mixed residual
+    std::vector<int> rp(M + 1, 0), cols;
+    std::vector<double2> vals;
+    for (int i = 0; i < M; ++i) {
+        for (int j = 0; j < M; ++j) {
+            double2 v = H0[(size_t)i * M + j];
+            if (v.x != 0.0 || v.y != 0.0) {
+                cols.push_back(j);
+                vals.push_back(v);
+            }
+        }
+        rp[i + 1] = (int)cols.size();
+    }
+    for (int p = 0; p < 2; ++p) {
+        Lead &ld = s->lead[p];
+        const void *hsrc = d->lead_H0[p] ? (const void *)d->lead_H0[p] : (const void *)d->H0;
+        const void *vsrc = d->lead_V[p] ? (const void *)d->lead_V[p] : (const void *)d->V;
+        if ((r = to_host(ld.hH0, hsrc, MM, "lead_H0")) != KNIT_OK ||
+            (r = to_host(ld.hV, vsrc, MM, "lead_V")) != KNIT_OK) {
+            knit_system_destroy(s);
+            return r;
+        }
+        if (!hermitian(ld.hH0.data(), M)) {
+            knit_system_destroy(s);
+            return fail(KNIT_ERR_INVALID, "lead_H0[%d] is not Hermitian", p);
+        }
+        int b = block_structure(ld.hV.data(), M, B);
+        ld.vb = b == 0 ? M : b;   // dense coupling allowed for the decimation solver
+        ld.scalar = scalar_identity(ld.hV.data(), M, &ld.t2);
+    }
+    s->leads_same = std::equal(s->lead[0].hH0.begin(), s->lead[0].hH0.end(), s->lead[1].hH0.begin(),
+                               [](double2 a, double2 b) { return a.x == b.x && a.y == b.y; }) &&
+                    std::equal(s->lead[0].hV.begin(), s->lead[0].hV.end(), s->lead[1].hV.begin(),
+                               [](double2 a, double2 b) { return a.x == b.x && a.y == b.y; });
+    if ((r = to_device(&s->H0, H0.data(), MM, "H0")) != KNIT_OK ||
+        (r = to_device(&s->V, V.data(), MM * P, "V")) != KNIT_OK ||
+        (r = to_device(&s->sign, hs.data(), (size_t)B, "sign")) != KNIT_OK ||
+        (r = to_device(&s->h0_rowptr, rp.data(), rp.size(), "H0 rows")) != KNIT_OK ||
+        (r = to_device(&s->h0_col, cols.data(), cols.size(), "H0 cols")) != KNIT_OK ||
+        (r = to_device(&s->h0_val, vals.data(), vals.size(), "H0 vals")) != KNIT_OK) {
+        knit_system_destroy(s);
+        return r;
+    }
+    if (d->onsite && (r = to_device(&s->onsite, hon.data(), hon.size(), "onsite")) != KNIT_OK) {
+        knit_system_destroy(s);
+        return r;
+    }
+    for (int p = 0; p < 2; ++p) {
+        Lead &ld = s->lead[p];
+        if ((r = to_device(&ld.H0, ld.hH0.data(), MM, "lead_H0")) != KNIT_OK ||
+            (r = to_device(&ld.V, ld.hV.data(), MM, "lead_V")) != KNIT_OK) {
+            knit_system_destroy(s);
+            return r;
+        }
+    }
+    *out = s;
+    return KNIT_OK;
+}
+
+knit_status knit_system_destroy(knit_system s)
+{
+    if (!s) return KNIT_OK;
+    cudaSetDevice(s->device);
+    cudaFree(s->H0);
+    cudaFree(s->V);
+    cudaFree(s->sign);
+    cudaFree(s->onsite);
+    cudaFree(s->h0_rowptr);
+    cudaFree(s->h0_col);
+    cudaFree(s->h0_val);
+    for (int p = 0; p < 2; ++p) {
+        cudaFree(s->lead[p].H0);
+        cudaFree(s->lead[p].V);
+        cudaFree(s->lead[p].U);
+        cudaFree(s->lead[p].A);
+    }
+    DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
+                      &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos};
+    for (DevBuf *b : bufs) b->release();
+    delete s;
+    return KNIT_OK;
+}
+
+knit_status knit_lead_selfenergy(knit_system s, int32_t lead, const double *E, int32_t nE,
+                                 const knit_lead_opts *opts, knit_c128 *sigma, int32_t *iters,
+                                 double *residual, void *stream)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if (lead != 0 && lead != 1) return fail(KNIT_ERR_INVALID, "lead must be 0 or 1");
+    if (!E || nE <= 0 || !sigma) return fail(KNIT_ERR_INVALID, "E, nE and sigma are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t MM = (size_t)s->M * s->M;
+    const double *dE;
+    if ((r = stage_in(s->E, E, (size_t)nE, st, &dE, "E")) != KNIT_OK) return r;
+    double2 *dS;
+    bool hS;
+    if ((r = stage_out(s->sigL, (double2 *)sigma, MM * nE, &dS, &hS, "sigma")) != KNIT_OK) return r;
+    CK(s->gL.ensure(sizeof(double2) * MM * nE), "g workspace");
+    CK(s->lit.ensure(sizeof(int) * nE * 2), "iterations");
+    int *dIt = s->lit.as<int>(), *dSt = dIt + nE;
+    if ((r = compute_sigma(s, lead, dE, nE, opts, dS, s->gL.as<double2>(), dSt, dIt, st)) != KNIT_OK)
+        return r;
+    bool sync = hS;
+    if (hS) CK(cudaMemcpyAsync(sigma, dS, sizeof(double2) * MM * nE, cudaMemcpyDeviceToHost, st), "sigma out");
+    if (iters) {
+        if (is_device_ptr(iters)) {
+            CK(cudaMemcpyAsync(iters, dIt, sizeof(int) * nE, cudaMemcpyDeviceToDevice, st), "iters");
+        } else {
+            CK(cudaMemcpyAsync(iters, dIt, sizeof(int) * nE, cudaMemcpyDeviceToHost, st), "iters");
+            sync = true;
+        }
+    }
+    if (residual) {
+        const int grid = std::min(nE, s->nsm * 4);
+        CK(s->decw.ensure(sizeof(double2) * MM * grid), "residual workspace");
+        CK(s->lres.ensure(sizeof(double) * nE), "residual");
+        CK(knit_launch_lead_residual(s->lead[lead].H0, s->lead[lead].V, s->M, s->lead[lead].vb, lead,
+                                     dE, nE, s->gL.as<double2>(), s->decw.as<double2>(),
+                                     s->lres.as<double>(), grid, st),
+           "lead residual");
+        bool hr = !is_device_ptr(residual);
+        CK(cudaMemcpyAsync(residual, s->lres.p, sizeof(double) * nE,
+                           hr ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st),
+           "residual out");
+        sync = sync || hr;
+    }
+    return finish(st, sync, "knit_lead_selfenergy");
+}
+
+static knit_status transmission_impl(knit_system s, const double *E, int32_t nE,
+                                     const uint64_t *seeds, int32_t nS, double W,
+                                     const knit_c128 *sigmaL, const knit_c128 *sigmaR,
+                                     int32_t precision, const knit_lead_opts *opts, double *T,
+                                     int32_t *status, void *stream)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if ((r = check_batch(s, E, nE, nS, precision, W)) != KNIT_OK) return r;
+    if (!T) return fail(KNIT_ERR_INVALID, "T is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t MM = (size_t)s->M * s->M;
+    const int n = nE * nS;
+    InstDev in{};
+    in.n = n;
+    in.nS = nS;
+    in.W = W;
+    if ((r = stage_in(s->E, E, (size_t)nE, st, &in.E, "E")) != KNIT_OK) return r;
+    if ((r = stage_in(s->seeds, seeds, (size_t)nS, st, &in.seeds, "seeds")) != KNIT_OK) return r;
+    if (sigmaL) {
+        const double2 *a, *b;
+        if ((r = stage_in(s->sigL, (const double2 *)sigmaL, MM * nE, st, &a, "sigmaL")) != KNIT_OK ||
+            (r = stage_in(s->sigR, (const double2 *)sigmaR, MM * nE, st, &b, "sigmaR")) != KNIT_OK)
+            return r;
+        in.sigL = a;
+        in.sigR = b;
+        in.lstatus = nullptr;
+    } else {
+        const int *lst;
+        if ((r = both_sigmas(s, in.E, nE, opts, st, &in.sigL, &in.sigR, &lst)) != KNIT_OK) return r;
+        int *l0 = s->lst.as<int>();
+        combine_status<<<(nE + 255) / 256, 256, 0, st>>>(l0, l0 + nE, nE);
+        CK(cudaGetLastError(), "status combine");
+        in.lstatus = l0;
+    }
+    bool hT, hSt = false;
+    if ((r = stage_out(s->T, T, (size_t)n, &in.T, &hT, "T")) != KNIT_OK) return r;
+    if ((r = stage_out(s->status, (int *)status, (size_t)n, &in.status, &hSt, "status")) != KNIT_OK)
+        return r;
+    if ((r = run_sweep(s, in, precision, st)) != KNIT_OK) return r;
+    if (hT) CK(cudaMemcpyAsync(T, in.T, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
+    if (hSt)
+        CK(cudaMemcpyAsync(status, in.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
+    return finish(st, hT || hSt, "knit_transmission");
+}
+
+knit_status knit_transmission(knit_system s, const double *E, int32_t nE, const uint64_t *seeds,
+                              int32_t nS, double W, int32_t precision,
+                              const knit_lead_opts *opts, double *T, int32_t *status, void *stream)
+{
+    return transmission_impl(s, E, nE, seeds, nS, W, nullptr, nullptr, precision, opts, T, status,
+                             stream);
+}
+
+knit_status knit_transmission_sigma(knit_system s, const double *E, int32_t nE,
+                                    const uint64_t *seeds, int32_t nS, double W,
+                                    const knit_c128 *sigmaL, const knit_c128 *sigmaR,
+                                    int32_t precision, double *T, int32_t *status, void *stream)
+{
+    if (!sigmaL || !sigmaR) return fail(KNIT_ERR_INVALID, "sigmaL and sigmaR are required");
+    return transmission_impl(s, E, nE, seeds, nS, W, sigmaL, sigmaR, precision, nullptr, T, status,
+                             stream);
+}
+
+knit_status knit_ldos(knit_system s, const double *E, int32_t nE, const uint64_t *seeds,
+                      int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
+                      double *ldos, double *T, int32_t *status, void *stream)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if ((r = check_batch(s, E, nE, nS, KNIT_FP64, W)) != KNIT_OK) return r;
+    if (!ldos) return fail(KNIT_ERR_INVALID, "ldos is NULL");
+    if (saving_level == 0)
+        return fail(KNIT_ERR_INVALID, "saving_level 0 keeps nothing: no local observables");
+    if (saving_level < -1) return fail(KNIT_ERR_INVALID, "saving_level must be -1 or >= 1");
+    const int save = saving_level == -1 ? 1 : std::min(saving_level, s->L);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t MM = (size_t)s->M * s->M;
+    const int n = nE * nS;
+    InstDev in{};
+    in.n = n;
+    in.nS = nS;
+    in.W = W;
+    if ((r = stage_in(s->E, E, (size_t)nE, st, &in.E, "E")) != KNIT_OK) return r;
+    if ((r = stage_in(s->seeds, seeds, (size_t)nS, st, &in.seeds, "seeds")) != KNIT_OK) return r;
+    const int *lst;
+    if ((r = both_sigmas(s, in.E, nE, opts, st, &in.sigL, &in.sigR, &lst)) != KNIT_OK) return r;
+    int *l0 = s->lst.as<int>();
+    combine_status<<<(nE + 255) / 256, 256, 0, st>>>(l0, l0 + nE, nE);
+    in.lstatus = l0;
+    bool hL, hT = false, hSt = false;
+    double *dL;
+    if ((r = stage_out(s->ldos, ldos, (size_t)n * s->L * s->M, &dL, &hL, "ldos")) != KNIT_OK) return r;
+    if ((r = stage_out(s->T, T, (size_t)n, &in.T, &hT, "T")) != KNIT_OK) return r;
+    if ((r = stage_out(s->status, (int *)status, (size_t)n, &in.status, &hSt, "status")) != KNIT_OK)
+        return r;
+    SysDev sd = s->dev();
+    CK(s->queue.ensure(sizeof(int)), "queue");
+    in.queue = s->queue.as<int>();
+    CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
+    const int grid = std::max(1, std::min(n, s->nsm));
+    int use_smem = knit_fp64_smem_bytes(s->M, 1, 4) <= 220 * 1024;
+    if (!use_smem) CK(s->work.ensure(sizeof(double2) * 4 * MM * grid), "ldos workspace");
+    const int nck = (s->L + save - 1) / save;
+    CK(s->ckpt.ensure(sizeof(double2) * MM * (size_t)(nck + save) * grid), "checkpoint workspace");
+    CK(knit_launch_ldos_fp64(&sd, &in, grid, s->work.as<double2>(), use_smem, s->ckpt.as<double2>(),
+                             save, dL, st),
+       "ldos launch");
+    if (hL) CK(cudaMemcpyAsync(ldos, dL, sizeof(double) * n * s->L * s->M, cudaMemcpyDeviceToHost, st), "ldos out");
+    if (hT) CK(cudaMemcpyAsync(T, in.T, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
+    if (hSt)
+        CK(cudaMemcpyAsync(status, in.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
+    return finish(st, hL || hT || hSt, "knit_ldos");
+}
+
+}  // extern "C"

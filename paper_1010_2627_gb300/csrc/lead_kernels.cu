@@ -1,0 +1,378 @@
+// lead_kernels.cu -- lead surface Green functions and self-energies in FP64
+// (KNIT user guide Sec. 5.3 B: a lead is the semi-infinite repetition of its
+// interface cell H0 with inter-cell hopping V; the hopping to the system is
+// the same V).  Left lead: g = (E - H0 - V g V^dagger)^{-1}, Sigma = V g V^dagger;
+// right lead: g = (E - H0 - V^dagger g V)^{-1}, Sigma = V^dagger g V.
+//
+//  * knit_jacobi_kernel: eigen-decomposition H0 = U diag(w) U^dagger of a
+//    Hermitian cell by parallel cyclic Jacobi rotations (one CTA, once per
+//    lead).  For V = t I every transverse mode k is a 1D chain with the
+//    retarded surface function g_k = (x - i sqrt(4|t|^2 - x^2)) / (2|t|^2),
+//    x = E - w_k, inside the band and (x - sgn(x) sqrt(x^2 - 4|t|^2)) / (2|t|^2)
+//    outside; knit_modes_sigma_kernel assembles Sigma = |t|^2 U diag(g_k) U^dagger.
+//  * knit_decimation_kernel: Sancho-Rubio decimation (Lopez Sancho, Lopez
+//    Sancho & Rubio 1985) at E + i eta for general cells, one CTA per energy.
+//  * knit_lead_residual_kernel: max-norm of g - (E - H0 - V g V^dagger)^{-1}
+//    at eta = 0, the fixed-point check of either solver.
+
+#include "dense_fp64.cuh"
+
+// ---------------------------------------------------------------------------
+// A (M x M, Hermitian) -> diag in A, eigenvectors in U (global memory).
+extern "C" __global__ void __launch_bounds__(256)
+knit_jacobi_kernel(double2 *A, double2 *U, int M, int max_sweeps, double tol, int *sweeps_out)
+{
+    __shared__ double rc[128], rs[128];
+    __shared__ double2 rph[128];
+    __shared__ int rp[128], rq[128];
+    __shared__ double red[8];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int Me = M + (M & 1);   // even count with a dummy index M for odd M
+    const int npair = Me / 2;
+    for (int e = tid; e < M * M; e += nt) {
+        int i = e / M, j = e - i * M;
+        U[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, dia = 0.0;
+        for (int e = tid; e < M * M; e += nt) {
+            int i = e / M, j = e - i * M;
+            double v = fabs(A[e].x) + fabs(A[e].y);
+            if (i != j) off = fmax(off, v);
+            else dia = fmax(dia, v);
+        }
+        // block max via shared memory
+        for (int o = 16; o > 0; o >>= 1) {
+            off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
+            dia = fmax(dia, __shfl_xor_sync(0xffffffffu, dia, o));
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = off;
+        __syncthreads();
+        double offm = 0.0;
+        for (int w = 0; w < nt / 32; ++w) offm = fmax(offm, red[w]);
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = dia;
+        __syncthreads();
+        double diam = 0.0;
+        for (int w = 0; w < nt / 32; ++w) diam = fmax(diam, red[w]);
+        __syncthreads();
+        if (offm <= tol * fmax(diam, 1e-300) || offm == 0.0) break;
+        for (int r = 0; r < Me - 1; ++r) {
+            // round-robin pairing: slot 0 fixed, slots 1..Me-1 rotate by r
+            for (int t = tid; t < npair; t += nt) {
+                int a = t == 0 ? 0 : 1 + (t - 1 + r) % (Me - 1);
+                int bslot = Me - 1 - t;
+                int b = 1 + (bslot - 1 + r) % (Me - 1);
+                int p = min(a, b), q = max(a, b);
+                double c = 1.0, sn = 0.0;
+                double2 ph = make_double2(1.0, 0.0);
+                if (q < M) {
+                    double2 apq = A[(size_t)p * M + q];
+                    double rr = hypot(apq.x, apq.y);
+                    if (rr > 0.0) {
+                        ph = make_double2(apq.x / rr, apq.y / rr);
+                        double tau = (A[(size_t)q * M + q].x - A[(size_t)p * M + p].x) / (2.0 * rr);
+                        double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        sn = tt * c;
+                    }
+                }
+                rp[t] = p;
+                rq[t] = q;
+                rc[t] = c;
+                rs[t] = sn;
+                rph[t] = ph;
+            }
+            __syncthreads();
+            // columns: A <- A W, U <- U W with W = [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
+            for (int e = tid; e < npair * M; e += nt) {
+                int t = e / M, i = e - t * M;
+                int p = rp[t], q = rq[t];
+                if (q >= M) continue;
+                double c = rc[t], sn = rs[t];
+                double2 phc = cconj(rph[t]);
+                for (int w = 0; w < 2; ++w) {
+                    double2 *X = w == 0 ? A : U;
+                    double2 xp = X[(size_t)i * M + p], xq = X[(size_t)i * M + q];
+                    double2 xqp = cmul(phc, xq);
+                    X[(size_t)i * M + p] = make_double2(c * xp.x - sn * xqp.x, c * xp.y - sn * xqp.y);
+                    X[(size_t)i * M + q] = make_double2(sn * xp.x + c * xqp.x, sn * xp.y + c * xqp.y);
+                }
+            }
+            __syncthreads();
+            // rows: A <- W^dagger A
+            for (int e = tid; e < npair * M; e += nt) {
+                int t = e / M, j = e - t * M;
+                int p = rp[t], q = rq[t];
+                if (q >= M) continue;
+                double c = rc[t], sn = rs[t];
+                double2 ph = rph[t];
+                double2 ap = A[(size_t)p * M + j], aq = A[(size_t)q * M + j];
+                double2 aqp = cmul(ph, aq);
+                A[(size_t)p * M + j] = make_double2(c * ap.x - sn * aqp.x, c * ap.y - sn * aqp.y);
+                A[(size_t)q * M + j] = make_double2(sn * ap.x + c * aqp.x, sn * ap.y + c * aqp.y);
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// ---------------------------------------------------------------------------
+// Sigma(E_e) = |t|^2 U diag(g_k(E_e - w_k)) U^dagger, one CTA per energy (grid-stride)
+extern "C" __global__ void __launch_bounds__(256)
+knit_modes_sigma_kernel(const double2 *U, const double2 *Adiag, int M, double t2, const double *E,
+                        int nE, double2 *sigma, double2 *gout)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *gk = reinterpret_cast<double2 *>(smem_raw);
+    for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+        const double En = E[e];
+        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+            double x = En - Adiag[(size_t)k * M + k].x;
+            double b = 4.0 * t2;
+            double2 g;
+            if (x * x < b) g = make_double2(x / (2.0 * t2), -sqrt(b - x * x) / (2.0 * t2));
+            else g = make_double2((x - copysign(sqrt(x * x - b), x)) / (2.0 * t2), 0.0);
+            gk[k] = g;
+        }
+        __syncthreads();
+        double2 *S = sigma + (size_t)e * M * M;
+        double2 *G = gout ? gout + (size_t)e * M * M : nullptr;
+        for (int q = threadIdx.x; q < M * M; q += blockDim.x) {
+            int i = q / M, j = q - i * M;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < M; ++k)
+                acc = cfma(cmul(U[(size_t)i * M + k], gk[k]), cconj(U[(size_t)j * M + k]), acc);
+            S[q] = cscale(acc, t2);
+            if (G) G[q] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sancho-Rubio decimation, one CTA per energy (grid-stride).  side 0: alpha = V
+// (surface -> next cell outward), beta = V^dagger; side 1: the reverse.
+// work: per CTA 8 M*M complex.  Outputs Sigma, g, iterations, status.
+extern "C" __global__ void __launch_bounds__(256)
+knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int side, const double *E,
+                       int nE, double eta, double tol, int maxit, double2 *work, double2 *sigma,
+                       double2 *gout, int *iters, int *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GJScratch64 sc;
+    unsigned char *p = smem_raw;
+    sc.row = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2) * M;
+    sc.col = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2) * M;
+    sc.pval = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2);
+    double *red = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 32;
+    sc.perm = reinterpret_cast<int *>(p);
+    p += sizeof(int) * M;
+    sc.flag = reinterpret_cast<int *>(p);
+    p += sizeof(int);
+    sc.piv = reinterpret_cast<int *>(p);
+
+    const size_t MM = (size_t)M * M;
+    double2 *w = work + (size_t)blockIdx.x * 8 * MM;
+    double2 *eps = w, *eps_s = w + MM, *al = w + 2 * MM, *be = w + 3 * MM;
+    double2 *gb = w + 4 * MM, *t1 = w + 5 * MM, *t2 = w + 6 * MM, *t3 = w + 7 * MM;
+    for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+        const double2 z = make_double2(E[e], eta);
+        for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+            int i = q / M, j = q - i * M;
+            double2 v = V[q], vd = cconj(V[(size_t)j * M + i]);
+            eps[q] = H0[q];
+            eps_s[q] = H0[q];
+            al[q] = side == 0 ? v : vd;
+            be[q] = side == 0 ? vd : v;
+        }
+        __syncthreads();
+        int it = 0, st = ST_NOCONVERGE;
+        for (it = 0; it < maxit; ++it) {
+            double na = 0.0, nb = 0.0;
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                na = fmax(na, hypot(al[q].x, al[q].y));
+                nb = fmax(nb, hypot(be[q].x, be[q].y));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                na = fmax(na, __shfl_xor_sync(0xffffffffu, na, o));
+                nb = fmax(nb, __shfl_xor_sync(0xffffffffu, nb, o));
+            }
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = na + 0.0 * nb;
+            if ((threadIdx.x & 31) == 0) red[16 + (threadIdx.x >> 5)] = nb;
+            __syncthreads();
+            double mna = 0.0, mnb = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                mna = fmax(mna, red[q]);
+                mnb = fmax(mnb, red[16 + q]);
+            }
+            __syncthreads();
+            if (mna + mnb < tol) { st = ST_OK; break; }
+            if (!isfinite(mna + mnb)) break;
+            // gb = (z - eps)^{-1}
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                int i = q / M, j = q - i * M;
+                double2 v = make_double2(-eps[q].x, -eps[q].y);
+                if (i == j) v = cadd(v, z);
+                gb[q] = v;
+            }
+            __syncthreads();
+            if (gj_invert64(gb, M, sc) != ST_OK) { st = ST_SINGULAR; break; }
+            gemm64(gb, be, t1, M);    // gb beta
+            gemm64(gb, al, t2, M);    // gb alpha
+            gemm64(al, t1, t3, M);    // alpha gb beta
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                eps_s[q] = cadd(eps_s[q], t3[q]);
+                eps[q] = cadd(eps[q], t3[q]);
+            }
+            __syncthreads();
+            gemm64(be, t2, t3, M);    // beta gb alpha
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) eps[q] = cadd(eps[q], t3[q]);
+            __syncthreads();
+            gemm64(al, t2, t3, M);    // alpha gb alpha -> new alpha (after beta update)
+            gemm64(be, t1, t2, M);    // beta gb beta
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                al[q] = t3[q];
+                be[q] = t2[q];
+            }
+            __syncthreads();
+        }
+        double2 *S = sigma + (size_t)e * MM;
+        double2 *G = gout + (size_t)e * MM;
+        if (st == ST_OK) {
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                int i = q / M, j = q - i * M;
+                double2 v = make_double2(-eps_s[q].x, -eps_s[q].y);
+                if (i == j) v = cadd(v, z);
+                G[q] = v;
+            }
+            __syncthreads();
+            if (gj_invert64(G, M, sc) != ST_OK) st = ST_SINGULAR;
+        }
+        if (st == ST_OK) {
+            // Sigma = alpha0 g beta0: left V g V^dagger, right V^dagger g V
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                int i = q / M, j = q - i * M;
+                S[q] = side == 0 ? vxvd64(V, G, M, vb, i, j) : vdxv64(V, G, M, vb, i, j);
+            }
+        } else {
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x)
+                S[q] = make_double2(nan(""), nan(""));
+        }
+        if (threadIdx.x == 0) {
+            if (iters) iters[e] = it;
+            if (status) status[e] = st;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// residual[e] = max |g - (E - H0 - V g V^dagger)^{-1}| (side 0) or with
+// V^dagger g V (side 1), at eta = 0.  work: per CTA 1 M*M complex.
+extern "C" __global__ void __launch_bounds__(256)
+knit_lead_residual_kernel(const double2 *H0, const double2 *V, int M, int vb, int side, const double *E,
+                          int nE, const double2 *g, double2 *work, double *residual)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GJScratch64 sc;
+    unsigned char *p = smem_raw;
+    sc.row = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2) * M;
+    sc.col = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2) * M;
+    sc.pval = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2);
+    double *red = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 32;
+    sc.perm = reinterpret_cast<int *>(p);
+    p += sizeof(int) * M;
+    sc.flag = reinterpret_cast<int *>(p);
+    p += sizeof(int);
+    sc.piv = reinterpret_cast<int *>(p);
+    const size_t MM = (size_t)M * M;
+    double2 *A = work + (size_t)blockIdx.x * MM;
+    for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+        const double2 *ge = g + (size_t)e * MM;
+        for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+            int i = q / M, j = q - i * M;
+            double2 s = side == 0 ? vxvd64(V, ge, M, vb, i, j) : vdxv64(V, ge, M, vb, i, j);
+            double2 v = csub(make_double2(-H0[q].x, -H0[q].y), s);
+            if (i == j) v.x += E[e];
+            A[q] = v;
+        }
+        __syncthreads();
+        double r = 0.0;
+        if (gj_invert64(A, M, sc) != ST_OK) {
+            r = INFINITY;
+        } else {
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                double2 d = csub(A[q], ge[q]);
+                r = fmax(r, hypot(d.x, d.y));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, red[q]);
+            residual[e] = m;
+        }
+        __syncthreads();
+    }
+}
+
+extern "C" size_t knit_gj_smem_bytes(int M)
+{
+    return (size_t)M * sizeof(double2) * 2 + sizeof(double2) + sizeof(double) * 32 +
+           sizeof(int) * (M + 2) + 64;
+}
+
+// host launch helpers used by the C-ABI implementation
+extern "C" cudaError_t knit_launch_jacobi(double2 *A, double2 *U, int M, int *sweeps,
+                                          cudaStream_t stream)
+{
+    knit_jacobi_kernel<<<1, 256, 0, stream>>>(A, U, M, 60, 1e-15, sweeps);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t knit_launch_modes_sigma(const double2 *U, const double2 *A, int M, double t2,
+                                               const double *E, int nE, double2 *sigma,
+                                               double2 *g, int grid, cudaStream_t stream)
+{
+    knit_modes_sigma_kernel<<<grid, 256, sizeof(double2) * M, stream>>>(U, A, M, t2, E, nE,
+                                                                         sigma, g);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t knit_launch_decimation(const double2 *H0, const double2 *V, int M, int vb,
+                                              int side, const double *E, int nE, double eta,
+                                              double tol, int maxit, double2 *work,
+                                              double2 *sigma, double2 *g, int *iters,
+                                              int *status, int grid, cudaStream_t stream)
+{
+    knit_decimation_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(
+        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t knit_launch_lead_residual(const double2 *H0, const double2 *V, int M, int vb,
+                                                 int side, const double *E, int nE,
+                                                 const double2 *g, double2 *work,
+                                                 double *residual, int grid, cudaStream_t stream)
+{
+    knit_lead_residual_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(H0, V, M, vb, side, E,
+                                                                            nE, g, work, residual);
+    return cudaGetLastError();
+}

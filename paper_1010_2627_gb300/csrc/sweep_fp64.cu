@@ -1,0 +1,297 @@
+// sweep_fp64.cu -- the slice sweep in complex128 (the plain FP64 path).
+//
+// One CTA walks one instance (energy, disorder seed) at a time and takes the
+// next instance from an atomic counter.  Per slice n (KNIT user guide
+// Sec. 5.3 D, knitting in slice form; Eq. 2 by block elimination):
+//     A_0 = E - H_0 - Sigma_L,   A_n = E - H_n - V_n g_{n-1} V_n^dagger (n >= 1),
+//     A_{L-1} additionally - Sigma_R,
+//     g_n = A_n^{-1}                                   (Gauss-Jordan, FP64)
+//     G_{0,0} = g_0,  G_{0,n} = G_{0,n-1} V_n^dagger g_n
+// and at the end the Sec. 2.3 transmission
+//     T = Re Tr[Gamma_L G_{0,L-1} Gamma_R G_{0,L-1}^dagger],  Gamma = i(Sigma - Sigma^dagger).
+// The LDOS kernel adds the sewing pass (Sec. 5.3 D):
+//     G_{L-1,L-1} = g_{L-1},  G_{n,n} = g_n + g_n V_{n+1}^dagger G_{n+1,n+1} V_{n+1} g_n,
+//     LDOS[n][x] = -Im G_{n,n}[x][x] / pi,
+// with the forward g_n kept every `save` slices (KNIT's saving_level) and
+// the slices in between recomputed segment by segment.
+//
+// Matrices live in shared memory when three (four for LDOS) M x M complex128
+// buffers fit, else in a per-CTA global workspace.
+
+#include "dense_fp64.cuh"
+
+namespace {
+
+struct Bufs {
+    double2 *P, *Q, *F, *X;
+    GJScratch64 gj;
+    double *red;
+};
+
+__device__ Bufs carve(const SysDev &s, double2 *work, int use_smem, int nbuf)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int M = s.M;
+    const size_t MM = (size_t)M * M;
+    Bufs b;
+    unsigned char *p = smem_raw;
+    double2 *mat;
+    if (use_smem) {
+        mat = reinterpret_cast<double2 *>(p);
+        p += sizeof(double2) * MM * nbuf;
+    } else {
+        mat = work + (size_t)blockIdx.x * MM * nbuf;
+    }
+    b.P = mat;
+    b.Q = mat + MM;
+    b.F = mat + 2 * MM;
+    b.X = nbuf > 3 ? mat + 3 * MM : nullptr;
+    b.gj.row = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2) * M;
+    b.gj.col = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2) * M;
+    b.gj.pval = reinterpret_cast<double2 *>(p);
+    p += sizeof(double2);
+    b.red = reinterpret_cast<double *>(p);
+    p += sizeof(double) * 32;
+    b.gj.perm = reinterpret_cast<int *>(p);
+    p += sizeof(int) * M;
+    b.gj.flag = reinterpret_cast<int *>(p);
+    p += sizeof(int);
+    b.gj.piv = reinterpret_cast<int *>(p);
+    return b;
+}
+
+// on-site energy of orbital x in slice n
+KNIT_DEV double onsite_at(const SysDev &s, uint64_t ms, double W, int n, int x)
+{
+    if (s.onsite) return s.onsite[(size_t)n * s.M + x];
+    if (W == 0.0) return 0.0;
+    return s.sign[x % s.block] * knit_disorder(ms, n, x / s.block, W);
+}
+
+// A = E - H_n - [Sigma_L | V_n gprev V_n^dagger] - [Sigma_R]
+__device__ void form_A(const SysDev &s, int n, double E, uint64_t ms, double W,
+                       const double2 *gprev, const double2 *SL, const double2 *SR, double2 *A)
+{
+    const int M = s.M, L = s.L;
+    const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * M * M;
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+        int i = e / M, j = e - i * M;
+        double2 h = s.H0[e];
+        double2 a = make_double2(-h.x, -h.y);
+        if (i == j) a.x += E - onsite_at(s, ms, W, n, i);
+        if (n == 0) a = csub(a, SL[e]);
+        else a = csub(a, vxvd64(Vn, gprev, M, s.vb, i, j));
+        if (n == L - 1) a = csub(a, SR[e]);
+        A[e] = a;
+    }
+    __syncthreads();
+}
+
+__device__ void copy_mat(const double2 *src, double2 *dst, int M)
+{
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) dst[e] = src[e];
+    __syncthreads();
+}
+
+__device__ int take_instance(int *queue, int *sh)
+{
+    if (threadIdx.x == 0) *sh = atomicAdd(queue, 1);
+    __syncthreads();
+    int v = *sh;
+    __syncthreads();
+    return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" __global__ void __launch_bounds__(256)
+knit_sweep_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem)
+{
+    __shared__ int sh_inst;
+    Bufs b = carve(s, work, use_smem, 3);
+    const int M = s.M, L = s.L;
+    const size_t MM = (size_t)M * M;
+    for (;;) {
+        const int inst = take_instance(in.queue, &sh_inst);
+        if (inst >= in.n) break;
+        const int ie = inst / in.nS;
+        const double E = in.E[ie];
+        const uint64_t ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
+        const double W = in.W;
+        const double2 *SL = in.sigL + (size_t)ie * MM;
+        const double2 *SR = in.sigR + (size_t)ie * MM;
+        double2 *P = b.P, *Q = b.Q, *F = b.F;   // P = g_{n-1}, Q = G_{0,n-1}, F free
+        int st = in.lstatus ? in.lstatus[ie] : ST_OK;
+        for (int n = 0; n < L && st == ST_OK; ++n) {
+            form_A(s, n, E, ms, W, P, SL, SR, F);
+            st = gj_invert64(F, M, b.gj);
+            if (st != ST_OK) break;
+            if (n == 0) {
+                copy_mat(F, Q, M);
+            } else {
+                const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
+                gemm64_avd_b(Q, Vn, s.vb, F, P, M);   // G_{0,n} = G_{0,n-1} V_n^dagger g_n
+                double2 *t = Q;
+                Q = P;
+                P = t;
+            }
+            double2 *t = P;   // g_n becomes the previous slice's function
+            P = F;
+            F = t;
+        }
+        double T = 0.0;
+        if (st == ST_OK) {
+            gemm64_gamma(Q, SR, F, M);     // G Gamma_R
+            gemm64_nc(F, Q, P, M);         // G Gamma_R G^dagger
+            T = trace_gamma64(SL, P, M, b.red);
+            if (!isfinite(T)) st = ST_NONFINITE;
+        }
+        if (threadIdx.x == 0) {
+            in.T[inst] = T;
+            if (in.status) in.status[inst] = st;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward sweep with checkpoints + sewing.  ckpt: per CTA ((L + save - 1)/save)
+// saved g's followed by `save` segment slots, M*M complex each.
+extern "C" __global__ void __launch_bounds__(256)
+knit_ldos_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem, double2 *ckpt, int save,
+                      double *ldos)
+{
+    __shared__ int sh_inst;
+    Bufs b = carve(s, work, use_smem, 4);
+    const int M = s.M, L = s.L;
+    const size_t MM = (size_t)M * M;
+    const int nck = (L + save - 1) / save;
+    double2 *cks = ckpt + (size_t)blockIdx.x * (nck + save) * MM;   // checkpoints
+    double2 *seg = cks + (size_t)nck * MM;                          // segment slots
+    for (;;) {
+        const int inst = take_instance(in.queue, &sh_inst);
+        if (inst >= in.n) break;
+        const int ie = inst / in.nS;
+        const double E = in.E[ie];
+        const uint64_t ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
+        const double W = in.W;
+        const double2 *SL = in.sigL + (size_t)ie * MM;
+        const double2 *SR = in.sigR + (size_t)ie * MM;
+        double *out = ldos + (size_t)inst * L * M;
+        double2 *P = b.P, *Q = b.Q, *F = b.F;
+        int st = in.lstatus ? in.lstatus[ie] : ST_OK;
+        // forward, keeping g_n for n % save == 0
+        for (int n = 0; n < L && st == ST_OK; ++n) {
+            form_A(s, n, E, ms, W, P, SL, SR, F);
+            st = gj_invert64(F, M, b.gj);
+            if (st != ST_OK) break;
+            if (n % save == 0) copy_mat(F, cks + (size_t)(n / save) * MM, M);
+            if (n == 0) {
+                copy_mat(F, Q, M);
+            } else {
+                const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
+                gemm64_avd_b(Q, Vn, s.vb, F, P, M);
+                double2 *t = Q;
+                Q = P;
+                P = t;
+            }
+            double2 *t = P;
+            P = F;
+            F = t;
+        }
+        double T = 0.0;
+        if (st == ST_OK) {
+            gemm64_gamma(Q, SR, F, M);
+            gemm64_nc(F, Q, b.X, M);
+            T = trace_gamma64(SL, b.X, M, b.red);
+            if (!isfinite(T)) st = ST_NONFINITE;
+        }
+        // sewing: G_nn in Q, walking n = L-1 .. 0
+        if (st == ST_OK) {
+            copy_mat(P, Q, M);   // P holds g_{L-1} = G_{L-1,L-1}
+            for (int x = threadIdx.x; x < M; x += blockDim.x)
+                out[(size_t)(L - 1) * M + x] = -Q[(size_t)x * M + x].y / 3.141592653589793;
+            int seg_lo = -1;   // first slice held in the segment slots
+            for (int n = L - 2; n >= 0 && st == ST_OK; --n) {
+                const double2 *gn;
+                if (n % save == 0) {
+                    gn = cks + (size_t)(n / save) * MM;
+                } else {
+                    const int c = (n / save) * save;
+                    if (seg_lo != c) {
+                        // recompute g_{c+1} .. g_{min(c+save, L)-1} from checkpoint g_c
+                        copy_mat(cks + (size_t)(c / save) * MM, P, M);
+                        const int hi = min(c + save, L);
+                        for (int m = c + 1; m < hi && m <= n; ++m) {
+                            form_A(s, m, E, ms, W, P, SL, SR, F);
+                            st = gj_invert64(F, M, b.gj);
+                            if (st != ST_OK) break;
+                            copy_mat(F, seg + (size_t)(m - c) * MM, M);
+                            double2 *t = P;
+                            P = F;
+                            F = t;
+                        }
+                        seg_lo = c;
+                        if (st != ST_OK) break;
+                    }
+                    gn = seg + (size_t)(n - c) * MM;
+                }
+                const double2 *Vn1 = s.V + (size_t)((n + 1) % s.Vperiod) * MM;
+                // F = V^dagger G_{n+1,n+1} V
+                for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+                    int i = e / M, j = e - i * M;
+                    F[e] = vdxv64(Vn1, Q, M, s.vb, i, j);
+                }
+                __syncthreads();
+                gemm64(gn, F, b.X, M);   // g_n V^dagger G V
+                gemm64(b.X, gn, Q, M);   // ... g_n
+                for (int e = threadIdx.x; e < M * M; e += blockDim.x) Q[e] = cadd(Q[e], gn[e]);
+                __syncthreads();
+                for (int x = threadIdx.x; x < M; x += blockDim.x)
+                    out[(size_t)n * M + x] = -Q[(size_t)x * M + x].y / 3.141592653589793;
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (in.T) in.T[inst] = T;
+            if (in.status) in.status[inst] = st;
+        }
+        __syncthreads();
+    }
+}
+
+// shared-memory bytes for the kernels above (matrices in shared memory or not)
+extern "C" size_t knit_fp64_smem_bytes(int M, int use_smem, int nbuf)
+{
+    size_t b = (size_t)M * sizeof(double2) * 2 + sizeof(double2) + sizeof(double) * 32 +
+               sizeof(int) * (M + 2) + 64;
+    if (use_smem) b += (size_t)nbuf * M * M * sizeof(double2);
+    return b;
+}
+
+// host launch helpers used by the C-ABI implementation
+extern "C" cudaError_t knit_launch_sweep_fp64(const SysDev *s, const InstDev *in, int grid,
+                                              double2 *work, int use_smem, cudaStream_t stream)
+{
+    size_t sm = knit_fp64_smem_bytes(s->M, use_smem, 3);
+    cudaError_t e = cudaFuncSetAttribute(knit_sweep_fp64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    knit_sweep_fp64_kernel<<<grid, 256, sm, stream>>>(*s, *in, work, use_smem);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t knit_launch_ldos_fp64(const SysDev *s, const InstDev *in, int grid,
+                                             double2 *work, int use_smem, double2 *ckpt, int save,
+                                             double *ldos, cudaStream_t stream)
+{
+    size_t sm = knit_fp64_smem_bytes(s->M, use_smem, 4);
+    cudaError_t e = cudaFuncSetAttribute(knit_ldos_fp64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    knit_ldos_fp64_kernel<<<grid, 256, sm, stream>>>(*s, *in, work, use_smem, ckpt, save, ldos);
+    return cudaGetLastError();
+}

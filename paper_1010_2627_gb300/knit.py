@@ -1,0 +1,256 @@
+"""Thin ctypes binding of the C-ABI in ``include/knit.h`` (libknit.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C entry points.  The functions keep the C names
+(``knit_system_create``, ``knit_lead_selfenergy``, ``knit_transmission``,
+``knit_transmission_sigma``, ``knit_ldos``, ...); arrays may be numpy arrays
+(host memory) or torch CUDA tensors (device memory), and ``stream`` may be a
+``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer.
+
+The library must have been built (``paper_1010_2627_gb300.build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KNIT_OK, KNIT_ERR_INVALID, KNIT_ERR_OOM, KNIT_ERR_CUDA = 0, 1, 2, 3
+KNIT_ERR_SINGULAR, KNIT_ERR_NOCONVERGE, KNIT_ERR_TIMEOUT, KNIT_ERR_NONFINITE = 4, 5, 6, 7
+KNIT_FP64, KNIT_MIXED = 0, 1
+KNIT_LEAD_AUTO, KNIT_LEAD_MODES, KNIT_LEAD_DECIMATION = 0, 1, 2
+
+P = ctypes.c_void_p
+i32, f64 = ctypes.c_int32, ctypes.c_double
+
+
+class knit_system_desc(ctypes.Structure):
+    _fields_ = [("M", i32), ("L", i32), ("block", i32), ("onsite_sign", P), ("H0", P),
+                ("onsite", P), ("V", P), ("Vperiod", i32), ("lead_H0", P * 2), ("lead_V", P * 2)]
+
+
+class knit_lead_opts(ctypes.Structure):
+    _fields_ = [("method", i32), ("eta", f64), ("tol", f64), ("maxit", i32)]
+
+
+class KnitError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"knit error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# every entry point the header declares, with its ctypes signature
+_SIGS = {
+    "knit_system_create": (i32, [P, P]),
+    "knit_system_destroy": (i32, [P]),
+    "knit_lead_selfenergy": (i32, [P, i32, P, i32, P, P, P, P, P]),
+    "knit_transmission": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P]),
+    "knit_transmission_sigma": (i32, [P, P, i32, P, i32, f64, P, P, i32, P, P, P]),
+    "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P]),
+    "knit_last_error": (ctypes.c_char_p, []),
+    "knit_version": (ctypes.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libknit.so (must be built).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: the CUDA library must be built "
+                               "(paper_1010_2627_gb300.build.build()); there is no fallback")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def knit_last_error() -> str:
+    return load().knit_last_error().decode()
+
+
+def knit_version() -> str:
+    return load().knit_version().decode()
+
+
+def _check(rc: int):
+    if rc != KNIT_OK:
+        raise KnitError(rc, knit_last_error())
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return P(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return P(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return P(stream.cuda_stream)
+    return P(int(stream))
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _opts(method=KNIT_LEAD_AUTO, eta=0.0, tol=0.0, maxit=0):
+    return knit_lead_opts(int(method), float(eta), float(tol), int(maxit))
+
+
+# ---------------------------------------------------------------------------
+# C entry points with the C names
+
+def knit_system_create(M, L, H0, V, block=1, onsite_sign=None, onsite=None, lead_H0=(None, None),
+                       lead_V=(None, None)):
+    """Create a system (see include/knit.h); returns an opaque handle (int)."""
+    H0 = _c128(H0)
+    V = _c128(V)
+    Vp = 1 if V.ndim == 2 else V.shape[0]
+    keep = [H0, V]
+    d = knit_system_desc()
+    d.M, d.L, d.block, d.Vperiod = int(M), int(L), int(block), int(Vp)
+    d.H0, d.V = _ptr(H0), _ptr(V)
+    if onsite_sign is not None:
+        s = np.ascontiguousarray(onsite_sign, dtype=np.float64)
+        keep.append(s)
+        d.onsite_sign = _ptr(s)
+    if onsite is not None:
+        o = np.ascontiguousarray(onsite, dtype=np.float64)
+        keep.append(o)
+        d.onsite = _ptr(o)
+    for p in range(2):
+        if lead_H0[p] is not None:
+            h = _c128(lead_H0[p])
+            keep.append(h)
+            d.lead_H0[p] = h.ctypes.data
+        if lead_V[p] is not None:
+            v = _c128(lead_V[p])
+            keep.append(v)
+            d.lead_V[p] = v.ctypes.data
+    h = P()
+    _check(load().knit_system_create(ctypes.byref(d), ctypes.byref(h)))
+    return h.value
+
+
+def knit_system_destroy(handle):
+    _check(load().knit_system_destroy(P(handle)))
+
+
+def knit_lead_selfenergy(handle, lead, E, sigma, opts=None, iters=None, residual=None,
+                         stream=None):
+    o = opts if opts is not None else None
+    _check(load().knit_lead_selfenergy(P(handle), int(lead), _ptr(E), int(len(E)),
+                                       None if o is None else ctypes.byref(o), _ptr(sigma),
+                                       _ptr(iters), _ptr(residual), _stream(stream)))
+
+
+def knit_transmission(handle, E, seeds, W, precision, T, status=None, opts=None, nE=None, nS=None,
+                      stream=None):
+    nE = len(E) if nE is None else nE
+    nS = (1 if seeds is None else len(seeds)) if nS is None else nS
+    _check(load().knit_transmission(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS), float(W),
+                                    int(precision), None if opts is None else ctypes.byref(opts),
+                                    _ptr(T), _ptr(status), _stream(stream)))
+
+
+def knit_transmission_sigma(handle, E, seeds, W, sigmaL, sigmaR, precision, T, status=None,
+                            nE=None, nS=None, stream=None):
+    nE = len(E) if nE is None else nE
+    nS = (1 if seeds is None else len(seeds)) if nS is None else nS
+    _check(load().knit_transmission_sigma(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS),
+                                          float(W), _ptr(sigmaL), _ptr(sigmaR), int(precision),
+                                          _ptr(T), _ptr(status), _stream(stream)))
+
+
+def knit_ldos(handle, E, seeds, W, saving_level, ldos, T=None, status=None, opts=None, nE=None,
+              nS=None, stream=None):
+    nE = len(E) if nE is None else nE
+    nS = (1 if seeds is None else len(seeds)) if nS is None else nS
+    _check(load().knit_ldos(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS), float(W),
+                            int(saving_level), None if opts is None else ctypes.byref(opts),
+                            _ptr(ldos), _ptr(T), _ptr(status), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper over a SliceSystem (paper_1010_2627_gb300.inputs)
+
+class System:
+    """Owns one knit_system built from an ``inputs.SliceSystem``."""
+
+    def __init__(self, ss, onsite=None):
+        self.M, self.L = ss.M, ss.L
+        self.handle = knit_system_create(ss.M, ss.L, ss.H0, ss.V, block=ss.block,
+                                         onsite_sign=ss.sign, onsite=onsite,
+                                         lead_H0=ss.lead_H0, lead_V=ss.lead_V)
+
+    def close(self):
+        if self.handle:
+            knit_system_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lead_selfenergy(self, lead, E, method=KNIT_LEAD_AUTO, eta=0.0, want_residual=False):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        S = np.empty((len(E), self.M, self.M), np.complex128)
+        it = np.zeros(len(E), np.int32)
+        res = np.zeros(len(E)) if want_residual else None
+        knit_lead_selfenergy(self.handle, lead, E, S, _opts(method, eta), it, res)
+        return S, it, res
+
+    def transmission(self, E, seeds=None, W=0.0, precision=KNIT_FP64, method=KNIT_LEAD_AUTO):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        nS = 1 if sd is None else len(sd)
+        T = np.empty(len(E) * nS)
+        st = np.empty(len(E) * nS, np.int32)
+        knit_transmission(self.handle, E, sd, W, precision, T, st, _opts(method))
+        return T.reshape(len(E), nS), st.reshape(len(E), nS)
+
+    def transmission_sigma(self, E, SL, SR, seeds=None, W=0.0, precision=KNIT_FP64):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        nS = 1 if sd is None else len(sd)
+        T = np.empty(len(E) * nS)
+        st = np.empty(len(E) * nS, np.int32)
+        knit_transmission_sigma(self.handle, E, sd, W, _c128(SL), _c128(SR), precision, T, st)
+        return T.reshape(len(E), nS), st.reshape(len(E), nS)
+
+    def ldos(self, E, seeds=None, W=0.0, saving_level=-1, method=KNIT_LEAD_AUTO):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        nS = 1 if sd is None else len(sd)
+        out = np.empty((len(E) * nS, self.L, self.M))
+        T = np.empty(len(E) * nS)
+        st = np.empty(len(E) * nS, np.int32)
+        knit_ldos(self.handle, E, sd, W, saving_level, out, T, st, _opts(method))
+        return (out.reshape(len(E), nS, self.L, self.M), T.reshape(len(E), nS),
+                st.reshape(len(E), nS))

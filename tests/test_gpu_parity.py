@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle on the
+same seeded inputs.  Tolerances: |dT| / max(1, N_ch) <= 1e-8 for KNIT_FP64
+and <= 1e-6 for KNIT_MIXED (N_ch = open channels of the clean leads)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1010_2627_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-8
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def knit():
+    from paper_1010_2627_gb300 import build, knit as k
+    build.build()
+    k.load()
+    return k
+
+
+def nch_square(M, E, t=1.0):
+    ek = 2 * t * np.cos(np.arange(1, M + 1) * np.pi / (M + 1))
+    return np.sum(np.abs(E - ek) < 2 * abs(t))
+
+
+def oracle_T(ss, E, seed, W, method="dense"):
+    eps = oracle.onsite(seed, ss.L, ss.M, W, block=ss.block, sign=ss.sign) if W else None
+    S = oracle.sigma_square(ss.M, ss.V[0][0, 0].real, E)
+    if method == "dense":
+        return oracle.dense(ss.H0, ss.V, eps, ss.L, E, S, S)["T_LR"]
+    return oracle.rgf(ss.H0, ss.V, eps, ss.L, E, S, S)["T"]
+
+
+# --------------------------------------------------------------------------
+# leads
+
+@pytest.mark.parametrize("M", [1, 8, 37, 64])
+def test_lead_modes_matches_closed_form(knit, M):
+    ss = inputs.square(M, 4)
+    sysk = knit.System(ss)
+    E = inputs.energy_grid(-3.9, 3.9, 17)
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_MODES, want_residual=True)
+        for e, Ee in enumerate(E):
+            assert np.abs(S[e] - oracle.sigma_square(M, 1.0, Ee)).max() < 1e-12
+        assert res.max() < 1e-11
+
+
+@pytest.mark.parametrize("M", [4, 12])
+def test_lead_decimation_matches_oracle(knit, M):
+    ss = inputs.square(M, 4)
+    sysk = knit.System(ss)
+    E = np.array([-2.7, -0.35, 0.8, 1.9])
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION, eta=1e-13,
+                                          want_residual=True)
+        assert (it > 0).all()
+        for e, Ee in enumerate(E):
+            _, So, _ = oracle.decimation(ss.H0, ss.V[0], Ee, lead, eta=1e-13)
+            assert np.abs(S[e] - So).max() < 1e-9
+            assert np.abs(S[e] - oracle.sigma_square(M, 1.0, Ee)).max() < 1e-9
+        assert res.max() < 1e-9
+
+
+def test_lead_decimation_bdg(knit):
+    b = inputs.bdg(2, 3, mu=-1.0, delta=0.1, alpha=0.2)
+    sysk = knit.System(b)
+    E = np.array([-0.13, 0.07])
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, eta=1e-12, want_residual=True)
+        for e, Ee in enumerate(E):
+            _, So, _ = oracle.decimation(b.lead_H0[lead], b.lead_V[lead], Ee, lead, eta=1e-12)
+            assert np.abs(S[e] - So).max() < 1e-8
+
+
+# --------------------------------------------------------------------------
+# transmission, small configuration: square M=8, L=16, W=1, seed 0, 64 energies
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_MIXED)])
+def test_small_config_all_energies(knit, precision, tol):
+    ss = inputs.square(8, 16)
+    E = inputs.energy_grid(-3.9, 3.9, 64)
+    sysk = knit.System(ss)
+    T, st = sysk.transmission(E, seeds=[0], W=1.0, precision=precision)
+    assert (st == 0).all()
+    for e, Ee in enumerate(E):
+        To = oracle_T(ss, Ee, 0, 1.0)
+        assert abs(T[e, 0] - To) / max(1, nch_square(8, Ee)) <= tol, (Ee, T[e, 0], To)
+
+
+@pytest.mark.parametrize("M,L", [(1, 1), (1, 7), (3, 1), (5, 2), (16, 9), (20, 5), (33, 4),
+                                 (40, 3), (64, 6)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ragged_widths_and_lengths(knit, M, L, precision):
+    ss = inputs.square(M, L)
+    E = np.array([-2.95, -0.61, 0.05, 1.37, 3.3])
+    seeds = np.array([3, 11], np.uint64)
+    sysk = knit.System(ss)
+    T, st = sysk.transmission(E, seeds=seeds, W=2.0, precision=precision)
+    assert (st == 0).all()
+    tol = TOL_FP64 if precision == 0 else TOL_MIXED
+    for e, Ee in enumerate(E):
+        for s, sd in enumerate(seeds):
+            To = oracle_T(ss, Ee, int(sd), 2.0)
+            assert abs(T[e, s] - To) / max(1, nch_square(M, Ee)) <= tol, (M, L, Ee, sd)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_clean_ribbon_integer_plateaus(knit, precision):
+    M = 24
+    ss = inputs.square(M, 40)
+    ek = 2 * np.cos(np.arange(1, M + 1) * np.pi / (M + 1))
+    E = inputs.energy_grid(-3.9, 3.9, 41)
+    E = E[np.min(np.abs(np.abs(E[:, None] - ek[None]) - 2), axis=1) > 1e-3]
+    T, st = knit.System(ss).transmission(E, precision=precision)
+    nopen = np.array([nch_square(M, e) for e in E])
+    assert np.abs(T[:, 0] - nopen).max() < (1e-9 if precision == 0 else 1e-6)
+
+
+def test_explicit_onsite_and_general_diagonal_v(knit):
+    """explicit on-site array and a diagonal V that is not a multiple of I
+    (leads stay clean t I)."""
+    rng = np.random.default_rng(5)
+    M, L = 12, 9
+    ss = inputs.square(M, L)
+    V = np.diag(1.0 + 0.3 * rng.standard_normal(M)).astype(np.complex128)
+    eps = rng.uniform(-1, 1, (L, M))
+    sysk = knit.System(inputs.SliceSystem(M, L, ss.H0, V, lead_V=(np.eye(M), np.eye(M))),
+                       onsite=eps)
+    E = np.array([-1.1, 0.4])
+    for precision, tol in ((0, TOL_FP64), (1, TOL_MIXED)):
+        T, st = sysk.transmission(E, precision=precision)
+        for e, Ee in enumerate(E):
+            S = oracle.sigma_square(M, 1.0, Ee)
+            To = oracle.dense(ss.H0, V, eps, L, Ee, S, S)["T_LR"]
+            assert abs(T[e, 0] - To) <= tol * max(1, nch_square(M, Ee))
+
+
+def test_block_coupling_bdg_fp64(knit):
+    b = inputs.bdg(3, 6, mu=-1.0, delta=0.1, alpha=0.2)
+    sysk = knit.System(b)
+    E = np.array([-0.11, 0.05])
+    T, st = sysk.transmission(E, seeds=[4], W=1.0, precision=0)
+    assert (st == 0).all()
+    eps = oracle.onsite(4, b.L, b.M, 1.0, block=4, sign=b.sign)
+    for e, Ee in enumerate(E):
+        SL = oracle.decimation(b.lead_H0[0], b.lead_V[0], Ee, 0, eta=1e-12)[1]
+        SR = oracle.decimation(b.lead_H0[1], b.lead_V[1], Ee, 1, eta=1e-12)[1]
+        To = oracle.dense(b.H0, b.V, eps, b.L, Ee, SL, SR)["T_LR"]
+        assert abs(T[e, 0] - To) < 1e-7
+
+
+def test_sigma_supplied_sweep_matches(knit):
+    ss = inputs.square(10, 12)
+    E = np.array([-1.5, 0.3])
+    S = np.stack([oracle.sigma_square(10, 1.0, e) for e in E])
+    sysk = knit.System(ss)
+    for precision in (0, 1):
+        T1, _ = sysk.transmission(E, seeds=[1, 2], W=1.5, precision=precision)
+        T2, _ = sysk.transmission_sigma(E, S, S, seeds=[1, 2], W=1.5, precision=precision)
+        assert np.abs(T1 - T2).max() < 1e-9
+
+
+def test_device_pointers_match_host(knit):
+    torch = pytest.importorskip("torch")
+    ss = inputs.square(16, 20)
+    sysk = knit.System(ss)
+    E = inputs.energy_grid(-3.0, 3.0, 7)
+    seeds = np.array([0, 5, 9], np.uint64)
+    Th, _ = sysk.transmission(E, seeds, W=1.0, precision=1)
+    dE = torch.tensor(E, device="cuda")
+    ds = torch.tensor(seeds.astype(np.int64), device="cuda")
+    dT = torch.empty(len(E) * 3, dtype=torch.float64, device="cuda")
+    dst = torch.empty(len(E) * 3, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    knit.knit_transmission(sysk.handle, dE, ds, 1.0, 1, dT, dst, nE=len(E), nS=3, stream=s)
+    torch.cuda.synchronize()
+    assert np.array_equal(dT.cpu().numpy().reshape(len(E), 3), Th)
+    assert (dst.cpu().numpy() == 0).all()
+
+
+# --------------------------------------------------------------------------
+# LDOS (sewing)
+
+@pytest.mark.parametrize("saving_level", [-1, 1, 3, 5, 16])
+def test_ldos_small_config(knit, saving_level):
+    ss = inputs.square(8, 16)
+    E = inputs.energy_grid(-3.9, 3.9, 8)
+    sysk = knit.System(ss)
+    ld, T, st = sysk.ldos(E, seeds=[0], W=1.0, saving_level=saving_level)
+    assert (st == 0).all()
+    eps = oracle.onsite(0, 16, 8, 1.0)
+    for e, Ee in enumerate(E):
+        S = oracle.sigma_square(8, 1.0, Ee)
+        d = oracle.dense(ss.H0, ss.V, eps, 16, Ee, S, S, want_ldos=True)
+        assert np.abs(ld[e, 0] - d["ldos"]).max() < 1e-9 * max(1.0, np.abs(d["ldos"]).max())
+        assert abs(T[e, 0] - d["T_LR"]) < 1e-9
+
+
+def test_ldos_clean_ribbon_closed_form(knit):
+    M, L, E = 6, 11, 0.37
+    y = np.arange(1, M + 1)
+    phi = np.sqrt(2 / (M + 1)) * np.sin(np.outer(y, y) * np.pi / (M + 1))
+    ek = 2 * np.cos(y * np.pi / (M + 1))
+    op = np.abs(E - ek) < 2
+    rho = (phi[:, op] ** 2 / (np.pi * np.sqrt(4 - (E - ek[op]) ** 2))).sum(axis=1)
+    ld, T, st = knit.System(inputs.square(M, L)).ldos([E], saving_level=4)
+    assert np.abs(ld[0, 0] - rho[None, :]).max() < 1e-11
+
+
+# --------------------------------------------------------------------------
+# status and argument errors
+
+def test_singular_pivot_reports_status(knit):
+    ss = inputs.chain(1)
+    sysk = knit.System(ss, onsite=np.array([[0.5]]))
+    Z = np.zeros((1, 1, 1), np.complex128)
+    for precision in (0, 1):
+        T, st = sysk.transmission_sigma(np.array([0.5]), Z, Z, precision=precision)
+        assert st[0, 0] == knit.KNIT_ERR_SINGULAR
+
+
+def test_invalid_arguments(knit):
+    ss = inputs.square(80, 3)
+    sysk = knit.System(ss)
+    with pytest.raises(knit.KnitError) as ei:
+        sysk.transmission([0.1], precision=knit.KNIT_MIXED)
+    assert ei.value.code == knit.KNIT_ERR_INVALID
+    with pytest.raises(knit.KnitError):
+        sysk.ldos([0.1], saving_level=0)
+    bad = inputs.square(4, 3)
+    bad.H0 = bad.H0 + 1j * np.triu(np.ones((4, 4)), 1)
+    with pytest.raises(knit.KnitError):
+        knit.System(bad)
+    with pytest.raises(knit.KnitError):
+        knit.knit_system_create(0, 3, np.zeros((1, 1)), np.zeros((1, 1)))
+
+
+# --------------------------------------------------------------------------
+# the bench workload at full size (square M=64, L=512, W=2, 1024 energies x 8
+# seeds), checked on sampled instances the oracle computes one by one
+
+def test_full_bench_workload_sampled(knit):
+    ss = inputs.square(64, 512)
+    E = inputs.energy_grid(-3.9, 3.9, 1024)
+    seeds = np.arange(8, dtype=np.uint64)
+    sysk = knit.System(ss)
+    T, st = sysk.transmission(E, seeds, W=2.0, precision=knit.KNIT_MIXED)
+    assert (st == 0).all()
+    assert np.isfinite(T).all() and (T >= -1e-9).all()
+    rng = np.random.default_rng(2024)
+    picks = [(int(e), int(s)) for e, s in zip(rng.integers(0, 1024, 6), rng.integers(0, 8, 6))]
+    for e, s in picks:
+        To = oracle_T(ss, E[e], s, 2.0, method="rgf")
+        assert abs(T[e, s] - To) / max(1, nch_square(64, E[e])) <= TOL_MIXED, (e, s)
