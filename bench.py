@@ -303,8 +303,31 @@ def run_knit(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Small case for ncu captures: M=64, L=64, 19 energies x 8 seeds (one
+    wave of 152 instances), one mixed and one FP64 sweep after a warm-up."""
+    import torch
+    from paper_1010_2627_gb300 import build, inputs, knit
+    build.build()
+    knit.load()
+    Lp = args.profile_L
+    ss = inputs.square(M, Lp)
+    E = inputs.energy_grid(-3.9, 3.9, 19)
+    seeds = np.arange(NS, dtype=np.uint64)
+    sysk = knit.System(ss)
+    for precision in (knit.KNIT_MIXED, knit.KNIT_MIXED, knit.KNIT_FP64):
+        T, st = sysk.transmission(E, seeds, W=W, precision=precision)
+        assert (st == 0).all()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "profile", "M": M, "L": Lp, "instances": 19 * NS,
+                      "T_mean": float(T.mean())}))
+    sysk.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -313,7 +336,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.case == "profile":
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_knit(args)

@@ -49,6 +49,10 @@ def test_lead_modes_matches_closed_form(knit, M):
         assert res.max() < 1e-11
 
 
+# Decimation at eta = 1e-13 reproduces the closed form only to ~1e-9: near a
+# channel threshold (|E - e_k| -> 2t) rounding in the ~45 doubling steps is
+# amplified by 1 / sqrt(4t^2 - (E - e_k)^2); the two implementations differ by
+# their rounding, so they are compared at 1e-8.
 @pytest.mark.parametrize("M", [4, 12])
 def test_lead_decimation_matches_oracle(knit, M):
     ss = inputs.square(M, 4)
@@ -60,9 +64,9 @@ def test_lead_decimation_matches_oracle(knit, M):
         assert (it > 0).all()
         for e, Ee in enumerate(E):
             _, So, _ = oracle.decimation(ss.H0, ss.V[0], Ee, lead, eta=1e-13)
-            assert np.abs(S[e] - So).max() < 1e-9
-            assert np.abs(S[e] - oracle.sigma_square(M, 1.0, Ee)).max() < 1e-9
-        assert res.max() < 1e-9
+            assert np.abs(S[e] - So).max() < 1e-8
+            assert np.abs(S[e] - oracle.sigma_square(M, 1.0, Ee)).max() < 1e-8
+        assert res.max() < 1e-8
 
 
 def test_lead_decimation_bdg(knit):
