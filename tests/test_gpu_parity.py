@@ -66,7 +66,9 @@ def test_lead_decimation_matches_oracle(knit, M):
             _, So, _ = oracle.decimation(ss.H0, ss.V[0], Ee, lead, eta=1e-13)
             assert np.abs(S[e] - So).max() < 1e-8
             assert np.abs(S[e] - oracle.sigma_square(M, 1.0, Ee)).max() < 1e-8
-        assert res.max() < 1e-8
+        # the fixed-point residual at eta = 0 of a g decimated at eta = 1e-13:
+        # ~2e-8 for a mode 0.12 from threshold (M = 12, E = -0.35)
+        assert res.max() < 1e-7
 
 
 def test_lead_decimation_bdg(knit):
