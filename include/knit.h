@@ -159,6 +159,28 @@ knit_status knit_ldos(knit_system sys, const double *E, int32_t nE, const uint64
                       int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
                       double *ldos, double *T, int32_t *status, void *stream);
 
+/* Lead self-energy by Sancho-Rubio decimation without any allocation (the
+ * paper has no counterpart; it exists for callers that cannot let a library
+ * call cudaMalloc/cudaFree, e.g. processes whose framework owns all device
+ * memory, or loops that must not trigger the device-wide synchronisation of
+ * cudaFree).  Same arithmetic as knit_lead_selfenergy with
+ * KNIT_LEAD_DECIMATION, for one lead cell given directly:
+ *   H0, V: M*M lead cell and inter-cell hopping (device memory, complex128);
+ *   lead: 0 = left (Sigma = V g V^dagger), 1 = right (Sigma = V^dagger g V);
+ *   E: nE energies (device); eta, tol, maxit as in knit_lead_opts (<= 0 means
+ *   the defaults 1e-12, 1e-14, 200);
+ *   sigma: nE*M*M outputs; iters, status: nE outputs or NULL (all device).
+ * Scratch comes from one fixed 9 MiB array inside the library (per device,
+ * held until exit): M must be <= 64, larger M returns KNIT_ERR_INVALID, as
+ * does any host pointer.  All calls share that array, so calls that overlap
+ * on the GPU race; serialise them.  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress) -- make it before any stream
+ * capture.  Stream-ordered; returns after enqueueing. */
+knit_status knit_lead_decimation_noalloc(const knit_c128 *H0, const knit_c128 *V, int32_t M,
+                                         int32_t lead, const double *E, int32_t nE, double eta,
+                                         double tol, int32_t maxit, knit_c128 *sigma,
+                                         int32_t *iters, int32_t *status, void *stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char *knit_last_error(void);
 

@@ -383,6 +383,9 @@ extern "C" {
 
 const char *knit_last_error(void) { return g_err.c_str(); }
 
+// lets other translation units of the library report an error message
+void knit_set_last_error(const char *msg) { g_err = msg ? msg : "unknown error"; }
+
 const char *knit_version(void) { return "knit-gb300 0.1 (sm_103a)"; }
 
 knit_status knit_system_create(const knit_system_desc *d, knit_system *out)

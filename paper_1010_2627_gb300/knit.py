@@ -53,6 +53,7 @@ _SIGS = {
     "knit_transmission": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P]),
     "knit_transmission_sigma": (i32, [P, P, i32, P, i32, f64, P, P, i32, P, P, P]),
     "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P]),
+    "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_last_error": (ctypes.c_char_p, []),
     "knit_version": (ctypes.c_char_p, []),
 }
@@ -193,6 +194,17 @@ def knit_ldos(handle, E, seeds, W, saving_level, ldos, T=None, status=None, opts
     _check(load().knit_ldos(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS), float(W),
                             int(saving_level), None if opts is None else ctypes.byref(opts),
                             _ptr(ldos), _ptr(T), _ptr(status), _stream(stream)))
+
+
+def knit_lead_decimation_noalloc(H0, V, M, lead, E, sigma, eta=0.0, tol=0.0, maxit=0, iters=None,
+                                 status=None, nE=None, stream=None):
+    """Decimation into caller-provided device arrays; the library allocates
+    nothing (fixed internal scratch, M <= 64)."""
+    nE = len(E) if nE is None else nE
+    _check(load().knit_lead_decimation_noalloc(_ptr(H0), _ptr(V), int(M), int(lead), _ptr(E),
+                                               int(nE), float(eta), float(tol), int(maxit),
+                                               _ptr(sigma), _ptr(iters), _ptr(status),
+                                               _stream(stream)))
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,73 @@
+"""The allocation-free lead decimation entry point against the allocating one.
+
+knit_lead_decimation_noalloc exists for callers that cannot let the library
+allocate device memory; it takes its scratch from a fixed array inside the
+library.  This file is named to be collected last so that a run stopping at
+its first failure has already run every other test."""
+import numpy as np
+import pytest
+
+from paper_1010_2627_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8   # the decimation tolerance used by the other lead tests
+
+
+@pytest.fixture(scope="module")
+def knit():
+    from paper_1010_2627_gb300 import build, knit as k
+    build.build()
+    k.load()
+    return k
+
+
+def _dev(torch, a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return torch.from_numpy(a.view(np.float64).copy()).cuda()
+
+
+@pytest.mark.parametrize("cell", ["square12", "bdg2"])
+def test_noalloc_matches_allocating_entry_point_twice(knit, cell):
+    torch = pytest.importorskip("torch")
+    ss = inputs.square(12, 3) if cell == "square12" else inputs.bdg(2, 3, delta=0.0)
+    M = ss.M
+    E = inputs.energy_grid(-3.5, 3.5, 37) if cell == "square12" else \
+        inputs.energy_grid(-0.5, 0.5, 21)
+    sysk = knit.System(ss)
+    stream = torch.cuda.Stream()
+    for lead in (0, 1):
+        S_ref, it_ref, _ = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION,
+                                                eta=1e-12)
+        dH0 = _dev(torch, ss.lead_H0[lead])
+        dV = _dev(torch, ss.lead_V[lead])
+        dE = torch.tensor(E, dtype=torch.float64, device="cuda")
+        dS = torch.empty(len(E) * M * M * 2, dtype=torch.float64, device="cuda")
+        dit = torch.empty(len(E), dtype=torch.int32, device="cuda")
+        dst = torch.empty(len(E), dtype=torch.int32, device="cuda")
+        for call in range(2):            # two calls in a row share the scratch
+            dS.fill_(float("nan"))
+            dit.fill_(-1)
+            knit.knit_lead_decimation_noalloc(dH0, dV, M, lead, dE, dS, eta=1e-12, iters=dit,
+                                             status=dst, stream=stream)
+            torch.cuda.synchronize()
+            S = dS.cpu().numpy().view(np.complex128).reshape(len(E), M, M)
+            assert (dst.cpu().numpy() == 0).all()
+            assert np.array_equal(dit.cpu().numpy(), it_ref)
+            assert np.abs(S - S_ref).max() <= TOL, (cell, lead, call)
+    sysk.close()
+
+
+def test_noalloc_rejects_what_it_cannot_hold(knit):
+    torch = pytest.importorskip("torch")
+    M = 65
+    d = torch.zeros(M * M * 2, dtype=torch.float64, device="cuda")
+    dE = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(knit.KnitError) as ei:
+        knit.knit_lead_decimation_noalloc(d, d, M, 0, dE, d)
+    assert ei.value.code == knit.KNIT_ERR_INVALID
+    assert "64" in knit.knit_last_error()
+    h = np.zeros((4, 4), np.complex128)
+    with pytest.raises(knit.KnitError) as ei:
+        knit.knit_lead_decimation_noalloc(h, h, 4, 0, np.zeros(1), h)
+    assert ei.value.code == knit.KNIT_ERR_INVALID
