@@ -95,6 +95,22 @@ __device__ void copy_mat(const double2 *src, double2 *dst, int M)
     __syncthreads();
 }
 
+// C = (A V^dagger) B; for a diagonal V the columns of A are scaled in place
+// first (A is the previous G_{0,n-1}, dead after this product)
+__device__ void g1_update(double2 *A, const double2 *V, int vb, const double2 *B, double2 *C, int M)
+{
+    if (vb == 1) {
+        for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+            int k = e % M;
+            A[e] = cmul(A[e], cconj(V[(size_t)k * M + k]));
+        }
+        __syncthreads();
+        gemm64(A, B, C, M);
+    } else {
+        gemm64_avd_b(A, V, vb, B, C, M);
+    }
+}
+
 __device__ int take_instance(int *queue, int *sh)
 {
     if (threadIdx.x == 0) *sh = atomicAdd(queue, 1);
@@ -133,7 +149,7 @@ knit_sweep_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem)
                 copy_mat(F, Q, M);
             } else {
                 const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
-                gemm64_avd_b(Q, Vn, s.vb, F, P, M);   // G_{0,n} = G_{0,n-1} V_n^dagger g_n
+                g1_update(Q, Vn, s.vb, F, P, M);      // G_{0,n} = G_{0,n-1} V_n^dagger g_n
                 double2 *t = Q;
                 Q = P;
                 P = t;
@@ -193,7 +209,7 @@ knit_ldos_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem, double2
                 copy_mat(F, Q, M);
             } else {
                 const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
-                gemm64_avd_b(Q, Vn, s.vb, F, P, M);
+                g1_update(Q, Vn, s.vb, F, P, M);
                 double2 *t = Q;
                 Q = P;
                 P = t;

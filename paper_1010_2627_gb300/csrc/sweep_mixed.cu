@@ -47,6 +47,7 @@ struct MixedSmem {
     float2 vl[2][MP];      // lo
     int perm[MP];
     int pos[MP];
+    int used[MP];
     double red[NT / 32];
     int flag;
     int inst;
@@ -207,9 +208,17 @@ knit_sweep_mixed_kernel(SysDev s, InstDev in)
                     }
                     x[a][b] = v;
                 }
+            // Gauss-Jordan with implicit partial pivoting: no rows are moved; the
+            // pivot of column k is the largest |Re|+|Im| among rows not yet used
+            // (lowest row on ties).  Column k and the pivot row are zeroed in
+            // registers after staging, so every element then takes the same
+            // update x -= c_i r_j (c_p = -1, r_k = 1/pivot).  At the end
+            // A^{-1}[k][P[k']] = x[P[k]][k'] with P[k] the pivot row of step k.
+            for (int i = tid; i < MP; i += NT) sm.used[i] = 0;
+            __syncthreads();
             for (int k = 0; k < M; ++k) {
                 const int q = k & 1, kt = k & 15, kb = k >> 4;
-                // S1: stage column k (with pivot candidates) and row k
+                // S1: stage column k and the pivot candidates, zero column k
                 if (tx == kt) {
 #pragma unroll
                     for (int a = 0; a < RT; ++a) {
@@ -217,23 +226,16 @@ knit_sweep_mixed_kernel(SysDev s, InstDev in)
 #pragma unroll
                         for (int b = 1; b < RT; ++b)
                             if (b == kb) v = x[a][b];
-                        int i = ty + 16 * a;
+#pragma unroll
+                        for (int b = 0; b < RT; ++b)
+                            if (b == kb) x[a][b] = make_float2(0.f, 0.f);
+                        const int i = ty + 16 * a;
                         sm.col[q][i] = v;
-                        sm.val[q][i] = (i >= k && i < M) ? cabs1f(v) : -1.f;
-                    }
-                }
-                if (ty == kt) {
-#pragma unroll
-                    for (int b = 0; b < RT; ++b) {
-                        float2 v = x[0][b];
-#pragma unroll
-                        for (int a = 1; a < RT; ++a)
-                            if (a == kb) v = x[a][b];
-                        sm.rowk[q][tx + 16 * b] = v;
+                        sm.val[q][i] = (i < M && !sm.used[i]) ? cabs1f(v) : -1.f;
                     }
                 }
                 __syncthreads();
-                // S2: every warp finds the pivot row; row p owners stage it
+                // S2: every warp finds the pivot row p; its owners stage and zero it
                 float best = -1.f;
                 int p = MP;
                 for (int i = lane; i < MP; i += 32) {
@@ -246,64 +248,49 @@ knit_sweep_mixed_kernel(SysDev s, InstDev in)
                     break;
                 }
                 if (ty == (p & 15)) {
-                    const int pb = p >> 4;
+                    const int pa = p >> 4;
 #pragma unroll
-                    for (int b = 0; b < RT; ++b) {
-                        float2 v = x[0][b];
+                    for (int a = 0; a < RT; ++a) {
+                        if (a != pa) continue;
 #pragma unroll
-                        for (int a = 1; a < RT; ++a)
-                            if (a == pb) v = x[a][b];
-                        sm.rowp[q][tx + 16 * b] = v;
+                        for (int b = 0; b < RT; ++b) {
+                            sm.rowp[q][tx + 16 * b] = x[a][b];
+                            x[a][b] = make_float2(0.f, 0.f);
+                        }
                     }
                 }
-                if (tid == 0) sm.perm[k] = p;
+                if (tid == 0) {
+                    sm.perm[k] = p;
+                    sm.used[p] = 1;
+                }
                 __syncthreads();
-                // S3: exchange rows k and p, scale the pivot row, eliminate
-                const float2 pinv = crcpf(sm.rowp[q][k]);
+                // S3: uniform rank-1 update
+                const float2 pinv = crcpf(sm.col[q][p]);
                 float2 rs[RT];
 #pragma unroll
                 for (int b = 0; b < RT; ++b) {
-                    int j = tx + 16 * b;
+                    const int j = tx + 16 * b;
                     rs[b] = (j == k) ? pinv : cmulf(sm.rowp[q][j], pinv);
                 }
 #pragma unroll
                 for (int a = 0; a < RT; ++a) {
                     const int i = ty + 16 * a;
-                    if (i == k) {
+                    const float2 ci = (i == p) ? make_float2(-1.f, 0.f) : sm.col[q][i];
 #pragma unroll
-                        for (int b = 0; b < RT; ++b) x[a][b] = rs[b];
-                        continue;
-                    }
-                    const float2 ci = (i == p) ? sm.rowk[q][k] : sm.col[q][i];
-                    const float2 nci = make_float2(-ci.x, -ci.y);
-#pragma unroll
-                    for (int b = 0; b < RT; ++b) {
-                        const int j = tx + 16 * b;
-                        float2 old = (i == p) ? sm.rowk[q][j] : x[a][b];
-                        x[a][b] = (j == k) ? cmulf(nci, pinv) : cfmsf(ci, rs[b], old);
-                    }
+                    for (int b = 0; b < RT; ++b) x[a][b] = cfmsf(ci, rs[b], x[a][b]);
                 }
             }
             if (__syncthreads_or(st != ST_OK)) { st = ST_SINGULAR; break; }
-            // column order of the inverse: undo the row exchanges, last first
-            if (tid == 0) {
-                for (int j = 0; j < MP; ++j) sm.pos[j] = j;
-                for (int k = M - 1; k >= 0; --k) {
-                    int p = sm.perm[k];
-                    int t = sm.pos[k];
-                    sm.pos[k] = sm.pos[p];
-                    sm.pos[p] = t;
-                }
-                // pos[j] = column of x that becomes column j; invert into perm
-                for (int j = 0; j < MP; ++j) sm.perm[sm.pos[j]] = j;
-            }
+            // row r of x is row Pinv[r] of the inverse, column c is column P[c]
+            for (int k = tid; k < M; k += NT) sm.pos[sm.perm[k]] = k;
             __syncthreads();
 #pragma unroll
             for (int a = 0; a < RT; ++a)
 #pragma unroll
                 for (int b = 0; b < RT; ++b) {
-                    int i = ty + 16 * a, c = tx + 16 * b;
-                    sm.X[i * MP + sm.perm[c]] = x[a][b];
+                    const int i = ty + 16 * a, c = tx + 16 * b;
+                    if (i < M && c < M) sm.X[sm.pos[i] * MP + sm.perm[c]] = x[a][b];
+                    else sm.X[i * MP + c] = x[a][b];
                 }
             __syncthreads();
 
