@@ -212,6 +212,7 @@ def run_knit(args):
     ms_per_step = total_ms / args.steps
     value = ws * n / (ms_per_step / 1e3)
 
+    peaks = _peaks()
     # ---- the sweep kernel alone (Sigma precomputed): average launch duration
     SL = torch.empty(NE * M * M * 2, dtype=torch.float64, device="cuda")
     knit.knit_lead_selfenergy(sysk.handle, 0, dE, SL, stream=stream)
@@ -229,6 +230,8 @@ def run_knit(args):
     sweep_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     alg_flop = 16.0 * M ** 3 * L * n          # 16 M^3 real flop per slice-update
     achieved_tflops = alg_flop / (sweep_ms / 1e3) / 1e12
+    tc_flop = 18 * 8 * 2.0 * 128 * 64 * 16 * L * n
+    tc_tflops = tc_flop / (sweep_ms / 1e3) / 1e12
 
     # ---- plain FP64 GPU sweep on a one-wave subset (same energies/seeds grid)
     nsub_e = 19                                # 19 energies x 8 seeds = 152 instances
@@ -247,6 +250,15 @@ def run_knit(args):
     torch.cuda.synchronize()
     fp64_ms = a.elapsed_time(b)
     fp64_rate = nsub_e * NS / (fp64_ms / 1e3)
+    # the same subset through the CUDA-core residual path of the mixed sweep
+    dTc = torch.empty(nsub_e * NS, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        knit.knit_transmission(sysk.handle, dEs, ds, W, knit.KNIT_MIXED_CUDACORE, dTc, dsts,
+                               nE=nsub_e, nS=NS, stream=stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    cc_rate = nsub_e * NS / (a.elapsed_time(b) / 1e3)
     T64 = dTs.cpu().numpy().reshape(nsub_e, NS)
     ek = 2 * np.cos(np.arange(1, M + 1) * np.pi / (M + 1))
     nch = np.array([max(1, int(np.sum(np.abs(e - ek) < 2))) for e in E[sub]])
@@ -265,13 +277,12 @@ def run_knit(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = ws * n / (statistics.mean(e2e_ms) / 1e3)
 
-    peaks = _peaks()
-    launches_per_step = 3     # modes self-energy, status combine, mixed sweep
+    launches_per_step = 4     # modes self-energy, status combine, status fill, mixed sweep
     line = {
         "metric": METRIC, "value": value, "unit": "T(E) points/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64+df32 (complex64 inversion, double-float residual)", "data": "synthetic",
+        "dtype": "c64 inversion + bf16-digit tensor-core residual (f32 accumulate)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "M": M, "L": L, "W": W, "energies": NE, "seeds": NS,
                    "instances_per_gpu": n, "precision": "mixed",
                    "flush": "L2 flushed before every timed step (252 MB write)"},
@@ -279,14 +290,23 @@ def run_knit(args):
         "fp64_sweep": {"value": fp64_rate, "unit": "T(E) points/s",
                        "sample": f"{nsub_e} energies x {NS} seeds, one wave", "ms": fp64_ms,
                        "mixed_speedup": value / ws / fp64_rate,
+                       "mixed_cudacore_residual_rate": cc_rate,
                        "max_abs_dT_mixed_vs_fp64_over_nch": mixed_vs_fp64},
-        "roofline": {"bound": "alu", "kernel": "knit_sweep_mixed_kernel<64>",
+        "roofline": {"bound": "alu", "kernel": "knit_sweep_mixed_tc_kernel",
                      "achieved": achieved_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP32_ALU_PEAK_TFLOPS,
                      "traffic": None,
-                     "note": "algorithmic 16 M^3 flop per slice-update over the FP32 CUDA-core "
-                             "peak (152 SM x 128 lanes x 2 x 2.07 GHz); kernel timed alone",
-                     "kernel_ms": sweep_ms},
+                     "note": "algorithmic 16 M^3 flop per slice-update (the method's inversion "
+                             "plus product) over the FP32 CUDA-core peak 152 SM x 128 lanes x 2 "
+                             "x 2.07 GHz (Gauss-Jordan and refinement run there); kernel timed "
+                             "alone with CUDA events",
+                     "kernel_ms": sweep_ms,
+                     "tensor_pipe": {"executed_tflops": tc_tflops,
+                                     "peak": peaks.get("bf16_tflops"),
+                                     "frac": (tc_tflops / peaks["bf16_tflops"])
+                                     if peaks.get("bf16_tflops") else None,
+                                     "note": "bf16 digit products of the residual: 18 products "
+                                             "x 8 K-chunks x (128 x 64 x 16) MMA per slice"}},
         "e2e": {"value": e2e_val, "unit": "T(E) points/s", "h2d_bytes_per_step": 8 * NE + 8 * NS,
                 "d2h_bytes_per_step": 12 * n, "ms": statistics.mean(e2e_ms)},
         "gpu_launches": launches_per_step * args.steps,

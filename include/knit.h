@@ -70,9 +70,13 @@ typedef enum {
 /* Arithmetic of the slice sweep. */
 enum {
     KNIT_FP64 = 0,  /* complex128 throughout */
-    KNIT_MIXED = 1  /* complex64 inversion + one refinement step against a
-                       residual accumulated in double-float (hi + lo float)
-                       arithmetic; the state g_n is carried as hi + lo */
+    KNIT_MIXED = 1, /* complex64 inversion + one refinement step against a
+                       residual exact to ~2^-48; the state g_n is carried as
+                       hi + lo floats.  For 33 <= M <= 64 the residual's dense
+                       product runs on the tensor cores (bf16 digit slices,
+                       f32 accumulation), otherwise on CUDA cores */
+    KNIT_MIXED_CUDACORE = 2  /* KNIT_MIXED with the residual always accumulated
+                                in double-float arithmetic on CUDA cores */
 };
 
 /* Lead solver. */

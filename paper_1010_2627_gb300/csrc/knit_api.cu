@@ -21,7 +21,7 @@ extern "C" cudaError_t knit_launch_sweep_fp64(const SysDev *, const InstDev *, i
 extern "C" cudaError_t knit_launch_ldos_fp64(const SysDev *, const InstDev *, int, double2 *, int,
                                              double2 *, int, double *, cudaStream_t);
 extern "C" size_t knit_fp64_smem_bytes(int, int, int);
-extern "C" cudaError_t knit_launch_mixed(const SysDev *, const InstDev *, int, cudaStream_t);
+extern "C" cudaError_t knit_launch_mixed_impl(const SysDev *, const InstDev *, int, int, cudaStream_t);
 extern "C" int knit_mixed_max_M(void);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
 extern "C" cudaError_t knit_launch_modes_sigma(const double2 *, const double2 *, int, double,
@@ -340,8 +340,8 @@ knit_status run_sweep(knit_system s, InstDev in, int precision, cudaStream_t st)
     in.queue = s->queue.as<int>();
     CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
     const int grid = std::max(1, std::min(in.n, s->nsm));
-    if (precision == KNIT_MIXED) {
-        CK(knit_launch_mixed(&sd, &in, grid, st), "mixed sweep launch");
+    if (precision == KNIT_MIXED || precision == KNIT_MIXED_CUDACORE) {
+        CK(knit_launch_mixed_impl(&sd, &in, grid, precision == KNIT_MIXED, st), "mixed sweep launch");
         return KNIT_OK;
     }
     const size_t MM = (size_t)s->M * s->M;
@@ -358,9 +358,9 @@ knit_status check_batch(knit_system s, const double *E, int nE, int nS, int prec
     if (nE <= 0 || nS <= 0) return fail(KNIT_ERR_INVALID, "nE and nS must be positive");
     if ((long long)nE * nS > 0x7fffffffLL) return fail(KNIT_ERR_INVALID, "nE * nS too large");
     if (!std::isfinite(W)) return fail(KNIT_ERR_INVALID, "W is not finite");
-    if (precision != KNIT_FP64 && precision != KNIT_MIXED)
+    if (precision != KNIT_FP64 && precision != KNIT_MIXED && precision != KNIT_MIXED_CUDACORE)
         return fail(KNIT_ERR_INVALID, "unknown precision %d", precision);
-    if (precision == KNIT_MIXED) {
+    if (precision != KNIT_FP64) {
         if (s->M > knit_mixed_max_M())
             return fail(KNIT_ERR_INVALID, "KNIT_MIXED supports M <= %d (M = %d)", knit_mixed_max_M(),
                         s->M);

@@ -1,0 +1,292 @@
+// mixed_common.cuh -- pieces shared by the two mixed-precision sweep kernels
+// (sweep_mixed.cu: double-float residual on CUDA cores; sweep_mixed_tc.cu:
+// residual on the tcgen05 tensor cores).  One CTA of 256 threads works on a
+// padded MP x MP complex matrix; thread (ty, tx) = (tid / 16, tid % 16) owns
+// rows ty + 16a and columns tx + 16b (a, b < MP / 16).
+#pragma once
+
+#include "knit_common.cuh"
+
+namespace mixed {
+
+constexpr int NT = 256;
+
+KNIT_DEV void to_df(double d, float &h, float &l)
+{
+    h = __double2float_rn(d);
+    l = __double2float_rn(d - (double)h);
+}
+
+// (ah + al) * (bh + bl) for real double-floats -> (p, e) unnormalised
+KNIT_DEV void df_mul(float ah, float al, float bh, float bl, float &p, float &e)
+{
+    p = ah * bh;
+    e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+}
+
+// complex double-float product
+KNIT_DEV void cdf_mul(float2 ah, float2 al, float2 bh, float2 bl, float2 &rh, float2 &rl)
+{
+    float p1, e1, p2, e2, s, t;
+    df_mul(ah.x, al.x, bh.x, bl.x, p1, e1);
+    df_mul(ah.y, al.y, bh.y, bl.y, p2, e2);
+    two_sum(p1, -p2, s, t);
+    t += e1 - e2;
+    two_sum(s, t, rh.x, rl.x);
+    df_mul(ah.x, al.x, bh.y, bl.y, p1, e1);
+    df_mul(ah.y, al.y, bh.x, bl.x, p2, e2);
+    two_sum(p1, p2, s, t);
+    t += e1 + e2;
+    two_sum(s, t, rh.y, rl.y);
+}
+
+KNIT_DEV void cdf_add(float2 &h, float2 &l, float2 bh, float2 bl)
+{
+    float s, t;
+    two_sum(h.x, bh.x, s, t);
+    t += l.x + bl.x;
+    two_sum(s, t, h.x, l.x);
+    two_sum(h.y, bh.y, s, t);
+    t += l.y + bl.y;
+    two_sum(s, t, h.y, l.y);
+}
+
+template <int MP>
+struct GJShared {
+    float2 col[2][MP];
+    float2 rowp[2][MP];
+    float val[2][MP];
+    int used[MP];
+    int perm[MP];
+    int pos[MP];
+};
+
+// E - onsite of slice n for orbitals 0..MP-1 (0 in the padding)
+template <int MP>
+__device__ void slice_diag(double *eps, const SysDev &s, uint64_t ms, double W, double E, int n)
+{
+    for (int i = threadIdx.x; i < MP; i += NT) {
+        double d = 0.0;
+        if (i < s.M) {
+            double o = 0.0;
+            if (s.onsite) o = s.onsite[(size_t)n * s.M + i];
+            else if (W != 0.0) o = s.sign[i % s.block] * knit_disorder(ms, n, i / s.block, W);
+            d = E - o;
+        }
+        eps[i] = d;
+    }
+}
+
+// Gv = V_n g V_n^dagger (+ Sigma_L at n = 0, + Sigma_R at n = L - 1) in
+// double-float, in place over (Gh, Gl); vh/vl: diagonal of V per parity.
+template <int MP>
+__device__ void form_gv(float2 *Gh, float2 *Gl, const float2 (*vh)[MP], const float2 (*vl)[MP],
+                        int M, int n, int L, const double2 *SL, const double2 *SR)
+{
+    const int q = n & 1;
+    for (int e = threadIdx.x; e < MP * MP; e += NT) {
+        const int i = e / MP, j = e - i * MP;
+        float2 gh = make_float2(0.f, 0.f), gl = make_float2(0.f, 0.f);
+        if (i < M && j < M) {
+            if (n > 0) {
+                float2 th, tl;
+                float2 vjh = vh[q][j], vjl = vl[q][j];
+                vjh.y = -vjh.y;
+                vjl.y = -vjl.y;
+                cdf_mul(Gh[e], Gl[e], vjh, vjl, th, tl);
+                cdf_mul(vh[q][i], vl[q][i], th, tl, gh, gl);
+            } else {
+                double2 v = SL[(size_t)i * M + j];
+                float a, b, c, d;
+                to_df(v.x, a, b);
+                to_df(v.y, c, d);
+                gh = make_float2(a, c);
+                gl = make_float2(b, d);
+            }
+            if (n == L - 1) {
+                double2 v = SR[(size_t)i * M + j];
+                float a, b, c, d;
+                to_df(v.x, a, b);
+                to_df(v.y, c, d);
+                cdf_add(gh, gl, make_float2(a, c), make_float2(b, d));
+            }
+        }
+        Gh[e] = gh;
+        Gl[e] = gl;
+    }
+}
+
+// Gauss-Jordan inversion of the register tile x (M x M inside MP x MP) with
+// implicit partial pivoting: no rows are moved; the pivot of column k is the
+// largest |Re|+|Im| among rows not yet used (lowest row on ties).  Column k
+// and the pivot row are zeroed in registers after staging, so every element
+// then takes the same update x -= c_i r_j (c_p = -1, r_k = 1/pivot).  On
+// return A^{-1}[k][P[k']] = x[P[k]][k'], P[k] = g.perm[k].  Returns ST_OK or
+// ST_SINGULAR (uniform over the block).
+template <int MP>
+__device__ __forceinline__ int gj_regs(float2 (&x)[MP / 16][MP / 16], int M, GJShared<MP> &g)
+{
+    constexpr int RT = MP / 16;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15, lane = tid & 31;
+    int st = ST_OK;
+    for (int i = tid; i < MP; i += NT) g.used[i] = 0;
+    __syncthreads();
+    for (int k = 0; k < M; ++k) {
+        const int q = k & 1, kt = k & 15, kb = k >> 4;
+        if (tx == kt) {
+#pragma unroll
+            for (int a = 0; a < RT; ++a) {
+                float2 v = x[a][0];
+#pragma unroll
+                for (int b = 1; b < RT; ++b)
+                    if (b == kb) v = x[a][b];
+#pragma unroll
+                for (int b = 0; b < RT; ++b)
+                    if (b == kb) x[a][b] = make_float2(0.f, 0.f);
+                const int i = ty + 16 * a;
+                g.col[q][i] = v;
+                g.val[q][i] = (i < M && !g.used[i]) ? cabs1f(v) : -1.f;
+            }
+        }
+        __syncthreads();
+        float best = -1.f;
+        int p = MP;
+        for (int i = lane; i < MP; i += 32) {
+            float v = g.val[q][i];
+            if (v > best) { best = v; p = i; }
+        }
+        warp_argmaxf(best, p);
+        if (best <= 0.f) {
+            st = ST_SINGULAR;
+            break;
+        }
+        if (ty == (p & 15)) {
+            const int pa = p >> 4;
+#pragma unroll
+            for (int a = 0; a < RT; ++a) {
+                if (a != pa) continue;
+#pragma unroll
+                for (int b = 0; b < RT; ++b) {
+                    g.rowp[q][tx + 16 * b] = x[a][b];
+                    x[a][b] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        if (tid == 0) {
+            g.perm[k] = p;
+            g.used[p] = 1;
+        }
+        __syncthreads();
+        const float2 pinv = crcpf(g.col[q][p]);
+        float2 rs[RT];
+#pragma unroll
+        for (int b = 0; b < RT; ++b) {
+            const int j = tx + 16 * b;
+            rs[b] = (j == k) ? pinv : cmulf(g.rowp[q][j], pinv);
+        }
+#pragma unroll
+        for (int a = 0; a < RT; ++a) {
+            const int i = ty + 16 * a;
+            const float2 ci = (i == p) ? make_float2(-1.f, 0.f) : g.col[q][i];
+#pragma unroll
+            for (int b = 0; b < RT; ++b) x[a][b] = cfmsf(ci, rs[b], x[a][b]);
+        }
+    }
+    if (__syncthreads_or(st != ST_OK)) return ST_SINGULAR;
+    return ST_OK;
+}
+
+// store the inverse held in x (see gj_regs) into X (MP x MP, row-major)
+template <int MP>
+__device__ __forceinline__ void store_inverse(const float2 (&x)[MP / 16][MP / 16], int M, GJShared<MP> &g,
+                              float2 *X)
+{
+    constexpr int RT = MP / 16;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    for (int k = tid; k < M; k += NT) g.pos[g.perm[k]] = k;
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int b = 0; b < RT; ++b) {
+            const int i = ty + 16 * a, c = tx + 16 * b;
+            if (i < M && c < M) X[g.pos[i] * MP + g.perm[c]] = x[a][b];
+            else X[i * MP + c] = x[a][b];
+        }
+    __syncthreads();
+}
+
+// one refinement step g = X + X R, kept as hi + lo in (Gh, Gl); R has row
+// stride RS (padded rows avoid shared-memory bank conflicts where R is
+// written one row per lane)
+template <int MP, int RS = MP>
+__device__ __forceinline__ void refine(const float2 *X, const float2 *R, float2 *Gh, float2 *Gl, int M)
+{
+    constexpr int RT = MP / 16;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float2 acc[RT][RT];
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int b = 0; b < RT; ++b) acc[a][b] = make_float2(0.f, 0.f);
+    for (int k = 0; k < M; ++k) {
+        float2 xa[RT], rb[RT];
+#pragma unroll
+        for (int a = 0; a < RT; ++a) xa[a] = X[(ty + 16 * a) * MP + k];
+#pragma unroll
+        for (int b = 0; b < RT; ++b) rb[b] = R[k * RS + tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < RT; ++a)
+#pragma unroll
+            for (int b = 0; b < RT; ++b) acc[a][b] = cfmaf(xa[a], rb[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int b = 0; b < RT; ++b) {
+            const int e = (ty + 16 * a) * MP + tx + 16 * b;
+            const float2 xv = X[e];
+            float hx, lx, hy, ly;
+            two_sum(xv.x, acc[a][b].x, hx, lx);
+            two_sum(xv.y, acc[a][b].y, hy, ly);
+            Gh[e] = make_float2(hx, hy);
+            Gl[e] = make_float2(lx, ly);
+        }
+}
+
+// Transmission from G_LL = Gh + Gl by the unitarity identity, in FP64:
+// T = Re Tr[Gamma_R i(G - G^dagger)] - Re Tr[Gamma_R G Gamma_R G^dagger].
+// G: MP*MP complex128 scratch.
+template <int MP>
+__device__ double ward_T(const float2 *Gh, const float2 *Gl, double2 *G, const double2 *SR, int M,
+                         double *red)
+{
+    const int tid = threadIdx.x;
+    for (int e = tid; e < MP * MP; e += NT) {
+        float2 h = Gh[e], l = Gl[e];
+        G[e] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
+    __syncthreads();
+    double t = 0.0;
+    for (int e = tid; e < M * M; e += NT) {
+        const int i = e / M, j = e - i * M;
+        double2 d = csub(SR[(size_t)i * M + j], cconj(SR[(size_t)j * M + i]));
+        double2 gij = make_double2(-d.y, d.x);
+        double2 u = csub(G[j * MP + i], cconj(G[i * MP + j]));
+        double2 a = make_double2(-u.y, u.x);
+        t += gij.x * a.x - gij.y * a.y;
+        double2 y = make_double2(0.0, 0.0), z = make_double2(0.0, 0.0);
+        for (int k = 0; k < M; ++k) {
+            double2 d1 = csub(SR[(size_t)i * M + k], cconj(SR[(size_t)k * M + i]));
+            double2 d2 = csub(SR[(size_t)k * M + j], cconj(SR[(size_t)j * M + k]));
+            y = cfma(make_double2(-d1.y, d1.x), G[k * MP + j], y);
+            z = cfma(G[i * MP + k], make_double2(-d2.y, d2.x), z);
+        }
+        t -= y.x * z.x + y.y * z.y;
+    }
+    return block_sum(t, red);
+}
+
+}  // namespace mixed

@@ -1,0 +1,546 @@
+// sweep_mixed_tc.cu -- mixed-precision slice sweep with the refinement
+// residual on the tcgen05 tensor cores (padded width MP = 64, i.e. M in 33..64).
+//
+// Same recursion as sweep_mixed.cu (KNIT user guide Sec. 5.3 D, Eq. 2 by
+// block elimination; complex64 Gauss-Jordan + one refinement step, state g
+// carried as hi + lo, T from G_LL by the unitarity identity).  What differs is
+// the residual R = I - A X, whose dense part Gv X must be exact to ~2^-48:
+//
+//  * X is first rounded at a per-column power-of-two scale tau_n to 24 bits,
+//    X' = tau_n 2^-8 (d0 + d1 2^-8 + d2 2^-16), |d| <= 256 integers (three
+//    bf16 "digits", exact); the refinement then uses X' consistently, so X'
+//    only needs to be a good approximate inverse, not exact;
+//  * Gv (double-float) is cut at a per-row scale sigma_i into six digits
+//    (48 bits), Gv ~= sigma_i 2^-8 sum_p e_p 2^-8p;
+//  * the complex product is the real product of [[Gr, -Gi], [Gi, Gr]]
+//    (128 x 128) with [Xr; Xi] (128 x 64), run as 15 digit products
+//    (p + q <= 5, q <= 2) per K-chunk of 16 on tcgen05.mma kind::f16 (bf16 in,
+//    f32 accumulate in tensor memory).  Digits are stored pre-scaled by
+//    2^-8p / 2^-8q, so every product of one anti-diagonal d = p + q is an
+//    integer multiple of 2^-8d below 2^24 in magnitude: the diagonals d = 0,
+//    1, 2 accumulate exactly in three accumulators, d >= 3 share a fourth;
+//  * the four accumulators are combined in double-float and scaled by
+//    sigma_i tau_n 2^-16; the sparse D X' part and the identity are added
+//    with error-free products on CUDA cores.
+// This is the Ozaki splitting (Ozaki, Ogita, Oishi & Rump 2012) with bf16
+// slices, specialised to the refinement of an approximate inverse.
+//
+// Shared-memory operand tiles use the no-swizzle K-major layout: 8-row x
+// 16-byte core matrices, K-adjacent core matrices 128 B apart (descriptor
+// leading byte offset), 8-row groups 256 B apart (stride byte offset).
+
+#include <cuda_bf16.h>
+
+#include "mixed_common.cuh"
+
+using namespace mixed;
+
+namespace {
+
+constexpr int MPT = 64;               // padded width handled here
+constexpr int NDA = 7;                // digits of Gv
+constexpr int NDB = 3;                // digits of X
+constexpr int NPROD = 18;             // digit products with q <= 2, p + q <= 6
+constexpr int NACC = 5;               // accumulators: d = 0, 1, 2, 3 exact, d >= 4 shared
+constexpr int A_TILE = 128 * 16 * 2;  // bytes of one 128 x 16 bf16 tile
+constexpr int B_TILE = 64 * 16 * 2;   // bytes of one 64 x 16 bf16 tile
+constexpr int RS = MPT + 1;           // padded row stride of R
+constexpr int GS = MPT + 1;           // padded row stride of the Gv X' buffer
+constexpr int MAX_NNZ = 256;          // sparse H0 rows cached in shared memory up to this
+constexpr uint32_t TMEM_COLS = 512;   // 5 accumulators x 64 columns, rounded up
+constexpr long WAIT_LIMIT = 1L << 24; // bounded mbarrier polling
+
+__constant__ int c_prod_p[NPROD] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 4, 3, 2, 5, 4, 3, 6, 5, 4};
+__constant__ int c_prod_q[NPROD] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 0, 1, 2, 0, 1, 2, 0, 1, 2};
+
+struct TcSmem {
+    float2 X[MPT * MPT];                         // inverse, then X' (rounded)
+    union {
+        unsigned char adig[2 * NDA * A_TILE];    // A digits of two K-chunks
+        float2 R[MPT * RS];                      // residual (after the products)
+    } u;
+    union {
+        struct {
+            unsigned char bdig[NDB * 8 * B_TILE];  // B digits of all 8 K-chunks
+            float2 Gh[MPT * MPT];                  // g (hi) / Gv (hi)
+            float2 Gl[MPT * MPT];                  // g (lo) / Gv (lo)
+        } s;
+        float2 gvx[2 * MPT * GS];                // Gv X' as (hi, lo) per row of [Re; Im]
+    } w;
+    GJShared<MPT> gj;
+    double eps[MPT];
+    float2 vh[2][MPT];
+    float2 vl[2][MPT];
+    int rexp[MPT];
+    int cexp[MPT];
+    float cmax[4][MPT];
+    int h0rp[MPT + 1];
+    int h0c[MAX_NNZ];
+    float2 h0h[MAX_NNZ];
+    float2 h0l[MAX_NNZ];
+    double red[NT / 32];
+    unsigned long long mbar;
+    uint32_t tmem;
+    int inst;
+};
+
+KNIT_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+KNIT_DEV int tile_off(int r, int c) { return (r >> 3) * 256 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2; }
+
+KNIT_DEV uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;     // K-adjacent core matrices
+    d |= (uint64_t)(256 >> 4) << 32;     // 8-row groups
+    d |= (uint64_t)1 << 46;              // descriptor version
+    return d;
+}
+
+KNIT_DEV void put_bf16(unsigned char *tile, int r, int c, float v)
+{
+    *reinterpret_cast<__nv_bfloat16 *>(tile + tile_off(r, c)) = __float2bfloat16_rn(v);
+}
+
+// two K-adjacent values (c even) in one 32-bit store
+KNIT_DEV void put_bf16x2(unsigned char *tile, int r, int c, float v0, float v1)
+{
+    *reinterpret_cast<__nv_bfloat162 *>(tile + tile_off(r, c)) = __floats2bfloat162_rn(v0, v1);
+}
+
+// 2^e as a float for |e| <= 126 (exact power of two)
+KNIT_DEV float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+KNIT_DEV void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(tmem_d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+KNIT_DEV void mma_commit(unsigned long long *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// bounded wait for the mbarrier phase `parity`; returns 0 on timeout
+KNIT_DEV int mbar_wait(unsigned long long *mbar, uint32_t parity)
+{
+    uint32_t done = 0;
+    for (long it = 0; it < WAIT_LIMIT; ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+        if (done) return 1;
+    }
+    return 0;
+}
+
+KNIT_DEV void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
+KNIT_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+KNIT_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+KNIT_DEV void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// exponent e with |v| < 2^e for the largest |v| (0 for an all-zero set)
+KNIT_DEV int scale_exp(float mx)
+{
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    return e;
+}
+
+__global__ void fill_status(int *st, int n, int v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) st[i] = v;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(NT, 1)
+knit_sweep_mixed_tc_kernel(SysDev s, InstDev in)
+{
+    constexpr int RT = MPT / 16;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
+    float2 *const Gh = sm.w.s.Gh;
+    float2 *const Gl = sm.w.s.Gl;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int M = s.M, L = s.L;
+    const size_t MM = (size_t)M * M;
+    // D f32, A and B bf16, both K-major, N = 64, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
+                           ((128u >> 4) << 24);
+
+    // per-launch constants: diagonal of V as double-float, sparse H0 rows
+    for (int q = 0; q < 2; ++q)
+        for (int i = tid; i < MPT; i += NT) {
+            double2 v = make_double2(0.0, 0.0);
+            if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
+            float hx, lx, hy, ly;
+            to_df(v.x, hx, lx);
+            to_df(v.y, hy, ly);
+            sm.vh[q][i] = make_float2(hx, hy);
+            sm.vl[q][i] = make_float2(lx, ly);
+        }
+    const int nnz = s.h0_rowptr[M];
+    const bool h0_cached = nnz <= MAX_NNZ;
+    for (int i = tid; i <= MPT; i += NT) sm.h0rp[i] = s.h0_rowptr[min(i, M)];
+    if (h0_cached)
+        for (int c = tid; c < nnz; c += NT) {
+            const double2 h = s.h0_val[c];
+            float a, b, cc, d;
+            to_df(h.x, a, b);
+            to_df(h.y, cc, d);
+            sm.h0c[c] = s.h0_col[c];
+            sm.h0h[c] = make_float2(a, cc);
+            sm.h0l[c] = make_float2(b, d);
+        }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&sm.tmem)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    for (;;) {
+        if (tid == 0) sm.inst = atomicAdd(in.queue, 1);
+        __syncthreads();
+        const int inst = sm.inst;
+        __syncthreads();
+        if (inst >= in.n) break;
+        const int ie = inst / in.nS;
+        const double E = in.E[ie];
+        const uint64_t ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
+        const double W = in.W;
+        const double2 *SL = in.sigL + (size_t)ie * MM;
+        const double2 *SR = in.sigR + (size_t)ie * MM;
+        int st = in.lstatus ? in.lstatus[ie] : ST_OK;
+
+        for (int n = 0; n < L && st == ST_OK; ++n) {
+            slice_diag<MPT>(sm.eps, s, ms, W, E, n);
+            form_gv<MPT>(Gh, Gl, sm.vh, sm.vl, M, n, L, SL, SR);
+            __syncthreads();
+
+            // row scales of Gv: warp w takes rows 8w..8w+7, lanes run along the row
+            for (int r = 0; r < 8; ++r) {
+                const int i = 8 * warp + r;
+                const float2 g0 = Gh[i * MPT + lane], g1 = Gh[i * MPT + lane + 32];
+                float mx = fmaxf(fmaxf(fabsf(g0.x), fabsf(g0.y)), fmaxf(fabsf(g1.x), fabsf(g1.y)));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                if (lane == 0) sm.rexp[i] = scale_exp(mx);
+            }
+
+            // X = fl32(D - Gv_hi): staged in shared memory (diagonal, then the
+            // sparse H0 rows, one row per thread), then loaded into registers
+            for (int e = tid; e < MPT * MPT; e += NT) {
+                const int i = e >> 6, j = e & 63;
+                float2 v;
+                if (i < M && j < M) {
+                    const float2 g = Gh[e];
+                    v = make_float2(-g.x, -g.y);
+                    if (i == j) v.x += (float)sm.eps[i];
+                } else {
+                    v = make_float2(i == j ? 1.f : 0.f, 0.f);
+                }
+                sm.X[e] = v;
+            }
+            __syncthreads();
+            for (int i = tid; i < M; i += NT)
+                for (int c = sm.h0rp[i]; c < sm.h0rp[i + 1]; ++c) {
+                    int col;
+                    float2 h;
+                    if (h0_cached) {
+                        col = sm.h0c[c];
+                        h = sm.h0h[c];
+                    } else {
+                        col = s.h0_col[c];
+                        const double2 hd = s.h0_val[c];
+                        h = make_float2((float)hd.x, (float)hd.y);
+                    }
+                    float2 &v = sm.X[i * MPT + col];
+                    v.x -= h.x;
+                    v.y -= h.y;
+                }
+            __syncthreads();
+            float2 x[RT][RT];
+#pragma unroll
+            for (int a = 0; a < RT; ++a)
+#pragma unroll
+                for (int b = 0; b < RT; ++b) x[a][b] = sm.X[(ty + 16 * a) * MPT + tx + 16 * b];
+            st = gj_regs<MPT>(x, M, sm.gj);
+            if (st != ST_OK) break;
+            store_inverse<MPT>(x, M, sm.gj, sm.X);
+
+            // column scales of X: thread t scans rows 16 (t / 64) .. of column t % 64
+            {
+                const int nn = tid & 63, part = tid >> 6;
+                float mx = 0.f;
+#pragma unroll 4
+                for (int k = part * 16; k < part * 16 + 16; ++k) {
+                    const float2 v = sm.X[k * MPT + nn];
+                    mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+                }
+                sm.cmax[part][nn] = mx;
+            }
+            __syncthreads();
+            if (tid < MPT)
+                sm.cexp[tid] = scale_exp(fmaxf(fmaxf(sm.cmax[0][tid], sm.cmax[1][tid]),
+                                               fmaxf(sm.cmax[2][tid], sm.cmax[3][tid])));
+            __syncthreads();
+
+            // B digits (three per value) and X' = X rounded to them; work item
+            // e takes X[k][nn] and X[k+1][nn] (k even), lanes along nn, so each
+            // digit pair is one 32-bit store into B^T[nn][k..k+1]
+            for (int e = tid; e < MPT * MPT / 2; e += NT) {
+                const int k = (e >> 6) * 2, nn = e & 63;
+                const int ce = sm.cexp[nn];
+                const float dn = pow2f(-ce), up = pow2f(ce - 8);
+                float d[2][2][NDB];   // [row k / k+1][re / im][digit]
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float2 xv = sm.X[(k + r) * MPT + nn];
+                    float re, im;
+#pragma unroll
+                    for (int part = 0; part < 2; ++part) {
+                        float a = (part ? xv.y : xv.x) * dn;
+#pragma unroll
+                        for (int q = 0; q < NDB; ++q) {
+                            a *= 256.f;
+                            d[r][part][q] = rintf(a);
+                            a -= d[r][part][q];
+                        }
+                        const float xr = (d[r][part][0] + d[r][part][1] * 0.00390625f +
+                                          d[r][part][2] * 1.52587890625e-05f) * up;
+                        if (part) im = xr; else re = xr;
+                    }
+                    sm.X[(k + r) * MPT + nn] = make_float2(re, im);
+                }
+#pragma unroll
+                for (int part = 0; part < 2; ++part) {
+                    const int K = k + 64 * part;
+                    unsigned char *t = sm.w.s.bdig + (K >> 4) * B_TILE;
+                    float sc = 1.f;
+#pragma unroll
+                    for (int q = 0; q < NDB; ++q) {
+                        put_bf16x2(t + q * 8 * B_TILE, nn, K & 15, d[0][part][q] * sc,
+                                   d[1][part][q] * sc);
+                        sc *= 0.00390625f;
+                    }
+                }
+            }
+
+            // products: four groups, each two K-chunks sharing Gv columns 16g..16g+15
+            int first = (1 << NACC) - 1;   // accumulators not yet written this slice
+            for (int g = 0; g < 4 && !timed_out; ++g) {
+                if (g > 0) {
+                    const int ok = tid == 0 ? mbar_wait(&sm.mbar, phase) : 1;
+                    phase ^= 1u;
+                    if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                }
+                // A digits of Gv columns 16g..16g+15: chunk slot 0 holds K-chunk g
+                // (rows < 64: Gr, rows >= 64: Gi), slot 1 K-chunk g+4 (-Gi, Gr);
+                // work item e takes row i, columns kk and kk+1 (one 32-bit store)
+                for (int e = tid; e < MPT * 8; e += NT) {
+                    const int i = e >> 3, kk = (e & 7) * 2, k = 16 * g + kk;
+                    const float dn = pow2f(-sm.rexp[i]);
+                    const float2 gh0 = Gh[i * MPT + k], gl0 = Gl[i * MPT + k];
+                    const float2 gh1 = Gh[i * MPT + k + 1], gl1 = Gl[i * MPT + k + 1];
+                    // [column][re / im] running double-float remainders
+                    float ah[2][2] = {{gh0.x * dn, gh0.y * dn}, {gh1.x * dn, gh1.y * dn}};
+                    float al[2][2] = {{gl0.x * dn, gl0.y * dn}, {gl1.x * dn, gl1.y * dn}};
+                    unsigned char *t0 = sm.u.adig;
+                    unsigned char *t1 = sm.u.adig + NDA * A_TILE;
+                    float scale = 1.f;
+#pragma unroll
+                    for (int p = 0; p < NDA; ++p) {
+                        float dg[2][2];
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+#pragma unroll
+                            for (int part = 0; part < 2; ++part) {
+                                float h = ah[c][part] * 256.f, l = al[c][part] * 256.f;
+                                const float d = rintf(h);
+                                h -= d;
+                                two_sum(h, l, ah[c][part], al[c][part]);
+                                dg[c][part] = d * scale;
+                            }
+                        scale *= 0.00390625f;
+                        put_bf16x2(t0 + p * A_TILE, i, kk, dg[0][0], dg[1][0]);        // Gr
+                        put_bf16x2(t1 + p * A_TILE, i + 64, kk, dg[0][0], dg[1][0]);   // Gr
+                        put_bf16x2(t0 + p * A_TILE, i + 64, kk, dg[0][1], dg[1][1]);   // Gi
+                        put_bf16x2(t1 + p * A_TILE, i, kk, -dg[0][1], -dg[1][1]);      // -Gi
+                    }
+                }
+                async_proxy_fence();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    for (int slot = 0; slot < 2; ++slot) {
+                        const int chunk = g + 4 * slot;
+                        for (int pr = 0; pr < NPROD; ++pr) {
+                            const int p = c_prod_p[pr], q = c_prod_q[pr];
+                            const int acc = min(p + q, NACC - 1);
+                            const uint64_t ad =
+                                smem_desc(smem_u32(sm.u.adig + (slot * NDA + p) * A_TILE));
+                            const uint64_t bd =
+                                smem_desc(smem_u32(sm.w.s.bdig + (q * 8 + chunk) * B_TILE));
+                            mma_bf16(tmem + acc * 64, ad, bd, idesc, (first >> acc) & 1 ? 0u : 1u);
+                            first &= ~(1 << acc);
+                        }
+                    }
+                    mma_commit(&sm.mbar);
+                }
+            }
+            if (!timed_out) {
+                const int ok = tid == 0 ? mbar_wait(&sm.mbar, phase) : 1;
+                phase ^= 1u;
+                if (__syncthreads_or(!ok)) timed_out = true;
+            }
+            if (timed_out) {
+                st = ST_TIMEOUT;
+                break;
+            }
+            tc_fence_after();
+
+            // Gv X' = sigma_i tau_n 2^-16 (D0 + D1 + D2 + D3 + D4+), as (hi, lo):
+            // lane m of warp w holds row 32 (w % 4) + lane, columns 32 (w / 4) ..
+            {
+                const int m = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);
+                const int re = sm.rexp[m & 63];
+                const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0;
+                for (int j8 = 0; j8 < 32; j8 += 8) {
+                    uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
+                    tmem_ld8(tb + j8, v0);
+                    tmem_ld8(tb + 64 + j8, v1);
+                    tmem_ld8(tb + 128 + j8, v2);
+                    tmem_ld8(tb + 192 + j8, v3);
+                    tmem_ld8(tb + 256 + j8, v4);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int jx = 0; jx < 8; ++jx) {
+                        const int nn = c0 + j8 + jx;
+                        float hs, ls, t, te;
+                        two_sum(__uint_as_float(v0[jx]), __uint_as_float(v1[jx]), hs, ls);
+                        two_sum(hs, __uint_as_float(v2[jx]), t, te);
+                        ls += te;
+                        two_sum(t, __uint_as_float(v3[jx]), hs, te);
+                        ls += te;
+                        two_sum(hs, __uint_as_float(v4[jx]), t, te);
+                        ls += te;
+                        two_sum(t, ls, hs, ls);
+                        const float sc = pow2f(re + sm.cexp[nn] - 16);
+                        sm.w.gvx[m * GS + nn] = make_float2(hs * sc, ls * sc);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+
+            // R = I - D X' + Gv X' with error-free products, one element per (ty, tx) slot
+#pragma unroll
+            for (int a = 0; a < RT; ++a) {
+                const int i = ty + 16 * a;
+                float dh = 0.f, dl = 0.f;
+                if (i < M) to_df(sm.eps[i], dh, dl);
+#pragma unroll
+                for (int b = 0; b < RT; ++b) {
+                    const int j = tx + 16 * b;
+                    float2 r = make_float2(0.f, 0.f);
+                    if (i < M && j < M) {
+                        const float2 pr = sm.w.gvx[i * GS + j], pi = sm.w.gvx[(i + 64) * GS + j];
+                        float sr = pr.x, er = pr.y, si = pi.x, ei = pi.y;
+                        const float2 xij = sm.X[i * MPT + j];
+                        dot2_acc(-dh, -dl, xij.x, sr, er);
+                        dot2_acc(-dh, -dl, xij.y, si, ei);
+                        for (int c = sm.h0rp[i]; c < sm.h0rp[i + 1]; ++c) {
+                            int col;
+                            float2 hh, hl;
+                            if (h0_cached) {
+                                col = sm.h0c[c];
+                                hh = sm.h0h[c];
+                                hl = sm.h0l[c];
+                            } else {
+                                col = s.h0_col[c];
+                                const double2 hd = s.h0_val[c];
+                                to_df(hd.x, hh.x, hl.x);
+                                to_df(hd.y, hh.y, hl.y);
+                            }
+                            const float2 xc = sm.X[col * MPT + j];
+                            dot2_acc(hh.x, hl.x, xc.x, sr, er);
+                            dot2_acc(-hh.y, -hl.y, xc.y, sr, er);
+                            dot2_acc(hh.x, hl.x, xc.y, si, ei);
+                            dot2_acc(hh.y, hl.y, xc.x, si, ei);
+                        }
+                        if (i == j) {
+                            float t, te;
+                            two_sum(sr, 1.0f, t, te);
+                            sr = t;
+                            er += te;
+                        }
+                        r = make_float2(sr + er, si + ei);
+                    }
+                    sm.u.R[i * RS + j] = r;
+                }
+            }
+            __syncthreads();
+            refine<MPT, RS>(sm.X, sm.u.R, Gh, Gl, M);
+            __syncthreads();
+        }
+
+        double T = 0.0;
+        if (st == ST_OK) {
+            T = ward_T<MPT>(Gh, Gl, reinterpret_cast<double2 *>(sm.X), SR, M, sm.red);
+            if (!isfinite(T)) st = ST_NONFINITE;
+        }
+        if (tid == 0) {
+            in.T[inst] = T;
+            if (in.status) in.status[inst] = st;
+        }
+        __syncthreads();
+        if (timed_out) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// Host launch helper.  Instances that a timed-out CTA never reaches keep the
+// ST_TIMEOUT status written here first.
+extern "C" cudaError_t knit_launch_mixed_tc(const SysDev *s, const InstDev *in, int grid,
+                                            cudaStream_t stream)
+{
+    if (s->M > MPT || s->M <= 32) return cudaErrorInvalidValue;
+    static_assert(sizeof(TcSmem) <= 227 * 1024, "shared memory budget");
+    if (in->status) fill_status<<<(in->n + 255) / 256, 256, 0, stream>>>(in->status, in->n, ST_TIMEOUT);
+    size_t smb = sizeof(TcSmem);
+    cudaError_t e = cudaFuncSetAttribute(knit_sweep_mixed_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    if (e != cudaSuccess) return e;
+    knit_sweep_mixed_tc_kernel<<<grid, NT, smb, stream>>>(*s, *in);
+    return cudaGetLastError();
+}
+
+extern "C" size_t knit_mixed_tc_smem_bytes(void) { return sizeof(TcSmem); }

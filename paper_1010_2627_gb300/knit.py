@@ -21,7 +21,7 @@ from . import build as _build
 
 KNIT_OK, KNIT_ERR_INVALID, KNIT_ERR_OOM, KNIT_ERR_CUDA = 0, 1, 2, 3
 KNIT_ERR_SINGULAR, KNIT_ERR_NOCONVERGE, KNIT_ERR_TIMEOUT, KNIT_ERR_NONFINITE = 4, 5, 6, 7
-KNIT_FP64, KNIT_MIXED = 0, 1
+KNIT_FP64, KNIT_MIXED, KNIT_MIXED_CUDACORE = 0, 1, 2
 KNIT_LEAD_AUTO, KNIT_LEAD_MODES, KNIT_LEAD_DECIMATION = 0, 1, 2
 
 P = ctypes.c_void_p
