@@ -323,6 +323,65 @@ def run_knit(args):
         torch.distributed.destroy_process_group()
 
 
+def run_uneven(args):
+    """Uneven batch: 4096 square-lattice instances, M in {32,48,64,96,128},
+    L in {128,...,2048}, W ~ U[0,4], E ~ U(-3.9,3.9), seed = index, drawn from
+    a sampler seeded 12345; one plan, mixed precision (widths above 64 run the
+    FP64 sweep).  One step = lead self-energies + sweeps for all instances."""
+    import torch
+    from paper_1010_2627_gb300 import build, inputs, knit
+    build.build()
+    knit.load()
+    inst = inputs.uneven_instances(4096)
+    keys = sorted(set(zip(inst["M"].tolist(), inst["L"].tolist())))
+    systems = [knit.System(inputs.square(m, l)) for m, l in keys]
+    sys_index = np.array([keys.index((m, l)) for m, l in zip(inst["M"], inst["L"])], np.int32)
+    batch = knit.Batch(systems, sys_index, precision=knit.KNIT_MIXED)
+    n = len(sys_index)
+    stream = torch.cuda.Stream()
+    dE = torch.tensor(inst["E"], device="cuda")
+    ds = torch.tensor(inst["seeds"].astype(np.int64), device="cuda")
+    dW = torch.tensor(inst["W"], device="cuda")
+    dT = torch.empty(n, dtype=torch.float64, device="cuda")
+    dst = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        knit.knit_batch_transmission(batch.handle, dE, ds, dW, dT, dst, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+    torch.cuda.synchronize()
+    clocks = _clock_sampler()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    st = dst.cpu().numpy()
+    slices = int(inst["L"].sum())
+    mixed_mask = inst["M"] <= 64
+    print(json.dumps({
+        "metric": "T(E) points/s (uneven batch)", "value": n / (ms / 1e3),
+        "unit": "T(E) points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed for M <= 64, f64 above", "data": "synthetic",
+        "config": {"workload": "uneven square batch, 4096 instances, M in {32..128}, "
+                               "L in {128..2048}, W ~ U[0,4]", "systems": len(keys),
+                   "instances_mixed": int(mixed_mask.sum()),
+                   "flush": "L2 flushed before every timed step"},
+        "slice_updates_per_s": slices / (ms / 1e3), "clocks": _clock_summary(clocks, 0),
+        "status_nonzero": int((st != 0).sum())}), flush=True)
+    batch.close()
+
+
 def run_profile_case(args):
     """Small case for ncu captures: M=64, L=64, 19 energies x 8 seeds (one
     wave of 152 instances), one mixed and one FP64 sweep after a warm-up."""
@@ -346,7 +405,7 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "uneven"])
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -358,6 +417,8 @@ def main():
         args.warmup = 3
     if args.case == "profile":
         run_profile_case(args)
+    elif args.case == "uneven":
+        run_uneven(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

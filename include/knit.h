@@ -74,7 +74,9 @@ enum {
                        residual exact to ~2^-48; the state g_n is carried as
                        hi + lo floats.  For 33 <= M <= 64 the residual's dense
                        product runs on the tensor cores (bf16 digit slices,
-                       f32 accumulation), otherwise on CUDA cores */
+                       f32 accumulation), otherwise on CUDA cores.  Systems
+                       with M > 64 or non-diagonal inter-slice couplings run
+                       the KNIT_FP64 sweep instead. */
     KNIT_MIXED_CUDACORE = 2  /* KNIT_MIXED with the residual always accumulated
                                 in double-float arithmetic on CUDA cores */
 };
@@ -137,8 +139,7 @@ knit_status knit_lead_selfenergy(knit_system sys, int32_t lead, const double *E,
 
 /* Two-terminal transmission T_i (Sec. 2.3) for nE * nS instances.  The lead
  * self-energies are computed once per energy on the device (opts may be
- * NULL: AUTO).  precision: KNIT_FP64 or KNIT_MIXED (KNIT_MIXED needs
- * diagonal inter-slice couplings and M <= 64).  T: nE*nS outputs; status
+ * NULL: AUTO).  precision: KNIT_FP64, KNIT_MIXED or KNIT_MIXED_CUDACORE.  T: nE*nS outputs; status
  * (optional): nE*nS knit_status values. */
 knit_status knit_transmission(knit_system sys, const double *E, int32_t nE,
                               const uint64_t *seeds, int32_t nS, double W, int32_t precision,
@@ -162,6 +163,30 @@ knit_status knit_transmission_sigma(knit_system sys, const double *E, int32_t nE
 knit_status knit_ldos(knit_system sys, const double *E, int32_t nE, const uint64_t *seeds,
                       int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
                       double *ldos, double *T, int32_t *status, void *stream);
+
+/* Heterogeneous batches (uneven widths and lengths).  A batch plan holds
+ * nInst instances; instance i belongs to systems[sys_index[i]] (sys_index is
+ * read during the call; systems must outlive the plan and must not run other
+ * calls while the plan runs).  The plan groups instances per system for the
+ * lead solvers and per sweep kernel for the sweep, and orders each kernel's
+ * queue by decreasing cost M^3 L (longest processing time first), so each
+ * kernel variant is one persistent launch.  KNIT_MIXED instances whose
+ * system has M > 64 or non-diagonal couplings run in the FP64 sweep.  Lead
+ * eigen-decompositions are done here, so that a run with device pointers
+ * only enqueues kernels and can be captured in a CUDA graph. */
+typedef struct knit_batch_s *knit_batch;
+
+knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const int32_t *sys_index,
+                              int32_t nInst, int32_t precision, knit_batch *out);
+
+knit_status knit_batch_destroy(knit_batch batch);
+
+/* Run a plan: E, seeds and W hold one value per instance (seeds, W may be
+ * NULL: seed 0, no disorder); T and status (optional) receive one value per
+ * instance, in the caller's instance order (Sec. 2.3 transmission). */
+knit_status knit_batch_transmission(knit_batch batch, const double *E, const uint64_t *seeds,
+                                    const double *W, const knit_lead_opts *opts, double *T,
+                                    int32_t *status, void *stream);
 
 /* Lead self-energy by Sancho-Rubio decimation without any allocation (the
  * paper has no counterpart; it exists for callers that cannot let a library

@@ -16,12 +16,12 @@
 #include "../../include/knit.h"
 #include "knit_common.cuh"
 
-extern "C" cudaError_t knit_launch_sweep_fp64(const SysDev *, const InstDev *, int, double2 *, int,
+extern "C" cudaError_t knit_launch_sweep_fp64(const InstDev *, int, int, double2 *, int,
                                               cudaStream_t);
-extern "C" cudaError_t knit_launch_ldos_fp64(const SysDev *, const InstDev *, int, double2 *, int,
-                                             double2 *, int, double *, cudaStream_t);
+extern "C" cudaError_t knit_launch_ldos_fp64(const InstDev *, int, int, int, double2 *, int,
+                                             double2 *, int, double *, long long, cudaStream_t);
 extern "C" size_t knit_fp64_smem_bytes(int, int, int);
-extern "C" cudaError_t knit_launch_mixed_impl(const SysDev *, const InstDev *, int, int, cudaStream_t);
+extern "C" cudaError_t knit_launch_mixed_impl(const InstDev *, int, int, int, cudaStream_t);
 extern "C" int knit_mixed_max_M(void);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
 extern "C" cudaError_t knit_launch_modes_sigma(const double2 *, const double2 *, int, double,
@@ -113,6 +113,7 @@ struct knit_system_s {
     int device = 0, nsm = 1;
     double2 *H0 = nullptr, *V = nullptr, *h0_val = nullptr;
     double *sign = nullptr, *onsite = nullptr;
+    SysDev *d_sys = nullptr;   // device copy of dev() for the kernels' system table
     int *h0_rowptr = nullptr, *h0_col = nullptr;
     Lead lead[2];
     int leads_same = 0;
@@ -335,19 +336,20 @@ __global__ void combine_status(int *a, const int *b, int n)
 
 knit_status run_sweep(knit_system s, InstDev in, int precision, cudaStream_t st)
 {
-    SysDev sd = s->dev();
+    in.sys = s->d_sys;
     CK(s->queue.ensure(sizeof(int)), "queue");
     in.queue = s->queue.as<int>();
     CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
     const int grid = std::max(1, std::min(in.n, s->nsm));
-    if (precision == KNIT_MIXED || precision == KNIT_MIXED_CUDACORE) {
-        CK(knit_launch_mixed_impl(&sd, &in, grid, precision == KNIT_MIXED, st), "mixed sweep launch");
+    const bool mixed_ok = s->M <= knit_mixed_max_M() && s->vb == 1;
+    if ((precision == KNIT_MIXED || precision == KNIT_MIXED_CUDACORE) && mixed_ok) {
+        CK(knit_launch_mixed_impl(&in, s->M, grid, precision == KNIT_MIXED, st), "mixed sweep launch");
         return KNIT_OK;
     }
     const size_t MM = (size_t)s->M * s->M;
     int use_smem = knit_fp64_smem_bytes(s->M, 1, 3) <= 220 * 1024;
     if (!use_smem) CK(s->work.ensure(sizeof(double2) * 3 * MM * grid), "sweep workspace");
-    CK(knit_launch_sweep_fp64(&sd, &in, grid, s->work.as<double2>(), use_smem, st),
+    CK(knit_launch_sweep_fp64(&in, s->M, grid, s->work.as<double2>(), use_smem, st),
        "fp64 sweep launch");
     return KNIT_OK;
 }
@@ -360,12 +362,6 @@ knit_status check_batch(knit_system s, const double *E, int nE, int nS, int prec
     if (!std::isfinite(W)) return fail(KNIT_ERR_INVALID, "W is not finite");
     if (precision != KNIT_FP64 && precision != KNIT_MIXED && precision != KNIT_MIXED_CUDACORE)
         return fail(KNIT_ERR_INVALID, "unknown precision %d", precision);
-    if (precision != KNIT_FP64) {
-        if (s->M > knit_mixed_max_M())
-            return fail(KNIT_ERR_INVALID, "KNIT_MIXED supports M <= %d (M = %d)", knit_mixed_max_M(),
-                        s->M);
-        if (s->vb != 1) return fail(KNIT_ERR_INVALID, "KNIT_MIXED needs diagonal inter-slice V");
-    }
     return KNIT_OK;
 }
 
@@ -379,6 +375,64 @@ knit_status finish(cudaStream_t st, bool sync, const char *what)
 }  // namespace
 
 // ===========================================================================
+// Heterogeneous batches: instances of several systems, grouped per system for
+// the lead solvers and per kernel variant ("bucket") for the sweep, each
+// bucket's queue in decreasing cost M^3 L (longest-processing-time order).
+
+namespace {
+
+__global__ void gather_instances(const double *E, const uint64_t *seeds, const double *W,
+                                 const int *perm, int n, double *Ep, uint64_t *Sp, double *Wp)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int i = perm[p];
+    Ep[p] = E[i];
+    Sp[p] = seeds ? seeds[i] : 0ull;
+    Wp[p] = W ? W[i] : 0.0;
+}
+
+__global__ void fill_int(int *a, int n, int v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+}  // namespace
+
+struct knit_batch_s {
+    struct Bucket {
+        int kind = 0;          // 0 FP64 sweep, 1 mixed (CUDA-core or tensor-core residual)
+        int use_tc = 0;
+        int Mmax = 0, Lmax = 0;
+        std::vector<int> order;   // plan positions in cost order
+        DevBuf d_order;
+    };
+    int nInst = 0, precision = 0, device = 0, nsm = 1;
+    std::vector<knit_system> sys;            // distinct systems (not owned)
+    std::vector<int> perm;                   // plan position -> caller's instance
+    std::vector<int> start, count;           // per system: first plan position, count
+    std::vector<long long> sig_off;          // per plan position (elements)
+    long long sig_total = 0, g_max = 0;
+    std::vector<Bucket> buckets;
+    DevBuf d_systab, d_sys_of, d_perm, d_sig_off, E, seeds, W, Ep, Sp, Wp, sigL, sigR, gbuf,
+        lst, T, status, queue, work;
+};
+
+namespace {
+
+knit_status batch_release(knit_batch b)
+{
+    DevBuf *bufs[] = {&b->d_systab, &b->d_sys_of, &b->d_perm, &b->d_sig_off, &b->E, &b->seeds,
+                      &b->W, &b->Ep, &b->Sp, &b->Wp, &b->sigL, &b->sigR, &b->gbuf, &b->lst,
+                      &b->T, &b->status, &b->queue, &b->work};
+    for (DevBuf *x : bufs) x->release();
+    for (auto &bk : b->buckets) bk.d_order.release();
+    return KNIT_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *knit_last_error(void) { return g_err.c_str(); }
@@ -482,6 +536,13 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
             return r;
         }
     }
+    {
+        SysDev sd = s->dev();
+        if ((r = to_device(&s->d_sys, &sd, 1, "system table")) != KNIT_OK) {
+            knit_system_destroy(s);
+            return r;
+        }
+    }
     *out = s;
     return KNIT_OK;
 }
@@ -497,6 +558,7 @@ knit_status knit_system_destroy(knit_system s)
     cudaFree(s->h0_rowptr);
     cudaFree(s->h0_col);
     cudaFree(s->h0_val);
+    cudaFree(s->d_sys);
     for (int p = 0; p < 2; ++p) {
         cudaFree(s->lead[p].H0);
         cudaFree(s->lead[p].V);
@@ -653,7 +715,7 @@ knit_status knit_ldos(knit_system s, const double *E, int32_t nE, const uint64_t
     if ((r = stage_out(s->T, T, (size_t)n, &in.T, &hT, "T")) != KNIT_OK) return r;
     if ((r = stage_out(s->status, (int *)status, (size_t)n, &in.status, &hSt, "status")) != KNIT_OK)
         return r;
-    SysDev sd = s->dev();
+    in.sys = s->d_sys;
     CK(s->queue.ensure(sizeof(int)), "queue");
     in.queue = s->queue.as<int>();
     CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
@@ -662,14 +724,226 @@ knit_status knit_ldos(knit_system s, const double *E, int32_t nE, const uint64_t
     if (!use_smem) CK(s->work.ensure(sizeof(double2) * 4 * MM * grid), "ldos workspace");
     const int nck = (s->L + save - 1) / save;
     CK(s->ckpt.ensure(sizeof(double2) * MM * (size_t)(nck + save) * grid), "checkpoint workspace");
-    CK(knit_launch_ldos_fp64(&sd, &in, grid, s->work.as<double2>(), use_smem, s->ckpt.as<double2>(),
-                             save, dL, st),
+    CK(knit_launch_ldos_fp64(&in, s->M, s->L, grid, s->work.as<double2>(), use_smem,
+                             s->ckpt.as<double2>(), save, dL, (long long)s->L * s->M, st),
        "ldos launch");
     if (hL) CK(cudaMemcpyAsync(ldos, dL, sizeof(double) * n * s->L * s->M, cudaMemcpyDeviceToHost, st), "ldos out");
     if (hT) CK(cudaMemcpyAsync(T, in.T, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
     if (hSt)
         CK(cudaMemcpyAsync(status, in.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
     return finish(st, hL || hT || hSt, "knit_ldos");
+}
+
+
+knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const int32_t *sys_index,
+                              int32_t nInst, int32_t precision, knit_batch *out)
+{
+    if (!systems || !sys_index || !out || nSys <= 0 || nInst <= 0)
+        return fail(KNIT_ERR_INVALID, "knit_batch_create: bad arguments");
+    if (precision != KNIT_FP64 && precision != KNIT_MIXED && precision != KNIT_MIXED_CUDACORE)
+        return fail(KNIT_ERR_INVALID, "unknown precision %d", precision);
+    *out = nullptr;
+    std::vector<int> idx;
+    knit_status r = to_host(idx, sys_index, (size_t)nInst, "sys_index");
+    if (r != KNIT_OK) return r;
+    for (int i = 0; i < nSys; ++i)
+        if (!systems[i]) return fail(KNIT_ERR_INVALID, "systems[%d] is NULL", i);
+    for (int v : idx)
+        if (v < 0 || v >= nSys) return fail(KNIT_ERR_INVALID, "sys_index out of range");
+    knit_batch b = new (std::nothrow) knit_batch_s;
+    if (!b) return fail(KNIT_ERR_OOM, "host allocation");
+    b->nInst = nInst;
+    b->precision = precision;
+    b->sys.assign(systems, systems + nSys);
+    cudaGetDevice(&b->device);
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->device);
+    // plan order: instances grouped by system
+    b->start.assign(nSys, 0);
+    b->count.assign(nSys, 0);
+    for (int v : idx) b->count[v]++;
+    for (int k = 1; k < nSys; ++k) b->start[k] = b->start[k - 1] + b->count[k - 1];
+    b->perm.assign(nInst, 0);
+    std::vector<int> fill(b->start), sys_of(nInst);
+    for (int i = 0; i < nInst; ++i) {
+        const int p = fill[idx[i]]++;
+        b->perm[p] = i;
+        sys_of[p] = idx[i];
+    }
+    b->sig_off.assign(nInst, 0);
+    long long off = 0;
+    for (int k = 0; k < nSys; ++k) {
+        const long long MM = (long long)b->sys[k]->M * b->sys[k]->M;
+        for (int j = 0; j < b->count[k]; ++j) b->sig_off[b->start[k] + j] = off + j * MM;
+        off += MM * b->count[k];
+        b->g_max = std::max(b->g_max, MM * b->count[k]);
+    }
+    b->sig_total = off;
+    // buckets by kernel variant
+    auto kind_of = [&](knit_system s, int *use_tc, int *cls) {
+        const bool mixed_ok = precision != KNIT_FP64 && s->vb == 1 && s->M <= knit_mixed_max_M();
+        if (!mixed_ok) { *use_tc = 0; *cls = 0; return 0; }
+        *use_tc = precision == KNIT_MIXED && s->M > 32;
+        *cls = s->M <= 16 ? 1 : s->M <= 32 ? 2 : (*use_tc ? 3 : 4);
+        return 1;
+    };
+    std::vector<int> cls_bucket(5, -1);
+    for (int p = 0; p < nInst; ++p) {
+        knit_system s = b->sys[sys_of[p]];
+        int use_tc, cls;
+        int kind = kind_of(s, &use_tc, &cls);
+        if (cls_bucket[cls] < 0) {
+            cls_bucket[cls] = (int)b->buckets.size();
+            b->buckets.emplace_back();
+            b->buckets.back().kind = kind;
+            b->buckets.back().use_tc = use_tc;
+        }
+        auto &bk = b->buckets[cls_bucket[cls]];
+        bk.order.push_back(p);
+        bk.Mmax = std::max(bk.Mmax, s->M);
+        bk.Lmax = std::max(bk.Lmax, s->L);
+    }
+    for (auto &bk : b->buckets)
+        std::stable_sort(bk.order.begin(), bk.order.end(), [&](int a, int c) {
+            knit_system sa = b->sys[sys_of[a]], sc = b->sys[sys_of[c]];
+            double ca = (double)sa->M * sa->M * sa->M * sa->L;
+            double cc = (double)sc->M * sc->M * sc->M * sc->L;
+            return ca > cc;
+        });
+    // device tables
+    std::vector<SysDev> tab(nSys);
+    for (int k = 0; k < nSys; ++k) tab[k] = b->sys[k]->dev();
+    cudaError_t e;
+    if ((e = b->d_systab.ensure(sizeof(SysDev) * nSys)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_systab.p, tab.data(), sizeof(SysDev) * nSys, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = b->d_sys_of.ensure(sizeof(int) * nInst)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_sys_of.p, sys_of.data(), sizeof(int) * nInst, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = b->d_perm.ensure(sizeof(int) * nInst)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_perm.p, b->perm.data(), sizeof(int) * nInst, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = b->d_sig_off.ensure(sizeof(long long) * nInst)) != cudaSuccess ||
+        (e = cudaMemcpy(b->d_sig_off.p, b->sig_off.data(), sizeof(long long) * nInst, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = b->Ep.ensure(sizeof(double) * nInst)) != cudaSuccess ||
+        (e = b->Sp.ensure(sizeof(uint64_t) * nInst)) != cudaSuccess ||
+        (e = b->Wp.ensure(sizeof(double) * nInst)) != cudaSuccess ||
+        (e = b->sigL.ensure(sizeof(double2) * b->sig_total)) != cudaSuccess ||
+        (e = b->sigR.ensure(sizeof(double2) * b->sig_total)) != cudaSuccess ||
+        (e = b->gbuf.ensure(sizeof(double2) * b->g_max)) != cudaSuccess ||
+        (e = b->lst.ensure(sizeof(int) * 2 * nInst)) != cudaSuccess ||
+        (e = b->queue.ensure(sizeof(int) * b->buckets.size())) != cudaSuccess) {
+        batch_release(b);
+        delete b;
+        return cuda_fail(e, "knit_batch_create");
+    }
+    size_t work = 0;
+    for (auto &bk : b->buckets) {
+        if ((e = bk.d_order.ensure(sizeof(int) * bk.order.size())) != cudaSuccess ||
+            (e = cudaMemcpy(bk.d_order.p, bk.order.data(), sizeof(int) * bk.order.size(),
+                            cudaMemcpyHostToDevice)) != cudaSuccess) {
+            batch_release(b);
+            delete b;
+            return cuda_fail(e, "knit_batch_create");
+        }
+        if (bk.kind == 0 && knit_fp64_smem_bytes(bk.Mmax, 1, 3) > 220 * 1024)
+            work = std::max(work, sizeof(double2) * 3 * (size_t)bk.Mmax * bk.Mmax * b->nsm);
+    }
+    if (work && (e = b->work.ensure(work)) != cudaSuccess) {
+        batch_release(b);
+        delete b;
+        return cuda_fail(e, "knit_batch_create");
+    }
+    // lead eigen-decompositions now, so that runs only enqueue kernels
+    for (int k = 0; k < nSys; ++k)
+        for (int p = 0; p < 2; ++p)
+            if (b->sys[k]->lead[p].scalar && (r = ensure_modes(b->sys[k], p)) != KNIT_OK) {
+                batch_release(b);
+                delete b;
+                return r;
+            }
+    *out = b;
+    return KNIT_OK;
+}
+
+knit_status knit_batch_destroy(knit_batch b)
+{
+    if (!b) return KNIT_OK;
+    cudaSetDevice(b->device);
+    batch_release(b);
+    delete b;
+    return KNIT_OK;
+}
+
+knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_t *seeds,
+                                    const double *W, const knit_lead_opts *opts, double *T,
+                                    int32_t *status, void *stream)
+{
+    if (!b || !E || !T) return fail(KNIT_ERR_INVALID, "knit_batch_transmission: bad arguments");
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = b->nInst;
+    knit_status r;
+    const double *dE, *dW;
+    const uint64_t *dS;
+    if ((r = stage_in(b->E, E, (size_t)n, st, &dE, "E")) != KNIT_OK ||
+        (r = stage_in(b->seeds, seeds, (size_t)n, st, &dS, "seeds")) != KNIT_OK ||
+        (r = stage_in(b->W, W, (size_t)n, st, &dW, "W")) != KNIT_OK)
+        return r;
+    double *Ep = b->Ep.as<double>(), *Wp = b->Wp.as<double>();
+    uint64_t *Sp = b->Sp.as<uint64_t>();
+    gather_instances<<<(n + 255) / 256, 256, 0, st>>>(dE, dS, dW, b->d_perm.as<int>(), n, Ep, Sp, Wp);
+    CK(cudaGetLastError(), "gather");
+    // lead self-energies per system, for its instances' energies
+    int *lst = b->lst.as<int>();
+    for (size_t k = 0; k < b->sys.size(); ++k) {
+        if (!b->count[k]) continue;
+        knit_system s = b->sys[k];
+        const int p0 = b->start[k];
+        const long long off = b->sig_off[p0];
+        if ((r = compute_sigma(s, 0, Ep + p0, b->count[k], opts, b->sigL.as<double2>() + off,
+                               b->gbuf.as<double2>(), lst + p0, nullptr, st)) != KNIT_OK ||
+            (r = compute_sigma(s, 1, Ep + p0, b->count[k], opts, b->sigR.as<double2>() + off,
+                               b->gbuf.as<double2>(), lst + n + p0, nullptr, st)) != KNIT_OK)
+            return r;
+    }
+    combine_status<<<(n + 255) / 256, 256, 0, st>>>(lst, lst + n, n);
+    bool hT, hSt = false;
+    double *dT;
+    int *dSt;
+    if ((r = stage_out(b->T, T, (size_t)n, &dT, &hT, "T")) != KNIT_OK ||
+        (r = stage_out(b->status, (int *)status, (size_t)n, &dSt, &hSt, "status")) != KNIT_OK)
+        return r;
+    if (dSt) fill_int<<<(n + 255) / 256, 256, 0, st>>>(dSt, n, ST_TIMEOUT);
+    CK(cudaMemsetAsync(b->queue.p, 0, sizeof(int) * b->buckets.size(), st), "queue reset");
+    for (size_t q = 0; q < b->buckets.size(); ++q) {
+        auto &bk = b->buckets[q];
+        InstDev in{};
+        in.n = (int)bk.order.size();
+        in.nS = 1;
+        in.per_instance = 1;
+        in.sys = b->d_systab.as<SysDev>();
+        in.sys_of = b->d_sys_of.as<int>();
+        in.order = bk.d_order.as<int>();
+        in.E = Ep;
+        in.seeds = Sp;
+        in.Wi = Wp;
+        in.sigL = b->sigL.as<double2>();
+        in.sigR = b->sigR.as<double2>();
+        in.sig_off = b->d_sig_off.as<long long>();
+        in.T = dT;
+        in.status = dSt;
+        in.out_index = b->d_perm.as<int>();
+        in.lstatus = lst;
+        in.queue = b->queue.as<int>() + q;
+        const int grid = std::max(1, std::min(in.n, b->nsm));
+        if (bk.kind == 1) {
+            CK(knit_launch_mixed_impl(&in, bk.Mmax, grid, bk.use_tc, st), "mixed sweep launch");
+        } else {
+            const int use_smem = knit_fp64_smem_bytes(bk.Mmax, 1, 3) <= 220 * 1024;
+            CK(knit_launch_sweep_fp64(&in, bk.Mmax, grid, b->work.as<double2>(), use_smem, st),
+               "fp64 sweep launch");
+        }
+    }
+    if (hT) CK(cudaMemcpyAsync(T, dT, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
+    if (hSt) CK(cudaMemcpyAsync(status, dSt, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
+    return finish(st, hT || hSt, "knit_batch_transmission");
 }
 
 }  // extern "C"

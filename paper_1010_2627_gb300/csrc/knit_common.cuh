@@ -195,15 +195,64 @@ struct SysDev {
 };
 
 struct InstDev {
-    int n;                     // number of instances = nE * nS
-    int nS;                    // seeds per energy; instance i = (energy i / nS, seed i % nS)
-    const double *E;           // nE
-    const uint64_t *seeds;     // nS or nullptr (seed 0)
-    double W;                  // disorder strength
-    const double2 *sigL;       // nE*M*M
-    const double2 *sigR;       // nE*M*M
-    double *T;                 // n
-    int *status;               // n or nullptr
-    const int *lstatus;        // nE lead-solver status or nullptr; non-zero skips the instance
-    int *queue;                // one int, zeroed before launch: next instance to take
+    int n;                     // instances in this launch
+    int nS;                    // energy x seed grid: seeds per energy
+    int per_instance;          // 1: E, seed, W and self-energies given per instance
+    const SysDev *sys;         // system table (device memory)
+    const int *sys_of;         // system of each instance, or nullptr (system 0)
+    const int *order;          // queue position -> instance (cost order), or nullptr
+    const double *E;           // grid: nE values; per instance: one per instance
+    const uint64_t *seeds;     // grid: nS values; per instance: one per instance; nullptr = 0
+    double W;                  // disorder strength (grid mode, or when Wi is nullptr)
+    const double *Wi;          // per-instance disorder strength or nullptr
+    const double2 *sigL;       // grid: nE*M*M; per instance: concatenated blocks
+    const double2 *sigR;
+    const long long *sig_off;  // per instance: element offset of its blocks
+    double *T;                 // results, at out_index[inst] (or inst)
+    int *status;               // or nullptr
+    const int *out_index;      // output position of each instance, or nullptr
+    const int *lstatus;        // lead-solver status (grid: per energy; else per instance)
+    int *queue;                // one int, zeroed before launch: next queue position
 };
+
+// parameters of one instance
+struct InstParams {
+    int out;                   // output position
+    double E;
+    uint64_t ms;               // mixed seed of the disorder counter
+    double W;
+    const double2 *SL, *SR;
+    int st;                    // initial status (lead failures)
+};
+
+KNIT_DEV int take_position(const InstDev &in, int q) { return in.order ? in.order[q] : q; }
+
+KNIT_DEV const SysDev &inst_system(const InstDev &in, int inst)
+{
+    return in.sys[in.sys_of ? in.sys_of[inst] : 0];
+}
+
+KNIT_DEV InstParams inst_params(const InstDev &in, int inst, int M)
+{
+    InstParams p;
+    const size_t MM = (size_t)M * M;
+    if (in.per_instance) {
+        p.E = in.E[inst];
+        p.ms = knit_mix64(in.seeds ? in.seeds[inst] : 0ull);
+        p.W = in.Wi ? in.Wi[inst] : in.W;
+        const size_t off = in.sig_off ? (size_t)in.sig_off[inst] : (size_t)inst * MM;
+        p.SL = in.sigL + off;
+        p.SR = in.sigR + off;
+        p.st = in.lstatus ? in.lstatus[inst] : ST_OK;
+    } else {
+        const int ie = inst / in.nS;
+        p.E = in.E[ie];
+        p.ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
+        p.W = in.W;
+        p.SL = in.sigL + (size_t)ie * MM;
+        p.SR = in.sigR + (size_t)ie * MM;
+        p.st = in.lstatus ? in.lstatus[ie] : ST_OK;
+    }
+    p.out = in.out_index ? in.out_index[inst] : inst;
+    return p;
+}

@@ -1,8 +1,9 @@
 // sweep_fp64.cu -- the slice sweep in complex128 (the plain FP64 path).
 //
-// One CTA walks one instance (energy, disorder seed) at a time and takes the
-// next instance from an atomic counter.  Per slice n (KNIT user guide
-// Sec. 5.3 D, knitting in slice form; Eq. 2 by block elimination):
+// One CTA walks one instance (energy, disorder seed, system) at a time and
+// takes the next one from an atomic counter over a cost-ordered queue.  Per
+// slice n (KNIT user guide Sec. 5.3 D, knitting in slice form; Eq. 2 by block
+// elimination):
 //     A_0 = E - H_0 - Sigma_L,   A_n = E - H_n - V_n g_{n-1} V_n^dagger (n >= 1),
 //     A_{L-1} additionally - Sigma_R,
 //     g_n = A_n^{-1}                                   (Gauss-Jordan, FP64)
@@ -15,8 +16,9 @@
 // with the forward g_n kept every `save` slices (KNIT's saving_level) and
 // the slices in between recomputed segment by segment.
 //
-// Matrices live in shared memory when three (four for LDOS) M x M complex128
-// buffers fit, else in a per-CTA global workspace.
+// Matrices live in shared memory when three (four for LDOS) Mmax x Mmax
+// complex128 buffers fit, else in a per-CTA global workspace; Mmax is the
+// largest width among the launch's systems.
 
 #include "dense_fp64.cuh"
 
@@ -28,11 +30,10 @@ struct Bufs {
     double *red;
 };
 
-__device__ Bufs carve(const SysDev &s, double2 *work, int use_smem, int nbuf)
+__device__ Bufs carve(int Mmax, double2 *work, int use_smem, int nbuf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = s.M;
-    const size_t MM = (size_t)M * M;
+    const size_t MM = (size_t)Mmax * Mmax;
     Bufs b;
     unsigned char *p = smem_raw;
     double2 *mat;
@@ -47,15 +48,15 @@ __device__ Bufs carve(const SysDev &s, double2 *work, int use_smem, int nbuf)
     b.F = mat + 2 * MM;
     b.X = nbuf > 3 ? mat + 3 * MM : nullptr;
     b.gj.row = reinterpret_cast<double2 *>(p);
-    p += sizeof(double2) * M;
+    p += sizeof(double2) * Mmax;
     b.gj.col = reinterpret_cast<double2 *>(p);
-    p += sizeof(double2) * M;
+    p += sizeof(double2) * Mmax;
     b.gj.pval = reinterpret_cast<double2 *>(p);
     p += sizeof(double2);
     b.red = reinterpret_cast<double *>(p);
     p += sizeof(double) * 32;
     b.gj.perm = reinterpret_cast<int *>(p);
-    p += sizeof(int) * M;
+    p += sizeof(int) * Mmax;
     b.gj.flag = reinterpret_cast<int *>(p);
     p += sizeof(int);
     b.gj.piv = reinterpret_cast<int *>(p);
@@ -111,118 +112,105 @@ __device__ void g1_update(double2 *A, const double2 *V, int vb, const double2 *B
     }
 }
 
-__device__ int take_instance(int *queue, int *sh)
+// next instance from the queue (all threads), or -1 when the queue is empty
+__device__ int take_instance(const InstDev &in, int *sh)
 {
-    if (threadIdx.x == 0) *sh = atomicAdd(queue, 1);
+    if (threadIdx.x == 0) {
+        int q = atomicAdd(in.queue, 1);
+        *sh = q < in.n ? take_position(in, q) : -1;
+    }
     __syncthreads();
     int v = *sh;
     __syncthreads();
     return v;
 }
 
+// forward sweep: on return P = g_{L-1}, Q = G_{0,L-1}, F free
+__device__ int forward(const SysDev &s, const InstParams &ip, Bufs &b, double2 *&P, double2 *&Q,
+                       double2 *&F, double2 *ckpt, int save)
+{
+    const int M = s.M, L = s.L;
+    const size_t MM = (size_t)M * M;
+    int st = ip.st;
+    for (int n = 0; n < L && st == ST_OK; ++n) {
+        form_A(s, n, ip.E, ip.ms, ip.W, P, ip.SL, ip.SR, F);
+        st = gj_invert64(F, M, b.gj);
+        if (st != ST_OK) break;
+        if (ckpt && n % save == 0) copy_mat(F, ckpt + (size_t)(n / save) * MM, M);
+        if (n == 0) {
+            copy_mat(F, Q, M);
+        } else {
+            const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
+            g1_update(Q, Vn, s.vb, F, P, M);   // G_{0,n} = G_{0,n-1} V_n^dagger g_n
+            double2 *t = Q;
+            Q = P;
+            P = t;
+        }
+        double2 *t = P;   // g_n becomes the previous slice's function
+        P = F;
+        F = t;
+    }
+    return st;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 extern "C" __global__ void __launch_bounds__(256)
-knit_sweep_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem)
+knit_sweep_fp64_kernel(InstDev in, int Mmax, double2 *work, int use_smem)
 {
     __shared__ int sh_inst;
-    Bufs b = carve(s, work, use_smem, 3);
-    const int M = s.M, L = s.L;
-    const size_t MM = (size_t)M * M;
+    Bufs b = carve(Mmax, work, use_smem, 3);
     for (;;) {
-        const int inst = take_instance(in.queue, &sh_inst);
-        if (inst >= in.n) break;
-        const int ie = inst / in.nS;
-        const double E = in.E[ie];
-        const uint64_t ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
-        const double W = in.W;
-        const double2 *SL = in.sigL + (size_t)ie * MM;
-        const double2 *SR = in.sigR + (size_t)ie * MM;
+        const int inst = take_instance(in, &sh_inst);
+        if (inst < 0) break;
+        const SysDev s = inst_system(in, inst);
+        const InstParams ip = inst_params(in, inst, s.M);
         double2 *P = b.P, *Q = b.Q, *F = b.F;   // P = g_{n-1}, Q = G_{0,n-1}, F free
-        int st = in.lstatus ? in.lstatus[ie] : ST_OK;
-        for (int n = 0; n < L && st == ST_OK; ++n) {
-            form_A(s, n, E, ms, W, P, SL, SR, F);
-            st = gj_invert64(F, M, b.gj);
-            if (st != ST_OK) break;
-            if (n == 0) {
-                copy_mat(F, Q, M);
-            } else {
-                const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
-                g1_update(Q, Vn, s.vb, F, P, M);      // G_{0,n} = G_{0,n-1} V_n^dagger g_n
-                double2 *t = Q;
-                Q = P;
-                P = t;
-            }
-            double2 *t = P;   // g_n becomes the previous slice's function
-            P = F;
-            F = t;
-        }
+        int st = forward(s, ip, b, P, Q, F, nullptr, 1);
         double T = 0.0;
         if (st == ST_OK) {
-            gemm64_gamma(Q, SR, F, M);     // G Gamma_R
-            gemm64_nc(F, Q, P, M);         // G Gamma_R G^dagger
-            T = trace_gamma64(SL, P, M, b.red);
+            gemm64_gamma(Q, ip.SR, F, s.M);     // G Gamma_R
+            gemm64_nc(F, Q, P, s.M);            // G Gamma_R G^dagger
+            T = trace_gamma64(ip.SL, P, s.M, b.red);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (threadIdx.x == 0) {
-            in.T[inst] = T;
-            if (in.status) in.status[inst] = st;
+            in.T[ip.out] = T;
+            if (in.status) in.status[ip.out] = st;
         }
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// Forward sweep with checkpoints + sewing.  ckpt: per CTA ((L + save - 1)/save)
-// saved g's followed by `save` segment slots, M*M complex each.
+// Forward sweep with checkpoints + sewing.  ckpt: per CTA ((Lmax + save - 1)/save)
+// saved g's followed by `save` segment slots, Mmax*Mmax complex each.  ldos
+// receives L*M values per instance at out * ldos_stride.
 extern "C" __global__ void __launch_bounds__(256)
-knit_ldos_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem, double2 *ckpt, int save,
-                      double *ldos)
+knit_ldos_fp64_kernel(InstDev in, int Mmax, int Lmax, double2 *work, int use_smem, double2 *ckpt,
+                      int save, double *ldos, long long ldos_stride)
 {
     __shared__ int sh_inst;
-    Bufs b = carve(s, work, use_smem, 4);
-    const int M = s.M, L = s.L;
-    const size_t MM = (size_t)M * M;
-    const int nck = (L + save - 1) / save;
-    double2 *cks = ckpt + (size_t)blockIdx.x * (nck + save) * MM;   // checkpoints
-    double2 *seg = cks + (size_t)nck * MM;                          // segment slots
+    Bufs b = carve(Mmax, work, use_smem, 4);
+    const int nckmax = (Lmax + save - 1) / save;
     for (;;) {
-        const int inst = take_instance(in.queue, &sh_inst);
-        if (inst >= in.n) break;
-        const int ie = inst / in.nS;
-        const double E = in.E[ie];
-        const uint64_t ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
-        const double W = in.W;
-        const double2 *SL = in.sigL + (size_t)ie * MM;
-        const double2 *SR = in.sigR + (size_t)ie * MM;
-        double *out = ldos + (size_t)inst * L * M;
+        const int inst = take_instance(in, &sh_inst);
+        if (inst < 0) break;
+        const SysDev s = inst_system(in, inst);
+        const InstParams ip = inst_params(in, inst, s.M);
+        const int M = s.M, L = s.L;
+        const size_t MM = (size_t)M * M;
+        double2 *cks = ckpt + (size_t)blockIdx.x * (nckmax + save) * Mmax * Mmax;
+        double2 *seg = cks + (size_t)((L + save - 1) / save) * MM;
+        double *out = ldos + (size_t)ip.out * ldos_stride;
         double2 *P = b.P, *Q = b.Q, *F = b.F;
-        int st = in.lstatus ? in.lstatus[ie] : ST_OK;
-        // forward, keeping g_n for n % save == 0
-        for (int n = 0; n < L && st == ST_OK; ++n) {
-            form_A(s, n, E, ms, W, P, SL, SR, F);
-            st = gj_invert64(F, M, b.gj);
-            if (st != ST_OK) break;
-            if (n % save == 0) copy_mat(F, cks + (size_t)(n / save) * MM, M);
-            if (n == 0) {
-                copy_mat(F, Q, M);
-            } else {
-                const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
-                g1_update(Q, Vn, s.vb, F, P, M);
-                double2 *t = Q;
-                Q = P;
-                P = t;
-            }
-            double2 *t = P;
-            P = F;
-            F = t;
-        }
+        int st = forward(s, ip, b, P, Q, F, cks, save);
         double T = 0.0;
         if (st == ST_OK) {
-            gemm64_gamma(Q, SR, F, M);
+            gemm64_gamma(Q, ip.SR, F, M);
             gemm64_nc(F, Q, b.X, M);
-            T = trace_gamma64(SL, b.X, M, b.red);
+            T = trace_gamma64(ip.SL, b.X, M, b.red);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         // sewing: G_nn in Q, walking n = L-1 .. 0
@@ -238,11 +226,11 @@ knit_ldos_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem, double2
                 } else {
                     const int c = (n / save) * save;
                     if (seg_lo != c) {
-                        // recompute g_{c+1} .. g_{min(c+save, L)-1} from checkpoint g_c
+                        // recompute g_{c+1} .. g_n from checkpoint g_c
                         copy_mat(cks + (size_t)(c / save) * MM, P, M);
                         const int hi = min(c + save, L);
                         for (int m = c + 1; m < hi && m <= n; ++m) {
-                            form_A(s, m, E, ms, W, P, SL, SR, F);
+                            form_A(s, m, ip.E, ip.ms, ip.W, P, ip.SL, ip.SR, F);
                             st = gj_invert64(F, M, b.gj);
                             if (st != ST_OK) break;
                             copy_mat(F, seg + (size_t)(m - c) * MM, M);
@@ -272,8 +260,8 @@ knit_ldos_fp64_kernel(SysDev s, InstDev in, double2 *work, int use_smem, double2
             }
         }
         if (threadIdx.x == 0) {
-            if (in.T) in.T[inst] = T;
-            if (in.status) in.status[inst] = st;
+            if (in.T) in.T[ip.out] = T;
+            if (in.status) in.status[ip.out] = st;
         }
         __syncthreads();
     }
@@ -289,25 +277,27 @@ extern "C" size_t knit_fp64_smem_bytes(int M, int use_smem, int nbuf)
 }
 
 // host launch helpers used by the C-ABI implementation
-extern "C" cudaError_t knit_launch_sweep_fp64(const SysDev *s, const InstDev *in, int grid,
-                                              double2 *work, int use_smem, cudaStream_t stream)
+extern "C" cudaError_t knit_launch_sweep_fp64(const InstDev *in, int Mmax, int grid, double2 *work,
+                                              int use_smem, cudaStream_t stream)
 {
-    size_t sm = knit_fp64_smem_bytes(s->M, use_smem, 3);
+    size_t sm = knit_fp64_smem_bytes(Mmax, use_smem, 3);
     cudaError_t e = cudaFuncSetAttribute(knit_sweep_fp64_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    knit_sweep_fp64_kernel<<<grid, 256, sm, stream>>>(*s, *in, work, use_smem);
+    knit_sweep_fp64_kernel<<<grid, 256, sm, stream>>>(*in, Mmax, work, use_smem);
     return cudaGetLastError();
 }
 
-extern "C" cudaError_t knit_launch_ldos_fp64(const SysDev *s, const InstDev *in, int grid,
+extern "C" cudaError_t knit_launch_ldos_fp64(const InstDev *in, int Mmax, int Lmax, int grid,
                                              double2 *work, int use_smem, double2 *ckpt, int save,
-                                             double *ldos, cudaStream_t stream)
+                                             double *ldos, long long ldos_stride,
+                                             cudaStream_t stream)
 {
-    size_t sm = knit_fp64_smem_bytes(s->M, use_smem, 4);
+    size_t sm = knit_fp64_smem_bytes(Mmax, use_smem, 4);
     cudaError_t e = cudaFuncSetAttribute(knit_ldos_fp64_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    knit_ldos_fp64_kernel<<<grid, 256, sm, stream>>>(*s, *in, work, use_smem, ckpt, save, ldos);
+    knit_ldos_fp64_kernel<<<grid, 256, sm, stream>>>(*in, Mmax, Lmax, work, use_smem, ckpt, save,
+                                                     ldos, ldos_stride);
     return cudaGetLastError();
 }

@@ -45,52 +45,62 @@ struct MixedSmem {
     float2 vl[2][MP];      // lo
     double red[NT / 32];
     int inst;
+    int cur_sys;
 };
 
 }  // namespace
 
 template <int MP>
 __global__ void __launch_bounds__(NT, 1)
-knit_sweep_mixed_kernel(SysDev s, InstDev in)
+knit_sweep_mixed_kernel(InstDev in)
 {
     constexpr int RT = MP / 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MixedSmem<MP> &sm = *reinterpret_cast<MixedSmem<MP> *>(smem_raw);
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    const int M = s.M, L = s.L;
-    const size_t MM = (size_t)M * M;
-
-    // per-launch constants: H0 as complex64, diagonal of V as double-float
-    for (int e = tid; e < MP * MP; e += NT) {
-        int i = e / MP, j = e - i * MP;
-        double2 h = (i < M && j < M) ? s.H0[(size_t)i * M + j] : make_double2(0.0, 0.0);
-        sm.H0f[e] = make_float2((float)h.x, (float)h.y);
-    }
-    for (int q = 0; q < 2; ++q)
-        for (int i = tid; i < MP; i += NT) {
-            double2 v = make_double2(0.0, 0.0);
-            if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
-            float hx, lx, hy, ly;
-            to_df(v.x, hx, lx);
-            to_df(v.y, hy, ly);
-            sm.vh[q][i] = make_float2(hx, hy);
-            sm.vl[q][i] = make_float2(lx, ly);
-        }
-    __syncthreads();
+    if (tid == 0) sm.cur_sys = -1;
 
     for (;;) {
-        if (tid == 0) sm.inst = atomicAdd(in.queue, 1);
+        if (tid == 0) {
+            const int q = atomicAdd(in.queue, 1);
+            sm.inst = q < in.n ? take_position(in, q) : -1;
+        }
         __syncthreads();
         const int inst = sm.inst;
+        const int si = inst >= 0 && in.sys_of ? in.sys_of[inst] : 0;
+        const bool reload = inst >= 0 && si != sm.cur_sys;
         __syncthreads();
-        if (inst >= in.n) break;
-        const int ie = inst / in.nS;
-        const double E = in.E[ie];
-        const uint64_t ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
-        const double W = in.W;
-        const double2 *SL = in.sigL + (size_t)ie * MM;
-        const double2 *SR = in.sigR + (size_t)ie * MM;
-        int st = in.lstatus ? in.lstatus[ie] : ST_OK;
+        if (inst < 0) break;
+        const SysDev s = in.sys[si];
+        const int M = s.M, L = s.L;
+        const size_t MM = (size_t)M * M;
+        if (reload) {
+            // per-system constants: H0 as complex64, diagonal of V as double-float
+            for (int e = tid; e < MP * MP; e += NT) {
+                int i = e / MP, j = e - i * MP;
+                double2 h = (i < M && j < M) ? s.H0[(size_t)i * M + j] : make_double2(0.0, 0.0);
+                sm.H0f[e] = make_float2((float)h.x, (float)h.y);
+            }
+            for (int q = 0; q < 2; ++q)
+                for (int i = tid; i < MP; i += NT) {
+                    double2 v = make_double2(0.0, 0.0);
+                    if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
+                    float hx, lx, hy, ly;
+                    to_df(v.x, hx, lx);
+                    to_df(v.y, hy, ly);
+                    sm.vh[q][i] = make_float2(hx, hy);
+                    sm.vl[q][i] = make_float2(lx, ly);
+                }
+            if (tid == 0) sm.cur_sys = si;
+            __syncthreads();
+        }
+        const InstParams ip = inst_params(in, inst, M);
+        const double E = ip.E;
+        const uint64_t ms = ip.ms;
+        const double W = ip.W;
+        const double2 *SL = ip.SL;
+        const double2 *SR = ip.SR;
+        int st = ip.st;
 
         for (int n = 0; n < L && st == ST_OK; ++n) {
             slice_diag<MP>(sm.eps, s, ms, W, E, n);
@@ -207,42 +217,42 @@ knit_sweep_mixed_kernel(SysDev s, InstDev in)
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {
-            in.T[inst] = T;
-            if (in.status) in.status[inst] = st;
+            in.T[ip.out] = T;
+            if (in.status) in.status[ip.out] = st;
         }
         __syncthreads();
     }
 }
 
-template __global__ void knit_sweep_mixed_kernel<16>(SysDev, InstDev);
-template __global__ void knit_sweep_mixed_kernel<32>(SysDev, InstDev);
-template __global__ void knit_sweep_mixed_kernel<64>(SysDev, InstDev);
+template __global__ void knit_sweep_mixed_kernel<16>(InstDev);
+template __global__ void knit_sweep_mixed_kernel<32>(InstDev);
+template __global__ void knit_sweep_mixed_kernel<64>(InstDev);
 
-extern "C" cudaError_t knit_launch_mixed_tc(const SysDev *s, const InstDev *in, int grid,
-                                            cudaStream_t stream);
+extern "C" cudaError_t knit_launch_mixed_tc(const InstDev *in, int grid, cudaStream_t stream);
 
-// Host-side launch helper (the host API lives in knit_api.cu).  Widths
-// 33..64 take the tensor-core residual when use_tc is set.
-extern "C" cudaError_t knit_launch_mixed_impl(const SysDev *s, const InstDev *in, int grid,
-                                              int use_tc, cudaStream_t stream)
+// Host-side launch helper (the host API lives in knit_api.cu).  Mmax is the
+// largest width among the launch's systems; widths 33..64 take the
+// tensor-core residual when use_tc is set.
+extern "C" cudaError_t knit_launch_mixed_impl(const InstDev *in, int Mmax, int grid, int use_tc,
+                                              cudaStream_t stream)
 {
-    const int M = s->M;
+    const int M = Mmax;
     if (M <= 16) {
         size_t sm = sizeof(MixedSmem<16>);
         cudaFuncSetAttribute(knit_sweep_mixed_kernel<16>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        knit_sweep_mixed_kernel<16><<<grid, NT, sm, stream>>>(*s, *in);
+        knit_sweep_mixed_kernel<16><<<grid, NT, sm, stream>>>(*in);
     } else if (M <= 32) {
         size_t sm = sizeof(MixedSmem<32>);
         cudaFuncSetAttribute(knit_sweep_mixed_kernel<32>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        knit_sweep_mixed_kernel<32><<<grid, NT, sm, stream>>>(*s, *in);
+        knit_sweep_mixed_kernel<32><<<grid, NT, sm, stream>>>(*in);
     } else if (M <= 64) {
-        if (use_tc) return knit_launch_mixed_tc(s, in, grid, stream);
+        if (use_tc) return knit_launch_mixed_tc(in, grid, stream);
         size_t sm = sizeof(MixedSmem<64>);
         cudaFuncSetAttribute(knit_sweep_mixed_kernel<64>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        knit_sweep_mixed_kernel<64><<<grid, NT, sm, stream>>>(*s, *in);
+        knit_sweep_mixed_kernel<64><<<grid, NT, sm, stream>>>(*in);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -82,6 +82,8 @@ struct TcSmem {
     unsigned long long mbar;
     uint32_t tmem;
     int inst;
+    int cur_sys;
+    int h0_cached;
 };
 
 KNIT_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -167,7 +169,7 @@ __global__ void fill_status(int *st, int n, int v)
 }  // namespace
 
 __global__ void __launch_bounds__(NT, 1)
-knit_sweep_mixed_tc_kernel(SysDev s, InstDev in)
+knit_sweep_mixed_tc_kernel(InstDev in)
 {
     constexpr int RT = MPT / 16;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -176,42 +178,17 @@ knit_sweep_mixed_tc_kernel(SysDev s, InstDev in)
     float2 *const Gl = sm.w.s.Gl;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int warp = tid >> 5, lane = tid & 31;
-    const int M = s.M, L = s.L;
-    const size_t MM = (size_t)M * M;
     // D f32, A and B bf16, both K-major, N = 64, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
                            ((128u >> 4) << 24);
 
-    // per-launch constants: diagonal of V as double-float, sparse H0 rows
-    for (int q = 0; q < 2; ++q)
-        for (int i = tid; i < MPT; i += NT) {
-            double2 v = make_double2(0.0, 0.0);
-            if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
-            float hx, lx, hy, ly;
-            to_df(v.x, hx, lx);
-            to_df(v.y, hy, ly);
-            sm.vh[q][i] = make_float2(hx, hy);
-            sm.vl[q][i] = make_float2(lx, ly);
-        }
-    const int nnz = s.h0_rowptr[M];
-    const bool h0_cached = nnz <= MAX_NNZ;
-    for (int i = tid; i <= MPT; i += NT) sm.h0rp[i] = s.h0_rowptr[min(i, M)];
-    if (h0_cached)
-        for (int c = tid; c < nnz; c += NT) {
-            const double2 h = s.h0_val[c];
-            float a, b, cc, d;
-            to_df(h.x, a, b);
-            to_df(h.y, cc, d);
-            sm.h0c[c] = s.h0_col[c];
-            sm.h0h[c] = make_float2(a, cc);
-            sm.h0l[c] = make_float2(b, d);
-        }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(&sm.tmem)), "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
+        sm.cur_sys = -1;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.mbar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -223,18 +200,57 @@ knit_sweep_mixed_tc_kernel(SysDev s, InstDev in)
     bool timed_out = false;
 
     for (;;) {
-        if (tid == 0) sm.inst = atomicAdd(in.queue, 1);
+        if (tid == 0) {
+            const int q = atomicAdd(in.queue, 1);
+            sm.inst = q < in.n ? take_position(in, q) : -1;
+        }
         __syncthreads();
         const int inst = sm.inst;
+        const int si = inst >= 0 && in.sys_of ? in.sys_of[inst] : 0;
+        const bool reload = inst >= 0 && si != sm.cur_sys;
         __syncthreads();
-        if (inst >= in.n) break;
-        const int ie = inst / in.nS;
-        const double E = in.E[ie];
-        const uint64_t ms = knit_mix64(in.seeds ? in.seeds[inst - ie * in.nS] : 0ull);
-        const double W = in.W;
-        const double2 *SL = in.sigL + (size_t)ie * MM;
-        const double2 *SR = in.sigR + (size_t)ie * MM;
-        int st = in.lstatus ? in.lstatus[ie] : ST_OK;
+        if (inst < 0) break;
+        const SysDev s = in.sys[si];
+        const int M = s.M, L = s.L;
+        const size_t MM = (size_t)M * M;
+        if (reload) {
+            // per-system constants: diagonal of V as double-float, sparse H0 rows
+            for (int q = 0; q < 2; ++q)
+                for (int i = tid; i < MPT; i += NT) {
+                    double2 v = make_double2(0.0, 0.0);
+                    if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
+                    float hx, lx, hy, ly;
+                    to_df(v.x, hx, lx);
+                    to_df(v.y, hy, ly);
+                    sm.vh[q][i] = make_float2(hx, hy);
+                    sm.vl[q][i] = make_float2(lx, ly);
+                }
+            const int nnz = s.h0_rowptr[M];
+            for (int i = tid; i <= MPT; i += NT) sm.h0rp[i] = s.h0_rowptr[min(i, M)];
+            if (nnz <= MAX_NNZ)
+                for (int c = tid; c < nnz; c += NT) {
+                    const double2 h = s.h0_val[c];
+                    float a, b, cc, d;
+                    to_df(h.x, a, b);
+                    to_df(h.y, cc, d);
+                    sm.h0c[c] = s.h0_col[c];
+                    sm.h0h[c] = make_float2(a, cc);
+                    sm.h0l[c] = make_float2(b, d);
+                }
+            if (tid == 0) {
+                sm.cur_sys = si;
+                sm.h0_cached = nnz <= MAX_NNZ;
+            }
+            __syncthreads();
+        }
+        const bool h0_cached = sm.h0_cached;
+        const InstParams ip = inst_params(in, inst, M);
+        const double E = ip.E;
+        const uint64_t ms = ip.ms;
+        const double W = ip.W;
+        const double2 *SL = ip.SL;
+        const double2 *SR = ip.SR;
+        int st = ip.st;
 
         for (int n = 0; n < L && st == ST_OK; ++n) {
             slice_diag<MPT>(sm.eps, s, ms, W, E, n);
@@ -515,8 +531,8 @@ knit_sweep_mixed_tc_kernel(SysDev s, InstDev in)
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {
-            in.T[inst] = T;
-            if (in.status) in.status[inst] = st;
+            in.T[ip.out] = T;
+            if (in.status) in.status[ip.out] = st;
         }
         __syncthreads();
         if (timed_out) break;
@@ -529,17 +545,17 @@ knit_sweep_mixed_tc_kernel(SysDev s, InstDev in)
 
 // Host launch helper.  Instances that a timed-out CTA never reaches keep the
 // ST_TIMEOUT status written here first.
-extern "C" cudaError_t knit_launch_mixed_tc(const SysDev *s, const InstDev *in, int grid,
-                                            cudaStream_t stream)
+extern "C" cudaError_t knit_launch_mixed_tc(const InstDev *in, int grid, cudaStream_t stream)
 {
-    if (s->M > MPT || s->M <= 32) return cudaErrorInvalidValue;
     static_assert(sizeof(TcSmem) <= 227 * 1024, "shared memory budget");
-    if (in->status) fill_status<<<(in->n + 255) / 256, 256, 0, stream>>>(in->status, in->n, ST_TIMEOUT);
+    // outputs of instances a timed-out CTA never reaches keep ST_TIMEOUT
+    if (in->status && !in->out_index)
+        fill_status<<<(in->n + 255) / 256, 256, 0, stream>>>(in->status, in->n, ST_TIMEOUT);
     size_t smb = sizeof(TcSmem);
     cudaError_t e = cudaFuncSetAttribute(knit_sweep_mixed_tc_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
     if (e != cudaSuccess) return e;
-    knit_sweep_mixed_tc_kernel<<<grid, NT, smb, stream>>>(*s, *in);
+    knit_sweep_mixed_tc_kernel<<<grid, NT, smb, stream>>>(*in);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,9 @@ _SIGS = {
     "knit_transmission_sigma": (i32, [P, P, i32, P, i32, f64, P, P, i32, P, P, P]),
     "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
+    "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
+    "knit_batch_destroy": (i32, [P]),
+    "knit_batch_transmission": (i32, [P, P, P, P, P, P, P, P]),
     "knit_last_error": (ctypes.c_char_p, []),
     "knit_version": (ctypes.c_char_p, []),
 }
@@ -205,6 +208,56 @@ def knit_lead_decimation_noalloc(H0, V, M, lead, E, sigma, eta=0.0, tol=0.0, max
                                                int(nE), float(eta), float(tol), int(maxit),
                                                _ptr(sigma), _ptr(iters), _ptr(status),
                                                _stream(stream)))
+
+
+def knit_batch_create(handles, sys_index, precision):
+    """Plan a heterogeneous batch over system handles; returns the plan handle."""
+    arr = (P * len(handles))(*[P(h) for h in handles])
+    idx = np.ascontiguousarray(sys_index, dtype=np.int32)
+    out = P()
+    _check(load().knit_batch_create(arr, len(handles), _ptr(idx), len(idx), int(precision),
+                                    ctypes.byref(out)))
+    return out.value
+
+
+def knit_batch_destroy(plan):
+    _check(load().knit_batch_destroy(P(plan)))
+
+
+def knit_batch_transmission(plan, E, seeds, W, T, status=None, opts=None, stream=None):
+    _check(load().knit_batch_transmission(P(plan), _ptr(E), _ptr(seeds), _ptr(W),
+                                          None if opts is None else ctypes.byref(opts), _ptr(T),
+                                          _ptr(status), _stream(stream)))
+
+
+class Batch:
+    """A heterogeneous batch plan over ``System`` objects (kept alive here)."""
+
+    def __init__(self, systems, sys_index, precision=KNIT_MIXED):
+        self.systems = list(systems)
+        self.n = len(sys_index)
+        self.handle = knit_batch_create([s.handle for s in self.systems], sys_index, precision)
+
+    def close(self):
+        if self.handle:
+            knit_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def transmission(self, E, seeds=None, W=None, method=KNIT_LEAD_AUTO):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        Wv = None if W is None else np.ascontiguousarray(np.broadcast_to(W, (self.n,)),
+                                                          dtype=np.float64)
+        T = np.empty(self.n)
+        st = np.empty(self.n, np.int32)
+        knit_batch_transmission(self.handle, E, sd, Wv, T, st, _opts(method))
+        return T, st
 
 
 # ---------------------------------------------------------------------------

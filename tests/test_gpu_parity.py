@@ -229,11 +229,15 @@ def test_singular_pivot_reports_status(knit):
         assert st[0, 0] == knit.KNIT_ERR_SINGULAR
 
 
-def test_invalid_arguments(knit):
+def test_invalid_arguments_and_wide_mixed(knit):
     ss = inputs.square(80, 3)
     sysk = knit.System(ss)
+    # KNIT_MIXED above M = 64 runs the FP64 sweep
+    T1, _ = sysk.transmission([0.1, 1.3], precision=knit.KNIT_MIXED)
+    T0, _ = sysk.transmission([0.1, 1.3], precision=knit.KNIT_FP64)
+    assert np.array_equal(T0, T1)
     with pytest.raises(knit.KnitError) as ei:
-        sysk.transmission([0.1], precision=knit.KNIT_MIXED)
+        sysk.transmission([0.1], precision=7)
     assert ei.value.code == knit.KNIT_ERR_INVALID
     with pytest.raises(knit.KnitError):
         sysk.ldos([0.1], saving_level=0)
