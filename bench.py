@@ -372,7 +372,7 @@ def run_uneven(args):
         "metric": "T(E) points/s (uneven batch)", "value": n / (ms / 1e3),
         "unit": "T(E) points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "mixed for M <= 64, f64 above", "data": "synthetic",
+        "dtype": "c64 inversion + refinement (tensor-core residual for M in 33..64)", "data": "synthetic",
         "config": {"workload": "uneven square batch, 4096 instances, M in {32..128}, "
                                "L in {128..2048}, W ~ U[0,4]", "systems": len(keys),
                    "instances_mixed": int(mixed_mask.sum()),

@@ -74,9 +74,11 @@ enum {
                        residual exact to ~2^-48; the state g_n is carried as
                        hi + lo floats.  For 33 <= M <= 64 the residual's dense
                        product runs on the tensor cores (bf16 digit slices,
-                       f32 accumulation), otherwise on CUDA cores.  Systems
-                       with M > 64 or non-diagonal inter-slice couplings run
-                       the KNIT_FP64 sweep instead. */
+                       f32 accumulation), otherwise on CUDA cores.  Widths
+                       65..128 (and any width with 4 x 4 block couplings)
+                       use a 512-thread variant with the state in device
+                       memory; M > 128 or other coupling structures run the
+                       KNIT_FP64 sweep instead. */
     KNIT_MIXED_CUDACORE = 2  /* KNIT_MIXED with the residual always accumulated
                                 in double-float arithmetic on CUDA cores */
 };
@@ -171,7 +173,7 @@ knit_status knit_ldos(knit_system sys, const double *E, int32_t nE, const uint64
  * lead solvers and per sweep kernel for the sweep, and orders each kernel's
  * queue by decreasing cost M^3 L (longest processing time first), so each
  * kernel variant is one persistent launch.  KNIT_MIXED instances whose
- * system has M > 64 or non-diagonal couplings run in the FP64 sweep.  Lead
+ * system the mixed kernels do not cover run in the FP64 sweep.  Lead
  * eigen-decompositions are done here, so that a run with device pointers
  * only enqueues kernels and can be captured in a CUDA graph. */
 typedef struct knit_batch_s *knit_batch;

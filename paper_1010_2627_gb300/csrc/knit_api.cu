@@ -23,6 +23,8 @@ extern "C" cudaError_t knit_launch_ldos_fp64(const InstDev *, int, int, int, dou
 extern "C" size_t knit_fp64_smem_bytes(int, int, int);
 extern "C" cudaError_t knit_launch_mixed_impl(const InstDev *, int, int, int, cudaStream_t);
 extern "C" int knit_mixed_max_M(void);
+extern "C" size_t knit_mixed_wide_work_bytes(int);
+extern "C" cudaError_t knit_launch_mixed_wide(const InstDev *, int, int, void *, cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
 extern "C" cudaError_t knit_launch_modes_sigma(const double2 *, const double2 *, int, double,
                                                const double *, int, double2 *, double2 *, int,
@@ -334,6 +336,17 @@ __global__ void combine_status(int *a, const int *b, int n)
     if (i < n && a[i] == 0) a[i] = b[i];
 }
 
+// which sweep kernel serves a system at a given precision
+enum SweepKind { SWEEP_FP64 = 0, SWEEP_MIXED = 1, SWEEP_WIDE = 2 };
+
+int sweep_kind(const knit_system_s *s, int precision)
+{
+    if (precision == KNIT_FP64) return SWEEP_FP64;
+    if (s->vb == 1 && s->M <= knit_mixed_max_M()) return SWEEP_MIXED;
+    if ((s->vb == 1 || s->vb == 4) && s->M <= 128) return SWEEP_WIDE;
+    return SWEEP_FP64;
+}
+
 knit_status run_sweep(knit_system s, InstDev in, int precision, cudaStream_t st)
 {
     in.sys = s->d_sys;
@@ -341,9 +354,14 @@ knit_status run_sweep(knit_system s, InstDev in, int precision, cudaStream_t st)
     in.queue = s->queue.as<int>();
     CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
     const int grid = std::max(1, std::min(in.n, s->nsm));
-    const bool mixed_ok = s->M <= knit_mixed_max_M() && s->vb == 1;
-    if ((precision == KNIT_MIXED || precision == KNIT_MIXED_CUDACORE) && mixed_ok) {
+    const int kind = sweep_kind(s, precision);
+    if (kind == SWEEP_MIXED) {
         CK(knit_launch_mixed_impl(&in, s->M, grid, precision == KNIT_MIXED, st), "mixed sweep launch");
+        return KNIT_OK;
+    }
+    if (kind == SWEEP_WIDE) {
+        CK(s->work.ensure(knit_mixed_wide_work_bytes(s->M) * grid), "wide sweep workspace");
+        CK(knit_launch_mixed_wide(&in, s->M, grid, s->work.p, st), "wide mixed sweep launch");
         return KNIT_OK;
     }
     const size_t MM = (size_t)s->M * s->M;
@@ -402,7 +420,7 @@ __global__ void fill_int(int *a, int n, int v)
 
 struct knit_batch_s {
     struct Bucket {
-        int kind = 0;          // 0 FP64 sweep, 1 mixed (CUDA-core or tensor-core residual)
+        int kind = 0;          // 0 FP64 sweep, 1 mixed M <= 64, 2 mixed wide (M <= 128)
         int use_tc = 0;
         int Mmax = 0, Lmax = 0;
         std::vector<int> order;   // plan positions in cost order
@@ -780,13 +798,15 @@ knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const in
     b->sig_total = off;
     // buckets by kernel variant
     auto kind_of = [&](knit_system s, int *use_tc, int *cls) {
-        const bool mixed_ok = precision != KNIT_FP64 && s->vb == 1 && s->M <= knit_mixed_max_M();
-        if (!mixed_ok) { *use_tc = 0; *cls = 0; return 0; }
+        const int k = sweep_kind(s, precision);
+        *use_tc = 0;
+        if (k == SWEEP_FP64) { *cls = 0; return 0; }
+        if (k == SWEEP_WIDE) { *cls = 5; return 2; }
         *use_tc = precision == KNIT_MIXED && s->M > 32;
         *cls = s->M <= 16 ? 1 : s->M <= 32 ? 2 : (*use_tc ? 3 : 4);
         return 1;
     };
-    std::vector<int> cls_bucket(5, -1);
+    std::vector<int> cls_bucket(6, -1);
     for (int p = 0; p < nInst; ++p) {
         knit_system s = b->sys[sys_of[p]];
         int use_tc, cls;
@@ -844,6 +864,7 @@ knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const in
         }
         if (bk.kind == 0 && knit_fp64_smem_bytes(bk.Mmax, 1, 3) > 220 * 1024)
             work = std::max(work, sizeof(double2) * 3 * (size_t)bk.Mmax * bk.Mmax * b->nsm);
+        if (bk.kind == 2) work = std::max(work, knit_mixed_wide_work_bytes(bk.Mmax) * b->nsm);
     }
     if (work && (e = b->work.ensure(work)) != cudaSuccess) {
         batch_release(b);
@@ -935,6 +956,8 @@ knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_
         const int grid = std::max(1, std::min(in.n, b->nsm));
         if (bk.kind == 1) {
             CK(knit_launch_mixed_impl(&in, bk.Mmax, grid, bk.use_tc, st), "mixed sweep launch");
+        } else if (bk.kind == 2) {
+            CK(knit_launch_mixed_wide(&in, bk.Mmax, grid, b->work.p, st), "wide mixed sweep launch");
         } else {
             const int use_smem = knit_fp64_smem_bytes(bk.Mmax, 1, 3) <= 220 * 1024;
             CK(knit_launch_sweep_fp64(&in, bk.Mmax, grid, b->work.as<double2>(), use_smem, st),

@@ -64,10 +64,10 @@ struct GJShared {
 };
 
 // E - onsite of slice n for orbitals 0..MP-1 (0 in the padding)
-template <int MP>
+template <int MP, int NTH = NT>
 __device__ void slice_diag(double *eps, const SysDev &s, uint64_t ms, double W, double E, int n)
 {
-    for (int i = threadIdx.x; i < MP; i += NT) {
+    for (int i = threadIdx.x; i < MP; i += NTH) {
         double d = 0.0;
         if (i < s.M) {
             double o = 0.0;
@@ -81,12 +81,12 @@ __device__ void slice_diag(double *eps, const SysDev &s, uint64_t ms, double W, 
 
 // Gv = V_n g V_n^dagger (+ Sigma_L at n = 0, + Sigma_R at n = L - 1) in
 // double-float, in place over (Gh, Gl); vh/vl: diagonal of V per parity.
-template <int MP>
+template <int MP, int NTH = NT>
 __device__ void form_gv(float2 *Gh, float2 *Gl, const float2 (*vh)[MP], const float2 (*vl)[MP],
                         int M, int n, int L, const double2 *SL, const double2 *SR)
 {
     const int q = n & 1;
-    for (int e = threadIdx.x; e < MP * MP; e += NT) {
+    for (int e = threadIdx.x; e < MP * MP; e += NTH) {
         const int i = e / MP, j = e - i * MP;
         float2 gh = make_float2(0.f, 0.f), gl = make_float2(0.f, 0.f);
         if (i < M && j < M) {
@@ -125,27 +125,27 @@ __device__ void form_gv(float2 *Gh, float2 *Gl, const float2 (*vh)[MP], const fl
 // then takes the same update x -= c_i r_j (c_p = -1, r_k = 1/pivot).  On
 // return A^{-1}[k][P[k']] = x[P[k]][k'], P[k] = g.perm[k].  Returns ST_OK or
 // ST_SINGULAR (uniform over the block).
-template <int MP>
-__device__ __forceinline__ int gj_regs(float2 (&x)[MP / 16][MP / 16], int M, GJShared<MP> &g)
+template <int MP, int TY = 16, int TX = 16>
+__device__ __forceinline__ int gj_regs(float2 (&x)[MP / TY][MP / TX], int M, GJShared<MP> &g)
 {
-    constexpr int RT = MP / 16;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15, lane = tid & 31;
+    constexpr int RA = MP / TY, RB = MP / TX, NTH = TY * TX;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX, lane = tid & 31;
     int st = ST_OK;
-    for (int i = tid; i < MP; i += NT) g.used[i] = 0;
+    for (int i = tid; i < MP; i += NTH) g.used[i] = 0;
     __syncthreads();
     for (int k = 0; k < M; ++k) {
-        const int q = k & 1, kt = k & 15, kb = k >> 4;
+        const int q = k & 1, kt = k % TX, kb = k / TX;
         if (tx == kt) {
 #pragma unroll
-            for (int a = 0; a < RT; ++a) {
+            for (int a = 0; a < RA; ++a) {
                 float2 v = x[a][0];
 #pragma unroll
-                for (int b = 1; b < RT; ++b)
+                for (int b = 1; b < RB; ++b)
                     if (b == kb) v = x[a][b];
 #pragma unroll
-                for (int b = 0; b < RT; ++b)
+                for (int b = 0; b < RB; ++b)
                     if (b == kb) x[a][b] = make_float2(0.f, 0.f);
-                const int i = ty + 16 * a;
+                const int i = ty + TY * a;
                 g.col[q][i] = v;
                 g.val[q][i] = (i < M && !g.used[i]) ? cabs1f(v) : -1.f;
             }
@@ -162,14 +162,14 @@ __device__ __forceinline__ int gj_regs(float2 (&x)[MP / 16][MP / 16], int M, GJS
             st = ST_SINGULAR;
             break;
         }
-        if (ty == (p & 15)) {
-            const int pa = p >> 4;
+        if (ty == p % TY) {
+            const int pa = p / TY;
 #pragma unroll
-            for (int a = 0; a < RT; ++a) {
+            for (int a = 0; a < RA; ++a) {
                 if (a != pa) continue;
 #pragma unroll
-                for (int b = 0; b < RT; ++b) {
-                    g.rowp[q][tx + 16 * b] = x[a][b];
+                for (int b = 0; b < RB; ++b) {
+                    g.rowp[q][tx + TX * b] = x[a][b];
                     x[a][b] = make_float2(0.f, 0.f);
                 }
             }
@@ -180,18 +180,18 @@ __device__ __forceinline__ int gj_regs(float2 (&x)[MP / 16][MP / 16], int M, GJS
         }
         __syncthreads();
         const float2 pinv = crcpf(g.col[q][p]);
-        float2 rs[RT];
+        float2 rs[RB];
 #pragma unroll
-        for (int b = 0; b < RT; ++b) {
-            const int j = tx + 16 * b;
+        for (int b = 0; b < RB; ++b) {
+            const int j = tx + TX * b;
             rs[b] = (j == k) ? pinv : cmulf(g.rowp[q][j], pinv);
         }
 #pragma unroll
-        for (int a = 0; a < RT; ++a) {
-            const int i = ty + 16 * a;
+        for (int a = 0; a < RA; ++a) {
+            const int i = ty + TY * a;
             const float2 ci = (i == p) ? make_float2(-1.f, 0.f) : g.col[q][i];
 #pragma unroll
-            for (int b = 0; b < RT; ++b) x[a][b] = cfmsf(ci, rs[b], x[a][b]);
+            for (int b = 0; b < RB; ++b) x[a][b] = cfmsf(ci, rs[b], x[a][b]);
         }
     }
     if (__syncthreads_or(st != ST_OK)) return ST_SINGULAR;
@@ -199,19 +199,19 @@ __device__ __forceinline__ int gj_regs(float2 (&x)[MP / 16][MP / 16], int M, GJS
 }
 
 // store the inverse held in x (see gj_regs) into X (MP x MP, row-major)
-template <int MP>
-__device__ __forceinline__ void store_inverse(const float2 (&x)[MP / 16][MP / 16], int M, GJShared<MP> &g,
-                              float2 *X)
+template <int MP, int TY = 16, int TX = 16>
+__device__ __forceinline__ void store_inverse(const float2 (&x)[MP / TY][MP / TX], int M,
+                                              GJShared<MP> &g, float2 *X)
 {
-    constexpr int RT = MP / 16;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    for (int k = tid; k < M; k += NT) g.pos[g.perm[k]] = k;
+    constexpr int RA = MP / TY, RB = MP / TX, NTH = TY * TX;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
+    for (int k = tid; k < M; k += NTH) g.pos[g.perm[k]] = k;
     __syncthreads();
 #pragma unroll
-    for (int a = 0; a < RT; ++a)
+    for (int a = 0; a < RA; ++a)
 #pragma unroll
-        for (int b = 0; b < RT; ++b) {
-            const int i = ty + 16 * a, c = tx + 16 * b;
+        for (int b = 0; b < RB; ++b) {
+            const int i = ty + TY * a, c = tx + TX * b;
             if (i < M && c < M) X[g.pos[i] * MP + g.perm[c]] = x[a][b];
             else X[i * MP + c] = x[a][b];
         }
@@ -221,32 +221,33 @@ __device__ __forceinline__ void store_inverse(const float2 (&x)[MP / 16][MP / 16
 // one refinement step g = X + X R, kept as hi + lo in (Gh, Gl); R has row
 // stride RS (padded rows avoid shared-memory bank conflicts where R is
 // written one row per lane)
-template <int MP, int RS = MP>
-__device__ __forceinline__ void refine(const float2 *X, const float2 *R, float2 *Gh, float2 *Gl, int M)
+template <int MP, int RS = MP, int TY = 16, int TX = 16, int RA0 = 0, int NRA = MP / TY>
+__device__ __forceinline__ void refine(const float2 *X, const float2 *R, float2 *Gh, float2 *Gl,
+                                       int M)
 {
-    constexpr int RT = MP / 16;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    float2 acc[RT][RT];
+    constexpr int RB = MP / TX;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
+    float2 acc[NRA][RB];
 #pragma unroll
-    for (int a = 0; a < RT; ++a)
+    for (int a = 0; a < NRA; ++a)
 #pragma unroll
-        for (int b = 0; b < RT; ++b) acc[a][b] = make_float2(0.f, 0.f);
+        for (int b = 0; b < RB; ++b) acc[a][b] = make_float2(0.f, 0.f);
     for (int k = 0; k < M; ++k) {
-        float2 xa[RT], rb[RT];
+        float2 xa[NRA], rb[RB];
 #pragma unroll
-        for (int a = 0; a < RT; ++a) xa[a] = X[(ty + 16 * a) * MP + k];
+        for (int a = 0; a < NRA; ++a) xa[a] = X[(ty + TY * (RA0 + a)) * MP + k];
 #pragma unroll
-        for (int b = 0; b < RT; ++b) rb[b] = R[k * RS + tx + 16 * b];
+        for (int b = 0; b < RB; ++b) rb[b] = R[k * RS + tx + TX * b];
 #pragma unroll
-        for (int a = 0; a < RT; ++a)
+        for (int a = 0; a < NRA; ++a)
 #pragma unroll
-            for (int b = 0; b < RT; ++b) acc[a][b] = cfmaf(xa[a], rb[b], acc[a][b]);
+            for (int b = 0; b < RB; ++b) acc[a][b] = cfmaf(xa[a], rb[b], acc[a][b]);
     }
 #pragma unroll
-    for (int a = 0; a < RT; ++a)
+    for (int a = 0; a < NRA; ++a)
 #pragma unroll
-        for (int b = 0; b < RT; ++b) {
-            const int e = (ty + 16 * a) * MP + tx + 16 * b;
+        for (int b = 0; b < RB; ++b) {
+            const int e = (ty + TY * (RA0 + a)) * MP + tx + TX * b;
             const float2 xv = X[e];
             float hx, lx, hy, ly;
             two_sum(xv.x, acc[a][b].x, hx, lx);
@@ -259,18 +260,18 @@ __device__ __forceinline__ void refine(const float2 *X, const float2 *R, float2 
 // Transmission from G_LL = Gh + Gl by the unitarity identity, in FP64:
 // T = Re Tr[Gamma_R i(G - G^dagger)] - Re Tr[Gamma_R G Gamma_R G^dagger].
 // G: MP*MP complex128 scratch.
-template <int MP>
+template <int MP, int NTH = NT>
 __device__ double ward_T(const float2 *Gh, const float2 *Gl, double2 *G, const double2 *SR, int M,
                          double *red)
 {
     const int tid = threadIdx.x;
-    for (int e = tid; e < MP * MP; e += NT) {
+    for (int e = tid; e < MP * MP; e += NTH) {
         float2 h = Gh[e], l = Gl[e];
         G[e] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
     }
     __syncthreads();
     double t = 0.0;
-    for (int e = tid; e < M * M; e += NT) {
+    for (int e = tid; e < M * M; e += NTH) {
         const int i = e / M, j = e - i * M;
         double2 d = csub(SR[(size_t)i * M + j], cconj(SR[(size_t)j * M + i]));
         double2 gij = make_double2(-d.y, d.x);

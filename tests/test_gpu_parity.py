@@ -230,9 +230,9 @@ def test_singular_pivot_reports_status(knit):
 
 
 def test_invalid_arguments_and_wide_mixed(knit):
-    ss = inputs.square(80, 3)
+    ss = inputs.square(140, 2)
     sysk = knit.System(ss)
-    # KNIT_MIXED above M = 64 runs the FP64 sweep
+    # KNIT_MIXED above M = 128 runs the FP64 sweep
     T1, _ = sysk.transmission([0.1, 1.3], precision=knit.KNIT_MIXED)
     T0, _ = sysk.transmission([0.1, 1.3], precision=knit.KNIT_FP64)
     assert np.array_equal(T0, T1)
@@ -289,3 +289,38 @@ def test_mixed_tensor_core_and_cuda_core_residuals(knit, M, L):
             To = oracle_T(ss, Ee, int(sd), 2.0, method="rgf")
             assert abs(T_tc[e, s] - To) / nch <= TOL_MIXED, ("tc", M, Ee, sd)
             assert abs(T_cc[e, s] - To) / nch <= TOL_MIXED, ("cc", M, Ee, sd)
+
+
+# --------------------------------------------------------------------------
+# the wide mixed kernel: widths 65..128, and 4 x 4 block couplings
+
+@pytest.mark.parametrize("M,L", [(65, 3), (80, 5), (96, 2), (97, 4), (128, 3)])
+def test_wide_mixed_square(knit, M, L):
+    ss = inputs.square(M, L)
+    E = np.array([-3.1, -0.77, 0.4, 2.05])
+    seeds = np.array([2, 9], np.uint64)
+    T, st = knit.System(ss).transmission(E, seeds, W=2.0, precision=knit.KNIT_MIXED)
+    assert (st == 0).all()
+    for e, Ee in enumerate(E):
+        for s, sd in enumerate(seeds):
+            To = oracle_T(ss, Ee, int(sd), 2.0)
+            assert abs(T[e, s] - To) / max(1, nch_square(M, Ee)) <= TOL_MIXED, (M, Ee, sd)
+
+
+@pytest.mark.parametrize("Ns,L", [(3, 6), (32, 3)])
+def test_wide_mixed_bdg_blocks(knit, Ns, L):
+    b = inputs.bdg(Ns, L, mu=-1.0, delta=0.1, alpha=0.2)
+    sysk = knit.System(b)
+    E = np.array([-0.13, 0.04])
+    Tm, st = sysk.transmission(E, seeds=[4], W=1.0, precision=knit.KNIT_MIXED)
+    Td, _ = sysk.transmission(E, seeds=[4], W=1.0, precision=knit.KNIT_FP64)
+    assert (st == 0).all()
+    # channels of the BdG leads: at most 4 per site
+    assert np.abs(Tm - Td).max() <= TOL_MIXED * 4 * Ns
+    if Ns == 3:
+        eps = oracle.onsite(4, L, b.M, 1.0, block=4, sign=b.sign)
+        for e, Ee in enumerate(E):
+            SL = oracle.decimation(b.lead_H0[0], b.lead_V[0], Ee, 0, eta=1e-12)[1]
+            SR = oracle.decimation(b.lead_H0[1], b.lead_V[1], Ee, 1, eta=1e-12)[1]
+            To = oracle.dense(b.H0, b.V, eps, L, Ee, SL, SR)["T_LR"]
+            assert abs(Tm[e, 0] - To) < 1e-6
