@@ -91,7 +91,12 @@ enum {
                                  eigensolver once per system) and the retarded
                                  1D surface function per mode; exact for
                                  lead_V = t * I */
-    KNIT_LEAD_DECIMATION = 2  /* Sancho-Rubio decimation in FP64 at E + i eta */
+    KNIT_LEAD_DECIMATION = 2, /* Sancho-Rubio decimation in FP64 at E + i eta */
+    KNIT_LEAD_LEARNED = 3     /* a trained knit_lead_model predicts g, Newton's
+                                 method refines the fixed point at eta = 0 to a
+                                 residual max|A g - I| < 1e-12 (FP64, cells of
+                                 at most 8 orbitals); energies where Newton
+                                 fails fall back to DECIMATION */
 };
 
 typedef struct {
@@ -123,6 +128,7 @@ typedef struct {
     double eta;        /* decimation broadening (default 1e-12 when <= 0) */
     double tol;        /* decimation stop: max|alpha| + max|beta| < tol (default 1e-14) */
     int32_t maxit;     /* decimation iteration cap (default 200) */
+    const void *model[2]; /* KNIT_LEAD_LEARNED: knit_lead_model of the left / right lead */
 } knit_lead_opts;
 
 /* Lead self-energy Sigma_lead(E[e]) for nE energies (Sec. 5.3 B selfE(E)).
@@ -165,6 +171,43 @@ knit_status knit_transmission_sigma(knit_system sys, const double *E, int32_t nE
 knit_status knit_ldos(knit_system sys, const double *E, int32_t nE, const uint64_t *seeds,
                       int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
                       double *ldos, double *T, int32_t *status, void *stream);
+
+/* Learned warm start for a lead (the paper's lead solver has no learned
+ * component; this one speeds up and tightens the fixed point of Sec. 5.3 B).  A multilayer perceptron (input: the
+ * energy scaled to [-1, 1] over the training range; three hidden layers of
+ * 128 tanh units; output: real and imaginary parts of the M x M surface
+ * Green function g, row-major) is trained on the GPU with the library's own
+ * forward, backward and Adam kernels (FP32) on g from the library's own
+ * decimation at the training energies.  Parameters are stored as, for layers
+ * l = 0..3, W_l (out x in, row-major) then b_l.  Cells of at most 8 orbitals. */
+typedef struct knit_lead_model_s *knit_lead_model;
+
+/* Train for `epochs` passes over the training energies in shuffled
+ * mini-batches of `batch` (Adam, learning rate lr, shuffling and
+ * initialisation drawn from `seed`); opts (may be NULL) sets the decimation
+ * that makes the targets.  loss (optional, host, `epochs` values) receives the
+ * mean squared error of each epoch.  The model belongs to (sys, lead). */
+knit_status knit_lead_model_train(knit_system sys, int32_t lead, const double *E_train,
+                                  int32_t nTrain, int32_t epochs, int32_t batch, float lr,
+                                  uint64_t seed, const knit_lead_opts *opts, float *loss,
+                                  knit_lead_model *out, void *stream);
+
+knit_status knit_lead_model_destroy(knit_lead_model model);
+
+/* Number of parameters; copy them out / in (host or device float arrays). */
+int64_t knit_lead_model_num_params(knit_lead_model model);
+knit_status knit_lead_model_get_params(knit_lead_model model, float *params);
+knit_status knit_lead_model_set_params(knit_lead_model model, const float *params);
+
+/* Network output for nE energies: nE x 2 M^2 floats (re, im of g, row-major). */
+knit_status knit_lead_model_forward(knit_lead_model model, const double *E, int32_t nE, float *out,
+                                    void *stream);
+
+/* Mean squared error of the network against `target` (n x 2 M^2 floats) and
+ * its gradient with respect to every parameter (knit_lead_model_num_params
+ * floats), as used by training. */
+knit_status knit_lead_model_gradient(knit_lead_model model, const double *E, const float *target,
+                                     int32_t n, float *grad, float *loss, void *stream);
 
 /* Heterogeneous batches (uneven widths and lengths).  A batch plan holds
  * nInst instances; instance i belongs to systems[sys_index[i]] (sys_index is

@@ -33,6 +33,26 @@ extern "C" cudaError_t knit_launch_decimation(const double2 *, const double2 *, 
                                               const double *, int, double, double, int, double2 *,
                                               double2 *, double2 *, int *, int *, int,
                                               cudaStream_t);
+extern "C" cudaError_t knit_launch_decimation_failed(const double2 *, const double2 *, int, int,
+                                                     int, const double *, int, double, double, int,
+                                                     double2 *, double2 *, double2 *, int *, int *,
+                                                     int, cudaStream_t);
+extern "C" cudaError_t knit_mlp_linear_fwd(const float *, int, int, const float *, const float *,
+                                           int, float *, int, cudaStream_t);
+extern "C" cudaError_t knit_mlp_linear_bwd(const float *, const float *, int, int, const float *,
+                                           int, float *, float *, float *, int, cudaStream_t);
+extern "C" cudaError_t knit_mlp_mse(const float *, const float *, int, float *, float *,
+                                    cudaStream_t);
+extern "C" cudaError_t knit_mlp_adam(float *, const float *, float *, float *, int, float, int,
+                                     cudaStream_t);
+extern "C" cudaError_t knit_mlp_inputs(const double *, const int *, int, double, double, float *,
+                                       cudaStream_t);
+extern "C" cudaError_t knit_mlp_targets(const double2 *, const int *, int, int, float *,
+                                        cudaStream_t);
+extern "C" cudaError_t knit_launch_lead_newton(const double2 *, const double2 *, int, int,
+                                               const double *, int, const float *, double, int,
+                                               double2 *, double2 *, int *, int *, int,
+                                               cudaStream_t);
 extern "C" cudaError_t knit_launch_lead_residual(const double2 *, const double2 *, int, int, int,
                                                  const double *, int, const double2 *, double2 *,
                                                  double *, int, cudaStream_t);
@@ -140,6 +160,38 @@ struct knit_system_s {
         s.h0_val = h0_val;
         return s;
     }
+};
+
+// learned warm start of a lead's surface Green function (lead_mlp.cu)
+struct knit_lead_model_s {
+    static constexpr int NL = 4, HID = 128;
+    knit_system sys = nullptr;
+    int lead = 0, M = 0, device = 0;
+    int dims[NL + 1] = {1, HID, HID, HID, 0};
+    size_t woff[NL] = {}, boff[NL] = {}, nparam = 0;
+    double mid = 0.0, half = 1.0;
+    DevBuf params, grads, m, v, act, dact, U, Tt, loss, idx, tmpE;
+    int step = 0;
+    int maxB = 0;
+    knit_lead_model_s(int M_) : M(M_)
+    {
+        dims[NL] = 2 * M * M;
+        size_t o = 0;
+        for (int l = 0; l < NL; ++l) {
+            woff[l] = o;
+            o += (size_t)dims[l + 1] * dims[l];
+            boff[l] = o;
+            o += dims[l + 1];
+        }
+        nparam = o;
+    }
+    size_t act_off(int l) const   // activation l (0 = input) for a batch of maxB
+    {
+        size_t o = 0;
+        for (int k = 0; k < l; ++k) o += (size_t)maxB * dims[k];
+        return o;
+    }
+    size_t act_total() const { return act_off(NL + 1); }
 };
 
 namespace {
@@ -263,6 +315,47 @@ int resolve_method(const knit_system s, int p, const knit_lead_opts *o)
     return m;
 }
 
+// ---- learned lead model helpers
+knit_status model_reserve(knit_lead_model md, int B)
+{
+    if (B <= md->maxB) return KNIT_OK;
+    md->maxB = B;
+    CK(md->act.ensure(sizeof(float) * md->act_total()), "model activations");
+    CK(md->dact.ensure(sizeof(float) * md->act_total()), "model gradients");
+    CK(md->Tt.ensure(sizeof(float) * (size_t)B * md->dims[knit_lead_model_s::NL]), "model targets");
+    return KNIT_OK;
+}
+
+knit_status model_forward(knit_lead_model md, int B, cudaStream_t st)
+{
+    const int NL = knit_lead_model_s::NL;
+    const float *P = md->params.as<float>();
+    float *A = md->act.as<float>();
+    for (int l = 0; l < NL; ++l)
+        CK(knit_mlp_linear_fwd(A + md->act_off(l), B, md->dims[l], P + md->woff[l], P + md->boff[l],
+                               md->dims[l + 1], A + md->act_off(l + 1), l < NL - 1 ? 1 : 0, st),
+           "model forward");
+    return KNIT_OK;
+}
+
+// mean squared error against md->Tt, gradients into md->grads, loss added to md->loss
+knit_status model_backward(knit_lead_model md, int B, cudaStream_t st)
+{
+    const int NL = knit_lead_model_s::NL;
+    const float *P = md->params.as<float>();
+    float *A = md->act.as<float>(), *D = md->dact.as<float>(), *G = md->grads.as<float>();
+    const int dout = md->dims[NL];
+    CK(knit_mlp_mse(A + md->act_off(NL), md->Tt.as<float>(), B * dout, D + md->act_off(NL),
+                    md->loss.as<float>(), st),
+       "model loss");
+    for (int l = NL - 1; l >= 0; --l)
+        CK(knit_mlp_linear_bwd(D + md->act_off(l + 1), A + md->act_off(l), B, md->dims[l],
+                               P + md->woff[l], md->dims[l + 1], G + md->woff[l], G + md->boff[l],
+                               l > 0 ? D + md->act_off(l) : nullptr, l > 0 ? 1 : 0, st),
+           "model backward");
+    return KNIT_OK;
+}
+
 // Sigma_p at nE device energies into sig (and g into gout), per-energy status into lst
 knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
                           const knit_lead_opts *o, double2 *sig, double2 *gout, int *lst,
@@ -283,11 +376,34 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
         if (lit) CK(cudaMemsetAsync(lit, 0, sizeof(int) * nE, st), "lead iters");
         return KNIT_OK;
     }
-    if (method != KNIT_LEAD_DECIMATION) return fail(KNIT_ERR_INVALID, "unknown lead method %d", method);
     double eta = (o && o->eta > 0) ? o->eta : 1e-12;
     double tol = (o && o->tol > 0) ? o->tol : 1e-14;
     int maxit = (o && o->maxit > 0) ? o->maxit : 200;
     const size_t MM = (size_t)M * M;
+    if (method == KNIT_LEAD_LEARNED) {
+        knit_lead_model md = o ? (knit_lead_model)o->model[p] : nullptr;
+        if (!md || md->M != M || md->sys != s || md->lead != p)
+            return fail(KNIT_ERR_INVALID, "KNIT_LEAD_LEARNED needs a model trained for this lead");
+        if (!lit || !lst)
+            return fail(KNIT_ERR_INVALID, "KNIT_LEAD_LEARNED needs status and iteration buffers");
+        knit_status r = model_reserve(md, nE);
+        if (r != KNIT_OK) return r;
+        CK(knit_mlp_inputs(dE, nullptr, nE, md->mid, md->half, md->act.as<float>(), st),
+           "model inputs");
+        if ((r = model_forward(md, nE, st)) != KNIT_OK) return r;
+        CK(knit_launch_lead_newton(s->lead[p].H0, s->lead[p].V, M, p, dE, nE,
+                                   md->act.as<float>() + md->act_off(knit_lead_model_s::NL), 1e-12,
+                                   8, sig, gout, lit, lst, grid, st),
+           "lead newton");
+        // decimation for the energies Newton did not settle (fallback and judge)
+        CK(s->decw.ensure(sizeof(double2) * 8 * MM * grid), "decimation workspace");
+        CK(knit_launch_decimation_failed(s->lead[p].H0, s->lead[p].V, M, s->lead[p].vb, p, dE, nE,
+                                         eta, tol, maxit, s->decw.as<double2>(), sig, gout, lit,
+                                         lst, grid, st),
+           "decimation fallback");
+        return KNIT_OK;
+    }
+    if (method != KNIT_LEAD_DECIMATION) return fail(KNIT_ERR_INVALID, "unknown lead method %d", method);
     CK(s->decw.ensure(sizeof(double2) * 8 * MM * grid), "decimation workspace");
     CK(knit_launch_decimation(s->lead[p].H0, s->lead[p].V, M, s->lead[p].vb, p, dE, nE, eta, tol,
                               maxit, s->decw.as<double2>(), sig, gout, lit, lst, grid, st),
@@ -311,8 +427,9 @@ knit_status both_sigmas(knit_system s, const double *dE, int nE, const knit_lead
     CK(s->gL.ensure(sizeof(double2) * MM * nE), "g workspace");
     CK(s->lst.ensure(sizeof(int) * 2 * nE), "lead status");
     int *st0 = s->lst.as<int>(), *st1 = st0 + nE;
+    CK(s->lit.ensure(sizeof(int) * nE * 2), "iterations");
     knit_status r = compute_sigma(s, 0, dE, nE, o, s->sigL.as<double2>(), s->gL.as<double2>(),
-                                  st0, nullptr, st);
+                                  st0, s->lit.as<int>(), st);
     if (r != KNIT_OK) return r;
     *sL = s->sigL.as<double2>();
     if (s->leads_same && s->lead[0].scalar && resolve_method(s, 1, o) == KNIT_LEAD_MODES) {
@@ -322,7 +439,7 @@ knit_status both_sigmas(knit_system s, const double *dE, int nE, const knit_lead
         CK(s->sigR.ensure(sizeof(double2) * MM * nE), "sigma workspace");
         CK(s->gR.ensure(sizeof(double2) * MM * nE), "g workspace");
         r = compute_sigma(s, 1, dE, nE, o, s->sigR.as<double2>(), s->gR.as<double2>(), st1,
-                          nullptr, st);
+                          s->lit.as<int>() + nE, st);
         if (r != KNIT_OK) return r;
         *sR = s->sigR.as<double2>();
     }
@@ -967,6 +1084,202 @@ knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_
     if (hT) CK(cudaMemcpyAsync(T, dT, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
     if (hSt) CK(cudaMemcpyAsync(status, dSt, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
     return finish(st, hT || hSt, "knit_batch_transmission");
+}
+
+
+// ---------------------------------------------------------------------------
+// learned lead model
+
+knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_train, int32_t nTrain,
+                                  int32_t epochs, int32_t batch, float lr, uint64_t seed,
+                                  const knit_lead_opts *opts, float *loss_out,
+                                  knit_lead_model *out, void *stream)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if (!out || !E_train || nTrain < 2 || epochs < 1 || batch < 1 || !(lr > 0.f))
+        return fail(KNIT_ERR_INVALID, "knit_lead_model_train: bad arguments");
+    if (lead != 0 && lead != 1) return fail(KNIT_ERR_INVALID, "lead must be 0 or 1");
+    if (s->M > 8) return fail(KNIT_ERR_INVALID, "learned leads support cells of at most 8 orbitals");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> hE;
+    if ((r = to_host(hE, E_train, (size_t)nTrain, "E_train")) != KNIT_OK) return r;
+    knit_lead_model md = new (std::nothrow) knit_lead_model_s(s->M);
+    if (!md) return fail(KNIT_ERR_OOM, "host allocation");
+    md->sys = s;
+    md->lead = lead;
+    md->device = s->device;
+    const double lo = *std::min_element(hE.begin(), hE.end());
+    const double hi = *std::max_element(hE.begin(), hE.end());
+    md->mid = 0.5 * (lo + hi);
+    md->half = std::max(0.5 * (hi - lo), 1e-6);
+    auto cleanup = [&](knit_status code) {
+        DevBuf *bufs[] = {&md->params, &md->grads, &md->m, &md->v, &md->act, &md->dact, &md->U,
+                          &md->Tt, &md->loss, &md->idx, &md->tmpE};
+        for (DevBuf *b : bufs) b->release();
+        delete md;
+        return code;
+    };
+    // initial weights: uniform in +-sqrt(6 / (fan_in + fan_out)) from a SplitMix64 stream
+    std::vector<float> P(md->nparam, 0.f);
+    uint64_t z = seed;
+    auto urand = [&]() {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x ^= x >> 31;
+        return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < knit_lead_model_s::NL; ++l) {
+        const double a = std::sqrt(6.0 / (md->dims[l] + md->dims[l + 1]));
+        for (size_t q = 0; q < (size_t)md->dims[l + 1] * md->dims[l]; ++q)
+            P[md->woff[l] + q] = (float)(a * (2.0 * urand() - 1.0));
+    }
+    cudaError_t e;
+    if ((e = md->params.ensure(sizeof(float) * md->nparam)) != cudaSuccess ||
+        (e = md->grads.ensure(sizeof(float) * md->nparam)) != cudaSuccess ||
+        (e = md->m.ensure(sizeof(float) * md->nparam)) != cudaSuccess ||
+        (e = md->v.ensure(sizeof(float) * md->nparam)) != cudaSuccess ||
+        (e = md->loss.ensure(sizeof(float))) != cudaSuccess ||
+        (e = md->tmpE.ensure(sizeof(double) * nTrain)) != cudaSuccess ||
+        (e = md->idx.ensure(sizeof(int) * nTrain)) != cudaSuccess ||
+        (e = cudaMemcpy(md->params.p, P.data(), sizeof(float) * md->nparam, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(md->m.p, 0, sizeof(float) * md->nparam)) != cudaSuccess ||
+        (e = cudaMemset(md->v.p, 0, sizeof(float) * md->nparam)) != cudaSuccess ||
+        (e = cudaMemcpy(md->tmpE.p, hE.data(), sizeof(double) * nTrain, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "model allocation"));
+    // targets: the library's own decimation at every training energy
+    const size_t MM = (size_t)s->M * s->M;
+    DevBuf gtr, sgtr, sttr;
+    if ((e = gtr.ensure(sizeof(double2) * MM * nTrain)) != cudaSuccess ||
+        (e = sgtr.ensure(sizeof(double2) * MM * nTrain)) != cudaSuccess ||
+        (e = sttr.ensure(sizeof(int) * nTrain)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "training targets"));
+    knit_lead_opts dec{};
+    dec.method = KNIT_LEAD_DECIMATION;
+    if (opts) {
+        dec.eta = opts->eta;
+        dec.tol = opts->tol;
+        dec.maxit = opts->maxit;
+    }
+    if ((r = compute_sigma(s, lead, md->tmpE.as<double>(), nTrain, &dec, sgtr.as<double2>(),
+                           gtr.as<double2>(), sttr.as<int>(), nullptr, st)) != KNIT_OK)
+        return cleanup(r);
+    std::vector<int> hst(nTrain);
+    if ((e = cudaMemcpyAsync(hst.data(), sttr.p, sizeof(int) * nTrain, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "training targets"));
+    std::vector<int> valid;
+    for (int i = 0; i < nTrain; ++i)
+        if (hst[i] == ST_OK) valid.push_back(i);
+    if (valid.size() < 2) return cleanup(fail(KNIT_ERR_NOCONVERGE, "decimation failed on the training set"));
+    const int nv = (int)valid.size();
+    const int B = std::min(batch, nv);
+    if ((r = model_reserve(md, B)) != KNIT_OK) return cleanup(r);
+    const int dout = md->dims[knit_lead_model_s::NL];
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int i = nv - 1; i > 0; --i) {   // Fisher-Yates shuffle of the valid set
+            const int j = (int)(urand() * (i + 1));
+            std::swap(valid[i], valid[std::min(j, i)]);
+        }
+        if ((e = cudaMemcpyAsync(md->idx.p, valid.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(md->loss.p, 0, sizeof(float), st)) != cudaSuccess)
+            return cleanup(cuda_fail(e, "training"));
+        int nb = 0;
+        for (int b0 = 0; b0 + B <= nv; b0 += B, ++nb) {
+            const int *ib = md->idx.as<int>() + b0;
+            if ((e = knit_mlp_inputs(md->tmpE.as<double>(), ib, B, md->mid, md->half,
+                                     md->act.as<float>(), st)) != cudaSuccess ||
+                (e = knit_mlp_targets(gtr.as<double2>(), ib, B, (int)MM, md->Tt.as<float>(), st)) != cudaSuccess)
+                return cleanup(cuda_fail(e, "training batch"));
+            if ((r = model_forward(md, B, st)) != KNIT_OK || (r = model_backward(md, B, st)) != KNIT_OK)
+                return cleanup(r);
+            if ((e = knit_mlp_adam(md->params.as<float>(), md->grads.as<float>(), md->m.as<float>(),
+                                   md->v.as<float>(), (int)md->nparam, lr, ++md->step, st)) != cudaSuccess)
+                return cleanup(cuda_fail(e, "adam"));
+        }
+        if (loss_out) {
+            float l = 0.f;
+            if ((e = cudaMemcpyAsync(&l, md->loss.p, sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return cleanup(cuda_fail(e, "training loss"));
+            loss_out[ep] = nb ? l / nb : 0.f;
+        }
+    }
+    (void)dout;
+    CK(cudaStreamSynchronize(st), "training");
+    *out = md;
+    return KNIT_OK;
+}
+
+knit_status knit_lead_model_destroy(knit_lead_model md)
+{
+    if (!md) return KNIT_OK;
+    cudaSetDevice(md->device);
+    DevBuf *bufs[] = {&md->params, &md->grads, &md->m, &md->v, &md->act, &md->dact, &md->U,
+                      &md->Tt, &md->loss, &md->idx, &md->tmpE};
+    for (DevBuf *b : bufs) b->release();
+    delete md;
+    return KNIT_OK;
+}
+
+int64_t knit_lead_model_num_params(knit_lead_model md) { return md ? (int64_t)md->nparam : 0; }
+
+knit_status knit_lead_model_get_params(knit_lead_model md, float *params)
+{
+    if (!md || !params) return fail(KNIT_ERR_INVALID, "NULL argument");
+    CK(cudaMemcpy(params, md->params.p, sizeof(float) * md->nparam, cudaMemcpyDefault), "get params");
+    return KNIT_OK;
+}
+
+knit_status knit_lead_model_set_params(knit_lead_model md, const float *params)
+{
+    if (!md || !params) return fail(KNIT_ERR_INVALID, "NULL argument");
+    CK(cudaMemcpy(md->params.p, params, sizeof(float) * md->nparam, cudaMemcpyDefault), "set params");
+    return KNIT_OK;
+}
+
+knit_status knit_lead_model_forward(knit_lead_model md, const double *E, int32_t nE, float *out,
+                                    void *stream)
+{
+    if (!md || !E || !out || nE < 1) return fail(KNIT_ERR_INVALID, "bad arguments");
+    CK(cudaSetDevice(md->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    knit_status r;
+    const double *dE;
+    if ((r = stage_in(md->tmpE, E, (size_t)nE, st, &dE, "E")) != KNIT_OK) return r;
+    if ((r = model_reserve(md, nE)) != KNIT_OK) return r;
+    CK(knit_mlp_inputs(dE, nullptr, nE, md->mid, md->half, md->act.as<float>(), st), "inputs");
+    if ((r = model_forward(md, nE, st)) != KNIT_OK) return r;
+    const size_t n = (size_t)nE * md->dims[knit_lead_model_s::NL];
+    CK(cudaMemcpyAsync(out, md->act.as<float>() + md->act_off(knit_lead_model_s::NL),
+                       sizeof(float) * n, cudaMemcpyDefault, st), "forward out");
+    return finish(st, true, "knit_lead_model_forward");
+}
+
+knit_status knit_lead_model_gradient(knit_lead_model md, const double *E, const float *target,
+                                     int32_t n, float *grad, float *loss, void *stream)
+{
+    if (!md || !E || !target || !grad || n < 1) return fail(KNIT_ERR_INVALID, "bad arguments");
+    CK(cudaSetDevice(md->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    knit_status r;
+    const double *dE;
+    if ((r = stage_in(md->tmpE, E, (size_t)n, st, &dE, "E")) != KNIT_OK) return r;
+    if ((r = model_reserve(md, n)) != KNIT_OK) return r;
+    const int dout = md->dims[knit_lead_model_s::NL];
+    CK(cudaMemcpyAsync(md->Tt.p, target, sizeof(float) * (size_t)n * dout, cudaMemcpyDefault, st),
+       "targets");
+    CK(knit_mlp_inputs(dE, nullptr, n, md->mid, md->half, md->act.as<float>(), st), "inputs");
+    CK(md->loss.ensure(sizeof(float)), "loss");
+    CK(cudaMemsetAsync(md->loss.p, 0, sizeof(float), st), "loss");
+    if ((r = model_forward(md, n, st)) != KNIT_OK || (r = model_backward(md, n, st)) != KNIT_OK)
+        return r;
+    CK(cudaMemcpyAsync(grad, md->grads.p, sizeof(float) * md->nparam, cudaMemcpyDefault, st), "grad");
+    if (loss) CK(cudaMemcpyAsync(loss, md->loss.p, sizeof(float), cudaMemcpyDefault, st), "loss");
+    return finish(st, true, "knit_lead_model_gradient");
 }
 
 }  // extern "C"

@@ -161,7 +161,7 @@ knit_modes_sigma_kernel(const double2 *U, const double2 *Adiag, int M, double t2
 extern "C" __global__ void __launch_bounds__(256)
 knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int side, const double *E,
                        int nE, double eta, double tol, int maxit, double2 *work, double2 *sigma,
-                       double2 *gout, int *iters, int *status)
+                       double2 *gout, int *iters, int *status, int only_failed)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GJScratch64 sc;
@@ -185,6 +185,7 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
     double2 *eps = w, *eps_s = w + MM, *al = w + 2 * MM, *be = w + 3 * MM;
     double2 *gb = w + 4 * MM, *t1 = w + 5 * MM, *t2 = w + 6 * MM, *t3 = w + 7 * MM;
     for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+        if (only_failed && status[e] == ST_OK) continue;   // uniform over the block
         const double2 z = make_double2(E[e], eta);
         for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
             int i = q / M, j = q - i * M;
@@ -363,7 +364,21 @@ extern "C" cudaError_t knit_launch_decimation(const double2 *H0, const double2 *
                                               int *status, int grid, cudaStream_t stream)
 {
     knit_decimation_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(
-        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status);
+        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status, 0);
+    return cudaGetLastError();
+}
+
+// decimation of only the energies whose status is not ST_OK (fallback after
+// the learned start); their iteration counts are overwritten
+extern "C" cudaError_t knit_launch_decimation_failed(const double2 *H0, const double2 *V, int M,
+                                                     int vb, int side, const double *E, int nE,
+                                                     double eta, double tol, int maxit,
+                                                     double2 *work, double2 *sigma, double2 *g,
+                                                     int *iters, int *status, int grid,
+                                                     cudaStream_t stream)
+{
+    knit_decimation_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(
+        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status, 1);
     return cudaGetLastError();
 }
 

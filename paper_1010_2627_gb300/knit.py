@@ -22,7 +22,7 @@ from . import build as _build
 KNIT_OK, KNIT_ERR_INVALID, KNIT_ERR_OOM, KNIT_ERR_CUDA = 0, 1, 2, 3
 KNIT_ERR_SINGULAR, KNIT_ERR_NOCONVERGE, KNIT_ERR_TIMEOUT, KNIT_ERR_NONFINITE = 4, 5, 6, 7
 KNIT_FP64, KNIT_MIXED, KNIT_MIXED_CUDACORE = 0, 1, 2
-KNIT_LEAD_AUTO, KNIT_LEAD_MODES, KNIT_LEAD_DECIMATION = 0, 1, 2
+KNIT_LEAD_AUTO, KNIT_LEAD_MODES, KNIT_LEAD_DECIMATION, KNIT_LEAD_LEARNED = 0, 1, 2, 3
 
 P = ctypes.c_void_p
 i32, f64 = ctypes.c_int32, ctypes.c_double
@@ -34,7 +34,7 @@ class knit_system_desc(ctypes.Structure):
 
 
 class knit_lead_opts(ctypes.Structure):
-    _fields_ = [("method", i32), ("eta", f64), ("tol", f64), ("maxit", i32)]
+    _fields_ = [("method", i32), ("eta", f64), ("tol", f64), ("maxit", i32), ("model", P * 2)]
 
 
 class KnitError(RuntimeError):
@@ -55,6 +55,14 @@ _SIGS = {
     "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
+    "knit_lead_model_train": (i32, [P, i32, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64,
+                                    P, P, P, P]),
+    "knit_lead_model_destroy": (i32, [P]),
+    "knit_lead_model_num_params": (ctypes.c_int64, [P]),
+    "knit_lead_model_get_params": (i32, [P, P]),
+    "knit_lead_model_set_params": (i32, [P, P]),
+    "knit_lead_model_forward": (i32, [P, P, i32, P, P]),
+    "knit_lead_model_gradient": (i32, [P, P, P, i32, P, P, P]),
     "knit_batch_destroy": (i32, [P]),
     "knit_batch_transmission": (i32, [P, P, P, P, P, P, P, P]),
     "knit_last_error": (ctypes.c_char_p, []),
@@ -121,8 +129,11 @@ def _c128(a):
     return np.ascontiguousarray(a, dtype=np.complex128)
 
 
-def _opts(method=KNIT_LEAD_AUTO, eta=0.0, tol=0.0, maxit=0):
-    return knit_lead_opts(int(method), float(eta), float(tol), int(maxit))
+def _opts(method=KNIT_LEAD_AUTO, eta=0.0, tol=0.0, maxit=0, models=(None, None)):
+    o = knit_lead_opts(int(method), float(eta), float(tol), int(maxit))
+    for p in range(2):
+        o.model[p] = models[p]
+    return o
 
 
 # ---------------------------------------------------------------------------
@@ -230,6 +241,63 @@ def knit_batch_transmission(plan, E, seeds, W, T, status=None, opts=None, stream
                                           _ptr(status), _stream(stream)))
 
 
+class LeadModel:
+    """A learned warm start for one lead of a System (see include/knit.h)."""
+
+    def __init__(self, system, lead, E_train, epochs=200, batch=256, lr=1e-3, seed=0, eta=0.0):
+        self.system = system
+        self.lead = lead
+        E = np.ascontiguousarray(E_train, dtype=np.float64)
+        self.loss = np.zeros(epochs, np.float32)
+        out = P()
+        o = _opts(KNIT_LEAD_DECIMATION, eta)
+        _check(load().knit_lead_model_train(P(system.handle), int(lead), _ptr(E), len(E),
+                                            int(epochs), int(batch), ctypes.c_float(lr),
+                                            ctypes.c_uint64(seed), ctypes.byref(o),
+                                            _ptr(self.loss), ctypes.byref(out), None))
+        self.handle = out.value
+
+    def close(self):
+        if self.handle:
+            _check(load().knit_lead_model_destroy(P(self.handle)))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_params(self):
+        return int(load().knit_lead_model_num_params(P(self.handle)))
+
+    def get_params(self):
+        out = np.empty(self.num_params, np.float32)
+        _check(load().knit_lead_model_get_params(P(self.handle), _ptr(out)))
+        return out
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().knit_lead_model_set_params(P(self.handle), _ptr(p)))
+
+    def forward(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        M = self.system.M
+        out = np.empty((len(E), 2 * M * M), np.float32)
+        _check(load().knit_lead_model_forward(P(self.handle), _ptr(E), len(E), _ptr(out), None))
+        return out
+
+    def gradient(self, E, target):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        grad = np.empty(self.num_params, np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(load().knit_lead_model_gradient(P(self.handle), _ptr(E), _ptr(t), len(E),
+                                               _ptr(grad), _ptr(loss), None))
+        return grad, float(loss[0])
+
+
 class Batch:
     """A heterogeneous batch plan over ``System`` objects (kept alive here)."""
 
@@ -283,12 +351,14 @@ class System:
         except Exception:
             pass
 
-    def lead_selfenergy(self, lead, E, method=KNIT_LEAD_AUTO, eta=0.0, want_residual=False):
+    def lead_selfenergy(self, lead, E, method=KNIT_LEAD_AUTO, eta=0.0, want_residual=False,
+                        models=(None, None)):
         E = np.ascontiguousarray(E, dtype=np.float64)
         S = np.empty((len(E), self.M, self.M), np.complex128)
         it = np.zeros(len(E), np.int32)
         res = np.zeros(len(E)) if want_residual else None
-        knit_lead_selfenergy(self.handle, lead, E, S, _opts(method, eta), it, res)
+        mods = tuple(None if m is None else m.handle for m in models)
+        knit_lead_selfenergy(self.handle, lead, E, S, _opts(method, eta, models=mods), it, res)
         return S, it, res
 
     def transmission(self, E, seeds=None, W=0.0, precision=KNIT_FP64, method=KNIT_LEAD_AUTO):

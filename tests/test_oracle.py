@@ -301,3 +301,36 @@ def test_bdg_particle_hole_symmetry():
         Tee = _bdg_T(b, E, eps, "e")
         Thh = _bdg_T(b, -E, eps, "h")
         assert abs(Tee - Thh) < 1e-9, (E, Tee, Thh)
+
+
+# --------------------------------------------------------------------------
+# Reference of the lead-model network (forward and gradient)
+
+def test_mlp_reference_gradient_matches_finite_differences():
+    from oracle import mlp
+    dims = [1, 5, 4, 3, 6]
+    rng = np.random.default_rng(11)
+    _, n = mlp.layout(dims)
+    p = rng.standard_normal(n) * 0.7
+    u = rng.uniform(-1, 1, (7, 1))
+    t = rng.standard_normal((7, 6))
+    loss, g = mlp.loss_and_grad(p, dims, u, t)
+    h = 1e-6
+    for k in rng.choice(n, 25, replace=False):
+        e = np.zeros(n)
+        e[k] = h
+        fd = (mlp.loss_and_grad(p + e, dims, u, t)[0] - mlp.loss_and_grad(p - e, dims, u, t)[0]) / (2 * h)
+        assert abs(fd - g[k]) < 1e-7 * max(1.0, abs(fd)), k
+
+
+def test_mlp_reference_special_cases():
+    from oracle import mlp
+    dims = [1, 3, 3, 3, 2]
+    _, n = mlp.layout(dims)
+    p = np.zeros(n)
+    offs, _ = mlp.layout(dims)
+    p[offs[-1][1]:offs[-1][1] + 2] = [0.25, -1.5]     # output bias only
+    y = mlp.forward(p, dims, np.array([[0.3], [-0.9]]))[-1]
+    assert np.array_equal(y, np.array([[0.25, -1.5], [0.25, -1.5]]))
+    loss, g = mlp.loss_and_grad(p, dims, np.array([[0.3]]), np.array([[0.25, -1.5]]))
+    assert loss == 0.0 and not g.any()
