@@ -162,9 +162,11 @@ def run_knit(args):
     build.build()
     knit.load()
 
+    from paper_1010_2627_gb300 import shard
     ss = inputs.square(M, L)
-    shift = (rank * 0.37 / NE) if ws > 1 else 0.0   # distinct energies per rank
-    E = inputs.energy_grid(-3.9 + shift, 3.9 + shift, NE)
+    # weak scaling: the global grid has NE energies per rank, rank r takes
+    # every ws-th energy (its own 1024-energy shard of the same interval)
+    E = inputs.energy_grid(-3.9, 3.9, NE * ws)[shard.interleave(NE * ws, ws, rank)]
     seeds = np.arange(NS, dtype=np.uint64)
     n = NE * NS
     sysk = knit.System(ss)
