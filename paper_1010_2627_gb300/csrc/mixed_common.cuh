@@ -61,6 +61,7 @@ struct GJShared {
     int used[MP];
     int perm[MP];
     int pos[MP];
+    int flag;
 };
 
 // E - onsite of slice n for orbitals 0..MP-1 (0 in the padding)
@@ -198,6 +199,144 @@ __device__ __forceinline__ int gj_regs(float2 (&x)[MP / TY][MP / TX], int M, GJS
     return ST_OK;
 }
 
+// 1 / a for the pivots of gj_blocked: a is scaled by the power of two 2^-e
+// (e the exponent of max(|Re|, |Im|), exact) into [1, 2), so one IEEE
+// reciprocal of |a|^2 in [1, 8] suffices and nothing overflows or flushes
+KNIT_DEV float2 crcp_pow2f(float2 a)
+{
+    const float m = fmaxf(fabsf(a.x), fabsf(a.y));
+    const int e = min(max(((__float_as_int(m) >> 23) & 0xff) - 127, -126), 126);
+    const float s = __int_as_float((127 - e) << 23);
+    const float ax = a.x * s, ay = a.y * s;
+    const float d = __frcp_rn(fmaf(ax, ax, ay * ay)) * s;
+    return make_float2(ax * d, -ay * d);
+}
+
+// Blocked Gauss-Jordan inversion of X (M x M inside MP x MP, row-major,
+// shared memory, in place) with the same implicit partial pivoting and the
+// same result layout as gj_regs.  One elimination step with pivot row p and
+// column k is the exact rank-1 update x -= u v^T with u = x[:, k] - e_p and
+// v = (x[p, :] + e_k) / x[p][k]: it zeroes the pivot column and row and
+// writes their new values in one stroke.  Steps are grouped in panels of NB
+// columns.  Warp 0 runs a panel's steps alone, keeping the panel columns
+// current in registers and forming each pivot row from X minus the panel's
+// pending updates; U (NB x MP) and V (NB x MP) collect u and v.  Then the
+// whole block applies X -= U^T V.  So the block meets at two barriers per
+// panel instead of two per column, and the pivot search is one warp
+// reduction of (|Re|+|Im| with its low mantissa bits cleared | inverted row)
+// keys: the largest magnitude to 2^-17, lowest row on near-ties.
+template <int MP, int TY, int TX, int NB = 8>
+__device__ __forceinline__ int gj_blocked(float2 *X, int M, float2 *U, float2 *V, GJShared<MP> &g)
+{
+    static_assert(MP % 32 == 0 && MP % NB == 0 && 32 % NB == 0 && MP <= 128, "panel layout");
+    constexpr int RA = MP / TY, RB = MP / TX, R2 = MP / 32, IB = MP <= 64 ? 6 : 7;
+    constexpr unsigned IMASK = (1u << IB) - 1u, FULL = 0xffffffffu;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX, lane = tid & 31;
+    bool open[R2];   // warp 0: row lane + 32t may still become a pivot row
+#pragma unroll
+    for (int t = 0; t < R2; ++t) open[t] = lane + 32 * t < M;
+    for (int K = 0; K < M; K += NB) {
+        if (tid < 32) {
+            const int tK = K >> 5, lK = K & 31;   // panel columns: lanes lK.., slot tK
+            float2 pc[R2][NB];   // panel columns, rows lane + 32t
+            float2 vh[R2][NB];   // this lane's entries of the panel's v vectors
+#pragma unroll
+            for (int t = 0; t < R2; ++t)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) pc[t][c] = X[(lane + 32 * t) * MP + K + c];
+            int bad = 0;
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk) {
+                const int k = K + kk;
+                if (k >= M) break;
+                unsigned key = 0u;
+#pragma unroll
+                for (int t = 0; t < R2; ++t)
+                    if (open[t])
+                        key = max(key, (__float_as_uint(cabs1f(pc[t][kk])) & ~IMASK) |
+                                           (IMASK - (unsigned)(lane + 32 * t)));
+                key = __reduce_max_sync(FULL, key);
+                if ((key & ~IMASK) == 0u) { bad = 1; break; }
+                const int p = (int)(IMASK - (key & IMASK)), pl = p & 31, pt = p >> 5;
+                float2 own = pc[0][kk];
+#pragma unroll
+                for (int t = 1; t < R2; ++t)
+                    if (t == pt) own = pc[t][kk];
+                const float2 piv = make_float2(__shfl_sync(FULL, own.x, pl),
+                                               __shfl_sync(FULL, own.y, pl));
+                float2 up[NB];   // u vectors of the earlier steps at row p
+#pragma unroll
+                for (int c = 0; c < kk; ++c) up[c] = U[c * MP + p];
+                float2 rv[R2];
+#pragma unroll
+                for (int t = 0; t < R2; ++t) {
+                    float2 r = X[p * MP + lane + 32 * t];
+#pragma unroll
+                    for (int c = 0; c < kk; ++c) r = cfmsf(up[c], vh[t][c], r);
+                    rv[t] = r;
+                }
+                const float2 rinv = crcp_pow2f(piv);
+                float2 uu[R2];
+#pragma unroll
+                for (int t = 0; t < R2; ++t) {
+                    const int j = lane + 32 * t;
+                    float2 v = cmulf(rv[t], rinv);
+                    if (j == k) { v.x += rinv.x; v.y += rinv.y; }
+                    vh[t][kk] = v;
+                    V[kk * MP + j] = v;
+                    float2 u = pc[t][kk];
+                    if (j == p) { u.x -= 1.f; open[t] = false; }
+                    U[kk * MP + j] = u;
+                    uu[t] = u;
+                }
+                if (lane == 0) g.perm[k] = p;
+                float2 vs = vh[0][kk];
+#pragma unroll
+                for (int t = 1; t < R2; ++t)
+                    if (t == tK) vs = vh[t][kk];
+#pragma unroll
+                for (int c = kk + 1; c < NB; ++c) {
+                    const float2 vk = make_float2(__shfl_sync(FULL, vs.x, lK + c),
+                                                  __shfl_sync(FULL, vs.y, lK + c));
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) pc[t][c] = cfmsf(uu[t], vk, pc[t][c]);
+                }
+                __syncwarp();
+            }
+            if (lane == 0) g.flag = bad;
+        }
+        __syncthreads();
+        if (g.flag) return ST_SINGULAR;
+        // X -= U^T V over the whole matrix, a register tile per thread
+        const int nk = min(NB, M - K);
+        float2 acc[RA][RB];
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b) acc[a][b] = X[(ty + TY * a) * MP + tx + TX * b];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+            if (c < nk) {
+                float2 ua[RA], vb[RB];
+#pragma unroll
+                for (int a = 0; a < RA; ++a) ua[a] = U[c * MP + ty + TY * a];
+#pragma unroll
+                for (int b = 0; b < RB; ++b) vb[b] = V[c * MP + tx + TX * b];
+#pragma unroll
+                for (int a = 0; a < RA; ++a)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) acc[a][b] = cfmsf(ua[a], vb[b], acc[a][b]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b) X[(ty + TY * a) * MP + tx + TX * b] = acc[a][b];
+        __syncthreads();
+    }
+    return ST_OK;
+}
+
 // store the inverse held in x (see gj_regs) into X (MP x MP, row-major)
 template <int MP, int TY = 16, int TX = 16>
 __device__ __forceinline__ void store_inverse(const float2 (&x)[MP / TY][MP / TX], int M,
@@ -252,6 +391,151 @@ __device__ __forceinline__ void refine(const float2 *X, const float2 *R, float2 
             float hx, lx, hy, ly;
             two_sum(xv.x, acc[a][b].x, hx, lx);
             two_sum(xv.y, acc[a][b].y, hy, ly);
+            Gh[e] = make_float2(hx, hy);
+            Gl[e] = make_float2(lx, ly);
+        }
+}
+
+// Largest value of a non-negative float over the block (NTH threads);
+// buf holds NTH / 32 words.  Non-negative floats order like their bit
+// patterns, so each warp reduces the bits in one instruction.
+template <int NTH>
+__device__ __forceinline__ float block_max_nonneg(float v, unsigned *buf)
+{
+    const unsigned k = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+    if ((threadIdx.x & 31) == 0) buf[threadIdx.x >> 5] = k;
+    __syncthreads();
+    unsigned m = 0u;
+#pragma unroll
+    for (int w = 0; w < NTH / 32; ++w) m = max(m, buf[w]);
+    return __uint_as_float(m);
+}
+
+// With R = I - A X' exact, A^{-1} = X' (I - R)^{-1} = X' (I + R + R^2 + ...):
+// one refinement step keeps I + R and leaves an error of order |R|^2, each
+// further term multiplies it by |R|.  neumann_terms picks how many further
+// terms bring (sqrt(M) max|R_ij|)^(2 + n) below NEUMANN_TOL (at most
+// NEUMANN_MAX); well-conditioned slices need none.
+constexpr int NEUMANN_MAX = 8;
+constexpr float NEUMANN_TOL = 1e-8f;
+KNIT_DEV int neumann_terms(float rmax, int M)
+{
+    const float p = sqrtf((float)M) * rmax;
+    float t = p * p;
+    int n = 0;
+    while (t > NEUMANN_TOL && n < NEUMANN_MAX) {
+        t *= p;
+        ++n;
+    }
+    return n;
+}
+
+// One Horner step of the series on the thread's tile rows RA0 .. RA0+NRA-1:
+// acc = R + R S (R, S with row stride RS; zero outside M x M)
+template <int MP, int RS, int TY, int TX, int RA0 = 0, int NRA = MP / TY>
+__device__ __forceinline__ void neumann_tile(const float2 *R, const float2 *S,
+                                             float2 (&acc)[NRA][MP / TX], int M)
+{
+    constexpr int RB = MP / TX;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
+#pragma unroll
+    for (int a = 0; a < NRA; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[a][b] = R[(ty + TY * (RA0 + a)) * RS + tx + TX * b];
+    for (int k = 0; k < M; ++k) {
+        float2 ra[NRA], sb[RB];
+#pragma unroll
+        for (int a = 0; a < NRA; ++a) ra[a] = R[(ty + TY * (RA0 + a)) * RS + k];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) sb[b] = S[k * RS + tx + TX * b];
+#pragma unroll
+        for (int a = 0; a < NRA; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b) acc[a][b] = cfmaf(ra[a], sb[b], acc[a][b]);
+    }
+}
+
+// The further terms in place: S (row stride RS) receives R + R S_prev n
+// times, starting from S_prev = R.  Every thread holds its whole tile, so
+// one barrier between the reads and the writes of a step suffices.
+template <int MP, int RS, int TY, int TX>
+__device__ __forceinline__ void neumann_inplace(const float2 *R, float2 *S, int M, int n)
+{
+    constexpr int RA = MP / TY, RB = MP / TX;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
+    for (int t = 0; t < n; ++t) {
+        float2 acc[RA][RB];
+        neumann_tile<MP, RS, TY, TX>(R, t == 0 ? R : S, acc, M);
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < RA; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b) S[(ty + TY * a) * RS + tx + TX * b] = acc[a][b];
+        __syncthreads();
+    }
+}
+
+// Above this largest |R_ij| the refinement product X S is accumulated
+// error-free (refine_exact): the rounding of an fp32 product, about
+// 2^-24 sqrt(M) max|R_ij| relative, would otherwise enter every later slice.
+constexpr float EXACT_RMAX = 1e-4f;
+
+// s + e += a * b with the product's rounding error kept (TwoProduct by FMA,
+// running sum by two_sum)
+KNIT_DEV void dot2_acc1(float a, float b, float &s, float &e)
+{
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    float t, te;
+    two_sum(s, p, t, te);
+    s = t;
+    e += te + pe;
+}
+
+// refine with X S accumulated as double-float: g = X + (X S)_hi + (X S)_lo
+template <int MP, int RS = MP, int TY = 16, int TX = 16, int RA0 = 0, int NRA = MP / TY>
+__device__ __forceinline__ void refine_exact(const float2 *X, const float2 *S, float2 *Gh,
+                                             float2 *Gl, int M)
+{
+    constexpr int RB = MP / TX;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX;
+    float2 sh[NRA][RB], se[NRA][RB];
+#pragma unroll
+    for (int a = 0; a < NRA; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            sh[a][b] = make_float2(0.f, 0.f);
+            se[a][b] = make_float2(0.f, 0.f);
+        }
+    for (int k = 0; k < M; ++k) {
+        float2 xa[NRA], sb[RB];
+#pragma unroll
+        for (int a = 0; a < NRA; ++a) xa[a] = X[(ty + TY * (RA0 + a)) * MP + k];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) sb[b] = S[k * RS + tx + TX * b];
+#pragma unroll
+        for (int a = 0; a < NRA; ++a)
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                dot2_acc1(xa[a].x, sb[b].x, sh[a][b].x, se[a][b].x);
+                dot2_acc1(-xa[a].y, sb[b].y, sh[a][b].x, se[a][b].x);
+                dot2_acc1(xa[a].x, sb[b].y, sh[a][b].y, se[a][b].y);
+                dot2_acc1(xa[a].y, sb[b].x, sh[a][b].y, se[a][b].y);
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < NRA; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int e = (ty + TY * (RA0 + a)) * MP + tx + TX * b;
+            const float2 xv = X[e];
+            float hx, lx, hy, ly;
+            two_sum(xv.x, sh[a][b].x, hx, lx);
+            lx += se[a][b].x;
+            two_sum(hx, lx, hx, lx);
+            two_sum(xv.y, sh[a][b].y, hy, ly);
+            ly += se[a][b].y;
+            two_sum(hy, ly, hy, ly);
             Gh[e] = make_float2(hx, hy);
             Gl[e] = make_float2(lx, ly);
         }

@@ -39,11 +39,13 @@ struct MixedSmem {
     float2 Gh[MP * MP];    // g (hi) / Gv (hi)
     float2 Gl[MP * MP];    // g (lo) / Gv (lo)
     float2 H0f[MP * MP];   // complex64 copy of H0 for forming X
+    float2 S[MP * MP];     // further Neumann terms of the refinement
     GJShared<MP> gj;
     double eps[MP];        // E - onsite for the current slice
     float2 vh[2][MP];      // diagonal of V (per parity), hi
     float2 vl[2][MP];      // lo
     double red[NT / 32];
+    unsigned redu[NT / 32];
     int inst;
     int cur_sys;
 };
@@ -129,6 +131,7 @@ knit_sweep_mixed_kernel(InstDev in)
             store_inverse<MP>(x, M, sm.gj, sm.X);
 
             // ---- residual R = I - D X + Gv X in double-float
+            float rloc = 0.f;
             {
                 float2 ah[RT][RT], al[RT][RT];
 #pragma unroll
@@ -204,10 +207,17 @@ knit_sweep_mixed_kernel(InstDev in)
                             r = make_float2(sx + ex, ah[a][b].y + al[a][b].y);
                         }
                         sm.R[i * MP + j] = r;
+                        rloc = fmaxf(rloc, fmaxf(fabsf(r.x), fabsf(r.y)));
                     }
             }
-            __syncthreads();
-            refine<MP>(sm.X, sm.R, sm.Gh, sm.Gl, M);
+            const float rmax = block_max_nonneg<NT>(rloc, sm.redu);
+            const int nx = neumann_terms(rmax, M);
+            float2 *const S = nx ? sm.S : sm.R;
+            neumann_inplace<MP, MP, 16, 16>(sm.R, S, M, nx);
+            if (rmax > EXACT_RMAX)
+                refine_exact<MP>(sm.X, S, sm.Gh, sm.Gl, M);
+            else
+                refine<MP>(sm.X, S, sm.Gh, sm.Gl, M);
             __syncthreads();
         }
 

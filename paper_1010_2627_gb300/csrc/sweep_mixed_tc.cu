@@ -38,6 +38,8 @@ using namespace mixed;
 namespace {
 
 constexpr int MPT = 64;               // padded width handled here
+constexpr int NTT = 512, TYT = 16, TXT = 32;   // 16 x 32 thread grid
+constexpr int RA = MPT / TYT, RB = MPT / TXT;
 constexpr int NDA = 7;                // digits of Gv
 constexpr int NDB = 3;                // digits of X
 constexpr int NPROD = 18;             // digit products with q <= 2, p + q <= 6
@@ -46,6 +48,7 @@ constexpr int A_TILE = 128 * 16 * 2;  // bytes of one 128 x 16 bf16 tile
 constexpr int B_TILE = 64 * 16 * 2;   // bytes of one 64 x 16 bf16 tile
 constexpr int RS = MPT + 1;           // padded row stride of R
 constexpr int GS = MPT + 1;           // padded row stride of the Gv X' buffer
+constexpr int GJ_NB = 8;              // Gauss-Jordan panel width
 constexpr int MAX_NNZ = 256;          // sparse H0 rows cached in shared memory up to this
 constexpr uint32_t TMEM_COLS = 512;   // 5 accumulators x 64 columns, rounded up
 constexpr long WAIT_LIMIT = 1L << 24; // bounded mbarrier polling
@@ -58,6 +61,10 @@ struct TcSmem {
     union {
         unsigned char adig[2 * NDA * A_TILE];    // A digits of two K-chunks
         float2 R[MPT * RS];                      // residual (after the products)
+        struct {
+            float2 U[GJ_NB * MPT];
+            float2 V[GJ_NB * MPT];
+        } pv;                                    // Gauss-Jordan panel updates
     } u;
     union {
         struct {
@@ -67,18 +74,20 @@ struct TcSmem {
         } s;
         float2 gvx[2 * MPT * GS];                // Gv X' as (hi, lo) per row of [Re; Im]
     } w;
+    static_assert(MPT * RS * sizeof(float2) <= sizeof(w.s.bdig), "series buffer");
     GJShared<MPT> gj;
     double eps[MPT];
     float2 vh[2][MPT];
     float2 vl[2][MPT];
     int rexp[MPT];
     int cexp[MPT];
-    float cmax[4][MPT];
+    float cmax[NTT / MPT][MPT];
     int h0rp[MPT + 1];
     int h0c[MAX_NNZ];
     float2 h0h[MAX_NNZ];
     float2 h0l[MAX_NNZ];
-    double red[NT / 32];
+    double red[NTT / 32];
+    unsigned redu[NTT / 32];
     unsigned long long mbar;
     uint32_t tmem;
     int inst;
@@ -168,15 +177,14 @@ __global__ void fill_status(int *st, int n, int v)
 
 }  // namespace
 
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NTT, 1)
 knit_sweep_mixed_tc_kernel(InstDev in)
 {
-    constexpr int RT = MPT / 16;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
     float2 *const Gh = sm.w.s.Gh;
     float2 *const Gl = sm.w.s.Gl;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int tid = threadIdx.x, ty = tid / TXT, tx = tid % TXT;
     const int warp = tid >> 5, lane = tid & 31;
     // D f32, A and B bf16, both K-major, N = 64, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
@@ -216,7 +224,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
         if (reload) {
             // per-system constants: diagonal of V as double-float, sparse H0 rows
             for (int q = 0; q < 2; ++q)
-                for (int i = tid; i < MPT; i += NT) {
+                for (int i = tid; i < MPT; i += NTT) {
                     double2 v = make_double2(0.0, 0.0);
                     if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
                     float hx, lx, hy, ly;
@@ -226,9 +234,9 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                     sm.vl[q][i] = make_float2(lx, ly);
                 }
             const int nnz = s.h0_rowptr[M];
-            for (int i = tid; i <= MPT; i += NT) sm.h0rp[i] = s.h0_rowptr[min(i, M)];
+            for (int i = tid; i <= MPT; i += NTT) sm.h0rp[i] = s.h0_rowptr[min(i, M)];
             if (nnz <= MAX_NNZ)
-                for (int c = tid; c < nnz; c += NT) {
+                for (int c = tid; c < nnz; c += NTT) {
                     const double2 h = s.h0_val[c];
                     float a, b, cc, d;
                     to_df(h.x, a, b);
@@ -253,13 +261,13 @@ knit_sweep_mixed_tc_kernel(InstDev in)
         int st = ip.st;
 
         for (int n = 0; n < L && st == ST_OK; ++n) {
-            slice_diag<MPT>(sm.eps, s, ms, W, E, n);
-            form_gv<MPT>(Gh, Gl, sm.vh, sm.vl, M, n, L, SL, SR);
+            slice_diag<MPT, NTT>(sm.eps, s, ms, W, E, n);
+            form_gv<MPT, NTT>(Gh, Gl, sm.vh, sm.vl, M, n, L, SL, SR);
             __syncthreads();
 
-            // row scales of Gv: warp w takes rows 8w..8w+7, lanes run along the row
-            for (int r = 0; r < 8; ++r) {
-                const int i = 8 * warp + r;
+            // row scales of Gv: warp w takes rows 4w..4w+3, lanes run along the row
+            for (int r = 0; r < MPT / (NTT / 32); ++r) {
+                const int i = (MPT / (NTT / 32)) * warp + r;
                 const float2 g0 = Gh[i * MPT + lane], g1 = Gh[i * MPT + lane + 32];
                 float mx = fmaxf(fmaxf(fabsf(g0.x), fabsf(g0.y)), fmaxf(fabsf(g1.x), fabsf(g1.y)));
 #pragma unroll
@@ -269,7 +277,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
 
             // X = fl32(D - Gv_hi): staged in shared memory (diagonal, then the
             // sparse H0 rows, one row per thread), then loaded into registers
-            for (int e = tid; e < MPT * MPT; e += NT) {
+            for (int e = tid; e < MPT * MPT; e += NTT) {
                 const int i = e >> 6, j = e & 63;
                 float2 v;
                 if (i < M && j < M) {
@@ -282,7 +290,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                 sm.X[e] = v;
             }
             __syncthreads();
-            for (int i = tid; i < M; i += NT)
+            for (int i = tid; i < M; i += NTT)
                 for (int c = sm.h0rp[i]; c < sm.h0rp[i + 1]; ++c) {
                     int col;
                     float2 h;
@@ -299,36 +307,40 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                     v.y -= h.y;
                 }
             __syncthreads();
-            float2 x[RT][RT];
-#pragma unroll
-            for (int a = 0; a < RT; ++a)
-#pragma unroll
-                for (int b = 0; b < RT; ++b) x[a][b] = sm.X[(ty + 16 * a) * MPT + tx + 16 * b];
-            st = gj_regs<MPT>(x, M, sm.gj);
+            st = gj_blocked<MPT, TYT, TXT, GJ_NB>(sm.X, M, sm.u.pv.U, sm.u.pv.V, sm.gj);
             if (st != ST_OK) break;
-            store_inverse<MPT>(x, M, sm.gj, sm.X);
+            {
+                float2 x[RA][RB];
+#pragma unroll
+                for (int a = 0; a < RA; ++a)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) x[a][b] = sm.X[(ty + TYT * a) * MPT + tx + TXT * b];
+                store_inverse<MPT, TYT, TXT>(x, M, sm.gj, sm.X);
+            }
 
-            // column scales of X: thread t scans rows 16 (t / 64) .. of column t % 64
+            // column scales of X: thread t scans rows 8 (t / 64) .. of column t % 64
             {
                 const int nn = tid & 63, part = tid >> 6;
                 float mx = 0.f;
 #pragma unroll 4
-                for (int k = part * 16; k < part * 16 + 16; ++k) {
+                for (int k = part * 8; k < part * 8 + 8; ++k) {
                     const float2 v = sm.X[k * MPT + nn];
                     mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
                 }
                 sm.cmax[part][nn] = mx;
             }
             __syncthreads();
-            if (tid < MPT)
-                sm.cexp[tid] = scale_exp(fmaxf(fmaxf(sm.cmax[0][tid], sm.cmax[1][tid]),
-                                               fmaxf(sm.cmax[2][tid], sm.cmax[3][tid])));
+            if (tid < MPT) {
+                float mx = 0.f;
+                for (int part = 0; part < NTT / MPT; ++part) mx = fmaxf(mx, sm.cmax[part][tid]);
+                sm.cexp[tid] = scale_exp(mx);
+            }
             __syncthreads();
 
             // B digits (three per value) and X' = X rounded to them; work item
             // e takes X[k][nn] and X[k+1][nn] (k even), lanes along nn, so each
             // digit pair is one 32-bit store into B^T[nn][k..k+1]
-            for (int e = tid; e < MPT * MPT / 2; e += NT) {
+            for (int e = tid; e < MPT * MPT / 2; e += NTT) {
                 const int k = (e >> 6) * 2, nn = e & 63;
                 const int ce = sm.cexp[nn];
                 const float dn = pow2f(-ce), up = pow2f(ce - 8);
@@ -377,7 +389,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                 // A digits of Gv columns 16g..16g+15: chunk slot 0 holds K-chunk g
                 // (rows < 64: Gr, rows >= 64: Gi), slot 1 K-chunk g+4 (-Gi, Gr);
                 // work item e takes row i, columns kk and kk+1 (one 32-bit store)
-                for (int e = tid; e < MPT * 8; e += NT) {
+                for (int e = tid; e < MPT * 8; e += NTT) {
                     const int i = e >> 3, kk = (e & 7) * 2, k = 16 * g + kk;
                     const float dn = pow2f(-sm.rexp[i]);
                     const float2 gh0 = Gh[i * MPT + k], gl0 = Gl[i * MPT + k];
@@ -441,12 +453,12 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             tc_fence_after();
 
             // Gv X' = sigma_i tau_n 2^-16 (D0 + D1 + D2 + D3 + D4+), as (hi, lo):
-            // lane m of warp w holds row 32 (w % 4) + lane, columns 32 (w / 4) ..
+            // lane m of warp w holds row 32 (w % 4) + lane, columns 16 (w / 4) ..
             {
-                const int m = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);
+                const int m = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
                 const int re = sm.rexp[m & 63];
                 const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0;
-                for (int j8 = 0; j8 < 32; j8 += 8) {
+                for (int j8 = 0; j8 < 16; j8 += 8) {
                     uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
                     tmem_ld8(tb + j8, v0);
                     tmem_ld8(tb + 64 + j8, v1);
@@ -475,14 +487,15 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             __syncthreads();
 
             // R = I - D X' + Gv X' with error-free products, one element per (ty, tx) slot
+            float rloc = 0.f;
 #pragma unroll
-            for (int a = 0; a < RT; ++a) {
-                const int i = ty + 16 * a;
+            for (int a = 0; a < RA; ++a) {
+                const int i = ty + TYT * a;
                 float dh = 0.f, dl = 0.f;
                 if (i < M) to_df(sm.eps[i], dh, dl);
 #pragma unroll
-                for (int b = 0; b < RT; ++b) {
-                    const int j = tx + 16 * b;
+                for (int b = 0; b < RB; ++b) {
+                    const int j = tx + TXT * b;
                     float2 r = make_float2(0.f, 0.f);
                     if (i < M && j < M) {
                         const float2 pr = sm.w.gvx[i * GS + j], pi = sm.w.gvx[(i + 64) * GS + j];
@@ -518,16 +531,25 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                         r = make_float2(sr + er, si + ei);
                     }
                     sm.u.R[i * RS + j] = r;
+                    rloc = fmaxf(rloc, fmaxf(fabsf(r.x), fabsf(r.y)));
                 }
             }
-            __syncthreads();
-            refine<MPT, RS>(sm.X, sm.u.R, Gh, Gl, M);
+            // further Neumann terms where A_n is ill-conditioned, in the B-digit
+            // buffer (free once the products are read back)
+            const float rmax = block_max_nonneg<NTT>(rloc, sm.redu);
+            const int nx = neumann_terms(rmax, M);
+            float2 *const S = nx ? reinterpret_cast<float2 *>(sm.w.s.bdig) : sm.u.R;
+            neumann_inplace<MPT, RS, TYT, TXT>(sm.u.R, S, M, nx);
+            if (rmax > EXACT_RMAX)
+                refine_exact<MPT, RS, TYT, TXT>(sm.X, S, Gh, Gl, M);
+            else
+                refine<MPT, RS, TYT, TXT>(sm.X, S, Gh, Gl, M);
             __syncthreads();
         }
 
         double T = 0.0;
         if (st == ST_OK) {
-            T = ward_T<MPT>(Gh, Gl, reinterpret_cast<double2 *>(sm.X), SR, M, sm.red);
+            T = ward_T<MPT, NTT>(Gh, Gl, reinterpret_cast<double2 *>(sm.X), SR, M, sm.red);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {
@@ -555,7 +577,7 @@ extern "C" cudaError_t knit_launch_mixed_tc(const InstDev *in, int grid, cudaStr
     cudaError_t e = cudaFuncSetAttribute(knit_sweep_mixed_tc_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
     if (e != cudaSuccess) return e;
-    knit_sweep_mixed_tc_kernel<<<grid, NT, smb, stream>>>(*in);
+    knit_sweep_mixed_tc_kernel<<<grid, NTT, smb, stream>>>(*in);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ struct WideSmem {
     float2 vbh[2][MP * VBMAX];   // diagonal blocks of V per parity: [i][kk] = V[i][bi + kk]
     float2 vbl[2][MP * VBMAX];
     double red[NTW / 32];
+    unsigned redu[NTW / 32];
     int inst;
     int cur_sys;
 };
@@ -42,6 +43,7 @@ struct WideWork {   // per-CTA device workspace
     float2 Gh[MP * MP];   // state g_{n-1} (hi, lo)
     float2 Gl[MP * MP];
     float2 R[MP * MP];    // residual
+    float2 S[2][MP * MP]; // further Neumann terms (two buffers in turn)
     union {
         struct {
             float2 Vh[MP * MP];   // Gv (hi, lo) during the sweep
@@ -140,9 +142,10 @@ __device__ void form_gv_block(const float2 *Gh, const float2 *Gl, float2 *Oh, fl
 
 // residual rows ty + 16 (A0 + a), a < NA, in double-float; written to R
 template <int MP, int A0, int NA>
-__device__ __forceinline__ void residual_pass(const SysDev &s, const float2 *X, const float2 *Gh,
-                                              const float2 *Gl, const double *eps, float2 *R)
+__device__ __forceinline__ float residual_pass(const SysDev &s, const float2 *X, const float2 *Gh,
+                                               const float2 *Gl, const double *eps, float2 *R)
 {
+    float rloc = 0.f;   // largest |Re|, |Im| written, returned
     constexpr int RB = MP / TXW;
     const int tid = threadIdx.x, ty = tid / TXW, tx = tid % TXW;
     const int M = s.M;
@@ -217,8 +220,21 @@ __device__ __forceinline__ void residual_pass(const SysDev &s, const float2 *X, 
                 r = make_float2(sx + ex, ah[a][b].y + al[a][b].y);
             }
             R[i * MP + j] = r;
+            rloc = fmaxf(rloc, fmaxf(fabsf(r.x), fabsf(r.y)));
         }
     }
+    return rloc;
+}
+
+// rows RA0 .. RA0+NRA-1 of the thread's tile of acc into S (row stride MP)
+template <int MP, int RA0, int NRA>
+__device__ __forceinline__ void store_tile(const float2 (&acc)[NRA][MP / TXW], float2 *S)
+{
+    const int tid = threadIdx.x, ty = tid / TXW, tx = tid % TXW;
+#pragma unroll
+    for (int a = 0; a < NRA; ++a)
+#pragma unroll
+        for (int b = 0; b < MP / TXW; ++b) S[(ty + TYW * (RA0 + a)) * MP + tx + TXW * b] = acc[a][b];
 }
 
 }  // namespace
@@ -304,11 +320,35 @@ knit_sweep_mixed_wide_kernel(InstDev in, WideWork<MP> *work)
             st = gj_regs<MP, TYW, TXW>(x, M, sm.gj);
             if (st != ST_OK) break;
             store_inverse<MP, TYW, TXW>(x, M, sm.gj, sm.X);
-            residual_pass<MP, 0, 4>(s, sm.X, wk.u.v.Vh, wk.u.v.Vl, sm.eps, wk.R);
-            residual_pass<MP, 4, RA - 4>(s, sm.X, wk.u.v.Vh, wk.u.v.Vl, sm.eps, wk.R);
-            __syncthreads();
-            refine<MP, MP, TYW, TXW, 0, 4>(sm.X, wk.R, wk.Gh, wk.Gl, M);
-            refine<MP, MP, TYW, TXW, 4, RA - 4>(sm.X, wk.R, wk.Gh, wk.Gl, M);
+            float rloc = residual_pass<MP, 0, 4>(s, sm.X, wk.u.v.Vh, wk.u.v.Vl, sm.eps, wk.R);
+            rloc = fmaxf(rloc, residual_pass<MP, 4, RA - 4>(s, sm.X, wk.u.v.Vh, wk.u.v.Vl, sm.eps,
+                                                            wk.R));
+            // further Neumann terms where A_n is ill-conditioned (two buffers in turn)
+            const float rmax = block_max_nonneg<NTW>(rloc, sm.redu);
+            const int nx = neumann_terms(rmax, M);
+            const float2 *S = wk.R;
+            for (int t = 0; t < nx; ++t) {
+                float2 *const So = wk.S[t & 1];
+                {
+                    float2 acc[4][RB];
+                    neumann_tile<MP, MP, TYW, TXW, 0, 4>(wk.R, S, acc, M);
+                    store_tile<MP, 0, 4>(acc, So);
+                }
+                {
+                    float2 acc[RA - 4][RB];
+                    neumann_tile<MP, MP, TYW, TXW, 4, RA - 4>(wk.R, S, acc, M);
+                    store_tile<MP, 4, RA - 4>(acc, So);
+                }
+                __syncthreads();
+                S = So;
+            }
+            if (rmax > EXACT_RMAX) {
+                refine_exact<MP, MP, TYW, TXW, 0, 4>(sm.X, S, wk.Gh, wk.Gl, M);
+                refine_exact<MP, MP, TYW, TXW, 4, RA - 4>(sm.X, S, wk.Gh, wk.Gl, M);
+            } else {
+                refine<MP, MP, TYW, TXW, 0, 4>(sm.X, S, wk.Gh, wk.Gl, M);
+                refine<MP, MP, TYW, TXW, 4, RA - 4>(sm.X, S, wk.Gh, wk.Gl, M);
+            }
             __syncthreads();
         }
 

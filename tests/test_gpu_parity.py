@@ -264,11 +264,25 @@ def test_full_bench_workload_sampled(knit):
     # unitarity identity (a difference of two O(N_ch) traces), so its error
     # is absolute, not relative to T
     assert np.isfinite(T).all() and (T >= -TOL_MIXED).all()
+    nch = np.array([max(1, nch_square(64, x)) for x in E])
     rng = np.random.default_rng(2024)
     picks = [(int(e), int(s)) for e, s in zip(rng.integers(0, 1024, 6), rng.integers(0, 8, 6))]
+    # near the band edges A_n is often ill-conditioned (kappa ~ 1e5) and a
+    # single refinement step is not enough there: random band-edge picks and
+    # five instances where it was seen to fail
+    picks += [(int(e), int(s)) for e, s in zip(rng.integers(0, 64, 3), rng.integers(0, 8, 3))]
+    picks += [(int(e), int(s)) for e, s in zip(rng.integers(960, 1024, 3), rng.integers(0, 8, 3))]
+    picks += [(64, 2), (1004, 1), (20, 2), (1012, 3), (32, 3)]
     for e, s in picks:
         To = oracle_T(ss, E[e], s, 2.0, method="rgf")
-        assert abs(T[e, s] - To) / max(1, nch_square(64, E[e])) <= TOL_MIXED, (e, s)
+        assert abs(T[e, s] - To) / nch[e] <= TOL_MIXED, (e, s, T[e, s], To)
+    # every band-edge instance against the FP64 sweep (itself held to the
+    # oracle at TOL_FP64 by the tests above)
+    edge = np.r_[0:32, 992:1024]
+    Tf, stf = sysk.transmission(E[edge], seeds, W=2.0, precision=knit.KNIT_FP64)
+    assert (stf == 0).all()
+    dT = np.abs(T[edge] - Tf) / nch[edge, None]
+    assert dT.max() <= TOL_MIXED, (dT.max(), np.unravel_index(dT.argmax(), dT.shape))
 
 
 # --------------------------------------------------------------------------
