@@ -2,28 +2,35 @@
 // residual on the tcgen05 tensor cores (padded width MP = 64, i.e. M in 33..64).
 //
 // Same recursion as sweep_mixed.cu (KNIT user guide Sec. 5.3 D, Eq. 2 by
-// block elimination; complex64 Gauss-Jordan + one refinement step, state g
-// carried as hi + lo, T from G_LL by the unitarity identity).  What differs is
-// the residual R = I - A X, whose dense part Gv X must be exact to ~2^-48:
+// block elimination; complex64 inversion + refinement, state g carried as
+// hi + lo, T from G_LL by the unitarity identity).  Per slice n:
 //
-//  * X is first rounded at a per-column power-of-two scale tau_n to 24 bits,
+//  * Gv' = V g V^dagger (+ Sigma terms) + H0 - D_n in double-float, so that
+//    A_n = -Gv' and the residual of an approximate inverse X' is
+//    R = I - A_n X' = I + Gv' X';
+//  * X = complex64 inverse of fl32(A_n) by blocked Gauss-Jordan with
+//    implicit partial pivoting (gj_blocked, 512 threads);
+//  * X is rounded at a per-column power-of-two scale tau_n to 24 bits,
 //    X' = tau_n 2^-8 (d0 + d1 2^-8 + d2 2^-16), |d| <= 256 integers (three
-//    bf16 "digits", exact); the refinement then uses X' consistently, so X'
-//    only needs to be a good approximate inverse, not exact;
-//  * Gv (double-float) is cut at a per-row scale sigma_i into six digits
-//    (48 bits), Gv ~= sigma_i 2^-8 sum_p e_p 2^-8p;
+//    bf16 "digits", exact, and X' itself exact in fp32); the refinement uses
+//    X' consistently, so X' only needs to be a good approximate inverse;
+//  * Gv' is cut at a per-row scale sigma_i into seven digits (56 bits),
+//    Gv' ~= sigma_i 2^-8 sum_p e_p 2^-8p;
 //  * the complex product is the real product of [[Gr, -Gi], [Gi, Gr]]
-//    (128 x 128) with [Xr; Xi] (128 x 64), run as 15 digit products
-//    (p + q <= 5, q <= 2) per K-chunk of 16 on tcgen05.mma kind::f16 (bf16 in,
+//    (128 x 128) with [Xr; Xi] (128 x 64), run as 18 digit products
+//    (p + q <= 6, q <= 2) per K-chunk of 16 on tcgen05.mma kind::f16 (bf16 in,
 //    f32 accumulate in tensor memory).  Digits are stored pre-scaled by
 //    2^-8p / 2^-8q, so every product of one anti-diagonal d = p + q is an
-//    integer multiple of 2^-8d below 2^24 in magnitude: the diagonals d = 0,
-//    1, 2 accumulate exactly in three accumulators, d >= 3 share a fourth;
-//  * the four accumulators are combined in double-float and scaled by
-//    sigma_i tau_n 2^-16; the sparse D X' part and the identity are added
-//    with error-free products on CUDA cores.
-// This is the Ozaki splitting (Ozaki, Ogita, Oishi & Rump 2012) with bf16
-// slices, specialised to the refinement of an approximate inverse.
+//    integer multiple of 2^-8d below 2^24 in magnitude: the diagonals
+//    d = 0 .. 3 accumulate exactly in four accumulators, d >= 4 share a fifth;
+//  * the five accumulators are summed in double-float, scaled by
+//    sigma_i tau_n 2^-16, the identity added, and R rounded once to fp32;
+//  * g = X' (I + R + R^2 + ...) with as many terms as max|R_ij| asks for,
+//    the product X' S accumulated error-free where max|R_ij| is large
+//    (mixed_common.cuh: neumann_terms, refine_exact).
+// The digit products are the Ozaki splitting (Ozaki, Ogita, Oishi & Rump
+// 2012) with bf16 slices, specialised to the residual of an approximate
+// inverse.
 //
 // Shared-memory operand tiles use the no-swizzle K-major layout: 8-row x
 // 16-byte core matrices, K-adjacent core matrices 128 B apart (descriptor
@@ -47,7 +54,6 @@ constexpr int NACC = 5;               // accumulators: d = 0, 1, 2, 3 exact, d >
 constexpr int A_TILE = 128 * 16 * 2;  // bytes of one 128 x 16 bf16 tile
 constexpr int B_TILE = 64 * 16 * 2;   // bytes of one 64 x 16 bf16 tile
 constexpr int RS = MPT + 1;           // padded row stride of R
-constexpr int GS = MPT + 1;           // padded row stride of the Gv X' buffer
 constexpr int GJ_NB = 8;              // Gauss-Jordan panel width
 constexpr int MAX_NNZ = 256;          // sparse H0 rows cached in shared memory up to this
 constexpr uint32_t TMEM_COLS = 512;   // 5 accumulators x 64 columns, rounded up
@@ -72,7 +78,6 @@ struct TcSmem {
             float2 Gh[MPT * MPT];                  // g (hi) / Gv (hi)
             float2 Gl[MPT * MPT];                  // g (lo) / Gv (lo)
         } s;
-        float2 gvx[2 * MPT * GS];                // Gv X' as (hi, lo) per row of [Re; Im]
     } w;
     static_assert(MPT * RS * sizeof(float2) <= sizeof(w.s.bdig), "series buffer");
     GJShared<MPT> gj;
@@ -107,11 +112,6 @@ KNIT_DEV uint64_t smem_desc(uint32_t addr)
     d |= (uint64_t)(256 >> 4) << 32;     // 8-row groups
     d |= (uint64_t)1 << 46;              // descriptor version
     return d;
-}
-
-KNIT_DEV void put_bf16(unsigned char *tile, int r, int c, float v)
-{
-    *reinterpret_cast<__nv_bfloat16 *>(tile + tile_off(r, c)) = __float2bfloat16_rn(v);
 }
 
 // two K-adjacent values (c even) in one 32-bit store
@@ -264,6 +264,30 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             slice_diag<MPT, NTT>(sm.eps, s, ms, W, E, n);
             form_gv<MPT, NTT>(Gh, Gl, sm.vh, sm.vl, M, n, L, SL, SR);
             __syncthreads();
+            // Gv' = Gv + H0 - D in double-float, one row per thread, so that
+            // A_n = -Gv' and the residual is R = I + Gv' X'
+            for (int i = tid; i < M; i += NTT) {
+                float dh, dl;
+                to_df(sm.eps[i], dh, dl);
+                cdf_add(Gh[i * MPT + i], Gl[i * MPT + i], make_float2(-dh, 0.f),
+                        make_float2(-dl, 0.f));
+                for (int c = sm.h0rp[i]; c < sm.h0rp[i + 1]; ++c) {
+                    int col;
+                    float2 hh, hl;
+                    if (h0_cached) {
+                        col = sm.h0c[c];
+                        hh = sm.h0h[c];
+                        hl = sm.h0l[c];
+                    } else {
+                        col = s.h0_col[c];
+                        const double2 hd = s.h0_val[c];
+                        to_df(hd.x, hh.x, hl.x);
+                        to_df(hd.y, hh.y, hl.y);
+                    }
+                    cdf_add(Gh[i * MPT + col], Gl[i * MPT + col], hh, hl);
+                }
+            }
+            __syncthreads();
 
             // row scales of Gv: warp w takes rows 4w..4w+3, lanes run along the row
             for (int r = 0; r < MPT / (NTT / 32); ++r) {
@@ -275,37 +299,13 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                 if (lane == 0) sm.rexp[i] = scale_exp(mx);
             }
 
-            // X = fl32(D - Gv_hi): staged in shared memory (diagonal, then the
-            // sparse H0 rows, one row per thread), then loaded into registers
+            // X = fl32(A_n) = -Gv'_hi (identity in the padding)
             for (int e = tid; e < MPT * MPT; e += NTT) {
                 const int i = e >> 6, j = e & 63;
-                float2 v;
-                if (i < M && j < M) {
-                    const float2 g = Gh[e];
-                    v = make_float2(-g.x, -g.y);
-                    if (i == j) v.x += (float)sm.eps[i];
-                } else {
-                    v = make_float2(i == j ? 1.f : 0.f, 0.f);
-                }
-                sm.X[e] = v;
+                const float2 g = Gh[e];
+                sm.X[e] = (i < M && j < M) ? make_float2(-g.x, -g.y)
+                                           : make_float2(i == j ? 1.f : 0.f, 0.f);
             }
-            __syncthreads();
-            for (int i = tid; i < M; i += NTT)
-                for (int c = sm.h0rp[i]; c < sm.h0rp[i + 1]; ++c) {
-                    int col;
-                    float2 h;
-                    if (h0_cached) {
-                        col = sm.h0c[c];
-                        h = sm.h0h[c];
-                    } else {
-                        col = s.h0_col[c];
-                        const double2 hd = s.h0_val[c];
-                        h = make_float2((float)hd.x, (float)hd.y);
-                    }
-                    float2 &v = sm.X[i * MPT + col];
-                    v.x -= h.x;
-                    v.y -= h.y;
-                }
             __syncthreads();
             st = gj_blocked<MPT, TYT, TXT, GJ_NB>(sm.X, M, sm.u.pv.U, sm.u.pv.V, sm.gj);
             if (st != ST_OK) break;
@@ -452,11 +452,16 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             }
             tc_fence_after();
 
-            // Gv X' = sigma_i tau_n 2^-16 (D0 + D1 + D2 + D3 + D4+), as (hi, lo):
-            // lane m of warp w holds row 32 (w % 4) + lane, columns 16 (w / 4) ..
+            // R = I + Gv' X' = I + sigma_i tau_n 2^-16 (D0 + D1 + D2 + D3 + D4+):
+            // lane m of warp w holds row 32 (w % 4) + lane of [Re; Im],
+            // columns 16 (w / 4) ..; the five accumulators are summed as
+            // double-float before the single rounding to the stored R
+            float rloc = 0.f;
             {
                 const int m = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
-                const int re = sm.rexp[m & 63];
+                const int i = m & 63, part = m >> 6;
+                const int re = sm.rexp[i];
+                float *const Rf = reinterpret_cast<float *>(sm.u.R);
                 const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0;
                 for (int j8 = 0; j8 < 16; j8 += 8) {
                     uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
@@ -477,63 +482,22 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                         ls += te;
                         two_sum(hs, __uint_as_float(v4[jx]), t, te);
                         ls += te;
-                        two_sum(t, ls, hs, ls);
                         const float sc = pow2f(re + sm.cexp[nn] - 16);
-                        sm.w.gvx[m * GS + nn] = make_float2(hs * sc, ls * sc);
+                        hs = t * sc;
+                        ls *= sc;
+                        if (part == 0 && i == nn) {
+                            two_sum(hs, 1.0f, t, te);
+                            hs = t;
+                            ls += te;
+                        }
+                        const float r = (i < M && nn < M) ? hs + ls : 0.f;
+                        Rf[2 * (i * RS + nn) + part] = r;
+                        rloc = fmaxf(rloc, fabsf(r));
                     }
                 }
             }
             tc_fence_before();
-            __syncthreads();
 
-            // R = I - D X' + Gv X' with error-free products, one element per (ty, tx) slot
-            float rloc = 0.f;
-#pragma unroll
-            for (int a = 0; a < RA; ++a) {
-                const int i = ty + TYT * a;
-                float dh = 0.f, dl = 0.f;
-                if (i < M) to_df(sm.eps[i], dh, dl);
-#pragma unroll
-                for (int b = 0; b < RB; ++b) {
-                    const int j = tx + TXT * b;
-                    float2 r = make_float2(0.f, 0.f);
-                    if (i < M && j < M) {
-                        const float2 pr = sm.w.gvx[i * GS + j], pi = sm.w.gvx[(i + 64) * GS + j];
-                        float sr = pr.x, er = pr.y, si = pi.x, ei = pi.y;
-                        const float2 xij = sm.X[i * MPT + j];
-                        dot2_acc(-dh, -dl, xij.x, sr, er);
-                        dot2_acc(-dh, -dl, xij.y, si, ei);
-                        for (int c = sm.h0rp[i]; c < sm.h0rp[i + 1]; ++c) {
-                            int col;
-                            float2 hh, hl;
-                            if (h0_cached) {
-                                col = sm.h0c[c];
-                                hh = sm.h0h[c];
-                                hl = sm.h0l[c];
-                            } else {
-                                col = s.h0_col[c];
-                                const double2 hd = s.h0_val[c];
-                                to_df(hd.x, hh.x, hl.x);
-                                to_df(hd.y, hh.y, hl.y);
-                            }
-                            const float2 xc = sm.X[col * MPT + j];
-                            dot2_acc(hh.x, hl.x, xc.x, sr, er);
-                            dot2_acc(-hh.y, -hl.y, xc.y, sr, er);
-                            dot2_acc(hh.x, hl.x, xc.y, si, ei);
-                            dot2_acc(hh.y, hl.y, xc.x, si, ei);
-                        }
-                        if (i == j) {
-                            float t, te;
-                            two_sum(sr, 1.0f, t, te);
-                            sr = t;
-                            er += te;
-                        }
-                        r = make_float2(sr + er, si + ei);
-                    }
-                    sm.u.R[i * RS + j] = r;
-                    rloc = fmaxf(rloc, fmaxf(fabsf(r.x), fabsf(r.y)));
-                }
-            }
             // further Neumann terms where A_n is ill-conditioned, in the B-digit
             // buffer (free once the products are read back)
             const float rmax = block_max_nonneg<NTT>(rloc, sm.redu);
