@@ -61,6 +61,7 @@ struct GJShared {
     int used[MP];
     int perm[MP];
     int pos[MP];
+    float2 rinv[16];   // gj_blocked: 1 / pivot of the current panel's steps
     int flag;
 };
 
@@ -218,28 +219,38 @@ KNIT_DEV float2 crcp_pow2f(float2 a)
 // column k is the exact rank-1 update x -= u v^T with u = x[:, k] - e_p and
 // v = (x[p, :] + e_k) / x[p][k]: it zeroes the pivot column and row and
 // writes their new values in one stroke.  Steps are grouped in panels of NB
-// columns.  Warp 0 runs a panel's steps alone, keeping the panel columns
-// current in registers and forming each pivot row from X minus the panel's
-// pending updates; U (NB x MP) and V (NB x MP) collect u and v.  Then the
-// whole block applies X -= U^T V.  So the block meets at two barriers per
-// panel instead of two per column, and the pivot search is one warp
-// reduction of (|Re|+|Im| with its low mantissa bits cleared | inverted row)
-// keys: the largest magnitude to 2^-17, lowest row on near-ties.
+// columns.  Warp 0 runs a panel's steps alone on the panel columns, kept
+// current in registers: the pivot search, 1 / pivot and the update of the
+// panel need nothing outside them.  Then the same warp forms the panel's v
+// vectors for every column by forward substitution,
+// v_k = (X[p_k, :] - sum_{c<k} u_c[p_k] v_c + e_k) / x[p_k][k], and the
+// whole block applies X -= U V (U: MP x gj_ust(NB), row i holds u_c[i];
+// V: NB x MP).  So the block meets at two barriers per panel, and a step's
+// latency is one warp reduction of (|Re|+|Im| with its low mantissa bits
+// cleared | inverted row) keys -- the largest magnitude to 2^-17, lowest
+// row on near-ties -- plus broadcasts of the pivot row's panel entries.
+//
+// row stride of gj_blocked's U: rows of NB complex values padded to a
+// multiple of 16 bytes plus 16, so that two steps load as one 16-byte vector
+// and the panel warp's column stores spread over the banks
+__host__ __device__ constexpr int gj_ust(int nb) { return nb + 2; }
+
 template <int MP, int TY, int TX, int NB = 8>
 __device__ __forceinline__ int gj_blocked(float2 *X, int M, float2 *U, float2 *V, GJShared<MP> &g)
 {
     static_assert(MP % 32 == 0 && MP % NB == 0 && 32 % NB == 0 && MP <= 128, "panel layout");
+    static_assert(NB % 2 == 0, "steps are loaded in pairs");
     constexpr int RA = MP / TY, RB = MP / TX, R2 = MP / 32, IB = MP <= 64 ? 6 : 7;
+    constexpr int UST = gj_ust(NB);
     constexpr unsigned IMASK = (1u << IB) - 1u, FULL = 0xffffffffu;
     const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX, lane = tid & 31;
     bool open[R2];   // warp 0: row lane + 32t may still become a pivot row
 #pragma unroll
     for (int t = 0; t < R2; ++t) open[t] = lane + 32 * t < M;
     for (int K = 0; K < M; K += NB) {
+        const int nk = min(NB, M - K);
         if (tid < 32) {
-            const int tK = K >> 5, lK = K & 31;   // panel columns: lanes lK.., slot tK
             float2 pc[R2][NB];   // panel columns, rows lane + 32t
-            float2 vh[R2][NB];   // this lane's entries of the panel's v vectors
 #pragma unroll
             for (int t = 0; t < R2; ++t)
 #pragma unroll
@@ -247,8 +258,7 @@ __device__ __forceinline__ int gj_blocked(float2 *X, int M, float2 *U, float2 *V
             int bad = 0;
 #pragma unroll
             for (int kk = 0; kk < NB; ++kk) {
-                const int k = K + kk;
-                if (k >= M) break;
+                if (kk >= nk) break;
                 unsigned key = 0u;
 #pragma unroll
                 for (int t = 0; t < R2; ++t)
@@ -258,74 +268,94 @@ __device__ __forceinline__ int gj_blocked(float2 *X, int M, float2 *U, float2 *V
                 key = __reduce_max_sync(FULL, key);
                 if ((key & ~IMASK) == 0u) { bad = 1; break; }
                 const int p = (int)(IMASK - (key & IMASK)), pl = p & 31, pt = p >> 5;
-                float2 own = pc[0][kk];
+                // the pivot row's current panel entries, from lane p % 32
+                float2 prow[NB];
 #pragma unroll
-                for (int t = 1; t < R2; ++t)
-                    if (t == pt) own = pc[t][kk];
-                const float2 piv = make_float2(__shfl_sync(FULL, own.x, pl),
-                                               __shfl_sync(FULL, own.y, pl));
-                float2 up[NB];   // u vectors of the earlier steps at row p
+                for (int c = kk; c < NB; ++c) {
+                    float2 own = pc[0][c];
 #pragma unroll
-                for (int c = 0; c < kk; ++c) up[c] = U[c * MP + p];
-                float2 rv[R2];
-#pragma unroll
-                for (int t = 0; t < R2; ++t) {
-                    float2 r = X[p * MP + lane + 32 * t];
-#pragma unroll
-                    for (int c = 0; c < kk; ++c) r = cfmsf(up[c], vh[t][c], r);
-                    rv[t] = r;
+                    for (int t = 1; t < R2; ++t)
+                        if (t == pt) own = pc[t][c];
+                    prow[c] = make_float2(__shfl_sync(FULL, own.x, pl), __shfl_sync(FULL, own.y, pl));
                 }
-                const float2 rinv = crcp_pow2f(piv);
+                const float2 rinv = crcp_pow2f(prow[kk]);
                 float2 uu[R2];
 #pragma unroll
                 for (int t = 0; t < R2; ++t) {
-                    const int j = lane + 32 * t;
-                    float2 v = cmulf(rv[t], rinv);
-                    if (j == k) { v.x += rinv.x; v.y += rinv.y; }
-                    vh[t][kk] = v;
-                    V[kk * MP + j] = v;
+                    const int i = lane + 32 * t;
                     float2 u = pc[t][kk];
-                    if (j == p) { u.x -= 1.f; open[t] = false; }
-                    U[kk * MP + j] = u;
+                    if (i == p) { u.x -= 1.f; open[t] = false; }
+                    U[i * UST + kk] = u;
                     uu[t] = u;
                 }
-                if (lane == 0) g.perm[k] = p;
-                float2 vs = vh[0][kk];
-#pragma unroll
-                for (int t = 1; t < R2; ++t)
-                    if (t == tK) vs = vh[t][kk];
+                if (lane == 0) {
+                    g.perm[K + kk] = p;
+                    g.rinv[kk] = rinv;
+                }
 #pragma unroll
                 for (int c = kk + 1; c < NB; ++c) {
-                    const float2 vk = make_float2(__shfl_sync(FULL, vs.x, lK + c),
-                                                  __shfl_sync(FULL, vs.y, lK + c));
+                    const float2 vk = cmulf(prow[c], rinv);
 #pragma unroll
                     for (int t = 0; t < R2; ++t) pc[t][c] = cfmsf(uu[t], vk, pc[t][c]);
                 }
-                __syncwarp();
+            }
+            __syncwarp();
+            if (!bad) {
+                // v vectors of the panel for columns j = lane + 32t, one t at a
+                // time in registers; V is stored after each, so that no store
+                // sits between the loads of X and U of one substitution
+#pragma unroll
+                for (int t = 0; t < R2; ++t) {
+                    const int j = lane + 32 * t;
+                    float2 vj[NB];
+#pragma unroll
+                    for (int kk = 0; kk < NB; ++kk) {
+                        if (kk < nk) {
+                            const int p = g.perm[K + kk];
+                            float2 r = X[p * MP + j];
+#pragma unroll
+                            for (int c = 0; c < kk; ++c) r = cfmsf(U[p * UST + c], vj[c], r);
+                            if (j == K + kk) r.x += 1.f;
+                            vj[kk] = cmulf(r, g.rinv[kk]);
+                        }
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < NB; ++kk)
+                        if (kk < nk) V[kk * MP + j] = vj[kk];
+                }
             }
             if (lane == 0) g.flag = bad;
         }
         __syncthreads();
         if (g.flag) return ST_SINGULAR;
-        // X -= U^T V over the whole matrix, a register tile per thread
-        const int nk = min(NB, M - K);
+        // X -= U V over the whole matrix, a register tile per thread; U rows
+        // are read two steps per 16-byte load
         float2 acc[RA][RB];
 #pragma unroll
         for (int a = 0; a < RA; ++a)
 #pragma unroll
             for (int b = 0; b < RB; ++b) acc[a][b] = X[(ty + TY * a) * MP + tx + TX * b];
 #pragma unroll
-        for (int c = 0; c < NB; ++c) {
+        for (int c = 0; c < NB; c += 2) {
             if (c < nk) {
-                float2 ua[RA], vb[RB];
+                float4 ua[RA];
+                float2 vb0[RB], vb1[RB];
 #pragma unroll
-                for (int a = 0; a < RA; ++a) ua[a] = U[c * MP + ty + TY * a];
+                for (int a = 0; a < RA; ++a)
+                    ua[a] = *reinterpret_cast<const float4 *>(U + (ty + TY * a) * UST + c);
 #pragma unroll
-                for (int b = 0; b < RB; ++b) vb[b] = V[c * MP + tx + TX * b];
+                for (int b = 0; b < RB; ++b) {
+                    vb0[b] = V[c * MP + tx + TX * b];
+                    vb1[b] = V[(c + 1) * MP + tx + TX * b];
+                }
+                const bool two = c + 1 < nk;
 #pragma unroll
                 for (int a = 0; a < RA; ++a)
 #pragma unroll
-                    for (int b = 0; b < RB; ++b) acc[a][b] = cfmsf(ua[a], vb[b], acc[a][b]);
+                    for (int b = 0; b < RB; ++b) {
+                        acc[a][b] = cfmsf(make_float2(ua[a].x, ua[a].y), vb0[b], acc[a][b]);
+                        if (two) acc[a][b] = cfmsf(make_float2(ua[a].z, ua[a].w), vb1[b], acc[a][b]);
+                    }
             }
         }
 #pragma unroll
@@ -335,6 +365,267 @@ __device__ __forceinline__ int gj_blocked(float2 *X, int M, float2 *U, float2 *V
         __syncthreads();
     }
     return ST_OK;
+}
+
+template <bool B> struct BoolC { static constexpr bool value = B; };
+
+// 1 / a for the pivots of gj_lookahead, without a branch: a is scaled by
+// the power of two 2^-e (e the exponent of max(|Re|, |Im|), exact) into
+// [1, 2), and |a|^2 in [1, 8] takes one approximate reciprocal.  The result
+// only seeds an inverse that the refinement corrects.
+KNIT_DEV float2 crcp_fastf(float2 a)
+{
+    const float m = fmaxf(fabsf(a.x), fabsf(a.y));
+    const int e = min(max(((__float_as_int(m) >> 23) & 0xff) - 127, -126), 126);
+    const float s = __int_as_float((127 - e) << 23);
+    const float ax = a.x * s, ay = a.y * s;
+    const float d = __fdividef(1.0f, fmaf(ax, ax, ay * ay)) * s;
+    return make_float2(ax * d, -ay * d);
+}
+
+// Gauss-Jordan with look-ahead: the algorithm of gj_blocked (same implicit
+// pivoting, same result layout), rescheduled so that a panel's elimination
+// overlaps the previous panel's rank update.  For panel P (columns
+// K .. K+NB-1) one step reads only the panel columns, so
+//   * the warps on the other three schedulers (warp 0 keeps its scheduler
+//     to itself) apply X -= U V of panel P-1 to the panel-P columns, signal
+//     warp 0 through named barrier 1, and go on with all other columns,
+//     register-tiled over their rows, while
+//   * warp 0 runs the NB steps on the panel-P columns;
+// then, after one barrier, one thread per column forms panel P's v vectors
+// by forward substitution from the pivot rows of the matrix at the start of
+// the panel (an explicit inverse of the substitution's triangular matrix
+// would not be bounded by the pivoting, and loses accuracy on
+// ill-conditioned A).  Ub / Vb hold two panels' U (MP x gj_ust(NB)) and
+// V (NB x MP) in turn.
+template <int MP, int NTH, int TY, int TX, int NB = 8, int NWA = NTH / 32 - NTH / 128>
+__device__ __forceinline__ int gj_lookahead(float2 *X, int M, float2 *Ub, float2 *Vb,
+                                            GJShared<MP> &g)
+{
+    static_assert(MP % 32 == 0 && MP % NB == 0 && 32 % NB == 0 && MP <= 128, "panel layout");
+    static_assert(NB % 2 == 0 && MP <= NTH && TY * TX == NTH, "thread layout");
+    constexpr int RA = MP / TY, RB = MP / TX, R2 = MP / 32, IB = MP <= 64 ? 6 : 7;
+    constexpr int UST = gj_ust(NB), NW = NTH / 32;
+    static_assert(NWA >= 1 && NWA <= NW - NW / 4, "workers: warps off warp 0's scheduler");
+    constexpr unsigned IMASK = (1u << IB) - 1u, FULL = 0xffffffffu;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid % TX, lane = tid & 31, warp = tid >> 5;
+    bool open[R2];   // warp 0: row lane + 32t may still become a pivot row
+#pragma unroll
+    for (int t = 0; t < R2; ++t) open[t] = lane + 32 * t < M;
+    const int NP = (M + NB - 1) / NB;
+    for (int P = 0;; ++P) {
+        const int K = P * NB;
+        const float2 *Up = Ub + ((P + 1) & 1) * MP * UST;   // panel P-1
+        const float2 *Vp = Vb + ((P + 1) & 1) * NB * MP;
+        const int nkp = P > 0 ? min(NB, M - (P - 1) * NB) : 0;
+        if (P == NP) {
+            // the last panel's update, over the whole matrix
+            float2 acc[RA][RB];
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[a][b] = X[(ty + TY * a) * MP + tx + TX * b];
+#pragma unroll
+            for (int c = 0; c < NB; c += 2) {
+                if (c < nkp) {
+                    float4 ua[RA];
+                    float2 vb0[RB], vb1[RB];
+#pragma unroll
+                    for (int a = 0; a < RA; ++a)
+                        ua[a] = *reinterpret_cast<const float4 *>(Up + (ty + TY * a) * UST + c);
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) {
+                        vb0[b] = Vp[c * MP + tx + TX * b];
+                        vb1[b] = Vp[(c + 1) * MP + tx + TX * b];
+                    }
+                    const bool two = c + 1 < nkp;
+#pragma unroll
+                    for (int a = 0; a < RA; ++a)
+#pragma unroll
+                        for (int b = 0; b < RB; ++b) {
+                            acc[a][b] = cfmsf(make_float2(ua[a].x, ua[a].y), vb0[b], acc[a][b]);
+                            if (two) acc[a][b] = cfmsf(make_float2(ua[a].z, ua[a].w), vb1[b], acc[a][b]);
+                        }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < RB; ++b) X[(ty + TY * a) * MP + tx + TX * b] = acc[a][b];
+            __syncthreads();
+            return ST_OK;
+        }
+        const int nk = min(NB, M - K);
+        float2 *const U = Ub + (P & 1) * MP * UST;
+        float2 *const V = Vb + (P & 1) * NB * MP;
+        if (warp == 0) {
+            // wait until the workers have brought the panel columns up to date
+            if (P > 0) asm volatile("bar.sync 1, %0;" ::"r"(32 * (NWA + 1)) : "memory");
+            float2 pc[R2][NB];   // panel columns, rows lane + 32t
+#pragma unroll
+            for (int t = 0; t < R2; ++t)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) pc[t][c] = X[(lane + 32 * t) * MP + K + c];
+            int pk[NB];        // pivot rows of the panel's steps
+            float2 rk[NB];     // and 1 / pivot
+            bool bad = false;
+            // the NB steps; a full panel runs them without bound checks, and
+            // no step branches (a vanishing pivot only raises bad)
+            auto steps = [&](auto fullc) {
+                constexpr bool FULLP = decltype(fullc)::value;
+#pragma unroll
+                for (int kk = 0; kk < NB; ++kk) {
+                    if (!FULLP && kk >= nk) break;
+                    unsigned key = 0u;
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        const unsigned kt = (__float_as_uint(cabs1f(pc[t][kk])) & ~IMASK) |
+                                            (IMASK - (unsigned)(lane + 32 * t));
+                        key = max(key, open[t] ? kt : 0u);
+                    }
+                    key = __reduce_max_sync(FULL, key);
+                    bad |= (key & ~IMASK) == 0u;
+                    const int p = (int)(IMASK - (key & IMASK)), pl = p & 31, pt = p >> 5;
+                    pk[kk] = p;
+                    // the pivot row's current panel entries, from lane p % 32:
+                    // the pivot and the next column first (they lead to the
+                    // next step's pivot search), the rest after
+                    float2 prow[NB];
+                    auto fetch = [&](int c) {
+                        float2 own = pc[0][c];
+#pragma unroll
+                        for (int t = 1; t < R2; ++t) own = t == pt ? pc[t][c] : own;
+                        prow[c] = make_float2(__shfl_sync(FULL, own.x, pl), __shfl_sync(FULL, own.y, pl));
+                    };
+                    fetch(kk);
+                    if (kk + 1 < NB) fetch(kk + 1);
+                    const float2 rinv = crcp_fastf(prow[kk]);
+                    if (kk + 1 < NB) {
+                        const float2 vk = cmulf(prow[kk + 1], rinv);
+#pragma unroll
+                        for (int t = 0; t < R2; ++t) {
+                            float2 u = pc[t][kk];
+                            u.x -= lane + 32 * t == p ? 1.f : 0.f;
+                            pc[t][kk + 1] = cfmsf(u, vk, pc[t][kk + 1]);
+                        }
+                    }
+#pragma unroll
+                    for (int c = kk + 2; c < NB; ++c) fetch(c);
+#pragma unroll
+                    for (int c = kk + 2; c < NB; ++c) {
+                        const float2 vk = cmulf(prow[c], rinv);
+#pragma unroll
+                        for (int t = 0; t < R2; ++t) {
+                            const int i = lane + 32 * t;
+                            float2 u = pc[t][kk];
+                            u.x -= i == p ? 1.f : 0.f;
+                            pc[t][c] = cfmsf(u, vk, pc[t][c]);
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        const int i = lane + 32 * t;
+                        float2 u = pc[t][kk];
+                        u.x -= i == p ? 1.f : 0.f;
+                        U[i * UST + kk] = u;
+                        open[t] = open[t] && i != p;
+                    }
+                    rk[kk] = rinv;
+                }
+            };
+            if (nk == NB) steps(BoolC<true>{});
+            else steps(BoolC<false>{});
+            if (lane == 0)
+#pragma unroll
+                for (int kk = 0; kk < NB; ++kk)
+                    if (kk < nk) {
+                        g.perm[K + kk] = pk[kk];
+                        g.rinv[kk] = rk[kk];
+                    }
+            if (lane == 0) g.flag = bad ? 1 : 0;
+        } else if ((warp & 3) != 0 && warp - 1 - (warp >> 2) < NWA && P > 0) {
+            // workers (the warps off warp 0's scheduler) apply X -= U V of
+            // panel P-1: first to the panel-P columns, which warp 0 waits
+            // for, then to all other columns
+            const int wa = warp - 1 - (warp >> 2);   // 0 .. NWA-1
+            for (int e = wa * 32 + lane; e < MP * NB; e += 32 * NWA) {
+                const int i = e / NB, c = e % NB;
+                float2 acc = X[i * MP + K + c];
+#pragma unroll
+                for (int cp = 0; cp < NB; ++cp)
+                    if (cp < nkp) acc = cfmsf(Up[i * UST + cp], Vp[cp * MP + K + c], acc);
+                X[i * MP + K + c] = acc;
+            }
+            asm volatile("bar.arrive 1, %0;" ::"r"(32 * (NWA + 1)) : "memory");
+            // rows wa, wa + NWA, ... (at most RW), lanes along the row
+            constexpr int RW = (MP + NWA - 1) / NWA;
+            float2 acc[RW][R2];
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int i = wa + NWA * r;
+#pragma unroll
+                for (int t = 0; t < R2; ++t)
+                    acc[r][t] = i < MP ? X[i * MP + lane + 32 * t] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int c = 0; c < NB; c += 2) {
+                if (c < nkp) {
+                    float2 v0[R2], v1[R2];
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        v0[t] = Vp[c * MP + lane + 32 * t];
+                        v1[t] = Vp[(c + 1) * MP + lane + 32 * t];
+                    }
+                    const bool two = c + 1 < nkp;
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) {
+                        const int i = wa + NWA * r;
+                        if (i < MP) {
+                            const float4 q = *reinterpret_cast<const float4 *>(Up + i * UST + c);
+#pragma unroll
+                            for (int t = 0; t < R2; ++t) {
+                                acc[r][t] = cfmsf(make_float2(q.x, q.y), v0[t], acc[r][t]);
+                                if (two) acc[r][t] = cfmsf(make_float2(q.z, q.w), v1[t], acc[r][t]);
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int i = wa + NWA * r;
+                if (i < MP)
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        const int j = lane + 32 * t;
+                        if (j < K || j >= K + NB) X[i * MP + j] = acc[r][t];
+                    }
+            }
+        }
+        __syncthreads();
+        if (g.flag) return ST_SINGULAR;
+        if (tid < MP) {
+            // the panel's v vectors by forward substitution, one column per
+            // thread: v_k = (X[p_k, j] + [j = K+k] - sum_{c<k} u_c[p_k] v_c) / pivot_k
+            const int j = tid;
+            float2 vj[NB];
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk) {
+                if (kk < nk) {
+                    const int p = g.perm[K + kk];
+                    float2 r = X[p * MP + j];
+                    if (j == K + kk) r.x += 1.f;
+#pragma unroll
+                    for (int c = 0; c < kk; ++c) r = cfmsf(U[p * UST + c], vj[c], r);
+                    vj[kk] = cmulf(r, g.rinv[kk]);
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk)
+                if (kk < nk) V[kk * MP + j] = vj[kk];
+        }
+        __syncthreads();
+    }
 }
 
 // store the inverse held in x (see gj_regs) into X (MP x MP, row-major)

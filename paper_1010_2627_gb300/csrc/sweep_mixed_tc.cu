@@ -9,7 +9,7 @@
 //    A_n = -Gv' and the residual of an approximate inverse X' is
 //    R = I - A_n X' = I + Gv' X';
 //  * X = complex64 inverse of fl32(A_n) by blocked Gauss-Jordan with
-//    implicit partial pivoting (gj_blocked, 512 threads);
+//    implicit partial pivoting and look-ahead (gj_lookahead, 512 threads);
 //  * X is rounded at a per-column power-of-two scale tau_n to 24 bits,
 //    X' = tau_n 2^-8 (d0 + d1 2^-8 + d2 2^-16), |d| <= 256 integers (three
 //    bf16 "digits", exact, and X' itself exact in fp32); the refinement uses
@@ -68,9 +68,9 @@ struct TcSmem {
         unsigned char adig[2 * NDA * A_TILE];    // A digits of two K-chunks
         float2 R[MPT * RS];                      // residual (after the products)
         struct {
-            float2 U[GJ_NB * MPT];
-            float2 V[GJ_NB * MPT];
-        } pv;                                    // Gauss-Jordan panel updates
+            float2 U[2 * MPT * gj_ust(GJ_NB)];
+            float2 V[2 * GJ_NB * MPT];
+        } pv;                                    // Gauss-Jordan panels (two in turn)
     } u;
     union {
         struct {
@@ -307,7 +307,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                                            : make_float2(i == j ? 1.f : 0.f, 0.f);
             }
             __syncthreads();
-            st = gj_blocked<MPT, TYT, TXT, GJ_NB>(sm.X, M, sm.u.pv.U, sm.u.pv.V, sm.gj);
+            st = gj_lookahead<MPT, NTT, TYT, TXT, GJ_NB>(sm.X, M, sm.u.pv.U, sm.u.pv.V, sm.gj);
             if (st != ST_OK) break;
             {
                 float2 x[RA][RB];
