@@ -6,6 +6,7 @@
 #pragma once
 
 #include "knit_common.cuh"
+#include "dense_fp64.cuh"
 
 namespace mixed {
 
@@ -557,49 +558,54 @@ __device__ __forceinline__ int gj_lookahead(float2 *X, int M, float2 *Ub, float2
                 X[i * MP + K + c] = acc;
             }
             asm volatile("bar.arrive 1, %0;" ::"r"(32 * (NWA + 1)) : "memory");
-            // rows wa, wa + NWA, ... (at most RW), lanes along the row
+            // rows wa, wa + NWA, ... (at most RW), lanes along the row, in
+            // chunks of RWC rows (at most 12 accumulators per lane)
             constexpr int RW = (MP + NWA - 1) / NWA;
-            float2 acc[RW][R2];
+            constexpr int RWC = RW < 12 / R2 ? RW : (12 / R2 > 0 ? 12 / R2 : 1);
+#pragma unroll 1
+            for (int r0 = 0; r0 < RW; r0 += RWC) {
+                float2 acc[RWC][R2];
 #pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const int i = wa + NWA * r;
+                for (int r = 0; r < RWC; ++r) {
+                    const int i = wa + NWA * (r0 + r);
 #pragma unroll
-                for (int t = 0; t < R2; ++t)
-                    acc[r][t] = i < MP ? X[i * MP + lane + 32 * t] : make_float2(0.f, 0.f);
-            }
+                    for (int t = 0; t < R2; ++t)
+                        acc[r][t] = i < MP ? X[i * MP + lane + 32 * t] : make_float2(0.f, 0.f);
+                }
 #pragma unroll
-            for (int c = 0; c < NB; c += 2) {
-                if (c < nkp) {
-                    float2 v0[R2], v1[R2];
+                for (int c = 0; c < NB; c += 2) {
+                    if (c < nkp) {
+                        float2 v0[R2], v1[R2];
 #pragma unroll
-                    for (int t = 0; t < R2; ++t) {
-                        v0[t] = Vp[c * MP + lane + 32 * t];
-                        v1[t] = Vp[(c + 1) * MP + lane + 32 * t];
-                    }
-                    const bool two = c + 1 < nkp;
+                        for (int t = 0; t < R2; ++t) {
+                            v0[t] = Vp[c * MP + lane + 32 * t];
+                            v1[t] = Vp[(c + 1) * MP + lane + 32 * t];
+                        }
+                        const bool two = c + 1 < nkp;
 #pragma unroll
-                    for (int r = 0; r < RW; ++r) {
-                        const int i = wa + NWA * r;
-                        if (i < MP) {
-                            const float4 q = *reinterpret_cast<const float4 *>(Up + i * UST + c);
+                        for (int r = 0; r < RWC; ++r) {
+                            const int i = wa + NWA * (r0 + r);
+                            if (i < MP) {
+                                const float4 q = *reinterpret_cast<const float4 *>(Up + i * UST + c);
 #pragma unroll
-                            for (int t = 0; t < R2; ++t) {
-                                acc[r][t] = cfmsf(make_float2(q.x, q.y), v0[t], acc[r][t]);
-                                if (two) acc[r][t] = cfmsf(make_float2(q.z, q.w), v1[t], acc[r][t]);
+                                for (int t = 0; t < R2; ++t) {
+                                    acc[r][t] = cfmsf(make_float2(q.x, q.y), v0[t], acc[r][t]);
+                                    if (two) acc[r][t] = cfmsf(make_float2(q.z, q.w), v1[t], acc[r][t]);
+                                }
                             }
                         }
                     }
                 }
-            }
 #pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                const int i = wa + NWA * r;
-                if (i < MP)
+                for (int r = 0; r < RWC; ++r) {
+                    const int i = wa + NWA * (r0 + r);
+                    if (i < MP)
 #pragma unroll
-                    for (int t = 0; t < R2; ++t) {
-                        const int j = lane + 32 * t;
-                        if (j < K || j >= K + NB) X[i * MP + j] = acc[r][t];
-                    }
+                        for (int t = 0; t < R2; ++t) {
+                            const int j = lane + 32 * t;
+                            if (j < K || j >= K + NB) X[i * MP + j] = acc[r][t];
+                        }
+                }
             }
         }
         __syncthreads();
@@ -719,6 +725,81 @@ KNIT_DEV int neumann_terms(float rmax, int M)
         ++n;
     }
     return n;
+}
+
+// The series cannot reach NEUMANN_TOL within NEUMANN_MAX terms (or max|R_ij|
+// is not a number): the complex64 inverse is no approximate inverse, A_n
+// being nearly singular -- near a resonance of the part of the system left
+// of slice n, which long disordered samples meet.  The slice is then
+// inverted in FP64 (fallback_*).
+KNIT_DEV bool refinement_fails(float rmax, int M)
+{
+    const float p = sqrtf((float)M) * rmax;
+    float t = p * p;
+#pragma unroll
+    for (int n = 0; n < NEUMANN_MAX; ++n) t *= p;
+    return !(t <= NEUMANN_TOL);
+}
+
+// scratch of gj_invert64 carved from raw memory: (2M + 1) complex128 and
+// M + 2 ints, 16-byte aligned base
+KNIT_DEV GJScratch64 fallback_scratch(void *base, int M)
+{
+    GJScratch64 sc;
+    sc.row = reinterpret_cast<double2 *>(base);
+    sc.col = sc.row + M;
+    sc.pval = sc.col + M;
+    sc.perm = reinterpret_cast<int *>(sc.pval + 1);
+    sc.flag = sc.perm + M;
+    sc.piv = sc.flag + 1;
+    return sc;
+}
+
+// A_n in FP64 (row-major, leading dimension M) from the double-float Gv
+// (Gh + Gl, row stride ldg): A = -Gv, plus diag(eps) - H0 when eps is given
+// (kernels whose Gv does not already carry them).  Ends with __syncthreads.
+KNIT_DEV void fallback_form_a(double2 *A, const float2 *Gh, const float2 *Gl, int ldg, int M,
+                              const double *eps, const SysDev &s)
+{
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+        const int i = e / M, j = e - i * M;
+        const float2 h = Gh[i * ldg + j], l = Gl[i * ldg + j];
+        A[e] = make_double2(-((double)h.x + (double)l.x), -((double)h.y + (double)l.y));
+    }
+    __syncthreads();
+    if (eps) {
+        for (int i = threadIdx.x; i < M; i += blockDim.x) {
+            A[i * M + i].x += eps[i];
+            for (int c = s.h0_rowptr[i]; c < s.h0_rowptr[i + 1]; ++c) {
+                const double2 h = s.h0_val[c];
+                double2 &a = A[i * M + s.h0_col[c]];
+                a.x -= h.x;
+                a.y -= h.y;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// the FP64 inverse back into the double-float state (identity in the
+// padding, as the refinement leaves it).  Ends with __syncthreads.
+KNIT_DEV void fallback_store_g(const double2 *A, float2 *Gh, float2 *Gl, int ldg, int MPad, int M)
+{
+    for (int e = threadIdx.x; e < MPad * MPad; e += blockDim.x) {
+        const int i = e / MPad, j = e - i * MPad;
+        float2 h, l;
+        if (i < M && j < M) {
+            const double2 v = A[i * M + j];
+            to_df(v.x, h.x, l.x);
+            to_df(v.y, h.y, l.y);
+        } else {
+            h = make_float2(i == j ? 1.f : 0.f, 0.f);
+            l = make_float2(0.f, 0.f);
+        }
+        Gh[i * ldg + j] = h;
+        Gl[i * ldg + j] = l;
+    }
+    __syncthreads();
 }
 
 // One Horner step of the series on the thread's tile rows RA0 .. RA0+NRA-1:

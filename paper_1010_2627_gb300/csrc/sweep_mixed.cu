@@ -35,7 +35,8 @@ namespace {
 template <int MP>
 struct MixedSmem {
     float2 X[MP * MP];     // inverse of the complex64 A_n (columns in final order)
-    float2 R[MP * MP];     // residual (X and R together hold G_LL as complex128 at the end)
+    float2 R[MP * MP];     // residual (X and R together hold G_LL as complex128 at the end,
+                           // and A_n as complex128 on a slice inverted in FP64)
     float2 Gh[MP * MP];    // g (hi) / Gv (hi)
     float2 Gl[MP * MP];    // g (lo) / Gv (lo)
     float2 H0f[MP * MP];   // complex64 copy of H0 for forming X
@@ -126,8 +127,24 @@ knit_sweep_mixed_kernel(InstDev in)
                     }
                     x[a][b] = v;
                 }
-            st = gj_regs<MP>(x, M, sm.gj);
-            if (st != ST_OK) break;
+            if constexpr (MP >= 32) {
+                // look-ahead Gauss-Jordan in shared memory (U, V panels in the
+                // residual and series buffers, free until the residual)
+#pragma unroll
+                for (int a = 0; a < RT; ++a)
+#pragma unroll
+                    for (int b = 0; b < RT; ++b) sm.X[(ty + 16 * a) * MP + tx + 16 * b] = x[a][b];
+                __syncthreads();
+                st = gj_lookahead<MP, NT, 16, 16>(sm.X, M, sm.R, sm.S, sm.gj);
+                if (st != ST_OK) break;
+#pragma unroll
+                for (int a = 0; a < RT; ++a)
+#pragma unroll
+                    for (int b = 0; b < RT; ++b) x[a][b] = sm.X[(ty + 16 * a) * MP + tx + 16 * b];
+            } else {
+                st = gj_regs<MP>(x, M, sm.gj);
+                if (st != ST_OK) break;
+            }
             store_inverse<MP>(x, M, sm.gj, sm.X);
 
             // ---- residual R = I - D X + Gv X in double-float
@@ -211,6 +228,16 @@ knit_sweep_mixed_kernel(InstDev in)
                     }
             }
             const float rmax = block_max_nonneg<NT>(rloc, sm.redu);
+            if (refinement_fails(rmax, M)) {
+                // near-singular A_n: this slice in FP64, in the X and R
+                // buffers (contiguous), scratch in the series buffer
+                double2 *const A64 = reinterpret_cast<double2 *>(sm.X);
+                fallback_form_a(A64, sm.Gh, sm.Gl, MP, M, sm.eps, s);
+                st = gj_invert64(A64, M, fallback_scratch(sm.S, M));
+                if (st != ST_OK) break;
+                fallback_store_g(A64, sm.Gh, sm.Gl, MP, MP, M);
+                continue;
+            }
             const int nx = neumann_terms(rmax, M);
             float2 *const S = nx ? sm.S : sm.R;
             neumann_inplace<MP, MP, 16, 16>(sm.R, S, M, nx);

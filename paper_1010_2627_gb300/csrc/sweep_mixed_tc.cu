@@ -80,6 +80,7 @@ struct TcSmem {
         } s;
     } w;
     static_assert(MPT * RS * sizeof(float2) <= sizeof(w.s.bdig), "series buffer");
+    static_assert(sizeof(X) + sizeof(u) >= MPT * MPT * sizeof(double2), "FP64 fallback matrix");
     GJShared<MPT> gj;
     double eps[MPT];
     float2 vh[2][MPT];
@@ -501,6 +502,16 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             // further Neumann terms where A_n is ill-conditioned, in the B-digit
             // buffer (free once the products are read back)
             const float rmax = block_max_nonneg<NTT>(rloc, sm.redu);
+            if (refinement_fails(rmax, M)) {
+                // near-singular A_n: this slice in FP64, in the X and
+                // residual buffers (contiguous), scratch in the B digits
+                double2 *const A64 = reinterpret_cast<double2 *>(sm.X);
+                fallback_form_a(A64, Gh, Gl, MPT, M, nullptr, s);
+                st = gj_invert64(A64, M, fallback_scratch(sm.w.s.bdig, M));
+                if (st != ST_OK) break;
+                fallback_store_g(A64, Gh, Gl, MPT, MPT, M);
+                continue;
+            }
             const int nx = neumann_terms(rmax, M);
             float2 *const S = nx ? reinterpret_cast<float2 *>(sm.w.s.bdig) : sm.u.R;
             neumann_inplace<MPT, RS, TYT, TXT>(sm.u.R, S, M, nx);

@@ -25,9 +25,13 @@ namespace {
 constexpr int NTW = 512, TYW = 16, TXW = 32;
 constexpr int VBMAX = 4;
 
+constexpr int GJW_NB = 4;   // Gauss-Jordan panel width (four rows per lane at MP = 128)
+
 template <int MP>
 struct WideSmem {
     float2 X[MP * MP];
+    float2 gjU[2 * MP * gj_ust(GJW_NB)];   // Gauss-Jordan panels (two in turn)
+    float2 gjV[2 * GJW_NB * MP];
     GJShared<MP> gj;
     double eps[MP];
     float2 vbh[2][MP * VBMAX];   // diagonal blocks of V per parity: [i][kk] = V[i][bi + kk]
@@ -43,7 +47,8 @@ struct WideWork {   // per-CTA device workspace
     float2 Gh[MP * MP];   // state g_{n-1} (hi, lo)
     float2 Gl[MP * MP];
     float2 R[MP * MP];    // residual
-    float2 S[2][MP * MP]; // further Neumann terms (two buffers in turn)
+    float2 S[2][MP * MP]; // further Neumann terms (two buffers in turn); A_n as complex128
+                          // on a slice inverted in FP64
     union {
         struct {
             float2 Vh[MP * MP];   // Gv (hi, lo) during the sweep
@@ -312,19 +317,31 @@ knit_sweep_mixed_wide_kernel(InstDev in, WideWork<MP> *work)
                     v.y -= (float)h.y;
                 }
             __syncthreads();
-            float2 x[RA][RB];
-#pragma unroll
-            for (int a = 0; a < RA; ++a)
-#pragma unroll
-                for (int b = 0; b < RB; ++b) x[a][b] = sm.X[(ty + TYW * a) * MP + tx + TXW * b];
-            st = gj_regs<MP, TYW, TXW>(x, M, sm.gj);
+            st = gj_lookahead<MP, NTW, TYW, TXW, GJW_NB>(sm.X, M, sm.gjU, sm.gjV, sm.gj);
             if (st != ST_OK) break;
-            store_inverse<MP, TYW, TXW>(x, M, sm.gj, sm.X);
+            {
+                float2 x[RA][RB];
+#pragma unroll
+                for (int a = 0; a < RA; ++a)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) x[a][b] = sm.X[(ty + TYW * a) * MP + tx + TXW * b];
+                store_inverse<MP, TYW, TXW>(x, M, sm.gj, sm.X);
+            }
             float rloc = residual_pass<MP, 0, 4>(s, sm.X, wk.u.v.Vh, wk.u.v.Vl, sm.eps, wk.R);
             rloc = fmaxf(rloc, residual_pass<MP, 4, RA - 4>(s, sm.X, wk.u.v.Vh, wk.u.v.Vl, sm.eps,
                                                             wk.R));
             // further Neumann terms where A_n is ill-conditioned (two buffers in turn)
             const float rmax = block_max_nonneg<NTW>(rloc, sm.redu);
+            if (refinement_fails(rmax, M)) {
+                // near-singular A_n: this slice in FP64, in the two series
+                // buffers (contiguous), scratch in the residual buffer
+                double2 *const A64 = reinterpret_cast<double2 *>(wk.S[0]);
+                fallback_form_a(A64, wk.u.v.Vh, wk.u.v.Vl, MP, M, sm.eps, s);
+                st = gj_invert64(A64, M, fallback_scratch(wk.R, M));
+                if (st != ST_OK) break;
+                fallback_store_g(A64, wk.Gh, wk.Gl, MP, MP, M);
+                continue;
+            }
             const int nx = neumann_terms(rmax, M);
             const float2 *S = wk.R;
             for (int t = 0; t < nx; ++t) {

@@ -285,6 +285,35 @@ def test_full_bench_workload_sampled(knit):
     assert dT.max() <= TOL_MIXED, (dT.max(), np.unravel_index(dT.argmax(), dT.shape))
 
 
+# long, strongly disordered samples: some slices are near a resonance of the
+# part of the system on their left and A_n is then too ill-conditioned for a
+# complex64 inverse to be refined (these six once returned NaN, and before
+# that wrong finite values); the mixed kernels invert such slices in FP64
+
+@pytest.mark.parametrize("M,L,W,E,seed", [
+    (32, 2048, 2.11693192691528, 0.17926026799803774, 160),
+    (48, 2048, 3.077710220990085, 2.286072835612979, 1339),
+    (64, 2048, 2.3306432864144835, 0.10009286158901398, 984),
+    (64, 2048, 3.1184058224373716, 2.558299270491075, 204),
+    (96, 2048, 2.6323940524500853, -1.836557541971652, 688),
+    (128, 2048, 3.2215960155737164, 0.7464612669955728, 885),
+])
+def test_mixed_long_localized_samples(knit, M, L, W, E, seed):
+    ss = inputs.square(M, L)
+    sysk = knit.System(ss)
+    Ea, sd = np.array([E]), np.array([seed], np.uint64)
+    Tf, stf = sysk.transmission(Ea, sd, W=W, precision=knit.KNIT_FP64)
+    Tm, stm = sysk.transmission(Ea, sd, W=W, precision=knit.KNIT_MIXED)
+    Tc, stc = sysk.transmission(Ea, sd, W=W, precision=knit.KNIT_MIXED_CUDACORE)
+    assert stf[0, 0] == 0 and stm[0, 0] == 0 and stc[0, 0] == 0
+    nch = max(1, nch_square(M, E))
+    assert abs(Tm[0, 0] - Tf[0, 0]) / nch <= TOL_MIXED, (Tm[0, 0], Tf[0, 0])
+    assert abs(Tc[0, 0] - Tf[0, 0]) / nch <= TOL_MIXED, (Tc[0, 0], Tf[0, 0])
+    if M == 32:
+        To = oracle_T(ss, E, seed, W, method="rgf")
+        assert abs(Tf[0, 0] - To) / nch <= TOL_FP64, (Tf[0, 0], To)
+
+
 # --------------------------------------------------------------------------
 # the two residual paths of KNIT_MIXED: tensor cores (33 <= M <= 64) and CUDA cores
 
