@@ -33,6 +33,10 @@ NE, NS = 1024, 8
 METRIC = "T(E) points/s (mixed sweep, |dT| <= 1e-6 vs FP64)"
 WORKLOAD = "square M=64 L=512 W=2, 1024 energies x 8 seeds, two clean leads"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu pass) of one
+# launch of the sweep kernel on exactly this workload, for the kernel as it
+# stands; set to None whenever the kernel changes until it is measured again
+SWEEP_TRAFFIC_BYTES = 69.5e6
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
@@ -297,7 +301,7 @@ def run_knit(args):
         "roofline": {"bound": "alu", "kernel": "knit_sweep_mixed_tc_kernel",
                      "achieved": achieved_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP32_ALU_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": SWEEP_TRAFFIC_BYTES,
                      "note": "algorithmic 16 M^3 flop per slice-update (the method's inversion "
                              "plus product) over the FP32 CUDA-core peak 152 SM x 128 lanes x 2 "
                              "x 2.07 GHz (Gauss-Jordan and refinement run there); kernel timed "
@@ -328,8 +332,9 @@ def run_knit(args):
 def run_uneven(args):
     """Uneven batch: 4096 square-lattice instances, M in {32,48,64,96,128},
     L in {128,...,2048}, W ~ U[0,4], E ~ U(-3.9,3.9), seed = index, drawn from
-    a sampler seeded 12345; one plan, mixed precision (widths above 64 run the
-    FP64 sweep).  One step = lead self-energies + sweeps for all instances."""
+    a sampler seeded 12345; one plan, mixed precision (widths 33..64 on the
+    tensor-core kernel, 32 and below on the CUDA-core one, 65..128 on the wide
+    one).  One step = lead self-energies + sweeps for all instances."""
     import torch
     from paper_1010_2627_gb300 import build, inputs, knit
     build.build()
