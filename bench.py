@@ -410,9 +410,66 @@ def run_profile_case(args):
     sysk.close()
 
 
+def run_ldos_case(args):
+    """LDOS through the sewing pass, mixed vs FP64: square M=64, L=512, W=2,
+    38 energies x 8 seeds (two waves of 152 instances), saving_level 8 (one
+    checkpoint every 8 slices, the slices between recomputed).  One step = the
+    whole LDOS call for all instances; reports LDOS points/s (instances/s) and
+    the largest difference between the two precisions."""
+    import torch
+    from paper_1010_2627_gb300 import build, inputs, knit
+    build.build()
+    knit.load()
+    ss = inputs.square(M, L)
+    ne, save = 38, 8
+    E = inputs.energy_grid(-3.9, 3.9, ne)
+    seeds = np.arange(NS, dtype=np.uint64)
+    n = ne * NS
+    sysk = knit.System(ss)
+    stream = torch.cuda.Stream()
+    dE = torch.tensor(E, device="cuda")
+    ds = torch.tensor(seeds.astype(np.int64), device="cuda")
+    out = {}
+    for name, prec in (("mixed", knit.KNIT_MIXED), ("fp64", knit.KNIT_FP64)):
+        dL = torch.empty(n * L * M, dtype=torch.float64, device="cuda")
+        dst = torch.empty(n, dtype=torch.int32, device="cuda")
+
+        def step():
+            knit.knit_ldos(sysk.handle, dE, ds, W, save, dL, None, dst, nE=ne, nS=NS,
+                           stream=stream, precision=prec)
+
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        out[name] = (n / (ms / 1e3), ms, dL.cpu().numpy(), int((dst != 0).sum().item()))
+    diff = float(np.abs(out["mixed"][2] - out["fp64"][2]).max() / np.abs(out["fp64"][2]).max())
+    print(json.dumps({
+        "metric": "LDOS points/s (sewing pass, mixed vs FP64)", "value": out["mixed"][0],
+        "unit": "LDOS points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": out["mixed"][1], "higher_is_better": True, "dtype": "c64 forward + "
+        "double-float sewing", "data": "synthetic",
+        "config": {"workload": f"square M={M} L={L} W={W}, {ne} energies x {NS} seeds, "
+                               f"saving_level {save}"},
+        "fp64": {"value": out["fp64"][0], "ms": out["fp64"][1]},
+        "mixed_speedup": out["mixed"][0] / out["fp64"][0],
+        "max_abs_dldos_over_max_ldos": diff,
+        "status_nonzero": out["mixed"][3] + out["fp64"][3]}), flush=True)
+    sysk.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bench", choices=["bench", "profile", "uneven"])
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "uneven", "ldos"])
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -426,6 +483,8 @@ def main():
         run_profile_case(args)
     elif args.case == "uneven":
         run_uneven(args)
+    elif args.case == "ldos":
+        run_ldos_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

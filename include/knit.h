@@ -161,16 +161,21 @@ knit_status knit_transmission_sigma(knit_system sys, const double *E, int32_t nE
                                     const knit_c128 *sigmaL, const knit_c128 *sigmaR,
                                     int32_t precision, double *T, int32_t *status, void *stream);
 
-/* Local density of states (Sec. 5.3 D knitting followed by sewing), FP64:
+/* Local density of states (Sec. 5.3 D knitting followed by sewing):
  * ldos (nE*nS*L*M, row-major [i][n][x]) receives -Im G_nn[x][x]/pi; T
  * (optional) the transmission; status (optional) per instance (ldos of an
  * instance with non-zero status is unspecified).  saving_level follows
  * knitANDsew (Sec. 7.3): -1 keeps every forward g_n; k >= 1 keeps every k-th
  * and recomputes the slices in between during the backward pass; 0 (keep
- * nothing) is rejected because the backward pass needs the forward g_n. */
+ * nothing) is rejected because the backward pass needs the forward g_n.
+ * precision: KNIT_FP64, or KNIT_MIXED / KNIT_MIXED_CUDACORE (the same
+ * thing here) for widths up to 64 with diagonal inter-slice couplings: the
+ * forward pass is the mixed sweep, checkpoints are kept as double-float and
+ * the sewing products are formed in double-float; other systems run in FP64. */
 knit_status knit_ldos(knit_system sys, const double *E, int32_t nE, const uint64_t *seeds,
-                      int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
-                      double *ldos, double *T, int32_t *status, void *stream);
+                      int32_t nS, double W, int32_t precision, int32_t saving_level,
+                      const knit_lead_opts *opts, double *ldos, double *T, int32_t *status,
+                      void *stream);
 
 /* Learned warm start for a lead (the paper's lead solver has no learned
  * component; this one speeds up and tightens the fixed point of Sec. 5.3 B).  A multilayer perceptron (input: the

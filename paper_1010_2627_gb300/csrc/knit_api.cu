@@ -23,6 +23,9 @@ extern "C" cudaError_t knit_launch_ldos_fp64(const InstDev *, int, int, int, dou
 extern "C" size_t knit_fp64_smem_bytes(int, int, int);
 extern "C" cudaError_t knit_launch_mixed_impl(const InstDev *, int, int, int, cudaStream_t);
 extern "C" int knit_mixed_max_M(void);
+extern "C" size_t knit_ldos_mixed_work_bytes(int, int, int);
+extern "C" cudaError_t knit_launch_ldos_mixed(const InstDev *, int, int, int, int, void *, double *,
+                                              long long, cudaStream_t);
 extern "C" size_t knit_mixed_wide_work_bytes(int);
 extern "C" cudaError_t knit_launch_mixed_wide(const InstDev *, int, int, void *, cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
@@ -819,12 +822,13 @@ knit_status knit_transmission_sigma(knit_system s, const double *E, int32_t nE,
 }
 
 knit_status knit_ldos(knit_system s, const double *E, int32_t nE, const uint64_t *seeds,
-                      int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
-                      double *ldos, double *T, int32_t *status, void *stream)
+                      int32_t nS, double W, int32_t precision, int32_t saving_level,
+                      const knit_lead_opts *opts, double *ldos, double *T, int32_t *status,
+                      void *stream)
 {
     knit_status r = check_system(s);
     if (r != KNIT_OK) return r;
-    if ((r = check_batch(s, E, nE, nS, KNIT_FP64, W)) != KNIT_OK) return r;
+    if ((r = check_batch(s, E, nE, nS, precision, W)) != KNIT_OK) return r;
     if (!ldos) return fail(KNIT_ERR_INVALID, "ldos is NULL");
     if (saving_level == 0)
         return fail(KNIT_ERR_INVALID, "saving_level 0 keeps nothing: no local observables");
@@ -855,13 +859,22 @@ knit_status knit_ldos(knit_system s, const double *E, int32_t nE, const uint64_t
     in.queue = s->queue.as<int>();
     CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
     const int grid = std::max(1, std::min(n, s->nsm));
-    int use_smem = knit_fp64_smem_bytes(s->M, 1, 4) <= 220 * 1024;
-    if (!use_smem) CK(s->work.ensure(sizeof(double2) * 4 * MM * grid), "ldos workspace");
-    const int nck = (s->L + save - 1) / save;
-    CK(s->ckpt.ensure(sizeof(double2) * MM * (size_t)(nck + save) * grid), "checkpoint workspace");
-    CK(knit_launch_ldos_fp64(&in, s->M, s->L, grid, s->work.as<double2>(), use_smem,
-                             s->ckpt.as<double2>(), save, dL, (long long)s->L * s->M, st),
-       "ldos launch");
+    if (sweep_kind(s, precision) == SWEEP_MIXED) {
+        CK(s->ckpt.ensure(knit_ldos_mixed_work_bytes(s->M, s->L, save) * grid),
+           "checkpoint workspace");
+        CK(knit_launch_ldos_mixed(&in, s->M, s->L, grid, save, s->ckpt.p, dL,
+                                  (long long)s->L * s->M, st),
+           "mixed ldos launch");
+    } else {
+        int use_smem = knit_fp64_smem_bytes(s->M, 1, 4) <= 220 * 1024;
+        if (!use_smem) CK(s->work.ensure(sizeof(double2) * 4 * MM * grid), "ldos workspace");
+        const int nck = (s->L + save - 1) / save;
+        CK(s->ckpt.ensure(sizeof(double2) * MM * (size_t)(nck + save) * grid),
+           "checkpoint workspace");
+        CK(knit_launch_ldos_fp64(&in, s->M, s->L, grid, s->work.as<double2>(), use_smem,
+                                 s->ckpt.as<double2>(), save, dL, (long long)s->L * s->M, st),
+           "ldos launch");
+    }
     if (hL) CK(cudaMemcpyAsync(ldos, dL, sizeof(double) * n * s->L * s->M, cudaMemcpyDeviceToHost, st), "ldos out");
     if (hT) CK(cudaMemcpyAsync(T, in.T, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
     if (hSt)

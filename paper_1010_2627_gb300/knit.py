@@ -52,7 +52,7 @@ _SIGS = {
     "knit_lead_selfenergy": (i32, [P, i32, P, i32, P, P, P, P, P]),
     "knit_transmission": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P]),
     "knit_transmission_sigma": (i32, [P, P, i32, P, i32, f64, P, P, i32, P, P, P]),
-    "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P]),
+    "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, i32, P, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
     "knit_lead_model_train": (i32, [P, i32, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64,
@@ -202,11 +202,12 @@ def knit_transmission_sigma(handle, E, seeds, W, sigmaL, sigmaR, precision, T, s
 
 
 def knit_ldos(handle, E, seeds, W, saving_level, ldos, T=None, status=None, opts=None, nE=None,
-              nS=None, stream=None):
+              nS=None, stream=None, precision=KNIT_FP64):
     nE = len(E) if nE is None else nE
     nS = (1 if seeds is None else len(seeds)) if nS is None else nS
     _check(load().knit_ldos(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS), float(W),
-                            int(saving_level), None if opts is None else ctypes.byref(opts),
+                            int(precision), int(saving_level),
+                            None if opts is None else ctypes.byref(opts),
                             _ptr(ldos), _ptr(T), _ptr(status), _stream(stream)))
 
 
@@ -379,13 +380,15 @@ class System:
         knit_transmission_sigma(self.handle, E, sd, W, _c128(SL), _c128(SR), precision, T, st)
         return T.reshape(len(E), nS), st.reshape(len(E), nS)
 
-    def ldos(self, E, seeds=None, W=0.0, saving_level=-1, method=KNIT_LEAD_AUTO):
+    def ldos(self, E, seeds=None, W=0.0, saving_level=-1, method=KNIT_LEAD_AUTO,
+             precision=KNIT_FP64):
         E = np.ascontiguousarray(E, dtype=np.float64)
         sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
         nS = 1 if sd is None else len(sd)
         out = np.empty((len(E) * nS, self.L, self.M))
         T = np.empty(len(E) * nS)
         st = np.empty(len(E) * nS, np.int32)
-        knit_ldos(self.handle, E, sd, W, saving_level, out, T, st, _opts(method))
+        knit_ldos(self.handle, E, sd, W, saving_level, out, T, st, _opts(method),
+                  precision=precision)
         return (out.reshape(len(E), nS, self.L, self.M), T.reshape(len(E), nS),
                 st.reshape(len(E), nS))

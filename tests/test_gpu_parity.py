@@ -217,6 +217,52 @@ def test_ldos_clean_ribbon_closed_form(knit):
     assert np.abs(ld[0, 0] - rho[None, :]).max() < 1e-11
 
 
+# LDOS in mixed precision: forward mixed sweep, double-float checkpoints and
+# double-float sewing products.  Tolerance: 1e-6 of the largest LDOS value,
+# the mixed contract of T (the sewing products are exact to ~2^-44 relative;
+# what remains is the forward state's error, which near band edges of long
+# bars reaches the 1e-7 level that T shows there), against the dense oracle
+# where it is cheap and against the FP64 sweep otherwise
+TOL_LDOS_MIXED = 1e-6
+
+
+@pytest.mark.parametrize("saving_level", [-1, 3, 16])
+def test_ldos_mixed_small_config(knit, saving_level):
+    ss = inputs.square(8, 16)
+    E = inputs.energy_grid(-3.9, 3.9, 8)
+    sysk = knit.System(ss)
+    ld, T, st = sysk.ldos(E, seeds=[0], W=1.0, saving_level=saving_level,
+                          precision=knit.KNIT_MIXED)
+    assert (st == 0).all()
+    eps = oracle.onsite(0, 16, 8, 1.0)
+    for e, Ee in enumerate(E):
+        S = oracle.sigma_square(8, 1.0, Ee)
+        d = oracle.dense(ss.H0, ss.V, eps, 16, Ee, S, S, want_ldos=True)
+        assert np.abs(ld[e, 0] - d["ldos"]).max() <= TOL_LDOS_MIXED * np.abs(d["ldos"]).max()
+        assert abs(T[e, 0] - d["T_LR"]) / max(1, nch_square(8, Ee)) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("M,L,saving_level", [(37, 23, 5), (64, 96, -1), (64, 96, 8)])
+def test_ldos_mixed_matches_fp64(knit, M, L, saving_level):
+    ss = inputs.square(M, L)
+    E = np.array([-3.71, -0.9, 0.05, 2.6])
+    seeds = np.array([3, 11], np.uint64)
+    sysk = knit.System(ss)
+    lf, Tf, sf = sysk.ldos(E, seeds=seeds, W=2.0, saving_level=saving_level)
+    lm, Tm, sm = sysk.ldos(E, seeds=seeds, W=2.0, saving_level=saving_level,
+                           precision=knit.KNIT_MIXED)
+    assert (sf == 0).all() and (sm == 0).all()
+    assert np.abs(lm - lf).max() <= TOL_LDOS_MIXED * np.abs(lf).max(), np.abs(lm - lf).max()
+    # the sum rule: LDOS per slice of the mixed run summed over orbitals is
+    # positive everywhere
+    assert (lm.sum(axis=-1) > 0).all()
+    if M == 37:
+        eps = oracle.onsite(3, L, M, 2.0)
+        S = oracle.sigma_square(M, 1.0, E[1])
+        d = oracle.rgf(ss.H0, ss.V, eps, L, E[1], S, S, want_ldos=True)
+        assert np.abs(lm[1, 0] - d["ldos"]).max() <= TOL_LDOS_MIXED * np.abs(d["ldos"]).max()
+
+
 # --------------------------------------------------------------------------
 # status and argument errors
 
