@@ -1,18 +1,21 @@
 // sweep_mixed.cu -- the slice sweep in mixed precision with the residual on
 // CUDA cores (complex64 inversion, double-float refinement), padded widths
-// MP in {16, 32, 64}.
+// MP in {16, 32, 64}, and the local density of states built on it.
 //
-// Per slice n, with the state g_{n-1} carried as hi + lo complex64 pairs
-// (KNIT user guide Sec. 5.3 D knitting in slice form; Eq. 2 by block
-// elimination):
+// Per slice n (mixed_step), with the state g_{n-1} carried as hi + lo
+// complex64 pairs (KNIT user guide Sec. 5.3 D knitting in slice form; Eq. 2
+// by block elimination):
 //   1. Gv = V_n g_{n-1} V_n^dagger (+ Sigma_L at n = 0, + Sigma_R at n = L-1)
 //      formed in double-float, so that A_n = D_n - Gv with D_n = E - H_n;
 //   2. X = fl32(D_n - Gv_hi) inverted by Gauss-Jordan with implicit partial
-//      pivoting in registers;
+//      pivoting (look-ahead blocked form for MP >= 32, in registers at 16);
 //   3. residual R = I - A_n X accumulated with error-free products and sums
 //      (TwoProduct / TwoSum, "Dot2" of Ogita, Rump & Oishi 2005), using the
 //      exact D_n and both words of Gv, then rounded to complex64;
-//   4. one refinement step g_n = X + X R, kept as hi + lo (TwoSum).
+//   4. g_n = X (I + R + R^2 + ...) kept as hi + lo, with as many terms as
+//      max|R_ij| asks for, the product X S error-free when max|R_ij| is large,
+//      and the slice inverted in FP64 when the series cannot converge
+//      (mixed_common.cuh).
 // The last g (slice L-1, which includes Sigma_R) is the exact G_{L-1,L-1} of
 // the whole system, and the transmission follows from it by the unitarity
 // (Ward) identity i(G - G^dagger) = G (Gamma_L + Gamma_R) G^dagger:
