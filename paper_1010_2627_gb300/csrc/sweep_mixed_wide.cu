@@ -3,16 +3,18 @@
 // with 4 x 4 blocks (spin x Nambu sites).
 //
 // Same recursion and arithmetic as sweep_mixed.cu (KNIT user guide Sec. 5.3 D;
-// complex64 Gauss-Jordan with implicit partial pivoting, one refinement step
-// against a double-float residual, state g kept as hi + lo, T from G_LL by the
-// unitarity identity), laid out for the larger matrices:
+// complex64 look-ahead Gauss-Jordan with implicit partial pivoting,
+// refinement against a double-float residual with as many Neumann terms as
+// max|R_ij| asks for and an FP64 inversion of slices where it cannot
+// converge, state g kept as hi + lo, T from G_LL by the unitarity identity),
+// laid out for the larger matrices:
 //  * one CTA of 512 threads per instance; thread (ty, tx) = (tid / 32, tid % 32)
 //    owns rows ty + 16a (a < MP/16) and columns tx + 32b (b < MP/32) of the
 //    register tile, so a warp shares one row set and its lanes run along rows
 //    (broadcast loads of the state rows, conflict-free shared columns);
-//  * the inverse X lives in shared memory; the state (hi, lo), the residual
-//    and the FP64 scratch of the final trace live in a per-CTA workspace in
-//    device memory (L2-resident at ~640 KB per CTA);
+//  * the inverse X and the Gauss-Jordan panels (4 columns) live in shared
+//    memory; the state (hi, lo), the residual, the series buffers and the
+//    FP64 scratch live in a per-CTA workspace in device memory (L2-resident);
 //  * the residual and the refinement product are computed in two passes over
 //    half the tile rows each to bound registers.
 
