@@ -17,6 +17,48 @@
 
 #include "dense_fp64.cuh"
 
+// Is the Hermitian matrix A (M x M, row-major, overwritten) positive
+// semidefinite up to -tol * max_k A_kk?  Semidefinite Cholesky: a pivot below
+// that bound fails; pivots within it end their column (set to zero).  All
+// threads of the block call it; red holds 32 doubles.
+static __device__ int psd_check64(double2 *A, int M, double *red)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double dmax = 0.0;
+    for (int k = tid; k < M; k += nt) dmax = fmax(dmax, A[(size_t)k * M + k].x);
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dmax;
+    __syncthreads();
+    double m = 0.0;
+    for (int w = 0; w < nt / 32; ++w) m = fmax(m, red[w]);
+    __syncthreads();
+    const double tol = 1e-9 * m;
+    for (int k = 0; k < M; ++k) {
+        const double piv = A[(size_t)k * M + k].x;   // uniform: read after a barrier
+        if (!(piv >= -tol)) return 0;
+        const double inv = piv > tol ? 1.0 / sqrt(piv) : 0.0;
+        for (int i = k + 1 + tid; i < M; i += nt) A[(size_t)i * M + k] = cscale(A[(size_t)i * M + k], inv);
+        __syncthreads();
+        const int n = M - k - 1;
+        for (int e = tid; e < n * n; e += nt) {
+            const int i = k + 1 + e / n, j = k + 1 + e % n;
+            A[(size_t)i * M + j] = cfms(A[(size_t)i * M + k], cconj(A[(size_t)j * M + k]),
+                                        A[(size_t)i * M + j]);
+        }
+        __syncthreads();
+    }
+    return 1;
+}
+
+// decimation retries: eta, 100 eta, 1e4 eta, 1e6 eta; a surface g counts as
+// converged when it satisfies its fixed point at its own eta to this relative
+// max-norm and lies on the retarded branch (i(g - g^dagger) positive
+// semidefinite): at eta ~ 1e-12 the doubling can lose enough precision on wide
+// leads to land on another solution of the fixed-point equation
+constexpr int DEC_ATTEMPTS = 4;
+constexpr double DEC_SELF_TOL = 1e-5;
+
 // ---------------------------------------------------------------------------
 // A (M x M, Hermitian) -> diag in A, eigenvectors in U (global memory).
 extern "C" __global__ void __launch_bounds__(256)
@@ -186,7 +228,15 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
     double2 *gb = w + 4 * MM, *t1 = w + 5 * MM, *t2 = w + 6 * MM, *t3 = w + 7 * MM;
     for (int e = blockIdx.x; e < nE; e += gridDim.x) {
         if (only_failed && status[e] == ST_OK) continue;   // uniform over the block
-        const double2 z = make_double2(E[e], eta);
+        double2 *S = sigma + (size_t)e * MM;
+        double2 *G = gout + (size_t)e * MM;
+        int it = 0, st = ST_NOCONVERGE;
+        // decimation at E + i eta; if the surface g does not satisfy its own
+        // fixed point at that eta (the doubling lost precision, which wide
+        // leads with many slow modes meet at eta ~ 1e-13), again at 100x eta
+        double eta_k = eta;
+        for (int attempt = 0; attempt < DEC_ATTEMPTS; ++attempt, eta_k *= 100.0) {
+        const double2 z = make_double2(E[e], eta_k);
         for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
             int i = q / M, j = q - i * M;
             double2 v = V[q], vd = cconj(V[(size_t)j * M + i]);
@@ -196,7 +246,7 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
             be[q] = side == 0 ? vd : v;
         }
         __syncthreads();
-        int it = 0, st = ST_NOCONVERGE;
+        st = ST_NOCONVERGE;
         for (it = 0; it < maxit; ++it) {
             double na = 0.0, nb = 0.0;
             for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
@@ -247,8 +297,6 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
             }
             __syncthreads();
         }
-        double2 *S = sigma + (size_t)e * MM;
-        double2 *G = gout + (size_t)e * MM;
         if (st == ST_OK) {
             for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
                 int i = q / M, j = q - i * M;
@@ -258,6 +306,61 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
             }
             __syncthreads();
             if (gj_invert64(G, M, sc) != ST_OK) st = ST_SINGULAR;
+        }
+        if (st == ST_OK) {
+            // self-consistency at z: t1 = (z - H0 - V g V^dagger)^{-1} (left;
+            // right with V^dagger, V) against g, relative max-norm
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                int i = q / M, j = q - i * M;
+                double2 w2 = side == 0 ? vxvd64(V, G, M, vb, i, j) : vdxv64(V, G, M, vb, i, j);
+                double2 v = make_double2(-H0[q].x - w2.x, -H0[q].y - w2.y);
+                if (i == j) v = cadd(v, z);
+                t1[q] = v;
+            }
+            __syncthreads();
+            if (gj_invert64(t1, M, sc) != ST_OK) {
+                st = ST_SINGULAR;
+            } else {
+                // dm: fixed-point mismatch; gm: size of g; plus the retarded
+                // branch, whose diagonal of i(g - g^dagger) = -2 Im g_kk is >= 0
+                // (the doubling can also land on a non-retarded fixed point)
+                double dm = 0.0, gm = 0.0;
+                for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                    dm = fmax(dm, cabs1(csub(t1[q], G[q])));
+                    gm = fmax(gm, cabs1(G[q]));
+                }
+                for (int k = threadIdx.x; k < M; k += blockDim.x)
+                    if (G[(size_t)k * M + k].y > 0.0) dm = INFINITY;
+                for (int o = 16; o > 0; o >>= 1) {
+                    dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+                    gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+                }
+                __syncthreads();
+                if ((threadIdx.x & 31) == 0) {
+                    red[threadIdx.x >> 5] = dm;
+                    red[16 + (threadIdx.x >> 5)] = gm;
+                }
+                __syncthreads();
+                double mdm = 0.0, mgm = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+                    mdm = fmax(mdm, red[q]);
+                    mgm = fmax(mgm, red[16 + q]);
+                }
+                __syncthreads();
+                if (!(mdm <= DEC_SELF_TOL * mgm)) st = ST_NOCONVERGE;   // also NaN
+            }
+        }
+        if (st == ST_OK) {
+            // the whole retarded condition: i(g - g^dagger) positive semidefinite
+            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+                const int i = q / M, j = q - i * M;
+                const double2 a = G[q], b = cconj(G[(size_t)j * M + i]);
+                t2[q] = make_double2(-(a.y - b.y), a.x - b.x);   // i (a - b)
+            }
+            __syncthreads();
+            if (!psd_check64(t2, M, red)) st = ST_NOCONVERGE;
+        }
+        if (st == ST_OK) break;
         }
         if (st == ST_OK) {
             // Sigma = alpha0 g beta0: left V g V^dagger, right V^dagger g V

@@ -71,6 +71,24 @@ def test_lead_decimation_matches_oracle(knit, M):
         assert res.max() < 1e-7
 
 
+def test_decimation_wide_bdg_lead_is_retarded(knit):
+    """A 32-site spin x Nambu lead (128 orbitals): at eta ~ 1e-12 the doubling
+    loses enough precision to land on non-retarded solutions of the fixed
+    point (Gamma with eigenvalues of both signs) at these energies; the solver
+    must detect that, retry at a larger eta and return a retarded Sigma."""
+    b = inputs.bdg(32, 4, mu=-1.0, t=1.0, delta=0.1, alpha=0.2)
+    sysk = knit.System(b)
+    E = np.array([-0.18359375, 0.17578125, -0.14921875, -0.06484375])
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION,
+                                          want_residual=True)
+        for k in range(len(E)):
+            G = 1j * (S[k] - S[k].conj().T)
+            ev = np.linalg.eigvalsh((G + G.conj().T) / 2)
+            assert ev.min() >= -1e-9 * ev.max(), (lead, E[k], ev.min())
+            assert res[k] < 1e-5, (lead, E[k], res[k])
+
+
 def test_lead_decimation_bdg(knit):
     b = inputs.bdg(2, 3, mu=-1.0, delta=0.1, alpha=0.2)
     sysk = knit.System(b)
