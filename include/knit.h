@@ -112,6 +112,15 @@ typedef struct {
     int32_t Vperiod;             /* 1 or 2 */
     const knit_c128 *lead_H0[2]; /* left/right lead cell (M*M); NULL = H0 */
     const knit_c128 *lead_V[2];  /* left/right lead inter-cell hopping (M*M); NULL = V[0] */
+    int32_t lead_Vperiod[2];     /* 0 or 1: one coupling as above.  2: lead_V[p] holds two
+                                    M*M couplings [V_first, V_second] that alternate going
+                                    outward, V_first coupling the system's end slice to the
+                                    lead's surface slice (H_{0,-1} on the left, H_{L,L-1} on
+                                    the right, slice-forward orientation H_{n,n-1}) and
+                                    V_second the surface slice to the next one, as in an
+                                    armchair ribbon (Sec. 6.3); NULL lead_V[p] continues the
+                                    system's own V.  The lead is solved as a two-slice
+                                    supercell by DECIMATION (AUTO picks it). */
 } knit_system_desc;
 
 /* Copy the description into a new system (all pointers are read during the
@@ -135,7 +144,8 @@ typedef struct {
  * lead: 0 = left, 1 = right.  sigma: nE*M*M outputs (caller-owned).
  * iters (nE, optional): decimation iterations (0 for MODES); residual (nE,
  * optional): max-norm of g - (E - H0 - V g V^dagger)^{-1} at eta = 0, computed
- * in FP64 on the device.  opts may be NULL (AUTO). */
+ * in FP64 on the device (for a period-2 lead: of the supercell's g).  opts may
+ * be NULL (AUTO). */
 knit_status knit_lead_selfenergy(knit_system sys, int32_t lead, const double *E, int32_t nE,
                                  const knit_lead_opts *opts, knit_c128 *sigma, int32_t *iters,
                                  double *residual, void *stream);

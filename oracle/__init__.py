@@ -124,22 +124,75 @@ def sigma_square(M: int, t: float, E: float) -> np.ndarray:
     return out
 
 
+def _retarded_fixed_point(H0, V, g, z, side):
+    """Is g the retarded solution of its lead's fixed point at the complex
+    energy z: g = (z - H0 - V g V^dagger)^{-1} (left; right with V^dagger,
+    V) to 1e-5 relative max-norm, and i(g - g^dagger) positive semidefinite?"""
+    if not np.isfinite(g).all():
+        return False
+    M = H0.shape[0]
+    W = V @ g @ V.conj().T if side == 0 else V.conj().T @ g @ V
+    A = np.linalg.inv(z * np.eye(M) - H0 - W)
+    if not np.abs(A - g).max() <= 1e-5 * np.abs(g).max():
+        return False
+    G = 1j * (g - g.conj().T)
+    ev = np.linalg.eigvalsh((G + G.conj().T) / 2)
+    return ev.min() >= -1e-9 * max(ev.max(), 0.0)
+
+
 def decimation(H0, V, E: float, side: int, eta: float = 1e-12, tol: float = 1e-15,
                maxit: int = 200):
-    """Sancho-Rubio surface g and self-energy of a lead (side 0 left, 1 right).
+    """Sancho-Rubio surface g and self-energy of a lead (side 0 left, 1 right)
+    at E + i eta.  The retarded solution of the fixed point is wanted (a
+    reading of Sec. 5.3 B): when the doubling loses enough precision to end on
+    anything else (non-finite, not a fixed point at its own eta to 1e-5, or
+    i(g - g^dagger) not positive semidefinite), it is run again at 100x eta,
+    up to eta * 1e6.
 
     Returns (g, Sigma, iterations)."""
     H0 = _c(H0, np.complex128)
     V = _c(V, np.complex128)
     M = H0.shape[0]
-    g = np.empty((M, M), dtype=np.complex128)
-    S = np.empty((M, M), dtype=np.complex128)
-    it = ctypes.c_int(0)
-    rc = _load().orc_lead_decimation(M, _p(H0), _p(V), E, eta, side, tol, maxit, _p(g), _p(S),
-                                     ctypes.byref(it))
-    if rc != OK:
-        raise OracleError(rc, "decimation")
-    return g, S, it.value
+    for k in range(4):
+        eta_k = eta * 100.0 ** k
+        g = np.empty((M, M), dtype=np.complex128)
+        S = np.empty((M, M), dtype=np.complex128)
+        it = ctypes.c_int(0)
+        rc = _load().orc_lead_decimation(M, _p(H0), _p(V), E, eta_k, side, tol, maxit, _p(g),
+                                         _p(S), ctypes.byref(it))
+        if rc == OK and _retarded_fixed_point(H0, V, g, E + 1j * eta_k, side):
+            return g, S, it.value
+    raise OracleError(rc if rc != OK else ERR_NOCONVERGE, "decimation")
+
+
+def decimation_period2(H0, V_first, V_second, E: float, side: int, eta: float = 1e-12,
+                       tol: float = 1e-15, maxit: int = 200):
+    """Self-energy on the system's end slice of a lead whose inter-slice
+    couplings alternate V_first, V_second going outward (V_first couples the
+    end slice to the lead's surface slice; slice-forward orientation
+    H_{n,n-1}), from the surface function of the lead's two-slice cell
+    (Sec. 5.3 B with a cell of two slices).  Returns Sigma (M x M)."""
+    H0 = np.asarray(H0, np.complex128)
+    Vf = np.asarray(V_first, np.complex128)
+    Vs = np.asarray(V_second, np.complex128)
+    M = H0.shape[0]
+    Hc = np.zeros((2 * M, 2 * M), np.complex128)
+    Vc = np.zeros_like(Hc)
+    Hc[:M, :M] = H0
+    Hc[M:, M:] = H0
+    if side == 0:
+        # cell (s_-1, s_-2): H_{s-1,s-2} = V_second; next cell couples via H_{s-2,s-3} = V_first
+        Hc[:M, M:] = Vs
+        Hc[M:, :M] = Vs.conj().T
+        Vc[M:, :M] = Vf
+    else:
+        # cell (s_L, s_L+1): H_{s_L+1,s_L} = V_second; next cell via H_{s_L+2,s_L+1} = V_first
+        Hc[M:, :M] = Vs
+        Hc[:M, M:] = Vs.conj().T
+        Vc[:M, M:] = Vf
+    g, _, _ = decimation(Hc, Vc, E, side, eta=eta, tol=tol, maxit=maxit)
+    g11 = g[:M, :M]
+    return Vf @ g11 @ Vf.conj().T if side == 0 else Vf.conj().T @ g11 @ Vf
 
 
 def _sys_arrays(H0, V, eps, L):

@@ -36,6 +36,8 @@ extern "C" cudaError_t knit_launch_decimation(const double2 *, const double2 *, 
                                               const double *, int, double, double, int, double2 *,
                                               double2 *, double2 *, int *, int *, int,
                                               cudaStream_t);
+extern "C" cudaError_t knit_launch_sigma_block(const double2 *, const double2 *, int, int, int, int,
+                                               double2 *, double2 *, int, cudaStream_t);
 extern "C" cudaError_t knit_launch_decimation_failed(const double2 *, const double2 *, int, int,
                                                      int, const double *, int, double, double, int,
                                                      double2 *, double2 *, double2 *, int *, int *,
@@ -122,7 +124,9 @@ struct DevBuf {
 };
 
 struct Lead {
-    double2 *H0 = nullptr, *V = nullptr;   // device copies
+    double2 *H0 = nullptr, *V = nullptr;   // device copies (Mp x Mp)
+    int Mp = 0;         // cell size: M, or 2M for a period-2 lead solved as a supercell
+    double2 *C = nullptr;                  // period-2 lead: system-to-surface coupling (M x M)
     int vb = 1;
     int scalar = 0;     // V = t * identity
     double t2 = 0.0;    // |t|^2
@@ -144,6 +148,7 @@ struct knit_system_s {
     int leads_same = 0;
     // grow-only workspaces
     DevBuf E, seeds, T, status, queue, sigL, sigR, gL, gR, lst, lit, lres, work, ckpt, decw, ldos;
+    DevBuf p2g, p2s, p2t;   // period-2 leads: supercell g and Sigma, block-product scratch
 
     SysDev dev() const
     {
@@ -367,6 +372,30 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
     const int M = s->M;
     const int method = resolve_method(s, p, o);
     const int grid = std::min(nE, s->nsm * 4);
+    if (s->lead[p].Mp != M) {
+        // period-2 lead: decimation of the two-slice supercell, then the end
+        // slice's Sigma from the surface block
+        if (method != KNIT_LEAD_DECIMATION)
+            return fail(KNIT_ERR_INVALID, "lead %d has period 2: only DECIMATION applies", p);
+        const int Mp = s->lead[p].Mp;
+        const size_t MMp = (size_t)Mp * Mp;
+        const double eta = (o && o->eta > 0) ? o->eta : 1e-12;
+        const double tol = (o && o->tol > 0) ? o->tol : 1e-14;
+        const int maxit = (o && o->maxit > 0) ? o->maxit : 200;
+        CK(s->decw.ensure(sizeof(double2) * 8 * MMp * grid), "decimation workspace");
+        CK(s->p2g.ensure(sizeof(double2) * MMp * nE), "supercell g");
+        CK(s->p2s.ensure(sizeof(double2) * MMp * nE), "supercell sigma");
+        CK(s->p2t.ensure(sizeof(double2) * (size_t)M * M * grid), "block scratch");
+        CK(knit_launch_decimation(s->lead[p].H0, s->lead[p].V, Mp, Mp, p, dE, nE, eta, tol, maxit,
+                                  s->decw.as<double2>(), s->p2s.as<double2>(),
+                                  s->p2g.as<double2>(), lit, lst, grid, st),
+           "supercell decimation");
+        CK(knit_launch_sigma_block(s->lead[p].C, s->p2g.as<double2>(), M, Mp, p, nE,
+                                   s->p2t.as<double2>(), sig, grid, st),
+           "supercell self-energy");
+        (void)gout;
+        return KNIT_OK;
+    }
     if (method == KNIT_LEAD_MODES) {
         if (!s->lead[p].scalar)
             return fail(KNIT_ERR_INVALID, "lead %d: MODES needs lead_V = t * identity", p);
@@ -632,12 +661,16 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
         }
         rp[i + 1] = (int)cols.size();
     }
+    std::vector<double2> hC[2];
     for (int p = 0; p < 2; ++p) {
         Lead &ld = s->lead[p];
+        const int per = d->lead_Vperiod[p] <= 1 ? 1 : d->lead_Vperiod[p];
+        if (per != 1 && per != 2) {
+            knit_system_destroy(s);
+            return fail(KNIT_ERR_INVALID, "lead_Vperiod[%d] must be 0, 1 or 2", p);
+        }
         const void *hsrc = d->lead_H0[p] ? (const void *)d->lead_H0[p] : (const void *)d->H0;
-        const void *vsrc = d->lead_V[p] ? (const void *)d->lead_V[p] : (const void *)d->V;
-        if ((r = to_host(ld.hH0, hsrc, MM, "lead_H0")) != KNIT_OK ||
-            (r = to_host(ld.hV, vsrc, MM, "lead_V")) != KNIT_OK) {
+        if ((r = to_host(ld.hH0, hsrc, MM, "lead_H0")) != KNIT_OK) {
             knit_system_destroy(s);
             return r;
         }
@@ -645,11 +678,62 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
             knit_system_destroy(s);
             return fail(KNIT_ERR_INVALID, "lead_H0[%d] is not Hermitian", p);
         }
-        int b = block_structure(ld.hV.data(), M, B);
-        ld.vb = b == 0 ? M : b;   // dense coupling allowed for the decimation solver
-        ld.scalar = scalar_identity(ld.hV.data(), M, &ld.t2);
+        if (per == 1) {
+            const void *vsrc = d->lead_V[p] ? (const void *)d->lead_V[p] : (const void *)d->V;
+            if ((r = to_host(ld.hV, vsrc, MM, "lead_V")) != KNIT_OK) {
+                knit_system_destroy(s);
+                return r;
+            }
+            ld.Mp = M;
+            int b = block_structure(ld.hV.data(), M, B);
+            ld.vb = b == 0 ? M : b;   // dense coupling allowed for the decimation solver
+            ld.scalar = scalar_identity(ld.hV.data(), M, &ld.t2);
+            continue;
+        }
+        // period 2: [V_first, V_second], given or continuing the system's V
+        std::vector<double2> vv;
+        if (d->lead_V[p]) {
+            if ((r = to_host(vv, d->lead_V[p], 2 * MM, "lead_V")) != KNIT_OK) {
+                knit_system_destroy(s);
+                return r;
+            }
+        } else {
+            const int n0 = p == 0 ? 0 : L % P, n1 = p == 0 ? 1 % P : (L + 1) % P;
+            vv.assign(V.begin() + (size_t)n0 * MM, V.begin() + (size_t)(n0 + 1) * MM);
+            vv.insert(vv.end(), V.begin() + (size_t)n1 * MM, V.begin() + (size_t)(n1 + 1) * MM);
+        }
+        const double2 *Vf = vv.data(), *Vs = vv.data() + MM;
+        // supercell (surface slice first): left  H0c = [[H0, A], [A^+, H0]], coupling to the
+        // next cell outward [[0, 0], [B, 0]]; right H0c = [[H0, A^+], [A, H0]], coupling
+        // [[0, B], [0, 0]] (slice-forward orientation); A = V_second, B = V_first
+        const int Mp = 2 * M;
+        ld.Mp = Mp;
+        std::vector<double2> Hc((size_t)Mp * Mp, make_double2(0.0, 0.0)), Vc = Hc;
+        auto at = [&](std::vector<double2> &X, int i, int j) -> double2 & { return X[(size_t)i * Mp + j]; };
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                const double2 h = ld.hH0[(size_t)i * M + j];
+                const double2 a = Vs[(size_t)i * M + j], b = Vf[(size_t)i * M + j];
+                const double2 ad = make_double2(Vs[(size_t)j * M + i].x, -Vs[(size_t)j * M + i].y);
+                at(Hc, i, j) = h;
+                at(Hc, M + i, M + j) = h;
+                if (p == 0) {
+                    at(Hc, i, M + j) = a;
+                    at(Hc, M + i, j) = ad;
+                    at(Vc, M + i, j) = b;
+                } else {
+                    at(Hc, M + i, j) = a;
+                    at(Hc, i, M + j) = ad;
+                    at(Vc, i, M + j) = b;
+                }
+            }
+        ld.hH0 = Hc;
+        ld.hV = Vc;
+        hC[p].assign(Vf, Vf + MM);
+        ld.vb = Mp;
+        ld.scalar = 0;
     }
-    s->leads_same = std::equal(s->lead[0].hH0.begin(), s->lead[0].hH0.end(), s->lead[1].hH0.begin(),
+    s->leads_same = s->lead[0].Mp == M && s->lead[1].Mp == M && std::equal(s->lead[0].hH0.begin(), s->lead[0].hH0.end(), s->lead[1].hH0.begin(),
                                [](double2 a, double2 b) { return a.x == b.x && a.y == b.y; }) &&
                     std::equal(s->lead[0].hV.begin(), s->lead[0].hV.end(), s->lead[1].hV.begin(),
                                [](double2 a, double2 b) { return a.x == b.x && a.y == b.y; });
@@ -668,8 +752,10 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
     }
     for (int p = 0; p < 2; ++p) {
         Lead &ld = s->lead[p];
-        if ((r = to_device(&ld.H0, ld.hH0.data(), MM, "lead_H0")) != KNIT_OK ||
-            (r = to_device(&ld.V, ld.hV.data(), MM, "lead_V")) != KNIT_OK) {
+        const size_t MMp = (size_t)ld.Mp * ld.Mp;
+        if ((r = to_device(&ld.H0, ld.hH0.data(), MMp, "lead_H0")) != KNIT_OK ||
+            (r = to_device(&ld.V, ld.hV.data(), MMp, "lead_V")) != KNIT_OK ||
+            (ld.Mp != M && (r = to_device(&ld.C, hC[p].data(), MM, "lead coupling")) != KNIT_OK)) {
             knit_system_destroy(s);
             return r;
         }
@@ -700,11 +786,13 @@ knit_status knit_system_destroy(knit_system s)
     for (int p = 0; p < 2; ++p) {
         cudaFree(s->lead[p].H0);
         cudaFree(s->lead[p].V);
+        cudaFree(s->lead[p].C);
         cudaFree(s->lead[p].U);
         cudaFree(s->lead[p].A);
     }
     DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
-                      &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos};
+                      &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
+                      &s->p2g, &s->p2s, &s->p2t};
     for (DevBuf *b : bufs) b->release();
     delete s;
     return KNIT_OK;
@@ -742,11 +830,13 @@ knit_status knit_lead_selfenergy(knit_system s, int32_t lead, const double *E, i
     }
     if (residual) {
         const int grid = std::min(nE, s->nsm * 4);
-        CK(s->decw.ensure(sizeof(double2) * MM * grid), "residual workspace");
+        const Lead &ld = s->lead[lead];
+        const bool cell2 = ld.Mp != s->M;   // residual of the supercell's g
+        CK(s->decw.ensure(sizeof(double2) * 3 * (size_t)ld.Mp * ld.Mp * grid), "residual workspace");
         CK(s->lres.ensure(sizeof(double) * nE), "residual");
-        CK(knit_launch_lead_residual(s->lead[lead].H0, s->lead[lead].V, s->M, s->lead[lead].vb, lead,
-                                     dE, nE, s->gL.as<double2>(), s->decw.as<double2>(),
-                                     s->lres.as<double>(), grid, st),
+        CK(knit_launch_lead_residual(ld.H0, ld.V, ld.Mp, ld.vb, lead, dE, nE,
+                                     cell2 ? s->p2g.as<double2>() : s->gL.as<double2>(),
+                                     s->decw.as<double2>(), s->lres.as<double>(), grid, st),
            "lead residual");
         bool hr = !is_device_ptr(residual);
         CK(cudaMemcpyAsync(residual, s->lres.p, sizeof(double) * nE,
@@ -1114,6 +1204,8 @@ knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_t
         return fail(KNIT_ERR_INVALID, "knit_lead_model_train: bad arguments");
     if (lead != 0 && lead != 1) return fail(KNIT_ERR_INVALID, "lead must be 0 or 1");
     if (s->M > 8) return fail(KNIT_ERR_INVALID, "learned leads support cells of at most 8 orbitals");
+    if (s->lead[lead].Mp != s->M)
+        return fail(KNIT_ERR_INVALID, "learned leads support period-1 leads only");
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<double> hE;

@@ -13,9 +13,38 @@
 //  * knit_decimation_kernel: Sancho-Rubio decimation (Lopez Sancho, Lopez
 //    Sancho & Rubio 1985) at E + i eta for general cells, one CTA per energy.
 //  * knit_lead_residual_kernel: max-norm of g - (E - H0 - V g V^dagger)^{-1}
-//    at eta = 0, the fixed-point check of either solver.
+//    at eta = 0, the fixed-point check of either solver (work: 3 M*M per CTA).
 
 #include "dense_fp64.cuh"
+
+// W = V G V^dagger (side 0) or V^dagger G V (side 1): elementwise for
+// block-diagonal V (blocks up to 4), as two products for a dense V (a
+// period-2 lead's supercell coupling).  tmp: M*M scratch.  Ends with a barrier.
+static __device__ void vgv64(const double2 *V, const double2 *G, int M, int vb, int side,
+                             double2 *tmp, double2 *W)
+{
+    if (vb <= 4) {
+        for (int q = threadIdx.x; q < M * M; q += blockDim.x) {
+            const int i = q / M, j = q - i * M;
+            W[q] = side == 0 ? vxvd64(V, G, M, vb, i, j) : vdxv64(V, G, M, vb, i, j);
+        }
+        __syncthreads();
+        return;
+    }
+    if (side == 0) {
+        gemm64(V, G, tmp, M);       // V G
+        gemm64_nc(tmp, V, W, M);    // (V G) V^dagger
+        return;
+    }
+    gemm64(G, V, tmp, M);           // G V
+    for (int q = threadIdx.x; q < M * M; q += blockDim.x) {
+        const int i = q / M, j = q - i * M;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int k = 0; k < M; ++k) acc = cfma(cconj(V[(size_t)k * M + i]), tmp[(size_t)k * M + j], acc);
+        W[q] = acc;
+    }
+    __syncthreads();
+}
 
 // Is the Hermitian matrix A (M x M, row-major, overwritten) positive
 // semidefinite up to -tol * max_k A_kk?  Semidefinite Cholesky: a pivot below
@@ -310,10 +339,10 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
         if (st == ST_OK) {
             // self-consistency at z: t1 = (z - H0 - V g V^dagger)^{-1} (left;
             // right with V^dagger, V) against g, relative max-norm
+            vgv64(V, G, M, vb, side, t2, t3);
             for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
                 int i = q / M, j = q - i * M;
-                double2 w2 = side == 0 ? vxvd64(V, G, M, vb, i, j) : vdxv64(V, G, M, vb, i, j);
-                double2 v = make_double2(-H0[q].x - w2.x, -H0[q].y - w2.y);
+                double2 v = make_double2(-H0[q].x - t3[q].x, -H0[q].y - t3[q].y);
                 if (i == j) v = cadd(v, z);
                 t1[q] = v;
             }
@@ -364,10 +393,7 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
         }
         if (st == ST_OK) {
             // Sigma = alpha0 g beta0: left V g V^dagger, right V^dagger g V
-            for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
-                int i = q / M, j = q - i * M;
-                S[q] = side == 0 ? vxvd64(V, G, M, vb, i, j) : vdxv64(V, G, M, vb, i, j);
-            }
+            vgv64(V, G, M, vb, side, t1, S);
         } else {
             for (int q = threadIdx.x; q < (int)MM; q += blockDim.x)
                 S[q] = make_double2(nan(""), nan(""));
@@ -404,13 +430,13 @@ knit_lead_residual_kernel(const double2 *H0, const double2 *V, int M, int vb, in
     p += sizeof(int);
     sc.piv = reinterpret_cast<int *>(p);
     const size_t MM = (size_t)M * M;
-    double2 *A = work + (size_t)blockIdx.x * MM;
+    double2 *A = work + (size_t)blockIdx.x * 3 * MM, *tmp = A + MM, *Wv = A + 2 * MM;
     for (int e = blockIdx.x; e < nE; e += gridDim.x) {
         const double2 *ge = g + (size_t)e * MM;
+        vgv64(V, ge, M, vb, side, tmp, Wv);
         for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
             int i = q / M, j = q - i * M;
-            double2 s = side == 0 ? vxvd64(V, ge, M, vb, i, j) : vdxv64(V, ge, M, vb, i, j);
-            double2 v = csub(make_double2(-H0[q].x, -H0[q].y), s);
+            double2 v = csub(make_double2(-H0[q].x, -H0[q].y), Wv[q]);
             if (i == j) v.x += E[e];
             A[q] = v;
         }
@@ -492,5 +518,52 @@ extern "C" cudaError_t knit_launch_lead_residual(const double2 *H0, const double
 {
     knit_lead_residual_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(H0, V, M, vb, side, E,
                                                                             nE, g, work, residual);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Self-energy on the system's end slice from a two-slice supercell lead:
+// g11 = the surface slice's block of the supercell surface function gcell
+// (Mp x Mp, Mp = 2M, per energy); left Sigma = C g11 C^dagger, right
+// Sigma = C^dagger g11 C.  One CTA per energy (grid-stride), tmp: M*M per CTA.
+extern "C" __global__ void __launch_bounds__(256)
+knit_sigma_block_kernel(const double2 *C, const double2 *gcell, int M, int Mp, int side, int nE,
+                        double2 *tmp, double2 *sigma)
+{
+    const size_t MM = (size_t)M * M, MMp = (size_t)Mp * Mp;
+    double2 *T = tmp + (size_t)blockIdx.x * MM;
+    for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+        const double2 *g = gcell + (size_t)e * MMp;
+        // T = C g11 (left) or C^dagger g11 (right)
+        for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+            const int i = q / M, j = q - i * M;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < M; ++k) {
+                const double2 c = side == 0 ? C[(size_t)i * M + k] : cconj(C[(size_t)k * M + i]);
+                acc = cfma(c, g[(size_t)k * Mp + j], acc);
+            }
+            T[q] = acc;
+        }
+        __syncthreads();
+        // Sigma = T C^dagger (left) or T C (right)
+        double2 *S = sigma + (size_t)e * MM;
+        for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
+            const int i = q / M, j = q - i * M;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < M; ++k) {
+                const double2 c = side == 0 ? cconj(C[(size_t)j * M + k]) : C[(size_t)k * M + j];
+                acc = cfma(T[(size_t)i * M + k], c, acc);
+            }
+            S[q] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+extern "C" cudaError_t knit_launch_sigma_block(const double2 *C, const double2 *gcell, int M, int Mp,
+                                               int side, int nE, double2 *tmp, double2 *sigma,
+                                               int grid, cudaStream_t stream)
+{
+    knit_sigma_block_kernel<<<grid, 256, 0, stream>>>(C, gcell, M, Mp, side, nE, tmp, sigma);
     return cudaGetLastError();
 }

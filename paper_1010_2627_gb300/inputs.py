@@ -35,7 +35,8 @@ class SliceSystem:
     block: int = 1
     sign: np.ndarray = field(default_factory=lambda: np.ones(1))
     lead_H0: tuple = ()            # (left, right) cells, (M, M) each
-    lead_V: tuple = ()             # (left, right) inter-cell couplings, (M, M) each
+    lead_V: tuple = ()             # (left, right) inter-cell couplings, (M, M) each, or
+                                   # (2, M, M) for a period-2 lead [V_first, V_second]
     name: str = ""
 
     def __post_init__(self):
@@ -78,15 +79,20 @@ def armchair(M: int, L: int, t: float = 2.7) -> SliceSystem:
     """Honeycomb ribbon as a brick wall: slice n = a zigzag row of M sites with
     in-row hopping t; vertical bonds between rows n-1 and n at sites x with
     (x + n) even, so V alternates with period 2.  The ribbon edges (x = 0 and
-    x = M - 1) run along the armchair direction."""
+    x = M - 1) run along the armchair direction.  The leads are the same clean
+    ribbon continued: period-2 leads whose couplings go on alternating
+    (left: H_{0,-1} = V_0, then V_1; right: H_{L,L-1} = V_{L mod 2}, then
+    V_{(L+1) mod 2})."""
     H0 = np.zeros((M, M), np.complex128)
     i = np.arange(M - 1)
     H0[i, i + 1] = t
     H0[i + 1, i] = t
     x = np.arange(M)
     V = np.stack([np.diag(t * ((x + k) % 2 == 0).astype(np.float64)) for k in range(2)])
-    return SliceSystem(M, L, H0, V.astype(np.complex128), lead_V=(V[0], V[1]),
-                       name=f"armchair M={M} L={L} t={t}")
+    V = V.astype(np.complex128)
+    left = np.stack([V[0], V[1]])
+    right = np.stack([V[L % 2], V[(L + 1) % 2]])
+    return SliceSystem(M, L, H0, V, lead_V=(left, right), name=f"armchair M={M} L={L} t={t}")
 
 
 _s0 = np.eye(2, dtype=np.complex128)

@@ -30,7 +30,8 @@ i32, f64 = ctypes.c_int32, ctypes.c_double
 
 class knit_system_desc(ctypes.Structure):
     _fields_ = [("M", i32), ("L", i32), ("block", i32), ("onsite_sign", P), ("H0", P),
-                ("onsite", P), ("V", P), ("Vperiod", i32), ("lead_H0", P * 2), ("lead_V", P * 2)]
+                ("onsite", P), ("V", P), ("Vperiod", i32), ("lead_H0", P * 2), ("lead_V", P * 2),
+                ("lead_Vperiod", i32 * 2)]
 
 
 class knit_lead_opts(ctypes.Structure):
@@ -140,8 +141,9 @@ def _opts(method=KNIT_LEAD_AUTO, eta=0.0, tol=0.0, maxit=0, models=(None, None))
 # C entry points with the C names
 
 def knit_system_create(M, L, H0, V, block=1, onsite_sign=None, onsite=None, lead_H0=(None, None),
-                       lead_V=(None, None)):
-    """Create a system (see include/knit.h); returns an opaque handle (int)."""
+                       lead_V=(None, None), lead_Vperiod=(0, 0)):
+    """Create a system (see include/knit.h); returns an opaque handle (int).
+    A lead_V[p] of shape (2, M, M) is a period-2 lead [V_first, V_second]."""
     H0 = _c128(H0)
     V = _c128(V)
     Vp = 1 if V.ndim == 2 else V.shape[0]
@@ -162,10 +164,13 @@ def knit_system_create(M, L, H0, V, block=1, onsite_sign=None, onsite=None, lead
             h = _c128(lead_H0[p])
             keep.append(h)
             d.lead_H0[p] = h.ctypes.data
+        d.lead_Vperiod[p] = int(lead_Vperiod[p])
         if lead_V[p] is not None:
             v = _c128(lead_V[p])
             keep.append(v)
             d.lead_V[p] = v.ctypes.data
+            if v.ndim == 3 and v.shape[0] == 2:
+                d.lead_Vperiod[p] = 2
     h = P()
     _check(load().knit_system_create(ctypes.byref(d), ctypes.byref(h)))
     return h.value

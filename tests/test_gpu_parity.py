@@ -207,6 +207,58 @@ def test_device_pointers_match_host(knit):
 
 
 # --------------------------------------------------------------------------
+# armchair (graphene) ribbons with period-2 leads (Sec. 6.3)
+
+def test_armchair_period2_lead_selfenergy(knit):
+    ss = inputs.armchair(16, 5)
+    sysk = knit.System(ss)
+    E = np.array([-4.1, -0.6, 0.35, 1.9, 5.2])
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, want_residual=True)
+        for e, Ee in enumerate(E):
+            So = oracle.decimation_period2(ss.H0, *ss.lead_V[lead], Ee, lead)
+            assert np.abs(S[e] - So).max() < 1e-8 * max(1.0, np.abs(So).max()), (lead, Ee)
+            assert res[e] < 1e-7, (lead, Ee, res[e])
+
+
+def armchair_oracle_T(ss, E, eps=None, method="dense"):
+    SL = oracle.decimation_period2(ss.H0, *ss.lead_V[0], E, 0)
+    SR = oracle.decimation_period2(ss.H0, *ss.lead_V[1], E, 1)
+    if method == "dense":
+        return oracle.dense(ss.H0, ss.V, eps, ss.L, E, SL, SR)["T_LR"]
+    return oracle.rgf(ss.H0, ss.V, eps, ss.L, E, SL, SR)["T"]
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_MIXED)])
+def test_armchair_clean_ribbon_integer_plateaus(knit, precision, tol):
+    ss = inputs.armchair(32, 12)
+    E = np.array([-6.3, -2.45, -0.7, 0.52, 1.85, 3.3, 7.1])
+    T, st = knit.System(ss).transmission(E, precision=precision)
+    assert (st == 0).all()
+    for e, Ee in enumerate(E):
+        To = armchair_oracle_T(ss, Ee)
+        n = round(To)
+        assert abs(To - n) < 1e-6
+        assert abs(T[e, 0] - To) / max(1, n) <= tol, (Ee, T[e, 0], To)
+
+
+@pytest.mark.parametrize("M,L,precision", [(24, 30, 0), (24, 30, 1), (64, 40, 1), (96, 9, 1)])
+def test_armchair_disordered_ribbon(knit, M, L, precision):
+    ss = inputs.armchair(M, L)
+    E = np.array([-2.9, 0.8, 4.4])
+    seeds = np.array([5], np.uint64)
+    W = 0.5 * 2.7
+    T, st = knit.System(ss).transmission(E, seeds, W=W, precision=precision)
+    assert (st == 0).all()
+    eps = oracle.onsite(5, L, M, W)
+    clean = knit.System(inputs.armchair(M, 2)).transmission(E)[0][:, 0]
+    tol = TOL_FP64 if precision == 0 else TOL_MIXED
+    for e, Ee in enumerate(E):
+        To = armchair_oracle_T(ss, Ee, eps, method="rgf")
+        assert abs(T[e, 0] - To) / max(1, round(clean[e])) <= tol, (Ee, T[e, 0], To)
+
+
+# --------------------------------------------------------------------------
 # LDOS (sewing)
 
 @pytest.mark.parametrize("saving_level", [-1, 1, 3, 5, 16])

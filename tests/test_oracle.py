@@ -334,3 +334,36 @@ def test_mlp_reference_special_cases():
     assert np.array_equal(y, np.array([[0.25, -1.5], [0.25, -1.5]]))
     loss, g = mlp.loss_and_grad(p, dims, np.array([[0.3]]), np.array([[0.25, -1.5]]))
     assert loss == 0.0 and not g.any()
+
+
+# --------------------------------------------------------------------------
+# period-2 leads (armchair ribbons): the two-slice cell
+
+def test_period2_lead_with_equal_couplings_is_the_period1_lead():
+    rng = np.random.default_rng(21)
+    M = 4
+    A = rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))
+    H0 = (A + A.conj().T) / 4
+    V = 0.8 * (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))) / np.sqrt(M)
+    for side in (0, 1):
+        for E in (-0.7, 0.3, 1.1):
+            _, S1, _ = oracle.decimation(H0, V, E, side, eta=1e-10)
+            S2 = oracle.decimation_period2(H0, V, V, E, side, eta=1e-10)
+            assert np.abs(S2 - S1).max() < 1e-8 * max(1.0, np.abs(S1).max()), (side, E)
+
+
+def test_clean_armchair_ribbon_has_integer_plateaus():
+    """A clean armchair ribbon between leads made of the same ribbon transmits
+    an integer number of channels, the same in both directions."""
+    M, L = 8, 6
+    ss = inputs.armchair(M, L)
+    seen = set()
+    for E in (0.45, 1.3, 2.2, 3.1, -1.7):
+        SL = oracle.decimation_period2(ss.H0, *ss.lead_V[0], E, 0)
+        SR = oracle.decimation_period2(ss.H0, *ss.lead_V[1], E, 1)
+        d = oracle.dense(ss.H0, ss.V, None, L, E, SL, SR)
+        T = d["T_LR"]
+        assert abs(T - round(T)) < 1e-6, (E, T)
+        assert abs(d["T_RL"] - T) < 1e-8
+        seen.add(round(T))
+    assert max(seen) >= 1 and len(seen) >= 2
