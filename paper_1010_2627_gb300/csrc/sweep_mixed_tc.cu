@@ -17,13 +17,15 @@
 //  * Gv' is cut at a per-row scale sigma_i into seven digits (56 bits),
 //    Gv' ~= sigma_i 2^-8 sum_p e_p 2^-8p;
 //  * the complex product is the real product of [[Gr, -Gi], [Gi, Gr]]
-//    (128 x 128) with [Xr; Xi] (128 x 64), run as 18 digit products
-//    (p + q <= 6, q <= 2) per K-chunk of 16 on tcgen05.mma kind::f16 (bf16 in,
-//    f32 accumulate in tensor memory).  Digits are stored pre-scaled by
-//    2^-8p / 2^-8q, so every product of one anti-diagonal d = p + q is an
-//    integer multiple of 2^-8d below 2^24 in magnitude: the diagonals
-//    d = 0 .. 3 accumulate exactly in four accumulators, d >= 4 share a fifth;
-//  * the five accumulators are summed in double-float, scaled by
+//    (128 x 128) with [Xr; Xi] (128 x 64): the 18 digit products
+//    (p + q <= 6, q <= 2) of a K-chunk of 16 run as 7 tcgen05.mma kind::f16
+//    (bf16 in, f32 accumulate in tensor memory), one per A digit p against
+//    the chunk's B digits q = 0 .. min(2, 6 - p) stored side by side
+//    (N = 64 per digit), so product (p, q) lands in accumulator p + q.
+//    Digits are stored pre-scaled by 2^-8p / 2^-8q, so every product of one
+//    anti-diagonal d = p + q is an integer multiple of 2^-8d below 2^24 in
+//    magnitude: each of the seven accumulators d = 0 .. 6 sums exactly;
+//  * the seven accumulators are summed in double-float, scaled by
 //    sigma_i tau_n 2^-16, the identity added, and R rounded once to fp32;
 //  * g = X' (I + R + R^2 + ...) with as many terms as max|R_ij| asks for,
 //    the product X' S accumulated error-free where max|R_ij| is large
@@ -49,8 +51,7 @@ constexpr int NTT = 512, TYT = 16, TXT = 32;   // 16 x 32 thread grid
 constexpr int RA = MPT / TYT, RB = MPT / TXT;
 constexpr int NDA = 7;                // digits of Gv
 constexpr int NDB = 3;                // digits of X
-constexpr int NPROD = 18;             // digit products with q <= 2, p + q <= 6
-constexpr int NACC = 5;               // accumulators: d = 0, 1, 2, 3 exact, d >= 4 shared
+constexpr int NACC = 7;               // accumulators d = p + q = 0 .. 6, each exact
 constexpr int A_TILE = 128 * 16 * 2;  // bytes of one 128 x 16 bf16 tile
 constexpr int B_TILE = 64 * 16 * 2;   // bytes of one 64 x 16 bf16 tile
 constexpr int RS = MPT + 1;           // padded row stride of R
@@ -59,8 +60,6 @@ constexpr int MAX_NNZ = 256;          // sparse H0 rows cached in shared memory 
 constexpr uint32_t TMEM_COLS = 512;   // 5 accumulators x 64 columns, rounded up
 constexpr long WAIT_LIMIT = 1L << 24; // bounded mbarrier polling
 
-__constant__ int c_prod_p[NPROD] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 4, 3, 2, 5, 4, 3, 6, 5, 4};
-__constant__ int c_prod_q[NPROD] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 0, 1, 2, 0, 1, 2, 0, 1, 2};
 
 struct TcSmem {
     float2 X[MPT * MPT];                         // inverse, then X' (rounded)
@@ -158,6 +157,13 @@ KNIT_DEV void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
                  : "r"(taddr));
 }
 
+// zero 8 consecutive accumulator columns of the warp's 32 TMEM lanes
+KNIT_DEV void tmem_zero8(uint32_t taddr)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
+                 ::"r"(taddr), "r"(0u) : "memory");
+}
+
 KNIT_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 KNIT_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 KNIT_DEV void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -188,7 +194,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
     const int tid = threadIdx.x, ty = tid / TXT, tx = tid % TXT;
     const int warp = tid >> 5, lane = tid & 31;
     // D f32, A and B bf16, both K-major, N = 64, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) |
+    const uint32_t idesc_n64 = (1u << 4) | (1u << 7) | (1u << 10) |
                            ((128u >> 4) << 24);
 
     if (warp == 0) {
@@ -368,11 +374,11 @@ knit_sweep_mixed_tc_kernel(InstDev in)
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
                     const int K = k + 64 * part;
-                    unsigned char *t = sm.w.s.bdig + (K >> 4) * B_TILE;
+                    unsigned char *t = sm.w.s.bdig + (K >> 4) * NDB * B_TILE;
                     float sc = 1.f;
 #pragma unroll
                     for (int q = 0; q < NDB; ++q) {
-                        put_bf16x2(t + q * 8 * B_TILE, nn, K & 15, d[0][part][q] * sc,
+                        put_bf16x2(t + q * B_TILE, nn, K & 15, d[0][part][q] * sc,
                                    d[1][part][q] * sc);
                         sc *= 0.00390625f;
                     }
@@ -380,7 +386,18 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             }
 
             // products: four groups, each two K-chunks sharing Gv columns 16g..16g+15
-            int first = (1 << NACC) - 1;   // accumulators not yet written this slice
+            // accumulators to zero (each warp the columns its epilogue reads), so
+            // that every product accumulates
+            {
+                tc_fence_after();
+                const uint32_t tz = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * (warp >> 2);
+#pragma unroll
+                for (int dacc = 0; dacc < NACC; ++dacc) {
+                    tmem_zero8(tz + 64 * dacc);
+                    tmem_zero8(tz + 64 * dacc + 8);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
             for (int g = 0; g < 4 && !timed_out; ++g) {
                 if (g > 0) {
                     const int ok = tid == 0 ? mbar_wait(&sm.mbar, phase) : 1;
@@ -426,17 +443,18 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                 __syncthreads();
                 if (tid == 0) {
                     tc_fence_after();
+                    // one MMA per A digit p against the B digits q = 0 .. min(2, 6 - p)
+                    // of the chunk, stored contiguously (N = 64 per digit): products
+                    // (p, q) land in accumulators p + q, i.e. columns 64 p ..
                     for (int slot = 0; slot < 2; ++slot) {
                         const int chunk = g + 4 * slot;
-                        for (int pr = 0; pr < NPROD; ++pr) {
-                            const int p = c_prod_p[pr], q = c_prod_q[pr];
-                            const int acc = min(p + q, NACC - 1);
+                        const uint64_t bd = smem_desc(smem_u32(sm.w.s.bdig + chunk * NDB * B_TILE));
+#pragma unroll
+                        for (int p = 0; p < NDA; ++p) {
+                            const uint32_t nq = (uint32_t)min(NDB, NDA - p);
                             const uint64_t ad =
                                 smem_desc(smem_u32(sm.u.adig + (slot * NDA + p) * A_TILE));
-                            const uint64_t bd =
-                                smem_desc(smem_u32(sm.w.s.bdig + (q * 8 + chunk) * B_TILE));
-                            mma_bf16(tmem + acc * 64, ad, bd, idesc, (first >> acc) & 1 ? 0u : 1u);
-                            first &= ~(1 << acc);
+                            mma_bf16(tmem + 64 * p, ad, bd, idesc_n64 | (((64u * nq) >> 3) << 17), 1u);
                         }
                     }
                     mma_commit(&sm.mbar);
@@ -453,9 +471,9 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             }
             tc_fence_after();
 
-            // R = I + Gv' X' = I + sigma_i tau_n 2^-16 (D0 + D1 + D2 + D3 + D4+):
+            // R = I + Gv' X' = I + sigma_i tau_n 2^-16 (D0 + ... + D6):
             // lane m of warp w holds row 32 (w % 4) + lane of [Re; Im],
-            // columns 16 (w / 4) ..; the five accumulators are summed as
+            // columns 16 (w / 4) ..; the seven accumulators are summed as
             // double-float before the single rounding to the stored R
             float rloc = 0.f;
             {
@@ -465,23 +483,36 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                 float *const Rf = reinterpret_cast<float *>(sm.u.R);
                 const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0;
                 for (int j8 = 0; j8 < 16; j8 += 8) {
-                    uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
+                    uint32_t v0[8], v1[8], v2[8], v3[8];
+                    float hsum[8], lsum[8];
                     tmem_ld8(tb + j8, v0);
                     tmem_ld8(tb + 64 + j8, v1);
                     tmem_ld8(tb + 128 + j8, v2);
                     tmem_ld8(tb + 192 + j8, v3);
-                    tmem_ld8(tb + 256 + j8, v4);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int jx = 0; jx < 8; ++jx) {
-                        const int nn = c0 + j8 + jx;
                         float hs, ls, t, te;
                         two_sum(__uint_as_float(v0[jx]), __uint_as_float(v1[jx]), hs, ls);
                         two_sum(hs, __uint_as_float(v2[jx]), t, te);
                         ls += te;
                         two_sum(t, __uint_as_float(v3[jx]), hs, te);
+                        hsum[jx] = hs;
+                        lsum[jx] = ls + te;
+                    }
+                    tmem_ld8(tb + 256 + j8, v0);
+                    tmem_ld8(tb + 320 + j8, v1);
+                    tmem_ld8(tb + 384 + j8, v2);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int jx = 0; jx < 8; ++jx) {
+                        const int nn = c0 + j8 + jx;
+                        float hs = hsum[jx], ls = lsum[jx], t, te;
+                        two_sum(hs, __uint_as_float(v0[jx]), t, te);
                         ls += te;
-                        two_sum(hs, __uint_as_float(v4[jx]), t, te);
+                        two_sum(t, __uint_as_float(v1[jx]), hs, te);
+                        ls += te;
+                        two_sum(hs, __uint_as_float(v2[jx]), t, te);
                         ls += te;
                         const float sc = pow2f(re + sm.cexp[nn] - 16);
                         hs = t * sc;
