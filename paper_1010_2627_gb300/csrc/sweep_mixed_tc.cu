@@ -57,7 +57,7 @@ constexpr int B_TILE = 64 * 16 * 2;   // bytes of one 64 x 16 bf16 tile
 constexpr int RS = MPT + 1;           // padded row stride of R
 constexpr int GJ_NB = 8;              // Gauss-Jordan panel width
 constexpr int MAX_NNZ = 256;          // sparse H0 rows cached in shared memory up to this
-constexpr uint32_t TMEM_COLS = 512;   // 5 accumulators x 64 columns, rounded up
+constexpr uint32_t TMEM_COLS = 512;   // 7 accumulators x 64 columns, rounded up
 constexpr long WAIT_LIMIT = 1L << 24; // bounded mbarrier polling
 
 
