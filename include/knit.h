@@ -171,6 +171,29 @@ knit_status knit_transmission_sigma(knit_system sys, const double *E, int32_t nE
                                     const knit_c128 *sigmaL, const knit_c128 *sigmaR,
                                     int32_t precision, double *T, int32_t *status, void *stream);
 
+/* Transmission eigenvalues and shot noise (Sec. 8: "conductance, shot noise,
+ * transmission eigenvalues"; Sec. 2.3: T_kl is the trace of
+ * G_kl Gamma_l G_kl^+ Gamma_k, whose eigenvalues are the transmission
+ * eigenvalues tau_n).  Instances as for knit_transmission.  For instance i:
+ *   tau   (nE*nS*M, required): the M eigenvalues of the Hermitian matrix
+ *         Gamma_R^{1/2} G_L1 Gamma_L G_L1^dagger Gamma_R^{1/2}, in decreasing
+ *         order -- the transmission eigenvalues, in [0, 1] up to rounding,
+ *         followed by (numerically) zero ones for closed channels;
+ *   noise (nE*nS, optional): sum_n tau_n (1 - tau_n), the zero-temperature
+ *         shot noise in units of 2 e^3 |V| / h (Fano factor noise / T);
+ *   T, status (optional): as for knit_transmission (T = sum_n tau_n up to
+ *         rounding).
+ * Instances with a non-zero status get NaN in tau and noise.  The matrix is
+ * formed from G_LL, the last slice's diagonal block of the sweep (FP64 or
+ * mixed, as `precision` selects), by the unitarity identity of the retarded
+ * function, and diagonalised in FP64 (cyclic Jacobi).  M <= 256; device
+ * workspace ~2 n M^2 complex128 (n = nE*nS). */
+knit_status knit_transmission_eigenvalues(knit_system sys, const double *E, int32_t nE,
+                                          const uint64_t *seeds, int32_t nS, double W,
+                                          int32_t precision, const knit_lead_opts *opts,
+                                          double *tau, double *noise, double *T, int32_t *status,
+                                          void *stream);
+
 /* Local density of states (Sec. 5.3 D knitting followed by sewing):
  * ldos (nE*nS*L*M, row-major [i][n][x]) receives -Im G_nn[x][x]/pi; T
  * (optional) the transmission; status (optional) per instance (ldos of an

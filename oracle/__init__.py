@@ -23,6 +23,9 @@ ctypes:
                      sewing), plain loops
 * ``rgf_batch``      ``rgf`` over many instances on all host cores (the CPU
                      baseline)
+* ``transmission_eigenvalues``, ``shot_noise``
+                     the eigenvalues of the matrix inside Sec. 2.3's
+                     transmission trace, and sum tau (1 - tau)
 * ``onsite``         counter-based Anderson disorder (Sec. 6.1)
 
 Parity status: every function here is pinned by ``tests/test_oracle.py``
@@ -77,7 +80,7 @@ def _load():
             lib.orc_dense_flat.restype = i32
             lib.orc_dense_flat.argtypes = [i32, i32, P, P, P, i32, f64, P, P, P, P, P, P, P]
             lib.orc_rgf_flat.restype = i32
-            lib.orc_rgf_flat.argtypes = [i32, i32, P, P, P, i32, f64, P, P, P, P, P]
+            lib.orc_rgf_flat.argtypes = [i32, i32, P, P, P, i32, f64, P, P, P, P, P, P]
             lib.orc_dense_general.restype = i32
             lib.orc_dense_general.argtypes = [i32, P, f64, i32, P, P, i32, P, P, P]
             lib.orc_rgf_batch.restype = i32
@@ -241,18 +244,49 @@ def dense_general(H, E: float, idx0, Sig0, idx1, Sig1):
 
 
 def rgf(H0, V, eps, L: int, E: float, SigL, SigR, want_ldos: bool = False):
-    """The slice-by-slice method: returns dict(T, ldos, G11)."""
+    """The slice-by-slice method: returns dict(T, ldos, G11, G1L)."""
     H0, V, eps, M = _sys_arrays(H0, V, eps, L)
     SigL = _c(SigL, np.complex128)
     SigR = _c(SigR, np.complex128)
     T = np.empty(1)
     ldos = np.empty((L, M)) if want_ldos else None
     G11 = np.empty((M, M), np.complex128) if want_ldos else None
+    G1L = np.empty((M, M), np.complex128)
     rc = _load().orc_rgf_flat(M, L, _p(H0), _p(eps), _p(V), V.shape[0], E, _p(SigL), _p(SigR),
-                              _p(T), _p(ldos), _p(G11))
+                              _p(T), _p(ldos), _p(G11), _p(G1L))
     if rc != OK:
         raise OracleError(rc, "rgf")
-    return dict(T=float(T[0]), ldos=ldos, G11=G11)
+    return dict(T=float(T[0]), ldos=ldos, G11=G11, G1L=G1L)
+
+
+def _gamma(Sig):
+    Sig = np.asarray(Sig, dtype=np.complex128)
+    return 1j * (Sig - Sig.conj().T)
+
+
+def _psd_sqrt(G):
+    w, U = np.linalg.eigh((G + G.conj().T) / 2)
+    return (U * np.sqrt(np.clip(w, 0.0, None))) @ U.conj().T
+
+
+def transmission_eigenvalues(G1L, SigL, SigR):
+    """Transmission eigenvalues tau_n, decreasing (M values).
+
+    Sec. 2.3 writes T_kl as the trace of G_kl Gamma_l G_kl^+ Gamma_k; with
+    k = L (slice 1), l = R (slice L) its eigenvalues are the tau_n, taken here
+    in the Hermitian form Gamma_L^{1/2} G_1L Gamma_R G_1L^+ Gamma_L^{1/2}
+    (same spectrum; Gamma^{1/2} and the eigenvalues by numpy's Hermitian
+    eigensolver).  Gamma = i (Sigma - Sigma^+)."""
+    S = _psd_sqrt(_gamma(SigL))
+    G1L = np.asarray(G1L, dtype=np.complex128)
+    H = S @ G1L @ _gamma(SigR) @ G1L.conj().T @ S
+    return np.linalg.eigvalsh((H + H.conj().T) / 2)[::-1].copy()
+
+
+def shot_noise(tau):
+    """sum_n tau_n (1 - tau_n): zero-temperature shot noise in units of 2 e^3 |V| / h."""
+    tau = np.asarray(tau, dtype=np.float64)
+    return float(np.sum(tau * (1.0 - tau)))
 
 
 def rgf_batch(H0, V, L: int, E, seeds, W, SigL, SigR, sig_index, block: int = 1, sign=None,

@@ -426,10 +426,11 @@ out:
  * Backward (only if ldos != NULL): G_{L-1,L-1} = g_{L-1},
  *           G_{n,n} = g_n + g_n V_{n+1}^dagger G_{n+1,n+1} V_{n+1} g_n,
  *           ldos[n*M + x] = -Im G_{n,n}[x][x] / pi.
- * G11_out (M x M) receives G_{0,0} of the full system when ldos is computed.
+ * G11_out (M x M) receives G_{0,0} of the full system when ldos is computed;
+ * G1L_out (M x M, optional) receives G_{0,L-1}.
  * Returns ORC_OK, ORC_ERR_SINGULAR or ORC_ERR_OOM. */
 int orc_rgf(const orc_system *s, double E, const cplx *SigL, const cplx *SigR,
-            double *T, double *ldos, cplx *G11_out)
+            double *T, double *ldos, cplx *G11_out, cplx *G1L_out)
 {
     int M = s->M, L = s->L;
     size_t MM = (size_t)M * M;
@@ -472,6 +473,7 @@ int orc_rgf(const orc_system *s, double E, const cplx *SigL, const cplx *SigR,
     gamma_of(M, SigL, Ga);
     gamma_of(M, SigR, Gb);
     if (T) *T = trace_gxgx(M, Ga, G1n, Gb);
+    if (G1L_out) memcpy(G1L_out, G1n, sizeof(cplx) * MM);
     if (keep) {
         /* sewing: G_{n,n} from G_{n+1,n+1}; Gnn held in gprev */
         memcpy(gprev, gs + (size_t)(L - 1) * MM, sizeof(cplx) * MM);
@@ -514,7 +516,7 @@ int orc_rgf_batch(int M, int L, const cplx *H0, const cplx *V, int Vperiod, int 
         orc_onsite_fill(seed[i], L, M, block, sign, W[i], eps);
         orc_system s = {M, L, H0, eps, V, Vperiod};
         size_t off = (size_t)sig_index[i] * M * M;
-        status[i] = orc_rgf(&s, E[i], SigL + off, SigR + off, &T[i], NULL, NULL);
+        status[i] = orc_rgf(&s, E[i], SigL + off, SigR + off, &T[i], NULL, NULL, NULL);
         free(eps);
     }
     for (int i = 0; i < nInst; ++i)
@@ -542,10 +544,10 @@ int orc_dense_flat(int M, int L, const cplx *H0, const double *eps, const cplx *
 
 int orc_rgf_flat(int M, int L, const cplx *H0, const double *eps, const cplx *V, int Vperiod,
                  double E, const cplx *SigL, const cplx *SigR, double *T, double *ldos,
-                 cplx *G11)
+                 cplx *G11, cplx *G1L)
 {
     orc_system s = {M, L, H0, eps, V, Vperiod};
-    return orc_rgf(&s, E, SigL, SigR, T, ldos, G11);
+    return orc_rgf(&s, E, SigL, SigR, T, ldos, G11, G1L);
 }
 
 /* The plain definition for an arbitrary geometry with two leads (Sec. 2.2

@@ -29,6 +29,10 @@ extern "C" cudaError_t knit_launch_ldos_mixed(const InstDev *, int, int, int, in
 extern "C" size_t knit_mixed_wide_work_bytes(int);
 extern "C" cudaError_t knit_launch_mixed_wide(const InstDev *, int, int, void *, cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
+extern "C" cudaError_t knit_launch_gamma_sqrt(const double2 *, int, int, double2 *, double2 *,
+                                              cudaStream_t);
+extern "C" cudaError_t knit_launch_tau(const double2 *, const double2 *, int, int, int, const int *,
+                                       double2 *, double2 *, int, double *, double *, cudaStream_t);
 extern "C" cudaError_t knit_launch_modes_sigma(const double2 *, const double2 *, int, double,
                                                const double *, int, double2 *, double2 *, int,
                                                cudaStream_t);
@@ -149,6 +153,7 @@ struct knit_system_s {
     // grow-only workspaces
     DevBuf E, seeds, T, status, queue, sigL, sigR, gL, gR, lst, lit, lres, work, ckpt, decw, ldos;
     DevBuf p2g, p2s, p2t;   // period-2 leads: supercell g and Sigma, block-product scratch
+    DevBuf gll, tq, tw, ts, tg, tau, noise;   // transmission eigenvalues: G_LL, Q, scratch, out
 
     SysDev dev() const
     {
@@ -792,7 +797,8 @@ knit_status knit_system_destroy(knit_system s)
     }
     DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
                       &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
-                      &s->p2g, &s->p2s, &s->p2t};
+                      &s->p2g, &s->p2s, &s->p2t, &s->gll, &s->tq, &s->tw, &s->ts, &s->tg,
+                      &s->tau, &s->noise};
     for (DevBuf *b : bufs) b->release();
     delete s;
     return KNIT_OK;
@@ -909,6 +915,73 @@ knit_status knit_transmission_sigma(knit_system s, const double *E, int32_t nE,
     if (!sigmaL || !sigmaR) return fail(KNIT_ERR_INVALID, "sigmaL and sigmaR are required");
     return transmission_impl(s, E, nE, seeds, nS, W, sigmaL, sigmaR, precision, nullptr, T, status,
                              stream);
+}
+
+knit_status knit_transmission_eigenvalues(knit_system s, const double *E, int32_t nE,
+                                          const uint64_t *seeds, int32_t nS, double W,
+                                          int32_t precision, const knit_lead_opts *opts,
+                                          double *tau, double *noise, double *T, int32_t *status,
+                                          void *stream)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if ((r = check_batch(s, E, nE, nS, precision, W)) != KNIT_OK) return r;
+    if (!tau) return fail(KNIT_ERR_INVALID, "tau is NULL");
+    if (s->M > 256) return fail(KNIT_ERR_INVALID, "transmission eigenvalues need M <= 256 (M = %d)", s->M);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int M = s->M;
+    const size_t MM = (size_t)M * M;
+    const int n = nE * nS;
+    InstDev in{};
+    in.n = n;
+    in.nS = nS;
+    in.W = W;
+    if ((r = stage_in(s->E, E, (size_t)nE, st, &in.E, "E")) != KNIT_OK) return r;
+    if ((r = stage_in(s->seeds, seeds, (size_t)nS, st, &in.seeds, "seeds")) != KNIT_OK) return r;
+    const int *lst;
+    if ((r = both_sigmas(s, in.E, nE, opts, st, &in.sigL, &in.sigR, &lst)) != KNIT_OK) return r;
+    int *l0 = s->lst.as<int>();
+    combine_status<<<(nE + 255) / 256, 256, 0, st>>>(l0, l0 + nE, nE);
+    CK(cudaGetLastError(), "status combine");
+    in.lstatus = l0;
+    // the status array is always needed on the device: it marks the
+    // instances whose eigenvalues are undefined
+    bool hT = false, hSt = false, hTau = false, hNoise = false;
+    if ((r = stage_out(s->T, T, (size_t)n, &in.T, &hT, "T")) != KNIT_OK) return r;
+    if (!in.T) {
+        CK(s->T.ensure(sizeof(double) * n), "T");
+        in.T = s->T.as<double>();
+    }
+    if ((r = stage_out(s->status, (int *)status, (size_t)n, &in.status, &hSt, "status")) != KNIT_OK)
+        return r;
+    if (!in.status) {
+        CK(s->status.ensure(sizeof(int) * n), "status");
+        in.status = s->status.as<int>();
+    }
+    double *dtau, *dnoise;
+    if ((r = stage_out(s->tau, tau, (size_t)n * M, &dtau, &hTau, "tau")) != KNIT_OK) return r;
+    if ((r = stage_out(s->noise, noise, (size_t)n, &dnoise, &hNoise, "noise")) != KNIT_OK) return r;
+    CK(s->gll.ensure(sizeof(double2) * MM * n), "G_LL workspace");
+    in.GLL = s->gll.as<double2>();
+    if ((r = run_sweep(s, in, precision, st)) != KNIT_OK) return r;
+    // Gamma_R^{1/2} per energy, then Q per instance and its eigenvalues
+    CK(s->tg.ensure(sizeof(double2) * 2 * MM * nE), "Gamma workspace");
+    CK(s->ts.ensure(sizeof(double2) * MM * nE), "Gamma_R^1/2");
+    CK(knit_launch_gamma_sqrt(in.sigR, M, nE, s->tg.as<double2>(), s->ts.as<double2>(), st),
+       "Gamma_R^1/2 launch");
+    const int grid = std::max(1, std::min(n, 8 * s->nsm));
+    CK(s->tq.ensure(sizeof(double2) * MM * n), "Q workspace");
+    CK(s->tw.ensure(sizeof(double2) * 2 * MM * grid), "Q scratch");
+    CK(knit_launch_tau(in.GLL, s->ts.as<double2>(), M, n, nS, in.status, s->tq.as<double2>(),
+                       s->tw.as<double2>(), grid, dtau, dnoise, st),
+       "eigenvalue launch");
+    if (hTau) CK(cudaMemcpyAsync(tau, dtau, sizeof(double) * n * M, cudaMemcpyDeviceToHost, st), "tau out");
+    if (hNoise)
+        CK(cudaMemcpyAsync(noise, dnoise, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "noise out");
+    if (hT) CK(cudaMemcpyAsync(T, in.T, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
+    if (hSt)
+        CK(cudaMemcpyAsync(status, in.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
+    return finish(st, hTau || hNoise || hT || hSt, "knit_transmission_eigenvalues");
 }
 
 knit_status knit_ldos(knit_system s, const double *E, int32_t nE, const uint64_t *seeds,

@@ -213,6 +213,7 @@ struct InstDev {
     const int *out_index;      // output position of each instance, or nullptr
     const int *lstatus;        // lead-solver status (grid: per energy; else per instance)
     int *queue;                // one int, zeroed before launch: next queue position
+    double2 *GLL;              // optional: G_LL (M x M, complex128) at out position * M * M
 };
 
 // parameters of one instance

@@ -946,4 +946,14 @@ __device__ double ward_T(const float2 *Gh, const float2 *Gl, double2 *G, const d
     return block_sum(t, red);
 }
 
+// G_LL from ward_T's scratch G (MP x MP, row-major) into dst (M x M)
+template <int MP, int NTH = NT>
+__device__ void store_gll(const double2 *G, int M, double2 *dst)
+{
+    for (int e = threadIdx.x; e < M * M; e += NTH) {
+        const int i = e / M, j = e - i * M;
+        dst[e] = G[i * MP + j];
+    }
+}
+
 }  // namespace mixed

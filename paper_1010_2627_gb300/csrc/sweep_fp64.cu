@@ -170,6 +170,7 @@ knit_sweep_fp64_kernel(InstDev in, int Mmax, double2 *work, int use_smem)
         int st = forward(s, ip, b, P, Q, F, nullptr, 1);
         double T = 0.0;
         if (st == ST_OK) {
+            if (in.GLL) copy_mat(P, in.GLL + (size_t)ip.out * s.M * s.M, s.M);   // G_LL = g_{L-1}
             gemm64_gamma(Q, ip.SR, F, s.M);     // G Gamma_R
             gemm64_nc(F, Q, P, s.M);            // G Gamma_R G^dagger
             T = trace_gamma64(ip.SL, P, s.M, b.red);

@@ -272,6 +272,8 @@ knit_sweep_mixed_kernel(InstDev in)
         double T = 0.0;
         if (st == ST_OK) {
             T = ward_T<MP>(sm.Gh, sm.Gl, reinterpret_cast<double2 *>(sm.X), ip.SR, M, sm.red);
+            if (in.GLL)
+                store_gll<MP>(reinterpret_cast<double2 *>(sm.X), M, in.GLL + (size_t)ip.out * M * M);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {

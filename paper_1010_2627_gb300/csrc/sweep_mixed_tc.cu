@@ -556,6 +556,8 @@ knit_sweep_mixed_tc_kernel(InstDev in)
         double T = 0.0;
         if (st == ST_OK) {
             T = ward_T<MPT, NTT>(Gh, Gl, reinterpret_cast<double2 *>(sm.X), SR, M, sm.red);
+            if (in.GLL)
+                store_gll<MPT, NTT>(reinterpret_cast<double2 *>(sm.X), M, in.GLL + (size_t)ip.out * M * M);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {

@@ -374,6 +374,7 @@ knit_sweep_mixed_wide_kernel(InstDev in, WideWork<MP> *work)
         double T = 0.0;
         if (st == ST_OK) {
             T = ward_T<MP, NTW>(wk.Gh, wk.Gl, wk.u.G, ip.SR, M, sm.red);
+            if (in.GLL) store_gll<MP, NTW>(wk.u.G, M, in.GLL + (size_t)ip.out * M * M);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {

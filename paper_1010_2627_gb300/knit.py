@@ -54,6 +54,7 @@ _SIGS = {
     "knit_transmission": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P]),
     "knit_transmission_sigma": (i32, [P, P, i32, P, i32, f64, P, P, i32, P, P, P]),
     "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, i32, P, P, P, P, P]),
+    "knit_transmission_eigenvalues": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
     "knit_lead_model_train": (i32, [P, i32, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64,
@@ -204,6 +205,17 @@ def knit_transmission_sigma(handle, E, seeds, W, sigmaL, sigmaR, precision, T, s
     _check(load().knit_transmission_sigma(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS),
                                           float(W), _ptr(sigmaL), _ptr(sigmaR), int(precision),
                                           _ptr(T), _ptr(status), _stream(stream)))
+
+
+def knit_transmission_eigenvalues(handle, E, seeds, W, precision, tau, noise=None, T=None,
+                                  status=None, opts=None, nE=None, nS=None, stream=None):
+    nE = len(E) if nE is None else nE
+    nS = (1 if seeds is None else len(seeds)) if nS is None else nS
+    _check(load().knit_transmission_eigenvalues(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS),
+                                                float(W), int(precision),
+                                                None if opts is None else ctypes.byref(opts),
+                                                _ptr(tau), _ptr(noise), _ptr(T), _ptr(status),
+                                                _stream(stream)))
 
 
 def knit_ldos(handle, E, seeds, W, saving_level, ldos, T=None, status=None, opts=None, nE=None,
@@ -384,6 +396,23 @@ class System:
         st = np.empty(len(E) * nS, np.int32)
         knit_transmission_sigma(self.handle, E, sd, W, _c128(SL), _c128(SR), precision, T, st)
         return T.reshape(len(E), nS), st.reshape(len(E), nS)
+
+    def transmission_eigenvalues(self, E, seeds=None, W=0.0, precision=KNIT_FP64,
+                                 method=KNIT_LEAD_AUTO):
+        """(tau, noise, T, status): tau (nE, nS, M) in decreasing order,
+        noise = sum tau (1 - tau), T and status as for transmission."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        nS = 1 if sd is None else len(sd)
+        n = len(E) * nS
+        tau = np.empty((n, self.M))
+        noise = np.empty(n)
+        T = np.empty(n)
+        st = np.empty(n, np.int32)
+        knit_transmission_eigenvalues(self.handle, E, sd, W, precision, tau, noise, T, st,
+                                      _opts(method))
+        return (tau.reshape(len(E), nS, self.M), noise.reshape(len(E), nS),
+                T.reshape(len(E), nS), st.reshape(len(E), nS))
 
     def ldos(self, E, seeds=None, W=0.0, saving_level=-1, method=KNIT_LEAD_AUTO,
              precision=KNIT_FP64):

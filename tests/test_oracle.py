@@ -367,3 +367,108 @@ def test_clean_armchair_ribbon_has_integer_plateaus():
         assert abs(d["T_RL"] - T) < 1e-8
         seen.add(round(T))
     assert max(seen) >= 1 and len(seen) >= 2
+
+
+# --------------------------------------------------------------------------
+# Transmission eigenvalues and shot noise (Sec. 8 capabilities; the
+# eigenvalues of the matrix inside Sec. 2.3's transmission trace)
+
+def _tau(ss, eps, E, SigL=None, SigR=None):
+    S = oracle.sigma_square(ss.M, 1.0, E) if SigL is None else SigL
+    SR = S if SigR is None else SigR
+    r = oracle.rgf(ss.H0, ss.V, eps, ss.L, E, S, SR)
+    return oracle.transmission_eigenvalues(r["G1L"], S, SR), r["T"]
+
+
+@pytest.mark.parametrize("E", [-1.3, 0.45, 1.7])
+def test_tau_single_impurity_closed_form(E):
+    """1D chain, one on-site impurity eps0: T = 1 / (1 + (eps0 / (2 t sin k))^2),
+    E = 2 t cos k (textbook scattering off a delta potential on a lattice)."""
+    L = 7
+    for eps0 in (0.3, -1.1, 2.5):
+        eps = np.zeros((L, 1))
+        eps[3, 0] = eps0
+        tau, T = _tau(inputs.chain(L), eps, E)
+        k = np.arccos(E / 2)
+        want = 1.0 / (1.0 + (eps0 / (2 * np.sin(k))) ** 2)
+        assert tau.shape == (1,)
+        assert abs(tau[0] - want) < 1e-12 and abs(T - want) < 1e-12
+        assert abs(oracle.shot_noise(tau) - want * (1 - want)) < 1e-12
+
+
+def test_tau_two_decoupled_chains():
+    """Two uncoupled chains (M = 2, no transverse hopping): the eigenvalues are
+    the two chains' transmissions, each the closed form above."""
+    L, E = 6, 0.8
+    ss = inputs.SliceSystem(2, L, np.zeros((2, 2), np.complex128), np.eye(2, dtype=np.complex128))
+    eps = np.zeros((L, 2))
+    eps[2, 0], eps[4, 1] = 0.7, -1.9
+    S1 = oracle.sigma_square(1, 1.0, E)[0, 0]
+    S = np.diag([S1, S1])
+    tau, T = _tau(ss, eps, E, S, S)
+    k = np.arccos(E / 2)
+    want = sorted((1 / (1 + (e / (2 * np.sin(k))) ** 2) for e in (0.7, -1.9)), reverse=True)
+    assert np.abs(tau - want).max() < 1e-12
+    assert abs(T - sum(want)) < 1e-12
+
+
+@pytest.mark.parametrize("M", [4, 7])
+def test_tau_clean_ribbon_is_zero_or_one(M):
+    """Clean ribbon: every open transverse mode transmits fully, the rest not
+    at all, so the eigenvalues are N_ch ones and M - N_ch zeros; no noise."""
+    ek = 2 * np.cos(np.arange(1, M + 1) * np.pi / (M + 1))
+    for E in inputs.energy_grid(-3.7, 3.7, 13):
+        if np.min(np.abs(np.abs(E - ek) - 2)) < 1e-3:
+            continue
+        nopen = int(np.sum(np.abs(E - ek) < 2))
+        tau, _ = _tau(inputs.square(M, 5), None, E)
+        want = np.r_[np.ones(nopen), np.zeros(M - nopen)]
+        assert np.abs(tau - want).max() < 1e-10
+        assert abs(oracle.shot_noise(tau)) < 1e-9
+
+
+def test_tau_trace_bounds_and_left_right_spectra():
+    """Disordered ribbon: 0 <= tau <= 1, sum tau = the dense T (Sec. 2.3),
+    and the spectrum seen from the right lead (from G_L1, the dense solve's
+    other corner block) equals the one from the left, as a lossless
+    two-terminal scattering matrix requires."""
+    M, L = 6, 9
+    for seed, E in ((0, -1.7), (1, 0.2), (2, 2.6)):
+        eps = oracle.onsite(seed, L, M, 2.0)
+        ss = inputs.square(M, L)
+        S = oracle.sigma_square(M, 1.0, E)
+        tau, _ = _tau(ss, eps, E)
+        d = oracle.dense(ss.H0, ss.V, eps, L, E, S, S)
+        assert tau.min() > -1e-12 and tau.max() < 1 + 1e-12
+        assert abs(tau.sum() - d["T_LR"]) < 1e-11
+        w, U = np.linalg.eigh(gamma(S))
+        R = (U * np.sqrt(np.clip(w, 0, None))) @ U.conj().T
+        H = R @ d["GL1"] @ gamma(S) @ d["GL1"].conj().T @ R
+        right = np.linalg.eigvalsh((H + H.conj().T) / 2)[::-1]
+        assert np.abs(right - tau).max() < 1e-11
+
+
+def test_tau_unequal_leads_left_right_spectra():
+    """Different left and right self-energies (random retarded blocks): the
+    left and right spectra still agree and sum to the dense T; a product with
+    the two Gammas exchanged would not."""
+    rng = np.random.default_rng(7)
+    M, L = 5, 6
+    ss = inputs.square(M, L)
+    eps = oracle.onsite(3, L, M, 1.5)
+    for E in (-0.9, 0.6):
+        SL = inputs.random_retarded_sigma(rng, M)
+        SR = inputs.random_retarded_sigma(rng, M)
+        tau, _ = _tau(ss, eps, E, SL, SR)
+        d = oracle.dense(ss.H0, ss.V, eps, L, E, SL, SR)
+        assert abs(tau.sum() - d["T_LR"]) < 1e-11
+        w, U = np.linalg.eigh(gamma(SR))
+        R = (U * np.sqrt(np.clip(w, 0, None))) @ U.conj().T
+        H = R @ d["GL1"] @ gamma(SL) @ d["GL1"].conj().T @ R
+        right = np.linalg.eigvalsh((H + H.conj().T) / 2)[::-1]
+        assert np.abs(right - tau).max() < 1e-11
+        wl, Ul = np.linalg.eigh(gamma(SL))
+        RL = (Ul * np.sqrt(np.clip(wl, 0, None))) @ Ul.conj().T
+        Hx = R @ d["G1L"] @ gamma(SL) @ d["G1L"].conj().T @ R   # Gammas exchanged
+        swapped = np.linalg.eigvalsh((Hx + Hx.conj().T) / 2)[::-1]
+        assert np.abs(swapped - tau).max() > 1e-3
