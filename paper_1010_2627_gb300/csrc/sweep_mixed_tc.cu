@@ -34,15 +34,18 @@
 // 2012) with bf16 slices, specialised to the residual of an approximate
 // inverse.
 //
-// Shared-memory operand tiles use the no-swizzle K-major layout: 8-row x
-// 16-byte core matrices, K-adjacent core matrices 128 B apart (descriptor
-// leading byte offset), 8-row groups 256 B apart (stride byte offset).
+// Shared-memory operand tiles use the no-swizzle K-major layout of
+// tc_common.cuh: 8-row x 16-byte core matrices, K-adjacent core matrices
+// 128 B apart (descriptor leading byte offset), 8-row groups 256 B apart
+// (stride byte offset).
 
 #include <cuda_bf16.h>
 
 #include "mixed_common.cuh"
+#include "tc_common.cuh"
 
 using namespace mixed;
+using namespace tc;
 
 namespace {
 
@@ -52,13 +55,10 @@ constexpr int RA = MPT / TYT, RB = MPT / TXT;
 constexpr int NDA = 7;                // digits of Gv
 constexpr int NDB = 3;                // digits of X
 constexpr int NACC = 7;               // accumulators d = p + q = 0 .. 6, each exact
-constexpr int A_TILE = 128 * 16 * 2;  // bytes of one 128 x 16 bf16 tile
-constexpr int B_TILE = 64 * 16 * 2;   // bytes of one 64 x 16 bf16 tile
 constexpr int RS = MPT + 1;           // padded row stride of R
 constexpr int GJ_NB = 8;              // Gauss-Jordan panel width
 constexpr int MAX_NNZ = 256;          // sparse H0 rows cached in shared memory up to this
 constexpr uint32_t TMEM_COLS = 512;   // 7 accumulators x 64 columns, rounded up
-constexpr long WAIT_LIMIT = 1L << 24; // bounded mbarrier polling
 
 
 struct TcSmem {
@@ -100,73 +100,8 @@ struct TcSmem {
     int h0_cached;
 };
 
-KNIT_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-KNIT_DEV int tile_off(int r, int c) { return (r >> 3) * 256 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2; }
-
-KNIT_DEV uint64_t smem_desc(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)(128 >> 4) << 16;     // K-adjacent core matrices
-    d |= (uint64_t)(256 >> 4) << 32;     // 8-row groups
-    d |= (uint64_t)1 << 46;              // descriptor version
-    return d;
-}
-
-// two K-adjacent values (c even) in one 32-bit store
-KNIT_DEV void put_bf16x2(unsigned char *tile, int r, int c, float v0, float v1)
-{
-    *reinterpret_cast<__nv_bfloat162 *>(tile + tile_off(r, c)) = __floats2bfloat162_rn(v0, v1);
-}
-
 // 2^e as a float for |e| <= 126 (exact power of two)
 KNIT_DEV float pow2f(int e) { return __int_as_float((127 + e) << 23); }
-
-KNIT_DEV void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                 ::"r"(tmem_d), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-
-KNIT_DEV void mma_commit(unsigned long long *mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 ::"r"(smem_u32(mbar)) : "memory");
-}
-
-// bounded wait for the mbarrier phase `parity`; returns 0 on timeout
-KNIT_DEV int mbar_wait(unsigned long long *mbar, uint32_t parity)
-{
-    uint32_t done = 0;
-    for (long it = 0; it < WAIT_LIMIT; ++it) {
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     "selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
-        if (done) return 1;
-    }
-    return 0;
-}
-
-KNIT_DEV void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                   "=r"(v[6]), "=r"(v[7])
-                 : "r"(taddr));
-}
-
-// zero 8 consecutive accumulator columns of the warp's 32 TMEM lanes
-KNIT_DEV void tmem_zero8(uint32_t taddr)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};"
-                 ::"r"(taddr), "r"(0u) : "memory");
-}
-
-KNIT_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-KNIT_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-KNIT_DEV void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // exponent e with |v| < 2^e for the largest |v| (0 for an all-zero set)
 KNIT_DEV int scale_exp(float mx)
@@ -207,9 +142,9 @@ knit_sweep_mixed_tc_kernel(InstDev in)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.mbar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = sm.tmem;
     uint32_t phase = 0;
     bool timed_out = false;
@@ -389,7 +324,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             // accumulators to zero (each warp the columns its epilogue reads), so
             // that every product accumulates
             {
-                tc_fence_after();
+                fence_after();
                 const uint32_t tz = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * (warp >> 2);
 #pragma unroll
                 for (int dacc = 0; dacc < NACC; ++dacc) {
@@ -439,10 +374,10 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                     }
                 }
                 async_proxy_fence();
-                tc_fence_before();
+                fence_before();
                 __syncthreads();
                 if (tid == 0) {
-                    tc_fence_after();
+                    fence_after();
                     // one MMA per A digit p against the B digits q = 0 .. min(2, 6 - p)
                     // of the chunk, stored contiguously (N = 64 per digit): products
                     // (p, q) land in accumulators p + q, i.e. columns 64 p ..
@@ -469,7 +404,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                 st = ST_TIMEOUT;
                 break;
             }
-            tc_fence_after();
+            fence_after();
 
             // R = I + Gv' X' = I + sigma_i tau_n 2^-16 (D0 + ... + D6):
             // lane m of warp w holds row 32 (w % 4) + lane of [Re; Im],
@@ -528,7 +463,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                     }
                 }
             }
-            tc_fence_before();
+            fence_before();
 
             // further Neumann terms where A_n is ill-conditioned, in the B-digit
             // buffer (free once the products are read back)
@@ -567,7 +502,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
         __syncthreads();
         if (timed_out) break;
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
