@@ -513,9 +513,80 @@ def run_bdg_case(args):
     sysk.close()
 
 
+def run_eigen_case(args):
+    """Transmission eigenvalues and shot noise on the bench workload (square
+    M=64, L=512, W=2, 1024 energies x 8 seeds, mixed sweep): one step = lead
+    self-energies, the sweep with G_LL stored, Gamma_R^{1/2} per energy, the
+    Hermitian matrix per instance and its FP64 Jacobi eigenvalues, for all
+    8192 instances, outputs in device memory.  Beside it: the same call for
+    T alone, so the eigenvalue pipeline's own cost reads as the difference."""
+    import torch
+    from paper_1010_2627_gb300 import build, inputs, knit
+    build.build()
+    knit.load()
+    ss = inputs.square(M, L)
+    E = inputs.energy_grid(-3.9, 3.9, NE)
+    seeds = np.arange(NS, dtype=np.uint64)
+    n = NE * NS
+    sysk = knit.System(ss)
+    stream = torch.cuda.Stream()
+    dE = torch.tensor(E, device="cuda")
+    ds = torch.tensor(seeds.astype(np.int64), device="cuda")
+    dtau = torch.empty(n * M, dtype=torch.float64, device="cuda")
+    dnoise = torch.empty(n, dtype=torch.float64, device="cuda")
+    dT = torch.empty(n, dtype=torch.float64, device="cuda")
+    dst = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def eig_step():
+        knit.knit_transmission_eigenvalues(sysk.handle, dE, ds, W, knit.KNIT_MIXED, dtau, dnoise,
+                                           dT, dst, nE=NE, nS=NS, stream=stream)
+
+    def t_step():
+        knit.knit_transmission(sysk.handle, dE, ds, W, knit.KNIT_MIXED, dT, dst, nE=NE, nS=NS,
+                               stream=stream)
+
+    res = {}
+    for name, fn in (("eig", eig_step), ("T", t_step)):
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        res[name] = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    eig_step()
+    torch.cuda.synchronize()
+    tau = dtau.cpu().numpy().reshape(n, M)
+    noise = dnoise.cpu().numpy()
+    T = dT.cpu().numpy()
+    st = dst.cpu().numpy()
+    ok = (st == 0) & (T > 0.5)
+    print(json.dumps({
+        "metric": "T(E) points/s with transmission eigenvalues and shot noise (mixed sweep)",
+        "value": n / (res["eig"] / 1e3), "unit": "T(E) points/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["eig"],
+        "higher_is_better": True, "dtype": "c64 sweep + FP64 eigenvalues", "data": "synthetic",
+        "config": {"workload": f"square M={M} L={L} W={W}, {NE} energies x {NS} seeds, "
+                               "eigenvalues of every instance"},
+        "T_only_ms_per_step": res["T"],
+        "eigenvalue_pipeline_ms": res["eig"] - res["T"],
+        "max_abs_sum_tau_minus_T": float(np.abs(tau.sum(axis=1) - T)[st == 0].max()),
+        "tau_range": [float(tau[st == 0].min()), float(tau[st == 0].max())],
+        "mean_fano_T_gt_half": float(np.mean(noise[ok] / T[ok])) if ok.any() else None,
+        "status_nonzero": int((st != 0).sum())}), flush=True)
+    sysk.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="bench", choices=["bench", "profile", "uneven", "ldos", "bdg"])
+    ap.add_argument("--case", default="bench",
+                    choices=["bench", "profile", "uneven", "ldos", "bdg", "eigen"])
     ap.add_argument("--bdg-energies", dest="bdg_energies", type=int, default=2048)
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,6 +605,8 @@ def main():
         run_ldos_case(args)
     elif args.case == "bdg":
         run_bdg_case(args)
+    elif args.case == "eigen":
+        run_eigen_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

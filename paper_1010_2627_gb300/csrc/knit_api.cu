@@ -29,10 +29,11 @@ extern "C" cudaError_t knit_launch_ldos_mixed(const InstDev *, int, int, int, in
 extern "C" size_t knit_mixed_wide_work_bytes(int);
 extern "C" cudaError_t knit_launch_mixed_wide(const InstDev *, int, int, void *, cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
-extern "C" cudaError_t knit_launch_gamma_sqrt(const double2 *, int, int, double2 *, double2 *,
-                                              cudaStream_t);
-extern "C" cudaError_t knit_launch_tau(const double2 *, const double2 *, int, int, int, const int *,
-                                       double2 *, double2 *, int, double *, double *, cudaStream_t);
+extern "C" cudaError_t knit_launch_gamma_factor(const double2 *, int, int, double2 *, double2 *,
+                                                int *, cudaStream_t);
+extern "C" size_t knit_tau_work_bytes(int);
+extern "C" cudaError_t knit_launch_tau(const double2 *, const double2 *, const int *, int, int, int,
+                                       const int *, void *, int, double *, double *, cudaStream_t);
 extern "C" cudaError_t knit_launch_modes_sigma(const double2 *, const double2 *, int, double,
                                                const double *, int, double2 *, double2 *, int,
                                                cudaStream_t);
@@ -153,7 +154,7 @@ struct knit_system_s {
     // grow-only workspaces
     DevBuf E, seeds, T, status, queue, sigL, sigR, gL, gR, lst, lit, lres, work, ckpt, decw, ldos;
     DevBuf p2g, p2s, p2t;   // period-2 leads: supercell g and Sigma, block-product scratch
-    DevBuf gll, tq, tw, ts, tg, tau, noise;   // transmission eigenvalues: G_LL, Q, scratch, out
+    DevBuf gll, tw, ts, tg, trk, tau, noise;   // transmission eigenvalues: G_LL, scratch, W, rank, out
 
     SysDev dev() const
     {
@@ -797,7 +798,7 @@ knit_status knit_system_destroy(knit_system s)
     }
     DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
                       &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
-                      &s->p2g, &s->p2s, &s->p2t, &s->gll, &s->tq, &s->tw, &s->ts, &s->tg,
+                      &s->p2g, &s->p2s, &s->p2t, &s->gll, &s->tw, &s->ts, &s->tg, &s->trk,
                       &s->tau, &s->noise};
     for (DevBuf *b : bufs) b->release();
     delete s;
@@ -964,16 +965,17 @@ knit_status knit_transmission_eigenvalues(knit_system s, const double *E, int32_
     CK(s->gll.ensure(sizeof(double2) * MM * n), "G_LL workspace");
     in.GLL = s->gll.as<double2>();
     if ((r = run_sweep(s, in, precision, st)) != KNIT_OK) return r;
-    // Gamma_R^{1/2} per energy, then Q per instance and its eigenvalues
-    CK(s->tg.ensure(sizeof(double2) * 2 * MM * nE), "Gamma workspace");
-    CK(s->ts.ensure(sizeof(double2) * MM * nE), "Gamma_R^1/2");
-    CK(knit_launch_gamma_sqrt(in.sigR, M, nE, s->tg.as<double2>(), s->ts.as<double2>(), st),
-       "Gamma_R^1/2 launch");
-    const int grid = std::max(1, std::min(n, 8 * s->nsm));
-    CK(s->tq.ensure(sizeof(double2) * MM * n), "Q workspace");
-    CK(s->tw.ensure(sizeof(double2) * 2 * MM * grid), "Q scratch");
-    CK(knit_launch_tau(in.GLL, s->ts.as<double2>(), M, n, nS, in.status, s->tq.as<double2>(),
-                       s->tw.as<double2>(), grid, dtau, dnoise, st),
+    // Gamma_R = W W^dagger per energy, then Q = W^dagger K W per instance and its eigenvalues
+    CK(s->tg.ensure(sizeof(double2) * MM * nE), "Gamma workspace");
+    CK(s->ts.ensure(sizeof(double2) * MM * nE), "Gamma factor");
+    CK(s->trk.ensure(sizeof(int) * nE), "Gamma rank");
+    CK(knit_launch_gamma_factor(in.sigR, M, nE, s->tg.as<double2>(), s->ts.as<double2>(),
+                                s->trk.as<int>(), st),
+       "Gamma factor launch");
+    const int grid = std::max(1, std::min(n, s->nsm));
+    CK(s->tw.ensure(std::max<size_t>(knit_tau_work_bytes(M) * grid, 256)), "eigenvalue scratch");
+    CK(knit_launch_tau(in.GLL, s->ts.as<double2>(), s->trk.as<int>(), M, n, nS, in.status, s->tw.p,
+                       grid, dtau, dnoise, st),
        "eigenvalue launch");
     if (hTau) CK(cudaMemcpyAsync(tau, dtau, sizeof(double) * n * M, cudaMemcpyDeviceToHost, st), "tau out");
     if (hNoise)

@@ -89,15 +89,10 @@ constexpr int DEC_ATTEMPTS = 4;
 constexpr double DEC_SELF_TOL = 1e-5;
 
 // ---------------------------------------------------------------------------
-// A (M x M, Hermitian) -> diag in A, eigenvectors in U (global memory; U may
-// be nullptr for eigenvalues only).  Block b takes the matrices at offset
-// b * M * M of A and U (a batch of independent problems); sweeps_out, when
-// given, receives block 0's sweep count.
+// A (M x M, Hermitian) -> diag in A, eigenvectors in U (global memory).
 extern "C" __global__ void __launch_bounds__(256)
 knit_jacobi_kernel(double2 *A, double2 *U, int M, int max_sweeps, double tol, int *sweeps_out)
 {
-    A += (size_t)blockIdx.x * M * M;
-    if (U) U += (size_t)blockIdx.x * M * M;
     __shared__ double rc[128], rs[128];
     __shared__ double2 rph[128];
     __shared__ int rp[128], rq[128];
@@ -105,11 +100,10 @@ knit_jacobi_kernel(double2 *A, double2 *U, int M, int max_sweeps, double tol, in
     const int tid = threadIdx.x, nt = blockDim.x;
     const int Me = M + (M & 1);   // even count with a dummy index M for odd M
     const int npair = Me / 2;
-    if (U)
-        for (int e = tid; e < M * M; e += nt) {
-            int i = e / M, j = e - i * M;
-            U[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-        }
+    for (int e = tid; e < M * M; e += nt) {
+        int i = e / M, j = e - i * M;
+        U[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    }
     __syncthreads();
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
@@ -171,7 +165,7 @@ knit_jacobi_kernel(double2 *A, double2 *U, int M, int max_sweeps, double tol, in
                 if (q >= M) continue;
                 double c = rc[t], sn = rs[t];
                 double2 phc = cconj(rph[t]);
-                for (int w = 0; w < (U ? 2 : 1); ++w) {
+                for (int w = 0; w < 2; ++w) {
                     double2 *X = w == 0 ? A : U;
                     double2 xp = X[(size_t)i * M + p], xq = X[(size_t)i * M + q];
                     double2 xqp = cmul(phc, xq);
@@ -195,7 +189,7 @@ knit_jacobi_kernel(double2 *A, double2 *U, int M, int max_sweeps, double tol, in
             __syncthreads();
         }
     }
-    if (tid == 0 && sweeps_out && blockIdx.x == 0) *sweeps_out = sweep;
+    if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
 // ---------------------------------------------------------------------------
@@ -480,15 +474,6 @@ extern "C" cudaError_t knit_launch_jacobi(double2 *A, double2 *U, int M, int *sw
                                           cudaStream_t stream)
 {
     knit_jacobi_kernel<<<1, 256, 0, stream>>>(A, U, M, 60, 1e-15, sweeps);
-    return cudaGetLastError();
-}
-
-// count independent Hermitian problems at A + b M^2 (eigenvectors at U + b M^2
-// when U is given)
-extern "C" cudaError_t knit_launch_jacobi_batch(double2 *A, double2 *U, int M, int count,
-                                                cudaStream_t stream)
-{
-    knit_jacobi_kernel<<<count, 256, 0, stream>>>(A, U, M, 60, 1e-15, nullptr);
     return cudaGetLastError();
 }
 
