@@ -23,6 +23,8 @@ ctypes:
                      sewing), plain loops
 * ``rgf_batch``      ``rgf`` over many instances on all host cores (the CPU
                      baseline)
+* ``lesser_parts``   lead-resolved densities and bond currents from
+                     G^<_l = i G Gamma_l G^+ (Sec. 2.3), dense numpy inverse
 * ``transmission_eigenvalues``, ``shot_noise``
                      the eigenvalues of the matrix inside Sec. 2.3's
                      transmission trace, and sum tau (1 - tau)
@@ -281,6 +283,54 @@ def transmission_eigenvalues(G1L, SigL, SigR):
     G1L = np.asarray(G1L, dtype=np.complex128)
     H = S @ G1L @ _gamma(SigR) @ G1L.conj().T @ S
     return np.linalg.eigvalsh((H + H.conj().T) / 2)[::-1].copy()
+
+
+def lesser_parts(H0, V, eps, L: int, E: float, SigL, SigR):
+    """Lead-resolved parts of the lesser function, G^<_l = i G Gamma_l G^+
+    (Sec. 2.3, with Gamma_l = i (Sigma_l - Sigma_l^+)), from the plain dense
+    inverse of E - H - Sigma_L - Sigma_R (numpy).  Returns a dict of
+
+    rhoL, rhoR (L, M): A^l_xx / (2 pi) with A^l = G Gamma_l G^+ -- the density
+        of states injected by lead l (the non-equilibrium density is
+        f_L rhoL + f_R rhoR);
+    jx (L - 1, M): current carried by left-injected states from orbital x of
+        slice n into slice n + 1, sum_y -2 Im[H_{(n,x),(n+1,y)} A^L_{(n+1,y),(n,x)}];
+    jt (L, E_up): the same along the edges x < y of H0 inside each slice, in
+        row-major order of H0's nonzero entries above the diagonal;
+    ldos (L, M): -Im G_xx / pi, and T (Sec. 2.3 trace)."""
+    H0, V, eps, M = _sys_arrays(H0, V, eps, L)
+    N = M * L
+    H = np.zeros((N, N), np.complex128)
+    for n in range(L):
+        H[n * M:(n + 1) * M, n * M:(n + 1) * M] = H0 + (np.diag(eps[n]) if eps is not None else 0)
+        if n + 1 < L:
+            Vn = V[(n + 1) % V.shape[0]]
+            H[(n + 1) * M:(n + 2) * M, n * M:(n + 1) * M] = Vn
+            H[n * M:(n + 1) * M, (n + 1) * M:(n + 2) * M] = Vn.conj().T
+    A = E * np.eye(N) - H
+    A[:M, :M] -= _c(SigL, np.complex128)
+    A[N - M:, N - M:] -= _c(SigR, np.complex128)
+    G = np.linalg.inv(A)
+    GL, GR = _gamma(SigL), _gamma(SigR)
+    AL = G[:, :M] @ GL @ G[:, :M].conj().T
+    AR = G[:, N - M:] @ GR @ G[:, N - M:].conj().T
+    rhoL = (np.real(np.diag(AL)) / (2 * np.pi)).reshape(L, M)
+    rhoR = (np.real(np.diag(AR)) / (2 * np.pi)).reshape(L, M)
+    jx = np.zeros((max(L - 1, 0), M))
+    for n in range(L - 1):
+        for x in range(M):
+            a = n * M + x
+            jx[n, x] = sum(-2 * np.imag(H[a, (n + 1) * M + y] * AL[(n + 1) * M + y, a])
+                           for y in range(M))
+    edges = [(x, y) for x in range(M) for y in range(x + 1, M) if H0[x, y] != 0]
+    jt = np.zeros((L, len(edges)))
+    for n in range(L):
+        for e, (x, y) in enumerate(edges):
+            a, b = n * M + x, n * M + y
+            jt[n, e] = -2 * np.imag(H[a, b] * AL[b, a])
+    ldos = (-np.imag(np.diag(G)) / np.pi).reshape(L, M)
+    T = float(np.real(np.trace(GL @ G[:M, N - M:] @ GR @ G[:M, N - M:].conj().T)))
+    return dict(rhoL=rhoL, rhoR=rhoR, jx=jx, jt=jt, edges=edges, ldos=ldos, T=T)
 
 
 def shot_noise(tau):

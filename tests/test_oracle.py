@@ -472,3 +472,64 @@ def test_tau_unequal_leads_left_right_spectra():
         Hx = R @ d["G1L"] @ gamma(SL) @ d["G1L"].conj().T @ R   # Gammas exchanged
         swapped = np.linalg.eigvalsh((Hx + Hx.conj().T) / 2)[::-1]
         assert np.abs(swapped - tau).max() > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Lesser function by lead (Sec. 2.3: G^< = sum_l f_l i G Gamma_l G^+):
+# injected densities and bond currents
+
+def _lesser(ss, eps, E, SL=None, SR=None):
+    S = oracle.sigma_square(ss.M, 1.0, E) if SL is None else SL
+    return oracle.lesser_parts(ss.H0, ss.V, eps, ss.L, E, S, S if SR is None else SR)
+
+
+def test_lesser_clean_chain_closed_form():
+    """Clean chain: each lead injects half of the density of states,
+    1 / (2 pi sqrt(4 - E^2)) per site, and every bond carries T = 1."""
+    for E in (-1.6, 0.3, 1.9):
+        r = _lesser(inputs.chain(6), None, E)
+        half = 1 / (2 * np.pi * np.sqrt(4 - E * E))
+        assert np.abs(r["rhoL"] - half).max() < 1e-12 and np.abs(r["rhoR"] - half).max() < 1e-12
+        assert np.abs(r["jx"] - 1.0).max() < 1e-12
+
+
+def test_lesser_sum_rule_conservation_kirchhoff():
+    """Disordered ribbon: rhoL + rhoR = LDOS (of the C dense solve); the
+    left-injected current through every slice interface is T; at every
+    interior orbital inflow = outflow (diagonal V, so the bond into (n, x) is
+    jx[n - 1, x]); and the density injected from the right equals the one
+    injected from the left in the mirror-image system."""
+    M, L = 5, 7
+    for seed, E in ((0, -1.2), (4, 0.55), (9, 2.3)):
+        ss = inputs.square(M, L)
+        eps = oracle.onsite(seed, L, M, 2.0)
+        S = oracle.sigma_square(M, 1.0, E)
+        r = _lesser(ss, eps, E)
+        d = oracle.dense(ss.H0, ss.V, eps, L, E, S, S, want_ldos=True)
+        assert np.abs(r["rhoL"] + r["rhoR"] - d["ldos"]).max() < 1e-12
+        assert np.abs(r["jx"].sum(axis=1) - d["T_LR"]).max() < 1e-11
+        net = np.zeros((L, M))
+        net[:-1] += r["jx"]
+        net[1:] -= r["jx"]
+        for e, (x, y) in enumerate(r["edges"]):
+            net[:, x] += r["jt"][:, e]
+            net[:, y] -= r["jt"][:, e]
+        assert np.abs(net[1:-1]).max() < 1e-11
+        assert abs(net[0].sum() - d["T_LR"]) < 1e-11
+        rR = oracle.lesser_parts(ss.H0[::-1, ::-1], ss.V, eps[::-1, ::-1], L, E, S, S)
+        # the mirror image system: right injection becomes left injection
+        assert np.abs(rR["rhoL"][::-1, ::-1] - r["rhoR"]).max() < 1e-12
+
+
+def test_lesser_complex_hamiltonian_conservation():
+    """Random Hermitian slices with complex couplings and unequal random
+    leads: the sum rule and current conservation still hold."""
+    rng = np.random.default_rng(11)
+    ss = inputs.random_slice_system(rng, 3, 5, P=2)
+    SL = inputs.random_retarded_sigma(rng, 3)
+    SR = inputs.random_retarded_sigma(rng, 3)
+    for E in (-0.7, 0.4):
+        r = oracle.lesser_parts(ss.H0, ss.V, None, 5, E, SL, SR)
+        d = oracle.dense(ss.H0, ss.V, None, 5, E, SL, SR, want_ldos=True)
+        assert np.abs(r["rhoL"] + r["rhoR"] - d["ldos"]).max() < 1e-11
+        assert np.abs(r["jx"].sum(axis=1) - d["T_LR"]).max() < 1e-11
