@@ -194,6 +194,33 @@ knit_status knit_transmission_eigenvalues(knit_system sys, const double *E, int3
                                           double *tau, double *noise, double *T, int32_t *status,
                                           void *stream);
 
+/* Lead-resolved lesser function along the sewing pass (Sec. 2.3:
+ * G^< = sum_l f_l G^<_l with G^<_l = i G Gamma_l G^+, Gamma_l = i(Sigma_l -
+ * Sigma_l^+); Sec. 5.3 D sewing; the non-equilibrium density and local
+ * currents of Sec. 7.3 getG_lesser), energy-resolved and per injecting lead,
+ * for instances as in knit_transmission; FP64.  With A^l = G Gamma_l G^+:
+ *   rhoL, rhoR (nE*nS*L*M, [i][n][x]): A^l_{(n,x),(n,x)} / 2pi, the density of
+ *         states injected by the left / right lead (rhoL + rhoR = LDOS; the
+ *         non-equilibrium density at energy E is f_L rhoL + f_R rhoR);
+ *   jx    (nE*nS*(L-1)*M, [i][n][x]): current carried by left-injected states
+ *         from orbital x of slice n into slice n+1,
+ *         sum_y -2 Im[H_{(n,x),(n+1,y)} A^L_{(n+1,y),(n,x)}] (units e/h per
+ *         unit energy; sum_x jx = T for every n);
+ *   jt    (nE*nS*L*nedge, [i][n][e]): the same along the e-th edge x < y of
+ *         H0 inside slice n, edges in row-major order of H0's nonzero entries
+ *         above the diagonal (knit_system_num_edges gives nedge), positive
+ *         from x to y.
+ * Any of the four may be NULL (not all).  T, status (optional) as for
+ * knit_transmission.  saving_level as for knit_ldos.  Device workspace per
+ * SM: (8 + ceil(L / k) + k) M^2 complex128 (k = saving_level). */
+knit_status knit_lesser(knit_system sys, const double *E, int32_t nE, const uint64_t *seeds,
+                        int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
+                        double *rhoL, double *rhoR, double *jx, double *jt, double *T,
+                        int32_t *status, void *stream);
+
+/* Number of nonzero entries of H0 above its diagonal (the edges of jt). */
+knit_status knit_system_num_edges(knit_system sys, int32_t *count);
+
 /* Local density of states (Sec. 5.3 D knitting followed by sewing):
  * ldos (nE*nS*L*M, row-major [i][n][x]) receives -Im G_nn[x][x]/pi; T
  * (optional) the transmission; status (optional) per instance (ldos of an

@@ -21,6 +21,9 @@ extern "C" cudaError_t knit_launch_sweep_fp64(const InstDev *, int, int, double2
 extern "C" cudaError_t knit_launch_ldos_fp64(const InstDev *, int, int, int, double2 *, int,
                                              double2 *, int, double *, long long, cudaStream_t);
 extern "C" size_t knit_fp64_smem_bytes(int, int, int);
+extern "C" cudaError_t knit_launch_lesser_fp64(const InstDev *, int, int, int, double2 *, double2 *,
+                                               int, const int2 *, int, double *, double *, double *,
+                                               double *, cudaStream_t);
 extern "C" cudaError_t knit_launch_mixed_impl(const InstDev *, int, int, int, cudaStream_t);
 extern "C" int knit_mixed_max_M(void);
 extern "C" size_t knit_ldos_mixed_work_bytes(int, int, int);
@@ -149,12 +152,15 @@ struct knit_system_s {
     double *sign = nullptr, *onsite = nullptr;
     SysDev *d_sys = nullptr;   // device copy of dev() for the kernels' system table
     int *h0_rowptr = nullptr, *h0_col = nullptr;
+    int2 *h0_edges = nullptr;  // nonzeros of H0 above the diagonal, row-major (x < y)
+    int n_edges = 0;
     Lead lead[2];
     int leads_same = 0;
     // grow-only workspaces
     DevBuf E, seeds, T, status, queue, sigL, sigR, gL, gR, lst, lit, lres, work, ckpt, decw, ldos;
     DevBuf p2g, p2s, p2t;   // period-2 leads: supercell g and Sigma, block-product scratch
     DevBuf gll, tw, ts, tg, trk, tau, noise;   // transmission eigenvalues: G_LL, scratch, W, rank, out
+    DevBuf lrl, lrr, ljx, ljt;                 // lesser function outputs staged for host pointers
 
     SysDev dev() const
     {
@@ -743,6 +749,17 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
                                [](double2 a, double2 b) { return a.x == b.x && a.y == b.y; }) &&
                     std::equal(s->lead[0].hV.begin(), s->lead[0].hV.end(), s->lead[1].hV.begin(),
                                [](double2 a, double2 b) { return a.x == b.x && a.y == b.y; });
+    std::vector<int2> edges;
+    for (int x = 0; x < M; ++x)
+        for (int y = x + 1; y < M; ++y) {
+            const double2 h = H0[(size_t)x * M + y];
+            if (h.x != 0.0 || h.y != 0.0) edges.push_back(make_int2(x, y));
+        }
+    s->n_edges = (int)edges.size();
+    if (!edges.empty() && (r = to_device(&s->h0_edges, edges.data(), edges.size(), "H0 edges")) != KNIT_OK) {
+        knit_system_destroy(s);
+        return r;
+    }
     if ((r = to_device(&s->H0, H0.data(), MM, "H0")) != KNIT_OK ||
         (r = to_device(&s->V, V.data(), MM * P, "V")) != KNIT_OK ||
         (r = to_device(&s->sign, hs.data(), (size_t)B, "sign")) != KNIT_OK ||
@@ -788,6 +805,7 @@ knit_status knit_system_destroy(knit_system s)
     cudaFree(s->h0_rowptr);
     cudaFree(s->h0_col);
     cudaFree(s->h0_val);
+    cudaFree(s->h0_edges);
     cudaFree(s->d_sys);
     for (int p = 0; p < 2; ++p) {
         cudaFree(s->lead[p].H0);
@@ -799,7 +817,7 @@ knit_status knit_system_destroy(knit_system s)
     DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
                       &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
                       &s->p2g, &s->p2s, &s->p2t, &s->gll, &s->tw, &s->ts, &s->tg, &s->trk,
-                      &s->tau, &s->noise};
+                      &s->tau, &s->noise, &s->lrl, &s->lrr, &s->ljx, &s->ljt};
     for (DevBuf *b : bufs) b->release();
     delete s;
     return KNIT_OK;
@@ -984,6 +1002,75 @@ knit_status knit_transmission_eigenvalues(knit_system s, const double *E, int32_
     if (hSt)
         CK(cudaMemcpyAsync(status, in.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
     return finish(st, hTau || hNoise || hT || hSt, "knit_transmission_eigenvalues");
+}
+
+knit_status knit_system_num_edges(knit_system s, int32_t *count)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if (!count) return fail(KNIT_ERR_INVALID, "count is NULL");
+    *count = s->n_edges;
+    return KNIT_OK;
+}
+
+knit_status knit_lesser(knit_system s, const double *E, int32_t nE, const uint64_t *seeds,
+                        int32_t nS, double W, int32_t saving_level, const knit_lead_opts *opts,
+                        double *rhoL, double *rhoR, double *jx, double *jt, double *T,
+                        int32_t *status, void *stream)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if ((r = check_batch(s, E, nE, nS, KNIT_FP64, W)) != KNIT_OK) return r;
+    if (!rhoL && !rhoR && !jx && !jt) return fail(KNIT_ERR_INVALID, "no output requested");
+    if (saving_level == 0)
+        return fail(KNIT_ERR_INVALID, "saving_level 0 keeps nothing: no local observables");
+    if (saving_level < -1) return fail(KNIT_ERR_INVALID, "saving_level must be -1 or >= 1");
+    const int save = saving_level == -1 ? 1 : std::min(saving_level, s->L);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int M = s->M, L = s->L;
+    const size_t MM = (size_t)M * M;
+    const int n = nE * nS;
+    InstDev in{};
+    in.n = n;
+    in.nS = nS;
+    in.W = W;
+    if ((r = stage_in(s->E, E, (size_t)nE, st, &in.E, "E")) != KNIT_OK) return r;
+    if ((r = stage_in(s->seeds, seeds, (size_t)nS, st, &in.seeds, "seeds")) != KNIT_OK) return r;
+    const int *lst;
+    if ((r = both_sigmas(s, in.E, nE, opts, st, &in.sigL, &in.sigR, &lst)) != KNIT_OK) return r;
+    int *l0 = s->lst.as<int>();
+    combine_status<<<(nE + 255) / 256, 256, 0, st>>>(l0, l0 + nE, nE);
+    CK(cudaGetLastError(), "status combine");
+    in.lstatus = l0;
+    bool hl = false, hr = false, hx = false, ht = false, hT = false, hSt = false;
+    double *dl, *dr, *dx, *dt;
+    const size_t nlm = (size_t)n * L * M, nx = (size_t)n * (L - 1) * M, ne = (size_t)n * L * s->n_edges;
+    if ((r = stage_out(s->lrl, rhoL, nlm, &dl, &hl, "rhoL")) != KNIT_OK ||
+        (r = stage_out(s->lrr, rhoR, nlm, &dr, &hr, "rhoR")) != KNIT_OK ||
+        (r = stage_out(s->ljx, jx, std::max<size_t>(nx, 1), &dx, &hx, "jx")) != KNIT_OK ||
+        (r = stage_out(s->ljt, jt, std::max<size_t>(ne, 1), &dt, &ht, "jt")) != KNIT_OK ||
+        (r = stage_out(s->T, T, (size_t)n, &in.T, &hT, "T")) != KNIT_OK ||
+        (r = stage_out(s->status, (int *)status, (size_t)n, &in.status, &hSt, "status")) != KNIT_OK)
+        return r;
+    in.sys = s->d_sys;
+    CK(s->queue.ensure(sizeof(int)), "queue");
+    in.queue = s->queue.as<int>();
+    CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
+    const int grid = std::max(1, std::min(n, s->nsm));
+    CK(s->work.ensure(sizeof(double2) * 8 * MM * grid), "lesser workspace");
+    const int nck = (L + save - 1) / save;
+    CK(s->ckpt.ensure(sizeof(double2) * MM * (size_t)(nck + save) * grid), "checkpoint workspace");
+    CK(knit_launch_lesser_fp64(&in, M, L, grid, s->work.as<double2>(), s->ckpt.as<double2>(), save,
+                               s->h0_edges, s->n_edges, dl, dr, dx, s->n_edges ? dt : nullptr, st),
+       "lesser launch");
+    if (hl) CK(cudaMemcpyAsync(rhoL, dl, sizeof(double) * nlm, cudaMemcpyDeviceToHost, st), "rhoL out");
+    if (hr) CK(cudaMemcpyAsync(rhoR, dr, sizeof(double) * nlm, cudaMemcpyDeviceToHost, st), "rhoR out");
+    if (hx && nx) CK(cudaMemcpyAsync(jx, dx, sizeof(double) * nx, cudaMemcpyDeviceToHost, st), "jx out");
+    if (ht && ne) CK(cudaMemcpyAsync(jt, dt, sizeof(double) * ne, cudaMemcpyDeviceToHost, st), "jt out");
+    if (hT) CK(cudaMemcpyAsync(T, in.T, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
+    if (hSt)
+        CK(cudaMemcpyAsync(status, in.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
+    return finish(st, hl || hr || hx || ht || hT || hSt, "knit_lesser");
 }
 
 knit_status knit_ldos(knit_system s, const double *E, int32_t nE, const uint64_t *seeds,

@@ -55,6 +55,8 @@ _SIGS = {
     "knit_transmission_sigma": (i32, [P, P, i32, P, i32, f64, P, P, i32, P, P, P]),
     "knit_ldos": (i32, [P, P, i32, P, i32, f64, i32, i32, P, P, P, P, P]),
     "knit_transmission_eigenvalues": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P, P]),
+    "knit_lesser": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P, P, P, P]),
+    "knit_system_num_edges": (i32, [P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
     "knit_lead_model_train": (i32, [P, i32, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64,
@@ -216,6 +218,22 @@ def knit_transmission_eigenvalues(handle, E, seeds, W, precision, tau, noise=Non
                                                 None if opts is None else ctypes.byref(opts),
                                                 _ptr(tau), _ptr(noise), _ptr(T), _ptr(status),
                                                 _stream(stream)))
+
+
+def knit_lesser(handle, E, seeds, W, saving_level, rhoL=None, rhoR=None, jx=None, jt=None,
+                T=None, status=None, opts=None, nE=None, nS=None, stream=None):
+    nE = len(E) if nE is None else nE
+    nS = (1 if seeds is None else len(seeds)) if nS is None else nS
+    _check(load().knit_lesser(P(handle), _ptr(E), int(nE), _ptr(seeds), int(nS), float(W),
+                              int(saving_level), None if opts is None else ctypes.byref(opts),
+                              _ptr(rhoL), _ptr(rhoR), _ptr(jx), _ptr(jt), _ptr(T), _ptr(status),
+                              _stream(stream)))
+
+
+def knit_system_num_edges(handle) -> int:
+    c = ctypes.c_int32(0)
+    _check(load().knit_system_num_edges(P(handle), ctypes.byref(c)))
+    return int(c.value)
 
 
 def knit_ldos(handle, E, seeds, W, saving_level, ldos, T=None, status=None, opts=None, nE=None,
@@ -413,6 +431,27 @@ class System:
                                       _opts(method))
         return (tau.reshape(len(E), nS, self.M), noise.reshape(len(E), nS),
                 T.reshape(len(E), nS), st.reshape(len(E), nS))
+
+    def lesser(self, E, seeds=None, W=0.0, saving_level=-1, method=KNIT_LEAD_AUTO):
+        """dict(rhoL, rhoR (nE, nS, L, M), jx (nE, nS, L-1, M), jt (nE, nS, L, nedge),
+        T, status): lead-resolved densities and left-injected bond currents."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        nS = 1 if sd is None else len(sd)
+        n = len(E) * nS
+        ne = knit_system_num_edges(self.handle)
+        rl = np.empty((n, self.L, self.M))
+        rr = np.empty((n, self.L, self.M))
+        jx = np.empty((n, max(self.L - 1, 0), self.M))
+        jt = np.empty((n, self.L, ne))
+        T = np.empty(n)
+        st = np.empty(n, np.int32)
+        knit_lesser(self.handle, E, sd, W, saving_level, rl, rr, jx if jx.size else None,
+                    jt if jt.size else None, T, st, _opts(method))
+        sh = (len(E), nS)
+        return dict(rhoL=rl.reshape(sh + rl.shape[1:]), rhoR=rr.reshape(sh + rr.shape[1:]),
+                    jx=jx.reshape(sh + jx.shape[1:]), jt=jt.reshape(sh + jt.shape[1:]),
+                    T=T.reshape(sh), status=st.reshape(sh))
 
     def ldos(self, E, seeds=None, W=0.0, saving_level=-1, method=KNIT_LEAD_AUTO,
              precision=KNIT_FP64):
