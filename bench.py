@@ -583,10 +583,83 @@ def run_eigen_case(args):
     sysk.close()
 
 
+def run_lesser_case(args):
+    """Lead-resolved lesser function (FP64 sewing pass with the column towards
+    the right lead): square M=64, L=512, W=2, 38 energies x 8 seeds (two
+    waves of 152 instances), saving_level 8.  One step = the whole call for
+    all instances: densities injected by each lead and left-injected bond
+    currents for every slice.  Beside it: the FP64 LDOS call on the same
+    instances, and the largest violation of current conservation
+    (sum_x jx[n][x] = T for every slice interface)."""
+    import torch
+    from paper_1010_2627_gb300 import build, inputs, knit
+    build.build()
+    knit.load()
+    ss = inputs.square(M, L)
+    ne, save = 38, 8
+    E = inputs.energy_grid(-3.9, 3.9, ne)
+    seeds = np.arange(NS, dtype=np.uint64)
+    n = ne * NS
+    sysk = knit.System(ss)
+    nedge = knit.knit_system_num_edges(sysk.handle)
+    stream = torch.cuda.Stream()
+    dE = torch.tensor(E, device="cuda")
+    ds = torch.tensor(seeds.astype(np.int64), device="cuda")
+    rl = torch.empty(n * L * M, dtype=torch.float64, device="cuda")
+    rr = torch.empty(n * L * M, dtype=torch.float64, device="cuda")
+    jx = torch.empty(n * (L - 1) * M, dtype=torch.float64, device="cuda")
+    jt = torch.empty(n * L * nedge, dtype=torch.float64, device="cuda")
+    dT = torch.empty(n, dtype=torch.float64, device="cuda")
+    dst = torch.empty(n, dtype=torch.int32, device="cuda")
+    dL = torch.empty(n * L * M, dtype=torch.float64, device="cuda")
+
+    def lesser_step():
+        knit.knit_lesser(sysk.handle, dE, ds, W, save, rl, rr, jx, jt, dT, dst, nE=ne, nS=NS,
+                         stream=stream)
+
+    def ldos_step():
+        knit.knit_ldos(sysk.handle, dE, ds, W, save, dL, None, None, nE=ne, nS=NS,
+                       stream=stream, precision=knit.KNIT_FP64)
+
+    res = {}
+    for name, fn in (("lesser", lesser_step), ("ldos", ldos_step)):
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, args.warmup)):
+                fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        res[name] = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    lesser_step()
+    torch.cuda.synchronize()
+    T = dT.cpu().numpy()
+    st = dst.cpu().numpy()
+    cons = np.abs(jx.cpu().numpy().reshape(n, L - 1, M).sum(axis=2) - T[:, None])
+    sumrule = np.abs((rl + rr - dL).cpu().numpy()).max()
+    print(json.dumps({
+        "metric": "lesser-function points/s (injected densities + bond currents, FP64)",
+        "value": n / (res["lesser"] / 1e3), "unit": "instances/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["lesser"],
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"square M={M} L={L} W={W}, {ne} energies x {NS} seeds, "
+                               f"saving_level {save}"},
+        "fp64_ldos_ms_per_step": res["ldos"],
+        "max_abs_current_conservation": float(cons[st == 0].max()),
+        "max_abs_rhoL_plus_rhoR_minus_ldos": float(sumrule),
+        "status_nonzero": int((st != 0).sum())}), flush=True)
+    sysk.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "profile", "uneven", "ldos", "bdg", "eigen"])
+                    choices=["bench", "profile", "uneven", "ldos", "bdg", "eigen", "lesser"])
     ap.add_argument("--bdg-energies", dest="bdg_energies", type=int, default=2048)
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
@@ -607,6 +680,8 @@ def main():
         run_bdg_case(args)
     elif args.case == "eigen":
         run_eigen_case(args)
+    elif args.case == "lesser":
+        run_lesser_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
