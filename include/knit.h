@@ -221,6 +221,44 @@ knit_status knit_lesser(knit_system sys, const double *E, int32_t nE, const uint
 /* Number of nonzero entries of H0 above its diagonal (the edges of jt). */
 knit_status knit_system_num_edges(knit_system sys, int32_t *count);
 
+/* ---------------------------------------------------------------------
+ * Arbitrary two-lead geometries (Sec. 5.3: knitting through an interface of
+ * varying width; Sec. 2.2 worked example, Fig. 3).  H is the N x N
+ * Hermitian Hamiltonian of the system's sites (dense, row-major, host or
+ * device memory); lead p is attached to the n_lead_sites[p] sites
+ * lead_sites[p] (in the order of its self-energy's rows).  The library cuts
+ * the sites into slices of varying width: breadth-first layers from lead 0's
+ * sites, the layers from the first one holding a lead-1 site onwards merged
+ * into the last slice (sites not connected to lead 0 are left out), so that
+ * H is block tridiagonal with rectangular couplings.  KNIT_ERR_INVALID for
+ * N outside 1 .. 8192, a non-Hermitian H (relative 1e-12), overlapping or
+ * out-of-range lead sites, or lead 1 not connected to lead 0. */
+typedef struct knit_graph_s *knit_graph;
+typedef struct {
+    int32_t N;
+    const knit_c128 *H;
+    int32_t n_lead_sites[2];
+    const int32_t *lead_sites[2];
+} knit_graph_desc;
+
+knit_status knit_graph_create(const knit_graph_desc *desc, knit_graph *out);
+knit_status knit_graph_destroy(knit_graph g);
+
+/* The slicing: number of slices, their widths (nslices values, optional) and
+ * the slice of every site (N values, -1 for a site not connected to lead 0;
+ * optional). */
+knit_status knit_graph_slices(knit_graph g, int32_t *nslices, int32_t *widths,
+                              int32_t *slice_of);
+
+/* T_01 = Re Tr[Gamma_0 G_01 Gamma_1 G_01^dagger] (Sec. 2.3, k = 0, l = 1) for
+ * nE energies, by the knitting sweep over the slices in FP64; sigma0
+ * (nE x w0 x w0) and sigma1 (nE x w1 x w1) are the leads' retarded
+ * self-energies on their sites (e.g. knit_lead_selfenergy of a system whose
+ * lead cells are the leads').  T: nE outputs; status (optional) per energy. */
+knit_status knit_graph_transmission(knit_graph g, const double *E, int32_t nE,
+                                    const knit_c128 *sigma0, const knit_c128 *sigma1, double *T,
+                                    int32_t *status, void *stream);
+
 /* Local density of states (Sec. 5.3 D knitting followed by sewing):
  * ldos (nE*nS*L*M, row-major [i][n][x]) receives -Im G_nn[x][x]/pi; T
  * (optional) the transmission; status (optional) per instance (ldos of an

@@ -21,6 +21,9 @@ extern "C" cudaError_t knit_launch_sweep_fp64(const InstDev *, int, int, double2
 extern "C" cudaError_t knit_launch_ldos_fp64(const InstDev *, int, int, int, double2 *, int,
                                              double2 *, int, double *, long long, cudaStream_t);
 extern "C" size_t knit_fp64_smem_bytes(int, int, int);
+extern "C" cudaError_t knit_launch_graph_fp64(const GraphDev *, const double *, int, const double2 *,
+                                              const double2 *, double2 *, int, double *, int *,
+                                              cudaStream_t);
 extern "C" cudaError_t knit_launch_lesser_fp64(const InstDev *, int, int, int, double2 *, double2 *,
                                                int, const int2 *, int, double *, double *, double *,
                                                double *, cudaStream_t);
@@ -180,6 +183,16 @@ struct knit_system_s {
         s.h0_val = h0_val;
         return s;
     }
+};
+
+// an arbitrary two-lead geometry cut into slices of varying width (graph_sweep.cu)
+struct knit_graph_s {
+    int N = 0, K = 0, Mmax = 0, w0 = 0, w1 = 0, device = 0, nsm = 1;
+    std::vector<int> hwidth, hslice_of;   // slice widths; slice of every site (-1: unreachable)
+    double2 *blocks = nullptr;
+    int *width = nullptr, *p1 = nullptr;
+    long long *hoff = nullptr, *voff = nullptr;
+    DevBuf work, E, T, status, s0, s1;
 };
 
 // learned warm start of a lead's surface Green function (lead_mlp.cu)
@@ -1002,6 +1015,159 @@ knit_status knit_transmission_eigenvalues(knit_system s, const double *E, int32_
     if (hSt)
         CK(cudaMemcpyAsync(status, in.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
     return finish(st, hTau || hNoise || hT || hSt, "knit_transmission_eigenvalues");
+}
+
+knit_status knit_graph_destroy(knit_graph g)
+{
+    if (!g) return KNIT_OK;
+    cudaSetDevice(g->device);
+    cudaFree(g->blocks);
+    cudaFree(g->width);
+    cudaFree(g->p1);
+    cudaFree(g->hoff);
+    cudaFree(g->voff);
+    DevBuf *bufs[] = {&g->work, &g->E, &g->T, &g->status, &g->s0, &g->s1};
+    for (DevBuf *b : bufs) b->release();
+    delete g;
+    return KNIT_OK;
+}
+
+knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
+{
+    if (!d || !out) return fail(KNIT_ERR_INVALID, "knit_graph_create: NULL argument");
+    *out = nullptr;
+    const int N = d->N, w0 = d->n_lead_sites[0], w1 = d->n_lead_sites[1];
+    if (N <= 0 || N > 8192) return fail(KNIT_ERR_INVALID, "N = %d out of range (1 .. 8192)", N);
+    if (!d->H || !d->lead_sites[0] || !d->lead_sites[1] || w0 <= 0 || w1 <= 0)
+        return fail(KNIT_ERR_INVALID, "H and both lead site lists are required");
+    std::vector<double2> H;
+    std::vector<int> l0, l1;
+    knit_status r;
+    if ((r = to_host(H, d->H, (size_t)N * N, "H")) != KNIT_OK) return r;
+    if ((r = to_host(l0, d->lead_sites[0], (size_t)w0, "lead_sites[0]")) != KNIT_OK) return r;
+    if ((r = to_host(l1, d->lead_sites[1], (size_t)w1, "lead_sites[1]")) != KNIT_OK) return r;
+    std::vector<int> which(N, -1);
+    for (int p = 0; p < 2; ++p)
+        for (int v : p ? l1 : l0) {
+            if (v < 0 || v >= N) return fail(KNIT_ERR_INVALID, "lead site %d out of range", v);
+            if (which[v] != -1) return fail(KNIT_ERR_INVALID, "site %d listed twice among the leads", v);
+            which[v] = p;
+        }
+    double hmax = 0.0;
+    for (double2 h : H) hmax = std::max(hmax, std::hypot(h.x, h.y));
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double2 a = H[(size_t)i * N + j], b = H[(size_t)j * N + i];
+            if (std::fabs(a.x - b.x) > 1e-12 * hmax || std::fabs(a.y + b.y) > 1e-12 * hmax)
+                return fail(KNIT_ERR_INVALID, "H is not Hermitian at (%d, %d)", i, j);
+        }
+    // breadth-first layers from lead 0's sites
+    std::vector<int> depth(N, -1), queue(l0);
+    for (int v : l0) depth[v] = 0;
+    for (size_t q = 0; q < queue.size(); ++q) {
+        const int u = queue[q];
+        for (int v = 0; v < N; ++v) {
+            const double2 h = H[(size_t)u * N + v];
+            if (v != u && depth[v] < 0 && (h.x != 0.0 || h.y != 0.0)) {
+                depth[v] = depth[u] + 1;
+                queue.push_back(v);
+            }
+        }
+    }
+    int d1 = 1 << 30;
+    for (int v : l1) {
+        if (depth[v] < 0) return fail(KNIT_ERR_INVALID, "lead 1 site %d is not connected to lead 0", v);
+        d1 = std::min(d1, depth[v]);
+    }
+    // slices: layers 0 .. d1-1, then every reachable site at depth >= d1
+    const int K = d1 + 1;
+    std::vector<std::vector<int>> sl(K);
+    sl[0] = l0;
+    for (int v = 0; v < N; ++v)
+        if (depth[v] > 0) sl[std::min(depth[v], d1)].push_back(v);
+    auto g = new knit_graph_s;
+    g->N = N;
+    g->K = K;
+    g->w0 = w0;
+    g->w1 = w1;
+    g->hslice_of.assign(N, -1);
+    std::vector<int> pos(N, -1);
+    for (int k = 0; k < K; ++k) {
+        g->hwidth.push_back((int)sl[k].size());
+        g->Mmax = std::max(g->Mmax, (int)sl[k].size());
+        for (size_t a = 0; a < sl[k].size(); ++a) {
+            g->hslice_of[sl[k][a]] = k;
+            pos[sl[k][a]] = (int)a;
+        }
+    }
+    std::vector<int> p1(w1);
+    for (int a = 0; a < w1; ++a) p1[a] = pos[l1[a]];
+    // blocks: H_k, then V_k = H_{k,k-1}
+    std::vector<double2> blk;
+    std::vector<long long> hoff(K), voff(K, 0);
+    for (int k = 0; k < K; ++k) {
+        hoff[k] = (long long)blk.size();
+        for (int a : sl[k])
+            for (int b : sl[k]) blk.push_back(H[(size_t)a * N + b]);
+        if (k > 0) {
+            voff[k] = (long long)blk.size();
+            for (int a : sl[k])
+                for (int b : sl[k - 1]) blk.push_back(H[(size_t)a * N + b]);
+        }
+    }
+    cudaGetDevice(&g->device);
+    cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device);
+    if ((r = to_device(&g->blocks, blk.data(), blk.size(), "graph blocks")) != KNIT_OK ||
+        (r = to_device(&g->width, g->hwidth.data(), (size_t)K, "slice widths")) != KNIT_OK ||
+        (r = to_device(&g->p1, p1.data(), (size_t)w1, "lead 1 positions")) != KNIT_OK ||
+        (r = to_device(&g->hoff, hoff.data(), (size_t)K, "block offsets")) != KNIT_OK ||
+        (r = to_device(&g->voff, voff.data(), (size_t)K, "block offsets")) != KNIT_OK) {
+        knit_graph_destroy(g);
+        return r;
+    }
+    *out = g;
+    return KNIT_OK;
+}
+
+knit_status knit_graph_slices(knit_graph g, int32_t *nslices, int32_t *widths, int32_t *slice_of)
+{
+    if (!g || !nslices) return fail(KNIT_ERR_INVALID, "knit_graph_slices: NULL argument");
+    *nslices = g->K;
+    if (widths) std::copy(g->hwidth.begin(), g->hwidth.end(), widths);
+    if (slice_of) std::copy(g->hslice_of.begin(), g->hslice_of.end(), slice_of);
+    return KNIT_OK;
+}
+
+knit_status knit_graph_transmission(knit_graph g, const double *E, int32_t nE,
+                                    const knit_c128 *sigma0, const knit_c128 *sigma1, double *T,
+                                    int32_t *status, void *stream)
+{
+    if (!g) return fail(KNIT_ERR_INVALID, "graph is NULL");
+    if (!E || !sigma0 || !sigma1 || !T) return fail(KNIT_ERR_INVALID, "E, sigma0, sigma1 and T are required");
+    if (nE <= 0) return fail(KNIT_ERR_INVALID, "nE must be positive");
+    cudaSetDevice(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    knit_status r;
+    const double *dE;
+    const double2 *d0, *d1;
+    if ((r = stage_in(g->E, E, (size_t)nE, st, &dE, "E")) != KNIT_OK ||
+        (r = stage_in(g->s0, (const double2 *)sigma0, (size_t)nE * g->w0 * g->w0, st, &d0, "sigma0")) != KNIT_OK ||
+        (r = stage_in(g->s1, (const double2 *)sigma1, (size_t)nE * g->w1 * g->w1, st, &d1, "sigma1")) != KNIT_OK)
+        return r;
+    bool hT, hSt = false;
+    double *dT;
+    int *dSt;
+    if ((r = stage_out(g->T, T, (size_t)nE, &dT, &hT, "T")) != KNIT_OK ||
+        (r = stage_out(g->status, (int *)status, (size_t)nE, &dSt, &hSt, "status")) != KNIT_OK)
+        return r;
+    const int grid = std::max(1, std::min(nE, g->nsm));
+    CK(g->work.ensure(sizeof(double2) * 5 * (size_t)g->Mmax * g->Mmax * grid), "graph workspace");
+    GraphDev gd{g->K, g->Mmax, g->w0, g->w1, g->width, g->hoff, g->voff, g->blocks, g->p1};
+    CK(knit_launch_graph_fp64(&gd, dE, nE, d0, d1, g->work.as<double2>(), grid, dT, dSt, st),
+       "graph sweep launch");
+    if (hT) CK(cudaMemcpyAsync(T, dT, sizeof(double) * nE, cudaMemcpyDeviceToHost, st), "T out");
+    if (hSt) CK(cudaMemcpyAsync(status, dSt, sizeof(int) * nE, cudaMemcpyDeviceToHost, st), "status out");
+    return finish(st, hT || hSt, "knit_graph_transmission");
 }
 
 knit_status knit_system_num_edges(knit_system s, int32_t *count)

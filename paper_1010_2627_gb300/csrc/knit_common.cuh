@@ -216,6 +216,16 @@ struct InstDev {
     double2 *GLL;              // optional: G_LL (M x M, complex128) at out position * M * M
 };
 
+// an arbitrary two-lead geometry cut into K slices (graph_sweep.cu)
+struct GraphDev {
+    int K, Mmax, w0, w1;
+    const int *width;          // K slice widths
+    const long long *hoff;     // offset of H_k (M_k x M_k) in blocks
+    const long long *voff;     // offset of V_k = H_{k,k-1} (M_k x M_{k-1}) in blocks, k >= 1
+    const double2 *blocks;
+    const int *p1;             // positions of lead 1's sites in the last slice (w1)
+};
+
 // parameters of one instance
 struct InstParams {
     int out;                   // output position

@@ -38,6 +38,10 @@ class knit_lead_opts(ctypes.Structure):
     _fields_ = [("method", i32), ("eta", f64), ("tol", f64), ("maxit", i32), ("model", P * 2)]
 
 
+class knit_graph_desc(ctypes.Structure):
+    _fields_ = [("N", i32), ("H", P), ("n_lead_sites", i32 * 2), ("lead_sites", P * 2)]
+
+
 class KnitError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"knit error {code}: {msg}")
@@ -57,6 +61,10 @@ _SIGS = {
     "knit_transmission_eigenvalues": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P, P]),
     "knit_lesser": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P, P, P, P]),
     "knit_system_num_edges": (i32, [P, P]),
+    "knit_graph_create": (i32, [P, P]),
+    "knit_graph_destroy": (i32, [P]),
+    "knit_graph_slices": (i32, [P, P, P, P]),
+    "knit_graph_transmission": (i32, [P, P, i32, P, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
     "knit_lead_model_train": (i32, [P, i32, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64,
@@ -228,6 +236,71 @@ def knit_lesser(handle, E, seeds, W, saving_level, rhoL=None, rhoR=None, jx=None
                               int(saving_level), None if opts is None else ctypes.byref(opts),
                               _ptr(rhoL), _ptr(rhoR), _ptr(jx), _ptr(jt), _ptr(T), _ptr(status),
                               _stream(stream)))
+
+
+def knit_graph_create(H, lead0, lead1):
+    """Handle of an arbitrary two-lead geometry (H: N x N complex128)."""
+    H = np.ascontiguousarray(H, dtype=np.complex128)
+    l0 = np.ascontiguousarray(lead0, dtype=np.int32)
+    l1 = np.ascontiguousarray(lead1, dtype=np.int32)
+    d = knit_graph_desc()
+    d.N = H.shape[0]
+    d.H = _ptr(H)
+    d.n_lead_sites[0], d.n_lead_sites[1] = len(l0), len(l1)
+    d.lead_sites[0], d.lead_sites[1] = _ptr(l0), _ptr(l1)
+    out = P()
+    _check(load().knit_graph_create(ctypes.byref(d), ctypes.byref(out)))
+    return out.value
+
+
+def knit_graph_destroy(handle):
+    _check(load().knit_graph_destroy(P(handle)))
+
+
+def knit_graph_slices(handle, N):
+    """(widths, slice_of) of the slicing."""
+    k = ctypes.c_int32(0)
+    _check(load().knit_graph_slices(P(handle), ctypes.byref(k), None, None))
+    w = np.empty(k.value, np.int32)
+    so = np.empty(N, np.int32)
+    _check(load().knit_graph_slices(P(handle), ctypes.byref(k), _ptr(w), _ptr(so)))
+    return w, so
+
+
+def knit_graph_transmission(handle, E, sigma0, sigma1, T, status=None, nE=None, stream=None):
+    nE = len(E) if nE is None else nE
+    _check(load().knit_graph_transmission(P(handle), _ptr(E), int(nE), _ptr(sigma0), _ptr(sigma1),
+                                          _ptr(T), _ptr(status), _stream(stream)))
+
+
+class Graph:
+    """Owns one knit_graph (an arbitrary two-lead geometry)."""
+
+    def __init__(self, H, lead0, lead1):
+        self.N = np.asarray(H).shape[0]
+        self.w = (len(lead0), len(lead1))
+        self.handle = knit_graph_create(H, lead0, lead1)
+
+    def close(self):
+        if self.handle:
+            knit_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def slices(self):
+        return knit_graph_slices(self.handle, self.N)
+
+    def transmission(self, E, sigma0, sigma1):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        T = np.empty(len(E))
+        st = np.empty(len(E), np.int32)
+        knit_graph_transmission(self.handle, E, _c128(sigma0), _c128(sigma1), T, st)
+        return T, st
 
 
 def knit_system_num_edges(handle) -> int:
