@@ -23,6 +23,9 @@ ctypes:
                      sewing), plain loops
 * ``rgf_batch``      ``rgf`` over many instances on all host cores (the CPU
                      baseline)
+* ``transmission_matrix``
+                     T_kl between every pair of several leads of a site
+                     graph (Sec. 2.3), dense numpy inverse
 * ``lesser_parts``   lead-resolved densities and bond currents from
                      G^<_l = i G Gamma_l G^+ (Sec. 2.3), dense numpy inverse
 * ``transmission_eigenvalues``, ``shot_noise``
@@ -283,6 +286,29 @@ def transmission_eigenvalues(G1L, SigL, SigR):
     G1L = np.asarray(G1L, dtype=np.complex128)
     H = S @ G1L @ _gamma(SigR) @ G1L.conj().T @ S
     return np.linalg.eigvalsh((H + H.conj().T) / 2)[::-1].copy()
+
+
+def transmission_matrix(H, E: float, lead_sites, sigmas):
+    """Multi-terminal transmissions T_kl = Re Tr[Gamma_k G_kl Gamma_l G_kl^+]
+    (Sec. 2.3, G^+_lk = (G_kl)^dagger for the retarded G) of an arbitrary
+    site graph with leads k attached to the sites lead_sites[k] through
+    self-energies sigmas[k], by the plain dense inverse of E - H - sum Sigma
+    (numpy).  Returns a (P, P) array with a zero diagonal."""
+    H = np.asarray(H, dtype=np.complex128)
+    N = H.shape[0]
+    A = E * np.eye(N) - H
+    idx = [np.asarray(s, dtype=int) for s in lead_sites]
+    for s, S in zip(idx, sigmas):
+        A[np.ix_(s, s)] -= np.asarray(S, dtype=np.complex128)
+    G = np.linalg.inv(A)
+    P = len(idx)
+    T = np.zeros((P, P))
+    for k in range(P):
+        for l in range(P):
+            if k != l:
+                B = G[np.ix_(idx[k], idx[l])]
+                T[k, l] = np.real(np.trace(_gamma(sigmas[k]) @ B @ _gamma(sigmas[l]) @ B.conj().T))
+    return T
 
 
 def lesser_parts(H0, V, eps, L: int, E: float, SigL, SigR):

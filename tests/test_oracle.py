@@ -533,3 +533,52 @@ def test_lesser_complex_hamiltonian_conservation():
         d = oracle.dense(ss.H0, ss.V, None, 5, E, SL, SR, want_ldos=True)
         assert np.abs(r["rhoL"] + r["rhoR"] - d["ldos"]).max() < 1e-11
         assert np.abs(r["jx"].sum(axis=1) - d["T_LR"]).max() < 1e-11
+
+
+# --------------------------------------------------------------------------
+# Multi-terminal transmissions (Sec. 2.3 T_kl between every pair of leads)
+
+def _chain_sigma(E):
+    """t^2 g_s of a semi-infinite chain with hopping t = 1 (1 x 1)."""
+    return oracle.sigma_square(1, 1.0, E)
+
+
+@pytest.mark.parametrize("E", [-1.4, 0.0, 0.8, 1.9])
+def test_y_junction_closed_form(E):
+    """Three semi-infinite chains (t = 1) meeting at one site: with
+    E = 2 cos k every pair transmits T = 4 sin^2 k / (cos^2 k + 9 sin^2 k)
+    (the centre's G = 1 / (E - 3 e^{ik}), Gamma = 2 sin k); 4/9 at E = 0."""
+    N = 4                          # centre 0, first site of each arm 1..3
+    H = np.zeros((N, N), np.complex128)
+    for a in (1, 2, 3):
+        H[0, a] = H[a, 0] = 1.0
+    S = _chain_sigma(E)
+    T = oracle.transmission_matrix(H, E, [[1], [2], [3]], [S, S, S])
+    k = np.arccos(E / 2)
+    want = 4 * np.sin(k) ** 2 / (np.cos(k) ** 2 + 9 * np.sin(k) ** 2)
+    off = T[~np.eye(3, dtype=bool)]
+    assert np.abs(off - want).max() < 1e-12
+    assert np.all(np.diag(T) == 0)
+
+
+def test_transmission_matrix_two_leads_and_sum_rule():
+    """Two leads: the dense two-lead C routine's T_{0<-1} and T_{1<-0}; four
+    leads on a random complex graph: sum_l T_kl = sum_l T_lk for every lead
+    (Buttiker's sum rule for a lossless conductor)."""
+    rng = np.random.default_rng(5)
+    H, idx0, idx1, w0, w1 = inputs.lshape_example()
+    for E in (-1.59, 0.41):
+        S0, S1 = oracle.sigma_square(w0, 1.0, E), oracle.sigma_square(w1, 1.0, E)
+        T = oracle.transmission_matrix(H, E, [idx0, idx1], [S0, S1])
+        T10, T01 = oracle.dense_general(H, E, idx0, S0, idx1, S1)
+        assert abs(T[0, 1] - T01) < 1e-11 and abs(T[1, 0] - T10) < 1e-11
+    N = 30
+    A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    Hr = (A + A.conj().T) / 2 * (rng.random((N, N)) < 0.2)
+    Hr = (Hr + Hr.conj().T) / 2
+    sites = rng.permutation(N)[:9]
+    leads = [sites[:2], sites[2:4], sites[4:7], sites[7:9]]
+    sig = [inputs.random_retarded_sigma(rng, len(s)) for s in leads]
+    T = oracle.transmission_matrix(Hr, 0.3, leads, sig)
+    assert np.abs(T.sum(axis=1) - T.sum(axis=0)).max() < 1e-10
+    assert (T[~np.eye(4, dtype=bool)] > -1e-12).all()
