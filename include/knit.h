@@ -222,17 +222,20 @@ knit_status knit_lesser(knit_system sys, const double *E, int32_t nE, const uint
 knit_status knit_system_num_edges(knit_system sys, int32_t *count);
 
 /* ---------------------------------------------------------------------
- * Arbitrary two-lead geometries (Sec. 5.3: knitting through an interface of
- * varying width; Sec. 2.2 worked example, Fig. 3).  H is the N x N
- * Hermitian Hamiltonian of the system's sites (dense, row-major, host or
- * device memory); lead p is attached to the n_lead_sites[p] sites
- * lead_sites[p] (in the order of its self-energy's rows).  The library cuts
- * the sites into slices of varying width: breadth-first layers from lead 0's
- * sites, the layers from the first one holding a lead-1 site onwards merged
- * into the last slice (sites not connected to lead 0 are left out), so that
- * H is block tridiagonal with rectangular couplings.  KNIT_ERR_INVALID for
- * N outside 1 .. 8192, a non-Hermitian H (relative 1e-12), overlapping or
- * out-of-range lead sites, or lead 1 not connected to lead 0. */
+ * Arbitrary geometries (Sec. 5.3: knitting through an interface of varying
+ * width; Sec. 2.2 worked example, Fig. 3; Sec. 7.3 conductance_matrix).  H
+ * is the N x N Hermitian Hamiltonian of the system's sites (dense,
+ * row-major, host or device memory); lead p is attached to the
+ * n_lead_sites[p] sites lead_sites[p] (in the order of its self-energy's
+ * rows).  The library cuts the sites into slices of varying width:
+ * breadth-first layers from lead 0's sites, the layers from the first one
+ * holding a site of another lead onwards merged into the last slice (sites
+ * not connected to lead 0 are left out), so that H is block tridiagonal with
+ * rectangular couplings and every lead but lead 0 sits in the last slice.
+ * KNIT_ERR_INVALID for N outside 1 .. 8192, fewer than 2 or more than 64
+ * leads, a non-Hermitian H (relative 1e-12), overlapping or out-of-range lead
+ * sites, or a lead not connected to lead 0.  The graph calls return after
+ * the sweep has finished. */
 typedef struct knit_graph_s *knit_graph;
 typedef struct {
     int32_t N;
@@ -240,8 +243,16 @@ typedef struct {
     int32_t n_lead_sites[2];
     const int32_t *lead_sites[2];
 } knit_graph_desc;
+typedef struct {
+    int32_t N;
+    const knit_c128 *H;
+    int32_t n_leads;                 /* P >= 2 */
+    const int32_t *n_lead_sites;     /* P */
+    const int32_t *const *lead_sites;/* P lists */
+} knit_graph_multi_desc;
 
 knit_status knit_graph_create(const knit_graph_desc *desc, knit_graph *out);
+knit_status knit_graph_create_multi(const knit_graph_multi_desc *desc, knit_graph *out);
 knit_status knit_graph_destroy(knit_graph g);
 
 /* The slicing: number of slices, their widths (nslices values, optional) and
@@ -258,6 +269,14 @@ knit_status knit_graph_slices(knit_graph g, int32_t *nslices, int32_t *widths,
 knit_status knit_graph_transmission(knit_graph g, const double *E, int32_t nE,
                                     const knit_c128 *sigma0, const knit_c128 *sigma1, double *T,
                                     int32_t *status, void *stream);
+
+/* Multi-terminal transmissions (Sec. 2.3 T_kl for every pair of leads; Sec.
+ * 7.3 conductance_matrix): Tmat (nE x P x P, [e][k][l]) receives
+ * T_kl = Re Tr[Gamma_k G_kl Gamma_l G_kl^dagger] for k != l and 0 on the
+ * diagonal; sigma: P pointers, lead p's self-energies nE x w_p x w_p. */
+knit_status knit_graph_conductance(knit_graph g, const double *E, int32_t nE,
+                                   const knit_c128 *const *sigma, double *Tmat, int32_t *status,
+                                   void *stream);
 
 /* Local density of states (Sec. 5.3 D knitting followed by sewing):
  * ldos (nE*nS*L*M, row-major [i][n][x]) receives -Im G_nn[x][x]/pi; T

@@ -21,8 +21,9 @@ extern "C" cudaError_t knit_launch_sweep_fp64(const InstDev *, int, int, double2
 extern "C" cudaError_t knit_launch_ldos_fp64(const InstDev *, int, int, int, double2 *, int,
                                              double2 *, int, double *, long long, cudaStream_t);
 extern "C" size_t knit_fp64_smem_bytes(int, int, int);
-extern "C" cudaError_t knit_launch_graph_fp64(const GraphDev *, const double *, int, const double2 *,
-                                              const double2 *, double2 *, int, double *, int *,
+extern "C" cudaError_t knit_launch_graph_fp64(const GraphDev *, const double *, int, double2 *, int,
+                                              double *, int *, cudaStream_t);
+extern "C" cudaError_t knit_launch_graph_pick(const double *, int, int, int, int, double *,
                                               cudaStream_t);
 extern "C" cudaError_t knit_launch_lesser_fp64(const InstDev *, int, int, int, double2 *, double2 *,
                                                int, const int2 *, int, double *, double *, double *,
@@ -185,14 +186,14 @@ struct knit_system_s {
     }
 };
 
-// an arbitrary two-lead geometry cut into slices of varying width (graph_sweep.cu)
+// an arbitrary geometry with P leads cut into slices of varying width (graph_sweep.cu)
 struct knit_graph_s {
-    int N = 0, K = 0, Mmax = 0, w0 = 0, w1 = 0, device = 0, nsm = 1;
-    std::vector<int> hwidth, hslice_of;   // slice widths; slice of every site (-1: unreachable)
+    int N = 0, K = 0, Mmax = 0, P = 0, device = 0, nsm = 1;
+    std::vector<int> hwidth, hslice_of, hlw;   // slice widths; slice of every site; lead widths
     double2 *blocks = nullptr;
-    int *width = nullptr, *p1 = nullptr;
+    int *width = nullptr, *lw = nullptr, *lpos = nullptr, *loff = nullptr;
     long long *hoff = nullptr, *voff = nullptr;
-    DevBuf work, E, T, status, s0, s1;
+    DevBuf work, E, Tm, T, status, sigp, sigs;
 };
 
 // learned warm start of a lead's surface Green function (lead_mlp.cu)
@@ -1023,36 +1024,40 @@ knit_status knit_graph_destroy(knit_graph g)
     cudaSetDevice(g->device);
     cudaFree(g->blocks);
     cudaFree(g->width);
-    cudaFree(g->p1);
+    cudaFree(g->lw);
+    cudaFree(g->lpos);
+    cudaFree(g->loff);
     cudaFree(g->hoff);
     cudaFree(g->voff);
-    DevBuf *bufs[] = {&g->work, &g->E, &g->T, &g->status, &g->s0, &g->s1};
+    DevBuf *bufs[] = {&g->work, &g->E, &g->Tm, &g->T, &g->status, &g->sigp, &g->sigs};
     for (DevBuf *b : bufs) b->release();
     delete g;
     return KNIT_OK;
 }
 
-knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
+namespace {
+
+knit_status graph_build(int N, const knit_c128 *Hin, int P, const int32_t *nsites,
+                        const int32_t *const *sites, knit_graph *out)
 {
-    if (!d || !out) return fail(KNIT_ERR_INVALID, "knit_graph_create: NULL argument");
     *out = nullptr;
-    const int N = d->N, w0 = d->n_lead_sites[0], w1 = d->n_lead_sites[1];
     if (N <= 0 || N > 8192) return fail(KNIT_ERR_INVALID, "N = %d out of range (1 .. 8192)", N);
-    if (!d->H || !d->lead_sites[0] || !d->lead_sites[1] || w0 <= 0 || w1 <= 0)
-        return fail(KNIT_ERR_INVALID, "H and both lead site lists are required");
+    if (P < 2 || P > 64) return fail(KNIT_ERR_INVALID, "%d leads: 2 .. 64 supported", P);
+    if (!Hin || !nsites || !sites) return fail(KNIT_ERR_INVALID, "H and the lead site lists are required");
     std::vector<double2> H;
-    std::vector<int> l0, l1;
     knit_status r;
-    if ((r = to_host(H, d->H, (size_t)N * N, "H")) != KNIT_OK) return r;
-    if ((r = to_host(l0, d->lead_sites[0], (size_t)w0, "lead_sites[0]")) != KNIT_OK) return r;
-    if ((r = to_host(l1, d->lead_sites[1], (size_t)w1, "lead_sites[1]")) != KNIT_OK) return r;
+    if ((r = to_host(H, Hin, (size_t)N * N, "H")) != KNIT_OK) return r;
+    std::vector<std::vector<int>> ls(P);
     std::vector<int> which(N, -1);
-    for (int p = 0; p < 2; ++p)
-        for (int v : p ? l1 : l0) {
+    for (int p = 0; p < P; ++p) {
+        if (nsites[p] <= 0 || !sites[p]) return fail(KNIT_ERR_INVALID, "lead %d has no sites", p);
+        if ((r = to_host(ls[p], sites[p], (size_t)nsites[p], "lead sites")) != KNIT_OK) return r;
+        for (int v : ls[p]) {
             if (v < 0 || v >= N) return fail(KNIT_ERR_INVALID, "lead site %d out of range", v);
             if (which[v] != -1) return fail(KNIT_ERR_INVALID, "site %d listed twice among the leads", v);
             which[v] = p;
         }
+    }
     double hmax = 0.0;
     for (double2 h : H) hmax = std::max(hmax, std::hypot(h.x, h.y));
     for (int i = 0; i < N; ++i)
@@ -1062,8 +1067,8 @@ knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
                 return fail(KNIT_ERR_INVALID, "H is not Hermitian at (%d, %d)", i, j);
         }
     // breadth-first layers from lead 0's sites
-    std::vector<int> depth(N, -1), queue(l0);
-    for (int v : l0) depth[v] = 0;
+    std::vector<int> depth(N, -1), queue(ls[0]);
+    for (int v : ls[0]) depth[v] = 0;
     for (size_t q = 0; q < queue.size(); ++q) {
         const int u = queue[q];
         for (int v = 0; v < N; ++v) {
@@ -1075,21 +1080,22 @@ knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
         }
     }
     int d1 = 1 << 30;
-    for (int v : l1) {
-        if (depth[v] < 0) return fail(KNIT_ERR_INVALID, "lead 1 site %d is not connected to lead 0", v);
-        d1 = std::min(d1, depth[v]);
-    }
+    for (int p = 1; p < P; ++p)
+        for (int v : ls[p]) {
+            if (depth[v] < 0)
+                return fail(KNIT_ERR_INVALID, "site %d of lead %d is not connected to lead 0", v, p);
+            d1 = std::min(d1, depth[v]);
+        }
     // slices: layers 0 .. d1-1, then every reachable site at depth >= d1
     const int K = d1 + 1;
     std::vector<std::vector<int>> sl(K);
-    sl[0] = l0;
+    sl[0] = ls[0];
     for (int v = 0; v < N; ++v)
         if (depth[v] > 0) sl[std::min(depth[v], d1)].push_back(v);
     auto g = new knit_graph_s;
     g->N = N;
     g->K = K;
-    g->w0 = w0;
-    g->w1 = w1;
+    g->P = P;
     g->hslice_of.assign(N, -1);
     std::vector<int> pos(N, -1);
     for (int k = 0; k < K; ++k) {
@@ -1100,8 +1106,12 @@ knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
             pos[sl[k][a]] = (int)a;
         }
     }
-    std::vector<int> p1(w1);
-    for (int a = 0; a < w1; ++a) p1[a] = pos[l1[a]];
+    std::vector<int> lpos, loff;
+    for (int p = 0; p < P; ++p) {
+        g->hlw.push_back((int)ls[p].size());
+        loff.push_back((int)lpos.size());
+        for (int v : ls[p]) lpos.push_back(pos[v]);
+    }
     // blocks: H_k, then V_k = H_{k,k-1}
     std::vector<double2> blk;
     std::vector<long long> hoff(K), voff(K, 0);
@@ -1119,7 +1129,9 @@ knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
     cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device);
     if ((r = to_device(&g->blocks, blk.data(), blk.size(), "graph blocks")) != KNIT_OK ||
         (r = to_device(&g->width, g->hwidth.data(), (size_t)K, "slice widths")) != KNIT_OK ||
-        (r = to_device(&g->p1, p1.data(), (size_t)w1, "lead 1 positions")) != KNIT_OK ||
+        (r = to_device(&g->lw, g->hlw.data(), (size_t)P, "lead widths")) != KNIT_OK ||
+        (r = to_device(&g->lpos, lpos.data(), lpos.size(), "lead positions")) != KNIT_OK ||
+        (r = to_device(&g->loff, loff.data(), loff.size(), "lead offsets")) != KNIT_OK ||
         (r = to_device(&g->hoff, hoff.data(), (size_t)K, "block offsets")) != KNIT_OK ||
         (r = to_device(&g->voff, voff.data(), (size_t)K, "block offsets")) != KNIT_OK) {
         knit_graph_destroy(g);
@@ -1127,6 +1139,61 @@ knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
     }
     *out = g;
     return KNIT_OK;
+}
+
+// the sweep for nE energies: Tm (device, nE x P x P) and status (device)
+knit_status graph_run(knit_graph g, const double *E, int nE, const knit_c128 *const *sigma,
+                      double *Tm, int *status, cudaStream_t st)
+{
+    knit_status r;
+    const double *dE;
+    if ((r = stage_in(g->E, E, (size_t)nE, st, &dE, "E")) != KNIT_OK) return r;
+    // self-energies: device copies of host arrays in one buffer, then the pointer table
+    std::vector<const double2 *> ptr(g->P);
+    size_t host_elems = 0;
+    for (int p = 0; p < g->P; ++p) {
+        if (!sigma[p]) return fail(KNIT_ERR_INVALID, "self-energy of lead %d is NULL", p);
+        if (!is_device_ptr(sigma[p])) host_elems += (size_t)nE * g->hlw[p] * g->hlw[p];
+    }
+    CK(g->sigs.ensure(sizeof(double2) * std::max<size_t>(host_elems, 1)), "self-energy staging");
+    size_t off = 0;
+    for (int p = 0; p < g->P; ++p) {
+        const size_t n = (size_t)nE * g->hlw[p] * g->hlw[p];
+        if (is_device_ptr(sigma[p])) {
+            ptr[p] = (const double2 *)sigma[p];
+        } else {
+            ptr[p] = g->sigs.as<double2>() + off;
+            CK(cudaMemcpyAsync((void *)ptr[p], sigma[p], sizeof(double2) * n, cudaMemcpyHostToDevice, st),
+               "self-energy in");
+            off += n;
+        }
+    }
+    CK(g->sigp.ensure(sizeof(double2 *) * g->P), "self-energy table");
+    CK(cudaMemcpyAsync(g->sigp.p, ptr.data(), sizeof(double2 *) * g->P, cudaMemcpyHostToDevice, st),
+       "self-energy table");
+    const int grid = std::max(1, std::min(nE, g->nsm));
+    CK(g->work.ensure(sizeof(double2) * 6 * (size_t)g->Mmax * g->Mmax * grid), "graph workspace");
+    GraphDev gd{g->K, g->Mmax, g->P, g->width, g->hoff, g->voff, g->blocks, g->lw, g->lpos, g->loff,
+                g->sigp.as<const double2 *>()};
+    CK(knit_launch_graph_fp64(&gd, dE, nE, g->work.as<double2>(), grid, Tm, status, st),
+       "graph sweep launch");
+    // the pointer table and host staging must outlive the launch
+    CK(cudaStreamSynchronize(st), "graph sweep");
+    return KNIT_OK;
+}
+
+}  // namespace
+
+knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
+{
+    if (!d || !out) return fail(KNIT_ERR_INVALID, "knit_graph_create: NULL argument");
+    return graph_build(d->N, d->H, 2, d->n_lead_sites, d->lead_sites, out);
+}
+
+knit_status knit_graph_create_multi(const knit_graph_multi_desc *d, knit_graph *out)
+{
+    if (!d || !out) return fail(KNIT_ERR_INVALID, "knit_graph_create_multi: NULL argument");
+    return graph_build(d->N, d->H, d->n_leads, d->n_lead_sites, d->lead_sites, out);
 }
 
 knit_status knit_graph_slices(knit_graph g, int32_t *nslices, int32_t *widths, int32_t *slice_of)
@@ -1138,33 +1205,50 @@ knit_status knit_graph_slices(knit_graph g, int32_t *nslices, int32_t *widths, i
     return KNIT_OK;
 }
 
+knit_status knit_graph_conductance(knit_graph g, const double *E, int32_t nE,
+                                   const knit_c128 *const *sigma, double *Tmat, int32_t *status,
+                                   void *stream)
+{
+    if (!g) return fail(KNIT_ERR_INVALID, "graph is NULL");
+    if (!E || !sigma || !Tmat) return fail(KNIT_ERR_INVALID, "E, sigma and Tmat are required");
+    if (nE <= 0) return fail(KNIT_ERR_INVALID, "nE must be positive");
+    cudaSetDevice(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    knit_status r;
+    bool hT, hSt = false;
+    double *dT;
+    int *dSt;
+    const size_t nT = (size_t)nE * g->P * g->P;
+    if ((r = stage_out(g->Tm, Tmat, nT, &dT, &hT, "Tmat")) != KNIT_OK ||
+        (r = stage_out(g->status, (int *)status, (size_t)nE, &dSt, &hSt, "status")) != KNIT_OK)
+        return r;
+    if ((r = graph_run(g, E, nE, sigma, dT, dSt, st)) != KNIT_OK) return r;
+    if (hT) CK(cudaMemcpyAsync(Tmat, dT, sizeof(double) * nT, cudaMemcpyDeviceToHost, st), "Tmat out");
+    if (hSt) CK(cudaMemcpyAsync(status, dSt, sizeof(int) * nE, cudaMemcpyDeviceToHost, st), "status out");
+    return finish(st, hT || hSt, "knit_graph_conductance");
+}
+
 knit_status knit_graph_transmission(knit_graph g, const double *E, int32_t nE,
                                     const knit_c128 *sigma0, const knit_c128 *sigma1, double *T,
                                     int32_t *status, void *stream)
 {
     if (!g) return fail(KNIT_ERR_INVALID, "graph is NULL");
+    if (g->P != 2) return fail(KNIT_ERR_INVALID, "knit_graph_transmission needs a two-lead graph");
     if (!E || !sigma0 || !sigma1 || !T) return fail(KNIT_ERR_INVALID, "E, sigma0, sigma1 and T are required");
     if (nE <= 0) return fail(KNIT_ERR_INVALID, "nE must be positive");
     cudaSetDevice(g->device);
     cudaStream_t st = (cudaStream_t)stream;
     knit_status r;
-    const double *dE;
-    const double2 *d0, *d1;
-    if ((r = stage_in(g->E, E, (size_t)nE, st, &dE, "E")) != KNIT_OK ||
-        (r = stage_in(g->s0, (const double2 *)sigma0, (size_t)nE * g->w0 * g->w0, st, &d0, "sigma0")) != KNIT_OK ||
-        (r = stage_in(g->s1, (const double2 *)sigma1, (size_t)nE * g->w1 * g->w1, st, &d1, "sigma1")) != KNIT_OK)
-        return r;
     bool hT, hSt = false;
     double *dT;
     int *dSt;
     if ((r = stage_out(g->T, T, (size_t)nE, &dT, &hT, "T")) != KNIT_OK ||
         (r = stage_out(g->status, (int *)status, (size_t)nE, &dSt, &hSt, "status")) != KNIT_OK)
         return r;
-    const int grid = std::max(1, std::min(nE, g->nsm));
-    CK(g->work.ensure(sizeof(double2) * 5 * (size_t)g->Mmax * g->Mmax * grid), "graph workspace");
-    GraphDev gd{g->K, g->Mmax, g->w0, g->w1, g->width, g->hoff, g->voff, g->blocks, g->p1};
-    CK(knit_launch_graph_fp64(&gd, dE, nE, d0, d1, g->work.as<double2>(), grid, dT, dSt, st),
-       "graph sweep launch");
+    CK(g->Tm.ensure(sizeof(double) * 4 * (size_t)nE), "transmission matrix");
+    const knit_c128 *sig[2] = {sigma0, sigma1};
+    if ((r = graph_run(g, E, nE, sig, g->Tm.as<double>(), dSt, st)) != KNIT_OK) return r;
+    CK(knit_launch_graph_pick(g->Tm.as<double>(), nE, 2, 0, 1, dT, st), "transmission pick");
     if (hT) CK(cudaMemcpyAsync(T, dT, sizeof(double) * nE, cudaMemcpyDeviceToHost, st), "T out");
     if (hSt) CK(cudaMemcpyAsync(status, dSt, sizeof(int) * nE, cudaMemcpyDeviceToHost, st), "status out");
     return finish(st, hT || hSt, "knit_graph_transmission");

@@ -216,14 +216,19 @@ struct InstDev {
     double2 *GLL;              // optional: G_LL (M x M, complex128) at out position * M * M
 };
 
-// an arbitrary two-lead geometry cut into K slices (graph_sweep.cu)
+// an arbitrary geometry with P leads cut into K slices (graph_sweep.cu):
+// lead 0's sites are slice 0 (in order), every other lead's sites lie in the
+// last slice at positions lpos[loff[p] + a]
 struct GraphDev {
-    int K, Mmax, w0, w1;
+    int K, Mmax, P;
     const int *width;          // K slice widths
     const long long *hoff;     // offset of H_k (M_k x M_k) in blocks
     const long long *voff;     // offset of V_k = H_{k,k-1} (M_k x M_{k-1}) in blocks, k >= 1
     const double2 *blocks;
-    const int *p1;             // positions of lead 1's sites in the last slice (w1)
+    const int *lw;             // P lead widths
+    const int *lpos;           // lead sites' positions (slice 0 for lead 0, else the last slice)
+    const int *loff;           // P offsets into lpos
+    const double2 *const *sig; // P self-energy arrays, lead p at energy e: sig[p] + e * lw[p]^2
 };
 
 // parameters of one instance

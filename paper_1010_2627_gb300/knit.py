@@ -42,6 +42,10 @@ class knit_graph_desc(ctypes.Structure):
     _fields_ = [("N", i32), ("H", P), ("n_lead_sites", i32 * 2), ("lead_sites", P * 2)]
 
 
+class knit_graph_multi_desc(ctypes.Structure):
+    _fields_ = [("N", i32), ("H", P), ("n_leads", i32), ("n_lead_sites", P), ("lead_sites", P)]
+
+
 class KnitError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"knit error {code}: {msg}")
@@ -65,6 +69,8 @@ _SIGS = {
     "knit_graph_destroy": (i32, [P]),
     "knit_graph_slices": (i32, [P, P, P, P]),
     "knit_graph_transmission": (i32, [P, P, i32, P, P, P, P, P]),
+    "knit_graph_create_multi": (i32, [P, P]),
+    "knit_graph_conductance": (i32, [P, P, i32, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
     "knit_lead_model_train": (i32, [P, i32, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64,
@@ -253,6 +259,31 @@ def knit_graph_create(H, lead0, lead1):
     return out.value
 
 
+def knit_graph_create_multi(H, leads):
+    """Handle of an arbitrary geometry with several leads (site lists)."""
+    H = np.ascontiguousarray(H, dtype=np.complex128)
+    ls = [np.ascontiguousarray(l, dtype=np.int32) for l in leads]
+    n = np.array([len(l) for l in ls], np.int32)
+    ptrs = (P * len(ls))(*[l.ctypes.data for l in ls])
+    d = knit_graph_multi_desc()
+    d.N = H.shape[0]
+    d.H = _ptr(H)
+    d.n_leads = len(ls)
+    d.n_lead_sites = _ptr(n)
+    d.lead_sites = ctypes.cast(ptrs, P)
+    out = P()
+    _check(load().knit_graph_create_multi(ctypes.byref(d), ctypes.byref(out)))
+    return out.value
+
+
+def knit_graph_conductance(handle, E, sigmas, Tmat, status=None, nE=None, stream=None):
+    """sigmas: one (nE, w_p, w_p) complex128 array (or device tensor) per lead."""
+    nE = len(E) if nE is None else nE
+    ptrs = (P * len(sigmas))(*[_ptr(s) for s in sigmas])
+    _check(load().knit_graph_conductance(P(handle), _ptr(E), int(nE), ctypes.cast(ptrs, P),
+                                         _ptr(Tmat), _ptr(status), _stream(stream)))
+
+
 def knit_graph_destroy(handle):
     _check(load().knit_graph_destroy(P(handle)))
 
@@ -274,12 +305,16 @@ def knit_graph_transmission(handle, E, sigma0, sigma1, T, status=None, nE=None, 
 
 
 class Graph:
-    """Owns one knit_graph (an arbitrary two-lead geometry)."""
+    """Owns one knit_graph: Graph(H, lead0, lead1) or Graph(H, leads=[...])."""
 
-    def __init__(self, H, lead0, lead1):
+    def __init__(self, H, lead0=None, lead1=None, leads=None):
         self.N = np.asarray(H).shape[0]
-        self.w = (len(lead0), len(lead1))
-        self.handle = knit_graph_create(H, lead0, lead1)
+        if leads is None:
+            self.handle = knit_graph_create(H, lead0, lead1)
+            self.P = 2
+        else:
+            self.handle = knit_graph_create_multi(H, leads)
+            self.P = len(leads)
 
     def close(self):
         if self.handle:
@@ -301,6 +336,15 @@ class Graph:
         st = np.empty(len(E), np.int32)
         knit_graph_transmission(self.handle, E, _c128(sigma0), _c128(sigma1), T, st)
         return T, st
+
+    def conductance(self, E, sigmas):
+        """(Tmat (nE, P, P), status): T_kl between every pair of leads."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        Tm = np.empty((len(E), self.P, self.P))
+        st = np.empty(len(E), np.int32)
+        sig = [_c128(s) for s in sigmas]
+        knit_graph_conductance(self.handle, E, sig, Tm, st)
+        return Tm, st
 
 
 def knit_system_num_edges(handle) -> int:

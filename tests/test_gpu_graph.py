@@ -113,3 +113,68 @@ def test_graph_disconnected_sites_and_invalid(knit):
     Hn[0, 1] = 2.0
     with pytest.raises(Exception):
         knit.Graph(Hn, [0], [3])              # not Hermitian
+
+
+# --------------------------------------------------------------------------
+# several leads: the transmission matrix T_kl (Sec. 2.3, Sec. 7.3 conductance_matrix)
+
+def test_y_junction_closed_form(knit):
+    """Three chains meeting at one site: every pair transmits
+    4 sin^2 k / (cos^2 k + 9 sin^2 k) at E = 2 cos k."""
+    H = np.zeros((4, 4), np.complex128)
+    for a in (1, 2, 3):
+        H[0, a] = H[a, 0] = 1.0
+    E = np.array([-1.4, 0.0, 0.8, 1.9])
+    S = lead_sigma(knit, 1, E)
+    Tm, st = knit.Graph(H, leads=[[1], [2], [3]]).conductance(E, [S, S, S])
+    assert (st == 0).all()
+    k = np.arccos(E / 2)
+    want = 4 * np.sin(k) ** 2 / (np.cos(k) ** 2 + 9 * np.sin(k) ** 2)
+    off = ~np.eye(3, dtype=bool)
+    for e in range(len(E)):
+        assert np.abs(Tm[e][off] - want[e]).max() < 1e-12
+        assert np.all(np.diag(Tm[e]) == 0)
+
+
+def test_hall_bar_four_leads_matches_oracle(knit):
+    """A disordered 12 x 6 bar with leads on both ends and two side probes on
+    the top and bottom edges (the side leads sit at different depths, so the
+    last slice is merged): every T_kl against the dense oracle; Buttiker's
+    sum rule on the GPU output."""
+    Lx, Ly = 12, 6
+    rng = np.random.default_rng(3)
+    idx = lambda x, y: x * Ly + y
+    N = Lx * Ly
+    H = np.zeros((N, N), np.complex128)
+    for x in range(Lx):
+        for y in range(Ly):
+            H[idx(x, y), idx(x, y)] = rng.uniform(-1, 1)
+            if x + 1 < Lx:
+                H[idx(x, y), idx(x + 1, y)] = H[idx(x + 1, y), idx(x, y)] = 1.0
+            if y + 1 < Ly:
+                H[idx(x, y), idx(x, y + 1)] = H[idx(x, y + 1), idx(x, y)] = 1.0
+    leads = [[idx(0, y) for y in range(Ly)], [idx(Lx - 1, y) for y in range(Ly)],
+             [idx(x, Ly - 1) for x in range(4, 7)], [idx(x, 0) for x in range(6, 9)]]
+    E = np.array([-1.7, -0.3, 0.9])
+    sig = [lead_sigma(knit, len(l), E) for l in leads]
+    Tm, st = knit.Graph(H, leads=leads).conductance(E, sig)
+    assert (st == 0).all()
+    for e, Ee in enumerate(E):
+        To = oracle.transmission_matrix(H, Ee, leads, [s[e] for s in sig])
+        assert np.abs(Tm[e] - To).max() < 1e-10 * max(1.0, np.abs(To).max())
+        assert np.abs(Tm[e].sum(axis=1) - Tm[e].sum(axis=0)).max() < 1e-9
+
+
+def test_random_graph_four_leads_matches_oracle(knit):
+    rng = np.random.default_rng(17)
+    N = 50
+    H, _, _ = random_graph(rng, N, 0.05, 1, 1)
+    perm = rng.permutation(N)
+    leads = [perm[:2], perm[2:5], perm[5:6], perm[6:10]]
+    E = np.array([-0.6, 0.35])
+    sig = [np.stack([inputs.random_retarded_sigma(rng, len(l)) for _ in E]) for l in leads]
+    Tm, st = knit.Graph(H, leads=leads).conductance(E, sig)
+    assert (st == 0).all()
+    for e, Ee in enumerate(E):
+        To = oracle.transmission_matrix(H, Ee, leads, [s[e] for s in sig])
+        assert np.abs(Tm[e] - To).max() < 1e-9 * max(1.0, np.abs(To).max())
