@@ -9,7 +9,9 @@
 //    A_n = -Gv' and the residual of an approximate inverse X' is
 //    R = I - A_n X' = I + Gv' X';
 //  * X = complex64 inverse of fl32(A_n) by blocked Gauss-Jordan with
-//    implicit partial pivoting and look-ahead (gj_lookahead, 512 threads);
+//    implicit partial pivoting, the rank-8 panel updates on the tensor cores
+//    (gj_tc.cuh: bf16 terms, five exact-order accumulators in the same
+//    tensor memory, 320 of the 512 columns);
 //  * X is rounded at a per-column power-of-two scale tau_n to 24 bits,
 //    X' = tau_n 2^-8 (d0 + d1 2^-8 + d2 2^-16), |d| <= 256 integers (three
 //    bf16 "digits", exact, and X' itself exact in fp32); the refinement uses
@@ -41,6 +43,7 @@
 
 #include <cuda_bf16.h>
 
+#include "gj_tc.cuh"
 #include "mixed_common.cuh"
 #include "tc_common.cuh"
 
@@ -56,7 +59,6 @@ constexpr int NDA = 7;                // digits of Gv
 constexpr int NDB = 3;                // digits of X
 constexpr int NACC = 7;               // accumulators d = p + q = 0 .. 6, each exact
 constexpr int RS = MPT + 1;           // padded row stride of R
-constexpr int GJ_NB = 8;              // Gauss-Jordan panel width
 constexpr int MAX_NNZ = 256;          // sparse H0 rows cached in shared memory up to this
 constexpr uint32_t TMEM_COLS = 512;   // 7 accumulators x 64 columns, rounded up
 
@@ -66,10 +68,7 @@ struct TcSmem {
     union {
         unsigned char adig[2 * NDA * A_TILE];    // A digits of two K-chunks
         float2 R[MPT * RS];                      // residual (after the products)
-        struct {
-            float2 U[2 * MPT * gj_ust(GJ_NB)];
-            float2 V[2 * GJ_NB * MPT];
-        } pv;                                    // Gauss-Jordan panels (two in turn)
+        GjTcWork gw;                             // Gauss-Jordan panel and its operand terms
     } u;
     union {
         struct {
@@ -249,8 +248,11 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                                            : make_float2(i == j ? 1.f : 0.f, 0.f);
             }
             __syncthreads();
-            st = gj_lookahead<MPT, NTT, TYT, TXT, GJ_NB>(sm.X, M, sm.u.pv.U, sm.u.pv.V, sm.gj);
-            if (st != ST_OK) break;
+            st = gj_tc<NTT>(sm.X, M, sm.u.gw, sm.gj, tmem, &sm.mbar, phase);
+            if (st != ST_OK) {
+                timed_out = st == ST_TIMEOUT;
+                break;
+            }
             {
                 float2 x[RA][RB];
 #pragma unroll
