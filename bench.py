@@ -36,7 +36,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu pass) of one
 # launch of the sweep kernel on exactly this workload, for the kernel as it
 # stands; set to None whenever the kernel changes until it is measured again
-SWEEP_TRAFFIC_BYTES = 69.4e6
+SWEEP_TRAFFIC_BYTES = 70.05e6
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS_NOMINAL = 1.25
@@ -236,7 +236,10 @@ def run_knit(args):
     sweep_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     alg_flop = 16.0 * M ** 3 * L * n          # 16 M^3 real flop per slice-update
     achieved_tflops = alg_flop / (sweep_ms / 1e3) / 1e12
-    tc_flop = 18 * 8 * 2.0 * 128 * 64 * 16 * L * n
+    # executed tensor-core work per slice, in 128 x 64 x 16 MMA units: the
+    # residual's 18 digit products x 8 K-chunks and the Gauss-Jordan's 9 term
+    # products x 8 panels (M / 8 panels of 8 columns)
+    tc_flop = (18 * 8 + 9 * (M // 8)) * 2.0 * 128 * 64 * 16 * L * n
     tc_tflops = tc_flop / (sweep_ms / 1e3) / 1e12
 
     # ---- plain FP64 GPU sweep on a one-wave subset (same energies/seeds grid)
@@ -311,8 +314,10 @@ def run_knit(args):
                                      "peak": peaks.get("bf16_tflops"),
                                      "frac": (tc_tflops / peaks["bf16_tflops"])
                                      if peaks.get("bf16_tflops") else None,
-                                     "note": "bf16 digit products of the residual: 18 products "
-                                             "x 8 K-chunks x (128 x 64 x 16) MMA per slice"}},
+                                     "note": "bf16 products per slice: the residual's 18 digit "
+                                             "products x 8 K-chunks and the Gauss-Jordan panel "
+                                             "updates' 9 term products x 8 panels, each a "
+                                             "128 x 64 x 16 MMA"}},
         "e2e": {"value": e2e_val, "unit": "T(E) points/s", "h2d_bytes_per_step": 8 * NE + 8 * NS,
                 "d2h_bytes_per_step": 12 * n, "ms": statistics.mean(e2e_ms)},
         "gpu_launches": launches_per_step * args.steps,
