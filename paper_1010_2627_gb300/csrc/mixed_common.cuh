@@ -82,13 +82,50 @@ __device__ void slice_diag(double *eps, const SysDev &s, uint64_t ms, double W, 
     }
 }
 
+// A diagonal V with one value v on every orbital multiplies g by the real
+// number |v|^2 in V g V^dagger.  vuni (per parity): 0 general, 1 |v|^2 = 1
+// (V g V^dagger = g), 2 the factor (vch + vcl) as double-float.  Called by
+// thread 0 on the double diagonal of V (M values, stride `stride`).
+KNIT_DEV void classify_vdiag(const double2 *Vd, int stride, int M, int &vuni, float &vch, float &vcl)
+{
+    const double2 v0 = Vd[0];
+    bool same = true;
+    for (int i = 1; i < M; ++i) {
+        const double2 v = Vd[(size_t)i * stride];
+        same = same && v.x == v0.x && v.y == v0.y;
+    }
+    const double c = v0.x * v0.x + v0.y * v0.y;
+    vuni = !same || c == 0.0 ? 0 : (c == 1.0 ? 1 : 2);
+    to_df(c, vch, vcl);
+}
+
 // Gv = V_n g V_n^dagger (+ Sigma_L at n = 0, + Sigma_R at n = L - 1) in
-// double-float, in place over (Gh, Gl); vh/vl: diagonal of V per parity.
+// double-float, in place over (Gh, Gl); vh/vl: diagonal of V per parity;
+// vuni/vch/vcl (per parity, classify_vdiag) select the scalar form on the
+// slices without a lead term.
 template <int MP, int NTH = NT>
 __device__ void form_gv(float2 *Gh, float2 *Gl, const float2 (*vh)[MP], const float2 (*vl)[MP],
-                        int M, int n, int L, const double2 *SL, const double2 *SR)
+                        int M, int n, int L, const double2 *SL, const double2 *SR,
+                        const int *vuni, const float *vch, const float *vcl)
 {
     const int q = n & 1;
+    if (n > 0 && n < L - 1 && vuni[q]) {
+        const bool unit = vuni[q] == 1;
+        const float ch = vch[q], cl = vcl[q];
+        for (int e = threadIdx.x; e < MP * MP; e += NTH) {
+            const int i = e / MP, j = e - i * MP;
+            if (i >= M || j >= M) {
+                Gh[e] = make_float2(0.f, 0.f);
+                Gl[e] = make_float2(0.f, 0.f);
+            } else if (!unit) {
+                float2 gh = Gh[e], gl = Gl[e];
+                cdf_mul(gh, gl, make_float2(ch, 0.f), make_float2(cl, 0.f), gh, gl);
+                Gh[e] = gh;
+                Gl[e] = gl;
+            }
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < MP * MP; e += NTH) {
         const int i = e / MP, j = e - i * MP;
         float2 gh = make_float2(0.f, 0.f), gl = make_float2(0.f, 0.f);

@@ -46,6 +46,8 @@ struct MixedSmem {
     float2 S[MP * MP];     // further Neumann terms of the refinement
     GJShared<MP> gj;
     double eps[MP];        // E - onsite for the current slice
+    int vuni[2];           // V's diagonal uniform (classify_vdiag), per parity
+    float vch[2], vcl[2];
     float2 vh[2][MP];      // diagonal of V (per parity), hi
     float2 vl[2][MP];      // lo
     double red[NT / 32];
@@ -79,6 +81,9 @@ __device__ __forceinline__ void mixed_load_system(MixedSmem<MP> &sm, const SysDe
             sm.vh[q][i] = make_float2(hx, hy);
             sm.vl[q][i] = make_float2(lx, ly);
         }
+    if (tid < 2)
+        classify_vdiag(s.V + (size_t)(tid % s.Vperiod) * MM, M + 1, M, sm.vuni[tid], sm.vch[tid],
+                       sm.vcl[tid]);
     __syncthreads();
 }
 
@@ -97,7 +102,7 @@ __device__ __forceinline__ int mixed_step(MixedSmem<MP> &sm, const SysDev &s, co
     const double2 *SR = ip.SR;
     int st = ST_OK;
         slice_diag<MP>(sm.eps, s, ms, W, E, n);
-        form_gv<MP>(sm.Gh, sm.Gl, sm.vh, sm.vl, M, n, L, SL, SR);
+        form_gv<MP>(sm.Gh, sm.Gl, sm.vh, sm.vl, M, n, L, SL, SR, sm.vuni, sm.vch, sm.vcl);
         __syncthreads();
 
         // ---- X = fl32(D - Gv_hi), Gauss-Jordan in registers

@@ -83,6 +83,8 @@ struct TcSmem {
     double eps[MPT];
     float2 vh[2][MPT];
     float2 vl[2][MPT];
+    int vuni[2];
+    float vch[2], vcl[2];
     int rexp[MPT];
     int cexp[MPT];
     float cmax[NTT / MPT][MPT];
@@ -174,6 +176,9 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                     sm.vh[q][i] = make_float2(hx, hy);
                     sm.vl[q][i] = make_float2(lx, ly);
                 }
+            if (tid < 2)
+                classify_vdiag(s.V + (size_t)(tid % s.Vperiod) * MM, M + 1, M, sm.vuni[tid],
+                               sm.vch[tid], sm.vcl[tid]);
             const int nnz = s.h0_rowptr[M];
             for (int i = tid; i <= MPT; i += NTT) sm.h0rp[i] = s.h0_rowptr[min(i, M)];
             if (nnz <= MAX_NNZ)
@@ -203,7 +208,7 @@ knit_sweep_mixed_tc_kernel(InstDev in)
 
         for (int n = 0; n < L && st == ST_OK; ++n) {
             slice_diag<MPT, NTT>(sm.eps, s, ms, W, E, n);
-            form_gv<MPT, NTT>(Gh, Gl, sm.vh, sm.vl, M, n, L, SL, SR);
+            form_gv<MPT, NTT>(Gh, Gl, sm.vh, sm.vl, M, n, L, SL, SR, sm.vuni, sm.vch, sm.vcl);
             __syncthreads();
             // Gv' = Gv + H0 - D in double-float, one row per thread, so that
             // A_n = -Gv' and the residual is R = I + Gv' X'
