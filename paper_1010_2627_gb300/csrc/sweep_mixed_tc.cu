@@ -235,22 +235,35 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             }
             __syncthreads();
 
-            // row scales of Gv: warp w takes rows 4w..4w+3, lanes run along the row
-            for (int r = 0; r < MPT / (NTT / 32); ++r) {
-                const int i = (MPT / (NTT / 32)) * warp + r;
-                const float2 g0 = Gh[i * MPT + lane], g1 = Gh[i * MPT + lane + 32];
-                float mx = fmaxf(fmaxf(fabsf(g0.x), fabsf(g0.y)), fmaxf(fabsf(g1.x), fabsf(g1.y)));
+            // row scales of Gv and X = fl32(A_n) = -Gv'_hi (identity in the
+            // padding) in one pass: warp w takes rows 4w..4w+3, lanes run
+            // along the row, the four maxima reduce side by side
+            {
+                constexpr int RPW = MPT / (NTT / 32);
+                float mx[RPW];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-                if (lane == 0) sm.rexp[i] = scale_exp(mx);
-            }
-
-            // X = fl32(A_n) = -Gv'_hi (identity in the padding)
-            for (int e = tid; e < MPT * MPT; e += NTT) {
-                const int i = e >> 6, j = e & 63;
-                const float2 g = Gh[e];
-                sm.X[e] = (i < M && j < M) ? make_float2(-g.x, -g.y)
-                                           : make_float2(i == j ? 1.f : 0.f, 0.f);
+                for (int r = 0; r < RPW; ++r) {
+                    const int i = RPW * warp + r;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = lane + 32 * h;
+                        const float2 g = Gh[i * MPT + j];
+                        const float m = fmaxf(fabsf(g.x), fabsf(g.y));
+                        mx[r] = h ? fmaxf(mx[r], m) : m;
+                        sm.X[i * MPT + j] = (i < M && j < M) ? make_float2(-g.x, -g.y)
+                                                             : make_float2(i == j ? 1.f : 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int r = 0; r < RPW; ++r) mx[r] = fmaxf(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], o));
+                if (lane < RPW) {
+                    float m = mx[0];
+#pragma unroll
+                    for (int r = 1; r < RPW; ++r) m = lane == r ? mx[r] : m;
+                    sm.rexp[RPW * warp + lane] = scale_exp(m);
+                }
             }
             __syncthreads();
             st = gj_tc<NTT>(sm.X, M, sm.u.gw, sm.gj, tmem, &sm.mbar, phase);
