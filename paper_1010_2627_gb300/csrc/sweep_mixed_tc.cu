@@ -27,7 +27,8 @@
 //    Digits are stored pre-scaled by 2^-8p / 2^-8q, so every product of one
 //    anti-diagonal d = p + q is an integer multiple of 2^-8d below 2^24 in
 //    magnitude: each of the seven accumulators d = 0 .. 6 sums exactly;
-//  * the seven accumulators are summed in double-float, scaled by
+//  * the seven accumulators are summed -- 3 .. 6 (below 2^-24 of the
+//    leading one) in fp32, then with 0 .. 2 in double-float -- scaled by
 //    sigma_i tau_n 2^-16, the identity added, and R rounded once to fp32;
 //  * g = X' (I + R + R^2 + ...) with as many terms as max|R_ij| asks for,
 //    the product X' S accumulated error-free where max|R_ij| is large
@@ -428,8 +429,9 @@ knit_sweep_mixed_tc_kernel(InstDev in)
 
             // R = I + Gv' X' = I + sigma_i tau_n 2^-16 (D0 + ... + D6):
             // lane m of warp w holds row 32 (w % 4) + lane of [Re; Im],
-            // columns 16 (w / 4) ..; the seven accumulators are summed as
-            // double-float before the single rounding to the stored R
+            // columns 16 (w / 4) ..; the seven accumulators are summed (the
+            // leading three as double-float) before the single rounding to
+            // the stored R
             float rloc = 0.f;
             {
                 const int m = 32 * (warp & 3) + lane, c0 = 16 * (warp >> 2);
@@ -439,36 +441,32 @@ knit_sweep_mixed_tc_kernel(InstDev in)
                 const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0;
                 for (int j8 = 0; j8 < 16; j8 += 8) {
                     uint32_t v0[8], v1[8], v2[8], v3[8];
-                    float hsum[8], lsum[8];
+                    float small[8];
+                    // accumulators 3 .. 6 are below 2^-24 of the leading one:
+                    // their fp32 sum is as accurate as the double-float result
+                    tmem_ld8(tb + 192 + j8, v0);
+                    tmem_ld8(tb + 256 + j8, v1);
+                    tmem_ld8(tb + 320 + j8, v2);
+                    tmem_ld8(tb + 384 + j8, v3);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int jx = 0; jx < 8; ++jx)
+                        small[jx] = ((__uint_as_float(v3[jx]) + __uint_as_float(v2[jx])) +
+                                     __uint_as_float(v1[jx])) + __uint_as_float(v0[jx]);
                     tmem_ld8(tb + j8, v0);
                     tmem_ld8(tb + 64 + j8, v1);
                     tmem_ld8(tb + 128 + j8, v2);
-                    tmem_ld8(tb + 192 + j8, v3);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int jx = 0; jx < 8; ++jx) {
-                        float hs, ls, t, te;
-                        two_sum(__uint_as_float(v0[jx]), __uint_as_float(v1[jx]), hs, ls);
-                        two_sum(hs, __uint_as_float(v2[jx]), t, te);
-                        ls += te;
-                        two_sum(t, __uint_as_float(v3[jx]), hs, te);
-                        hsum[jx] = hs;
-                        lsum[jx] = ls + te;
-                    }
-                    tmem_ld8(tb + 256 + j8, v0);
-                    tmem_ld8(tb + 320 + j8, v1);
-                    tmem_ld8(tb + 384 + j8, v2);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int jx = 0; jx < 8; ++jx) {
                         const int nn = c0 + j8 + jx;
-                        float hs = hsum[jx], ls = lsum[jx], t, te;
-                        two_sum(hs, __uint_as_float(v0[jx]), t, te);
-                        ls += te;
-                        two_sum(t, __uint_as_float(v1[jx]), hs, te);
-                        ls += te;
+                        float hs, ls, t, te;
+                        two_sum(__uint_as_float(v0[jx]), __uint_as_float(v1[jx]), hs, ls);
                         two_sum(hs, __uint_as_float(v2[jx]), t, te);
                         ls += te;
+                        two_sum(t, small[jx], hs, te);
+                        ls += te;
+                        t = hs;
                         const float sc = pow2f(re + sm.cexp[nn] - 16);
                         hs = t * sc;
                         ls *= sc;
