@@ -255,6 +255,13 @@ knit_status knit_graph_create(const knit_graph_desc *desc, knit_graph *out);
 knit_status knit_graph_create_multi(const knit_graph_multi_desc *desc, knit_graph *out);
 knit_status knit_graph_destroy(knit_graph g);
 
+/* The slicing of a description without creating a graph (host work only, no
+ * device memory): number of slices and the slice of every site (N values,
+ * -1 for a site not connected to lead 0; optional).  Same checks and error
+ * codes as knit_graph_create_multi. */
+knit_status knit_graph_plan(const knit_graph_multi_desc *desc, int32_t *nslices,
+                            int32_t *slice_of);
+
 /* The slicing: number of slices, their widths (nslices values, optional) and
  * the slice of every site (N values, -1 for a site not connected to lead 0;
  * optional). */

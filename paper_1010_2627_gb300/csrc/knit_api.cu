@@ -236,7 +236,10 @@ knit_status to_host(std::vector<T> &dst, const void *src, size_t count, const ch
     dst.resize(count);
     if (count == 0) return KNIT_OK;
     if (!src) return fail(KNIT_ERR_INVALID, "%s is NULL", what);
-    CK(cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDefault), what);
+    if (is_device_ptr(src))
+        CK(cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost), what);
+    else
+        std::memcpy(dst.data(), src, sizeof(T) * count);   // host input: no driver needed
     return KNIT_OK;
 }
 
@@ -1037,10 +1040,17 @@ knit_status knit_graph_destroy(knit_graph g)
 
 namespace {
 
-knit_status graph_build(int N, const knit_c128 *Hin, int P, const int32_t *nsites,
-                        const int32_t *const *sites, knit_graph *out)
+// the slicing of a geometry (host only): slices sl (site lists), every
+// site's slice (-1: not connected to lead 0) and position within it
+struct GraphPlan {
+    std::vector<std::vector<int>> sl, ls;
+    std::vector<int> slice_of, pos;
+    std::vector<double2> H;
+};
+
+knit_status graph_plan(int N, const knit_c128 *Hin, int P, const int32_t *nsites,
+                       const int32_t *const *sites, GraphPlan &gp)
 {
-    *out = nullptr;
     if (N <= 0 || N > 8192) return fail(KNIT_ERR_INVALID, "N = %d out of range (1 .. 8192)", N);
     if (P < 2 || P > 64) return fail(KNIT_ERR_INVALID, "%d leads: 2 .. 64 supported", P);
     if (!Hin || !nsites || !sites) return fail(KNIT_ERR_INVALID, "H and the lead site lists are required");
@@ -1092,19 +1102,38 @@ knit_status graph_build(int N, const knit_c128 *Hin, int P, const int32_t *nsite
     sl[0] = ls[0];
     for (int v = 0; v < N; ++v)
         if (depth[v] > 0) sl[std::min(depth[v], d1)].push_back(v);
+    gp.slice_of.assign(N, -1);
+    gp.pos.assign(N, -1);
+    for (int k = 0; k < K; ++k)
+        for (size_t a = 0; a < sl[k].size(); ++a) {
+            gp.slice_of[sl[k][a]] = k;
+            gp.pos[sl[k][a]] = (int)a;
+        }
+    gp.sl = std::move(sl);
+    gp.ls = std::move(ls);
+    gp.H = std::move(H);
+    return KNIT_OK;
+}
+
+knit_status graph_build(int N, const knit_c128 *Hin, int P, const int32_t *nsites,
+                        const int32_t *const *sites, knit_graph *out)
+{
+    *out = nullptr;
+    GraphPlan gp;
+    knit_status r = graph_plan(N, Hin, P, nsites, sites, gp);
+    if (r != KNIT_OK) return r;
+    const std::vector<std::vector<int>> &sl = gp.sl, &ls = gp.ls;
+    const std::vector<double2> &H = gp.H;
+    const int K = (int)sl.size();
     auto g = new knit_graph_s;
     g->N = N;
     g->K = K;
     g->P = P;
-    g->hslice_of.assign(N, -1);
-    std::vector<int> pos(N, -1);
+    g->hslice_of = gp.slice_of;
+    const std::vector<int> &pos = gp.pos;
     for (int k = 0; k < K; ++k) {
         g->hwidth.push_back((int)sl[k].size());
         g->Mmax = std::max(g->Mmax, (int)sl[k].size());
-        for (size_t a = 0; a < sl[k].size(); ++a) {
-            g->hslice_of[sl[k][a]] = k;
-            pos[sl[k][a]] = (int)a;
-        }
     }
     std::vector<int> lpos, loff;
     for (int p = 0; p < P; ++p) {
@@ -1183,6 +1212,17 @@ knit_status graph_run(knit_graph g, const double *E, int nE, const knit_c128 *co
 }
 
 }  // namespace
+
+knit_status knit_graph_plan(const knit_graph_multi_desc *d, int32_t *nslices, int32_t *slice_of)
+{
+    if (!d || !nslices) return fail(KNIT_ERR_INVALID, "knit_graph_plan: NULL argument");
+    GraphPlan gp;
+    knit_status r = graph_plan(d->N, d->H, d->n_leads, d->n_lead_sites, d->lead_sites, gp);
+    if (r != KNIT_OK) return r;
+    *nslices = (int32_t)gp.sl.size();
+    if (slice_of) std::copy(gp.slice_of.begin(), gp.slice_of.end(), slice_of);
+    return KNIT_OK;
+}
 
 knit_status knit_graph_create(const knit_graph_desc *d, knit_graph *out)
 {

@@ -70,6 +70,7 @@ _SIGS = {
     "knit_graph_slices": (i32, [P, P, P, P]),
     "knit_graph_transmission": (i32, [P, P, i32, P, P, P, P, P]),
     "knit_graph_create_multi": (i32, [P, P]),
+    "knit_graph_plan": (i32, [P, P, P]),
     "knit_graph_conductance": (i32, [P, P, i32, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
@@ -259,8 +260,7 @@ def knit_graph_create(H, lead0, lead1):
     return out.value
 
 
-def knit_graph_create_multi(H, leads):
-    """Handle of an arbitrary geometry with several leads (site lists)."""
+def _multi_desc(H, leads):
     H = np.ascontiguousarray(H, dtype=np.complex128)
     ls = [np.ascontiguousarray(l, dtype=np.int32) for l in leads]
     n = np.array([len(l) for l in ls], np.int32)
@@ -271,6 +271,21 @@ def knit_graph_create_multi(H, leads):
     d.n_leads = len(ls)
     d.n_lead_sites = _ptr(n)
     d.lead_sites = ctypes.cast(ptrs, P)
+    return d, (H, ls, n, ptrs)   # keep the arrays alive with the descriptor
+
+
+def knit_graph_plan(H, leads):
+    """(nslices, slice_of) of the slicing, computed on the host."""
+    d, keep = _multi_desc(H, leads)
+    k = ctypes.c_int32(0)
+    so = np.empty(d.N, np.int32)
+    _check(load().knit_graph_plan(ctypes.byref(d), ctypes.byref(k), _ptr(so)))
+    return int(k.value), so
+
+
+def knit_graph_create_multi(H, leads):
+    """Handle of an arbitrary geometry with several leads (site lists)."""
+    d, keep = _multi_desc(H, leads)
     out = P()
     _check(load().knit_graph_create_multi(ctypes.byref(d), ctypes.byref(out)))
     return out.value
