@@ -456,7 +456,8 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
                                    md->act.as<float>() + md->act_off(knit_lead_model_s::NL), 1e-12,
                                    8, sig, gout, lit, lst, grid, st),
            "lead newton");
-        // decimation for the energies Newton did not settle (fallback and judge)
+        // decimation for the energies Newton did not settle (the fallback, and the
+        // arbiter of the warm start's error)
         CK(s->decw.ensure(sizeof(double2) * 8 * MM * grid), "decimation workspace");
         CK(knit_launch_decimation_failed(s->lead[p].H0, s->lead[p].V, M, s->lead[p].vb, p, dE, nE,
                                          eta, tol, maxit, s->decw.as<double2>(), sig, gout, lit,

@@ -20,7 +20,7 @@ def knit():
 
 @pytest.fixture(scope="module")
 def square_lead_model(knit):
-    """A square lead of width 4 (so the closed form is available as judge)."""
+    """A square lead of width 4 (so the closed form is available as the arbiter)."""
     ss = inputs.square(4, 3)
     sysk = knit.System(ss)
     E_train = np.random.default_rng(0).uniform(-3.6, 3.6, 3000)
