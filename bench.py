@@ -105,8 +105,8 @@ def cpu_baseline(E, seeds, budget_s=15.0):
     from paper_1010_2627_gb300 import inputs
     ss = inputs.square(M, L)
     nthr = oracle.max_threads()
-    # calibrate with one instance per core, then extend to ~budget
-    idx = np.linspace(0, len(E) - 1, 4 * nthr).astype(int)
+    # one instance per core at a time, up to 16 per core or ~budget seconds
+    idx = np.linspace(0, len(E) - 1, 16 * nthr).astype(int)
     Es = E[idx]
     sd = np.asarray([seeds[i % len(seeds)] for i in range(len(idx))], np.uint64)
     Sig = np.stack([oracle.sigma_square(M, 1.0, e) for e in Es])
