@@ -387,6 +387,13 @@ knit_status knit_lead_decimation_noalloc(const knit_c128 *H0, const knit_c128 *V
 /* Thread-local description of the last error (never NULL). */
 const char *knit_last_error(void);
 
+/* Host-side fault injection for tests: the n-th device allocation the
+ * library makes from now on (n = 0: the next one) fails as if the device were
+ * out of memory, so the call that makes it returns KNIT_ERR_OOM and releases
+ * what it had allocated; the injection then switches itself off.  n < 0
+ * switches it off.  Process-wide; no device work. */
+knit_status knit_debug_fail_alloc_after(int64_t n);
+
 /* Library version string. */
 const char *knit_version(void);
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -113,6 +114,26 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Every device allocation of the library goes through dev_alloc, so that a
+// test can make the n-th one from now on fail as if the device were out of
+// memory (host-side fault injection, armed by knit_debug_fail_alloc_after;
+// one-shot; off by default).
+std::atomic<long long> g_fail_alloc_after{-1};
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    long long k = g_fail_alloc_after.load();
+    while (k > 0 && !g_fail_alloc_after.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0 && g_fail_alloc_after.compare_exchange_strong(k, -1)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+
 struct DevBuf {
     void *p = nullptr;
     size_t n = 0;
@@ -126,9 +147,8 @@ struct DevBuf {
     {
         if (bytes <= n) return cudaSuccess;
         release();
-        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 256));
+        cudaError_t e = dev_alloc(&p, std::max<size_t>(bytes, 256));
         if (e == cudaSuccess) n = std::max<size_t>(bytes, 256);
-        else p = nullptr;
         return e;
     }
     template <typename T>
@@ -246,7 +266,7 @@ knit_status to_host(std::vector<T> &dst, const void *src, size_t count, const ch
 template <typename T>
 knit_status to_device(T **dst, const T *src, size_t count, const char *what)
 {
-    CK(cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(count, 1)), what);
+    CK(dev_alloc((void **)dst, sizeof(T) * std::max<size_t>(count, 1)), what);
     if (count) CK(cudaMemcpy(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice), what);
     return KNIT_OK;
 }
@@ -336,8 +356,8 @@ knit_status ensure_modes(knit_system s, int p)
     Lead &ld = s->lead[p];
     if (ld.modes_ready) return KNIT_OK;
     const size_t MM = (size_t)s->M * s->M;
-    CK(cudaMalloc((void **)&ld.U, sizeof(double2) * MM), "modes U");
-    CK(cudaMalloc((void **)&ld.A, sizeof(double2) * MM), "modes A");
+    if (!ld.U) CK(dev_alloc((void **)&ld.U, sizeof(double2) * MM), "modes U");
+    if (!ld.A) CK(dev_alloc((void **)&ld.A, sizeof(double2) * MM), "modes A");
     CK(cudaMemcpy(ld.A, ld.H0, sizeof(double2) * MM, cudaMemcpyDeviceToDevice), "modes copy");
     CK(knit_launch_jacobi(ld.A, ld.U, s->M, nullptr, 0), "jacobi launch");
     CK(cudaStreamSynchronize(0), "jacobi");
@@ -638,6 +658,12 @@ const char *knit_last_error(void) { return g_err.c_str(); }
 void knit_set_last_error(const char *msg) { g_err = msg ? msg : "unknown error"; }
 
 const char *knit_version(void) { return "knit-gb300 0.1 (sm_103a)"; }
+
+knit_status knit_debug_fail_alloc_after(int64_t n)
+{
+    g_fail_alloc_after.store(n < 0 ? -1 : (long long)n);
+    return KNIT_OK;
+}
 
 knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
 {

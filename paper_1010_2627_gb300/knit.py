@@ -71,6 +71,7 @@ _SIGS = {
     "knit_graph_transmission": (i32, [P, P, i32, P, P, P, P, P]),
     "knit_graph_create_multi": (i32, [P, P]),
     "knit_graph_plan": (i32, [P, P, P]),
+    "knit_debug_fail_alloc_after": (i32, [ctypes.c_int64]),
     "knit_graph_conductance": (i32, [P, P, i32, P, P, P, P]),
     "knit_lead_decimation_noalloc": (i32, [P, P, i32, i32, P, i32, f64, f64, i32, P, P, P, P]),
     "knit_batch_create": (i32, [P, i32, P, i32, i32, P]),
@@ -281,6 +282,11 @@ def knit_graph_plan(H, leads):
     so = np.empty(d.N, np.int32)
     _check(load().knit_graph_plan(ctypes.byref(d), ctypes.byref(k), _ptr(so)))
     return int(k.value), so
+
+
+def knit_debug_fail_alloc_after(n):
+    """Make the n-th device allocation from now on fail (n < 0: off)."""
+    _check(load().knit_debug_fail_alloc_after(int(n)))
 
 
 def knit_graph_create_multi(H, leads):

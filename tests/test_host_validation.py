@@ -133,3 +133,17 @@ def test_error_message_is_per_thread():
     t.start()
     t.join()
     assert knit.knit_last_error() == mine and "L = 0" in mine
+
+
+def test_injected_allocation_failure_is_reported_as_oom():
+    """Host-side fault injection: the armed allocation fails as out of
+    memory, the call reports KNIT_ERR_OOM, and the injection is one-shot."""
+    knit.knit_debug_fail_alloc_after(0)
+    code, msg = create_code(**base())
+    assert code == 2 and "out of memory" in msg, (code, msg)
+    code, _ = create_code(**base())
+    assert code == (CUDA if _no_gpu() else 0)
+    knit.knit_debug_fail_alloc_after(3)
+    knit.knit_debug_fail_alloc_after(-1)          # disarmed before it fired
+    code, _ = create_code(**base())
+    assert code == (CUDA if _no_gpu() else 0)
