@@ -520,6 +520,13 @@ knit_sweep_mixed_tc_kernel(InstDev in)
         __syncthreads();
         if (timed_out) break;
     }
+    if (timed_out) {
+        // the wait that ran out flipped the phase; the tensor cores may still
+        // write the accumulators of that commit: give it a second bounded wait
+        // before the tensor memory is released
+        if (tid == 0) mbar_wait(&sm.mbar, phase ^ 1u);
+        __syncthreads();
+    }
     fence_before();
     __syncthreads();
     if (warp == 0)
