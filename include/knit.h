@@ -234,8 +234,10 @@ knit_status knit_system_num_edges(knit_system sys, int32_t *count);
  * rectangular couplings and every lead but lead 0 sits in the last slice.
  * KNIT_ERR_INVALID for N outside 1 .. 8192, fewer than 2 or more than 64
  * leads, a non-Hermitian H (relative 1e-12), overlapping or out-of-range lead
- * sites, or a lead not connected to lead 0.  The graph calls return after
- * the sweep has finished. */
+ * sites, a lead not connected to lead 0, or a slice wider than 6144 sites.
+ * The sweep runs one energy per CTA (at most one CTA per SM, fewer when six
+ * widest-slice matrices per CTA would pass 8 GiB).  The graph calls return
+ * after the sweep has finished. */
 typedef struct knit_graph_s *knit_graph;
 typedef struct {
     int32_t N;

@@ -1067,6 +1067,10 @@ knit_status knit_graph_destroy(knit_graph g)
 
 namespace {
 
+// widest slice the graph sweep takes: its Gauss-Jordan scratch (two rows of
+// complex128 plus indices) must fit in one CTA's shared memory
+constexpr int KNIT_GRAPH_MAX_WIDTH = 6144;
+
 // the slicing of a geometry (host only): slices sl (site lists), every
 // site's slice (-1: not connected to lead 0) and position within it
 struct GraphPlan {
@@ -1129,6 +1133,10 @@ knit_status graph_plan(int N, const knit_c128 *Hin, int P, const int32_t *nsites
     sl[0] = ls[0];
     for (int v = 0; v < N; ++v)
         if (depth[v] > 0) sl[std::min(depth[v], d1)].push_back(v);
+    for (const auto &v : sl)
+        if ((int)v.size() > KNIT_GRAPH_MAX_WIDTH)
+            return fail(KNIT_ERR_INVALID, "a slice of %d sites: at most %d supported", (int)v.size(),
+                        KNIT_GRAPH_MAX_WIDTH);
     gp.slice_of.assign(N, -1);
     gp.pos.assign(N, -1);
     for (int k = 0; k < K; ++k)
@@ -1227,8 +1235,12 @@ knit_status graph_run(knit_graph g, const double *E, int nE, const knit_c128 *co
     CK(g->sigp.ensure(sizeof(double2 *) * g->P), "self-energy table");
     CK(cudaMemcpyAsync(g->sigp.p, ptr.data(), sizeof(double2 *) * g->P, cudaMemcpyHostToDevice, st),
        "self-energy table");
-    const int grid = std::max(1, std::min(nE, g->nsm));
-    CK(g->work.ensure(sizeof(double2) * 6 * (size_t)g->Mmax * g->Mmax * grid), "graph workspace");
+    // one CTA per energy up to one per SM, fewer when the per-CTA workspace
+    // (six Mmax x Mmax complex matrices) would pass 8 GiB in total
+    const size_t per_cta = sizeof(double2) * 6 * (size_t)g->Mmax * g->Mmax;
+    const int fit = (int)std::max<size_t>(1, (size_t(8) << 30) / per_cta);
+    const int grid = std::max(1, std::min(std::min(nE, g->nsm), fit));
+    CK(g->work.ensure(per_cta * grid), "graph workspace");
     GraphDev gd{g->K, g->Mmax, g->P, g->width, g->hoff, g->voff, g->blocks, g->lw, g->lpos, g->loff,
                 g->sigp.as<const double2 *>()};
     CK(knit_launch_graph_fp64(&gd, dE, nE, g->work.as<double2>(), grid, Tm, status, st),

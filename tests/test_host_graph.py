@@ -166,3 +166,15 @@ def test_plan_invalid():
     H2[2, 3] = H2[3, 2] = 0.0
     with pytest.raises(knit.KnitError):   # lead 1 not connected to lead 0
         knit.knit_graph_plan(H2, [[0], [3]])
+
+
+def test_plan_rejects_a_slice_wider_than_the_sweep_takes():
+    """A star: lead 0 at the centre, 6200 leaves in one layer, lead 1 one
+    step further out -- the layer of leaves is one slice of 6200 sites."""
+    n = 6200
+    N = n + 2
+    H = np.zeros((N, N), complex)      # 615 MB, passed without a copy
+    H[0, 1:n + 1] = H[1:n + 1, 0] = 1.0
+    H[1, N - 1] = H[N - 1, 1] = 1.0
+    with pytest.raises(knit.KnitError, match="at most 6144"):
+        knit.knit_graph_plan(H, [[0], [N - 1]])
