@@ -28,13 +28,16 @@ ctypes:
                      graph (Sec. 2.3), dense numpy inverse
 * ``lesser_parts``   lead-resolved densities and bond currents from
                      G^<_l = i G Gamma_l G^+ (Sec. 2.3), dense numpy inverse
+* ``graph_lesser``   the same lead-resolved densities, LDOS and bond currents
+                     for an arbitrary site graph with several leads
 * ``transmission_eigenvalues``, ``shot_noise``
                      the eigenvalues of the matrix inside Sec. 2.3's
                      transmission trace, and sum tau (1 - tau)
 * ``onsite``         counter-based Anderson disorder (Sec. 6.1)
 
-Parity status: every function here is pinned by ``tests/test_oracle.py``
-(closed forms, the paper's printed Fig. 3 values, brute force, identities).
+Parity status: every function here is pinned by ``tests/test_oracle.py`` and
+``tests/test_oracle_scattering.py`` (closed forms, the paper's printed Fig. 3
+values, brute force, identities, scattering states by mode matching).
 """
 from __future__ import annotations
 
@@ -357,6 +360,47 @@ def lesser_parts(H0, V, eps, L: int, E: float, SigL, SigR):
     ldos = (-np.imag(np.diag(G)) / np.pi).reshape(L, M)
     T = float(np.real(np.trace(GL @ G[:M, N - M:] @ GR @ G[:M, N - M:].conj().T)))
     return dict(rhoL=rhoL, rhoR=rhoR, jx=jx, jt=jt, edges=edges, ldos=ldos, T=T)
+
+
+def graph_lesser(H, E: float, lead_sites, sigmas):
+    """Lead-resolved local quantities of an arbitrary site graph with P leads
+    (Sec. 2.3: G^<_l = i G Gamma_l G^+ is the part of the lesser function fed
+    by lead l, Gamma_l = i (Sigma_l - Sigma_l^+); local currents between
+    neighbouring sites), from the plain dense inverse of E - H - sum Sigma
+    (numpy).  Returns a dict of
+
+    rho (P, N): A^l_ii / (2 pi) with A^l = G Gamma_l G^+, the density of
+        states injected by lead l;
+    ldos (N): -Im G_ii / pi;
+    edges (n_edge, 2): the pairs i < j with H_ij != 0, row-major;
+    J (P, n_edge): current carried by lead-l-injected states from i to j
+        along each edge, -2 Im[H_ij A^l_ji];
+    T (P, P): T_kl = Re Tr[Gamma_k G_kl Gamma_l G_kl^+] (zero diagonal)."""
+    H = np.asarray(H, dtype=np.complex128)
+    N = H.shape[0]
+    A = E * np.eye(N) - H
+    idx = [np.asarray(s, dtype=int) for s in lead_sites]
+    for s, S in zip(idx, sigmas):
+        A[np.ix_(s, s)] -= np.asarray(S, dtype=np.complex128)
+    G = np.linalg.inv(A)
+    P = len(idx)
+    edges = np.array([(i, j) for i in range(N) for j in range(i + 1, N) if H[i, j] != 0],
+                     dtype=int).reshape(-1, 2)
+    rho = np.zeros((P, N))
+    J = np.zeros((P, len(edges)))
+    T = np.zeros((P, P))
+    for l in range(P):
+        Gl = G[:, idx[l]]
+        Al = Gl @ _gamma(sigmas[l]) @ Gl.conj().T
+        rho[l] = np.real(np.diag(Al)) / (2 * np.pi)
+        for e, (i, j) in enumerate(edges):
+            J[l, e] = -2 * np.imag(H[i, j] * Al[j, i])
+        for k in range(P):
+            if k != l:
+                B = G[np.ix_(idx[k], idx[l])]
+                T[k, l] = np.real(np.trace(_gamma(sigmas[k]) @ B @ _gamma(sigmas[l]) @ B.conj().T))
+    ldos = -np.imag(np.diag(G)) / np.pi
+    return dict(rho=rho, ldos=ldos, edges=edges, J=J, T=T)
 
 
 def shot_noise(tau):

@@ -114,10 +114,12 @@ def slice_system_scattering(H0, V, eps, L, E, t):
                 psiR=np.array(psiR).reshape(len(openm), L, M), vR=v[openm])
 
 
-def graph_scattering(H, E, lead_site, t):
+def graph_scattering(H, E, lead_site, t, want_states=False):
     """Scattering matrix S[k, l] (flux-normalised; all leads alike) of a site
     graph with one-dimensional chain leads of hopping t, lead p attached by
-    hopping t to site lead_site[p].  Requires |E| < 2|t| (one open mode)."""
+    hopping t to site lead_site[p].  Requires |E| < 2|t| (one open mode).
+    With want_states also the scattering states psi[l] (unit incoming
+    amplitude in lead l) on the graph's sites and the lead velocity."""
     H = np.asarray(H, complex)
     N = H.shape[0]
     P = len(lead_site)
@@ -130,9 +132,14 @@ def graph_scattering(H, E, lead_site, t):
         A[N + p, s] = 1.0
         A[N + p, N + p] = -1.0
     S = np.zeros((P, P), complex)
+    psi = np.zeros((P, N), complex)
     for l, s in enumerate(lead_site):
         rhs = np.zeros(N + P, complex)
         rhs[s] += t * li
         rhs[N + l] = 1.0
-        S[:, l] = np.linalg.solve(A, rhs)[N:]
+        x = np.linalg.solve(A, rhs)
+        S[:, l] = x[N:]
+        psi[l] = x[:N]
+    if want_states:
+        return S, psi, abs(t) * abs(lo - 1.0 / lo)
     return S

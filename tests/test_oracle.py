@@ -535,6 +535,42 @@ def test_lesser_complex_hamiltonian_conservation():
         assert np.abs(r["jx"].sum(axis=1) - d["T_LR"]).max() < 1e-11
 
 
+def test_graph_lesser_reduces_to_the_slice_form():
+    """A slice system written out as a site graph with its two leads on the
+    end slices: graph_lesser's densities, LDOS, currents and T equal the slice
+    routine's (random complex slices, diagonal V, unequal random leads)."""
+    rng = np.random.default_rng(12)
+    M, L = 3, 4
+    X = rng.normal(size=(M, M)) + 1j * rng.normal(size=(M, M))
+    H0 = X + X.conj().T
+    V = np.diag(rng.normal(size=M) + 1j * rng.normal(size=M))
+    eps = rng.uniform(-1, 1, (L, M))
+    SL = inputs.random_retarded_sigma(rng, M)
+    SR = inputs.random_retarded_sigma(rng, M)
+    N = M * L
+    H = np.zeros((N, N), complex)
+    for n in range(L):
+        H[n * M:(n + 1) * M, n * M:(n + 1) * M] = H0 + np.diag(eps[n])
+        if n + 1 < L:
+            H[(n + 1) * M:(n + 2) * M, n * M:(n + 1) * M] = V
+            H[n * M:(n + 1) * M, (n + 1) * M:(n + 2) * M] = V.conj().T
+    for E in (-0.9, 0.3):
+        r = oracle.lesser_parts(H0, V, eps, L, E, SL, SR)
+        g = oracle.graph_lesser(H, E, [np.arange(M), np.arange(N - M, N)], [SL, SR])
+        assert np.abs(g["rho"][0] - r["rhoL"].ravel()).max() < 1e-12
+        assert np.abs(g["rho"][1] - r["rhoR"].ravel()).max() < 1e-12
+        assert np.abs(g["ldos"] - r["ldos"].ravel()).max() < 1e-12
+        assert abs(g["T"][1, 0] - r["T"]) < 1e-12
+        edge = {(int(i), int(j)): k for k, (i, j) in enumerate(g["edges"])}
+        for n in range(L - 1):
+            for x in range(M):
+                a, b = n * M + x, (n + 1) * M + x
+                assert abs(g["J"][0, edge[(a, b)]] - r["jx"][n, x]) < 1e-12
+        for n in range(L):
+            for k, (x, y) in enumerate(r["edges"]):
+                assert abs(g["J"][0, edge[(n * M + x, n * M + y)]] - r["jt"][n, k]) < 1e-12
+
+
 # --------------------------------------------------------------------------
 # Multi-terminal transmissions (Sec. 2.3 T_kl between every pair of leads)
 

@@ -144,3 +144,40 @@ def test_transmission_matrix_random_graph_and_two_lead_dense():
         S2 = sc.graph_scattering(H, E, [0, 8], 1.0)
         t10, t01 = oracle.dense_general(H, E, [0], sig, [8], sig)
         assert abs(t10 - abs(S2[1, 0]) ** 2) < TOL and abs(t01 - abs(S2[0, 1]) ** 2) < TOL
+
+
+@pytest.mark.parametrize("E", [-1.3, 0.1, 1.6])
+def test_graph_lesser_matches_scattering_states(E):
+    """Densities injected by each lead, the LDOS and the bond currents of a
+    random complex graph with four chain leads and of the chiral ring, from
+    scattering states; Kirchhoff's law at every site without a lead, and the
+    current leaving through lead k is T_kl."""
+    rng = np.random.default_rng(33)
+    N = 9
+    X = (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))) * (rng.random((N, N)) < 0.4)
+    H = np.triu(X, 1)
+    H = H + H.conj().T + np.diag(rng.normal(size=N))
+    H[np.arange(N - 1), np.arange(1, N)] += 1.0
+    H[np.arange(1, N), np.arange(N - 1)] += 1.0
+    for H, leads in ((H, [0, 3, 5, 8]), (chiral_ring(3, 0.7), [0, 1, 2])):
+        N, P = H.shape[0], len(leads)
+        S, psi, v = sc.graph_scattering(H, E, leads, 1.0, want_states=True)
+        sig = oracle.sigma_square(1, 1.0, E)
+        o = oracle.graph_lesser(H, E, [[s] for s in leads], [sig] * P)
+        assert np.abs(o["rho"] - np.abs(psi) ** 2 / (2 * np.pi * v)).max() < TOL
+        assert np.abs(o["ldos"] - o["rho"].sum(axis=0)).max() < TOL
+        for l in range(P):
+            for e, (i, j) in enumerate(o["edges"]):
+                want = -2 * np.imag(H[i, j] * psi[l, j] * np.conj(psi[l, i])) / v
+                assert abs(o["J"][l, e] - want) < TOL
+            out = np.zeros(N)          # net current leaving each site along the edges
+            for e, (i, j) in enumerate(o["edges"]):
+                out[i] += o["J"][l, e]
+                out[j] -= o["J"][l, e]
+            inner = np.setdiff1d(np.arange(N), leads)
+            assert np.abs(out[inner]).max(initial=0) < TOL
+            for k in range(P):
+                if k != l:     # what reaches lead k's site leaves into lead k
+                    assert abs(-out[leads[k]] - o["T"][k, l]) < TOL
+                    assert abs(o["T"][k, l] - abs(S[k, l]) ** 2) < TOL
+
