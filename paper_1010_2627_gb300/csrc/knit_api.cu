@@ -879,7 +879,7 @@ knit_status knit_lead_selfenergy(knit_system s, int32_t lead, const double *E, i
     const size_t MM = (size_t)s->M * s->M;
     const double *dE;
     if ((r = stage_in(s->E, E, (size_t)nE, st, &dE, "E")) != KNIT_OK) return r;
-    double2 *dS;
+    double2 *dS = nullptr;
     bool hS;
     if ((r = stage_out(s->sigL, (double2 *)sigma, MM * nE, &dS, &hS, "sigma")) != KNIT_OK) return r;
     CK(s->gL.ensure(sizeof(double2) * MM * nE), "g workspace");
