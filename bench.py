@@ -61,6 +61,19 @@ def _clock_sampler():
         return None
 
 
+def _smi_index(dev_index, seen):
+    """nvidia-smi's index of CUDA device dev_index: through
+    CUDA_VISIBLE_DEVICES when it lists plain indices, else the same number;
+    the only index sampled when that one is absent."""
+    want = str(dev_index)
+    vis = [x.strip() for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    if dev_index < len(vis) and vis[dev_index].isdigit():
+        want = vis[dev_index]
+    if want not in seen and len(seen) == 1:
+        want = next(iter(seen))
+    return want
+
+
 def _clock_summary(proc, dev_index):
     if proc is None:
         return None
@@ -70,11 +83,17 @@ def _clock_summary(proc, dev_index):
     except Exception:
         proc.kill()
         out, _ = proc.communicate()
+    return _parse_clocks(out, dev_index)
+
+
+def _parse_clocks(out, dev_index):
     sm, mx, reasons = [], [], set()
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    for line in out.splitlines():
-        f = [x.strip() for x in line.split(",")]
-        if len(f) < 9 or f[0] != str(dev_index):
+    rows = [[x.strip() for x in line.split(",")] for line in out.splitlines()]
+    rows = [f for f in rows if len(f) >= 9]
+    want = _smi_index(dev_index, {f[0] for f in rows})
+    for f in rows:
+        if f[0] != want:
             continue
         try:
             sm.append(float(f[1]))
