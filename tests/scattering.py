@@ -143,3 +143,29 @@ def graph_scattering(H, E, lead_site, t, want_states=False):
     if want_states:
         return S, psi, abs(t) * abs(lo - 1.0 / lo)
     return S
+
+
+def lead_surface_g_from_modes(H0, V, z, side):
+    """Retarded surface Green function of a general lead at complex energy
+    z = E + i eta from its Bloch modes (no decimation).  Left lead (side 0):
+    cell j + 1 lies outward of cell j with H_{j, j+1} = V, so a mode
+    psi_j = u lambda^j solves (z - H0 - lambda V - V^dagger / lambda) u = 0;
+    the m modes that decay outward at Im z > 0 (|lambda| < 1) give the Bloch
+    matrix F = U Lambda U^{-1} with psi_{j+1} = F psi_j, and eliminating
+    every outer cell leaves g = (z - H0 - V F)^{-1}.  Right lead (side 1):
+    V and V^dagger exchange roles.  Needs an invertible V."""
+    import scipy.linalg as sla
+    H0 = np.asarray(H0, complex)
+    V = np.asarray(V, complex)
+    m = H0.shape[0]
+    Vo, Vi = (V, V.conj().T) if side == 0 else (V.conj().T, V)
+    I, Z = np.eye(m), np.zeros((m, m))
+    # lambda [[I, 0], [0, Vo]] y = [[0, I], [-Vi, z - H0]] y, y = [u; lambda u]
+    A = np.block([[Z, I], [-Vi, z * I - H0]])
+    B = np.block([[I, Z], [Z, Vo]])
+    lam, Y = sla.eig(A, B)
+    out = np.flatnonzero(np.abs(lam) < 1.0)
+    assert len(out) == m, "a retarded lead has as many outgoing modes as orbitals"
+    U = Y[:m, out]
+    F = U @ np.diag(lam[out]) @ np.linalg.inv(U)
+    return np.linalg.inv(z * I - H0 - Vo @ F)

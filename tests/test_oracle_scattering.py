@@ -181,3 +181,35 @@ def test_graph_lesser_matches_scattering_states(E):
                     assert abs(-out[leads[k]] - o["T"][k, l]) < TOL
                     assert abs(o["T"][k, l] - abs(S[k, l]) ** 2) < TOL
 
+
+
+def test_decimation_matches_bloch_modes():
+    """The oracle's Sancho-Rubio decimation against the surface Green
+    function built from the lead's Bloch modes (the m modes decaying outward
+    at E + i eta, g = (z - H0 - V F)^{-1}), for random complex leads with a
+    non-Hermitian coupling and for spinful Nambu leads with Rashba coupling
+    and pairing; the two sides differ (V and V^dagger exchange roles), which
+    the comparison sees."""
+    from paper_1010_2627_gb300 import inputs
+    rng = np.random.default_rng(4)
+    eta = 1e-9
+    leads = []
+    for m in (1, 4, 7):
+        X = rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m))
+        V = np.eye(m) + 0.4 * (rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m)))
+        leads.append((0.5 * (X + X.conj().T), V, (-1.3, 0.2, 2.1)))
+    for ld in (0.0, 0.1):
+        b = inputs.bdg(2, 3, mu=-1.0, delta=0.1, alpha=0.2, lead_delta=ld)
+        leads.append((b.lead_H0[0], b.lead_V[0], (-0.13, 0.07, 0.4)))
+    for H0, V, energies in leads:
+        for E in energies:
+            gs = []
+            for side in (0, 1):
+                g, S, _ = oracle.decimation(H0, V, E, side, eta=eta)
+                gm = sc.lead_surface_g_from_modes(H0, V, E + 1j * eta, side)
+                assert np.abs(g - gm).max() < 1e-9 * max(1.0, np.abs(gm).max()), (E, side)
+                Vo = V if side == 0 else V.conj().T
+                assert np.abs(S - Vo @ gm @ Vo.conj().T).max() < 1e-9 * max(1.0, np.abs(S).max())
+                gs.append(gm)
+            if H0.shape[0] > 1 and not np.allclose(V, V.conj().T):   # a 1 x 1 V enters as |V|^2
+                assert np.abs(gs[0] - gs[1]).max() > 1e-3
