@@ -169,3 +169,84 @@ def lead_surface_g_from_modes(H0, V, z, side):
     U = Y[:m, out]
     F = U @ np.diag(lam[out]) @ np.linalg.inv(U)
     return np.linalg.inv(z * I - H0 - Vo @ F)
+
+
+def lead_modes(H0, V, E, side, eta=1e-9):
+    """Bloch modes of a general lead at real energy E, split into the m
+    outgoing ones (decaying outward at E + i eta, or propagating outward) and
+    the propagating incoming ones.  Cells j = 0, 1, ... run outward with
+    H_{j, j+1} = Vo (V for the left lead, V^dagger for the right one); a mode
+    is psi_j = u lambda^j with (E - H0 - lambda Vo - Vo^dagger / lambda) u = 0
+    and |u| = 1, and carries the outward current -2 Im(lambda u^dagger Vo u)
+    when |lambda| = 1.  Needs an invertible V and non-degenerate propagating
+    modes.  Returns (lam_out, U_out, v_out, lam_in, U_in, v_in) with v the
+    absolute currents (zero for evanescent outgoing modes)."""
+    import scipy.linalg as sla
+    H0 = np.asarray(H0, complex)
+    V = np.asarray(V, complex)
+    m = H0.shape[0]
+    Vo, Vi = (V, V.conj().T) if side == 0 else (V.conj().T, V)
+    I, Z = np.eye(m), np.zeros((m, m))
+
+    def pencil(z):
+        lam, Y = sla.eig(np.block([[Z, I], [-Vi, z * I - H0]]), np.block([[I, Z], [Z, Vo]]))
+        U = Y[:m] / np.linalg.norm(Y[:m], axis=0)
+        return lam, U
+
+    lam_c, _ = pencil(E + 1j * eta)
+    lam, U = pencil(E)
+    # pair every real-E mode with its shifted copy
+    used, out, inn = set(), [], []
+    for k in range(2 * m):
+        j = min((i for i in range(2 * m) if i not in used), key=lambda i: abs(lam_c[i] - lam[k]))
+        used.add(j)
+        (out if abs(lam_c[j]) < 1.0 else inn).append(k)
+    assert len(out) == m
+    cur = -2 * np.imag(lam * np.einsum("im,ij,jm->m", U.conj(), Vo, U))
+    prop = np.abs(np.abs(lam) - 1.0) < 1e-7
+    v_out = np.where(prop[out], np.abs(cur[out]), 0.0)
+    inn = [k for k in inn if prop[k]]
+    return lam[out], U[:, out], v_out, lam[inn], U[:, inn], np.abs(cur[inn])
+
+
+def slice_system_scattering_general(H0, V, eps, L, E, leads):
+    """T of a slice system (H_{n, n-1} = V, slices H0 + diag(eps_n)) between
+    two general leads leads[p] = (H0_p, V_p) that continue it (left cells to
+    the left with the same orientation, right cells to the right), by mode
+    matching: the system's end slice equals the lead wave continued one cell
+    inward.  Returns (T, R) summed over propagating modes, flux-normalised."""
+    H0 = np.asarray(H0, complex)
+    M = H0.shape[0]
+    N = M * L
+    modes = [lead_modes(*leads[p], E, p) for p in (0, 1)]
+    nu = N + 2 * M
+    A = np.zeros((nu, nu), complex)
+    for n in range(L):
+        b = slice(n * M, (n + 1) * M)
+        A[b, b] = E * np.eye(M) - H0 - (np.diag(eps[n]) if eps is not None else 0)
+        if n > 0:
+            A[b, (n - 1) * M:n * M] = -V
+        if n + 1 < L:
+            A[b, (n + 1) * M:(n + 2) * M] = -V.conj().T
+    rows = [slice(0, M), slice(N - M, N)]
+    cols = [slice(N, N + M), slice(N + M, N + 2 * M)]
+    Vo = [np.asarray(leads[0][1], complex), np.asarray(leads[1][1], complex).conj().T]
+    for p in (0, 1):
+        lo, Uo = modes[p][0], modes[p][1]
+        # the end slice couples to lead cell 0 through Vo: -Vo psi_cell0
+        A[rows[p], cols[p]] = -Vo[p] @ Uo
+        # matching: psi_end - sum_m b_m u_m / lambda_m = (incoming part)
+        A[cols[p], rows[p]] = np.eye(M)
+        A[cols[p], cols[p]] = -Uo / lo[None, :]
+    lo0, Uo0, vo0, li0, Ui0, vi0 = modes[0]
+    T = R = 0.0
+    for n in range(len(li0)):
+        rhs = np.zeros(nu, complex)
+        a = Ui0[:, n] / np.sqrt(vi0[n])
+        rhs[rows[0]] = Vo[0] @ a
+        rhs[cols[0]] = a / li0[n]
+        x = np.linalg.solve(A, rhs)
+        bL, bR = x[cols[0]], x[cols[1]]
+        T += np.sum(np.abs(bR) ** 2 * modes[1][2])
+        R += np.sum(np.abs(bL) ** 2 * vo0)
+    return T, R, len(li0)

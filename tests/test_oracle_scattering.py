@@ -213,3 +213,39 @@ def test_decimation_matches_bloch_modes():
                 gs.append(gm)
             if H0.shape[0] > 1 and not np.allclose(V, V.conj().T):   # a 1 x 1 V enters as |V|^2
                 assert np.abs(gs[0] - gs[1]).max() > 1e-3
+
+
+def _bdg_case(ld, E):
+    from paper_1010_2627_gb300 import inputs
+    b = inputs.bdg(2, 4, mu=-1.0, delta=0.1, alpha=0.2, lead_delta=ld)
+    eps = oracle.onsite(3, b.L, b.M, 0.5, block=b.block, sign=b.sign)
+    return b.H0, b.V[0], eps, b.L, [(b.lead_H0[p], b.lead_V[p]) for p in (0, 1)]
+
+
+def _random_lead_case(rng):
+    m, L = 3, 5
+    X = rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m))
+    H0 = 0.5 * (X + X.conj().T)
+    V = np.eye(m) + 0.3 * (rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m)))
+    eps = rng.uniform(-1, 1, (L, m))
+    return H0, V, eps, L, [(H0, V), (H0, V)]
+
+
+def test_sweep_T_matches_mode_matching_with_general_leads():
+    """rgf's T with decimated self-energies against mode matching with the
+    leads' Bloch modes (flux-normalised, T + R = number of open modes): BdG
+    bars with spin-orbit coupling and pairing, with normal leads and with
+    superconducting leads outside their gap, and a lead with a random
+    non-Hermitian coupling."""
+    rng = np.random.default_rng(9)
+    cases = [(_bdg_case(0.0, None), (-0.13, 0.07, 0.4)),
+             (_bdg_case(0.1, None), (-0.35, 0.4)),
+             (_random_lead_case(rng), (-1.1, 0.3, 1.7))]
+    for (H0, V, eps, L, leads), energies in cases:
+        for E in energies:
+            T, R, nopen = sc.slice_system_scattering_general(H0, V, eps, L, E, leads)
+            assert nopen > 0 and abs(T + R - nopen) < 1e-9
+            SL = oracle.decimation(*leads[0], E, 0, eta=1e-12)[1]
+            SR = oracle.decimation(*leads[1], E, 1, eta=1e-12)[1]
+            To = oracle.rgf(H0, V, eps, L, E, SL, SR)["T"]
+            assert abs(To - T) < 1e-8 * max(1.0, T), (E, To, T)
