@@ -153,7 +153,9 @@ def lead_surface_g_from_modes(H0, V, z, side):
     the m modes that decay outward at Im z > 0 (|lambda| < 1) give the Bloch
     matrix F = U Lambda U^{-1} with psi_{j+1} = F psi_j, and eliminating
     every outer cell leaves g = (z - H0 - V F)^{-1}.  Right lead (side 1):
-    V and V^dagger exchange roles.  Needs an invertible V."""
+    V and V^dagger exchange roles.  A singular V (a graphene ribbon's
+    two-slice cell) is fine: its modes with lambda = 0 are among the m, as
+    long as their U is invertible."""
     import scipy.linalg as sla
     H0 = np.asarray(H0, complex)
     V = np.asarray(V, complex)

@@ -187,9 +187,10 @@ def test_decimation_matches_bloch_modes():
     """The oracle's Sancho-Rubio decimation against the surface Green
     function built from the lead's Bloch modes (the m modes decaying outward
     at E + i eta, g = (z - H0 - V F)^{-1}), for random complex leads with a
-    non-Hermitian coupling and for spinful Nambu leads with Rashba coupling
-    and pairing; the two sides differ (V and V^dagger exchange roles), which
-    the comparison sees."""
+    non-Hermitian coupling, spinful Nambu leads with Rashba coupling and
+    pairing, and a graphene ribbon's two-slice cell (singular coupling); the
+    two sides differ (V and V^dagger exchange roles), which the comparison
+    sees."""
     from paper_1010_2627_gb300 import inputs
     rng = np.random.default_rng(4)
     eta = 1e-9
@@ -201,6 +202,15 @@ def test_decimation_matches_bloch_modes():
     for ld in (0.0, 0.1):
         b = inputs.bdg(2, 3, mu=-1.0, delta=0.1, alpha=0.2, lead_delta=ld)
         leads.append((b.lead_H0[0], b.lead_V[0], (-0.13, 0.07, 0.4)))
+    # graphene (armchair) ribbon: the two-slice cell of a period-2 lead, whose
+    # coupling to the next cell is singular
+    a = inputs.armchair(6, 4)
+    Vf, Vs = a.lead_V[0]
+    Hc = np.zeros((12, 12), complex)
+    Vc = np.zeros_like(Hc)
+    Hc[:6, :6] = Hc[6:, 6:] = a.H0
+    Hc[:6, 6:], Hc[6:, :6], Vc[6:, :6] = Vs, Vs.conj().T, Vf
+    leads.append((Hc, Vc, (-2.9, -0.8, 0.5, 2.2)))
     for H0, V, energies in leads:
         for E in energies:
             gs = []
