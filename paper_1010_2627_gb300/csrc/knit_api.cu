@@ -1127,12 +1127,56 @@ knit_status graph_plan(int N, const knit_c128 *Hin, int P, const int32_t *nsites
                 return fail(KNIT_ERR_INVALID, "site %d of lead %d is not connected to lead 0", v, p);
             d1 = std::min(d1, depth[v]);
         }
-    // slices: layers 0 .. d1-1, then every reachable site at depth >= d1
+    // Slices are the level sets of an integer function l with l = 0 exactly
+    // on lead 0's sites, l = K - 1 = d1 on every other lead's sites, and
+    // |l(u) - l(v)| <= 1 along every edge (so H is block tridiagonal).  The
+    // family l_s(v) = max(1, min(depth(v), d1, d1 - dist(v) + s)), dist the
+    // distance to the other leads' sites, has these properties for every
+    // s >= 0: s = 0 folds the sites behind a lead back into earlier slices,
+    // s = max dist gives the breadth-first layers with everything from depth
+    // d1 on merged into the last slice.  The plan takes the s with the least
+    // sweep work (sum of w_k^3 + w_k^2 w_{k-1}), the layers on ties.
+    std::vector<int> dist(N, -1), q2;
+    for (int p = 1; p < P; ++p)
+        for (int v : ls[p]) {
+            dist[v] = 0;
+            q2.push_back(v);
+        }
+    for (size_t q = 0; q < q2.size(); ++q) {
+        const int u = q2[q];
+        for (int v = 0; v < N; ++v) {
+            const double2 h = H[(size_t)u * N + v];
+            if (v != u && dist[v] < 0 && (h.x != 0.0 || h.y != 0.0)) {
+                dist[v] = dist[u] + 1;
+                q2.push_back(v);
+            }
+        }
+    }
+    int smax = 0;
+    for (int v = 0; v < N; ++v)
+        if (depth[v] >= 0) smax = std::max(smax, dist[v]);
+    auto level = [&](int v, int s) {
+        return depth[v] == 0 ? 0 : std::max(1, std::min(std::min(depth[v], d1), d1 - dist[v] + s));
+    };
     const int K = d1 + 1;
+    int best_s = smax;
+    double best = -1.0;
+    std::vector<double> w(K);
+    for (int sv = smax; sv >= 0; --sv) {
+        std::fill(w.begin(), w.end(), 0.0);
+        for (int v = 0; v < N; ++v)
+            if (depth[v] >= 0) w[level(v, sv)] += 1.0;
+        double cost = 0.0;
+        for (int k = 0; k < K; ++k) cost += w[k] * w[k] * (w[k] + (k > 0 ? w[k - 1] : 0.0));
+        if (best < 0.0 || cost < best) {
+            best = cost;
+            best_s = sv;
+        }
+    }
     std::vector<std::vector<int>> sl(K);
     sl[0] = ls[0];
     for (int v = 0; v < N; ++v)
-        if (depth[v] > 0) sl[std::min(depth[v], d1)].push_back(v);
+        if (depth[v] > 0) sl[level(v, best_s)].push_back(v);
     for (const auto &v : sl)
         if ((int)v.size() > KNIT_GRAPH_MAX_WIDTH)
             return fail(KNIT_ERR_INVALID, "a slice of %d sites: at most %d supported", (int)v.size(),

@@ -58,10 +58,28 @@ def check_plan(H, leads):
     assert K == 1 + min(d[v] for l in leads[1:] for v in l)
     for l in leads[1:]:
         assert (so[l] == K - 1).all()
-    # the slices before the last are the breadth-first layers
-    inner = d < K - 1
-    assert np.array_equal(so[inner & (d >= 0)], d[inner & (d >= 0)])
-    assert (so[d >= K - 1] == K - 1).all()
+    # the plan is the cheapest member of the family of level functions
+    # l_s = max(1, min(depth, D, D - dist + s)) (ties: the largest s, whose
+    # member s = max dist is the breadth-first layering)
+    D = K - 1
+    dist = bfs_depth(H, [v for l in leads[1:] for v in l])
+    on = d >= 0
+
+    def level(sv):
+        lv = np.where(on, np.maximum(1, np.minimum(np.minimum(d, D), D - dist + sv)), -1)
+        lv[list(leads[0])] = 0
+        return lv
+
+    def cost(lv):
+        w = np.bincount(lv[lv >= 0], minlength=K).astype(float)
+        return float(np.sum(w * w * (w + np.r_[0.0, w[:-1]])))
+
+    smax = int(dist[on].max())
+    costs = {sv: cost(level(sv)) for sv in range(smax + 1)}
+    best = min(costs.values())
+    s_pick = max(sv for sv, c in costs.items() if c == best)
+    assert np.array_equal(so, level(s_pick))
+    assert cost(so) <= cost(np.where(on, np.minimum(d, D), -1))   # never worse than the layers
     # no edge skips a slice: H is block tridiagonal in the slice order
     i, j = np.nonzero(H)
     off = i != j
@@ -178,3 +196,35 @@ def test_plan_rejects_a_slice_wider_than_the_sweep_takes():
     H[1, N - 1] = H[N - 1, 1] = 1.0
     with pytest.raises(knit.KnitError, match="at most 6144"):
         knit.knit_graph_plan(H, [[0], [N - 1]])
+
+
+def test_plan_side_contact_keeps_slices_narrow():
+    """A 6 x 20 bar with lead 0 on its left column and lead 1 along the right
+    half of its top edge: the breadth-first layers would merge the last ten
+    columns (60 sites) into one slice; the chosen plan folds the sites behind
+    the contact back into earlier slices and costs a fraction of the work."""
+    M, L = 6, 20
+    N = M * L
+    H = np.zeros((N, N))
+    for x in range(L):
+        for y in range(M):
+            s = x * M + y
+            if y + 1 < M:
+                H[s, s + 1] = H[s + 1, s] = 1.0
+            if x + 1 < L:
+                H[s, s + M] = H[s + M, s] = 1.0
+    lead1 = [x * M + M - 1 for x in range(10, 20)]
+    K, so = check_plan(H, [list(range(M)), lead1])
+    w = np.bincount(so, minlength=K)
+    assert w.max() <= 21 and set(np.flatnonzero(so == K - 1)) == set(lead1)
+    layers = np.bincount(np.minimum(bfs_depth(H, range(M)), K - 1), minlength=K)
+    assert layers.max() == 60
+    work = lambda w: float(np.sum(w ** 3.0 + w ** 2.0 * np.r_[0, w[:-1]]))
+    assert work(w) < 0.2 * work(layers)
+
+
+def test_plan_of_the_fig3_example():
+    from paper_1010_2627_gb300 import inputs
+    H, idx0, idx1, w0, w1 = inputs.lshape_example()
+    K, so = check_plan(H, [idx0, idx1])
+    assert (so >= 0).all() and (so[idx0] == 0).all() and (so[idx1] == K - 1).all()
