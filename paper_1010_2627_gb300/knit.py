@@ -527,6 +527,8 @@ class System:
 
     def lead_selfenergy(self, lead, E, method=KNIT_LEAD_AUTO, eta=0.0, want_residual=False,
                         models=(None, None)):
+        """(Sigma (nE, M, M), iterations (nE,), residual (nE,) or None) of lead
+        0 (left) or 1 (right) at the energies E."""
         E = np.ascontiguousarray(E, dtype=np.float64)
         S = np.empty((len(E), self.M, self.M), np.complex128)
         it = np.zeros(len(E), np.int32)
@@ -536,6 +538,8 @@ class System:
         return S, it, res
 
     def transmission(self, E, seeds=None, W=0.0, precision=KNIT_FP64, method=KNIT_LEAD_AUTO):
+        """(T (nE, nS), status (nE, nS)) for every energy x disorder seed;
+        W is the disorder strength, precision KNIT_FP64 or KNIT_MIXED."""
         E = np.ascontiguousarray(E, dtype=np.float64)
         sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
         nS = 1 if sd is None else len(sd)
@@ -545,6 +549,7 @@ class System:
         return T.reshape(len(E), nS), st.reshape(len(E), nS)
 
     def transmission_sigma(self, E, SL, SR, seeds=None, W=0.0, precision=KNIT_FP64):
+        """As transmission, with the lead self-energies SL, SR (nE, M, M) given."""
         E = np.ascontiguousarray(E, dtype=np.float64)
         sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
         nS = 1 if sd is None else len(sd)
@@ -593,6 +598,8 @@ class System:
 
     def ldos(self, E, seeds=None, W=0.0, saving_level=-1, method=KNIT_LEAD_AUTO,
              precision=KNIT_FP64):
+        """(LDOS (nE, nS, L, M), T (nE, nS), status (nE, nS)); saving_level k
+        keeps every k-th slice's g and recomputes the rest (-1: keep all)."""
         E = np.ascontiguousarray(E, dtype=np.float64)
         sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
         nS = 1 if sd is None else len(sd)
