@@ -253,8 +253,16 @@ typedef struct {
     const int32_t *const *lead_sites;/* P lists */
 } knit_graph_multi_desc;
 
+/* Two leads: copies H and the site lists (host or device memory), builds the
+ * slicing on the host and keeps device copies of the blocks in *out, owned by
+ * the library until knit_graph_destroy.  Errors as listed above, plus
+ * KNIT_ERR_OOM / KNIT_ERR_CUDA for device allocations and copies. */
 knit_status knit_graph_create(const knit_graph_desc *desc, knit_graph *out);
+
+/* The same for P >= 2 leads. */
 knit_status knit_graph_create_multi(const knit_graph_multi_desc *desc, knit_graph *out);
+
+/* Frees the graph and its device memory; NULL is accepted. */
 knit_status knit_graph_destroy(knit_graph g);
 
 /* The slicing of a description without creating a graph (host work only, no
@@ -323,11 +331,17 @@ knit_status knit_lead_model_train(knit_system sys, int32_t lead, const double *E
                                   uint64_t seed, const knit_lead_opts *opts, float *loss,
                                   knit_lead_model *out, void *stream);
 
+/* Frees the model and its device memory; NULL is accepted. */
 knit_status knit_lead_model_destroy(knit_lead_model model);
 
-/* Number of parameters; copy them out / in (host or device float arrays). */
+/* Number of parameters (0 for NULL). */
 int64_t knit_lead_model_num_params(knit_lead_model model);
+
+/* Copy the parameters out to a host or device float array of
+ * knit_lead_model_num_params values (layout above); KNIT_ERR_INVALID for NULL. */
 knit_status knit_lead_model_get_params(knit_lead_model model, float *params);
+
+/* Copy the parameters in from a host or device float array (same layout). */
 knit_status knit_lead_model_set_params(knit_lead_model model, const float *params);
 
 /* Network output for nE energies: nE x 2 M^2 floats (re, im of g, row-major). */
@@ -352,9 +366,14 @@ knit_status knit_lead_model_gradient(knit_lead_model model, const double *E, con
  * only enqueues kernels and can be captured in a CUDA graph. */
 typedef struct knit_batch_s *knit_batch;
 
+/* Build a plan for nInst instances over nSys systems (precision KNIT_FP64,
+ * KNIT_MIXED or KNIT_MIXED_CUDACORE).  KNIT_ERR_INVALID for NULL arguments,
+ * nSys or nInst below 1, a NULL system, a sys_index out of range or an
+ * unknown precision; KNIT_ERR_OOM / KNIT_ERR_CUDA for device failures. */
 knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const int32_t *sys_index,
                               int32_t nInst, int32_t precision, knit_batch *out);
 
+/* Frees the plan and its device memory (not the systems); NULL is accepted. */
 knit_status knit_batch_destroy(knit_batch batch);
 
 /* Run a plan: E, seeds and W hold one value per instance (seeds, W may be

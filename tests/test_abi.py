@@ -67,3 +67,20 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(knit, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no fallback"):
         knit.load()
+
+
+def test_every_declaration_is_documented():
+    """Each entry point of include/knit.h has its own comment right above it
+    (what it computes, argument layout, ownership, errors)."""
+    lines = open(os.path.join(ROOT, "include", "knit.h")).read().split("\n")
+    missing = []
+    for i, line in enumerate(lines):
+        m = re.match(r"^(?:knit_status|int64_t|const char \*)\s*(knit_\w+)\s*\(", line)
+        if not m:
+            continue
+        j = i - 1
+        while j >= 0 and not lines[j].strip():
+            j -= 1
+        if not lines[j].rstrip().endswith("*/"):
+            missing.append(m.group(1))
+    assert not missing, missing
