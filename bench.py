@@ -680,10 +680,126 @@ def run_lesser_case(args):
     sysk.close()
 
 
+def hall_bar(Lx=96, Ly=32, w_side=16, W_dis=1.0, seed=4):
+    """A disordered four-terminal bar as a site graph (square lattice, t = 1,
+    on-site U[-W/2, W/2] from a seeded generator): lead 0 on the left column,
+    lead 1 on the right column, leads 2 and 3 on the middle w_side sites of
+    the top and bottom edges."""
+    rng = np.random.default_rng(seed)
+    N = Lx * Ly
+    H = np.zeros((N, N), np.complex128)
+    for x in range(Lx):
+        for y in range(Ly):
+            s = x * Ly + y
+            H[s, s] = W_dis * (rng.random() - 0.5)
+            if y + 1 < Ly:
+                H[s, s + 1] = H[s + 1, s] = 1.0
+            if x + 1 < Lx:
+                H[s, s + Ly] = H[s + Ly, s] = 1.0
+    x0 = (Lx - w_side) // 2
+    leads = [np.arange(Ly), (Lx - 1) * Ly + np.arange(Ly),
+             np.array([x * Ly + Ly - 1 for x in range(x0, x0 + w_side)]),
+             np.array([x * Ly for x in range(x0, x0 + w_side)])]
+    return H, leads
+
+
+def graph_flop(widths, w0):
+    """Algorithmic FP64 flops of the knitting sweep per energy (8 per complex
+    FMA): per slice the inverse (w^3), V g V^dagger (w_{k-1}^2 w + w^2 w_{k-1}),
+    and the two carried blocks G_{0,k}, G_{k,0} (2 (w0 w_{k-1} w + w0 w^2))."""
+    f = 0.0
+    for k, w in enumerate(widths):
+        f += w ** 3
+        if k:
+            p = widths[k - 1]
+            f += p * p * w + w * w * p + 2 * (w0 * p * w + w0 * w * w)
+    return 8.0 * f
+
+
+def run_graph_case(args):
+    """Multi-terminal transmission matrix of a disordered four-terminal bar
+    (96 x 32 sites, leads of 32, 32, 16 and 16 sites; the knitting sweep over
+    an arbitrary geometry, FP64): one step = T_kl for every pair of leads at
+    256 energies, self-energies and outputs in device memory.  Beside it: the
+    oracle's dense solve on a bounded sample of energies."""
+    import torch
+    from paper_1010_2627_gb300 import build, inputs, knit
+    build.build()
+    knit.load()
+    H, leads = hall_bar()
+    ne = 256
+    E = inputs.energy_grid(-3.5, 3.5, ne)
+    g = knit.Graph(H, leads=leads)
+    widths, _ = g.slices()
+    sig = []
+    for l in leads:
+        S = knit.System(inputs.square(len(l), 2)).lead_selfenergy(0, E, method=knit.KNIT_LEAD_MODES)[0]
+        sig.append(torch.tensor(S, device="cuda"))
+    P = len(leads)
+    stream = torch.cuda.Stream()
+    dE = torch.tensor(E, device="cuda")
+    dTm = torch.empty(ne * P * P, dtype=torch.float64, device="cuda")
+    dst = torch.empty(ne, dtype=torch.int32, device="cuda")
+
+    def step():
+        knit.knit_graph_conductance(g.handle, dE, sig, dTm, dst, nE=ne, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    Tm = dTm.cpu().numpy().reshape(ne, P, P)
+    st = dst.cpu().numpy()
+    flop = graph_flop([int(w) for w in widths], len(leads[0])) * ne
+    achieved = flop / (ms / 1e3) / 1e12
+    line = {
+        "metric": "multi-terminal T_kl energies/s (knitting over an arbitrary geometry, FP64)",
+        "value": ne / (ms / 1e3), "unit": "energies/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"disordered four-terminal bar 96 x 32 (W = 1), leads 32/32/16/16 "
+                               f"sites, {ne} energies", "slices": len(widths),
+                   "max_slice_width": int(max(widths))},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
+                     "traffic": None,
+                     "note": "algorithmic flops from the slice widths (graph_flop) over the "
+                             "nominal FP64 rate"},
+        "buttiker_sum_rule_max": float(np.abs(Tm.sum(axis=2) - Tm.sum(axis=1))[st == 0].max()),
+        "status_nonzero": int((st != 0).sum())}
+    if args.cpu_baseline:
+        import oracle
+        t0, done = time.perf_counter(), 0
+        worst = 0.0
+        for e in np.linspace(0, ne - 1, 4).astype(int):
+            To = oracle.transmission_matrix(H, E[e], leads, [s[e].cpu().numpy() for s in sig])
+            worst = max(worst, float(np.abs(To - Tm[e]).max()))
+            done += 1
+            if time.perf_counter() - t0 > 20.0:
+                break
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt, "unit": "energies/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{done} energies, dense numpy inverse, {dt:.1f} s"}
+        line["max_abs_dT_vs_oracle"] = worst
+    print(json.dumps(line), flush=True)
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "profile", "uneven", "ldos", "bdg", "eigen", "lesser"])
+                    choices=["bench", "profile", "uneven", "ldos", "bdg", "eigen", "lesser",
+                             "graph"])
     ap.add_argument("--bdg-energies", dest="bdg_energies", type=int, default=2048)
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,6 +820,8 @@ def main():
         run_bdg_case(args)
     elif args.case == "eigen":
         run_eigen_case(args)
+    elif args.case == "graph":
+        run_graph_case(args)
     elif args.case == "lesser":
         run_lesser_case(args)
     elif args.impl == "reference":
