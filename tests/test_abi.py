@@ -84,3 +84,23 @@ def test_every_declaration_is_documented():
         if not lines[j].rstrip().endswith("*/"):
             missing.append(m.group(1))
     assert not missing, missing
+
+
+def _header_arities():
+    src = open(os.path.join(ROOT, "include", "knit.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(knit_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        name, params = m.group(1), " ".join(m.group(2).split())
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_header():
+    """The ctypes signatures take as many arguments as the C declarations
+    (a mismatch would pass garbage through the ABI)."""
+    from paper_1010_2627_gb300 import knit
+    ar = _header_arities()
+    assert set(ar) == set(knit._SIGS)
+    bad = {n: (ar[n], len(knit._SIGS[n][1])) for n in ar if ar[n] != len(knit._SIGS[n][1])}
+    assert not bad, bad
