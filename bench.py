@@ -37,9 +37,6 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # launch of the sweep kernel on exactly this workload, for the kernel as it
 # stands; set to None whenever the kernel changes until it is measured again
 SWEEP_TRAFFIC_BYTES = 69.85e6
-# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS_NOMINAL = 1.25
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -117,6 +114,42 @@ def _peaks():
         return {}
 
 
+# iterations per launch of each peak loop (a few ms each on GB300)
+PEAK_ITERS = {"mma_bf16_tflops": 40000, "mma_tf32_tflops": 40000, "dfma_tflops": 2000,
+              "ffma_tflops": 20000}
+
+
+def measure_peaks(knit, torch, stream, nsm, reps=5):
+    """The library's own peak loops (tcgen05 kind::f16 and kind::tf32 dense
+    MMA, FP64 and FP32 FMA), each timed with CUDA events on `stream` over
+    `reps` launches after one warm-up launch (median), with the SM clock
+    sampled during the loops.  Returns TFLOP/s per kind."""
+    kinds = {"mma_bf16_tflops": knit.KNIT_PEAK_MMA_BF16, "mma_tf32_tflops": knit.KNIT_PEAK_MMA_TF32,
+             "dfma_tflops": knit.KNIT_PEAK_DFMA, "ffma_tflops": knit.KNIT_PEAK_FFMA}
+    out = {}
+    clocks = _clock_sampler()
+    for name, kind in kinds.items():
+        knit.knit_peak_probe(kind, PEAK_ITERS[name], nsm, stream=stream, check=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        flop = 0.0
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                a.record(stream)
+                flop = knit.knit_peak_probe(kind, PEAK_ITERS[name], nsm, stream=stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        out[name] = flop / (ms / 1e3) / 1e12
+    out["clocks"] = _clock_summary(clocks, torch.cuda.current_device())
+    out["nsm"] = nsm
+    out["how"] = ("own loops (csrc/peaks.cu): one CTA per SM issuing back-to-back "
+                  "tcgen05.mma M=128 N=256 (K=16 bf16 / K=8 tf32) into one tensor-memory "
+                  "accumulator; 8 x 256 threads per SM with 8 independent FMA chains each; "
+                  f"CUDA events, median of {reps} launches after a warm-up")
+    return out
+
+
 def cpu_baseline(E, seeds, budget_s=15.0):
     """The oracle's slice sweep on all host cores over a bounded sample of the
     workload's instances; returns instances/s and what was sampled."""
@@ -153,16 +186,23 @@ def run_reference(args):
     from paper_1010_2627_gb300 import inputs
     E = inputs.energy_grid(-3.9, 3.9, NE)
     seeds = np.arange(NS, dtype=np.uint64)
-    times, vals = [], []
+    times, vals, step_ms = [], [], []
     for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         r = cpu_baseline(E, seeds, budget_s=8.0)
         if k >= args.warmup:
+            step_ms.append(1e3 * (time.perf_counter() - t0))
             vals.append(r["value"])
             times.append(r)
     v = statistics.median(vals)
+    # one step = one bounded sample of the workload's instances (measured);
+    # the whole 8192-instance workload at this rate is only extrapolated
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "T(E) points/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * NE * NS / v, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": statistics.median(step_ms),
+            "step": "a bounded sample of the workload (see cpu_baseline.sample), timed",
+            "full_workload_ms_extrapolated": 1e3 * NE * NS / v,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "instances": NE * NS, "flush": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": "T(E) points/s", "cores": times[-1]["cores"],
@@ -186,6 +226,8 @@ def run_knit(args):
     knit.load()
 
     from paper_1010_2627_gb300 import shard
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    pk = measure_peaks(knit, torch, torch.cuda.current_stream(), nsm)
     ss = inputs.square(M, L)
     # weak scaling: the global grid has NE energies per rank, rank r takes
     # every ws-th energy (its own 1024-energy shard of the same interval)
@@ -278,6 +320,7 @@ def run_knit(args):
     torch.cuda.synchronize()
     fp64_ms = a.elapsed_time(b)
     fp64_rate = nsub_e * NS / (fp64_ms / 1e3)
+    fp64_tflops = 16.0 * M ** 3 * L * nsub_e * NS / (fp64_ms / 1e3) / 1e12
     # the same subset through the CUDA-core residual path of the mixed sweep
     dTc = torch.empty(nsub_e * NS, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
@@ -318,25 +361,37 @@ def run_knit(args):
         "fp64_sweep": {"value": fp64_rate, "unit": "T(E) points/s",
                        "sample": f"{nsub_e} energies x {NS} seeds, one wave", "ms": fp64_ms,
                        "mixed_speedup": value / ws / fp64_rate,
+                       "roofline": {"bound": "fp64", "achieved": fp64_tflops,
+                                    "peak": pk["dfma_tflops"], "unit": "TFLOP/s",
+                                    "frac": fp64_tflops / pk["dfma_tflops"],
+                                    "note": "16 M^3 flop per slice-update over the measured "
+                                            "DFMA peak (own loop, csrc/peaks.cu); includes "
+                                            "the lead solve of the subset"},
                        "mixed_cudacore_residual_rate": cc_rate,
                        "max_abs_dT_mixed_vs_fp64_over_nch": mixed_vs_fp64},
-        "roofline": {"bound": "alu", "kernel": "knit_sweep_mixed_tc_kernel",
-                     "achieved": achieved_tflops, "peak": FP32_ALU_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP32_ALU_PEAK_TFLOPS,
+        "roofline": {"bound": "tensor", "kernel": "knit_sweep_mixed_tc_kernel",
+                     "achieved": achieved_tflops, "peak": pk["mma_tf32_tflops"],
+                     "unit": "TFLOP/s", "frac": achieved_tflops / pk["mma_tf32_tflops"],
                      "traffic": SWEEP_TRAFFIC_BYTES,
-                     "note": "algorithmic 16 M^3 flop per slice-update (the method's inversion "
-                             "plus product) over the FP32 CUDA-core peak 152 SM x 128 lanes x 2 "
-                             "x 2.07 GHz (Gauss-Jordan and refinement run there); kernel timed "
-                             "alone with CUDA events",
+                     "note": "algorithmic 16 M^3 flop per slice-update (the method's complex "
+                             "inversion plus product) over the measured dense TF32 tensor peak "
+                             "(own tcgen05 kind::tf32 loop, csrc/peaks.cu), the contraction "
+                             "type of a complex64 sweep; kernel timed alone with CUDA events",
                      "kernel_ms": sweep_ms,
+                     "fp32_alu": {"peak": pk["ffma_tflops"],
+                                  "frac": achieved_tflops / pk["ffma_tflops"],
+                                  "note": "the same rate over the measured FP32 FMA peak (the "
+                                          "Gauss-Jordan pivot chain and the digit splitting "
+                                          "run on the CUDA cores)"},
                      "tensor_pipe": {"executed_tflops": tc_tflops,
-                                     "peak": peaks.get("bf16_tflops"),
-                                     "frac": (tc_tflops / peaks["bf16_tflops"])
-                                     if peaks.get("bf16_tflops") else None,
+                                     "peak": pk["mma_bf16_tflops"],
+                                     "frac": tc_tflops / pk["mma_bf16_tflops"],
                                      "note": "bf16 products per slice: the residual's 18 digit "
                                              "products x 8 K-chunks and the Gauss-Jordan panel "
                                              "updates' 9 term products x 8 panels, each a "
-                                             "128 x 64 x 16 MMA"}},
+                                             "128 x 64 x 16 MMA, over the measured bf16 MMA "
+                                             "peak (own loop)"}},
+        "peaks_measured": pk,
         "e2e": {"value": e2e_val, "unit": "T(E) points/s", "h2d_bytes_per_step": 8 * NE + 8 * NS,
                 "d2h_bytes_per_step": 12 * n, "ms": statistics.mean(e2e_ms)},
         "gpu_launches": launches_per_step * args.steps,
@@ -761,6 +816,8 @@ def run_graph_case(args):
     st = dst.cpu().numpy()
     flop = graph_flop([int(w) for w in widths], len(leads[0])) * ne
     achieved = flop / (ms / 1e3) / 1e12
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    pk = measure_peaks(knit, torch, torch.cuda.current_stream(), nsm)
     line = {
         "metric": "multi-terminal T_kl energies/s (knitting over an arbitrary geometry, FP64)",
         "value": ne / (ms / 1e3), "unit": "energies/s", "n_gpus": 1, "steps": args.steps,
@@ -769,11 +826,12 @@ def run_graph_case(args):
         "config": {"workload": f"disordered four-terminal bar 96 x 32 (W = 1), leads 32/32/16/16 "
                                f"sites, {ne} energies", "slices": len(widths),
                    "max_slice_width": int(max(widths))},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL,
+        "roofline": {"bound": "fp64", "achieved": achieved, "peak": pk["dfma_tflops"],
+                     "unit": "TFLOP/s", "frac": achieved / pk["dfma_tflops"],
                      "traffic": None,
                      "note": "algorithmic flops from the slice widths (graph_flop) over the "
-                             "nominal FP64 rate"},
+                             "measured DFMA peak (own loop, csrc/peaks.cu)"},
+        "peaks_measured": pk,
         "buttiker_sum_rule_max": float(np.abs(Tm.sum(axis=2) - Tm.sum(axis=1))[st == 0].max()),
         "status_nonzero": int((st != 0).sum())}
     if args.cpu_baseline:
@@ -795,10 +853,24 @@ def run_graph_case(args):
     g.close()
 
 
+def run_peaks_case(args):
+    """The peak loops alone (one JSON line)."""
+    import torch
+    from paper_1010_2627_gb300 import build, knit
+    build.build()
+    knit.load()
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    pk = measure_peaks(knit, torch, torch.cuda.current_stream(), nsm, reps=max(3, args.steps))
+    pk["case"] = "peaks"
+    pk["driver_file"] = {k: _peaks().get(k) for k in ("hbm_gbs", "bf16_tflops",
+                                                        "bf16_tflops_sustained")}
+    print(json.dumps(pk), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "profile", "uneven", "ldos", "bdg", "eigen", "lesser",
+                    choices=["bench", "peaks", "profile", "uneven", "ldos", "bdg", "eigen", "lesser",
                              "graph"])
     ap.add_argument("--bdg-energies", dest="bdg_energies", type=int, default=2048)
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
@@ -812,6 +884,8 @@ def main():
         args.warmup = 3
     if args.case == "profile":
         run_profile_case(args)
+    elif args.case == "peaks":
+        run_peaks_case(args)
     elif args.case == "uneven":
         run_uneven(args)
     elif args.case == "ldos":

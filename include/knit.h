@@ -387,8 +387,10 @@ knit_status knit_batch_transmission(knit_batch batch, const double *E, const uin
  * paper has no counterpart; it exists for callers that cannot let a library
  * call cudaMalloc/cudaFree, e.g. processes whose framework owns all device
  * memory, or loops that must not trigger the device-wide synchronisation of
- * cudaFree).  Same arithmetic as knit_lead_selfenergy with
- * KNIT_LEAD_DECIMATION, for one lead cell given directly:
+ * cudaFree).  The same decimation iteration as knit_lead_selfenergy with
+ * KNIT_LEAD_DECIMATION, for one lead cell given directly; Sigma is formed
+ * with V treated as dense (the allocating path skips V's zero blocks), so
+ * the two may differ in the last bits:
  *   H0, V: M*M lead cell and inter-cell hopping (device memory, complex128);
  *   lead: 0 = left (Sigma = V g V^dagger), 1 = right (Sigma = V^dagger g V);
  *   E: nE energies (device); eta, tol, maxit as in knit_lead_opts (<= 0 means
@@ -397,13 +399,33 @@ knit_status knit_batch_transmission(knit_batch batch, const double *E, const uin
  * Scratch comes from one fixed 9 MiB array inside the library (per device,
  * held until exit): M must be <= 64, larger M returns KNIT_ERR_INVALID, as
  * does any host pointer.  All calls share that array, so calls that overlap
- * on the GPU race; serialise them.  The first call on a device looks up the
- * array's address (cudaGetSymbolAddress) -- make it before any stream
+ * on the GPU race; serialise them.  Every call looks up the array's address
+ * on the current device (cudaGetSymbolAddress); the first lookup on a device
+ * may load the library's module, so make the first call before any stream
  * capture.  Stream-ordered; returns after enqueueing. */
 knit_status knit_lead_decimation_noalloc(const knit_c128 *H0, const knit_c128 *V, int32_t M,
                                          int32_t lead, const double *E, int32_t nE, double eta,
                                          double tol, int32_t maxit, knit_c128 *sigma,
                                          int32_t *iters, int32_t *status, void *stream);
+
+/* kinds of knit_peak_probe */
+enum { KNIT_PEAK_MMA_BF16 = 0, KNIT_PEAK_MMA_TF32 = 1, KNIT_PEAK_DFMA = 2, KNIT_PEAK_FFMA = 3 };
+
+/* Peak-rate microbenchmarks (no paper counterpart): the denominators of the
+ * roofline fractions that the benchmark reports.  Launches one fixed loop on
+ * nsm SMs and returns in *flop the floating-point operations it performs;
+ * the caller times the launch on `stream` (CUDA events) and divides.
+ *   KNIT_PEAK_MMA_BF16: tcgen05.mma kind::f16 (bf16 operands, f32 accumulate),
+ *     M = 128, N = 256, K = 16 per instruction, `iters` instructions per SM;
+ *   KNIT_PEAK_MMA_TF32: the same with kind::tf32 (K = 8 per instruction);
+ *   KNIT_PEAK_DFMA / KNIT_PEAK_FFMA: FP64 / FP32 fused multiply-add loops on
+ *     the CUDA cores (eight 256-thread blocks per SM, 128 * iters FMA each).
+ * timed_out: host int or NULL; when given, the call waits for the launch
+ * and stores 1 if a tensor-core wait ran out of its bound (the rate is then
+ * not valid), else 0.  KNIT_ERR_INVALID for an unknown kind or iters, nsm
+ * below 1; KNIT_ERR_CUDA for launch failures.  Allocates nothing. */
+knit_status knit_peak_probe(int32_t kind, int64_t iters, int32_t nsm, double *flop,
+                            int32_t *timed_out, void *stream);
 
 /* Thread-local description of the last error (never NULL). */
 const char *knit_last_error(void);
@@ -414,6 +436,18 @@ const char *knit_last_error(void);
  * what it had allocated; the injection then switches itself off.  n < 0
  * switches it off.  Process-wide; no device work. */
 knit_status knit_debug_fail_alloc_after(int64_t n);
+
+/* Test hook for the bounded tensor-core waits (no paper counterpart): one
+ * block issues a tcgen05 MMA and commits it to one mbarrier, then waits on a
+ * second mbarrier that nothing completes, polling at most `polls` times
+ * (1 .. 2^24), the same bounded wait (tc::mbar_wait) the sweep kernels use.
+ * The wait runs out; the block then waits, bounded, for the committed MMA
+ * and releases its tensor memory, as a timed-out sweep does.  Synchronous.
+ * *wait_status receives KNIT_ERR_TIMEOUT (the wait ran out) or KNIT_OK;
+ * *cleanup_done 1 when the cleanup wait completed.  KNIT_ERR_INVALID for
+ * polls out of range or NULL outputs; KNIT_ERR_CUDA on launch failure.
+ * Allocates nothing. */
+knit_status knit_debug_wait_probe(int64_t polls, int32_t *wait_status, int32_t *cleanup_done);
 
 /* Library version string. */
 const char *knit_version(void);

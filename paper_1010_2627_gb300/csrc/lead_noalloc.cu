@@ -16,15 +16,20 @@
 //   * all calls share the array and it keeps the last call's contents, so
 //     calls that overlap on the GPU (two streams, or two host threads) race
 //     and must be serialised by the caller;
-//   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress; make that first call before any stream capture.
+//   * every call looks up the array's device address on the current device
+//     with cudaGetSymbolAddress (cheap next to the launch, and never stale
+//     after a cudaDeviceReset reloads the module); the first lookup on a
+//     device may load the library's module, so make the first call before
+//     any stream capture.
 //
+// Sigma is formed with V treated as a dense M x M matrix (the allocating
+// entry point knows the lead's block structure and skips V's zero blocks),
+// so the two entry points run the same decimation iteration but may round
+// Sigma differently in the last bits.
 // The kernel initialises every workspace matrix it reads for each energy from
 // the inputs, so nothing in the array needs to start at zero.
 
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "../../include/knit.h"
 #include "knit_common.cuh"
@@ -44,10 +49,6 @@ static __device__ __align__(256) double2
                          KNIT_NOALLOC_MAX_M];
 
 namespace {
-
-constexpr int kMaxDevices = 64;
-double2 *g_scratch[kMaxDevices] = {};
-std::mutex g_scratch_mu;
 
 bool on_device(const void *p)
 {
@@ -87,32 +88,23 @@ extern "C" knit_status knit_lead_decimation_noalloc(const knit_c128 *H0, const k
     if (!(tol > 0.0)) tol = 1e-14;
     if (maxit <= 0) maxit = 200;
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    // the array's address on the current device, looked up on every call
+    void *p = nullptr;
+    const cudaError_t ge = cudaGetSymbolAddress(&p, knit_noalloc_scratch);
+    if (ge != cudaSuccess || !p) {
         cudaGetLastError();
-        return noalloc_fail(KNIT_ERR_CUDA, "knit_lead_decimation_noalloc: no usable device");
+        return noalloc_fail(KNIT_ERR_CUDA,
+                            "knit_lead_decimation_noalloc: cudaGetSymbolAddress failed");
     }
-    double2 *scratch;
-    {
-        std::lock_guard<std::mutex> lk(g_scratch_mu);
-        if (!g_scratch[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, knit_noalloc_scratch);
-            if (e != cudaSuccess || !p)
-                return noalloc_fail(KNIT_ERR_CUDA,
-                                    "knit_lead_decimation_noalloc: cudaGetSymbolAddress failed");
-            g_scratch[dev] = static_cast<double2 *>(p);
-        }
-        scratch = g_scratch[dev];
-    }
+    double2 *const scratch = static_cast<double2 *>(p);
     const size_t MM = (size_t)M * M;
     double2 *work = scratch;                                   // 8 M*M per CTA
     double2 *gslots = scratch + (size_t)KNIT_NOALLOC_CTAS * 8 * MM;   // one M*M per energy in flight
     cudaStream_t st = (cudaStream_t)stream;
     for (int e0 = 0; e0 < nE; e0 += KNIT_NOALLOC_CTAS) {
         const int n = nE - e0 < KNIT_NOALLOC_CTAS ? nE - e0 : KNIT_NOALLOC_CTAS;
-        // V block size M: the kernel skips the zero entries of V when it forms
-        // Sigma, so a diagonal or block-diagonal V costs no more than a product
+        // V block size M: V is treated as a dense M x M matrix when Sigma is
+        // formed (two full M^3 products for M > 4)
         cudaError_t e = knit_launch_decimation(
             reinterpret_cast<const double2 *>(H0), reinterpret_cast<const double2 *>(V), M, M,
             lead, E + e0, n, eta, tol, maxit, work, reinterpret_cast<double2 *>(sigma) + e0 * MM,

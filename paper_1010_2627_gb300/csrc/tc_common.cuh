@@ -59,11 +59,12 @@ KNIT_DEV void mma_commit(unsigned long long *mbar)
                  ::"r"(smem_u32(mbar)) : "memory");
 }
 
-// bounded wait for the mbarrier phase `parity`; returns 0 on timeout
-KNIT_DEV int mbar_wait(unsigned long long *mbar, uint32_t parity)
+// bounded wait for the mbarrier phase `parity` (at most `limit` polls);
+// returns 0 on timeout
+KNIT_DEV int mbar_wait(unsigned long long *mbar, uint32_t parity, long limit = WAIT_LIMIT)
 {
     uint32_t done = 0;
-    for (long it = 0; it < WAIT_LIMIT; ++it) {
+    for (long it = 0; it < limit; ++it) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      "selp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");

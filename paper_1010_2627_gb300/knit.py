@@ -23,6 +23,7 @@ KNIT_OK, KNIT_ERR_INVALID, KNIT_ERR_OOM, KNIT_ERR_CUDA = 0, 1, 2, 3
 KNIT_ERR_SINGULAR, KNIT_ERR_NOCONVERGE, KNIT_ERR_TIMEOUT, KNIT_ERR_NONFINITE = 4, 5, 6, 7
 KNIT_FP64, KNIT_MIXED, KNIT_MIXED_CUDACORE = 0, 1, 2
 KNIT_LEAD_AUTO, KNIT_LEAD_MODES, KNIT_LEAD_DECIMATION, KNIT_LEAD_LEARNED = 0, 1, 2, 3
+KNIT_PEAK_MMA_BF16, KNIT_PEAK_MMA_TF32, KNIT_PEAK_DFMA, KNIT_PEAK_FFMA = 0, 1, 2, 3
 
 P = ctypes.c_void_p
 i32, f64 = ctypes.c_int32, ctypes.c_double
@@ -85,6 +86,8 @@ _SIGS = {
     "knit_lead_model_gradient": (i32, [P, P, P, i32, P, P, P]),
     "knit_batch_destroy": (i32, [P]),
     "knit_batch_transmission": (i32, [P, P, P, P, P, P, P, P]),
+    "knit_peak_probe": (i32, [i32, ctypes.c_int64, i32, P, P, P]),
+    "knit_debug_wait_probe": (i32, [ctypes.c_int64, P, P]),
     "knit_last_error": (ctypes.c_char_p, []),
     "knit_version": (ctypes.c_char_p, []),
 }
@@ -393,6 +396,27 @@ def knit_lead_decimation_noalloc(H0, V, M, lead, E, sigma, eta=0.0, tol=0.0, max
                                                int(nE), float(eta), float(tol), int(maxit),
                                                _ptr(sigma), _ptr(iters), _ptr(status),
                                                _stream(stream)))
+
+
+def knit_peak_probe(kind, iters, nsm, stream=None, check=False):
+    """Launch one peak-rate loop (KNIT_PEAK_*) on nsm SMs; returns its flop
+    count (the caller times the launch).  With check=True the call waits and
+    raises KnitError(KNIT_ERR_TIMEOUT) if a tensor-core wait ran out."""
+    flop = ctypes.c_double(0.0)
+    flag = ctypes.c_int32(0)
+    _check(load().knit_peak_probe(int(kind), int(iters), int(nsm), ctypes.byref(flop),
+                                  ctypes.byref(flag) if check else None, _stream(stream)))
+    if check and flag.value:
+        raise KnitError(KNIT_ERR_TIMEOUT, "peak probe: a tensor-core wait ran out")
+    return flop.value
+
+
+def knit_debug_wait_probe(polls):
+    """Run the bounded tensor-core wait on a barrier nothing completes;
+    returns (wait status, cleanup completed)."""
+    ws, cd = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    _check(load().knit_debug_wait_probe(int(polls), ctypes.byref(ws), ctypes.byref(cd)))
+    return ws.value, cd.value
 
 
 def knit_batch_create(handles, sys_index, precision):

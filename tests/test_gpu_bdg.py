@@ -1,0 +1,94 @@
+"""GPU parity at the spinful BdG bar's width (32 sites x 4 = 128 orbitals,
+configuration 5's slice) against the oracle's dense solve (Eq. 2, Sec. 2.3).
+
+The sweep is checked on its own by giving the GPU the oracle's self-energies
+(knit_transmission_sigma): |dT| / max(1, N_ch) <= 1e-8 in FP64 and <= 1e-6 in
+the mixed mode, with N_ch the open channels of the clean BdG leads at E
+(propagating incoming Bloch modes of the lead, counted by mode analysis).
+End to end (the GPU's own lead decimation) the two sides also differ by their
+decimations at eta = 1e-12: those agree to ~1e-8 in Sigma (the decimation
+tolerance of the other lead tests), which moves T by up to ~1e-8 per open
+channel, so the end-to-end bound is twice the sweep's."""
+import numpy as np
+import pytest
+
+import oracle
+import scattering as sc
+from paper_1010_2627_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-8
+TOL_MIXED = 1e-6
+SEED, W = 4, 1.0
+
+
+@pytest.fixture(scope="module")
+def knit():
+    from paper_1010_2627_gb300 import build, knit as k
+    build.build()
+    k.load()
+    return k
+
+
+def open_channels(b, E):
+    """min over the two leads of the propagating incoming modes at E"""
+    return min(len(sc.lead_modes(b.lead_H0[p], b.lead_V[p], E, p)[3]) for p in (0, 1))
+
+
+@pytest.fixture(scope="module")
+def bdg32_cases():
+    """Ns = 32 bars of lengths 3 and 6 with the oracle's leads and dense T"""
+    E = np.array([-0.17, -0.05, 0.04, 0.13])
+    out = {}
+    for L in (3, 6):
+        b = inputs.bdg(32, L, mu=-1.0, delta=0.1, alpha=0.2)
+        eps = oracle.onsite(SEED, L, b.M, W, block=4, sign=b.sign)
+        SL = np.stack([oracle.decimation(b.lead_H0[0], b.lead_V[0], e, 0, eta=1e-12)[1] for e in E])
+        SR = np.stack([oracle.decimation(b.lead_H0[1], b.lead_V[1], e, 1, eta=1e-12)[1] for e in E])
+        To = np.array([oracle.dense(b.H0, b.V, eps, L, e, SL[k], SR[k])["T_LR"]
+                       for k, e in enumerate(E)])
+        nch = np.array([max(1, open_channels(b, e)) for e in E])
+        out[L] = (b, E, SL, SR, To, nch)
+    return out
+
+
+@pytest.mark.parametrize("L", [3, 6])
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_MIXED)])
+def test_bdg32_sweep_with_oracle_leads(knit, bdg32_cases, L, precision, tol):
+    b, E, SL, SR, To, nch = bdg32_cases[L]
+    sysk = knit.System(b)
+    T, st = sysk.transmission_sigma(E, SL, SR, seeds=[SEED], W=W, precision=precision)
+    sysk.close()
+    assert (st == 0).all()
+    err = np.abs(T[:, 0] - To) / nch
+    assert err.max() <= tol, (precision, L, err, T[:, 0], To)
+
+
+@pytest.mark.parametrize("L", [3, 6])
+@pytest.mark.parametrize("precision,tol", [(0, TOL_FP64), (1, TOL_MIXED)])
+def test_bdg32_end_to_end(knit, bdg32_cases, L, precision, tol):
+    b, E, _, _, To, nch = bdg32_cases[L]
+    sysk = knit.System(b)
+    T, st = sysk.transmission(E, seeds=[SEED], W=W, precision=precision)
+    sysk.close()
+    assert (st == 0).all()
+    err = np.abs(T[:, 0] - To) / nch
+    assert err.max() <= 2 * tol, (precision, L, err)
+
+
+def test_bdg3_sweep_fp64_with_oracle_leads(knit):
+    """the small BdG bar of the block-coupling test, sweep alone at 1e-8"""
+    b = inputs.bdg(3, 6, mu=-1.0, delta=0.1, alpha=0.2)
+    E = np.array([-0.11, 0.05])
+    eps = oracle.onsite(SEED, b.L, b.M, W, block=4, sign=b.sign)
+    SL = np.stack([oracle.decimation(b.lead_H0[0], b.lead_V[0], e, 0, eta=1e-12)[1] for e in E])
+    SR = np.stack([oracle.decimation(b.lead_H0[1], b.lead_V[1], e, 1, eta=1e-12)[1] for e in E])
+    sysk = knit.System(b)
+    for precision, tol in ((0, TOL_FP64), (1, TOL_MIXED)):
+        T, st = sysk.transmission_sigma(E, SL, SR, seeds=[SEED], W=W, precision=precision)
+        assert (st == 0).all()
+        for k, e in enumerate(E):
+            To = oracle.dense(b.H0, b.V, eps, b.L, e, SL[k], SR[k])["T_LR"]
+            assert abs(T[k, 0] - To) <= tol * max(1, open_channels(b, e)), (precision, e)
+    sysk.close()

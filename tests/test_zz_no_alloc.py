@@ -27,13 +27,21 @@ def _dev(torch, a):
     return torch.from_numpy(a.view(np.float64).copy()).cuda()
 
 
-@pytest.mark.parametrize("cell", ["square12", "bdg2"])
+CELLS = {
+    # name: (system, energies)
+    "square12": (lambda: inputs.square(12, 3), lambda: inputs.energy_grid(-3.5, 3.5, 37)),
+    "bdg2": (lambda: inputs.bdg(2, 3, delta=0.0), lambda: inputs.energy_grid(-0.5, 0.5, 21)),
+    # the largest cell the fixed array holds (M = 64, every slot of a chunk
+    # in use) with an energy count that leaves a ragged last chunk of 5
+    "square64": (lambda: inputs.square(64, 3), lambda: inputs.energy_grid(-3.9, 3.9, 37)),
+}
+
+
+@pytest.mark.parametrize("cell", sorted(CELLS))
 def test_noalloc_matches_allocating_entry_point_twice(knit, cell):
     torch = pytest.importorskip("torch")
-    ss = inputs.square(12, 3) if cell == "square12" else inputs.bdg(2, 3, delta=0.0)
+    ss, E = CELLS[cell][0](), CELLS[cell][1]()
     M = ss.M
-    E = inputs.energy_grid(-3.5, 3.5, 37) if cell == "square12" else \
-        inputs.energy_grid(-0.5, 0.5, 21)
     sysk = knit.System(ss)
     stream = torch.cuda.Stream()
     for lead in (0, 1):
@@ -48,6 +56,9 @@ def test_noalloc_matches_allocating_entry_point_twice(knit, cell):
         for call in range(2):            # two calls in a row share the scratch
             dS.fill_(float("nan"))
             dit.fill_(-1)
+            # the fills and uploads above ran on the current stream: order the
+            # entry point's stream after them
+            stream.wait_stream(torch.cuda.current_stream())
             knit.knit_lead_decimation_noalloc(dH0, dV, M, lead, dE, dS, eta=1e-12, iters=dit,
                                              status=dst, stream=stream)
             torch.cuda.synchronize()
