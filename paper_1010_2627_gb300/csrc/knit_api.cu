@@ -36,6 +36,8 @@ extern "C" cudaError_t knit_launch_ldos_mixed(const InstDev *, int, int, int, in
                                               long long, cudaStream_t);
 extern "C" size_t knit_mixed_wide_work_bytes(int);
 extern "C" cudaError_t knit_launch_mixed_wide(const InstDev *, int, int, void *, cudaStream_t);
+extern "C" size_t knit_mixed_tc128_work_bytes(void);
+extern "C" cudaError_t knit_launch_mixed_tc128(const InstDev *, int, void *, cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
 extern "C" cudaError_t knit_launch_gamma_factor(const double2 *, int, int, double2 *, double2 *,
                                                 int *, cudaStream_t);
@@ -536,13 +538,18 @@ __global__ void combine_status(int *a, const int *b, int n)
 }
 
 // which sweep kernel serves a system at a given precision
-enum SweepKind { SWEEP_FP64 = 0, SWEEP_MIXED = 1, SWEEP_WIDE = 2 };
+enum SweepKind { SWEEP_FP64 = 0, SWEEP_MIXED = 1, SWEEP_WIDE = 2, SWEEP_TC128 = 3 };
 
+// KNIT_MIXED: widths <= 64 with diagonal couplings on sweep_mixed(_tc).cu,
+// everything else up to 128 (diagonal or 4 x 4 block couplings) on the
+// tensor-core kernel of sweep_mixed_tc128.cu; KNIT_MIXED_CUDACORE keeps the
+// CUDA-core residual kernels (sweep_mixed.cu, sweep_mixed_wide.cu)
 int sweep_kind(const knit_system_s *s, int precision)
 {
     if (precision == KNIT_FP64) return SWEEP_FP64;
     if (s->vb == 1 && s->M <= knit_mixed_max_M()) return SWEEP_MIXED;
-    if ((s->vb == 1 || s->vb == 4) && s->M <= 128) return SWEEP_WIDE;
+    if ((s->vb == 1 || s->vb == 4) && s->M <= 128)
+        return precision == KNIT_MIXED ? SWEEP_TC128 : SWEEP_WIDE;
     return SWEEP_FP64;
 }
 
@@ -561,6 +568,11 @@ knit_status run_sweep(knit_system s, InstDev in, int precision, cudaStream_t st)
     if (kind == SWEEP_WIDE) {
         CK(s->work.ensure(knit_mixed_wide_work_bytes(s->M) * grid), "wide sweep workspace");
         CK(knit_launch_mixed_wide(&in, s->M, grid, s->work.p, st), "wide mixed sweep launch");
+        return KNIT_OK;
+    }
+    if (kind == SWEEP_TC128) {
+        CK(s->work.ensure(knit_mixed_tc128_work_bytes() * grid), "tensor-core sweep workspace");
+        CK(knit_launch_mixed_tc128(&in, grid, s->work.p, st), "tensor-core wide sweep launch");
         return KNIT_OK;
     }
     const size_t MM = (size_t)s->M * s->M;
@@ -1557,11 +1569,12 @@ knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const in
         *use_tc = 0;
         if (k == SWEEP_FP64) { *cls = 0; return 0; }
         if (k == SWEEP_WIDE) { *cls = 5; return 2; }
+        if (k == SWEEP_TC128) { *cls = 6; return 3; }
         *use_tc = precision == KNIT_MIXED && s->M > 32;
         *cls = s->M <= 16 ? 1 : s->M <= 32 ? 2 : (*use_tc ? 3 : 4);
         return 1;
     };
-    std::vector<int> cls_bucket(6, -1);
+    std::vector<int> cls_bucket(7, -1);
     for (int p = 0; p < nInst; ++p) {
         knit_system s = b->sys[sys_of[p]];
         int use_tc, cls;
@@ -1620,6 +1633,7 @@ knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const in
         if (bk.kind == 0 && knit_fp64_smem_bytes(bk.Mmax, 1, 3) > 220 * 1024)
             work = std::max(work, sizeof(double2) * 3 * (size_t)bk.Mmax * bk.Mmax * b->nsm);
         if (bk.kind == 2) work = std::max(work, knit_mixed_wide_work_bytes(bk.Mmax) * b->nsm);
+        if (bk.kind == 3) work = std::max(work, knit_mixed_tc128_work_bytes() * b->nsm);
     }
     if (work && (e = b->work.ensure(work)) != cudaSuccess) {
         batch_release(b);
@@ -1713,6 +1727,8 @@ knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_
             CK(knit_launch_mixed_impl(&in, bk.Mmax, grid, bk.use_tc, st), "mixed sweep launch");
         } else if (bk.kind == 2) {
             CK(knit_launch_mixed_wide(&in, bk.Mmax, grid, b->work.p, st), "wide mixed sweep launch");
+        } else if (bk.kind == 3) {
+            CK(knit_launch_mixed_tc128(&in, grid, b->work.p, st), "tensor-core wide sweep launch");
         } else {
             const int use_smem = knit_fp64_smem_bytes(bk.Mmax, 1, 3) <= 220 * 1024;
             CK(knit_launch_sweep_fp64(&in, bk.Mmax, grid, b->work.as<double2>(), use_smem, st),

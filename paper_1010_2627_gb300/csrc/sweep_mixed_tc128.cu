@@ -1,0 +1,1282 @@
+// sweep_mixed_tc128.cu -- the mixed-precision slice sweep for widths 65..128
+// (padded MP = 128) with all three matrix products on the tcgen05 tensor
+// cores: the Gauss-Jordan panel updates, the exact residual and the
+// refinement product.
+//
+// Same recursion and arithmetic as the other mixed sweeps (KNIT user guide
+// Sec. 5.3 D knitting in slice form, Eq. 2 by block elimination; complex64
+// inverse refined against a residual exact to ~2^-48, state g carried as
+// hi + lo, T from G_LL by the unitarity identity, sweep_mixed.cu).  Per
+// slice n, one CTA of 512 threads per instance:
+//
+//  A. Gv' = V g V^dagger (or Sigma_L at n = 0) (+ Sigma_R at n = L - 1)
+//     + H0 - diag(E - onsite) in double-float, in place over the state in a
+//     per-CTA workspace (L2); A_n = -Gv'.  X = fl32(A_n) goes straight into
+//     tensor memory: lane i = row i, columns 2c, 2c + 1 = Re, Im of X[i][c]
+//     (256 of the 512 columns).
+//  B. Gauss-Jordan with implicit partial pivoting (the elimination of
+//     gj_lookahead, panels of 8 columns) on X in tensor memory.  Per panel:
+//     the four lane-quarter warps copy the panel columns out of tensor
+//     memory, warp 0 runs the 8 pivot steps on them (4 rows per lane), the
+//     pivot rows of X at the start of the panel are read back, one thread
+//     per column forms the panel's v vectors by forward substitution, and
+//     X -= U V is issued as tcgen05.mma with D = X itself: A = -[Re U | Im U]
+//     (128 x 16), B^T row 2j + r = the real form of column j of V, each
+//     operand cut exactly into three bf16 terms, the six products of term
+//     order <= 2 accumulated in f32 -- an fp32-quality update with no read
+//     back.  The next panel's 16 columns go first in an N = 16 MMA of their
+//     own, so its pivot chain starts while the rest of the update runs.
+//  C. The permuted inverse is copied from tensor memory into shared memory
+//     in its true order (A^-1[pos[i]][perm[c]] = X[i][c]) and rounded per
+//     column j to X' = 2^(t_j - 8) (d0 + d1 2^-8 + d2 2^-16), |d| <= 128,
+//     t_j one more than the exponent of the column's largest entry.
+//  D. R = I + Gv' X' exact: transposed, R^T = I + X'^T Gv'^T, so that the
+//     tensor-memory lanes are the columns j of R: A = the three X' digits
+//     (128 x 256 in real form), B = the seven digits of 32 rows of Gv' per
+//     pass (cut at the row scale s_i + 1), products (p, q) of one
+//     anti-diagonal d = p + q in accumulator d (seven exact f32
+//     accumulators of 64 columns, 448 columns), four passes over the rows
+//     of Gv'.  With every digit at most 128 in magnitude each accumulator
+//     sums at most 3 x 2^14 x 256 < 2^24 per K of 256: exact by
+//     construction.  The accumulators are summed (3..6 in fp32, then with
+//     0..2 in double-float), scaled, the identity added and R rounded once.
+//  E. Neumann terms where max|R_ij| asks for them, an error-free product
+//     where max|R_ij| > 1e-4, and an FP64 inversion of the slice where the
+//     series cannot converge (CUDA cores, rare; mixed_common.cuh).
+//  F. g = X' + X' S: A = X' digits (rows i), B = the three bf16 terms of
+//     S scaled by 2^(t_k - 8) (exact powers of two), the six products of
+//     term order <= 2 into one f32 accumulator (256 columns), read back as
+//     g = X' + D with two_sum into the hi + lo state.
+//
+// Operand tiles use the no-swizzle K-major layout of tc_common.cuh.  Every
+// wait on the tensor cores is bounded (ST_TIMEOUT), and the tensor memory is
+// released after a second bounded wait for the last commit.
+
+#include <cuda_bf16.h>
+
+#include "gj_tc.cuh"
+#include "mixed_common.cuh"
+#include "tc_common.cuh"
+
+using namespace mixed;
+using namespace tc;
+
+namespace {
+
+constexpr int MP = 128;                // padded width
+constexpr int NTH = 512;               // 16 warps
+constexpr int XST = MP + 1;            // row stride (float2) of X' in shared memory
+constexpr int PST = 9;                 // row stride (float2) of the panel and U buffers
+constexpr int NB = 8;                  // Gauss-Jordan panel width
+constexpr int NDG = 7;                 // digits of Gv'
+constexpr int NDX = 3;                 // digits of X'
+constexpr int BT_RES = 64 * 32;        // bytes of one 64-row x 16 bf16 tile
+constexpr int BT_256 = 256 * 32;       // bytes of one 256-row x 16 bf16 tile
+constexpr uint32_t TMEM_COLS = 512;
+
+// the six bf16 term products (p, q) with p + q <= 2, smallest first
+__constant__ int kProdP[6] = {2, 1, 0, 1, 0, 0};
+__constant__ int kProdQ[6] = {0, 1, 2, 0, 1, 0};
+
+struct Tc128Smem {
+    union {
+        struct {                                       // Gauss-Jordan
+            float2 pan[MP * PST];                      // panel columns (relay out of TMEM)
+            float2 U[MP * PST];                        // u vectors of the panel
+            float2 prow[NB * MP];                      // pivot rows at the start of the panel
+            alignas(128) unsigned char adg[3 * A_TILE];    // -[Re U | Im U] terms, 128 x 16
+            alignas(128) unsigned char bdg[3 * BT_256];    // V terms in real form, 256 x 16
+        } gj;
+        struct {
+            float2 X[MP * XST];                        // X' in true order
+            union {
+                struct {
+                    alignas(128) unsigned char a[2][NDX * A_TILE];   // X'^T digits of a K-chunk
+                    alignas(128) unsigned char b[2][NDG * BT_RES];   // Gv' digits of a K-chunk
+                } res;
+                struct {
+                    alignas(128) unsigned char a[2][NDX * A_TILE];   // X' digits of a K-chunk
+                    alignas(128) unsigned char b[2][3 * BT_256];     // S terms of a K-chunk
+                } ref;
+            } t;
+        } mm;
+    } u;
+    double eps[MP];
+    float2 vh[2][MP];
+    float2 vl[2][MP];
+    int vuni[2];
+    float vch[2], vcl[2];
+    int rexp[MP];                  // Gv' row exponents
+    int cexp[MP];                  // X column exponents
+    float rmx[4][MP];              // partial row maxima of Gv'
+    float cmx[4][MP];              // partial column maxima of X
+    int perm[MP];
+    int pos[MP];
+    float2 rinv[NB];
+    int flag;
+    double red[NTH / 32];
+    unsigned redu[NTH / 32];
+    unsigned long long bar[4];     // 0: next-panel MMAs, 1: rest of the panel update, 2-3: chunk slots
+    uint32_t tmem;
+    int inst;
+    int cur_sys;
+};
+
+// per-CTA device workspace
+struct Tc128Work;
+static_assert((2 * MP + 1) * 16 + (MP + 2) * 4 <= (2 * MP + 48) * 16, "fallback scratch");
+
+struct Tc128Work {
+    float4 Gh[(MP / 2) * MP];      // state g / Gv' (hi): column pair jp, row i at jp * MP + i
+    float4 Gl[(MP / 2) * MP];      // (lo)
+    float2 R[MP * MP];             // residual, row-pair layout (sidx)
+    float2 S1[MP * MP];            // Neumann terms (two buffers in turn)
+    float2 S2[MP * MP];
+    double2 A64[MP * MP];          // FP64 fallback matrix; G_LL for the trace
+    double2 scr[2 * MP + 48];      // gj_invert64 scratch: (2M + 1) complex128 + (M + 2) ints
+};
+
+// float2 index of element (k, j) in the row-pair layout of R and S: rows k
+// and k + 1 (k even) of column j are adjacent
+KNIT_DEV int sidx(int k, int j) { return (((k >> 1) * MP + j) << 1) | (k & 1); }
+
+KNIT_DEV float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+KNIT_DEV int scale_exp(float mx)
+{
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    return e;
+}
+
+KNIT_DEV void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+                   "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                   "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+}
+
+KNIT_DEV void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+                   "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
+                   "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
+
+// three exact bf16 terms of 8 values, packed two per word (value 2c in the
+// low half), each term as two 16-byte halves of a 16-value tile row
+KNIT_DEV void split8(const float (&x)[8], uint4 &t0, uint4 &t1, uint4 &t2)
+{
+    uint32_t h[8], m[8], l[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) bf16_split3(x[c], h[c], m[c], l[c]);
+    t0 = make_uint4(pack_hi16(h[0], h[1]), pack_hi16(h[2], h[3]), pack_hi16(h[4], h[5]), pack_hi16(h[6], h[7]));
+    t1 = make_uint4(pack_hi16(m[0], m[1]), pack_hi16(m[2], m[3]), pack_hi16(m[4], m[5]), pack_hi16(m[6], m[7]));
+    t2 = make_uint4(pack_hi16(l[0], l[1]), pack_hi16(l[2], l[3]), pack_hi16(l[4], l[5]), pack_hi16(l[6], l[7]));
+}
+
+// write the three terms of 16 K-values of tile row r (row stride of the
+// term tiles: `stride` bytes)
+KNIT_DEV void put_terms16(unsigned char *tile, int stride, int r, const float (&lo)[8],
+                          const float (&hi)[8])
+{
+    uint4 a0, a1, a2, b0, b1, b2;
+    split8(lo, a0, a1, a2);
+    split8(hi, b0, b1, b2);
+    unsigned char *p = tile + tile_off(r, 0);
+    *reinterpret_cast<uint4 *>(p) = a0;
+    *reinterpret_cast<uint4 *>(p + 128) = b0;
+    *reinterpret_cast<uint4 *>(p + stride) = a1;
+    *reinterpret_cast<uint4 *>(p + stride + 128) = b1;
+    *reinterpret_cast<uint4 *>(p + 2 * stride) = a2;
+    *reinterpret_cast<uint4 *>(p + 2 * stride + 128) = b2;
+}
+
+// 2^-e x cut into 7 digits (double-float input), digit p pre-scaled by 2^-8p
+KNIT_DEV void digits7(float h, float l, float dn, float (&dg)[NDG])
+{
+    float ah = h * dn, al = l * dn;
+    float scale = 1.f;
+#pragma unroll
+    for (int p = 0; p < NDG; ++p) {
+        float th = ah * 256.f, tl = al * 256.f;
+        const float d = rintf(th);
+        th -= d;
+        two_sum(th, tl, ah, al);
+        dg[p] = d * scale;
+        scale *= 0.00390625f;
+    }
+}
+
+// X' digits (exact: X' is a 24-bit value at the column scale)
+KNIT_DEV void digits3(float x, float dn, float (&dg)[NDX])
+{
+    float a = x * dn;
+    float scale = 1.f;
+#pragma unroll
+    for (int q = 0; q < NDX; ++q) {
+        a *= 256.f;
+        const float d = rintf(a);
+        a -= d;
+        dg[q] = d * scale;
+        scale *= 0.00390625f;
+    }
+}
+
+// Commits in flight and the phase each barrier waits for next, kept
+// identically by every thread (all control flow around them is uniform).
+struct Bars {
+    uint32_t ph[4];
+    uint32_t pend[4];
+};
+
+// thread 0 waits (bounded) for barrier b; every thread learns the outcome.
+// On success the phase flips; after a time-out it stays, so that the
+// cleanup can wait once more for the commit still in flight.
+__device__ __forceinline__ bool bar_wait(Tc128Smem &sm, Bars &br, int b)
+{
+    const int ok = threadIdx.x == 0 ? mbar_wait(&sm.bar[b], br.ph[b]) : 1;
+    if (__syncthreads_or(!ok)) return false;
+    br.ph[b] ^= 1u;
+    br.pend[b] = 0u;
+    return true;
+}
+
+__global__ void fill_status128(int *st, int n, int v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) st[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// A. Gv' in place over the state, X = -Gv'_hi into tensor memory
+
+// V entry (r, c) of parity q as double-float (conjugated when conj is set)
+KNIT_DEV void v_df(const double2 *Vq, int M, int r, int c, bool conj, float2 &h, float2 &l)
+{
+    const double2 v = (r < M && c < M) ? Vq[(size_t)r * M + c] : make_double2(0.0, 0.0);
+    to_df(v.x, h.x, l.x);
+    to_df(conj ? -v.y : v.y, h.y, l.y);
+}
+
+// V g V^dagger for 4 x 4 block-diagonal V, in place: work item (block B, C;
+// column half hc) forms columns 4C + 2hc, 4C + 2hc + 1 of the block
+__device__ void gv_blocks4(Tc128Work &wk, const SysDev &s, int M, int q)
+{
+    const size_t MM = (size_t)M * M;
+    const double2 *Vq = s.V + (size_t)(q % s.Vperiod) * MM;
+    const int nb = (M + 3) / 4;
+    // all reads of the state happen before any write (the two column halves
+    // of a block read the whole block)
+    float4 outh[4][2], outl[4][2];   // [item][row a] as float4 = 2 complex columns
+    int idxs[4];
+    int nitem = 0;
+    for (int e = threadIdx.x; e < 2 * nb * nb; e += NTH, ++nitem) {
+        const int hc = e & 1, B = (e >> 1) % nb, C = (e >> 1) / nb;
+        // u[a][s] = sum_b g[a][b] conj(V[4C+s][4C+b]) for s = 2hc, 2hc + 1
+        float2 uh[4][2], ul[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float2 gh[4], gl[4];
+#pragma unroll
+            for (int cp = 0; cp < 2; ++cp) {
+                const int idx = (2 * C + cp) * MP + 4 * B + a;
+                const float4 h = wk.Gh[idx], l = wk.Gl[idx];
+                gh[2 * cp] = make_float2(h.x, h.y);
+                gh[2 * cp + 1] = make_float2(h.z, h.w);
+                gl[2 * cp] = make_float2(l.x, l.y);
+                gl[2 * cp + 1] = make_float2(l.z, l.w);
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    float2 vh, vl;
+                    v_df(Vq, M, 4 * C + 2 * hc + s2, 4 * C + b, true, vh, vl);
+                    if (vh.x == 0.f && vh.y == 0.f) continue;
+                    float2 ph, pl;
+                    cdf_mul(gh[b], gl[b], vh, vl, ph, pl);
+                    cdf_add(sh, sl, ph, pl);
+                }
+                uh[a][s2] = sh;
+                ul[a][s2] = sl;
+            }
+        }
+        // Gv[a][s] = sum_b V[4B+a][4B+b] u[b][s]
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float2 oh[2], ol[2];
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    float2 vh, vl;
+                    v_df(Vq, M, 4 * B + a, 4 * B + b, false, vh, vl);
+                    if (vh.x == 0.f && vh.y == 0.f) continue;
+                    float2 ph, pl;
+                    cdf_mul(vh, vl, uh[b][s2], ul[b][s2], ph, pl);
+                    cdf_add(sh, sl, ph, pl);
+                }
+                oh[s2] = sh;
+                ol[s2] = sl;
+            }
+            if (nitem < 4) {
+                outh[nitem][a] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
+                outl[nitem][a] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
+            }
+        }
+        if (nitem < 4) idxs[nitem] = (2 * C + hc) * MP + 4 * B;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < nitem)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                wk.Gh[idxs[k] + a] = outh[k][a];
+                wk.Gl[idxs[k] + a] = outl[k][a];
+            }
+}
+
+// Gv (V g V^dagger or Sigma_L) + Sigma_R, elementwise, in place; zero in the
+// padding.  vmode: 0 general diagonal V, 1 V g V^dagger already formed or
+// |v|^2 = 1, 2 scalar |v|^2 (vch + vcl)
+__device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, int M, int n, int L, int vmode,
+                               const double2 *SL, const double2 *SR)
+{
+    const int q = n & 1;
+    for (int e = threadIdx.x; e < (MP / 2) * MP; e += NTH) {
+        const int i = e % MP, jp = e / MP;
+        const float4 h4 = wk.Gh[e], l4 = wk.Gl[e];
+        float2 oh[2], ol[2];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int j = 2 * jp + s2;
+            float2 gh = s2 ? make_float2(h4.z, h4.w) : make_float2(h4.x, h4.y);
+            float2 gl = s2 ? make_float2(l4.z, l4.w) : make_float2(l4.x, l4.y);
+            if (i < M && j < M) {
+                if (n == 0) {
+                    const double2 v = SL[(size_t)i * M + j];
+                    float a, b, c, d;
+                    to_df(v.x, a, b);
+                    to_df(v.y, c, d);
+                    gh = make_float2(a, c);
+                    gl = make_float2(b, d);
+                } else if (vmode == 2) {
+                    cdf_mul(gh, gl, make_float2(sm.vch[q], 0.f), make_float2(sm.vcl[q], 0.f), gh, gl);
+                } else if (vmode == 0) {
+                    float2 th, tl, vjh = sm.vh[q][j], vjl = sm.vl[q][j];
+                    vjh.y = -vjh.y;
+                    vjl.y = -vjl.y;
+                    cdf_mul(gh, gl, vjh, vjl, th, tl);
+                    cdf_mul(sm.vh[q][i], sm.vl[q][i], th, tl, gh, gl);
+                }
+                if (n == L - 1) {
+                    const double2 v = SR[(size_t)i * M + j];
+                    float a, b, c, d;
+                    to_df(v.x, a, b);
+                    to_df(v.y, c, d);
+                    cdf_add(gh, gl, make_float2(a, c), make_float2(b, d));
+                }
+            } else {
+                gh = gl = make_float2(0.f, 0.f);
+            }
+            oh[s2] = gh;
+            ol[s2] = gl;
+        }
+        wk.Gh[e] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
+        wk.Gl[e] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
+    }
+}
+
+// + H0 - diag(eps), one row per thread (sparse H0)
+__device__ void gv_add_h0(Tc128Work &wk, const Tc128Smem &sm, const SysDev &s, int M)
+{
+    float2 *const gh = reinterpret_cast<float2 *>(wk.Gh);
+    float2 *const gl = reinterpret_cast<float2 *>(wk.Gl);
+    for (int i = threadIdx.x; i < M; i += NTH) {
+        // float2 index of (i, j): ((j >> 1) * MP + i) * 2 + (j & 1)
+        {
+            const int f = ((i >> 1) * MP + i) * 2 + (i & 1);
+            float dh, dl;
+            to_df(sm.eps[i], dh, dl);
+            cdf_add(gh[f], gl[f], make_float2(-dh, 0.f), make_float2(-dl, 0.f));
+        }
+        for (int c = s.h0_rowptr[i]; c < s.h0_rowptr[i + 1]; ++c) {
+            const int j = s.h0_col[c];
+            const double2 hd = s.h0_val[c];
+            float2 hh, hl;
+            to_df(hd.x, hh.x, hl.x);
+            to_df(hd.y, hh.y, hl.y);
+            const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+            cdf_add(gh[f], gl[f], hh, hl);
+        }
+    }
+}
+
+// X = -Gv'_hi (identity in the padding) into tensor memory and the partial
+// row maxima of |Gv'|: warp w takes rows 32 (w & 3) + lane and complex
+// columns 32 (w >> 2) .. + 31
+__device__ void x_to_tmem(const Tc128Work &wk, Tc128Smem &sm, uint32_t tmem, int M)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
+    float mx = 0.f;
+#pragma unroll 1
+    for (int gi = 0; gi < 4; ++gi) {
+        uint32_t v[16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int jp = 16 * cg + 4 * gi + u;
+            const float4 h = wk.Gh[jp * MP + i];
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(h.x), fabsf(h.y)), fmaxf(fabsf(h.z), fabsf(h.w))));
+            const int j0 = 2 * jp;
+            float2 x0 = make_float2(-h.x, -h.y), x1 = make_float2(-h.z, -h.w);
+            if (i >= M || j0 >= M) x0 = make_float2(i == j0 ? 1.f : 0.f, 0.f);
+            if (i >= M || j0 + 1 >= M) x1 = make_float2(i == j0 + 1 ? 1.f : 0.f, 0.f);
+            v[4 * u] = __float_as_uint(x0.x);
+            v[4 * u + 1] = __float_as_uint(x0.y);
+            v[4 * u + 2] = __float_as_uint(x1.x);
+            v[4 * u + 3] = __float_as_uint(x1.y);
+        }
+        tmem_st16(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 16 * gi, v);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    sm.rmx[cg][i] = mx;
+}
+
+// ---------------------------------------------------------------------------
+// B. Gauss-Jordan on X in tensor memory
+
+__device__ int gj_tmem(Tc128Smem &sm, uint32_t tmem, int M, Bars &br)
+{
+    constexpr int R2 = MP / 32, IB = 7;
+    constexpr unsigned IMASK = (1u << IB) - 1u, FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Mp = (M + NB - 1) / NB * NB;   // columns that the updates touch
+    const int NP = Mp / NB;
+    bool open[R2];
+#pragma unroll
+    for (int t = 0; t < R2; ++t) open[t] = lane + 32 * t < M;
+    int st = ST_OK;
+    for (int P = 0; P < NP; ++P) {
+        const int K = P * NB, nk = min(NB, M - K);
+        // 1. the panel columns out of tensor memory (after the previous
+        //    panel's first MMAs), relayed through shared memory to warp 0
+        bool to0 = false;   // the wait for the previous panel's first MMAs ran out
+        if (warp < 4) {
+            if (P > 0) to0 = !mbar_wait(&sm.bar[0], br.ph[0]);
+            fence_after();
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 2 * K, v);
+            wait_ld();
+            const int i = 32 * warp + lane;
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                sm.u.gj.pan[i * PST + c] = make_float2(__uint_as_float(v[2 * c]), __uint_as_float(v[2 * c + 1]));
+            fence_before();
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+        }
+        // 2. the pivot steps (warp 0)
+        if (warp == 0) {
+            float2 pc[R2][NB];
+#pragma unroll
+            for (int t = 0; t < R2; ++t)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) pc[t][c] = sm.u.gj.pan[(lane + 32 * t) * PST + c];
+            bool bad = to0;
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk) {
+                if (kk < nk) {
+                    unsigned key = 0u;
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        const unsigned kt = (__float_as_uint(cabs1f(pc[t][kk])) & ~IMASK) |
+                                            (IMASK - (unsigned)(lane + 32 * t));
+                        key = max(key, open[t] ? kt : 0u);
+                    }
+                    key = __reduce_max_sync(FULL, key);
+                    bad |= (key & ~IMASK) == 0u;
+                    const int p = (int)(IMASK - (key & IMASK)), pl = p & 31, pt = p >> 5;
+                    // the pivot row's remaining panel entries, from lane p % 32
+                    float2 prow[NB];
+#pragma unroll
+                    for (int c = kk; c < NB; ++c) {
+                        float2 own = pc[0][c];
+#pragma unroll
+                        for (int t = 1; t < R2; ++t) own = t == pt ? pc[t][c] : own;
+                        prow[c] = make_float2(__shfl_sync(FULL, own.x, pl), __shfl_sync(FULL, own.y, pl));
+                    }
+                    const float2 rinv = crcp_fastf(prow[kk]);
+                    float2 u[R2];
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        u[t] = pc[t][kk];
+                        u[t].x -= lane + 32 * t == p ? 1.f : 0.f;
+                    }
+#pragma unroll
+                    for (int c = kk + 1; c < NB; ++c) {
+                        const float2 vk = cmulf(prow[c], rinv);
+#pragma unroll
+                        for (int t = 0; t < R2; ++t) pc[t][c] = cfmsf(u[t], vk, pc[t][c]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        const int i = lane + 32 * t;
+                        sm.u.gj.U[i * PST + kk] = u[t];
+                        open[t] = open[t] && i != p;
+                    }
+                    if (lane == 0) {
+                        sm.perm[K + kk] = p;
+                        sm.rinv[kk] = rinv;
+                    }
+                }
+            }
+            // steps a partial panel does not take contribute nothing
+            for (int kk = nk; kk < NB; ++kk)
+#pragma unroll
+                for (int t = 0; t < R2; ++t) sm.u.gj.U[(lane + 32 * t) * PST + kk] = make_float2(0.f, 0.f);
+            if (lane == 0) sm.flag = bad ? 1 : 0;
+        }
+        // 3. X at the start of the panel (the whole previous update done):
+        //    the pivot rows into shared memory
+        {
+            const int ok = (P > 0 && tid == 0) ? mbar_wait(&sm.bar[1], br.ph[1]) : 1;
+            if (__syncthreads_or(!ok || to0)) {
+                st = ST_TIMEOUT;
+                break;
+            }
+            if (P > 0) {
+                br.ph[0] ^= 1u;
+                br.ph[1] ^= 1u;
+                br.pend[0] = br.pend[1] = 0u;
+            }
+        }
+        if (sm.flag) {
+            st = ST_SINGULAR;
+            break;
+        }
+        fence_after();
+        {
+            const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
+            int kpiv = -1;
+            for (int kk = 0; kk < nk; ++kk) kpiv = sm.perm[K + kk] == i ? kk : kpiv;
+            if (__any_sync(FULL, kpiv >= 0)) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
+                    wait_ld();
+                    if (kpiv >= 0)
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            sm.u.gj.prow[kpiv * MP + 32 * cg + 16 * h + c] =
+                                make_float2(__uint_as_float(v[2 * c]), __uint_as_float(v[2 * c + 1]));
+                }
+            }
+        }
+        fence_before();
+        __syncthreads();
+        // 4. v vectors (one thread per column j) and the operand terms:
+        //    B^T rows 2j = [Re v_k[j] | -Im v_k[j]], 2j + 1 = [Im v_k[j] | Re v_k[j]];
+        //    A rows i = -[Re u_k[i] | Im u_k[i]]
+        if (tid < MP) {
+            const int j = tid;
+            float2 vj[NB];
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk) {
+                vj[kk] = make_float2(0.f, 0.f);
+                if (kk < nk) {
+                    const int p = sm.perm[K + kk];
+                    float2 r = sm.u.gj.prow[kk * MP + j];
+                    if (j == K + kk) r.x += 1.f;
+#pragma unroll
+                    for (int c = 0; c < kk; ++c) r = cfmsf(sm.u.gj.U[p * PST + c], vj[c], r);
+                    vj[kk] = cmulf(r, sm.rinv[kk]);
+                }
+            }
+            float re[NB], im[NB], nim[NB];
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk) {
+                re[kk] = vj[kk].x;
+                im[kk] = vj[kk].y;
+                nim[kk] = -vj[kk].y;
+            }
+            put_terms16(sm.u.gj.bdg, BT_256, 2 * j, re, nim);
+            put_terms16(sm.u.gj.bdg, BT_256, 2 * j + 1, im, re);
+        } else if (tid < 2 * MP) {
+            const int i = tid - MP;
+            float re[NB], im[NB];
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk) {
+                const float2 uv = sm.u.gj.U[i * PST + kk];
+                re[kk] = -uv.x;
+                im[kk] = -uv.y;
+            }
+            put_terms16(sm.u.gj.adg, A_TILE, i, re, im);
+        }
+        async_proxy_fence();
+        fence_before();
+        __syncthreads();
+        // 5. the update X -= U V: the next panel's 16 columns first (bar 0),
+        //    then the rest of the touched columns (bar 1)
+        if (tid == 0) {
+            fence_after();
+            const int K2 = K + NB;
+            auto issue = [&](int c0, int ncol) {   // tensor-memory columns c0 .. c0 + ncol - 1
+                if (ncol <= 0) return;
+                const uint32_t idesc = idesc_bf16_m128((uint32_t)ncol);
+#pragma unroll
+                for (int pr = 0; pr < 6; ++pr) {
+                    const uint64_t ad = smem_desc(smem_u32(sm.u.gj.adg + kProdP[pr] * A_TILE));
+                    const uint64_t bd = smem_desc(smem_u32(sm.u.gj.bdg + kProdQ[pr] * BT_256 + (c0 / 8) * 256));
+                    mma_bf16(tmem + (uint32_t)c0, ad, bd, idesc, 1u);
+                }
+            };
+            if (K2 < Mp) {
+                issue(2 * K2, 16);
+                mma_commit(&sm.bar[0]);
+                issue(0, 2 * K2);
+                issue(2 * K2 + 16, 2 * Mp - 2 * K2 - 16);
+            } else {
+                issue(0, 2 * Mp);
+            }
+            mma_commit(&sm.bar[1]);
+        }
+        if (K + NB < Mp) br.pend[0] = 1u;
+        br.pend[1] = 1u;
+    }
+    if (st == ST_OK) {
+        // the last update complete before anyone reads X
+        if (!bar_wait(sm, br, 1)) st = ST_TIMEOUT;
+        fence_after();
+    }
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// C. X (permuted) from tensor memory into shared memory in true order, the
+//    column exponents, and X' = X rounded to three digits per column
+
+__device__ void x_from_tmem(Tc128Smem &sm, uint32_t tmem, int M)
+{
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int k = tid; k < MP; k += NTH) {
+        if (k >= M) sm.perm[k] = k;
+    }
+    __syncthreads();
+    for (int k = tid; k < MP; k += NTH) sm.pos[sm.perm[k]] = k;
+    __syncthreads();
+    const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
+    const int ti = sm.pos[i];
+    float2 *const X = sm.u.mm.X;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
+        wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int sc = 32 * cg + 16 * h + c;
+            X[ti * XST + sm.perm[sc]] = make_float2(__uint_as_float(v[2 * c]), __uint_as_float(v[2 * c + 1]));
+        }
+    }
+    fence_before();
+    __syncthreads();
+    // column maxima: thread (part, j) scans rows 32 part .. + 31 of column j
+    {
+        const int j = tid & (MP - 1), part = tid >> 7;
+        float mx = 0.f;
+        for (int r = 32 * part; r < 32 * part + 32; ++r) {
+            const float2 x = X[r * XST + j];
+            mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
+        }
+        sm.cmx[part][j] = mx;
+    }
+    __syncthreads();
+    if (tid < MP) {
+        const float mx = fmaxf(fmaxf(sm.cmx[0][tid], sm.cmx[1][tid]), fmaxf(sm.cmx[2][tid], sm.cmx[3][tid]));
+        sm.cexp[tid] = scale_exp(mx) + 1;   // one bit of headroom: |digits| <= 128
+        const float rm = fmaxf(fmaxf(sm.rmx[0][tid], sm.rmx[1][tid]), fmaxf(sm.rmx[2][tid], sm.rmx[3][tid]));
+        sm.rexp[tid] = scale_exp(rm) + 1;
+    }
+    __syncthreads();
+    // X' = X rounded to three digits at the column scale (exact in fp32)
+    for (int e = tid; e < MP * MP; e += NTH) {
+        const int r = e >> 7, j = e & (MP - 1);
+        const int ce = sm.cexp[j];
+        const float dn = pow2f(-ce), up = pow2f(ce - 8);
+        float2 x = X[r * XST + j];
+        float d[NDX];
+        digits3(x.x, dn, d);
+        x.x = (d[0] + d[1] + d[2]) * up;
+        digits3(x.y, dn, d);
+        x.y = (d[0] + d[1] + d[2]) * up;
+        X[r * XST + j] = x;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// D. the residual R = I + Gv' X' (transposed on the tensor cores)
+
+// A tile of chunk c: row j, K kk = digits of X'[k][j] (k = 16 (c % 8) + kk),
+// real part for c < 8, imaginary part for c >= 8
+__device__ void res_a_tile(const Tc128Smem &sm, unsigned char *a, int c)
+{
+    const float2 *X = sm.u.mm.X;
+    const int part = c >> 3, k0 = 16 * (c & 7);
+    for (int e = threadIdx.x; e < MP * 8; e += NTH) {
+        const int j = e & (MP - 1), kk = (e >> 7) * 2;
+        const float dn = pow2f(-sm.cexp[j]);
+        const float2 x0 = X[(k0 + kk) * XST + j], x1 = X[(k0 + kk + 1) * XST + j];
+        float d0[NDX], d1[NDX];
+        digits3(part ? x0.y : x0.x, dn, d0);
+        digits3(part ? x1.y : x1.x, dn, d1);
+#pragma unroll
+        for (int q = 0; q < NDX; ++q) put_bf16x2(a + q * A_TILE, j, kk, d0[q], d1[q]);
+    }
+}
+
+// B tiles of chunk c (rows 2i' = Gr, 2i' + 1 = Gi of Gv' rows i = 32 pass + i',
+// K = k - 16 c) from the double-float Gv' in the workspace, seven digits
+// side by side (digit p at p * BT_RES)
+__device__ void res_b_tile(const Tc128Work &wk, const Tc128Smem &sm, unsigned char *b, int pass,
+                           int c)
+{
+    const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
+    const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
+    const int k0 = 16 * c;
+    for (int e = threadIdx.x; e < 32 * 8 * 2; e += NTH) {
+        // e -> (i', kpair, part): i' fastest so that the Gv' reads coalesce
+        const int ip = e & 31, kk = ((e >> 5) & 7) * 2, part = e >> 8;
+        const int i = 32 * pass + ip;
+        const float dn = pow2f(-sm.rexp[i]);
+        float dg0[NDG], dg1[NDG];
+        {
+            const int k = k0 + kk;
+            const int f = ((k >> 1) * MP + i) * 2;      // (i, k) and (i, k + 1): one float4
+            const float4 h = *reinterpret_cast<const float4 *>(gh + f);
+            const float4 l = *reinterpret_cast<const float4 *>(gl + f);
+            digits7(part ? h.y : h.x, part ? l.y : l.x, dn, dg0);
+            digits7(part ? h.w : h.z, part ? l.w : l.z, dn, dg1);
+        }
+#pragma unroll
+        for (int p = 0; p < NDG; ++p) put_bf16x2(b + p * BT_RES, 2 * ip + part, kk, dg0[p], dg1[p]);
+    }
+}
+
+// the B tiles of chunk c + 8 from those of chunk c: rows 2i' = -Gi, 2i' + 1 = Gr
+__device__ void res_b_swap(const unsigned char *src, unsigned char *dst)
+{
+    // one 16-byte piece per work item: digit p, row r, K half h
+    for (int e = threadIdx.x; e < NDG * 64 * 2; e += NTH) {
+        const int h = e & 1, r = (e >> 1) & 63, p = e >> 7;
+        const int rs = r ^ 1;
+        const uint4 v = *reinterpret_cast<const uint4 *>(src + p * BT_RES + tile_off(rs, 8 * h));
+        uint4 w = v;
+        if ((r & 1) == 0) {   // -Gi: flip the sign bits of the eight bf16 values
+            w.x ^= 0x80008000u;
+            w.y ^= 0x80008000u;
+            w.z ^= 0x80008000u;
+            w.w ^= 0x80008000u;
+        }
+        *reinterpret_cast<uint4 *>(dst + p * BT_RES + tile_off(r, 8 * h)) = w;
+    }
+}
+
+// read back one pass: lane j of quarter qd, columns 16 cg .. + 15 (rows
+// i = 32 pass + 8 cg + c / 2, part c % 2) of every accumulator; returns the
+// largest |R_ij| written
+__device__ float res_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem, int pass, int M)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qd = warp & 3, cg = warp >> 2, j = 32 * qd + lane;
+    const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + 16 * cg;
+    const int ce = sm.cexp[j];
+    float rloc = 0.f;
+    float out[16];
+#pragma unroll
+    for (int j8 = 0; j8 < 16; j8 += 8) {
+        uint32_t v0[8], v1[8], v2[8], v3[8];
+        float small[8];
+        tmem_ld8(tb + 192 + j8, v0);
+        tmem_ld8(tb + 256 + j8, v1);
+        tmem_ld8(tb + 320 + j8, v2);
+        tmem_ld8(tb + 384 + j8, v3);
+        wait_ld();
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+            small[x] = ((__uint_as_float(v3[x]) + __uint_as_float(v2[x])) + __uint_as_float(v1[x])) +
+                       __uint_as_float(v0[x]);
+        tmem_ld8(tb + j8, v0);
+        tmem_ld8(tb + 64 + j8, v1);
+        tmem_ld8(tb + 128 + j8, v2);
+        wait_ld();
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int col = 16 * cg + j8 + x;        // accumulator column: row i' = col / 2, part col % 2
+            const int i = 32 * pass + (col >> 1), part = col & 1;
+            float hs, ls, t, te;
+            two_sum(__uint_as_float(v0[x]), __uint_as_float(v1[x]), hs, ls);
+            two_sum(hs, __uint_as_float(v2[x]), t, te);
+            ls += te;
+            two_sum(t, small[x], hs, te);
+            ls += te;
+            const float sc = pow2f(sm.rexp[i] + ce - 16);
+            hs *= sc;
+            ls *= sc;
+            if (part == 0 && i == j) {
+                two_sum(hs, 1.0f, t, te);
+                hs = t;
+                ls += te;
+            }
+            const float r = (i < M && j < M) ? hs + ls : 0.f;
+            out[j8 + x] = r;
+            rloc = fmaxf(rloc, fabsf(r));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int i = 32 * pass + 8 * cg + c;
+        wk.R[sidx(i, j)] = make_float2(out[2 * c], out[2 * c + 1]);
+    }
+    return rloc;
+}
+
+// ---------------------------------------------------------------------------
+// F. the refinement product X' S
+
+// A tile of chunk c: row i, K kk = digits of X'[i][k], k = 16 (c % 8) + kk
+__device__ void ref_a_tile(const Tc128Smem &sm, unsigned char *a, int c)
+{
+    const float2 *X = sm.u.mm.X;
+    const int part = c >> 3, k0 = 16 * (c & 7);
+    for (int e = threadIdx.x; e < MP * 8; e += NTH) {
+        const int kk = (e & 7) * 2, i = e >> 3;
+        const float2 x0 = X[i * XST + k0 + kk], x1 = X[i * XST + k0 + kk + 1];
+        float d0[NDX], d1[NDX];
+        digits3(part ? x0.y : x0.x, pow2f(-sm.cexp[k0 + kk]), d0);
+        digits3(part ? x1.y : x1.x, pow2f(-sm.cexp[k0 + kk + 1]), d1);
+#pragma unroll
+        for (int q = 0; q < NDX; ++q) put_bf16x2(a + q * A_TILE, i, kk, d0[q], d1[q]);
+    }
+}
+
+// B tile of chunk c: S scaled by 2^(t_k - 8) in real form, three exact bf16
+// terms (rows 2j = [Re | -Im], 2j + 1 = [Im | Re] of column j of S)
+__device__ void ref_b_tile(const float2 *S, const Tc128Smem &sm, unsigned char *b, int c)
+{
+    const int part = c >> 3, k0 = 16 * (c & 7);
+    for (int e = threadIdx.x; e < MP * 8; e += NTH) {
+        const int j = e & (MP - 1), kk = (e >> 7) * 2, k = k0 + kk;
+        const float4 s = *reinterpret_cast<const float4 *>(S + sidx(k, j));   // (k, j), (k + 1, j)
+        const float u0 = pow2f(sm.cexp[k] - 8), u1 = pow2f(sm.cexp[k + 1] - 8);
+        float r0, r1, c0, c1;   // row 2j and row 2j + 1 values at K positions k, k + 1
+        if (part == 0) {
+            r0 = s.x * u0; r1 = s.z * u1;      // Re
+            c0 = s.y * u0; c1 = s.w * u1;      // Im
+        } else {
+            r0 = -s.y * u0; r1 = -s.w * u1;    // -Im
+            c0 = s.x * u0; c1 = s.z * u1;      // Re
+        }
+        uint32_t h0, m0, l0, h1, m1, l1;
+        bf16_split3(r0, h0, m0, l0);
+        bf16_split3(r1, h1, m1, l1);
+        unsigned char *p = b + tile_off(2 * j, kk);
+        *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
+        *reinterpret_cast<uint32_t *>(p + BT_256) = pack_hi16(m0, m1);
+        *reinterpret_cast<uint32_t *>(p + 2 * BT_256) = pack_hi16(l0, l1);
+        bf16_split3(c0, h0, m0, l0);
+        bf16_split3(c1, h1, m1, l1);
+        p = b + tile_off(2 * j + 1, kk);
+        *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
+        *reinterpret_cast<uint32_t *>(p + BT_256) = pack_hi16(m0, m1);
+        *reinterpret_cast<uint32_t *>(p + 2 * BT_256) = pack_hi16(l0, l1);
+    }
+}
+
+// g = X' + D into the state: lane i of quarter qd, complex columns 32 cg ..
+__device__ void ref_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem, int M)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
+    const float2 *X = sm.u.mm.X;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
+        wait_ld();
+#pragma unroll
+        for (int cp = 0; cp < 8; ++cp) {
+            float2 oh[2], ol[2];
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int c = 2 * cp + s2, j = 32 * cg + 16 * h + c;
+                const float2 x = X[i * XST + j];
+                if (i < M && j < M) {
+                    two_sum(x.x, __uint_as_float(v[2 * c]), oh[s2].x, ol[s2].x);
+                    two_sum(x.y, __uint_as_float(v[2 * c + 1]), oh[s2].y, ol[s2].y);
+                } else {
+                    oh[s2] = make_float2(i == j ? 1.f : 0.f, 0.f);
+                    ol[s2] = make_float2(0.f, 0.f);
+                }
+            }
+            const int jp = 16 * cg + 8 * h + cp;
+            wk.Gh[jp * MP + i] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
+            wk.Gl[jp * MP + i] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// E. the rare paths on the CUDA cores (workspace operands)
+
+// So = R + R Si (row-pair layout), zero outside M x M
+__device__ void neumann_step(const float2 *R, const float2 *Si, float2 *So, int M)
+{
+    for (int e = threadIdx.x; e < MP * MP; e += NTH) {
+        const int i = e >> 7, j = e & (MP - 1);
+        float2 acc = R[sidx(i, j)];
+        if (i < M && j < M)
+            for (int k = 0; k < M; ++k) acc = cfmaf(R[sidx(i, k)], Si[sidx(k, j)], acc);
+        So[sidx(i, j)] = acc;
+    }
+}
+
+// g = X' + X' S with X' S accumulated error-free (TwoProduct + TwoSum)
+__device__ void refine_exact128(Tc128Work &wk, const Tc128Smem &sm, const float2 *S, int M)
+{
+    const float2 *X = sm.u.mm.X;
+    float2 *const gh = reinterpret_cast<float2 *>(wk.Gh);
+    float2 *const gl = reinterpret_cast<float2 *>(wk.Gl);
+    for (int e = threadIdx.x; e < MP * MP; e += NTH) {
+        const int i = e & (MP - 1), j = e >> 7;
+        const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+        if (i >= M || j >= M) {
+            gh[f] = make_float2(i == j ? 1.f : 0.f, 0.f);
+            gl[f] = make_float2(0.f, 0.f);
+            continue;
+        }
+        float2 sh = make_float2(0.f, 0.f), se = make_float2(0.f, 0.f);
+        for (int k = 0; k < M; ++k) {
+            const float2 xa = X[i * XST + k], sb = S[sidx(k, j)];
+            dot2_acc1(xa.x, sb.x, sh.x, se.x);
+            dot2_acc1(-xa.y, sb.y, sh.x, se.x);
+            dot2_acc1(xa.x, sb.y, sh.y, se.y);
+            dot2_acc1(xa.y, sb.x, sh.y, se.y);
+        }
+        const float2 xv = X[i * XST + j];
+        float hx, lx, hy, ly;
+        two_sum(xv.x, sh.x, hx, lx);
+        lx += se.x;
+        two_sum(hx, lx, hx, lx);
+        two_sum(xv.y, sh.y, hy, ly);
+        ly += se.y;
+        two_sum(hy, ly, hy, ly);
+        gh[f] = make_float2(hx, hy);
+        gl[f] = make_float2(lx, ly);
+    }
+}
+
+// near-singular A_n: this slice in FP64 from Gv' (still in the state)
+__device__ int fallback64(Tc128Work &wk, int M)
+{
+    const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
+    const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
+    for (int e = threadIdx.x; e < M * M; e += NTH) {
+        const int i = e / M, j = e - i * M;
+        const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+        wk.A64[e] = make_double2(-((double)gh[f].x + (double)gl[f].x), -((double)gh[f].y + (double)gl[f].y));
+    }
+    __syncthreads();
+    const int st = gj_invert64(wk.A64, M, fallback_scratch(wk.scr, M));
+    if (st != ST_OK) return st;
+    float2 *const oh = reinterpret_cast<float2 *>(wk.Gh);
+    float2 *const ol = reinterpret_cast<float2 *>(wk.Gl);
+    for (int e = threadIdx.x; e < MP * MP; e += NTH) {
+        const int i = e & (MP - 1), j = e >> 7;
+        const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+        float2 h, l;
+        if (i < M && j < M) {
+            const double2 v = wk.A64[i * M + j];
+            to_df(v.x, h.x, l.x);
+            to_df(v.y, h.y, l.y);
+        } else {
+            h = make_float2(i == j ? 1.f : 0.f, 0.f);
+            l = make_float2(0.f, 0.f);
+        }
+        oh[f] = h;
+        ol[f] = l;
+    }
+    __syncthreads();
+    return ST_OK;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(NTH, 1)
+knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Tc128Smem &sm = *reinterpret_cast<Tc128Smem *>(smem_raw);
+    Tc128Work &wk = work[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&sm.tmem)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        sm.cur_sys = -1;
+        for (int b = 0; b < 4; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.bar[b])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = sm.tmem;
+    Bars br = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+    bool timed_out = false;
+
+    for (;;) {
+        if (tid == 0) {
+            const int qn = atomicAdd(in.queue, 1);
+            sm.inst = qn < in.n ? take_position(in, qn) : -1;
+        }
+        __syncthreads();
+        const int inst = sm.inst;
+        const int si = inst >= 0 && in.sys_of ? in.sys_of[inst] : 0;
+        const bool reload = inst >= 0 && si != sm.cur_sys;
+        __syncthreads();
+        if (inst < 0) break;
+        const SysDev s = in.sys[si];
+        const int M = s.M, L = s.L, vb = s.vb;
+        const size_t MM = (size_t)M * M;
+        if (reload) {
+            for (int q = 0; q < 2; ++q)
+                for (int i = tid; i < MP; i += NTH) {
+                    double2 v = make_double2(0.0, 0.0);
+                    if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
+                    float hx, lx, hy, ly;
+                    to_df(v.x, hx, lx);
+                    to_df(v.y, hy, ly);
+                    sm.vh[q][i] = make_float2(hx, hy);
+                    sm.vl[q][i] = make_float2(lx, ly);
+                }
+            if (tid < 2) {
+                if (vb == 1)
+                    classify_vdiag(s.V + (size_t)(tid % s.Vperiod) * MM, M + 1, M, sm.vuni[tid],
+                                   sm.vch[tid], sm.vcl[tid]);
+                else
+                    sm.vuni[tid] = 1;   // V g V^dagger formed by the block pass
+            }
+            if (tid == 0) sm.cur_sys = si;
+            __syncthreads();
+        }
+        const InstParams ip = inst_params(in, inst, M);
+        int st = ip.st;
+
+        for (int n = 0; n < L && st == ST_OK; ++n) {
+            // ---- A
+            slice_diag<MP, NTH>(sm.eps, s, ip.ms, ip.W, ip.E, n);
+            if (vb == 4 && n > 0) {
+                gv_blocks4(wk, s, M, n & 1);
+                __syncthreads();
+            }
+            const int q = n & 1;
+            const int vmode = vb == 4 ? 1 : (sm.vuni[q] == 1 ? 1 : (sm.vuni[q] == 2 ? 2 : 0));
+            gv_elementwise(wk, sm, M, n, L, vmode, ip.SL, ip.SR);
+            __syncthreads();
+            gv_add_h0(wk, sm, s, M);
+            __syncthreads();
+            fence_after();
+            x_to_tmem(wk, sm, tmem, M);
+            fence_before();
+            __syncthreads();
+            fence_after();
+            // ---- B
+            st = gj_tmem(sm, tmem, M, br);
+            if (st != ST_OK) {
+                timed_out = st == ST_TIMEOUT;
+                break;
+            }
+            // ---- C
+            x_from_tmem(sm, tmem, M);
+            // ---- D
+            float rloc = 0.f;
+            const int nchunk = (M + 15) / 16;          // K-chunks per part
+            const int npass = (M + 31) / 32;
+            for (int pass = 0; pass < npass && !timed_out; ++pass) {
+                const int nseq = 2 * nchunk;
+                for (int sq = 0; sq < nseq; ++sq) {
+                    const int slot = sq & 1;
+                    const int c = (sq >> 1) + 8 * (sq & 1);
+                    if (sq >= 2 && !bar_wait(sm, br, 2 + slot)) { timed_out = true; break; }
+                    unsigned char *const a = sm.u.mm.t.res.a[slot];
+                    unsigned char *const b = sm.u.mm.t.res.b[slot];
+                    res_a_tile(sm, a, c);
+                    if ((sq & 1) == 0) res_b_tile(wk, sm, b, pass, c);
+                    else res_b_swap(sm.u.mm.t.res.b[slot ^ 1], b);
+                    async_proxy_fence();
+                    fence_before();
+                    __syncthreads();
+                    if (tid == 0) {
+                        fence_after();
+                        const uint64_t bd0 = smem_desc(smem_u32(b));
+#pragma unroll
+                        for (int qd = 0; qd < NDX; ++qd) {
+                            const uint64_t ad = smem_desc(smem_u32(a + qd * A_TILE));
+                            const uint32_t first = (sq == 0 && qd == 0) ? 0u : 1u;
+                            // B digits p = 0 .. 3 side by side (N = 256) at accumulator qd,
+                            // then p = 4 .. 6 - qd (N = 64 (3 - qd)) at accumulator qd + 4
+                            mma_bf16(tmem + 64 * qd, ad, bd0, idesc_bf16_m128(256), first);
+                            const uint64_t bd4 = smem_desc(smem_u32(b + 4 * BT_RES));
+                            mma_bf16(tmem + 64 * (qd + 4), ad, bd4,
+                                     idesc_bf16_m128((uint32_t)(64 * (3 - qd))), first);
+                        }
+                        mma_commit(&sm.bar[2 + slot]);
+                    }
+                    br.pend[2 + slot] = 1u;
+                }
+                if (timed_out) break;
+                // both slots' last commits
+                if (!bar_wait(sm, br, 2) || !bar_wait(sm, br, 3)) { timed_out = true; break; }
+                fence_after();
+                rloc = fmaxf(rloc, res_readback(wk, sm, tmem, pass, M));
+                fence_before();
+                __syncthreads();
+            }
+            if (timed_out) {
+                st = ST_TIMEOUT;
+                break;
+            }
+            // zero R in the rows no pass wrote (M < 128)
+            for (int e = tid; e < MP * MP; e += NTH) {
+                const int i = e >> 7, j = e & (MP - 1);
+                if (i >= 32 * npass) wk.R[sidx(i, j)] = make_float2(0.f, 0.f);
+            }
+            // ---- E
+            const float rmax = block_max_nonneg<NTH>(rloc, sm.redu);
+            if (refinement_fails(rmax, M)) {
+                st = fallback64(wk, M);
+                __syncthreads();
+                continue;
+            }
+            const int nx = neumann_terms(rmax, M);
+            const float2 *S = wk.R;
+            for (int t = 0; t < nx; ++t) {
+                float2 *const So = (t & 1) ? wk.S2 : wk.S1;
+                neumann_step(wk.R, S, So, M);
+                __syncthreads();
+                S = So;
+            }
+            if (rmax > EXACT_RMAX) {
+                refine_exact128(wk, sm, S, M);
+                __syncthreads();
+                continue;
+            }
+            // ---- F
+            for (int sq = 0; sq < 2 * nchunk && !timed_out; ++sq) {
+                const int slot = sq & 1;
+                const int c = (sq >> 1) + 8 * (sq & 1);
+                if (sq >= 2 && !bar_wait(sm, br, 2 + slot)) { timed_out = true; break; }
+                unsigned char *const a = sm.u.mm.t.ref.a[slot];
+                unsigned char *const b = sm.u.mm.t.ref.b[slot];
+                ref_a_tile(sm, a, c);
+                ref_b_tile(S, sm, b, c);
+                async_proxy_fence();
+                fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    fence_after();
+#pragma unroll
+                    for (int pr = 0; pr < 6; ++pr) {
+                        const uint64_t ad = smem_desc(smem_u32(a + kProdP[pr] * A_TILE));
+                        const uint64_t bd = smem_desc(smem_u32(b + kProdQ[pr] * BT_256));
+                        mma_bf16(tmem, ad, bd, idesc_bf16_m128(256), (sq == 0 && pr == 0) ? 0u : 1u);
+                    }
+                    mma_commit(&sm.bar[2 + slot]);
+                }
+                br.pend[2 + slot] = 1u;
+            }
+            if (!timed_out && (!bar_wait(sm, br, 2) || !bar_wait(sm, br, 3))) timed_out = true;
+            if (timed_out) {
+                st = ST_TIMEOUT;
+                break;
+            }
+            fence_after();
+            ref_readback(wk, sm, tmem, M);
+            fence_before();
+            __syncthreads();
+        }
+
+        double T = 0.0;
+        if (st == ST_OK) {
+            // G_LL = Gh + Gl, row-major, for the trace (S1 / S2 hold hi / lo)
+            const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
+            const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
+            for (int e = tid; e < MP * MP; e += NTH) {
+                const int i = e >> 7, j = e & (MP - 1);
+                const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+                wk.S1[e] = gh[f];
+                wk.S2[e] = gl[f];
+            }
+            __syncthreads();
+            T = ward_T<MP, NTH>(wk.S1, wk.S2, wk.A64, ip.SR, M, sm.red);
+            if (in.GLL) store_gll<MP, NTH>(wk.A64, M, in.GLL + (size_t)ip.out * M * M);
+            if (!isfinite(T)) st = ST_NONFINITE;
+        }
+        if (tid == 0) {
+            in.T[ip.out] = T;
+            if (in.status) in.status[ip.out] = st;
+        }
+        __syncthreads();
+        if (timed_out) break;
+    }
+    if (timed_out) {
+        // a wait ran out: every barrier with a commit still in flight gets a
+        // second bounded wait before the tensor memory is released
+        if (tid == 0)
+            for (int b = 0; b < 4; ++b)
+                if (br.pend[b]) mbar_wait(&sm.bar[b], br.ph[b]);
+        __syncthreads();
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+extern "C" size_t knit_mixed_tc128_work_bytes(void) { return sizeof(Tc128Work); }
+extern "C" size_t knit_mixed_tc128_smem_bytes(void) { return sizeof(Tc128Smem); }
+
+// Host launch helper.  Instances that a timed-out CTA never reaches keep the
+// ST_TIMEOUT status written here first.
+extern "C" cudaError_t knit_launch_mixed_tc128(const InstDev *in, int grid, void *work,
+                                               cudaStream_t stream)
+{
+    static_assert(sizeof(Tc128Smem) <= 227 * 1024, "shared memory budget");
+    if (in->status && !in->out_index)
+        fill_status128<<<(in->n + 255) / 256, 256, 0, stream>>>(in->status, in->n, ST_TIMEOUT);
+    const size_t smb = sizeof(Tc128Smem);
+    cudaError_t e = cudaFuncSetAttribute(knit_sweep_mixed_tc128_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    if (e != cudaSuccess) return e;
+    knit_sweep_mixed_tc128_kernel<<<grid, NTH, smb, stream>>>(*in, (Tc128Work *)work);
+    return cudaGetLastError();
+}
