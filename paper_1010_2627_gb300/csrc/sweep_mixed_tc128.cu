@@ -123,8 +123,8 @@ struct Tc128Smem {
 };
 
 // per-CTA device workspace
-struct Tc128Work;
 static_assert((2 * MP + 1) * 16 + (MP + 2) * 4 <= (2 * MP + 48) * 16, "fallback scratch");
+static_assert(2 * (MP / 4) * (MP / 4) <= 4 * NTH, "gv_blocks4 keeps at most 4 items per thread");
 
 struct Tc128Work {
     float4 Gh[(MP / 2) * MP];      // state g / Gv' (hi): column pair jp, row i at jp * MP + i
@@ -278,9 +278,9 @@ __device__ void gv_blocks4(Tc128Work &wk, const SysDev &s, int M, int q)
     const int nb = (M + 3) / 4;
     // all reads of the state happen before any write (the two column halves
     // of a block read the whole block)
-    float4 outh[4][2], outl[4][2];   // [item][row a] as float4 = 2 complex columns
+    float4 outh[4][4], outl[4][4];   // [item][row a] as float4 = 2 complex columns
     int idxs[4];
-    int nitem = 0;
+    int nitem = 0;   // at most 2 * 32 * 32 / NTH = 4 items per thread
     for (int e = threadIdx.x; e < 2 * nb * nb; e += NTH, ++nitem) {
         const int hc = e & 1, B = (e >> 1) % nb, C = (e >> 1) / nb;
         // u[a][s] = sum_b g[a][b] conj(V[4C+s][4C+b]) for s = 2hc, 2hc + 1
