@@ -752,30 +752,35 @@ __device__ void res_a_tile(const Tc128Smem &sm, unsigned char *a, int c)
 
 // B tiles of chunk c (rows 2i' = Gr, 2i' + 1 = Gi of Gv' rows i = 32 pass + i',
 // K = k - 16 c) from the double-float Gv' in the workspace, seven digits
-// side by side (digit p at p * BT_RES)
-__device__ void res_b_tile(const Tc128Work &wk, const Tc128Smem &sm, unsigned char *b, int pass,
-                           int c)
+// side by side (digit p at p * BT_RES).  Work item = thread: (i', k pair,
+// part), i' fastest so that the Gv' reads coalesce; the loads (one float4
+// of hi and one of lo: (i, k) and (i, k + 1)) are issued a chunk ahead.
+struct GvPre {
+    float4 h, l;
+};
+
+KNIT_DEV GvPre res_b_load(const Tc128Work &wk, int pass, int c)
 {
-    const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
-    const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
-    const int k0 = 16 * c;
-    for (int e = threadIdx.x; e < 32 * 8 * 2; e += NTH) {
-        // e -> (i', kpair, part): i' fastest so that the Gv' reads coalesce
-        const int ip = e & 31, kk = ((e >> 5) & 7) * 2, part = e >> 8;
-        const int i = 32 * pass + ip;
-        const float dn = pow2f(-sm.rexp[i]);
-        float dg0[NDG], dg1[NDG];
-        {
-            const int k = k0 + kk;
-            const int f = ((k >> 1) * MP + i) * 2;      // (i, k) and (i, k + 1): one float4
-            const float4 h = *reinterpret_cast<const float4 *>(gh + f);
-            const float4 l = *reinterpret_cast<const float4 *>(gl + f);
-            digits7(part ? h.y : h.x, part ? l.y : l.x, dn, dg0);
-            digits7(part ? h.w : h.z, part ? l.w : l.z, dn, dg1);
-        }
+    const int e = threadIdx.x;
+    const int ip = e & 31, kk = ((e >> 5) & 7) * 2;
+    const int i = 32 * pass + ip, k = 16 * (c & 7) + kk;
+    const int f = (k >> 1) * MP + i;
+    GvPre g;
+    g.h = wk.Gh[f];
+    g.l = wk.Gl[f];
+    return g;
+}
+
+__device__ void res_b_build(const GvPre &g, const Tc128Smem &sm, unsigned char *b, int pass)
+{
+    const int e = threadIdx.x;
+    const int ip = e & 31, kk = ((e >> 5) & 7) * 2, part = e >> 8;
+    const float dn = pow2f(-sm.rexp[32 * pass + ip]);
+    float dg0[NDG], dg1[NDG];
+    digits7(part ? g.h.y : g.h.x, part ? g.l.y : g.l.x, dn, dg0);
+    digits7(part ? g.h.w : g.h.z, part ? g.l.w : g.l.z, dn, dg1);
 #pragma unroll
-        for (int p = 0; p < NDG; ++p) put_bf16x2(b + p * BT_RES, 2 * ip + part, kk, dg0[p], dg1[p]);
-    }
+    for (int p = 0; p < NDG; ++p) put_bf16x2(b + p * BT_RES, 2 * ip + part, kk, dg0[p], dg1[p]);
 }
 
 // the B tiles of chunk c + 8 from those of chunk c: rows 2i' = -Gi, 2i' + 1 = Gr
@@ -857,10 +862,40 @@ __device__ float res_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem,
 }
 
 // ---------------------------------------------------------------------------
-// F. the refinement product X' S
+// F. the products D = X' S (refinement) and D = R S (further Neumann terms)
+//    on the tensor cores: A rows i, K = 16 (c % 8) + kk in the real form
+//    [Re | Im] (c < 8 | c >= 8), B^T rows 2j = [Re S | -Im S], 2j + 1 =
+//    [Im S | Re S], three exact bf16 terms each, the six products of term
+//    order <= 2 into one f32 accumulator (tensor-memory columns 0 .. 255).
+//    The chunks of one K range (c and c + 8) use the same loaded values.
 
-// A tile of chunk c: row i, K kk = digits of X'[i][k], k = 16 (c % 8) + kk
-__device__ void ref_a_tile(const Tc128Smem &sm, unsigned char *a, int c)
+// values of S (and of R for a Neumann term) one work item per thread half:
+// items e = tid, tid + NTH
+struct ProdPre {
+    float4 s[2];      // (k, j), (k + 1, j) of S for B item e: j = e % 128, kk = 2 (e / 128)
+    float2 r[2][2];   // R[i][k], R[i][k + 1] for A item e: kk = 2 (e % 8), i = e / 8
+};
+
+KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, int c)
+{
+    const int k0 = 16 * (c & 7);
+    ProdPre q;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = threadIdx.x + h * NTH;
+        const int j = e & (MP - 1), kk = (e >> 7) * 2;
+        q.s[h] = *reinterpret_cast<const float4 *>(S + sidx(k0 + kk, j));
+        if (R) {
+            const int ka = (e & 7) * 2, i = e >> 3;
+            q.r[h][0] = R[sidx(i, k0 + ka)];
+            q.r[h][1] = R[sidx(i, k0 + ka + 1)];
+        }
+    }
+    return q;
+}
+
+// A tile from X' (digits, at the column scale of X'; the scale goes into B)
+__device__ void prod_a_x(const Tc128Smem &sm, unsigned char *a, int c)
 {
     const float2 *X = sm.u.mm.X;
     const int part = c >> 3, k0 = 16 * (c & 7);
@@ -875,22 +910,44 @@ __device__ void ref_a_tile(const Tc128Smem &sm, unsigned char *a, int c)
     }
 }
 
-// B tile of chunk c: S scaled by 2^(t_k - 8) in real form, three exact bf16
-// terms (rows 2j = [Re | -Im], 2j + 1 = [Im | Re] of column j of S)
-__device__ void ref_b_tile(const float2 *S, const Tc128Smem &sm, unsigned char *b, int c)
+// A tile from R (three exact bf16 terms of each fp32 value)
+KNIT_DEV void prod_a_r(const ProdPre &q, unsigned char *a, int c)
+{
+    const int part = c >> 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = threadIdx.x + h * NTH;
+        const int kk = (e & 7) * 2, i = e >> 3;
+        const float v0 = part ? q.r[h][0].y : q.r[h][0].x;
+        const float v1 = part ? q.r[h][1].y : q.r[h][1].x;
+        uint32_t h0, m0, l0, h1, m1, l1;
+        bf16_split3(v0, h0, m0, l0);
+        bf16_split3(v1, h1, m1, l1);
+        unsigned char *p = a + tile_off(i, kk);
+        *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
+        *reinterpret_cast<uint32_t *>(p + A_TILE) = pack_hi16(m0, m1);
+        *reinterpret_cast<uint32_t *>(p + 2 * A_TILE) = pack_hi16(l0, l1);
+    }
+}
+
+// B tile from S, scaled by 2^(t_k - 8) when A holds the X' digits
+KNIT_DEV void prod_b(const ProdPre &q, const Tc128Smem &sm, unsigned char *b, int c, bool scaled)
 {
     const int part = c >> 3, k0 = 16 * (c & 7);
-    for (int e = threadIdx.x; e < MP * 8; e += NTH) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int e = threadIdx.x + h * NTH;
         const int j = e & (MP - 1), kk = (e >> 7) * 2, k = k0 + kk;
-        const float4 s = *reinterpret_cast<const float4 *>(S + sidx(k, j));   // (k, j), (k + 1, j)
-        const float u0 = pow2f(sm.cexp[k] - 8), u1 = pow2f(sm.cexp[k + 1] - 8);
-        float r0, r1, c0, c1;   // row 2j and row 2j + 1 values at K positions k, k + 1
+        const float4 sv = q.s[h];
+        const float u0 = scaled ? pow2f(sm.cexp[k] - 8) : 1.f;
+        const float u1 = scaled ? pow2f(sm.cexp[k + 1] - 8) : 1.f;
+        float r0, r1, c0, c1;   // rows 2j and 2j + 1 at K positions k, k + 1
         if (part == 0) {
-            r0 = s.x * u0; r1 = s.z * u1;      // Re
-            c0 = s.y * u0; c1 = s.w * u1;      // Im
+            r0 = sv.x * u0; r1 = sv.z * u1;      // Re
+            c0 = sv.y * u0; c1 = sv.w * u1;      // Im
         } else {
-            r0 = -s.y * u0; r1 = -s.w * u1;    // -Im
-            c0 = s.x * u0; c1 = s.z * u1;      // Re
+            r0 = -sv.y * u0; r1 = -sv.w * u1;    // -Im
+            c0 = sv.x * u0; c1 = sv.z * u1;      // Re
         }
         uint32_t h0, m0, l0, h1, m1, l1;
         bf16_split3(r0, h0, m0, l0);
@@ -941,20 +998,72 @@ __device__ void ref_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem, 
     }
 }
 
-// ---------------------------------------------------------------------------
-// E. the rare paths on the CUDA cores (workspace operands)
-
-// So = R + R Si (row-pair layout), zero outside M x M
-__device__ void neumann_step(const float2 *R, const float2 *Si, float2 *So, int M)
+// a further Neumann term: So = R + D (zero outside M x M)
+__device__ void neumann_readback(const float2 *R, float2 *So, uint32_t tmem, int M)
 {
-    for (int e = threadIdx.x; e < MP * MP; e += NTH) {
-        const int i = e >> 7, j = e & (MP - 1);
-        float2 acc = R[sidx(i, j)];
-        if (i < M && j < M)
-            for (int k = 0; k < M; ++k) acc = cfmaf(R[sidx(i, k)], Si[sidx(k, j)], acc);
-        So[sidx(i, j)] = acc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
+        wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int j = 32 * cg + 16 * h + c;
+            float2 o = make_float2(0.f, 0.f);
+            if (i < M && j < M) {
+                const float2 r = R[sidx(i, j)];
+                o = make_float2(r.x + __uint_as_float(v[2 * c]), r.y + __uint_as_float(v[2 * c + 1]));
+            }
+            So[sidx(i, j)] = o;
+        }
     }
 }
+
+// D = A S on the tensor cores with A = X' (R null) or A = R; double-buffered
+// over the two chunk slots; every thread polls the slot's barrier before it
+// rewrites the slot, and the next K range's loads are issued a chunk ahead.
+// Returns false when a wait ran out (the commits in flight stay recorded).
+__device__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, const float2 *S,
+                           const float2 *R, int nchunk)
+{
+    const int nseq = 2 * nchunk;
+    ProdPre cur = prod_load(S, R, 0), nxt = cur;
+    for (int sq = 0; sq < nseq; ++sq) {
+        const int slot = sq & 1, c = (sq >> 1) + 8 * (sq & 1);
+        const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
+        if ((sq & 1) == 0 && sq + 2 < nseq) nxt = prod_load(S, R, (sq >> 1) + 1);
+        unsigned char *const a = sm.u.mm.t.ref.a[slot];
+        unsigned char *const b = sm.u.mm.t.ref.b[slot];
+        if (R) prod_a_r(cur, a, c);
+        else prod_a_x(sm, a, c);
+        prod_b(cur, sm, b, c, R == nullptr);
+        async_proxy_fence();
+        fence_before();
+        if (__syncthreads_or(!ok)) return false;
+        if (sq >= 2) {
+            br.ph[2 + slot] ^= 1u;
+            br.pend[2 + slot] = 0u;
+        }
+        if (threadIdx.x == 0) {
+            fence_after();
+#pragma unroll
+            for (int pr = 0; pr < 6; ++pr) {
+                const uint64_t ad = smem_desc(smem_u32(a + kProdP[pr] * A_TILE));
+                const uint64_t bd = smem_desc(smem_u32(b + kProdQ[pr] * BT_256));
+                mma_bf16(tmem, ad, bd, idesc_bf16_m128(256), (sq == 0 && pr == 0) ? 0u : 1u);
+            }
+            mma_commit(&sm.bar[2 + slot]);
+        }
+        br.pend[2 + slot] = 1u;
+        if (sq & 1) cur = nxt;
+    }
+    return bar_wait(sm, br, 2) && bar_wait(sm, br, 3);
+}
+
+// ---------------------------------------------------------------------------
+// E. the rare paths on the CUDA cores (workspace operands)
 
 // g = X' + X' S with X' S accumulated error-free (TwoProduct + TwoSum)
 __device__ void refine_exact128(Tc128Work &wk, const Tc128Smem &sm, const float2 *S, int M)
@@ -1123,21 +1232,29 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             const int npass = (M + 31) / 32;
             for (int pass = 0; pass < npass && !timed_out; ++pass) {
                 const int nseq = 2 * nchunk;
+                GvPre cur = res_b_load(wk, pass, 0), nxt = cur;
                 for (int sq = 0; sq < nseq; ++sq) {
                     const int slot = sq & 1;
                     const int c = (sq >> 1) + 8 * (sq & 1);
-                    if (sq >= 2 && !bar_wait(sm, br, 2 + slot)) { timed_out = true; break; }
+                    // every thread waits for the MMAs that last read this slot
+                    const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
+                    if ((sq & 1) == 0 && sq + 2 < nseq) nxt = res_b_load(wk, pass, (sq >> 1) + 1);
                     unsigned char *const a = sm.u.mm.t.res.a[slot];
                     unsigned char *const b = sm.u.mm.t.res.b[slot];
                     res_a_tile(sm, a, c);
-                    if ((sq & 1) == 0) res_b_tile(wk, sm, b, pass, c);
+                    if ((sq & 1) == 0) res_b_build(cur, sm, b, pass);
                     else res_b_swap(sm.u.mm.t.res.b[slot ^ 1], b);
                     async_proxy_fence();
                     fence_before();
-                    __syncthreads();
+                    if (__syncthreads_or(!ok)) { timed_out = true; break; }
+                    if (sq >= 2) {
+                        br.ph[2 + slot] ^= 1u;
+                        br.pend[2 + slot] = 0u;
+                    }
                     if (tid == 0) {
                         fence_after();
                         const uint64_t bd0 = smem_desc(smem_u32(b));
+                        const uint64_t bd4 = smem_desc(smem_u32(b + 4 * BT_RES));
 #pragma unroll
                         for (int qd = 0; qd < NDX; ++qd) {
                             const uint64_t ad = smem_desc(smem_u32(a + qd * A_TILE));
@@ -1145,13 +1262,13 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                             // B digits p = 0 .. 3 side by side (N = 256) at accumulator qd,
                             // then p = 4 .. 6 - qd (N = 64 (3 - qd)) at accumulator qd + 4
                             mma_bf16(tmem + 64 * qd, ad, bd0, idesc_bf16_m128(256), first);
-                            const uint64_t bd4 = smem_desc(smem_u32(b + 4 * BT_RES));
                             mma_bf16(tmem + 64 * (qd + 4), ad, bd4,
                                      idesc_bf16_m128((uint32_t)(64 * (3 - qd))), first);
                         }
                         mma_commit(&sm.bar[2 + slot]);
                     }
                     br.pend[2 + slot] = 1u;
+                    if (sq & 1) cur = nxt;
                 }
                 if (timed_out) break;
                 // both slots' last commits
@@ -1179,11 +1296,19 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             }
             const int nx = neumann_terms(rmax, M);
             const float2 *S = wk.R;
-            for (int t = 0; t < nx; ++t) {
+            for (int t = 0; t < nx && !timed_out; ++t) {
+                // S <- R + R S on the tensor cores
                 float2 *const So = (t & 1) ? wk.S2 : wk.S1;
-                neumann_step(wk.R, S, So, M);
+                if (!product_tc(sm, br, tmem, S, wk.R, nchunk)) { timed_out = true; break; }
+                fence_after();
+                neumann_readback(wk.R, So, tmem, M);
+                fence_before();
                 __syncthreads();
                 S = So;
+            }
+            if (timed_out) {
+                st = ST_TIMEOUT;
+                break;
             }
             if (rmax > EXACT_RMAX) {
                 refine_exact128(wk, sm, S, M);
@@ -1191,31 +1316,8 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                 continue;
             }
             // ---- F
-            for (int sq = 0; sq < 2 * nchunk && !timed_out; ++sq) {
-                const int slot = sq & 1;
-                const int c = (sq >> 1) + 8 * (sq & 1);
-                if (sq >= 2 && !bar_wait(sm, br, 2 + slot)) { timed_out = true; break; }
-                unsigned char *const a = sm.u.mm.t.ref.a[slot];
-                unsigned char *const b = sm.u.mm.t.ref.b[slot];
-                ref_a_tile(sm, a, c);
-                ref_b_tile(S, sm, b, c);
-                async_proxy_fence();
-                fence_before();
-                __syncthreads();
-                if (tid == 0) {
-                    fence_after();
-#pragma unroll
-                    for (int pr = 0; pr < 6; ++pr) {
-                        const uint64_t ad = smem_desc(smem_u32(a + kProdP[pr] * A_TILE));
-                        const uint64_t bd = smem_desc(smem_u32(b + kProdQ[pr] * BT_256));
-                        mma_bf16(tmem, ad, bd, idesc_bf16_m128(256), (sq == 0 && pr == 0) ? 0u : 1u);
-                    }
-                    mma_commit(&sm.bar[2 + slot]);
-                }
-                br.pend[2 + slot] = 1u;
-            }
-            if (!timed_out && (!bar_wait(sm, br, 2) || !bar_wait(sm, br, 3))) timed_out = true;
-            if (timed_out) {
+            if (!product_tc(sm, br, tmem, S, nullptr, nchunk)) {
+                timed_out = true;
                 st = ST_TIMEOUT;
                 break;
             }
