@@ -65,7 +65,6 @@ namespace {
 
 constexpr int MP = 128;                // padded width
 constexpr int NTH = 512;               // 16 warps
-constexpr int XST = MP + 1;            // row stride (float2) of X' in shared memory
 constexpr int PST = 9;                 // row stride (float2) of the panel and U buffers
 constexpr int NB = 8;                  // Gauss-Jordan panel width
 constexpr int NDG = 7;                 // digits of Gv'
@@ -87,29 +86,22 @@ struct Tc128Smem {
             alignas(128) unsigned char adg[3 * A_TILE];    // -[Re U | Im U] terms, 128 x 16
             alignas(128) unsigned char bdg[3 * BT_256];    // V terms in real form, 256 x 16
         } gj;
-        struct {
-            float2 X[MP * XST];                        // X' in true order
-            union {
-                struct {
-                    alignas(128) unsigned char a[2][NDX * A_TILE];   // X'^T digits of a K-chunk
-                    alignas(128) unsigned char b[2][NDG * BT_RES];   // Gv' digits of a K-chunk
-                } res;
-                struct {
-                    alignas(128) unsigned char a[2][NDX * A_TILE];   // X' digits of a K-chunk
-                    alignas(128) unsigned char b[2][3 * BT_256];     // S terms of a K-chunk
-                } ref;
-            } t;
-        } mm;
+        struct {                                       // residual
+            alignas(128) unsigned char lres[16][NDX * A_TILE];   // X'^T digits of every K-chunk
+            alignas(128) unsigned char b[2][NDG * BT_RES];       // Gv' digits of a K-chunk
+        } res;
+        struct {                                       // products X' S and R S
+            alignas(128) unsigned char a[2][NDX * A_TILE];
+            alignas(128) unsigned char b[2][3 * BT_256];
+        } ref;
     } u;
     double eps[MP];
-    float2 vh[2][MP];
-    float2 vl[2][MP];
     int vuni[2];
     float vch[2], vcl[2];
-    int rexp[MP];                  // Gv' row exponents
-    int cexp[MP];                  // X column exponents
-    float rmx[4][MP];              // partial row maxima of Gv'
-    float cmx[4][MP];              // partial column maxima of X
+    int rexp[MP];                  // Gv' row exponents (one bit of headroom included)
+    int cexp[MP];                  // X' column exponents, by true column
+    unsigned rmaxu[MP];            // row maxima of |Gv'| (float bits)
+    unsigned cmaxu[MP];            // column maxima of |X|, by stored column (float bits)
     int perm[MP];
     int pos[MP];
     float2 rinv[NB];
@@ -129,6 +121,7 @@ static_assert(2 * (MP / 4) * (MP / 4) <= 4 * NTH, "gv_blocks4 keeps at most 4 it
 struct Tc128Work {
     float4 Gh[(MP / 2) * MP];      // state g / Gv' (hi): column pair jp, row i at jp * MP + i
     float4 Gl[(MP / 2) * MP];      // (lo)
+    float4 Xt[(MP / 2) * MP];      // X' in true order, same layout
     float2 R[MP * MP];             // residual, row-pair layout (sidx)
     float2 S1[MP * MP];            // Neumann terms (two buffers in turn)
     float2 S2[MP * MP];
@@ -353,10 +346,11 @@ __device__ void gv_blocks4(Tc128Work &wk, const SysDev &s, int M, int q)
 // Gv (V g V^dagger or Sigma_L) + Sigma_R, elementwise, in place; zero in the
 // padding.  vmode: 0 general diagonal V, 1 V g V^dagger already formed or
 // |v|^2 = 1, 2 scalar |v|^2 (vch + vcl)
-__device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, int M, int n, int L, int vmode,
-                               const double2 *SL, const double2 *SR)
+__device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, int M, int n, int L,
+                               int vmode, const double2 *SL, const double2 *SR)
 {
     const int q = n & 1;
+    const double2 *Vd = s.V + (size_t)(q % s.Vperiod) * M * M;   // diagonal at stride M + 1
     for (int e = threadIdx.x; e < (MP / 2) * MP; e += NTH) {
         const int i = e % MP, jp = e / MP;
         const float4 h4 = wk.Gh[e], l4 = wk.Gl[e];
@@ -377,11 +371,14 @@ __device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, int M, int n, int L
                 } else if (vmode == 2) {
                     cdf_mul(gh, gl, make_float2(sm.vch[q], 0.f), make_float2(sm.vcl[q], 0.f), gh, gl);
                 } else if (vmode == 0) {
-                    float2 th, tl, vjh = sm.vh[q][j], vjl = sm.vl[q][j];
-                    vjh.y = -vjh.y;
-                    vjl.y = -vjl.y;
+                    const double2 vi = Vd[(size_t)i * (M + 1)], vj = Vd[(size_t)j * (M + 1)];
+                    float2 vih, vil, vjh, vjl, th, tl;
+                    to_df(vi.x, vih.x, vil.x);
+                    to_df(vi.y, vih.y, vil.y);
+                    to_df(vj.x, vjh.x, vjl.x);
+                    to_df(-vj.y, vjh.y, vjl.y);
                     cdf_mul(gh, gl, vjh, vjl, th, tl);
-                    cdf_mul(sm.vh[q][i], sm.vl[q][i], th, tl, gh, gl);
+                    cdf_mul(vih, vil, th, tl, gh, gl);
                 }
                 if (n == L - 1) {
                     const double2 v = SR[(size_t)i * M + j];
@@ -454,7 +451,7 @@ __device__ void x_to_tmem(const Tc128Work &wk, Tc128Smem &sm, uint32_t tmem, int
         tmem_st16(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 16 * gi, v);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    sm.rmx[cg][i] = mx;
+    atomicMax(&sm.rmaxu[i], __float_as_uint(mx));
 }
 
 // ---------------------------------------------------------------------------
@@ -667,21 +664,23 @@ __device__ int gj_tmem(Tc128Smem &sm, uint32_t tmem, int M, Bars &br)
 }
 
 // ---------------------------------------------------------------------------
-// C. X (permuted) from tensor memory into shared memory in true order, the
-//    column exponents, and X' = X rounded to three digits per column
+// C. X' from the permuted X in tensor memory (A^-1[pos[i]][perm[c]] =
+//    X[i][c]): column exponents, then per element the three digits at the
+//    column scale, written straight into the residual's A tiles (row j =
+//    true column, K = true row; chunk = part * 8 + row / 16) and X' itself
+//    in true order into the workspace
 
-__device__ void x_from_tmem(Tc128Smem &sm, uint32_t tmem, int M)
+__device__ void x_prime_from_tmem(Tc128Smem &sm, Tc128Work &wk, uint32_t tmem, int M)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int k = tid; k < MP; k += NTH) {
         if (k >= M) sm.perm[k] = k;
+        sm.cmaxu[k] = 0u;
     }
     __syncthreads();
     for (int k = tid; k < MP; k += NTH) sm.pos[sm.perm[k]] = k;
-    __syncthreads();
     const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
-    const int ti = sm.pos[i];
-    float2 *const X = sm.u.mm.X;
+    // column maxima over the stored rows (warp reductions, then across quarters)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         uint32_t v[32];
@@ -689,66 +688,51 @@ __device__ void x_from_tmem(Tc128Smem &sm, uint32_t tmem, int M)
         wait_ld();
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-            const int sc = 32 * cg + 16 * h + c;
-            X[ti * XST + sm.perm[sc]] = make_float2(__uint_as_float(v[2 * c]), __uint_as_float(v[2 * c + 1]));
+            const float m = fmaxf(fabsf(__uint_as_float(v[2 * c])), fabsf(__uint_as_float(v[2 * c + 1])));
+            const unsigned mu = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+            if (lane == c) atomicMax(&sm.cmaxu[32 * cg + 16 * h + c], mu);
         }
-    }
-    fence_before();
-    __syncthreads();
-    // column maxima: thread (part, j) scans rows 32 part .. + 31 of column j
-    {
-        const int j = tid & (MP - 1), part = tid >> 7;
-        float mx = 0.f;
-        for (int r = 32 * part; r < 32 * part + 32; ++r) {
-            const float2 x = X[r * XST + j];
-            mx = fmaxf(mx, fmaxf(fabsf(x.x), fabsf(x.y)));
-        }
-        sm.cmx[part][j] = mx;
     }
     __syncthreads();
     if (tid < MP) {
-        const float mx = fmaxf(fmaxf(sm.cmx[0][tid], sm.cmx[1][tid]), fmaxf(sm.cmx[2][tid], sm.cmx[3][tid]));
-        sm.cexp[tid] = scale_exp(mx) + 1;   // one bit of headroom: |digits| <= 128
-        const float rm = fmaxf(fmaxf(sm.rmx[0][tid], sm.rmx[1][tid]), fmaxf(sm.rmx[2][tid], sm.rmx[3][tid]));
-        sm.rexp[tid] = scale_exp(rm) + 1;
+        sm.cexp[sm.perm[tid]] = scale_exp(__uint_as_float(sm.cmaxu[tid])) + 1;   // |digits| <= 128
+        sm.rexp[tid] = scale_exp(__uint_as_float(sm.rmaxu[tid])) + 1;
     }
     __syncthreads();
-    // X' = X rounded to three digits at the column scale (exact in fp32)
-    for (int e = tid; e < MP * MP; e += NTH) {
-        const int r = e >> 7, j = e & (MP - 1);
-        const int ce = sm.cexp[j];
-        const float dn = pow2f(-ce), up = pow2f(ce - 8);
-        float2 x = X[r * XST + j];
-        float d[NDX];
-        digits3(x.x, dn, d);
-        x.x = (d[0] + d[1] + d[2]) * up;
-        digits3(x.y, dn, d);
-        x.y = (d[0] + d[1] + d[2]) * up;
-        X[r * XST + j] = x;
+    float2 *const xt = reinterpret_cast<float2 *>(wk.Xt);
+    const int ti = sm.pos[i];
+    unsigned char *const tre = sm.u.res.lres[ti >> 4];       // real part: chunk ti / 16
+    unsigned char *const tim = sm.u.res.lres[8 + (ti >> 4)]; // imaginary part
+    const int kk = ti & 15;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
+        wait_ld();
+#pragma unroll 4
+        for (int c = 0; c < 16; ++c) {
+            const int j = sm.perm[32 * cg + 16 * h + c];
+            const int ce = sm.cexp[j];
+            const float dn = pow2f(-ce), up = pow2f(ce - 8);
+            float dr[NDX], di[NDX];
+            digits3(__uint_as_float(v[2 * c]), dn, dr);
+            digits3(__uint_as_float(v[2 * c + 1]), dn, di);
+            const int off = tile_off(j, kk);
+#pragma unroll
+            for (int q = 0; q < NDX; ++q) {
+                *reinterpret_cast<__nv_bfloat16 *>(tre + q * A_TILE + off) = __float2bfloat16_rn(dr[q]);
+                *reinterpret_cast<__nv_bfloat16 *>(tim + q * A_TILE + off) = __float2bfloat16_rn(di[q]);
+            }
+            xt[((j >> 1) * MP + ti) * 2 + (j & 1)] =
+                make_float2((dr[0] + dr[1] + dr[2]) * up, (di[0] + di[1] + di[2]) * up);
+        }
     }
+    fence_before();
     __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
 // D. the residual R = I + Gv' X' (transposed on the tensor cores)
-
-// A tile of chunk c: row j, K kk = digits of X'[k][j] (k = 16 (c % 8) + kk),
-// real part for c < 8, imaginary part for c >= 8
-__device__ void res_a_tile(const Tc128Smem &sm, unsigned char *a, int c)
-{
-    const float2 *X = sm.u.mm.X;
-    const int part = c >> 3, k0 = 16 * (c & 7);
-    for (int e = threadIdx.x; e < MP * 8; e += NTH) {
-        const int j = e & (MP - 1), kk = (e >> 7) * 2;
-        const float dn = pow2f(-sm.cexp[j]);
-        const float2 x0 = X[(k0 + kk) * XST + j], x1 = X[(k0 + kk + 1) * XST + j];
-        float d0[NDX], d1[NDX];
-        digits3(part ? x0.y : x0.x, dn, d0);
-        digits3(part ? x1.y : x1.x, dn, d1);
-#pragma unroll
-        for (int q = 0; q < NDX; ++q) put_bf16x2(a + q * A_TILE, j, kk, d0[q], d1[q]);
-    }
-}
 
 // B tiles of chunk c (rows 2i' = Gr, 2i' + 1 = Gi of Gv' rows i = 32 pass + i',
 // K = k - 16 c) from the double-float Gv' in the workspace, seven digits
@@ -873,10 +857,10 @@ __device__ float res_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem,
 // items e = tid, tid + NTH
 struct ProdPre {
     float4 s[2];      // (k, j), (k + 1, j) of S for B item e: j = e % 128, kk = 2 (e / 128)
-    float2 r[2][2];   // R[i][k], R[i][k + 1] for A item e: kk = 2 (e % 8), i = e / 8
+    float4 a[2];      // (i, k), (i, k + 1) of X' or R for A item e: kk = 2 (e % 8), i = e / 8
 };
 
-KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, int c)
+KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, const float4 *Xt, int c)
 {
     const int k0 = 16 * (c & 7);
     ProdPre q;
@@ -885,28 +869,30 @@ KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, int c)
         const int e = threadIdx.x + h * NTH;
         const int j = e & (MP - 1), kk = (e >> 7) * 2;
         q.s[h] = *reinterpret_cast<const float4 *>(S + sidx(k0 + kk, j));
+        const int ka = (e & 7) * 2, i = e >> 3;
         if (R) {
-            const int ka = (e & 7) * 2, i = e >> 3;
-            q.r[h][0] = R[sidx(i, k0 + ka)];
-            q.r[h][1] = R[sidx(i, k0 + ka + 1)];
+            const float2 r0 = R[sidx(i, k0 + ka)], r1 = R[sidx(i, k0 + ka + 1)];
+            q.a[h] = make_float4(r0.x, r0.y, r1.x, r1.y);
+        } else {
+            q.a[h] = Xt[((k0 + ka) >> 1) * MP + i];
         }
     }
     return q;
 }
 
 // A tile from X' (digits, at the column scale of X'; the scale goes into B)
-__device__ void prod_a_x(const Tc128Smem &sm, unsigned char *a, int c)
+KNIT_DEV void prod_a_x(const ProdPre &q, const Tc128Smem &sm, unsigned char *a, int c)
 {
-    const float2 *X = sm.u.mm.X;
     const int part = c >> 3, k0 = 16 * (c & 7);
-    for (int e = threadIdx.x; e < MP * 8; e += NTH) {
-        const int kk = (e & 7) * 2, i = e >> 3;
-        const float2 x0 = X[i * XST + k0 + kk], x1 = X[i * XST + k0 + kk + 1];
-        float d0[NDX], d1[NDX];
-        digits3(part ? x0.y : x0.x, pow2f(-sm.cexp[k0 + kk]), d0);
-        digits3(part ? x1.y : x1.x, pow2f(-sm.cexp[k0 + kk + 1]), d1);
 #pragma unroll
-        for (int q = 0; q < NDX; ++q) put_bf16x2(a + q * A_TILE, i, kk, d0[q], d1[q]);
+    for (int h = 0; h < 2; ++h) {
+        const int e = threadIdx.x + h * NTH;
+        const int kk = (e & 7) * 2, i = e >> 3;
+        float d0[NDX], d1[NDX];
+        digits3(part ? q.a[h].y : q.a[h].x, pow2f(-sm.cexp[k0 + kk]), d0);
+        digits3(part ? q.a[h].w : q.a[h].z, pow2f(-sm.cexp[k0 + kk + 1]), d1);
+#pragma unroll
+        for (int qq = 0; qq < NDX; ++qq) put_bf16x2(a + qq * A_TILE, i, kk, d0[qq], d1[qq]);
     }
 }
 
@@ -918,8 +904,8 @@ KNIT_DEV void prod_a_r(const ProdPre &q, unsigned char *a, int c)
     for (int h = 0; h < 2; ++h) {
         const int e = threadIdx.x + h * NTH;
         const int kk = (e & 7) * 2, i = e >> 3;
-        const float v0 = part ? q.r[h][0].y : q.r[h][0].x;
-        const float v1 = part ? q.r[h][1].y : q.r[h][1].x;
+        const float v0 = part ? q.a[h].y : q.a[h].x;
+        const float v1 = part ? q.a[h].w : q.a[h].z;
         uint32_t h0, m0, l0, h1, m1, l1;
         bf16_split3(v0, h0, m0, l0);
         bf16_split3(v1, h1, m1, l1);
@@ -966,11 +952,11 @@ KNIT_DEV void prod_b(const ProdPre &q, const Tc128Smem &sm, unsigned char *b, in
 }
 
 // g = X' + D into the state: lane i of quarter qd, complex columns 32 cg ..
-__device__ void ref_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem, int M)
+__device__ void ref_readback(Tc128Work &wk, uint32_t tmem, int M)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
-    const float2 *X = sm.u.mm.X;
+    const float2 *X = reinterpret_cast<const float2 *>(wk.Xt);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         uint32_t v[32];
@@ -982,7 +968,7 @@ __device__ void ref_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem, 
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
                 const int c = 2 * cp + s2, j = 32 * cg + 16 * h + c;
-                const float2 x = X[i * XST + j];
+                const float2 x = X[((j >> 1) * MP + i) * 2 + (j & 1)];
                 if (i < M && j < M) {
                     two_sum(x.x, __uint_as_float(v[2 * c]), oh[s2].x, ol[s2].x);
                     two_sum(x.y, __uint_as_float(v[2 * c + 1]), oh[s2].y, ol[s2].y);
@@ -1026,18 +1012,18 @@ __device__ void neumann_readback(const float2 *R, float2 *So, uint32_t tmem, int
 // rewrites the slot, and the next K range's loads are issued a chunk ahead.
 // Returns false when a wait ran out (the commits in flight stay recorded).
 __device__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, const float2 *S,
-                           const float2 *R, int nchunk)
+                           const float2 *R, const float4 *Xt, int nchunk)
 {
     const int nseq = 2 * nchunk;
-    ProdPre cur = prod_load(S, R, 0), nxt = cur;
+    ProdPre cur = prod_load(S, R, Xt, 0), nxt = cur;
     for (int sq = 0; sq < nseq; ++sq) {
         const int slot = sq & 1, c = (sq >> 1) + 8 * (sq & 1);
         const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
-        if ((sq & 1) == 0 && sq + 2 < nseq) nxt = prod_load(S, R, (sq >> 1) + 1);
-        unsigned char *const a = sm.u.mm.t.ref.a[slot];
-        unsigned char *const b = sm.u.mm.t.ref.b[slot];
+        if ((sq & 1) == 0 && sq + 2 < nseq) nxt = prod_load(S, R, Xt, (sq >> 1) + 1);
+        unsigned char *const a = sm.u.ref.a[slot];
+        unsigned char *const b = sm.u.ref.b[slot];
         if (R) prod_a_r(cur, a, c);
-        else prod_a_x(sm, a, c);
+        else prod_a_x(cur, sm, a, c);
         prod_b(cur, sm, b, c, R == nullptr);
         async_proxy_fence();
         fence_before();
@@ -1066,9 +1052,9 @@ __device__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, const float2 
 // E. the rare paths on the CUDA cores (workspace operands)
 
 // g = X' + X' S with X' S accumulated error-free (TwoProduct + TwoSum)
-__device__ void refine_exact128(Tc128Work &wk, const Tc128Smem &sm, const float2 *S, int M)
+__device__ void refine_exact128(Tc128Work &wk, const float2 *S, int M)
 {
-    const float2 *X = sm.u.mm.X;
+    const float2 *X = reinterpret_cast<const float2 *>(wk.Xt);
     float2 *const gh = reinterpret_cast<float2 *>(wk.Gh);
     float2 *const gl = reinterpret_cast<float2 *>(wk.Gl);
     for (int e = threadIdx.x; e < MP * MP; e += NTH) {
@@ -1081,13 +1067,13 @@ __device__ void refine_exact128(Tc128Work &wk, const Tc128Smem &sm, const float2
         }
         float2 sh = make_float2(0.f, 0.f), se = make_float2(0.f, 0.f);
         for (int k = 0; k < M; ++k) {
-            const float2 xa = X[i * XST + k], sb = S[sidx(k, j)];
+            const float2 xa = X[((k >> 1) * MP + i) * 2 + (k & 1)], sb = S[sidx(k, j)];
             dot2_acc1(xa.x, sb.x, sh.x, se.x);
             dot2_acc1(-xa.y, sb.y, sh.x, se.x);
             dot2_acc1(xa.x, sb.y, sh.y, se.y);
             dot2_acc1(xa.y, sb.x, sh.y, se.y);
         }
-        const float2 xv = X[i * XST + j];
+        const float2 xv = X[((j >> 1) * MP + i) * 2 + (j & 1)];
         float hx, lx, hy, ly;
         two_sum(xv.x, sh.x, hx, lx);
         lx += se.x;
@@ -1177,16 +1163,6 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
         const int M = s.M, L = s.L, vb = s.vb;
         const size_t MM = (size_t)M * M;
         if (reload) {
-            for (int q = 0; q < 2; ++q)
-                for (int i = tid; i < MP; i += NTH) {
-                    double2 v = make_double2(0.0, 0.0);
-                    if (i < M) v = s.V[(size_t)(q % s.Vperiod) * MM + (size_t)i * M + i];
-                    float hx, lx, hy, ly;
-                    to_df(v.x, hx, lx);
-                    to_df(v.y, hy, ly);
-                    sm.vh[q][i] = make_float2(hx, hy);
-                    sm.vl[q][i] = make_float2(lx, ly);
-                }
             if (tid < 2) {
                 if (vb == 1)
                     classify_vdiag(s.V + (size_t)(tid % s.Vperiod) * MM, M + 1, M, sm.vuni[tid],
@@ -1203,13 +1179,14 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
         for (int n = 0; n < L && st == ST_OK; ++n) {
             // ---- A
             slice_diag<MP, NTH>(sm.eps, s, ip.ms, ip.W, ip.E, n);
+            for (int i = tid; i < MP; i += NTH) sm.rmaxu[i] = 0u;
             if (vb == 4 && n > 0) {
                 gv_blocks4(wk, s, M, n & 1);
                 __syncthreads();
             }
             const int q = n & 1;
             const int vmode = vb == 4 ? 1 : (sm.vuni[q] == 1 ? 1 : (sm.vuni[q] == 2 ? 2 : 0));
-            gv_elementwise(wk, sm, M, n, L, vmode, ip.SL, ip.SR);
+            gv_elementwise(wk, sm, s, M, n, L, vmode, ip.SL, ip.SR);
             __syncthreads();
             gv_add_h0(wk, sm, s, M);
             __syncthreads();
@@ -1225,7 +1202,7 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                 break;
             }
             // ---- C
-            x_from_tmem(sm, tmem, M);
+            x_prime_from_tmem(sm, wk, tmem, M);
             // ---- D
             float rloc = 0.f;
             const int nchunk = (M + 15) / 16;          // K-chunks per part
@@ -1239,11 +1216,10 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                     // every thread waits for the MMAs that last read this slot
                     const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
                     if ((sq & 1) == 0 && sq + 2 < nseq) nxt = res_b_load(wk, pass, (sq >> 1) + 1);
-                    unsigned char *const a = sm.u.mm.t.res.a[slot];
-                    unsigned char *const b = sm.u.mm.t.res.b[slot];
-                    res_a_tile(sm, a, c);
+                    const unsigned char *const a = sm.u.res.lres[c];
+                    unsigned char *const b = sm.u.res.b[slot];
                     if ((sq & 1) == 0) res_b_build(cur, sm, b, pass);
-                    else res_b_swap(sm.u.mm.t.res.b[slot ^ 1], b);
+                    else res_b_swap(sm.u.res.b[slot ^ 1], b);
                     async_proxy_fence();
                     fence_before();
                     if (__syncthreads_or(!ok)) { timed_out = true; break; }
@@ -1299,7 +1275,7 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             for (int t = 0; t < nx && !timed_out; ++t) {
                 // S <- R + R S on the tensor cores
                 float2 *const So = (t & 1) ? wk.S2 : wk.S1;
-                if (!product_tc(sm, br, tmem, S, wk.R, nchunk)) { timed_out = true; break; }
+                if (!product_tc(sm, br, tmem, S, wk.R, wk.Xt, nchunk)) { timed_out = true; break; }
                 fence_after();
                 neumann_readback(wk.R, So, tmem, M);
                 fence_before();
@@ -1311,18 +1287,18 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                 break;
             }
             if (rmax > EXACT_RMAX) {
-                refine_exact128(wk, sm, S, M);
+                refine_exact128(wk, S, M);
                 __syncthreads();
                 continue;
             }
             // ---- F
-            if (!product_tc(sm, br, tmem, S, nullptr, nchunk)) {
+            if (!product_tc(sm, br, tmem, S, nullptr, wk.Xt, nchunk)) {
                 timed_out = true;
                 st = ST_TIMEOUT;
                 break;
             }
             fence_after();
-            ref_readback(wk, sm, tmem, M);
+            ref_readback(wk, tmem, M);
             fence_before();
             __syncthreads();
         }
