@@ -628,8 +628,9 @@ __device__ int gj_tmem(Tc128Smem &sm, uint32_t tmem, int M, Bars &br)
         fence_before();
         __syncthreads();
         // 5. the update X -= U V: the next panel's 16 columns first (bar 0),
-        //    then the rest of the touched columns (bar 1)
-        if (tid == 0) {
+        //    then the rest of the touched columns (bar 1); issued from warp 4,
+        //    so that the pivot warp is not held while the MMA queue drains
+        if (tid == 128) {
             fence_after();
             const int K2 = K + NB;
             auto issue = [&](int c0, int ncol) {   // tensor-memory columns c0 .. c0 + ncol - 1
@@ -657,7 +658,7 @@ __device__ int gj_tmem(Tc128Smem &sm, uint32_t tmem, int M, Bars &br)
     }
     if (st == ST_OK) {
         // the last update complete before anyone reads X
-        if (!bar_wait(sm, br, 1)) st = ST_TIMEOUT;
+        if (!bar_wait(sm, br, 1)) st = ST_TIMEOUT;   // polled by thread 0, shared by the block
         fence_after();
     }
     return st;
@@ -736,17 +737,29 @@ __device__ void x_prime_from_tmem(Tc128Smem &sm, Tc128Work &wk, uint32_t tmem, i
 
 // B tiles of chunk c (rows 2i' = Gr, 2i' + 1 = Gi of Gv' rows i = 32 pass + i',
 // K = k - 16 c) from the double-float Gv' in the workspace, seven digits
-// side by side (digit p at p * BT_RES).  Work item = thread: (i', k pair,
-// part), i' fastest so that the Gv' reads coalesce; the loads (one float4
-// of hi and one of lo: (i, k) and (i, k + 1)) are issued a chunk ahead.
+// side by side (digit p at p * BT_RES).  Work item = thread: warp w takes
+// tile rows 8 (w % 8) .. + 7 and K pairs 4 (w / 8) .. + 3, lane l row
+// l / 4 and K pair l % 4 of those, so that a warp's 32 four-byte stores fill
+// 128 contiguous bytes (no bank conflicts); tile row r = 2 i' + part.  The
+// loads (one float4 of hi and one of lo: (i, k) and (i, k + 1)) are issued
+// a chunk ahead.
 struct GvPre {
     float4 h, l;
 };
 
+KNIT_DEV void res_b_item(int &ip, int &kk, int &part)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int r = 8 * (w & 7) + (l >> 2);
+    ip = r >> 1;
+    part = r & 1;
+    kk = 2 * ((l & 3) + 4 * (w >> 3));
+}
+
 KNIT_DEV GvPre res_b_load(const Tc128Work &wk, int pass, int c)
 {
-    const int e = threadIdx.x;
-    const int ip = e & 31, kk = ((e >> 5) & 7) * 2;
+    int ip, kk, part;
+    res_b_item(ip, kk, part);
     const int i = 32 * pass + ip, k = 16 * (c & 7) + kk;
     const int f = (k >> 1) * MP + i;
     GvPre g;
@@ -757,8 +770,8 @@ KNIT_DEV GvPre res_b_load(const Tc128Work &wk, int pass, int c)
 
 __device__ void res_b_build(const GvPre &g, const Tc128Smem &sm, unsigned char *b, int pass)
 {
-    const int e = threadIdx.x;
-    const int ip = e & 31, kk = ((e >> 5) & 7) * 2, part = e >> 8;
+    int ip, kk, part;
+    res_b_item(ip, kk, part);
     const float dn = pow2f(-sm.rexp[32 * pass + ip]);
     float dg0[NDG], dg1[NDG];
     digits7(part ? g.h.y : g.h.x, part ? g.l.y : g.l.x, dn, dg0);
@@ -856,25 +869,50 @@ __device__ float res_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem,
 // values of S (and of R for a Neumann term) one work item per thread half:
 // items e = tid, tid + NTH
 struct ProdPre {
-    float4 s[2];      // (k, j), (k + 1, j) of S for B item e: j = e % 128, kk = 2 (e / 128)
-    float4 a[2];      // (i, k), (i, k + 1) of X' or R for A item e: kk = 2 (e % 8), i = e / 8
+    float4 s[4];      // (k, j), (k + 1, j) of S for the thread's four B items
+    float4 a[2];      // (i, k), (i, k + 1) of X' or R for the thread's two A items
 };
+
+// B item h of a thread (4 per thread, 2048 per chunk): tile row 2j + sub and
+// K pair kp; a warp's 32 four-byte stores cover 8 consecutive tile rows
+// (four columns j, both parities) x 4 K pairs = 128 contiguous bytes
+KNIT_DEV void prod_b_item(int h, int &j, int &sub, int &kp)
+{
+    const int e = threadIdx.x + h * NTH, l = e & 31, w = e >> 5;   // w = 0 .. 63
+    j = 4 * (w & 31) + (l >> 3);
+    sub = (l >> 2) & 1;
+    kp = (l & 3) + 4 * (w >> 5);
+}
+
+// A item h (2 per thread): tile row i, K pair kp; a warp covers 8 rows x 4
+// K pairs (conflict-free), the two items the two K halves
+KNIT_DEV void prod_a_item(int h, int &i, int &kp)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    i = 8 * w + (l >> 2);
+    kp = (l & 3) + 4 * h;
+}
 
 KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, const float4 *Xt, int c)
 {
     const int k0 = 16 * (c & 7);
     ProdPre q;
 #pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        int j, sub, kp;
+        prod_b_item(h, j, sub, kp);
+        q.s[h] = *reinterpret_cast<const float4 *>(S + sidx(k0 + 2 * kp, j));
+    }
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int e = threadIdx.x + h * NTH;
-        const int j = e & (MP - 1), kk = (e >> 7) * 2;
-        q.s[h] = *reinterpret_cast<const float4 *>(S + sidx(k0 + kk, j));
-        const int ka = (e & 7) * 2, i = e >> 3;
+        int i, kp;
+        prod_a_item(h, i, kp);
+        const int k = k0 + 2 * kp;
         if (R) {
-            const float2 r0 = R[sidx(i, k0 + ka)], r1 = R[sidx(i, k0 + ka + 1)];
+            const float2 r0 = R[sidx(i, k)], r1 = R[sidx(i, k + 1)];
             q.a[h] = make_float4(r0.x, r0.y, r1.x, r1.y);
         } else {
-            q.a[h] = Xt[((k0 + ka) >> 1) * MP + i];
+            q.a[h] = Xt[(k >> 1) * MP + i];
         }
     }
     return q;
@@ -886,8 +924,9 @@ KNIT_DEV void prod_a_x(const ProdPre &q, const Tc128Smem &sm, unsigned char *a, 
     const int part = c >> 3, k0 = 16 * (c & 7);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int e = threadIdx.x + h * NTH;
-        const int kk = (e & 7) * 2, i = e >> 3;
+        int i, kp;
+        prod_a_item(h, i, kp);
+        const int kk = 2 * kp;
         float d0[NDX], d1[NDX];
         digits3(part ? q.a[h].y : q.a[h].x, pow2f(-sm.cexp[k0 + kk]), d0);
         digits3(part ? q.a[h].w : q.a[h].z, pow2f(-sm.cexp[k0 + kk + 1]), d1);
@@ -902,8 +941,9 @@ KNIT_DEV void prod_a_r(const ProdPre &q, unsigned char *a, int c)
     const int part = c >> 3;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int e = threadIdx.x + h * NTH;
-        const int kk = (e & 7) * 2, i = e >> 3;
+        int i, kp;
+        prod_a_item(h, i, kp);
+        const int kk = 2 * kp;
         const float v0 = part ? q.a[h].y : q.a[h].x;
         const float v1 = part ? q.a[h].w : q.a[h].z;
         uint32_t h0, m0, l0, h1, m1, l1;
@@ -916,35 +956,28 @@ KNIT_DEV void prod_a_r(const ProdPre &q, unsigned char *a, int c)
     }
 }
 
-// B tile from S, scaled by 2^(t_k - 8) when A holds the X' digits
+// B tile from S, scaled by 2^(t_k - 8) when A holds the X' digits:
+// row 2j = [Re | -Im], row 2j + 1 = [Im | Re] of column j of S
 KNIT_DEV void prod_b(const ProdPre &q, const Tc128Smem &sm, unsigned char *b, int c, bool scaled)
 {
     const int part = c >> 3, k0 = 16 * (c & 7);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int e = threadIdx.x + h * NTH;
-        const int j = e & (MP - 1), kk = (e >> 7) * 2, k = k0 + kk;
+    for (int h = 0; h < 4; ++h) {
+        int j, sub, kp;
+        prod_b_item(h, j, sub, kp);
+        const int kk = 2 * kp, k = k0 + kk;
         const float4 sv = q.s[h];
         const float u0 = scaled ? pow2f(sm.cexp[k] - 8) : 1.f;
         const float u1 = scaled ? pow2f(sm.cexp[k + 1] - 8) : 1.f;
-        float r0, r1, c0, c1;   // rows 2j and 2j + 1 at K positions k, k + 1
-        if (part == 0) {
-            r0 = sv.x * u0; r1 = sv.z * u1;      // Re
-            c0 = sv.y * u0; c1 = sv.w * u1;      // Im
-        } else {
-            r0 = -sv.y * u0; r1 = -sv.w * u1;    // -Im
-            c0 = sv.x * u0; c1 = sv.z * u1;      // Re
-        }
+        // (part, sub): (0, 0) Re, (0, 1) Im, (1, 0) -Im, (1, 1) Re
+        const bool re = (part ^ sub) == 0;
+        const float sg = (part == 1 && sub == 0) ? -1.f : 1.f;
+        const float v0 = sg * (re ? sv.x : sv.y) * u0;
+        const float v1 = sg * (re ? sv.z : sv.w) * u1;
         uint32_t h0, m0, l0, h1, m1, l1;
-        bf16_split3(r0, h0, m0, l0);
-        bf16_split3(r1, h1, m1, l1);
-        unsigned char *p = b + tile_off(2 * j, kk);
-        *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
-        *reinterpret_cast<uint32_t *>(p + BT_256) = pack_hi16(m0, m1);
-        *reinterpret_cast<uint32_t *>(p + 2 * BT_256) = pack_hi16(l0, l1);
-        bf16_split3(c0, h0, m0, l0);
-        bf16_split3(c1, h1, m1, l1);
-        p = b + tile_off(2 * j + 1, kk);
+        bf16_split3(v0, h0, m0, l0);
+        bf16_split3(v1, h1, m1, l1);
+        unsigned char *p = b + tile_off(2 * j + sub, kk);
         *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
         *reinterpret_cast<uint32_t *>(p + BT_256) = pack_hi16(m0, m1);
         *reinterpret_cast<uint32_t *>(p + 2 * BT_256) = pack_hi16(l0, l1);
