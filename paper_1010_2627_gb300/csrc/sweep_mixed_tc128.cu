@@ -80,7 +80,11 @@ __constant__ int kProdQ[6] = {0, 1, 2, 0, 1, 0};
 struct Tc128Smem {
     union {
         struct {                                       // Gauss-Jordan
-            float2 pan[MP * PST];                      // panel columns (relay out of TMEM)
+            struct {
+                unsigned key;                          // the warp's best pivot key
+                unsigned pad;
+                float2 row[NB];                        // that row's panel entries
+            } cand[2][4];                              // per step parity, per lane-quarter warp
             float2 U[MP * PST];                        // u vectors of the panel
             float2 prow[NB * MP];                      // pivot rows at the start of the panel
             alignas(128) unsigned char adg[3 * A_TILE];    // -[Re U | Im U] terms, 128 x 16
@@ -459,93 +463,73 @@ __device__ void x_to_tmem(const Tc128Work &wk, Tc128Smem &sm, uint32_t tmem, int
 
 __device__ int gj_tmem(Tc128Smem &sm, uint32_t tmem, int M, Bars &br)
 {
-    constexpr int R2 = MP / 32, IB = 7;
+    constexpr int IB = 7;
     constexpr unsigned IMASK = (1u << IB) - 1u, FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Mp = (M + NB - 1) / NB * NB;   // columns that the updates touch
     const int NP = Mp / NB;
-    bool open[R2];
-#pragma unroll
-    for (int t = 0; t < R2; ++t) open[t] = lane + 32 * t < M;
+    // warps 0 .. 3 own the rows of their tensor-memory lane quarter
+    const int myrow = 32 * (warp & 3) + lane;
+    bool open = warp < 4 && myrow < M;   // the row may still become a pivot row
     int st = ST_OK;
     for (int P = 0; P < NP; ++P) {
         const int K = P * NB, nk = min(NB, M - K);
-        // 1. the panel columns out of tensor memory (after the previous
-        //    panel's first MMAs), relayed through shared memory to warp 0
         bool to0 = false;   // the wait for the previous panel's first MMAs ran out
+        // 1-2. the pivot steps, spread over the four lane-quarter warps: each
+        //      lane holds its own row's panel entries (out of tensor memory,
+        //      after the previous panel's first MMAs); per step every warp
+        //      posts its best candidate (key and row) and one 128-thread
+        //      barrier lets all four agree on the pivot
         if (warp < 4) {
             if (P > 0) to0 = !mbar_wait(&sm.bar[0], br.ph[0]);
             fence_after();
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 2 * K, v);
-            wait_ld();
-            const int i = 32 * warp + lane;
+            float2 pc[NB];
+            {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 2 * K, v);
+                wait_ld();
 #pragma unroll
-            for (int c = 0; c < NB; ++c)
-                sm.u.gj.pan[i * PST + c] = make_float2(__uint_as_float(v[2 * c]), __uint_as_float(v[2 * c + 1]));
-            fence_before();
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-        }
-        // 2. the pivot steps (warp 0)
-        if (warp == 0) {
-            float2 pc[R2][NB];
-#pragma unroll
-            for (int t = 0; t < R2; ++t)
-#pragma unroll
-                for (int c = 0; c < NB; ++c) pc[t][c] = sm.u.gj.pan[(lane + 32 * t) * PST + c];
+                for (int c = 0; c < NB; ++c) pc[c] = make_float2(__uint_as_float(v[2 * c]), __uint_as_float(v[2 * c + 1]));
+            }
             bool bad = to0;
 #pragma unroll
             for (int kk = 0; kk < NB; ++kk) {
                 if (kk < nk) {
-                    unsigned key = 0u;
+                    const unsigned kt = open ? ((__float_as_uint(cabs1f(pc[kk])) & ~IMASK) |
+                                                (IMASK - (unsigned)myrow))
+                                             : 0u;
+                    const unsigned wmax = __reduce_max_sync(FULL, kt);
+                    auto &slot = sm.u.gj.cand[kk & 1][warp];
+                    if (lane == 0) slot.key = wmax;
+                    if (wmax != 0u && kt == wmax)
 #pragma unroll
-                    for (int t = 0; t < R2; ++t) {
-                        const unsigned kt = (__float_as_uint(cabs1f(pc[t][kk])) & ~IMASK) |
-                                            (IMASK - (unsigned)(lane + 32 * t));
-                        key = max(key, open[t] ? kt : 0u);
-                    }
-                    key = __reduce_max_sync(FULL, key);
-                    bad |= (key & ~IMASK) == 0u;
-                    const int p = (int)(IMASK - (key & IMASK)), pl = p & 31, pt = p >> 5;
-                    // the pivot row's remaining panel entries, from lane p % 32
+                        for (int c = kk; c < NB; ++c) slot.row[c] = pc[c];
+                    asm volatile("bar.sync 2, 128;" ::: "memory");
+                    unsigned best = sm.u.gj.cand[kk & 1][0].key;
+#pragma unroll
+                    for (int w2 = 1; w2 < 4; ++w2) best = max(best, sm.u.gj.cand[kk & 1][w2].key);
+                    bad |= (best & ~IMASK) == 0u;
+                    const int p = (int)(IMASK - (best & IMASK));
+                    const auto &win = sm.u.gj.cand[kk & 1][(p >> 5) & 3];
                     float2 prow[NB];
 #pragma unroll
-                    for (int c = kk; c < NB; ++c) {
-                        float2 own = pc[0][c];
-#pragma unroll
-                        for (int t = 1; t < R2; ++t) own = t == pt ? pc[t][c] : own;
-                        prow[c] = make_float2(__shfl_sync(FULL, own.x, pl), __shfl_sync(FULL, own.y, pl));
-                    }
+                    for (int c = kk; c < NB; ++c) prow[c] = win.row[c];
                     const float2 rinv = crcp_fastf(prow[kk]);
-                    float2 u[R2];
+                    float2 u = pc[kk];
+                    u.x -= myrow == p ? 1.f : 0.f;
 #pragma unroll
-                    for (int t = 0; t < R2; ++t) {
-                        u[t] = pc[t][kk];
-                        u[t].x -= lane + 32 * t == p ? 1.f : 0.f;
-                    }
-#pragma unroll
-                    for (int c = kk + 1; c < NB; ++c) {
-                        const float2 vk = cmulf(prow[c], rinv);
-#pragma unroll
-                        for (int t = 0; t < R2; ++t) pc[t][c] = cfmsf(u[t], vk, pc[t][c]);
-                    }
-#pragma unroll
-                    for (int t = 0; t < R2; ++t) {
-                        const int i = lane + 32 * t;
-                        sm.u.gj.U[i * PST + kk] = u[t];
-                        open[t] = open[t] && i != p;
-                    }
-                    if (lane == 0) {
+                    for (int c = kk + 1; c < NB; ++c) pc[c] = cfmsf(u, cmulf(prow[c], rinv), pc[c]);
+                    sm.u.gj.U[myrow * PST + kk] = u;
+                    open = open && myrow != p;
+                    if (warp == 0 && lane == 0) {
                         sm.perm[K + kk] = p;
                         sm.rinv[kk] = rinv;
                     }
                 }
             }
             // steps a partial panel does not take contribute nothing
-            for (int kk = nk; kk < NB; ++kk)
-#pragma unroll
-                for (int t = 0; t < R2; ++t) sm.u.gj.U[(lane + 32 * t) * PST + kk] = make_float2(0.f, 0.f);
-            if (lane == 0) sm.flag = bad ? 1 : 0;
+            for (int kk = nk; kk < NB; ++kk) sm.u.gj.U[myrow * PST + kk] = make_float2(0.f, 0.f);
+            if (warp == 0 && lane == 0) sm.flag = bad ? 1 : 0;
         }
         // 3. X at the start of the panel (the whole previous update done):
         //    the pivot rows into shared memory
