@@ -727,48 +727,72 @@ __device__ void x_prime_from_tmem(Tc128Smem &sm, Tc128Work &wk, uint32_t tmem, i
 // 128 contiguous bytes (no bank conflicts); tile row r = 2 i' + part.  The
 // loads (one float4 of hi and one of lo: (i, k) and (i, k + 1)) are issued
 // a chunk ahead.
+// In the residual loop warps 0 .. 14 make the tiles and warp 15 only issues
+// the MMAs (an issuing thread can be held while the tensor cores' queue
+// drains, and would otherwise hold its warp's share of the next chunk).  The
+// 16 item groups of 32 go to warp g, and group 15 to warp 3, so that each of
+// the four schedulers (warps w, w + 4, ...) gets four groups.
+constexpr int NPROD = 15;           // producer warps
+constexpr int ISSUER = NPROD * 32;  // thread that issues the residual's MMAs
+
+KNIT_DEV int res_group2(int w) { return w == 3 ? 15 : -1; }   // a producer warp's second group
+
 struct GvPre {
-    float4 h, l;
+    float4 h[2], l[2];
 };
 
-KNIT_DEV void res_b_item(int &ip, int &kk, int &part)
+KNIT_DEV void res_b_item(int g, int &ip, int &kk, int &part)
 {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int r = 8 * (w & 7) + (l >> 2);
+    const int l = threadIdx.x & 31;
+    const int r = 8 * (g & 7) + (l >> 2);
     ip = r >> 1;
     part = r & 1;
-    kk = 2 * ((l & 3) + 4 * (w >> 3));
+    kk = 2 * ((l & 3) + 4 * (g >> 3));
 }
 
 KNIT_DEV GvPre res_b_load(const Tc128Work &wk, int pass, int c)
 {
-    int ip, kk, part;
-    res_b_item(ip, kk, part);
-    const int i = 32 * pass + ip, k = 16 * (c & 7) + kk;
-    const int f = (k >> 1) * MP + i;
-    GvPre g;
-    g.h = wk.Gh[f];
-    g.l = wk.Gl[f];
-    return g;
+    GvPre q;
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int g = h ? res_group2(w) : w;
+        if (w >= NPROD || g < 0) continue;
+        int ip, kk, part;
+        res_b_item(g, ip, kk, part);
+        const int i = 32 * pass + ip, k = 16 * (c & 7) + kk;
+        const int f = (k >> 1) * MP + i;
+        q.h[h] = wk.Gh[f];
+        q.l[h] = wk.Gl[f];
+    }
+    return q;
 }
 
-__device__ void res_b_build(const GvPre &g, const Tc128Smem &sm, unsigned char *b, int pass)
+__device__ void res_b_build(const GvPre &q, const Tc128Smem &sm, unsigned char *b, int pass)
 {
-    int ip, kk, part;
-    res_b_item(ip, kk, part);
-    const float dn = pow2f(-sm.rexp[32 * pass + ip]);
-    float dg0[NDG], dg1[NDG];
-    digits7(part ? g.h.y : g.h.x, part ? g.l.y : g.l.x, dn, dg0);
-    digits7(part ? g.h.w : g.h.z, part ? g.l.w : g.l.z, dn, dg1);
+    const int w = threadIdx.x >> 5;
 #pragma unroll
-    for (int p = 0; p < NDG; ++p) put_bf16x2(b + p * BT_RES, 2 * ip + part, kk, dg0[p], dg1[p]);
+    for (int h = 0; h < 2; ++h) {
+        const int g = h ? res_group2(w) : w;
+        if (w >= NPROD || g < 0) continue;
+        int ip, kk, part;
+        res_b_item(g, ip, kk, part);
+        const float dn = pow2f(-sm.rexp[32 * pass + ip]);
+        float dg0[NDG], dg1[NDG];
+        digits7(part ? q.h[h].y : q.h[h].x, part ? q.l[h].y : q.l[h].x, dn, dg0);
+        digits7(part ? q.h[h].w : q.h[h].z, part ? q.l[h].w : q.l[h].z, dn, dg1);
+#pragma unroll
+        for (int p = 0; p < NDG; ++p) put_bf16x2(b + p * BT_RES, 2 * ip + part, kk, dg0[p], dg1[p]);
+    }
 }
 
 // the B tiles of chunk c + 8 from those of chunk c: rows 2i' = -Gi, 2i' + 1 = Gr
+// (producer warps only)
 __device__ void res_b_swap(const unsigned char *src, unsigned char *dst)
 {
     // one 16-byte piece per work item: digit p, row r, K half h
-    for (int e = threadIdx.x; e < NDG * 64 * 2; e += NTH) {
+    if (threadIdx.x >= 32 * NPROD) return;
+    for (int e = threadIdx.x; e < NDG * 64 * 2; e += 32 * NPROD) {
         const int h = e & 1, r = (e >> 1) & 63, p = e >> 7;
         const int rs = r ^ 1;
         const uint4 v = *reinterpret_cast<const uint4 *>(src + p * BT_RES + tile_off(rs, 8 * h));
@@ -1230,8 +1254,8 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                 for (int sq = 0; sq < nseq; ++sq) {
                     const int slot = sq & 1;
                     const int c = (sq >> 1) + 8 * (sq & 1);
-                    // every thread waits for the MMAs that last read this slot
-                    const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
+                    // every producer waits for the MMAs that last read this slot
+                    const int ok = sq >= 2 && tid < ISSUER ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
                     if ((sq & 1) == 0 && sq + 2 < nseq) nxt = res_b_load(wk, pass, (sq >> 1) + 1);
                     const unsigned char *const a = sm.u.res.lres[c];
                     unsigned char *const b = sm.u.res.b[slot];
@@ -1244,7 +1268,7 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                         br.ph[2 + slot] ^= 1u;
                         br.pend[2 + slot] = 0u;
                     }
-                    if (tid == 0) {
+                    if (tid == ISSUER) {
                         fence_after();
                         const uint64_t bd0 = smem_desc(smem_u32(b));
                         const uint64_t bd4 = smem_desc(smem_u32(b + 4 * BT_RES));
