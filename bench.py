@@ -469,22 +469,25 @@ def run_uneven(args):
 
 
 def run_profile_case(args):
-    """Small case for ncu captures: M=64, L=64, 19 energies x 8 seeds (one
-    wave of 152 instances), one mixed and one FP64 sweep after a warm-up."""
+    """Small case for ncu captures: square lattice of width --profile-M
+    (default 64), L = --profile-L (default 64), W = 2, 19 energies x 8 seeds
+    (one wave of 152 instances), two mixed sweeps and one FP64 sweep (FP64
+    skipped above width 64, where it takes seconds)."""
     import torch
     from paper_1010_2627_gb300 import build, inputs, knit
     build.build()
     knit.load()
-    Lp = args.profile_L
-    ss = inputs.square(M, Lp)
+    Lp, Mp = args.profile_L, args.profile_M
+    ss = inputs.square(Mp, Lp)
     E = inputs.energy_grid(-3.9, 3.9, 19)
     seeds = np.arange(NS, dtype=np.uint64)
     sysk = knit.System(ss)
-    for precision in (knit.KNIT_MIXED, knit.KNIT_MIXED, knit.KNIT_FP64):
+    runs = (knit.KNIT_MIXED, knit.KNIT_MIXED) + ((knit.KNIT_FP64,) if Mp <= 64 else ())
+    for precision in runs:
         T, st = sysk.transmission(E, seeds, W=W, precision=precision)
         assert (st == 0).all()
     torch.cuda.synchronize()
-    print(json.dumps({"case": "profile", "M": M, "L": Lp, "instances": 19 * NS,
+    print(json.dumps({"case": "profile", "M": Mp, "L": Lp, "instances": 19 * NS,
                       "T_mean": float(T.mean())}))
     sysk.close()
 
@@ -874,6 +877,7 @@ def main():
                              "graph"])
     ap.add_argument("--bdg-energies", dest="bdg_energies", type=int, default=2048)
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
+    ap.add_argument("--profile-M", dest="profile_M", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

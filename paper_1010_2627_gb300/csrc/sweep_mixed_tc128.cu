@@ -876,45 +876,52 @@ __device__ float res_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem,
 
 // values of S (and of R for a Neumann term) one work item per thread half:
 // items e = tid, tid + NTH
+// Work of one K range (the chunks c and c + 8 use the same values) in
+// item groups of 32: 64 B groups (a group: 8 consecutive tile rows x 4 K
+// pairs, conflict-free stores), 32 A groups; group g goes to producer warp
+// g % 15, so a warp holds at most 5 B and 3 A items
+constexpr int PB = 5, PA = 3;
+
 struct ProdPre {
-    float4 s[4];      // (k, j), (k + 1, j) of S for the thread's four B items
-    float4 a[2];      // (i, k), (i, k + 1) of X' or R for the thread's two A items
+    float4 s[PB];     // (k, j), (k + 1, j) of S
+    float4 a[PA];     // (i, k), (i, k + 1) of X' or R
 };
 
-// B item h of a thread (4 per thread, 2048 per chunk): tile row 2j + sub and
-// K pair kp; a warp's 32 four-byte stores cover 8 consecutive tile rows
-// (four columns j, both parities) x 4 K pairs = 128 contiguous bytes
-KNIT_DEV void prod_b_item(int h, int &j, int &sub, int &kp)
+// B item of group g (0 .. 63): tile row 2j + sub, K pair kp
+KNIT_DEV void prod_b_item(int g, int &j, int &sub, int &kp)
 {
-    const int e = threadIdx.x + h * NTH, l = e & 31, w = e >> 5;   // w = 0 .. 63
-    j = 4 * (w & 31) + (l >> 3);
+    const int l = threadIdx.x & 31;
+    j = 4 * (g & 31) + (l >> 3);
     sub = (l >> 2) & 1;
-    kp = (l & 3) + 4 * (w >> 5);
+    kp = (l & 3) + 4 * (g >> 5);
 }
 
-// A item h (2 per thread): tile row i, K pair kp; a warp covers 8 rows x 4
-// K pairs (conflict-free), the two items the two K halves
-KNIT_DEV void prod_a_item(int h, int &i, int &kp)
+// A item of group g (0 .. 31): tile row i, K pair kp
+KNIT_DEV void prod_a_item(int g, int &i, int &kp)
 {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    i = 8 * w + (l >> 2);
-    kp = (l & 3) + 4 * h;
+    const int l = threadIdx.x & 31;
+    i = 8 * (g & 15) + (l >> 2);
+    kp = (l & 3) + 4 * (g >> 4);
 }
 
 KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, const float4 *Xt, int c)
 {
-    const int k0 = 16 * (c & 7);
+    const int k0 = 16 * (c & 7), w = threadIdx.x >> 5;
     ProdPre q;
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
+    for (int h = 0; h < PB; ++h) {
+        const int g = w + NPROD * h;
+        if (w >= NPROD || g >= 64) continue;
         int j, sub, kp;
-        prod_b_item(h, j, sub, kp);
+        prod_b_item(g, j, sub, kp);
         q.s[h] = *reinterpret_cast<const float4 *>(S + sidx(k0 + 2 * kp, j));
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < PA; ++h) {
+        const int g = w + NPROD * h;
+        if (w >= NPROD || g >= 32) continue;
         int i, kp;
-        prod_a_item(h, i, kp);
+        prod_a_item(g, i, kp);
         const int k = k0 + 2 * kp;
         if (R) {
             const float2 r0 = R[sidx(i, k)], r1 = R[sidx(i, k + 1)];
@@ -926,41 +933,35 @@ KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, const float4 *Xt, i
     return q;
 }
 
-// A tile from X' (digits, at the column scale of X'; the scale goes into B)
-KNIT_DEV void prod_a_x(const ProdPre &q, const Tc128Smem &sm, unsigned char *a, int c)
+// A tile: X' digits (at the column scale of X'; the scale goes into B), or
+// the three exact bf16 terms of R
+KNIT_DEV void prod_a(const ProdPre &q, const Tc128Smem &sm, unsigned char *a, int c, bool isx)
 {
-    const int part = c >> 3, k0 = 16 * (c & 7);
+    const int part = c >> 3, k0 = 16 * (c & 7), w = threadIdx.x >> 5;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < PA; ++h) {
+        const int g = w + NPROD * h;
+        if (w >= NPROD || g >= 32) continue;
         int i, kp;
-        prod_a_item(h, i, kp);
-        const int kk = 2 * kp;
-        float d0[NDX], d1[NDX];
-        digits3(part ? q.a[h].y : q.a[h].x, pow2f(-sm.cexp[k0 + kk]), d0);
-        digits3(part ? q.a[h].w : q.a[h].z, pow2f(-sm.cexp[k0 + kk + 1]), d1);
-#pragma unroll
-        for (int qq = 0; qq < NDX; ++qq) put_bf16x2(a + qq * A_TILE, i, kk, d0[qq], d1[qq]);
-    }
-}
-
-// A tile from R (three exact bf16 terms of each fp32 value)
-KNIT_DEV void prod_a_r(const ProdPre &q, unsigned char *a, int c)
-{
-    const int part = c >> 3;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int i, kp;
-        prod_a_item(h, i, kp);
+        prod_a_item(g, i, kp);
         const int kk = 2 * kp;
         const float v0 = part ? q.a[h].y : q.a[h].x;
         const float v1 = part ? q.a[h].w : q.a[h].z;
-        uint32_t h0, m0, l0, h1, m1, l1;
-        bf16_split3(v0, h0, m0, l0);
-        bf16_split3(v1, h1, m1, l1);
-        unsigned char *p = a + tile_off(i, kk);
-        *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
-        *reinterpret_cast<uint32_t *>(p + A_TILE) = pack_hi16(m0, m1);
-        *reinterpret_cast<uint32_t *>(p + 2 * A_TILE) = pack_hi16(l0, l1);
+        if (isx) {
+            float d0[NDX], d1[NDX];
+            digits3(v0, pow2f(-sm.cexp[k0 + kk]), d0);
+            digits3(v1, pow2f(-sm.cexp[k0 + kk + 1]), d1);
+#pragma unroll
+            for (int qq = 0; qq < NDX; ++qq) put_bf16x2(a + qq * A_TILE, i, kk, d0[qq], d1[qq]);
+        } else {
+            uint32_t h0, m0, l0, h1, m1, l1;
+            bf16_split3(v0, h0, m0, l0);
+            bf16_split3(v1, h1, m1, l1);
+            unsigned char *p = a + tile_off(i, kk);
+            *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
+            *reinterpret_cast<uint32_t *>(p + A_TILE) = pack_hi16(m0, m1);
+            *reinterpret_cast<uint32_t *>(p + 2 * A_TILE) = pack_hi16(l0, l1);
+        }
     }
 }
 
@@ -968,11 +969,13 @@ KNIT_DEV void prod_a_r(const ProdPre &q, unsigned char *a, int c)
 // row 2j = [Re | -Im], row 2j + 1 = [Im | Re] of column j of S
 KNIT_DEV void prod_b(const ProdPre &q, const Tc128Smem &sm, unsigned char *b, int c, bool scaled)
 {
-    const int part = c >> 3, k0 = 16 * (c & 7);
+    const int part = c >> 3, k0 = 16 * (c & 7), w = threadIdx.x >> 5;
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
+    for (int h = 0; h < PB; ++h) {
+        const int g = w + NPROD * h;
+        if (w >= NPROD || g >= 64) continue;
         int j, sub, kp;
-        prod_b_item(h, j, sub, kp);
+        prod_b_item(g, j, sub, kp);
         const int kk = 2 * kp, k = k0 + kk;
         const float4 sv = q.s[h];
         const float u0 = scaled ? pow2f(sm.cexp[k] - 8) : 1.f;
@@ -992,33 +995,38 @@ KNIT_DEV void prod_b(const ProdPre &q, const Tc128Smem &sm, unsigned char *b, in
     }
 }
 
-// g = X' + D into the state: lane i of quarter qd, complex columns 32 cg ..
+// g = X' + D into the state, D the sum of the two accumulators: lane i of
+// quarter qd, complex columns 32 cg .. + 31, eight at a time
 __device__ void ref_readback(Tc128Work &wk, uint32_t tmem, int M)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
     const float2 *X = reinterpret_cast<const float2 *>(wk.Xt);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
+    const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg;
+#pragma unroll 1
+    for (int h = 0; h < 4; ++h) {
+        uint32_t v[16], v2[16];
+        tmem_ld16(tb + 16 * h, v);
+        tmem_ld16(tb + 256 + 16 * h, v2);
         wait_ld();
 #pragma unroll
-        for (int cp = 0; cp < 8; ++cp) {
+        for (int cp = 0; cp < 4; ++cp) {
             float2 oh[2], ol[2];
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
-                const int c = 2 * cp + s2, j = 32 * cg + 16 * h + c;
+                const int c = 2 * cp + s2, j = 32 * cg + 8 * h + c;
                 const float2 x = X[((j >> 1) * MP + i) * 2 + (j & 1)];
+                const float dre = __uint_as_float(v[2 * c]) + __uint_as_float(v2[2 * c]);
+                const float dim = __uint_as_float(v[2 * c + 1]) + __uint_as_float(v2[2 * c + 1]);
                 if (i < M && j < M) {
-                    two_sum(x.x, __uint_as_float(v[2 * c]), oh[s2].x, ol[s2].x);
-                    two_sum(x.y, __uint_as_float(v[2 * c + 1]), oh[s2].y, ol[s2].y);
+                    two_sum(x.x, dre, oh[s2].x, ol[s2].x);
+                    two_sum(x.y, dim, oh[s2].y, ol[s2].y);
                 } else {
                     oh[s2] = make_float2(i == j ? 1.f : 0.f, 0.f);
                     ol[s2] = make_float2(0.f, 0.f);
                 }
             }
-            const int jp = 16 * cg + 8 * h + cp;
+            const int jp = 16 * cg + 4 * h + cp;
             wk.Gh[jp * MP + i] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
             wk.Gl[jp * MP + i] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
         }
@@ -1030,18 +1038,21 @@ __device__ void neumann_readback(const float2 *R, float2 *So, uint32_t tmem, int
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
+    const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg;
+#pragma unroll 1
+    for (int h = 0; h < 4; ++h) {
+        uint32_t v[16], v2[16];
+        tmem_ld16(tb + 16 * h, v);
+        tmem_ld16(tb + 256 + 16 * h, v2);
         wait_ld();
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-            const int j = 32 * cg + 16 * h + c;
+        for (int c = 0; c < 8; ++c) {
+            const int j = 32 * cg + 8 * h + c;
             float2 o = make_float2(0.f, 0.f);
             if (i < M && j < M) {
                 const float2 r = R[sidx(i, j)];
-                o = make_float2(r.x + __uint_as_float(v[2 * c]), r.y + __uint_as_float(v[2 * c + 1]));
+                o = make_float2(r.x + __uint_as_float(v[2 * c]) + __uint_as_float(v2[2 * c]),
+                                r.y + __uint_as_float(v[2 * c + 1]) + __uint_as_float(v2[2 * c + 1]));
             }
             So[sidx(i, j)] = o;
         }
@@ -1049,23 +1060,26 @@ __device__ void neumann_readback(const float2 *R, float2 *So, uint32_t tmem, int
 }
 
 // D = A S on the tensor cores with A = X' (R null) or A = R; double-buffered
-// over the two chunk slots; every thread polls the slot's barrier before it
-// rewrites the slot, and the next K range's loads are issued a chunk ahead.
-// Returns false when a wait ran out (the commits in flight stay recorded).
-__device__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, const float2 *S,
+// over the two chunk slots; warps 0 .. 14 make the tiles (each polls the
+// slot's barrier before it rewrites the slot) and load the next K range's
+// values after the second chunk of a range, warp 15 issues the MMAs, the
+// even chunks into the accumulator at tensor-memory column 0 and the odd ones
+// into the one at column 256 (the read-back adds the two).  Returns false
+// when a wait ran out (the commits in flight stay recorded).
+__device__ __noinline__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, const float2 *S,
                            const float2 *R, const float4 *Xt, int nchunk)
 {
-    const int nseq = 2 * nchunk;
-    ProdPre cur = prod_load(S, R, Xt, 0), nxt = cur;
+    const int nseq = 2 * nchunk, tid = threadIdx.x;
+    const bool producer = tid < ISSUER;
+    ProdPre cur = prod_load(S, R, Xt, 0);
     for (int sq = 0; sq < nseq; ++sq) {
         const int slot = sq & 1, c = (sq >> 1) + 8 * (sq & 1);
-        const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
-        if ((sq & 1) == 0 && sq + 2 < nseq) nxt = prod_load(S, R, Xt, (sq >> 1) + 1);
+        const int ok = sq >= 2 && producer ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
         unsigned char *const a = sm.u.ref.a[slot];
         unsigned char *const b = sm.u.ref.b[slot];
-        if (R) prod_a_r(cur, a, c);
-        else prod_a_x(cur, sm, a, c);
+        prod_a(cur, sm, a, c, R == nullptr);
         prod_b(cur, sm, b, c, R == nullptr);
+        if ((sq & 1) && sq + 1 < nseq) cur = prod_load(S, R, Xt, (sq >> 1) + 1);
         async_proxy_fence();
         fence_before();
         if (__syncthreads_or(!ok)) return false;
@@ -1073,18 +1087,18 @@ __device__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, const float2 
             br.ph[2 + slot] ^= 1u;
             br.pend[2 + slot] = 0u;
         }
-        if (threadIdx.x == 0) {
+        if (tid == ISSUER) {
             fence_after();
+            const uint32_t d = tmem + 256u * (uint32_t)slot;
 #pragma unroll
             for (int pr = 0; pr < 6; ++pr) {
                 const uint64_t ad = smem_desc(smem_u32(a + kProdP[pr] * A_TILE));
                 const uint64_t bd = smem_desc(smem_u32(b + kProdQ[pr] * BT_256));
-                mma_bf16(tmem, ad, bd, idesc_bf16_m128(256), (sq == 0 && pr == 0) ? 0u : 1u);
+                mma_bf16(d, ad, bd, idesc_bf16_m128(256), (sq < 2 && pr == 0) ? 0u : 1u);
             }
             mma_commit(&sm.bar[2 + slot]);
         }
         br.pend[2 + slot] = 1u;
-        if (sq & 1) cur = nxt;
     }
     return bar_wait(sm, br, 2) && bar_wait(sm, br, 3);
 }
