@@ -727,72 +727,48 @@ __device__ void x_prime_from_tmem(Tc128Smem &sm, Tc128Work &wk, uint32_t tmem, i
 // 128 contiguous bytes (no bank conflicts); tile row r = 2 i' + part.  The
 // loads (one float4 of hi and one of lo: (i, k) and (i, k + 1)) are issued
 // a chunk ahead.
-// In the residual loop warps 0 .. 14 make the tiles and warp 15 only issues
-// the MMAs (an issuing thread can be held while the tensor cores' queue
-// drains, and would otherwise hold its warp's share of the next chunk).  The
-// 16 item groups of 32 go to warp g, and group 15 to warp 3, so that each of
-// the four schedulers (warps w, w + 4, ...) gets four groups.
-constexpr int NPROD = 15;           // producer warps
-constexpr int ISSUER = NPROD * 32;  // thread that issues the residual's MMAs
-
-KNIT_DEV int res_group2(int w) { return w == 3 ? 15 : -1; }   // a producer warp's second group
-
 struct GvPre {
-    float4 h[2], l[2];
+    float4 h, l;
 };
 
-KNIT_DEV void res_b_item(int g, int &ip, int &kk, int &part)
+KNIT_DEV void res_b_item(int &ip, int &kk, int &part)
 {
-    const int l = threadIdx.x & 31;
-    const int r = 8 * (g & 7) + (l >> 2);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int r = 8 * (w & 7) + (l >> 2);
     ip = r >> 1;
     part = r & 1;
-    kk = 2 * ((l & 3) + 4 * (g >> 3));
+    kk = 2 * ((l & 3) + 4 * (w >> 3));
 }
 
 KNIT_DEV GvPre res_b_load(const Tc128Work &wk, int pass, int c)
 {
-    GvPre q;
-    const int w = threadIdx.x >> 5;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int g = h ? res_group2(w) : w;
-        if (w >= NPROD || g < 0) continue;
-        int ip, kk, part;
-        res_b_item(g, ip, kk, part);
-        const int i = 32 * pass + ip, k = 16 * (c & 7) + kk;
-        const int f = (k >> 1) * MP + i;
-        q.h[h] = wk.Gh[f];
-        q.l[h] = wk.Gl[f];
-    }
-    return q;
+    int ip, kk, part;
+    res_b_item(ip, kk, part);
+    const int i = 32 * pass + ip, k = 16 * (c & 7) + kk;
+    const int f = (k >> 1) * MP + i;
+    GvPre g;
+    g.h = wk.Gh[f];
+    g.l = wk.Gl[f];
+    return g;
 }
 
-__device__ void res_b_build(const GvPre &q, const Tc128Smem &sm, unsigned char *b, int pass)
+__device__ void res_b_build(const GvPre &g, const Tc128Smem &sm, unsigned char *b, int pass)
 {
-    const int w = threadIdx.x >> 5;
+    int ip, kk, part;
+    res_b_item(ip, kk, part);
+    const float dn = pow2f(-sm.rexp[32 * pass + ip]);
+    float dg0[NDG], dg1[NDG];
+    digits7(part ? g.h.y : g.h.x, part ? g.l.y : g.l.x, dn, dg0);
+    digits7(part ? g.h.w : g.h.z, part ? g.l.w : g.l.z, dn, dg1);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int g = h ? res_group2(w) : w;
-        if (w >= NPROD || g < 0) continue;
-        int ip, kk, part;
-        res_b_item(g, ip, kk, part);
-        const float dn = pow2f(-sm.rexp[32 * pass + ip]);
-        float dg0[NDG], dg1[NDG];
-        digits7(part ? q.h[h].y : q.h[h].x, part ? q.l[h].y : q.l[h].x, dn, dg0);
-        digits7(part ? q.h[h].w : q.h[h].z, part ? q.l[h].w : q.l[h].z, dn, dg1);
-#pragma unroll
-        for (int p = 0; p < NDG; ++p) put_bf16x2(b + p * BT_RES, 2 * ip + part, kk, dg0[p], dg1[p]);
-    }
+    for (int p = 0; p < NDG; ++p) put_bf16x2(b + p * BT_RES, 2 * ip + part, kk, dg0[p], dg1[p]);
 }
 
 // the B tiles of chunk c + 8 from those of chunk c: rows 2i' = -Gi, 2i' + 1 = Gr
-// (producer warps only)
 __device__ void res_b_swap(const unsigned char *src, unsigned char *dst)
 {
     // one 16-byte piece per work item: digit p, row r, K half h
-    if (threadIdx.x >= 32 * NPROD) return;
-    for (int e = threadIdx.x; e < NDG * 64 * 2; e += 32 * NPROD) {
+    for (int e = threadIdx.x; e < NDG * 64 * 2; e += NTH) {
         const int h = e & 1, r = (e >> 1) & 63, p = e >> 7;
         const int rs = r ^ 1;
         const uint4 v = *reinterpret_cast<const uint4 *>(src + p * BT_RES + tile_off(rs, 8 * h));
@@ -876,52 +852,45 @@ __device__ float res_readback(Tc128Work &wk, const Tc128Smem &sm, uint32_t tmem,
 
 // values of S (and of R for a Neumann term) one work item per thread half:
 // items e = tid, tid + NTH
-// Work of one K range (the chunks c and c + 8 use the same values) in
-// item groups of 32: 64 B groups (a group: 8 consecutive tile rows x 4 K
-// pairs, conflict-free stores), 32 A groups; group g goes to producer warp
-// g % 15, so a warp holds at most 5 B and 3 A items
-constexpr int PB = 5, PA = 3;
-
 struct ProdPre {
-    float4 s[PB];     // (k, j), (k + 1, j) of S
-    float4 a[PA];     // (i, k), (i, k + 1) of X' or R
+    float4 s[4];      // (k, j), (k + 1, j) of S for the thread's four B items
+    float4 a[2];      // (i, k), (i, k + 1) of X' or R for the thread's two A items
 };
 
-// B item of group g (0 .. 63): tile row 2j + sub, K pair kp
-KNIT_DEV void prod_b_item(int g, int &j, int &sub, int &kp)
+// B item h of a thread (4 per thread, 2048 per chunk): tile row 2j + sub and
+// K pair kp; a warp's 32 four-byte stores cover 8 consecutive tile rows
+// (four columns j, both parities) x 4 K pairs = 128 contiguous bytes
+KNIT_DEV void prod_b_item(int h, int &j, int &sub, int &kp)
 {
-    const int l = threadIdx.x & 31;
-    j = 4 * (g & 31) + (l >> 3);
+    const int e = threadIdx.x + h * NTH, l = e & 31, w = e >> 5;   // w = 0 .. 63
+    j = 4 * (w & 31) + (l >> 3);
     sub = (l >> 2) & 1;
-    kp = (l & 3) + 4 * (g >> 5);
+    kp = (l & 3) + 4 * (w >> 5);
 }
 
-// A item of group g (0 .. 31): tile row i, K pair kp
-KNIT_DEV void prod_a_item(int g, int &i, int &kp)
+// A item h (2 per thread): tile row i, K pair kp; a warp covers 8 rows x 4
+// K pairs (conflict-free), the two items the two K halves
+KNIT_DEV void prod_a_item(int h, int &i, int &kp)
 {
-    const int l = threadIdx.x & 31;
-    i = 8 * (g & 15) + (l >> 2);
-    kp = (l & 3) + 4 * (g >> 4);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    i = 8 * w + (l >> 2);
+    kp = (l & 3) + 4 * h;
 }
 
 KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, const float4 *Xt, int c)
 {
-    const int k0 = 16 * (c & 7), w = threadIdx.x >> 5;
+    const int k0 = 16 * (c & 7);
     ProdPre q;
 #pragma unroll
-    for (int h = 0; h < PB; ++h) {
-        const int g = w + NPROD * h;
-        if (w >= NPROD || g >= 64) continue;
+    for (int h = 0; h < 4; ++h) {
         int j, sub, kp;
-        prod_b_item(g, j, sub, kp);
+        prod_b_item(h, j, sub, kp);
         q.s[h] = *reinterpret_cast<const float4 *>(S + sidx(k0 + 2 * kp, j));
     }
 #pragma unroll
-    for (int h = 0; h < PA; ++h) {
-        const int g = w + NPROD * h;
-        if (w >= NPROD || g >= 32) continue;
+    for (int h = 0; h < 2; ++h) {
         int i, kp;
-        prod_a_item(g, i, kp);
+        prod_a_item(h, i, kp);
         const int k = k0 + 2 * kp;
         if (R) {
             const float2 r0 = R[sidx(i, k)], r1 = R[sidx(i, k + 1)];
@@ -933,35 +902,41 @@ KNIT_DEV ProdPre prod_load(const float2 *S, const float2 *R, const float4 *Xt, i
     return q;
 }
 
-// A tile: X' digits (at the column scale of X'; the scale goes into B), or
-// the three exact bf16 terms of R
-KNIT_DEV void prod_a(const ProdPre &q, const Tc128Smem &sm, unsigned char *a, int c, bool isx)
+// A tile from X' (digits, at the column scale of X'; the scale goes into B)
+KNIT_DEV void prod_a_x(const ProdPre &q, const Tc128Smem &sm, unsigned char *a, int c)
 {
-    const int part = c >> 3, k0 = 16 * (c & 7), w = threadIdx.x >> 5;
+    const int part = c >> 3, k0 = 16 * (c & 7);
 #pragma unroll
-    for (int h = 0; h < PA; ++h) {
-        const int g = w + NPROD * h;
-        if (w >= NPROD || g >= 32) continue;
+    for (int h = 0; h < 2; ++h) {
         int i, kp;
-        prod_a_item(g, i, kp);
+        prod_a_item(h, i, kp);
+        const int kk = 2 * kp;
+        float d0[NDX], d1[NDX];
+        digits3(part ? q.a[h].y : q.a[h].x, pow2f(-sm.cexp[k0 + kk]), d0);
+        digits3(part ? q.a[h].w : q.a[h].z, pow2f(-sm.cexp[k0 + kk + 1]), d1);
+#pragma unroll
+        for (int qq = 0; qq < NDX; ++qq) put_bf16x2(a + qq * A_TILE, i, kk, d0[qq], d1[qq]);
+    }
+}
+
+// A tile from R (three exact bf16 terms of each fp32 value)
+KNIT_DEV void prod_a_r(const ProdPre &q, unsigned char *a, int c)
+{
+    const int part = c >> 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int i, kp;
+        prod_a_item(h, i, kp);
         const int kk = 2 * kp;
         const float v0 = part ? q.a[h].y : q.a[h].x;
         const float v1 = part ? q.a[h].w : q.a[h].z;
-        if (isx) {
-            float d0[NDX], d1[NDX];
-            digits3(v0, pow2f(-sm.cexp[k0 + kk]), d0);
-            digits3(v1, pow2f(-sm.cexp[k0 + kk + 1]), d1);
-#pragma unroll
-            for (int qq = 0; qq < NDX; ++qq) put_bf16x2(a + qq * A_TILE, i, kk, d0[qq], d1[qq]);
-        } else {
-            uint32_t h0, m0, l0, h1, m1, l1;
-            bf16_split3(v0, h0, m0, l0);
-            bf16_split3(v1, h1, m1, l1);
-            unsigned char *p = a + tile_off(i, kk);
-            *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
-            *reinterpret_cast<uint32_t *>(p + A_TILE) = pack_hi16(m0, m1);
-            *reinterpret_cast<uint32_t *>(p + 2 * A_TILE) = pack_hi16(l0, l1);
-        }
+        uint32_t h0, m0, l0, h1, m1, l1;
+        bf16_split3(v0, h0, m0, l0);
+        bf16_split3(v1, h1, m1, l1);
+        unsigned char *p = a + tile_off(i, kk);
+        *reinterpret_cast<uint32_t *>(p) = pack_hi16(h0, h1);
+        *reinterpret_cast<uint32_t *>(p + A_TILE) = pack_hi16(m0, m1);
+        *reinterpret_cast<uint32_t *>(p + 2 * A_TILE) = pack_hi16(l0, l1);
     }
 }
 
@@ -969,13 +944,11 @@ KNIT_DEV void prod_a(const ProdPre &q, const Tc128Smem &sm, unsigned char *a, in
 // row 2j = [Re | -Im], row 2j + 1 = [Im | Re] of column j of S
 KNIT_DEV void prod_b(const ProdPre &q, const Tc128Smem &sm, unsigned char *b, int c, bool scaled)
 {
-    const int part = c >> 3, k0 = 16 * (c & 7), w = threadIdx.x >> 5;
+    const int part = c >> 3, k0 = 16 * (c & 7);
 #pragma unroll
-    for (int h = 0; h < PB; ++h) {
-        const int g = w + NPROD * h;
-        if (w >= NPROD || g >= 64) continue;
+    for (int h = 0; h < 4; ++h) {
         int j, sub, kp;
-        prod_b_item(g, j, sub, kp);
+        prod_b_item(h, j, sub, kp);
         const int kk = 2 * kp, k = k0 + kk;
         const float4 sv = q.s[h];
         const float u0 = scaled ? pow2f(sm.cexp[k] - 8) : 1.f;
@@ -995,38 +968,33 @@ KNIT_DEV void prod_b(const ProdPre &q, const Tc128Smem &sm, unsigned char *b, in
     }
 }
 
-// g = X' + D into the state, D the sum of the two accumulators: lane i of
-// quarter qd, complex columns 32 cg .. + 31, eight at a time
+// g = X' + D into the state: lane i of quarter qd, complex columns 32 cg ..
 __device__ void ref_readback(Tc128Work &wk, uint32_t tmem, int M)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
     const float2 *X = reinterpret_cast<const float2 *>(wk.Xt);
-    const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg;
-#pragma unroll 1
-    for (int h = 0; h < 4; ++h) {
-        uint32_t v[16], v2[16];
-        tmem_ld16(tb + 16 * h, v);
-        tmem_ld16(tb + 256 + 16 * h, v2);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
         wait_ld();
 #pragma unroll
-        for (int cp = 0; cp < 4; ++cp) {
+        for (int cp = 0; cp < 8; ++cp) {
             float2 oh[2], ol[2];
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
-                const int c = 2 * cp + s2, j = 32 * cg + 8 * h + c;
+                const int c = 2 * cp + s2, j = 32 * cg + 16 * h + c;
                 const float2 x = X[((j >> 1) * MP + i) * 2 + (j & 1)];
-                const float dre = __uint_as_float(v[2 * c]) + __uint_as_float(v2[2 * c]);
-                const float dim = __uint_as_float(v[2 * c + 1]) + __uint_as_float(v2[2 * c + 1]);
                 if (i < M && j < M) {
-                    two_sum(x.x, dre, oh[s2].x, ol[s2].x);
-                    two_sum(x.y, dim, oh[s2].y, ol[s2].y);
+                    two_sum(x.x, __uint_as_float(v[2 * c]), oh[s2].x, ol[s2].x);
+                    two_sum(x.y, __uint_as_float(v[2 * c + 1]), oh[s2].y, ol[s2].y);
                 } else {
                     oh[s2] = make_float2(i == j ? 1.f : 0.f, 0.f);
                     ol[s2] = make_float2(0.f, 0.f);
                 }
             }
-            const int jp = 16 * cg + 4 * h + cp;
+            const int jp = 16 * cg + 8 * h + cp;
             wk.Gh[jp * MP + i] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
             wk.Gl[jp * MP + i] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
         }
@@ -1038,21 +1006,18 @@ __device__ void neumann_readback(const float2 *R, float2 *So, uint32_t tmem, int
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qd = warp & 3, cg = warp >> 2, i = 32 * qd + lane;
-    const uint32_t tb = tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg;
-#pragma unroll 1
-    for (int h = 0; h < 4; ++h) {
-        uint32_t v[16], v2[16];
-        tmem_ld16(tb + 16 * h, v);
-        tmem_ld16(tb + 256 + 16 * h, v2);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + 64 * cg + 32 * h, v);
         wait_ld();
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int j = 32 * cg + 8 * h + c;
+        for (int c = 0; c < 16; ++c) {
+            const int j = 32 * cg + 16 * h + c;
             float2 o = make_float2(0.f, 0.f);
             if (i < M && j < M) {
                 const float2 r = R[sidx(i, j)];
-                o = make_float2(r.x + __uint_as_float(v[2 * c]) + __uint_as_float(v2[2 * c]),
-                                r.y + __uint_as_float(v[2 * c + 1]) + __uint_as_float(v2[2 * c + 1]));
+                o = make_float2(r.x + __uint_as_float(v[2 * c]), r.y + __uint_as_float(v[2 * c + 1]));
             }
             So[sidx(i, j)] = o;
         }
@@ -1060,26 +1025,23 @@ __device__ void neumann_readback(const float2 *R, float2 *So, uint32_t tmem, int
 }
 
 // D = A S on the tensor cores with A = X' (R null) or A = R; double-buffered
-// over the two chunk slots; warps 0 .. 14 make the tiles (each polls the
-// slot's barrier before it rewrites the slot) and load the next K range's
-// values after the second chunk of a range, warp 15 issues the MMAs, the
-// even chunks into the accumulator at tensor-memory column 0 and the odd ones
-// into the one at column 256 (the read-back adds the two).  Returns false
-// when a wait ran out (the commits in flight stay recorded).
+// over the two chunk slots; every thread polls the slot's barrier before it
+// rewrites the slot, and the next K range's loads are issued a chunk ahead.
+// Returns false when a wait ran out (the commits in flight stay recorded).
 __device__ __noinline__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, const float2 *S,
                            const float2 *R, const float4 *Xt, int nchunk)
 {
-    const int nseq = 2 * nchunk, tid = threadIdx.x;
-    const bool producer = tid < ISSUER;
-    ProdPre cur = prod_load(S, R, Xt, 0);
+    const int nseq = 2 * nchunk;
+    ProdPre cur = prod_load(S, R, Xt, 0), nxt = cur;
     for (int sq = 0; sq < nseq; ++sq) {
         const int slot = sq & 1, c = (sq >> 1) + 8 * (sq & 1);
-        const int ok = sq >= 2 && producer ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
+        const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
+        if ((sq & 1) == 0 && sq + 2 < nseq) nxt = prod_load(S, R, Xt, (sq >> 1) + 1);
         unsigned char *const a = sm.u.ref.a[slot];
         unsigned char *const b = sm.u.ref.b[slot];
-        prod_a(cur, sm, a, c, R == nullptr);
+        if (R) prod_a_r(cur, a, c);
+        else prod_a_x(cur, sm, a, c);
         prod_b(cur, sm, b, c, R == nullptr);
-        if ((sq & 1) && sq + 1 < nseq) cur = prod_load(S, R, Xt, (sq >> 1) + 1);
         async_proxy_fence();
         fence_before();
         if (__syncthreads_or(!ok)) return false;
@@ -1087,18 +1049,18 @@ __device__ __noinline__ bool product_tc(Tc128Smem &sm, Bars &br, uint32_t tmem, 
             br.ph[2 + slot] ^= 1u;
             br.pend[2 + slot] = 0u;
         }
-        if (tid == ISSUER) {
+        if (threadIdx.x == 0) {
             fence_after();
-            const uint32_t d = tmem + 256u * (uint32_t)slot;
 #pragma unroll
             for (int pr = 0; pr < 6; ++pr) {
                 const uint64_t ad = smem_desc(smem_u32(a + kProdP[pr] * A_TILE));
                 const uint64_t bd = smem_desc(smem_u32(b + kProdQ[pr] * BT_256));
-                mma_bf16(d, ad, bd, idesc_bf16_m128(256), (sq < 2 && pr == 0) ? 0u : 1u);
+                mma_bf16(tmem, ad, bd, idesc_bf16_m128(256), (sq == 0 && pr == 0) ? 0u : 1u);
             }
             mma_commit(&sm.bar[2 + slot]);
         }
         br.pend[2 + slot] = 1u;
+        if (sq & 1) cur = nxt;
     }
     return bar_wait(sm, br, 2) && bar_wait(sm, br, 3);
 }
@@ -1173,6 +1135,81 @@ __device__ int fallback64(Tc128Work &wk, int M)
     }
     __syncthreads();
     return ST_OK;
+}
+
+// T from G_LL = Gh + Gl by the unitarity identity (as ward_T of
+// mixed_common.cuh), in double-float on the CUDA cores (GB300's FP64 rate
+// is 1/72 of its FP32 rate; an FP64 trace would cost as much as ~20 slices):
+//   T = Re Tr[Gamma_R i(G - G^dagger)] - Re sum_ij (Gamma_R G)_ij conj((G Gamma_R)_ij)
+// with (G Gamma G^dagger)'s trace written through the Hermitian Gamma_R =
+// i(Sigma_R - Sigma_R^dagger), formed here in double-float (row-major hi / lo
+// in the workspace buffers R and S1).  Per-thread partial sums in FP64.
+__device__ double ward_T128(Tc128Work &wk, const double2 *SR, int M, double *red)
+{
+    float2 *const gmh = wk.R, *const gml = wk.S1;   // Gamma_R, row-major MP x MP
+    const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
+    const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
+    for (int e = threadIdx.x; e < MP * MP; e += NTH) {
+        const int i = e >> 7, k = e & (MP - 1);
+        float2 h = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+        if (i < M && k < M) {
+            const double2 a = SR[(size_t)i * M + k], b = SR[(size_t)k * M + i];
+            // i (a - conj(b))
+            to_df(-(a.y + b.y), h.x, l.x);
+            to_df(a.x - b.x, h.y, l.y);
+        }
+        gmh[e] = h;
+        gml[e] = l;
+    }
+    __syncthreads();
+    double t = 0.0;
+    // Re Tr[Gamma i(G - G^dagger)] = Re sum_ij Gamma_ij i (G_ji - conj(G_ij))
+    for (int e = threadIdx.x; e < M * M; e += NTH) {
+        const int i = e / M, j = e - i * M;
+        const int fji = ((i >> 1) * MP + j) * 2 + (i & 1), fij = ((j >> 1) * MP + i) * 2 + (j & 1);
+        const double gjr = (double)gh[fji].x + gl[fji].x, gji = (double)gh[fji].y + gl[fji].y;
+        const double gir = (double)gh[fij].x + gl[fij].x, gii = (double)gh[fij].y + gl[fij].y;
+        // a = i (G_ji - conj(G_ij)) = i ((gjr - gir) + i (gji + gii))
+        const double ar = -(gji + gii), ai = gjr - gir;
+        const double cr = (double)gmh[i * MP + j].x + gml[i * MP + j].x;
+        const double ci = (double)gmh[i * MP + j].y + gml[i * MP + j].y;
+        t += cr * ar - ci * ai;
+    }
+    // sum_ij (Gamma G)_ij conj((G Gamma)_ij): item (row i, column pair jp),
+    // lanes along jp (coalesced rows of G and Gamma, broadcast row i)
+    for (int e = threadIdx.x; e < MP * (MP / 2); e += NTH) {
+        const int i = e >> 6, jp = e & 63;
+        if (i >= M || 2 * jp >= M) continue;
+        float2 yh[2] = {}, yl[2] = {}, zh[2] = {}, zl[2] = {};
+        for (int k = 0; k < M; ++k) {
+            const float2 gik_h = gh[((k >> 1) * MP + i) * 2 + (k & 1)];
+            const float2 gik_l = gl[((k >> 1) * MP + i) * 2 + (k & 1)];
+            const float2 cik_h = gmh[i * MP + k], cik_l = gml[i * MP + k];
+            const float4 gkh = wk.Gh[jp * MP + k], gkl = wk.Gl[jp * MP + k];            // G[k][2jp], G[k][2jp + 1]
+            const float4 ckh = *reinterpret_cast<const float4 *>(gmh + k * MP + 2 * jp);  // Gamma[k][2jp ..]
+            const float4 ckl = *reinterpret_cast<const float4 *>(gml + k * MP + 2 * jp);
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const float2 gkj_h = s2 ? make_float2(gkh.z, gkh.w) : make_float2(gkh.x, gkh.y);
+                const float2 gkj_l = s2 ? make_float2(gkl.z, gkl.w) : make_float2(gkl.x, gkl.y);
+                const float2 ckj_h = s2 ? make_float2(ckh.z, ckh.w) : make_float2(ckh.x, ckh.y);
+                const float2 ckj_l = s2 ? make_float2(ckl.z, ckl.w) : make_float2(ckl.x, ckl.y);
+                float2 ph, pl;
+                cdf_mul(cik_h, cik_l, gkj_h, gkj_l, ph, pl);   // Gamma_ik G_kj
+                cdf_add(yh[s2], yl[s2], ph, pl);
+                cdf_mul(gik_h, gik_l, ckj_h, ckj_l, ph, pl);   // G_ik Gamma_kj
+                cdf_add(zh[s2], zl[s2], ph, pl);
+            }
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            if (2 * jp + s2 >= M) continue;
+            const double yr = (double)yh[s2].x + yl[s2].x, yi = (double)yh[s2].y + yl[s2].y;
+            const double zr = (double)zh[s2].x + zl[s2].x, zi = (double)zh[s2].y + zl[s2].y;
+            t -= yr * zr + yi * zi;
+        }
+    }
+    return block_sum(t, red);
 }
 
 }  // namespace
@@ -1268,8 +1305,8 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                 for (int sq = 0; sq < nseq; ++sq) {
                     const int slot = sq & 1;
                     const int c = (sq >> 1) + 8 * (sq & 1);
-                    // every producer waits for the MMAs that last read this slot
-                    const int ok = sq >= 2 && tid < ISSUER ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
+                    // every thread waits for the MMAs that last read this slot
+                    const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
                     if ((sq & 1) == 0 && sq + 2 < nseq) nxt = res_b_load(wk, pass, (sq >> 1) + 1);
                     const unsigned char *const a = sm.u.res.lres[c];
                     unsigned char *const b = sm.u.res.b[slot];
@@ -1282,7 +1319,7 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                         br.ph[2 + slot] ^= 1u;
                         br.pend[2 + slot] = 0u;
                     }
-                    if (tid == ISSUER) {
+                    if (tid == 0) {
                         fence_after();
                         const uint64_t bd0 = smem_desc(smem_u32(b));
                         const uint64_t bd4 = smem_desc(smem_u32(b + 4 * BT_RES));
@@ -1360,18 +1397,18 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
 
         double T = 0.0;
         if (st == ST_OK) {
-            // G_LL = Gh + Gl, row-major, for the trace (S1 / S2 hold hi / lo)
-            const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
-            const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
-            for (int e = tid; e < MP * MP; e += NTH) {
-                const int i = e >> 7, j = e & (MP - 1);
-                const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
-                wk.S1[e] = gh[f];
-                wk.S2[e] = gl[f];
+            T = ward_T128(wk, ip.SR, M, sm.red);
+            if (in.GLL) {
+                // G_LL in FP64 for the eigenvalue stage
+                const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
+                const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
+                double2 *const dst = in.GLL + (size_t)ip.out * M * M;
+                for (int e = tid; e < M * M; e += NTH) {
+                    const int i = e / M, j = e - i * M;
+                    const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+                    dst[e] = make_double2((double)gh[f].x + gl[f].x, (double)gh[f].y + gl[f].y);
+                }
             }
-            __syncthreads();
-            T = ward_T<MP, NTH>(wk.S1, wk.S2, wk.A64, ip.SR, M, sm.red);
-            if (in.GLL) store_gll<MP, NTH>(wk.A64, M, in.GLL + (size_t)ip.out * M * M);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {
