@@ -32,8 +32,9 @@
 //     t_j one more than the exponent of the column's largest entry.
 //  D. R = I + Gv' X' exact: transposed, R^T = I + X'^T Gv'^T, so that the
 //     tensor-memory lanes are the columns j of R: A = the three X' digits
-//     (128 x 256 in real form), B = the seven digits of 32 rows of Gv' per
-//     pass (cut at the row scale s_i + 1), products (p, q) of one
+//     (128 x 256 in real form, the contraction over X''s rows in their
+//     stored order, Gv''s columns gathered to match), B = the seven digits
+//     of 32 rows of Gv' per pass (cut at the row scale s_i + 1), products (p, q) of one
 //     anti-diagonal d = p + q in accumulator d (seven exact f32
 //     accumulators of 64 columns, 448 columns), four passes over the rows
 //     of Gv'.  With every digit at most 128 in magnitude each accumulator
@@ -686,9 +687,14 @@ __device__ void x_prime_from_tmem(Tc128Smem &sm, Tc128Work &wk, uint32_t tmem, i
     __syncthreads();
     float2 *const xt = reinterpret_cast<float2 *>(wk.Xt);
     const int ti = sm.pos[i];
-    unsigned char *const tre = sm.u.res.lres[ti >> 4];       // real part: chunk ti / 16
-    unsigned char *const tim = sm.u.res.lres[8 + (ti >> 4)]; // imaginary part
-    const int kk = ti & 15;
+    // the residual contracts over X''s rows in their stored order (K
+    // position i, the Gv' columns gathered through pos), so that a warp's
+    // lanes write 32 consecutive K positions of one tile row: even lanes
+    // store their value and their neighbour's as one word
+    unsigned char *const tre = sm.u.res.lres[i >> 4];        // real part: chunk i / 16
+    unsigned char *const tim = sm.u.res.lres[8 + (i >> 4)];  // imaginary part
+    const int kk = i & 14;
+    const bool even = (lane & 1) == 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         uint32_t v[32];
@@ -705,8 +711,12 @@ __device__ void x_prime_from_tmem(Tc128Smem &sm, Tc128Work &wk, uint32_t tmem, i
             const int off = tile_off(j, kk);
 #pragma unroll
             for (int q = 0; q < NDX; ++q) {
-                *reinterpret_cast<__nv_bfloat16 *>(tre + q * A_TILE + off) = __float2bfloat16_rn(dr[q]);
-                *reinterpret_cast<__nv_bfloat16 *>(tim + q * A_TILE + off) = __float2bfloat16_rn(di[q]);
+                const float nr = __shfl_down_sync(0xffffffffu, dr[q], 1);
+                const float ni = __shfl_down_sync(0xffffffffu, di[q], 1);
+                if (even) {
+                    *reinterpret_cast<__nv_bfloat162 *>(tre + q * A_TILE + off) = __floats2bfloat162_rn(dr[q], nr);
+                    *reinterpret_cast<__nv_bfloat162 *>(tim + q * A_TILE + off) = __floats2bfloat162_rn(di[q], ni);
+                }
             }
             xt[((j >> 1) * MP + ti) * 2 + (j & 1)] =
                 make_float2((dr[0] + dr[1] + dr[2]) * up, (di[0] + di[1] + di[2]) * up);
@@ -740,15 +750,20 @@ KNIT_DEV void res_b_item(int &ip, int &kk, int &part)
     kk = 2 * ((l & 3) + 4 * (w >> 3));
 }
 
-KNIT_DEV GvPre res_b_load(const Tc128Work &wk, int pass, int c)
+// K positions are X''s stored rows: Gv' columns pos[16 (c % 8) + kk] and the next
+KNIT_DEV GvPre res_b_load(const Tc128Work &wk, const Tc128Smem &sm, int pass, int c)
 {
     int ip, kk, part;
     res_b_item(ip, kk, part);
-    const int i = 32 * pass + ip, k = 16 * (c & 7) + kk;
-    const int f = (k >> 1) * MP + i;
+    const int i = 32 * pass + ip, ks = 16 * (c & 7) + kk;
+    const int k0 = sm.pos[ks], k1 = sm.pos[ks + 1];
+    const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
+    const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
+    const int f0 = ((k0 >> 1) * MP + i) * 2 + (k0 & 1), f1 = ((k1 >> 1) * MP + i) * 2 + (k1 & 1);
+    const float2 h0 = gh[f0], h1 = gh[f1], l0 = gl[f0], l1 = gl[f1];
     GvPre g;
-    g.h = wk.Gh[f];
-    g.l = wk.Gl[f];
+    g.h = make_float4(h0.x, h0.y, h1.x, h1.y);
+    g.l = make_float4(l0.x, l0.y, l1.x, l1.y);
     return g;
 }
 
@@ -1301,13 +1316,13 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             const int npass = (M + 31) / 32;
             for (int pass = 0; pass < npass && !timed_out; ++pass) {
                 const int nseq = 2 * nchunk;
-                GvPre cur = res_b_load(wk, pass, 0), nxt = cur;
+                GvPre cur = res_b_load(wk, sm, pass, 0), nxt = cur;
                 for (int sq = 0; sq < nseq; ++sq) {
                     const int slot = sq & 1;
                     const int c = (sq >> 1) + 8 * (sq & 1);
                     // every thread waits for the MMAs that last read this slot
                     const int ok = sq >= 2 ? mbar_wait(&sm.bar[2 + slot], br.ph[2 + slot]) : 1;
-                    if ((sq & 1) == 0 && sq + 2 < nseq) nxt = res_b_load(wk, pass, (sq >> 1) + 1);
+                    if ((sq & 1) == 0 && sq + 2 < nseq) nxt = res_b_load(wk, sm, pass, (sq >> 1) + 1);
                     const unsigned char *const a = sm.u.res.lres[c];
                     unsigned char *const b = sm.u.res.b[slot];
                     if ((sq & 1) == 0) res_b_build(cur, sm, b, pass);
