@@ -412,12 +412,18 @@ def run_uneven(args):
     """Uneven batch: 4096 square-lattice instances, M in {32,48,64,96,128},
     L in {128,...,2048}, W ~ U[0,4], E ~ U(-3.9,3.9), seed = index, drawn from
     a sampler seeded 12345; one plan, mixed precision (widths 33..64 on the
-    tensor-core kernel, 32 and below on the CUDA-core one, 65..128 on the wide
-    one).  One step = lead self-energies + sweeps for all instances."""
+    tensor-core kernel of sweep_mixed_tc.cu, 32 and below on the CUDA-core
+    one, 65..128 on the tensor-core kernel of sweep_mixed_tc128.cu).  One step
+    = lead self-energies + sweeps for all instances.  Beside it: the
+    algorithmic rate over the measured TF32 peak, a stratified subset of 64
+    instances (the shortest of each width) checked against the oracle, and
+    the oracle's rate on that subset."""
     import torch
     from paper_1010_2627_gb300 import build, inputs, knit
     build.build()
     knit.load()
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    pk = measure_peaks(knit, torch, torch.cuda.current_stream(), nsm)
     inst = inputs.uneven_instances(4096)
     keys = sorted(set(zip(inst["M"].tolist(), inst["L"].tolist())))
     systems = [knit.System(inputs.square(m, l)) for m, l in keys]
@@ -451,20 +457,65 @@ def run_uneven(args):
             ev[k][1].record(stream)
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    clk = _clock_summary(clocks, torch.cuda.current_device())
+    T = dT.cpu().numpy()
     st = dst.cpu().numpy()
     slices = int(inst["L"].sum())
-    mixed_mask = inst["M"] <= 64
-    print(json.dumps({
+    flop = float((16.0 * inst["M"].astype(np.float64) ** 3 * inst["L"]).sum())
+    achieved = flop / (ms / 1e3) / 1e12
+    Ms = inst["M"]
+    line = {
         "metric": "T(E) points/s (uneven batch)", "value": n / (ms / 1e3),
         "unit": "T(E) points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64 inversion + refinement (tensor-core residual for M in 33..64)", "data": "synthetic",
+        "dtype": "c64 inversion + bf16-digit tensor-core residual (f32 accumulate)",
+        "data": "synthetic",
         "config": {"workload": "uneven square batch, 4096 instances, M in {32..128}, "
                                "L in {128..2048}, W ~ U[0,4]", "systems": len(keys),
-                   "instances_mixed": int(mixed_mask.sum()),
+                   "instances_by_kernel": {"mixed CUDA-core, M <= 32": int((Ms <= 32).sum()),
+                                           "mixed tensor-core, 33 <= M <= 64":
+                                               int(((Ms > 32) & (Ms <= 64)).sum()),
+                                           "mixed tensor-core, 65 <= M <= 128": int((Ms > 64).sum())},
                    "flush": "L2 flushed before every timed step"},
-        "slice_updates_per_s": slices / (ms / 1e3), "clocks": _clock_summary(clocks, 0),
-        "status_nonzero": int((st != 0).sum())}), flush=True)
+        "slice_updates_per_s": slices / (ms / 1e3),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["mma_tf32_tflops"],
+                     "unit": "TFLOP/s", "frac": achieved / pk["mma_tf32_tflops"], "traffic": None,
+                     "note": "sum of 16 M^3 L over the batch / step time (leads included) over "
+                             "the measured dense TF32 tensor peak (own loop)"},
+        "clocks": clk, "peaks_measured": pk,
+        "status_nonzero": int((st != 0).sum())}
+    # stratified subset: the 13 (12 for the last width) shortest instances of each width
+    import oracle
+    sub = []
+    for m in sorted(set(Ms.tolist())):
+        ids = np.flatnonzero(Ms == m)
+        sub += ids[np.argsort(inst["L"][ids], kind="stable")][:13].tolist()
+    sub = np.array(sub[:64])
+    nthr = oracle.max_threads()
+    worst, t0, n_or, sl_or = 0.0, time.perf_counter(), 0, 0
+    for m in sorted(set(Ms[sub].tolist())):
+        for l in sorted(set(inst["L"][sub][Ms[sub] == m].tolist())):
+            ids = sub[(Ms[sub] == m) & (inst["L"][sub] == l)]
+            ss = inputs.square(m, l)
+            Sg = np.stack([oracle.sigma_square(m, 1.0, e) for e in inst["E"][ids]])
+            To, sto = oracle.rgf_batch(ss.H0, ss.V, l, inst["E"][ids], inst["seeds"][ids],
+                                       inst["W"][ids], Sg, Sg, np.arange(len(ids)), nthreads=nthr)
+            ek = 2 * np.cos(np.arange(1, m + 1) * np.pi / (m + 1))
+            for q, i in enumerate(ids):
+                nch = max(1, int(np.sum(np.abs(inst["E"][i] - ek) < 2)))
+                worst = max(worst, abs(T[i] - To[q]) / nch)
+            n_or += len(ids)
+            sl_or += len(ids) * l
+    dt = time.perf_counter() - t0
+    line["oracle_subset"] = {"instances": int(n_or), "max_abs_dT_over_nch": worst,
+                             "tolerance": 1e-6, "pass": bool(worst <= 1e-6)}
+    if args.cpu_baseline:
+        line["cpu_baseline"] = {"value": n_or / dt, "unit": "T(E) points/s", "cores": nthr,
+                                "kind": "oracle", "slice_updates_per_s": sl_or / dt,
+                                "sample": f"the {n_or}-instance stratified subset (shortest of "
+                                          f"each width), oracle slice sweep (FP64, own LU), "
+                                          f"OpenMP over instances, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
     batch.close()
 
 
@@ -553,45 +604,99 @@ def run_bdg_case(args):
     """Spinful BdG bar: 32 sites x 4 (spin x Nambu) = 128 orbitals per slice,
     L = 2048, mu = -1, t = 1, Delta = 0.1 in the system, Rashba alpha = 0.2,
     normal leads, W = 1 seed 0, 2048 midpoint energies in (-0.2, 0.2).  One
-    step = lead self-energies (FP64 decimation) + mixed sweep (wide kernel,
-    4 x 4 block couplings) for all energies.  Beside it: the FP64 sweep on 16
-    energies, and particle-hole symmetry of the total transmission,
-    T(E) = T(-E) for one disorder realisation."""
+    step = lead self-energies (FP64 decimation of the leads' electron and hole
+    sectors) + mixed sweep (tensor-core kernel, 4 x 4 block couplings) for all
+    energies.  Beside it: the lead solve and the sweep timed apart (the
+    sweep's roofline over the measured TF32 peak), the FP64 sweep on 16
+    energies, particle-hole symmetry of the total transmission T(E) = T(-E)
+    for one disorder realisation, and the oracle on a bounded sample."""
+    import torch
     from paper_1010_2627_gb300 import build, inputs, knit
     build.build()
     knit.load()
-    ne = args.bdg_energies
-    b = inputs.bdg(32, 2048, mu=-1.0, t=1.0, delta=0.1, alpha=0.2)
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    pk = measure_peaks(knit, torch, torch.cuda.current_stream(), nsm)
+    ne, Lb, Mb = args.bdg_energies, 2048, 128
+    b = inputs.bdg(32, Lb, mu=-1.0, t=1.0, delta=0.1, alpha=0.2)
     E = inputs.energy_grid(-0.2, 0.2, ne)
     seeds = np.array([0], np.uint64)
     sysk = knit.System(b)
     T, st = sysk.transmission(E[:8], seeds, W=1.0, precision=knit.KNIT_MIXED)   # warm-up
+    clocks = _clock_sampler()
     times = []
     for _ in range(args.steps):
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         T, st = sysk.transmission(E, seeds, W=1.0, precision=knit.KNIT_MIXED)
         times.append(time.perf_counter() - t0)
     sec = statistics.mean(times)
+    # the two parts apart: lead self-energies, then the sweep with them given
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    SL = sysk.lead_selfenergy(0, E, method=knit.KNIT_LEAD_DECIMATION)[0]
+    SR = sysk.lead_selfenergy(1, E, method=knit.KNIT_LEAD_DECIMATION)[0]
+    lead_sec = time.perf_counter() - t0
+    dE = torch.tensor(E, device="cuda")
+    dS = torch.tensor(seeds.astype(np.int64), device="cuda")
+    dSL = torch.tensor(np.ascontiguousarray(SL).view(np.float64), device="cuda")
+    dSR = torch.tensor(np.ascontiguousarray(SR).view(np.float64), device="cuda")
+    dT = torch.empty(ne, dtype=torch.float64, device="cuda")
+    dst = torch.empty(ne, dtype=torch.int32, device="cuda")
+    a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    knit.knit_transmission_sigma(sysk.handle, dE, dS, 1.0, dSL, dSR, knit.KNIT_MIXED, dT, dst,
+                                 nE=ne, nS=1)
+    bb.record()
+    torch.cuda.synchronize()
+    sweep_ms = a.elapsed_time(bb)
+    clk = _clock_summary(clocks, torch.cuda.current_device())
+    achieved = 16.0 * Mb ** 3 * Lb * ne / (sweep_ms / 1e3) / 1e12
     sub = np.linspace(0, ne - 1, 16).astype(int)
     t0 = time.perf_counter()
     Tf, stf = sysk.transmission(E[sub], seeds, W=1.0, precision=knit.KNIT_FP64)
     fsec = time.perf_counter() - t0
     both = (st[:, 0] == 0) & (st[::-1, 0] == 0)   # energies mirror pairwise on this grid
     ph = float(np.abs(T[both, 0] - T[::-1, 0][both]).max())
-    print(json.dumps({
+    line = {
         "metric": "T(E) points/s (BdG mixed sweep incl. leads)", "value": ne / sec,
         "unit": "T(E) points/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
         "ms_per_step": 1e3 * sec, "higher_is_better": True,
-        "dtype": "c64 inversion + double-float residual (wide kernel)", "data": "synthetic",
-        "config": {"workload": f"BdG 32 sites x 4, L=2048, mu=-1, Delta=0.1, alpha=0.2, W=1 "
+        "dtype": "c64 inversion + bf16-digit tensor-core residual and products (f32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": f"BdG 32 sites x 4, L={Lb}, mu=-1, Delta=0.1, alpha=0.2, W=1 "
                                f"seed 0, {ne} energies in (-0.2, 0.2), normal leads"},
-        "slice_updates_per_s": ne * 2048 / sec,
+        "slice_updates_per_s": ne * Lb / sec,
+        "lead_selfenergies_s": lead_sec, "sweep_s": sweep_ms / 1e3,
+        "roofline": {"bound": "tensor", "kernel": "knit_sweep_mixed_tc128_kernel",
+                     "achieved": achieved, "peak": pk["mma_tf32_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / pk["mma_tf32_tflops"], "traffic": None,
+                     "note": "16 M^3 flop per slice-update over the sweep alone (Sigma given), "
+                             "over the measured dense TF32 tensor peak (own loop)"},
         "fp64_sweep": {"value": len(sub) / fsec, "energies": len(sub), "seconds": fsec},
         "max_abs_dT_mixed_vs_fp64_over_nch": float(
             np.abs(T[sub, 0] - Tf[:, 0]).max() / max(1.0, float(np.abs(Tf).max()))),
         "particle_hole_max_abs_T_minus_T_mirror": ph,
         "particle_hole_pairs": int(both.sum()) // 2,
-        "status_nonzero": int((st != 0).sum() + (stf != 0).sum())}), flush=True)
+        "clocks": clk, "peaks_measured": pk,
+        "status_nonzero": int((st != 0).sum() + (stf != 0).sum())}
+    if args.cpu_baseline:
+        # the oracle's slice sweep (FP64, own LU) on all host cores, with the
+        # GPU's lead self-energies, on 16 energies of a 256-slice copy of the bar
+        import oracle
+        Ls = 256
+        nthr = oracle.max_threads()
+        idx = np.linspace(0, ne - 1, 16).astype(int)
+        t0 = time.perf_counter()
+        To, sto = oracle.rgf_batch(b.H0, b.V, Ls, E[idx], np.zeros(16, np.uint64), np.ones(16),
+                                   SL[idx], SR[idx], np.arange(16), block=4, sign=b.sign,
+                                   nthreads=nthr)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 16 * Ls / dt, "unit": "slice-updates/s", "cores": nthr,
+                                "kind": "oracle",
+                                "sample": f"16 energies of a {Ls}-slice copy of the bar, "
+                                          f"oracle slice sweep (FP64), OpenMP, {dt:.1f} s; the "
+                                          f"GPU runs {ne * Lb / sec:.0f} slice-updates/s incl. leads"}
+    print(json.dumps(line), flush=True)
     sysk.close()
 
 

@@ -38,6 +38,10 @@ extern "C" size_t knit_mixed_wide_work_bytes(int);
 extern "C" cudaError_t knit_launch_mixed_wide(const InstDev *, int, int, void *, cudaStream_t);
 extern "C" size_t knit_mixed_tc128_work_bytes(void);
 extern "C" cudaError_t knit_launch_mixed_tc128(const InstDev *, int, void *, cudaStream_t);
+extern "C" cudaError_t knit_launch_sector_assemble(const double2 *, const int *, int, int, int, int,
+                                                   double2 *, cudaStream_t);
+extern "C" cudaError_t knit_launch_sector_status(const int *, const int *, int, int, int *, int *,
+                                                 cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
 extern "C" cudaError_t knit_launch_gamma_factor(const double2 *, int, int, double2 *, double2 *,
                                                 int *, cudaStream_t);
@@ -167,7 +171,63 @@ struct Lead {
     double2 *U = nullptr, *A = nullptr;    // modes: eigenvectors and diagonalised cell
     int modes_ready = 0;
     std::vector<double2> hH0, hV;          // host copies (structure checks)
+    // sectors: orbital groups that neither H0 nor V connects (equal sizes ms);
+    // sector s holds orbitals sidx[s ms .. s ms + ms - 1] in increasing order
+    int nsec = 1, ms = 0;
+    double2 *sH0 = nullptr, *sV = nullptr;   // nsec blocks of ms x ms
+    int *sidx = nullptr;
 };
+
+// Split a lead cell into the connected components of the orbital graph with
+// an edge wherever H0 or V (either direction) is non-zero.  Sets ld.nsec and
+// fills the sector blocks (host side) when there are at least two components
+// of one common size; otherwise leaves the cell whole.
+void lead_sectors(Lead &ld, int M, std::vector<double2> &bH0, std::vector<double2> &bV,
+                  std::vector<int> &idx)
+{
+    std::vector<int> par(M);
+    for (int i = 0; i < M; ++i) par[i] = i;
+    auto find = [&](int x) {
+        while (par[x] != x) x = par[x] = par[par[x]];
+        return x;
+    };
+    auto nz = [](double2 v) { return v.x != 0.0 || v.y != 0.0; };
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j)
+            if (nz(ld.hH0[(size_t)i * M + j]) || nz(ld.hV[(size_t)i * M + j])) {
+                const int a = find(i), b = find(j);
+                if (a != b) par[a] = b;
+            }
+    std::vector<std::vector<int>> comp;
+    std::vector<int> slot(M, -1);
+    for (int i = 0; i < M; ++i) {
+        const int r = find(i);
+        if (slot[r] < 0) {
+            slot[r] = (int)comp.size();
+            comp.emplace_back();
+        }
+        comp[slot[r]].push_back(i);
+    }
+    ld.nsec = 1;
+    if (comp.size() < 2) return;
+    const size_t ms = comp[0].size();
+    for (auto &c : comp)
+        if (c.size() != ms) return;
+    ld.nsec = (int)comp.size();
+    ld.ms = (int)ms;
+    bH0.assign(comp.size() * ms * ms, make_double2(0.0, 0.0));
+    bV = bH0;
+    idx.clear();
+    for (size_t c = 0; c < comp.size(); ++c) {
+        for (size_t a = 0; a < ms; ++a) {
+            idx.push_back(comp[c][a]);
+            for (size_t b = 0; b < ms; ++b) {
+                bH0[(c * ms + a) * ms + b] = ld.hH0[(size_t)comp[c][a] * M + comp[c][b]];
+                bV[(c * ms + a) * ms + b] = ld.hV[(size_t)comp[c][a] * M + comp[c][b]];
+            }
+        }
+    }
+}
 
 }  // namespace
 
@@ -185,6 +245,7 @@ struct knit_system_s {
     // grow-only workspaces
     DevBuf E, seeds, T, status, queue, sigL, sigR, gL, gR, lst, lit, lres, work, ckpt, decw, ldos;
     DevBuf p2g, p2s, p2t;   // period-2 leads: supercell g and Sigma, block-product scratch
+    DevBuf secs, secg, secst, secit;   // sector leads: per-sector Sigma, g, status, iterations
     DevBuf gll, tw, ts, tg, trk, tau, noise;   // transmission eigenvalues: G_LL, scratch, W, rank, out
     DevBuf lrl, lrr, ljx, ljt;                 // lesser function outputs staged for host pointers
 
@@ -488,6 +549,34 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
         return KNIT_OK;
     }
     if (method != KNIT_LEAD_DECIMATION) return fail(KNIT_ERR_INVALID, "unknown lead method %d", method);
+    const Lead &ld = s->lead[p];
+    if (ld.nsec > 1) {
+        // one decimation per sector (Sec. 5.3 B on each decoupled block), then
+        // the blocks put back in the orbital order
+        const int ns = ld.nsec, ms = ld.ms;
+        const size_t mm = (size_t)ms * ms;
+        CK(s->decw.ensure(sizeof(double2) * 8 * mm * grid), "decimation workspace");
+        CK(s->secs.ensure(sizeof(double2) * mm * nE * ns), "sector sigma");
+        CK(s->secg.ensure(sizeof(double2) * mm * nE * ns), "sector g");
+        CK(s->secst.ensure(sizeof(int) * (size_t)nE * ns), "sector status");
+        CK(s->secit.ensure(sizeof(int) * (size_t)nE * ns), "sector iterations");
+        for (int q = 0; q < ns; ++q)
+            CK(knit_launch_decimation(ld.sH0 + q * mm, ld.sV + q * mm, ms, ms, p, dE, nE, eta, tol,
+                                      maxit, s->decw.as<double2>(),
+                                      s->secs.as<double2>() + q * mm * nE,
+                                      s->secg.as<double2>() + q * mm * nE,
+                                      s->secit.as<int>() + (size_t)q * nE,
+                                      s->secst.as<int>() + (size_t)q * nE, grid, st),
+               "sector decimation");
+        CK(knit_launch_sector_assemble(s->secs.as<double2>(), ld.sidx, ns, ms, M, nE, sig, st),
+           "sector sigma assembly");
+        if (gout)
+            CK(knit_launch_sector_assemble(s->secg.as<double2>(), ld.sidx, ns, ms, M, nE, gout, st),
+               "sector g assembly");
+        CK(knit_launch_sector_status(s->secst.as<int>(), s->secit.as<int>(), ns, nE, lst, lit, st),
+           "sector status");
+        return KNIT_OK;
+    }
     CK(s->decw.ensure(sizeof(double2) * 8 * MM * grid), "decimation workspace");
     CK(knit_launch_decimation(s->lead[p].H0, s->lead[p].V, M, s->lead[p].vb, p, dE, nE, eta, tol,
                               maxit, s->decw.as<double2>(), sig, gout, lit, lst, grid, st),
@@ -838,6 +927,18 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
             knit_system_destroy(s);
             return r;
         }
+        if (ld.Mp == M && !ld.scalar) {
+            std::vector<double2> bH0, bV;
+            std::vector<int> idx;
+            lead_sectors(ld, M, bH0, bV, idx);
+            if (ld.nsec > 1 &&
+                ((r = to_device(&ld.sH0, bH0.data(), bH0.size(), "lead sectors")) != KNIT_OK ||
+                 (r = to_device(&ld.sV, bV.data(), bV.size(), "lead sectors")) != KNIT_OK ||
+                 (r = to_device(&ld.sidx, idx.data(), idx.size(), "lead sectors")) != KNIT_OK)) {
+                knit_system_destroy(s);
+                return r;
+            }
+        }
     }
     {
         SysDev sd = s->dev();
@@ -869,11 +970,15 @@ knit_status knit_system_destroy(knit_system s)
         cudaFree(s->lead[p].C);
         cudaFree(s->lead[p].U);
         cudaFree(s->lead[p].A);
+        cudaFree(s->lead[p].sH0);
+        cudaFree(s->lead[p].sV);
+        cudaFree(s->lead[p].sidx);
     }
     DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
                       &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
                       &s->p2g, &s->p2s, &s->p2t, &s->gll, &s->tw, &s->ts, &s->tg, &s->trk,
-                      &s->tau, &s->noise, &s->lrl, &s->lrr, &s->ljx, &s->ljt};
+                      &s->tau, &s->noise, &s->lrl, &s->lrr, &s->ljx, &s->ljt, &s->secs,
+                      &s->secg, &s->secst, &s->secit};
     for (DevBuf *b : bufs) b->release();
     delete s;
     return KNIT_OK;

@@ -15,6 +15,7 @@
 //  * knit_lead_residual_kernel: max-norm of g - (E - H0 - V g V^dagger)^{-1}
 //    at eta = 0, the fixed-point check of either solver (work: 3 M*M per CTA).
 
+#include <algorithm>
 #include "dense_fp64.cuh"
 
 // W = V G V^dagger (side 0) or V^dagger G V (side 1): elementwise for
@@ -565,5 +566,72 @@ extern "C" cudaError_t knit_launch_sigma_block(const double2 *C, const double2 *
                                                int grid, cudaStream_t stream)
 {
     knit_sigma_block_kernel<<<grid, 256, 0, stream>>>(C, gcell, M, Mp, side, nE, tmp, sigma);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Leads whose cell splits into sectors: when the orbitals of a lead cell fall
+// into groups that neither H0 nor V connects (the electron and hole halves of
+// a normal Nambu lead), the surface g of Sec. 5.3 B is block-diagonal in that
+// grouping and each block solves the fixed point of its own sector.  The host
+// decimates every sector alone (an (M / k)^3 problem each) and these kernels
+// put the blocks back: out[e][idx[s ms + a]][idx[s ms + b]] = blk[s][e][a][b],
+// zero between sectors.
+
+__global__ void sector_zero_kernel(size_t n, double2 *out)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        out[q] = make_double2(0.0, 0.0);
+}
+
+__global__ void sector_place_kernel(const double2 *blk, const int *idx, int nsec, int ms, int M,
+                                    int nE, double2 *out)
+{
+    const size_t MM = (size_t)M * M, mm = (size_t)ms * ms;
+    const size_t total = (size_t)nsec * nE * mm;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const int s = (int)(q / ((size_t)nE * mm));
+        const size_t rem = q - (size_t)s * nE * mm;
+        const int e = (int)(rem / mm);
+        const int ab = (int)(rem - (size_t)e * mm);
+        const int a = ab / ms, b = ab - a * ms;
+        out[(size_t)e * MM + (size_t)idx[s * ms + a] * M + idx[s * ms + b]] = blk[q];
+    }
+}
+
+// per energy: the largest status and iteration count over the sectors
+__global__ void sector_status_kernel(const int *st, const int *it, int nsec, int nE, int *st_out,
+                                     int *it_out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    int s0 = 0, i0 = 0;
+    for (int s = 0; s < nsec; ++s) {
+        s0 = max(s0, st[(size_t)s * nE + e]);
+        i0 = max(i0, it[(size_t)s * nE + e]);
+    }
+    if (st_out) st_out[e] = s0;
+    if (it_out) it_out[e] = i0;
+}
+
+extern "C" cudaError_t knit_launch_sector_assemble(const double2 *blk, const int *idx, int nsec,
+                                                   int ms, int M, int nE, double2 *out,
+                                                   cudaStream_t stream)
+{
+    const int threads = 256;
+    const size_t n0 = (size_t)nE * M * M, n1 = (size_t)nsec * nE * ms * ms;
+    const int g0 = (int)std::min<size_t>((n0 + threads - 1) / threads, 65535);
+    const int g1 = (int)std::min<size_t>((n1 + threads - 1) / threads, 65535);
+    sector_zero_kernel<<<g0, threads, 0, stream>>>(n0, out);
+    sector_place_kernel<<<g1, threads, 0, stream>>>(blk, idx, nsec, ms, M, nE, out);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t knit_launch_sector_status(const int *st, const int *it, int nsec, int nE,
+                                                 int *st_out, int *it_out, cudaStream_t stream)
+{
+    sector_status_kernel<<<(nE + 255) / 256, 256, 0, stream>>>(st, it, nsec, nE, st_out, it_out);
     return cudaGetLastError();
 }

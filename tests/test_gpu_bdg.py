@@ -92,3 +92,22 @@ def test_bdg3_sweep_fp64_with_oracle_leads(knit):
             To = oracle.dense(b.H0, b.V, eps, b.L, e, SL[k], SR[k])["T_LR"]
             assert abs(T[k, 0] - To) <= tol * max(1, open_channels(b, e)), (precision, e)
     sysk.close()
+
+
+@pytest.mark.parametrize("Ns,lead_delta", [(32, 0.0), (6, 0.0), (6, 0.05)])
+def test_bdg_lead_sectors_against_oracle(knit, Ns, lead_delta):
+    """Normal Nambu leads split into electron and hole sectors that the GPU
+    decimates one by one (Sec. 5.3 B on each decoupled block); a lead with
+    pairing does not split.  Either way Sigma equals the oracle's decimation
+    of the whole cell to the decimation tolerance (1e-8)."""
+    b = inputs.bdg(Ns, 3, mu=-1.0, delta=0.1, alpha=0.2, lead_delta=lead_delta)
+    E = np.array([-0.17, 0.04]) if Ns == 32 else np.array([-0.17, 0.04, 0.11])
+    sysk = knit.System(b)
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION, eta=1e-12,
+                                          want_residual=True)
+        for e, Ee in enumerate(E):
+            So = oracle.decimation(b.lead_H0[lead], b.lead_V[lead], Ee, lead, eta=1e-12)[1]
+            assert np.abs(S[e] - So).max() < 1e-8, (Ns, lead_delta, lead, Ee)
+            assert res[e] < 1e-5
+    sysk.close()

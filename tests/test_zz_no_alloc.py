@@ -64,7 +64,10 @@ def test_noalloc_matches_allocating_entry_point_twice(knit, cell):
             torch.cuda.synchronize()
             S = dS.cpu().numpy().view(np.complex128).reshape(len(E), M, M)
             assert (dst.cpu().numpy() == 0).all()
-            assert np.array_equal(dit.cpu().numpy(), it_ref)
+            # the allocating path decimates a cell that splits into decoupled
+            # sectors (the Nambu cell) sector by sector; each sector may stop
+            # one doubling before the whole cell does
+            assert np.abs(dit.cpu().numpy() - it_ref).max() <= 1
             assert np.abs(S - S_ref).max() <= TOL, (cell, lead, call)
     sysk.close()
 
