@@ -116,7 +116,8 @@ def _peaks():
 
 # iterations per launch of each peak loop (a few ms each on GB300)
 PEAK_ITERS = {"mma_bf16_tflops": 40000, "mma_tf32_tflops": 40000, "dfma_tflops": 2000,
-              "ffma_tflops": 20000}
+              "ffma_tflops": 20000, "mma_bf16_pattern_tflops": 8000,
+              "mma_tf32_pattern_tflops": 8000}
 
 
 def measure_peaks(knit, torch, stream, nsm, reps=5):
@@ -125,7 +126,9 @@ def measure_peaks(knit, torch, stream, nsm, reps=5):
     `reps` launches after one warm-up launch (median), with the SM clock
     sampled during the loops.  Returns TFLOP/s per kind."""
     kinds = {"mma_bf16_tflops": knit.KNIT_PEAK_MMA_BF16, "mma_tf32_tflops": knit.KNIT_PEAK_MMA_TF32,
-             "dfma_tflops": knit.KNIT_PEAK_DFMA, "ffma_tflops": knit.KNIT_PEAK_FFMA}
+             "dfma_tflops": knit.KNIT_PEAK_DFMA, "ffma_tflops": knit.KNIT_PEAK_FFMA,
+             "mma_bf16_pattern_tflops": knit.KNIT_PEAK_MMA_RESIDUAL,
+             "mma_tf32_pattern_tflops": knit.KNIT_PEAK_MMA_RESIDUAL_TF32}
     out = {}
     clocks = _clock_sampler()
     for name, kind in kinds.items():
@@ -143,10 +146,18 @@ def measure_peaks(knit, torch, stream, nsm, reps=5):
         out[name] = flop / (ms / 1e3) / 1e12
     out["clocks"] = _clock_summary(clocks, torch.cuda.current_device())
     out["nsm"] = nsm
-    out["how"] = ("own loops (csrc/peaks.cu): one CTA per SM issuing back-to-back "
-                  "tcgen05.mma M=128 N=256 (K=16 bf16 / K=8 tf32) into one tensor-memory "
-                  "accumulator; 8 x 256 threads per SM with 8 independent FMA chains each; "
-                  f"CUDA events, median of {reps} launches after a warm-up")
+    # the roofline denominators: the higher of the two tensor-core loops per type
+    out["mma_bf16_single_tflops"] = out["mma_bf16_tflops"]
+    out["mma_tf32_single_tflops"] = out["mma_tf32_tflops"]
+    out["mma_bf16_tflops"] = max(out["mma_bf16_tflops"], out["mma_bf16_pattern_tflops"])
+    out["mma_tf32_tflops"] = max(out["mma_tf32_tflops"], out["mma_tf32_pattern_tflops"])
+    out["how"] = ("own loops (csrc/peaks.cu), one CTA per SM, one thread issuing back-to-back "
+                  "tcgen05.mma, M=128: (a) N=256 on one operand pair into two accumulators in "
+                  "turn, (b) the wide sweep's residual chunk (three A tiles, N=256 and "
+                  "N=192/128/64 into staggered accumulators); mma_*_tflops = the higher of "
+                  "(a) and (b) (K=16 bf16 / K=8 tf32); 8 x 256 threads per SM with 8 "
+                  f"independent FMA chains each; CUDA events, median of {reps} launches "
+                  "after a warm-up")
     return out
 
 

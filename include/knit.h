@@ -410,7 +410,8 @@ knit_status knit_lead_decimation_noalloc(const knit_c128 *H0, const knit_c128 *V
 
 /* kinds of knit_peak_probe */
 enum { KNIT_PEAK_MMA_BF16 = 0, KNIT_PEAK_MMA_TF32 = 1, KNIT_PEAK_DFMA = 2, KNIT_PEAK_FFMA = 3,
-       KNIT_PEAK_MMA_N64 = 4, KNIT_PEAK_MMA_N16 = 5, KNIT_PEAK_MMA_RESIDUAL = 6 };
+       KNIT_PEAK_MMA_N64 = 4, KNIT_PEAK_MMA_N16 = 5, KNIT_PEAK_MMA_RESIDUAL = 6,
+       KNIT_PEAK_MMA_RESIDUAL_TF32 = 7 };
 
 /* Peak-rate microbenchmarks (no paper counterpart): the denominators of the
  * roofline fractions that the benchmark reports.  Launches one fixed loop on
@@ -422,6 +423,7 @@ enum { KNIT_PEAK_MMA_BF16 = 0, KNIT_PEAK_MMA_TF32 = 1, KNIT_PEAK_DFMA = 2, KNIT_
  *   KNIT_PEAK_MMA_N64 / KNIT_PEAK_MMA_N16: the bf16 loop with N = 64 / 16;
  *   KNIT_PEAK_MMA_RESIDUAL: per iteration the six MMAs of one K-chunk of the
  *     wide tensor-core sweep's residual (three A tiles, N = 256 + 192 / 128 / 64);
+ *   KNIT_PEAK_MMA_RESIDUAL_TF32: the same pattern with kind::tf32 (K = 8);
  *   KNIT_PEAK_DFMA / KNIT_PEAK_FFMA: FP64 / FP32 fused multiply-add loops on
  *     the CUDA cores (eight 256-thread blocks per SM, 128 * iters FMA each).
  * timed_out: host int or NULL; when given, the call waits for the launch

@@ -8,11 +8,11 @@
 // block whose CUDA cores would otherwise be shared by the pivot chain and
 // the updates.  Per panel of 8 columns:
 //
-//  * warp 0 alone takes the 8 pivot steps on the panel columns (registers);
-//    after them one thread per column forms the panel's rows v_k of V,
+//  * warp 0 alone takes the 8 pivot steps on the panel columns (registers),
+//    and inside each step forms that step's row v_k of V for all 64 columns,
 //    v_k = (X[p_k, :] + e_k - sum_{c<k} u_c[p_k] v_c) / pivot_k, from the
-//    matrix at the start of the panel (the forward substitution of
-//    gj_lookahead), so that the pivot chain carries nothing else;
+//    matrix at the start of the panel -- the forward substitution of
+//    gj_lookahead, spread over the latency of the pivot chain;
 //  * all threads cut U (64 x 8) and V (8 x 64) into three bf16 terms each,
 //    x = h + m + l exactly for every fp32 x (bit masks, no conversions),
 //    into the operand tiles of
@@ -92,6 +92,7 @@ __device__ __forceinline__ int gj_tc(float2 *X, int M, GjTcWork &w, GJShared<64>
             for (int t = 0; t < R2; ++t)
 #pragma unroll
                 for (int c = 0; c < NB; ++c) pc[t][c] = X[(lane + 32 * t) * MP + K + c];
+            float2 v[NB][R2];    // v_k for columns lane + 32t
             bool bad = false;
             auto steps = [&](auto fullc) {
                 constexpr bool FULLP = decltype(fullc)::value;
@@ -152,10 +153,23 @@ __device__ __forceinline__ int gj_tc(float2 *X, int M, GjTcWork &w, GJShared<64>
                         w.U[i * UST + kk] = u[t];
                         open[t] = open[t] && i != p;
                     }
-                    if (lane == 0) {
-                        g.perm[K + kk] = p;
-                        g.rinv[kk] = rinv;
+                    // v_kk from row p of the matrix at the start of the panel
+                    __syncwarp();
+                    float2 xr[R2];
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) {
+                        xr[t] = X[p * MP + lane + 32 * t];
+                        if (lane + 32 * t == K + kk) xr[t].x += 1.f;
                     }
+#pragma unroll
+                    for (int c = 0; c < kk; ++c) {
+                        const float2 uc = w.U[p * UST + c];
+#pragma unroll
+                        for (int t = 0; t < R2; ++t) xr[t] = cfmsf(uc, v[c][t], xr[t]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < R2; ++t) v[kk][t] = cmulf(xr[t], rinv);
+                    if (lane == 0) g.perm[K + kk] = p;
                 }
             };
             if (nk == NB) steps(BoolC<true>{});
@@ -165,31 +179,18 @@ __device__ __forceinline__ int gj_tc(float2 *X, int M, GjTcWork &w, GJShared<64>
             for (int kk = 0; kk < NB; ++kk)
                 if (kk >= nk)
 #pragma unroll
-                    for (int t = 0; t < R2; ++t) w.U[(lane + 32 * t) * UST + kk] = make_float2(0.f, 0.f);
+                    for (int t = 0; t < R2; ++t) {
+                        v[kk][t] = make_float2(0.f, 0.f);
+                        w.U[(lane + 32 * t) * UST + kk] = make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+            for (int kk = 0; kk < NB; ++kk)
+#pragma unroll
+                for (int t = 0; t < R2; ++t) w.V[kk * MP + lane + 32 * t] = v[kk][t];
             if (lane == 0) g.flag = bad ? 1 : 0;
         }
         __syncthreads();
         if (g.flag) return ST_SINGULAR;
-        if (tid < MP) {
-            // the panel's v vectors, one column j per thread, from the pivot
-            // rows of the matrix at the start of the panel
-            const int j = tid;
-            float2 vj[NB];
-#pragma unroll
-            for (int kk = 0; kk < NB; ++kk) {
-                vj[kk] = make_float2(0.f, 0.f);
-                if (kk < nk) {
-                    const int p = g.perm[K + kk];
-                    float2 r = X[p * MP + j];
-                    if (j == K + kk) r.x += 1.f;
-#pragma unroll
-                    for (int c = 0; c < kk; ++c) r = cfmsf(w.U[p * UST + c], vj[c], r);
-                    vj[kk] = cmulf(r, g.rinv[kk]);
-                }
-                w.V[kk * MP + j] = vj[kk];
-            }
-        }
-        __syncthreads();
 
         // bf16 terms of the operands: thread (n, r, s) splits eight values
         // once and writes their three terms, 16 bytes each: s = 0, 1 the

@@ -239,6 +239,7 @@ struct knit_system_s {
     SysDev *d_sys = nullptr;   // device copy of dev() for the kernels' system table
     int *h0_rowptr = nullptr, *h0_col = nullptr;
     int2 *h0_edges = nullptr;  // nonzeros of H0 above the diagonal, row-major (x < y)
+    float4 *h0_dfh = nullptr, *h0_dfl = nullptr;   // H0 as double-float, width-128 layout
     int n_edges = 0;
     Lead lead[2];
     int leads_same = 0;
@@ -265,6 +266,8 @@ struct knit_system_s {
         s.h0_rowptr = h0_rowptr;
         s.h0_col = h0_col;
         s.h0_val = h0_val;
+        s.h0_dfh = h0_dfh;
+        s.h0_dfl = h0_dfl;
         return s;
     }
 };
@@ -914,6 +917,24 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
         knit_system_destroy(s);
         return r;
     }
+    if (M <= 128) {
+        // H0 in double-float, columns in pairs (jp, row i) as the width-128 sweep reads it
+        std::vector<float4> fh(64 * 128, make_float4(0.f, 0.f, 0.f, 0.f)), fl = fh;
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                const double2 v = H0[(size_t)i * M + j];
+                const float hx = (float)v.x, hy = (float)v.y;
+                const float lx = (float)(v.x - (double)hx), ly = (float)(v.y - (double)hy);
+                float4 &a = fh[(j >> 1) * 128 + i], &b = fl[(j >> 1) * 128 + i];
+                if (j & 1) { a.z = hx; a.w = hy; b.z = lx; b.w = ly; }
+                else { a.x = hx; a.y = hy; b.x = lx; b.y = ly; }
+            }
+        if ((r = to_device(&s->h0_dfh, fh.data(), fh.size(), "H0 double-float")) != KNIT_OK ||
+            (r = to_device(&s->h0_dfl, fl.data(), fl.size(), "H0 double-float")) != KNIT_OK) {
+            knit_system_destroy(s);
+            return r;
+        }
+    }
     if (d->onsite && (r = to_device(&s->onsite, hon.data(), hon.size(), "onsite")) != KNIT_OK) {
         knit_system_destroy(s);
         return r;
@@ -963,6 +984,8 @@ knit_status knit_system_destroy(knit_system s)
     cudaFree(s->h0_col);
     cudaFree(s->h0_val);
     cudaFree(s->h0_edges);
+    cudaFree(s->h0_dfh);
+    cudaFree(s->h0_dfl);
     cudaFree(s->d_sys);
     for (int p = 0; p < 2; ++p) {
         cudaFree(s->lead[p].H0);

@@ -192,6 +192,9 @@ struct SysDev {
     const int *h0_rowptr;      // M+1
     const int *h0_col;         // nnz
     const double2 *h0_val;     // nnz
+    // H0 as double-float (hi, lo) in the width-128 layout: column pair jp,
+    // row i at float4 jp * 128 + i; zero outside M x M (M <= 128, else null)
+    const float4 *h0_dfh, *h0_dfl;
 };
 
 struct InstDev {

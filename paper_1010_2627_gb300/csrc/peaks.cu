@@ -7,6 +7,9 @@
 //   KNIT_PEAK_MMA_TF32  the same with kind::tf32 (K = 8 per instruction)
 //   KNIT_PEAK_MMA_N64 / _N16   the bf16 loop with N = 64 / N = 16
 //   KNIT_PEAK_MMA_RESIDUAL     the wide sweep's residual MMA pattern per K-chunk
+//                              (six MMAs into staggered accumulators; _TF32 the
+//                              same with kind::tf32), which sustains a higher
+//                              rate than the single-tile loop
 //   KNIT_PEAK_DFMA      FP64 fused multiply-add on the CUDA cores
 //   KNIT_PEAK_FFMA      FP32 fused multiply-add on the CUDA cores
 //
@@ -90,14 +93,27 @@ peak_mma_kernel(long long iters, int tf32, int shape, int *status)
             const uint32_t id = (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
             for (long long it = 0; it < iters; ++it) mma_bf16(tmem, ad, bd, id, it > 0 ? 1u : 0u);
         } else {
+            const uint32_t fmt = tf32 ? 2u : 1u;
             for (long long it = 0; it < iters; ++it) {
                 const uint64_t b0 = smem_desc(smem_u32(sm.b[it & 1]));
                 const uint64_t b4 = smem_desc(smem_u32(sm.b[it & 1] + 4 * 64 * 32));
                 for (int q = 0; q < 3; ++q) {
                     const uint64_t aq = smem_desc(smem_u32(sm.a[q]));
-                    mma_bf16(tmem + 64 * q, aq, b0, idesc_bf16_m128(256), it > 0 || q > 0 ? 1u : 0u);
-                    mma_bf16(tmem + 64 * (q + 4), aq, b4, idesc_bf16_m128((uint32_t)(64 * (3 - q))),
-                             it > 0 || q > 0 ? 1u : 0u);
+                    const uint32_t acc = it > 0 || q > 0 ? 1u : 0u;
+                    const uint32_t i0 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+                    const uint32_t i1 = (1u << 4) | (fmt << 7) | (fmt << 10) |
+                                        (((uint32_t)(64 * (3 - q)) >> 3) << 17) | ((128u >> 4) << 24);
+                    if (tf32) {
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                                     ::"r"(tmem + 64 * q), "l"(aq), "l"(b0), "r"(i0), "r"(acc));
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                                     ::"r"(tmem + 64 * (q + 4)), "l"(aq), "l"(b4), "r"(i1), "r"(acc));
+                    } else {
+                        mma_bf16(tmem + 64 * q, aq, b0, i0, acc);
+                        mma_bf16(tmem + 64 * (q + 4), aq, b4, i1, acc);
+                    }
                 }
             }
         }
@@ -164,13 +180,15 @@ extern "C" knit_status knit_peak_probe(int32_t kind, int64_t iters, int32_t nsm,
     }
     case KNIT_PEAK_MMA_N64:
     case KNIT_PEAK_MMA_N16:
-    case KNIT_PEAK_MMA_RESIDUAL: {
+    case KNIT_PEAK_MMA_RESIDUAL:
+    case KNIT_PEAK_MMA_RESIDUAL_TF32: {
         if (!status && cudaGetSymbolAddress((void **)&status, g_peak_status) != cudaSuccess)
             return KNIT_ERR_CUDA;
         const int shape = kind == KNIT_PEAK_MMA_N64 ? 1 : kind == KNIT_PEAK_MMA_N16 ? 2 : 3;
+        const int tf32 = kind == KNIT_PEAK_MMA_RESIDUAL_TF32;
         const double n = shape == 1 ? 64.0 : shape == 2 ? 16.0 : 1152.0;
-        *flop = 2.0 * 128.0 * n * 16.0 * (double)iters * nsm;
-        peak_mma_kernel<<<nsm, PEAK_THREADS_MMA, 0, st>>>(iters, 0, shape, status);
+        *flop = 2.0 * 128.0 * n * (tf32 ? 8.0 : 16.0) * (double)iters * nsm;
+        peak_mma_kernel<<<nsm, PEAK_THREADS_MMA, 0, st>>>(iters, tf32, shape, status);
         break;
     }
     case KNIT_PEAK_DFMA:

@@ -99,6 +99,9 @@ struct Tc128Smem {
             alignas(128) unsigned char a[2][NDX * A_TILE];
             alignas(128) unsigned char b[2][3 * BT_256];
         } ref;
+        struct {                                       // slice set-up: V's 4 x 4 block rows
+            float2 vh[MP * 4], vl[MP * 4];             // row r: V[r][4 (r / 4) + b], b = 0 .. 3
+        } va;
     } u;
     double eps[MP];
     int vuni[2];
@@ -259,29 +262,30 @@ __global__ void fill_status128(int *st, int n, int v)
 // ---------------------------------------------------------------------------
 // A. Gv' in place over the state, X = -Gv'_hi into tensor memory
 
-// V entry (r, c) of parity q as double-float (conjugated when conj is set)
-KNIT_DEV void v_df(const double2 *Vq, int M, int r, int c, bool conj, float2 &h, float2 &l)
-{
-    const double2 v = (r < M && c < M) ? Vq[(size_t)r * M + c] : make_double2(0.0, 0.0);
-    to_df(v.x, h.x, l.x);
-    to_df(conj ? -v.y : v.y, h.y, l.y);
-}
-
-// V g V^dagger for 4 x 4 block-diagonal V, in place: work item (block B, C;
-// column half hc) forms columns 4C + 2hc, 4C + 2hc + 1 of the block
-__device__ void gv_blocks4(Tc128Work &wk, const SysDev &s, int M, int q)
+// V g V^dagger for 4 x 4 block-diagonal V (coupling of parity q) into the
+// workspace buffers S1 / S2 (hi / lo, same layout as the state): V's block
+// rows are staged in shared memory first; work item (block B, C; column
+// half hc) forms columns 4C + 2hc, 4C + 2hc + 1 of block (B, C)
+__device__ void gv_blocks4(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, int M, int q)
 {
     const size_t MM = (size_t)M * M;
     const double2 *Vq = s.V + (size_t)(q % s.Vperiod) * MM;
+    for (int e = threadIdx.x; e < MP * 4; e += NTH) {
+        const int r = e >> 2, c = 4 * (r >> 2) + (e & 3);
+        const double2 v = (r < M && c < M) ? Vq[(size_t)r * M + c] : make_double2(0.0, 0.0);
+        float2 h, l;
+        to_df(v.x, h.x, l.x);
+        to_df(v.y, h.y, l.y);
+        sm.u.va.vh[e] = h;
+        sm.u.va.vl[e] = l;
+    }
+    __syncthreads();
+    float4 *const oh = reinterpret_cast<float4 *>(wk.S1);
+    float4 *const ol = reinterpret_cast<float4 *>(wk.S2);
     const int nb = (M + 3) / 4;
-    // all reads of the state happen before any write (the two column halves
-    // of a block read the whole block)
-    float4 outh[4][4], outl[4][4];   // [item][row a] as float4 = 2 complex columns
-    int idxs[4];
-    int nitem = 0;   // at most 2 * 32 * 32 / NTH = 4 items per thread
-    for (int e = threadIdx.x; e < 2 * nb * nb; e += NTH, ++nitem) {
+    for (int e = threadIdx.x; e < 2 * nb * nb; e += NTH) {
         const int hc = e & 1, B = (e >> 1) % nb, C = (e >> 1) / nb;
-        // u[a][s] = sum_b g[a][b] conj(V[4C+s][4C+b]) for s = 2hc, 2hc + 1
+        // u[a][s] = sum_b g[4B+a][4C+b] conj(V[4C+2hc+s][4C+b])
         float2 uh[4][2], ul[4][2];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -297,12 +301,14 @@ __device__ void gv_blocks4(Tc128Work &wk, const SysDev &s, int M, int q)
             }
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
+                const int vr = 4 * C + 2 * hc + s2;
                 float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    float2 vh, vl;
-                    v_df(Vq, M, 4 * C + 2 * hc + s2, 4 * C + b, true, vh, vl);
+                    float2 vh = sm.u.va.vh[vr * 4 + b], vl = sm.u.va.vl[vr * 4 + b];
                     if (vh.x == 0.f && vh.y == 0.f) continue;
+                    vh.y = -vh.y;
+                    vl.y = -vl.y;
                     float2 ph, pl;
                     cdf_mul(gh[b], gl[b], vh, vl, ph, pl);
                     cdf_add(sh, sl, ph, pl);
@@ -314,51 +320,43 @@ __device__ void gv_blocks4(Tc128Work &wk, const SysDev &s, int M, int q)
         // Gv[a][s] = sum_b V[4B+a][4B+b] u[b][s]
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            float2 oh[2], ol[2];
+            float2 gvh[2], gvl[2];
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
                 float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    float2 vh, vl;
-                    v_df(Vq, M, 4 * B + a, 4 * B + b, false, vh, vl);
+                    const float2 vh = sm.u.va.vh[(4 * B + a) * 4 + b], vl = sm.u.va.vl[(4 * B + a) * 4 + b];
                     if (vh.x == 0.f && vh.y == 0.f) continue;
                     float2 ph, pl;
                     cdf_mul(vh, vl, uh[b][s2], ul[b][s2], ph, pl);
                     cdf_add(sh, sl, ph, pl);
                 }
-                oh[s2] = sh;
-                ol[s2] = sl;
+                gvh[s2] = sh;
+                gvl[s2] = sl;
             }
-            if (nitem < 4) {
-                outh[nitem][a] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
-                outl[nitem][a] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
-            }
+            const int idx = (2 * C + hc) * MP + 4 * B + a;
+            oh[idx] = make_float4(gvh[0].x, gvh[0].y, gvh[1].x, gvh[1].y);
+            ol[idx] = make_float4(gvl[0].x, gvl[0].y, gvl[1].x, gvl[1].y);
         }
-        if (nitem < 4) idxs[nitem] = (2 * C + hc) * MP + 4 * B;
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (k < nitem)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                wk.Gh[idxs[k] + a] = outh[k][a];
-                wk.Gl[idxs[k] + a] = outl[k][a];
-            }
 }
 
-// Gv (V g V^dagger or Sigma_L) + Sigma_R, elementwise, in place; zero in the
-// padding.  vmode: 0 general diagonal V, 1 V g V^dagger already formed or
-// |v|^2 = 1, 2 scalar |v|^2 (vch + vcl)
+// Gv' = (V g V^dagger or Sigma_L) + Sigma_R + H0 - diag(E - onsite) in
+// double-float, elementwise into the state buffers; zero in the padding.
+// vmode: 0 general diagonal V, 1 V g V^dagger already formed (4 x 4 block
+// couplings: read from S1 / S2) or |v|^2 = 1, 2 scalar |v|^2 (vch + vcl)
 __device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, int M, int n, int L,
-                               int vmode, const double2 *SL, const double2 *SR)
+                               int vmode, bool from_s, const double2 *SL, const double2 *SR)
 {
     const int q = n & 1;
     const double2 *Vd = s.V + (size_t)(q % s.Vperiod) * M * M;   // diagonal at stride M + 1
+    const float4 *srch = from_s ? reinterpret_cast<const float4 *>(wk.S1) : wk.Gh;
+    const float4 *srcl = from_s ? reinterpret_cast<const float4 *>(wk.S2) : wk.Gl;
     for (int e = threadIdx.x; e < (MP / 2) * MP; e += NTH) {
         const int i = e % MP, jp = e / MP;
-        const float4 h4 = wk.Gh[e], l4 = wk.Gl[e];
+        const float4 h4 = srch[e], l4 = srcl[e];
+        const float4 hh4 = s.h0_dfh[e], hl4 = s.h0_dfl[e];
         float2 oh[2], ol[2];
 #pragma unroll
         for (int s2 = 0; s2 < 2; ++s2) {
@@ -392,6 +390,13 @@ __device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, in
                     to_df(v.y, c, d);
                     cdf_add(gh, gl, make_float2(a, c), make_float2(b, d));
                 }
+                cdf_add(gh, gl, s2 ? make_float2(hh4.z, hh4.w) : make_float2(hh4.x, hh4.y),
+                        s2 ? make_float2(hl4.z, hl4.w) : make_float2(hl4.x, hl4.y));
+                if (i == j) {
+                    float dh, dl;
+                    to_df(sm.eps[i], dh, dl);
+                    cdf_add(gh, gl, make_float2(-dh, 0.f), make_float2(-dl, 0.f));
+                }
             } else {
                 gh = gl = make_float2(0.f, 0.f);
             }
@@ -400,31 +405,6 @@ __device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, in
         }
         wk.Gh[e] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
         wk.Gl[e] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
-    }
-}
-
-// + H0 - diag(eps), one row per thread (sparse H0)
-__device__ void gv_add_h0(Tc128Work &wk, const Tc128Smem &sm, const SysDev &s, int M)
-{
-    float2 *const gh = reinterpret_cast<float2 *>(wk.Gh);
-    float2 *const gl = reinterpret_cast<float2 *>(wk.Gl);
-    for (int i = threadIdx.x; i < M; i += NTH) {
-        // float2 index of (i, j): ((j >> 1) * MP + i) * 2 + (j & 1)
-        {
-            const int f = ((i >> 1) * MP + i) * 2 + (i & 1);
-            float dh, dl;
-            to_df(sm.eps[i], dh, dl);
-            cdf_add(gh[f], gl[f], make_float2(-dh, 0.f), make_float2(-dl, 0.f));
-        }
-        for (int c = s.h0_rowptr[i]; c < s.h0_rowptr[i + 1]; ++c) {
-            const int j = s.h0_col[c];
-            const double2 hd = s.h0_val[c];
-            float2 hh, hl;
-            to_df(hd.x, hh.x, hl.x);
-            to_df(hd.y, hh.y, hl.y);
-            const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
-            cdf_add(gh[f], gl[f], hh, hl);
-        }
     }
 }
 
@@ -1287,15 +1267,11 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             // ---- A
             slice_diag<MP, NTH>(sm.eps, s, ip.ms, ip.W, ip.E, n);
             for (int i = tid; i < MP; i += NTH) sm.rmaxu[i] = 0u;
-            if (vb == 4 && n > 0) {
-                gv_blocks4(wk, s, M, n & 1);
-                __syncthreads();
-            }
+            if (vb == 4 && n > 0) gv_blocks4(wk, sm, s, M, n & 1);
+            __syncthreads();   // eps (and the block pass's output) complete
             const int q = n & 1;
             const int vmode = vb == 4 ? 1 : (sm.vuni[q] == 1 ? 1 : (sm.vuni[q] == 2 ? 2 : 0));
-            gv_elementwise(wk, sm, s, M, n, L, vmode, ip.SL, ip.SR);
-            __syncthreads();
-            gv_add_h0(wk, sm, s, M);
+            gv_elementwise(wk, sm, s, M, n, L, vmode, vb == 4 && n > 0, ip.SL, ip.SR);
             __syncthreads();
             fence_after();
             x_to_tmem(wk, sm, tmem, M);

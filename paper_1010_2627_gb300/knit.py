@@ -25,6 +25,7 @@ KNIT_FP64, KNIT_MIXED, KNIT_MIXED_CUDACORE = 0, 1, 2
 KNIT_LEAD_AUTO, KNIT_LEAD_MODES, KNIT_LEAD_DECIMATION, KNIT_LEAD_LEARNED = 0, 1, 2, 3
 KNIT_PEAK_MMA_BF16, KNIT_PEAK_MMA_TF32, KNIT_PEAK_DFMA, KNIT_PEAK_FFMA = 0, 1, 2, 3
 KNIT_PEAK_MMA_N64, KNIT_PEAK_MMA_N16, KNIT_PEAK_MMA_RESIDUAL = 4, 5, 6
+KNIT_PEAK_MMA_RESIDUAL_TF32 = 7
 
 P = ctypes.c_void_p
 i32, f64 = ctypes.c_int32, ctypes.c_double
