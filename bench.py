@@ -689,7 +689,10 @@ def run_bdg_case(args):
         "particle_hole_max_abs_T_minus_T_mirror": ph,
         "particle_hole_pairs": int(both.sum()) // 2,
         "clocks": clk, "peaks_measured": pk,
-        "status_nonzero": int((st != 0).sum() + (stf != 0).sum())}
+        "status_nonzero": int((st != 0).sum() + (stf != 0).sum()),
+        "status_mixed": {int(c): int((st == c).sum()) for c in np.unique(st) if c != 0},
+        "status_fp64": {int(c): int((stf == c).sum()) for c in np.unique(stf) if c != 0},
+        "energies_status_nonzero": [float(E[k]) for k in np.nonzero(st[:, 0] != 0)[0][:8]]}
     if args.cpu_baseline:
         # the oracle's slice sweep (FP64, own LU) on all host cores, with the
         # GPU's lead self-energies, on 16 energies of a 256-slice copy of the bar
@@ -709,6 +712,122 @@ def run_bdg_case(args):
                                           f"GPU runs {ne * Lb / sec:.0f} slice-updates/s incl. leads"}
     print(json.dumps(line), flush=True)
     sysk.close()
+
+
+def run_graphene_case(args):
+    """Graphene armchair ribbon: honeycomb lattice t = 2.7 as a brick wall of
+    256 sites per row, L = 1024 rows, on-site disorder uniform in [-0.5, 0.5]
+    (W = 1, seed 0), 8192 midpoint energies in (-2, 2), clean ribbon leads
+    (period 2).  One step = both lead self-energies (the leads' two-slice
+    supercells decimated block by block in the basis of transverse modes) +
+    the KNIT_MIXED sweep, which the library runs on the half-row chain (128
+    orbitals, 2048 slices, tensor-core kernel), host E in, host T out.
+    Beside it: leads and sweep timed apart on the device (the sweep's roofline
+    over the measured TF32 peak), the FP64 row sweep on 16 energies, the
+    oracle on an 8-row copy, and the oracle's speed on a bounded sample."""
+    import torch
+    import oracle
+    from paper_1010_2627_gb300 import build, inputs, knit
+    build.build()
+    knit.load()
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    pk = measure_peaks(knit, torch, torch.cuda.current_stream(), nsm)
+    ne, Lg, Mg, Wg = args.graphene_energies, args.graphene_L, 256, 1.0
+    ss = inputs.armchair(Mg, Lg)
+    E = inputs.energy_grid(-2.0, 2.0, ne)
+    seeds = np.array([0], np.uint64)
+    t0 = time.perf_counter()
+    sysk = knit.System(ss)
+    create_s = time.perf_counter() - t0
+    kind, blocks = sysk.info(knit.KNIT_MIXED)
+    T, st = sysk.transmission(E[:8], seeds, W=Wg, precision=knit.KNIT_MIXED)   # warm-up
+    clocks = _clock_sampler()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T, st = sysk.transmission(E, seeds, W=Wg, precision=knit.KNIT_MIXED)
+        times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    # the two parts apart, on the device: lead self-energies, then the sweep
+    MM = Mg * Mg
+    dE = torch.tensor(E, device="cuda")
+    dS = torch.tensor(seeds.astype(np.int64), device="cuda")
+    dSL = torch.empty(2 * MM * ne, dtype=torch.float64, device="cuda")
+    dSR = torch.empty(2 * MM * ne, dtype=torch.float64, device="cuda")
+    dT = torch.empty(ne, dtype=torch.float64, device="cuda")
+    dst = torch.empty(ne, dtype=torch.int32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    knit.knit_lead_selfenergy(sysk.handle, 0, dE, dSL)
+    knit.knit_lead_selfenergy(sysk.handle, 1, dE, dSR)
+    ev[1].record()
+    knit.knit_transmission_sigma(sysk.handle, dE, dS, Wg, dSL, dSR, knit.KNIT_MIXED, dT, dst,
+                                 nE=ne, nS=1)
+    ev[2].record()
+    torch.cuda.synchronize()
+    lead_ms, sweep_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    clk = _clock_summary(clocks, torch.cuda.current_device())
+    Th = Mg // 2
+    achieved = 16.0 * Th ** 3 * (2 * Lg) * ne / (sweep_ms / 1e3) / 1e12
+    sub = np.linspace(0, ne - 1, 16).astype(int)
+    t0 = time.perf_counter()
+    Tf, stf = sysk.transmission(E[sub], seeds, W=Wg, precision=knit.KNIT_FP64)
+    fsec = time.perf_counter() - t0
+    sysk.close()
+    # the oracle's row sweep on an 8-row copy with the GPU's lead self-energies
+    Lo, Eo = 8, E[np.linspace(0, ne - 1, 4).astype(int)]
+    so = inputs.armchair(Mg, Lo)
+    ko = knit.System(so)
+    oSL, oSR = ko.lead_selfenergy(0, Eo)[0], ko.lead_selfenergy(1, Eo)[0]
+    To_gpu, sto_gpu = ko.transmission(Eo, seeds, W=Wg, precision=knit.KNIT_MIXED)
+    ko.close()
+    nthr = oracle.max_threads()
+    To, sto = oracle.rgf_batch(so.H0, so.V, Lo, Eo, np.zeros(len(Eo), np.uint64),
+                               np.full(len(Eo), Wg), oSL, oSR, np.arange(len(Eo)), nthreads=nthr)
+    line = {
+        "metric": "T(E) points/s (graphene mixed sweep incl. leads)", "value": ne / sec,
+        "unit": "T(E) points/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": 1e3 * sec, "higher_is_better": True,
+        "dtype": "c64 inversion + bf16-digit tensor-core residual and products (f32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": f"graphene armchair ribbon t=2.7, {Mg} sites per row, L={Lg} rows, "
+                               f"W=1 (uniform [-0.5, 0.5]) seed 0, {ne} energies in (-2, 2), "
+                               f"clean ribbon leads"},
+        "sweep_kernel": {knit.KNIT_SWEEP_MIXED_HALF_ROWS: "half-row chain on the tensor-core "
+                         "kernel (128 orbitals, 2L slices)"}.get(kind, kind),
+        "lead_blocks": blocks, "system_create_s": create_s,
+        "row_slice_updates_per_s": ne * Lg / sec,
+        "lead_selfenergies_s": lead_ms / 1e3, "sweep_s": sweep_ms / 1e3,
+        "roofline": {"bound": "tensor", "kernel": "knit_sweep_mixed_tc128_kernel",
+                     "achieved": achieved, "peak": pk["mma_tf32_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / pk["mma_tf32_tflops"], "traffic": None,
+                     "note": "16 M^3 flop per half-row slice-update (M = 128, 2L slices) over "
+                             "the sweep alone (Sigma given), over the measured dense TF32 "
+                             "tensor peak (own loop)"},
+        "fp64_row_sweep": {"value": len(sub) / fsec, "energies": len(sub), "seconds": fsec},
+        "max_abs_dT_mixed_vs_fp64": float(np.abs(T[sub, 0] - Tf[:, 0]).max()),
+        "oracle_subset": {"rows": Lo, "energies": len(Eo),
+                          "max_abs_dT": float(np.abs(To_gpu[:, 0] - To).max()),
+                          "status_nonzero": int((sto != 0).sum() + (sto_gpu != 0).sum())},
+        "clocks": clk, "peaks_measured": pk,
+        "status_nonzero": int((st != 0).sum() + (stf != 0).sum()),
+        "status_mixed": {int(c): int((st == c).sum()) for c in np.unique(st) if c != 0}}
+    if args.cpu_baseline:
+        # the oracle's row sweep (FP64, own LU) on all host cores, 16 energies
+        # of a 16-row copy with the GPU's lead self-energies
+        Lc = 16
+        sc_ = inputs.armchair(Mg, Lc)
+        t0 = time.perf_counter()
+        oracle.rgf_batch(sc_.H0, sc_.V, Lc, np.repeat(Eo, 4), np.zeros(16, np.uint64),
+                         np.full(16, Wg), oSL, oSR, np.repeat(np.arange(4), 4), nthreads=nthr)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 16 * Lc / dt, "unit": "row slice-updates/s",
+                                "cores": nthr, "kind": "oracle",
+                                "sample": f"16 instances of a {Lc}-row copy of the ribbon, oracle "
+                                          f"row sweep (FP64), OpenMP, {dt:.1f} s; the GPU runs "
+                                          f"{ne * Lg / sec:.0f} row slice-updates/s incl. leads"}
+    print(json.dumps(line), flush=True)
 
 
 def run_eigen_case(args):
@@ -990,8 +1109,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="bench",
                     choices=["bench", "peaks", "profile", "uneven", "ldos", "bdg", "eigen", "lesser",
-                             "graph"])
+                             "graph", "graphene"])
     ap.add_argument("--bdg-energies", dest="bdg_energies", type=int, default=2048)
+    ap.add_argument("--graphene-energies", dest="graphene_energies", type=int, default=8192)
+    ap.add_argument("--graphene-L", dest="graphene_L", type=int, default=1024)
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--profile-M", dest="profile_M", type=int, default=64)
     ap.add_argument("--gpus", type=int, default=1)
@@ -1016,6 +1137,8 @@ def main():
         run_eigen_case(args)
     elif args.case == "graph":
         run_graph_case(args)
+    elif args.case == "graphene":
+        run_graphene_case(args)
     elif args.case == "lesser":
         run_lesser_case(args)
     elif args.impl == "reference":

@@ -74,13 +74,16 @@ enum {
                        residual exact to ~2^-48; the state g_n is carried as
                        hi + lo floats.  For 33 <= M <= 64 the residual's dense
                        product runs on the tensor cores (bf16 digit slices,
-                       f32 accumulation), otherwise on CUDA cores.  Widths
-                       65..128 (and any width with 4 x 4 block couplings)
-                       use a 512-thread variant with the state in device
-                       memory; M > 128 or other coupling structures run the
+                       f32 accumulation), below on CUDA cores.  Widths
+                       65..128, and any width up to 128 with 4 x 4 block or
+                       tridiagonal couplings, use a 512-thread tensor-core
+                       variant (tcgen05, accumulators in tensor memory) with
+                       the state in device memory; M > 128 runs the
                        KNIT_FP64 sweep instead. */
     KNIT_MIXED_CUDACORE = 2  /* KNIT_MIXED with the residual always accumulated
-                                in double-float arithmetic on CUDA cores */
+                                in double-float arithmetic on CUDA cores
+                                (diagonal and 4 x 4 block couplings; other
+                                systems run in KNIT_FP64) */
 };
 
 /* Lead solver. */
@@ -108,8 +111,10 @@ typedef struct {
     const double *onsite;        /* L*M explicit diagonal shifts added to H0, or NULL;
                                     when given, W and seeds are ignored */
     const knit_c128 *V;          /* Vperiod*M*M, H_{n,n-1} = V[n % Vperiod]; each V must be
-                                    block-diagonal with `block` x `block` blocks */
-    int32_t Vperiod;             /* 1 or 2 */
+                                    block-diagonal with `block` x `block` blocks, or
+                                    tridiagonal (nonzeros only at |i - j| <= 1, as in a
+                                    honeycomb ribbon sliced by half-rows) */
+    int32_t Vperiod;             /* 1, 2 or 4 */
     const knit_c128 *lead_H0[2]; /* left/right lead cell (M*M); NULL = H0 */
     const knit_c128 *lead_V[2];  /* left/right lead inter-cell hopping (M*M); NULL = V[0] */
     int32_t lead_Vperiod[2];     /* 0 or 1: one coupling as above.  2: lead_V[p] holds two
@@ -125,8 +130,15 @@ typedef struct {
 
 /* Copy the description into a new system (all pointers are read during the
  * call only; host or device memory).  Returns KNIT_ERR_INVALID for sizes out
- * of range, a non-block-diagonal V, or a lead_V whose structure the lead
- * solvers do not support. */
+ * of range, a V neither block-diagonal nor tridiagonal, or a lead_V whose
+ * structure the lead solvers do not support.  A system wider than 128 whose
+ * rows split into two halves (those coupled to the previous row and the
+ * rest) with the same Hamiltonian block on every half-row and couplings of
+ * period <= 2 (a honeycomb ribbon, Sec. 6.3) also gets its half-row chain
+ * (width M / 2, 2L slices, couplings of period 4), on which KNIT_MIXED
+ * transmissions then run; a period-2 lead whose supercell splits into
+ * blocks of at most 4 modes in the eigenbasis of its cell Hamiltonian is
+ * solved block by block (knit_system_info reports both). */
 knit_status knit_system_create(const knit_system_desc *desc, knit_system *out);
 
 /* Free a system and its device workspace (NULL is accepted). */
@@ -220,6 +232,23 @@ knit_status knit_lesser(knit_system sys, const double *E, int32_t nE, const uint
 
 /* Number of nonzero entries of H0 above its diagonal (the edges of jt). */
 knit_status knit_system_num_edges(knit_system sys, int32_t *count);
+
+/* Sweep kernels (knit_system_info). */
+enum {
+    KNIT_SWEEP_FP64 = 0,           /* complex128 sweep */
+    KNIT_SWEEP_MIXED_NARROW = 1,   /* mixed, widths <= 64, diagonal couplings */
+    KNIT_SWEEP_MIXED_CUDACORE = 2, /* mixed, residual on CUDA cores, widths <= 128 */
+    KNIT_SWEEP_MIXED_TC128 = 3,    /* mixed, tensor-core kernel for widths <= 128 */
+    KNIT_SWEEP_MIXED_HALF_ROWS = 4 /* KNIT_SWEEP_MIXED_TC128 on the half-row chain */
+};
+
+/* Which sweep kernel knit_transmission (energy x seed grid) runs for this
+ * system at `precision` (*sweep, a KNIT_SWEEP_* value), and into how many
+ * independent blocks the decimation of each lead splits (lead_blocks[2];
+ * 1 = the whole cell or two-slice supercell).  Host only, no device work.
+ * KNIT_ERR_INVALID for NULL arguments or an unknown precision. */
+knit_status knit_system_info(knit_system sys, int32_t precision, int32_t *sweep,
+                             int32_t *lead_blocks);
 
 /* ---------------------------------------------------------------------
  * Arbitrary geometries (Sec. 5.3: knitting through an interface of varying

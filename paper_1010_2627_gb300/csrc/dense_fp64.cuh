@@ -157,6 +157,14 @@ KNIT_DEV double2 vxvd64(const double2 *V, const double2 *X, int M, int vb, int i
     return acc;
 }
 
+// decimation retries: eta, 100 eta, 1e4 eta, 1e6 eta; a surface g counts as
+// converged when it satisfies its fixed point at its own eta to this relative
+// max-norm and lies on the retarded branch (i(g - g^dagger) positive
+// semidefinite): at eta ~ 1e-12 the doubling can lose enough precision on wide
+// leads to land on another solution of the fixed-point equation
+constexpr int DEC_ATTEMPTS = 4;
+constexpr double DEC_SELF_TOL = 1e-5;
+
 // (V^dagger X V)_ij for a block-diagonal V
 KNIT_DEV double2 vdxv64(const double2 *V, const double2 *X, int M, int vb, int i, int j)
 {
@@ -174,18 +182,21 @@ KNIT_DEV double2 vdxv64(const double2 *V, const double2 *X, int M, int vb, int i
     return acc;
 }
 
-// C = (A V^dagger) B for a block-diagonal V, i.e. sum_k (A V^dagger)_ik B_kj
-static __device__ void gemm64_avd_b(const double2 *A, const double2 *V, int vb, const double2 *B,
-                             double2 *C, int M)
+// C = (A V^dagger) B for a block-diagonal V, i.e. sum_k (A V^dagger)_ik B_kj;
+// V's nonzeros lie within `band` of the diagonal (band >= vb: anywhere in the
+// block; a tridiagonal V is one block of M with band 1)
+static __device__ void gemm64_avd_b(const double2 *A, const double2 *V, int vb, int band,
+                                    const double2 *B, double2 *C, int M)
 {
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
         int i = e / M, j = e - i * M;
         double2 acc = make_double2(0.0, 0.0);
         for (int kb = 0; kb < M; kb += vb) {
             for (int k = kb; k < kb + vb; ++k) {
-                // (A V^dagger)_ik = sum_{l in block} A_il conj(V_kl)
+                // (A V^dagger)_ik = sum_{l in block, |l - k| <= band} A_il conj(V_kl)
                 double2 avd = make_double2(0.0, 0.0);
-                for (int l = kb; l < kb + vb; ++l)
+                const int l0 = max(kb, k - band), l1 = min(kb + vb, k + band + 1);
+                for (int l = l0; l < l1; ++l)
                     avd = cfma(A[(size_t)i * M + l], cconj(V[(size_t)k * M + l]), avd);
                 acc = cfma(avd, B[(size_t)k * M + j], acc);
             }

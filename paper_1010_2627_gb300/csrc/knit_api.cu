@@ -43,6 +43,15 @@ extern "C" cudaError_t knit_launch_sector_assemble(const double2 *, const int *,
 extern "C" cudaError_t knit_launch_sector_status(const int *, const int *, int, int, int *, int *,
                                                  cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
+extern "C" cudaError_t knit_launch_small_decimation(const double2 *, const double2 *, int, int, int,
+                                                    const double *, int, double, double, int,
+                                                    double2 *, int *, int *, cudaStream_t);
+extern "C" cudaError_t knit_launch_p2_sector_sigma(const double2 *, const int *, int, int, int,
+                                                   const double2 *, int, int, double2 *, double2 *,
+                                                   int, cudaStream_t);
+extern "C" cudaError_t knit_launch_p2_sector_cell(const double2 *, const int *, int, int,
+                                                  const double2 *, int, int, double2 *, int,
+                                                  cudaStream_t);
 extern "C" cudaError_t knit_launch_gamma_factor(const double2 *, int, int, double2 *, double2 *,
                                                 int *, cudaStream_t);
 extern "C" size_t knit_tau_work_bytes(int);
@@ -176,6 +185,13 @@ struct Lead {
     int nsec = 1, ms = 0;
     double2 *sH0 = nullptr, *sV = nullptr;   // nsec blocks of ms x ms
     int *sidx = nullptr;
+    // period-2 lead split in the cell's eigenbasis U (held in U): nsec
+    // supercell blocks of 2 ms x 2 ms in sH0 / sV, the modes of block c at
+    // sidx[c ms ..]; Cq: the nnz nonzero rows nzr[] of (C or C^dagger) U,
+    // modes in block order, transposed (nm x nnz)
+    double2 *Cq = nullptr;
+    int *nzr = nullptr;
+    int nnz = 0;
 };
 
 // Split a lead cell into the connected components of the orbital graph with
@@ -233,7 +249,14 @@ void lead_sectors(Lead &ld, int M, std::vector<double2> &bH0, std::vector<double
 
 struct knit_system_s {
     int M = 0, L = 0, block = 1, Vperiod = 1, vb = 1;
+    int vtri = 0;   // some V is tridiagonal, not block-diagonal (vb = M then)
     int device = 0, nsm = 1;
+    // the same system sliced by half-rows (width M / 2, 2L slices), which runs
+    // its KNIT_MIXED sweeps when M > 128; hsup: the half-rows the left and the
+    // right self-energy act on (2 x M / 2 sites of the end rows)
+    knit_system_s *half = nullptr;
+    int *hsup = nullptr;
+    int *xmap = nullptr;   // set on a half-row system: its orbitals' row sites
     double2 *H0 = nullptr, *V = nullptr, *h0_val = nullptr;
     double *sign = nullptr, *onsite = nullptr;
     SysDev *d_sys = nullptr;   // device copy of dev() for the kernels' system table
@@ -259,6 +282,7 @@ struct knit_system_s {
         s.Vperiod = Vperiod;
         s.vdiag = vb == 1;
         s.vb = vb;
+        s.vband = vtri ? 1 : vb;
         s.H0 = H0;
         s.V = V;
         s.sign = sign;
@@ -268,6 +292,7 @@ struct knit_system_s {
         s.h0_val = h0_val;
         s.h0_dfh = h0_dfh;
         s.h0_dfl = h0_dfl;
+        s.xmap = xmap;
         return s;
     }
 };
@@ -352,6 +377,17 @@ int block_structure(const double2 *A, int M, int block)
     return diag ? 1 : (bdiag ? block : 0);
 }
 
+// nonzeros only on the main diagonal and the two next to it
+bool tridiagonal(const double2 *A, int M)
+{
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            const double2 v = A[(size_t)i * M + j];
+            if ((v.x != 0.0 || v.y != 0.0) && std::abs(i - j) > 1) return false;
+        }
+    return true;
+}
+
 bool hermitian(const double2 *A, int M)
 {
     double mx = 0.0;
@@ -415,6 +451,279 @@ knit_status stage_out(DevBuf &buf, T *dst, size_t count, T **out, bool *host, co
     CK(buf.ensure(sizeof(T) * count), what);
     *out = buf.as<T>();
     return KNIT_OK;
+}
+
+// A period-2 lead (cell H0, couplings A inside the two-slice supercell and B
+// between supercells, C = B to the system) in the eigenbasis U of H0: the
+// supercell blocks that U^dagger A U and U^dagger B U leave decoupled (entries
+// below 1e-11 of the largest |H0|, |A|, |B| count as zero), each solved by
+// itself (lead_modes_p2.cu).  Leaves ld.nsec = 1 (the whole supercell) when
+// the eigenbasis does not split it into blocks of equal size up to 4 modes.
+knit_status p2_mode_sectors(Lead &ld, int M, int side, const std::vector<double2> &H0,
+                            const double2 *A, const double2 *B)
+{
+    const size_t MM = (size_t)M * M;
+    std::vector<double2> U(MM), D(MM);
+    {
+        double2 *dA = nullptr;
+        CK(dev_alloc((void **)&dA, sizeof(double2) * MM), "lead eigenbasis");
+        if (!ld.U) {
+            cudaError_t e = dev_alloc((void **)&ld.U, sizeof(double2) * MM);
+            if (e != cudaSuccess) {
+                cudaFree(dA);
+                CK(e, "lead eigenbasis");
+            }
+        }
+        cudaError_t e = cudaMemcpy(dA, H0.data(), sizeof(double2) * MM, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = knit_launch_jacobi(dA, ld.U, M, nullptr, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+        if (e == cudaSuccess) e = cudaMemcpy(U.data(), ld.U, sizeof(double2) * MM, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(D.data(), dA, sizeof(double2) * MM, cudaMemcpyDeviceToHost);
+        cudaFree(dA);
+        CK(e, "lead eigenbasis");
+    }
+    auto cab = [](double2 v) { return std::fabs(v.x) + std::fabs(v.y); };
+    auto cm = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+    double scale = 0.0, off = 0.0;
+    for (size_t q = 0; q < MM; ++q) {
+        scale = std::max({scale, cab(H0[q]), cab(A[q]), cab(B[q])});
+        if (q / M != q % M) off = std::max(off, cab(D[q]));
+    }
+    const double tol = 1e-11 * std::max(scale, 1e-300);
+    if (!(off <= tol)) return KNIT_OK;   // the eigensolver did not settle: keep the supercell
+    // X^ = U^dagger X U
+    auto sandwich = [&](const double2 *X) {
+        std::vector<double2> T(MM), R(MM);
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int k = 0; k < M; ++k) {
+                    const double2 t = cm(X[(size_t)i * M + k], U[(size_t)k * M + j]);
+                    acc.x += t.x;
+                    acc.y += t.y;
+                }
+                T[(size_t)i * M + j] = acc;
+            }
+        for (int i = 0; i < M; ++i)
+            for (int j = 0; j < M; ++j) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int k = 0; k < M; ++k) {
+                    const double2 u = U[(size_t)k * M + i];
+                    const double2 t = cm(make_double2(u.x, -u.y), T[(size_t)k * M + j]);
+                    acc.x += t.x;
+                    acc.y += t.y;
+                }
+                R[(size_t)i * M + j] = acc;
+            }
+        return R;
+    };
+    const std::vector<double2> Ah = sandwich(A), Bh = sandwich(B);
+    std::vector<int> par(M);
+    for (int i = 0; i < M; ++i) par[i] = i;
+    auto find = [&](int x) {
+        while (par[x] != x) x = par[x] = par[par[x]];
+        return x;
+    };
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j)
+            if (cab(Ah[(size_t)i * M + j]) > tol || cab(Bh[(size_t)i * M + j]) > tol) {
+                const int a = find(i), b = find(j);
+                if (a != b) par[a] = b;
+            }
+    std::vector<std::vector<int>> comp;
+    std::vector<int> slot(M, -1);
+    for (int i = 0; i < M; ++i) {
+        const int r = find(i);
+        if (slot[r] < 0) {
+            slot[r] = (int)comp.size();
+            comp.emplace_back();
+        }
+        comp[slot[r]].push_back(i);
+    }
+    const int ms = (int)comp[0].size(), ns = (int)comp.size();
+    if (ns < 2 || ms > 4) return KNIT_OK;
+    for (auto &c : comp)
+        if ((int)c.size() != ms) return KNIT_OK;
+    // per block: the supercell in the mode basis, (slice h, mode a) at h ms + a;
+    // left  [[lam, A^], [A^+, lam]] with coupling B^ from slice 1 to slice 0
+    // outward, right [[lam, A^+], [A^, lam]] with B^ from slice 0 to slice 1
+    const int N = 2 * ms;
+    std::vector<double2> sH((size_t)ns * N * N, make_double2(0.0, 0.0)), sV = sH;
+    std::vector<int> idx;
+    for (int c = 0; c < ns; ++c) {
+        double2 *h = sH.data() + (size_t)c * N * N, *v = sV.data() + (size_t)c * N * N;
+        for (int a = 0; a < ms; ++a) {
+            idx.push_back(comp[c][a]);
+            for (int b = 0; b < ms; ++b) {
+                const size_t ab = (size_t)comp[c][a] * M + comp[c][b], ba = (size_t)comp[c][b] * M + comp[c][a];
+                const double2 ah = Ah[ab], ahd = make_double2(Ah[ba].x, -Ah[ba].y);
+                if (a == b) h[a * N + b] = h[(ms + a) * N + ms + b] = D[ab];
+                if (side == 0) {
+                    h[a * N + ms + b] = ah;
+                    h[(ms + a) * N + b] = ahd;
+                    v[(ms + a) * N + b] = Bh[ab];
+                } else {
+                    h[(ms + a) * N + b] = ah;
+                    h[a * N + ms + b] = ahd;
+                    v[a * N + ms + b] = Bh[ab];
+                }
+            }
+        }
+    }
+    // Chat = C U (left) or C^dagger U (right), C = B; its nonzero rows
+    std::vector<int> nz;
+    std::vector<double2> Ch(MM);
+    for (int i = 0; i < M; ++i) {
+        bool any = false;
+        for (int j = 0; j < M; ++j) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < M; ++k) {
+                const double2 c = side == 0 ? B[(size_t)i * M + k]
+                                            : make_double2(B[(size_t)k * M + i].x, -B[(size_t)k * M + i].y);
+                const double2 t = cm(c, U[(size_t)k * M + j]);
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+            Ch[(size_t)i * M + j] = acc;
+            any = any || acc.x != 0.0 || acc.y != 0.0;
+        }
+        if (any) nz.push_back(i);
+    }
+    if (nz.empty()) return KNIT_OK;
+    const int nnz = (int)nz.size(), nm = ns * ms;
+    std::vector<double2> Cq((size_t)nm * nnz);
+    for (int q = 0; q < nm; ++q)
+        for (int r = 0; r < nnz; ++r) Cq[(size_t)q * nnz + r] = Ch[(size_t)nz[r] * M + idx[q]];
+    knit_status r;
+    if ((r = to_device(&ld.sH0, sH.data(), sH.size(), "lead blocks")) != KNIT_OK ||
+        (r = to_device(&ld.sV, sV.data(), sV.size(), "lead blocks")) != KNIT_OK ||
+        (r = to_device(&ld.sidx, idx.data(), idx.size(), "lead blocks")) != KNIT_OK ||
+        (r = to_device(&ld.Cq, Cq.data(), Cq.size(), "lead blocks")) != KNIT_OK ||
+        (r = to_device(&ld.nzr, nz.data(), nz.size(), "lead blocks")) != KNIT_OK)
+        return r;
+    ld.nsec = ns;
+    ld.ms = ms;
+    ld.nnz = nnz;
+    return KNIT_OK;
+}
+
+// Half-row slicing.  A system whose rows split into halves a_n (the sites
+// coupled to row n - 1) and b_n (the rest) such that the coupling to row n + 1
+// leaves from b_n only, every half-row carries the same Hamiltonian block, and
+// the split repeats with period 2 -- the honeycomb ribbon of Sec. 6.3 cut
+// between its two zigzag sublattice rows -- is the chain a_0, b_0, a_1, b_1,
+// ... of half the width: H_{b_n, a_n} = H0[b_n, a_n], H_{a_n, b_{n-1}} =
+// V_n[a_n, b_{n-1}] (couplings of period 4).  The same Green function, so the
+// same transmission, at a quarter of the dense work per row.
+struct HalfRows {
+    std::vector<int> a[2], b[2];   // by row parity, sites in increasing order
+};
+
+bool half_rows(const std::vector<double2> &H0, const std::vector<double2> &V, int M, int P, int B,
+               HalfRows &h)
+{
+    if (B != 1 || (P != 1 && P != 2) || M % 2 || M / 2 > 128) return false;
+    auto nz = [](double2 v) { return v.x != 0.0 || v.y != 0.0; };
+    const size_t MM = (size_t)M * M;
+    for (int pi = 0; pi < 2; ++pi) {
+        const double2 *Vn = V.data() + (size_t)(pi % P) * MM, *Vx = V.data() + (size_t)((pi + 1) % P) * MM;
+        std::vector<char> ina(M, 0);
+        for (int x = 0; x < M; ++x)
+            for (int y = 0; y < M; ++y)
+                if (nz(Vn[(size_t)x * M + y])) ina[x] = 1;
+        h.a[pi].clear();
+        h.b[pi].clear();
+        for (int x = 0; x < M; ++x) (ina[x] ? h.a[pi] : h.b[pi]).push_back(x);
+        if ((int)h.a[pi].size() != M / 2) return false;
+        for (int x = 0; x < M; ++x)
+            for (int y = 0; y < M; ++y)
+                if (nz(Vx[(size_t)x * M + y]) && ina[y]) return false;
+    }
+    const int Mh = M / 2;
+    const std::vector<int> *blk[4] = {&h.a[0], &h.b[0], &h.a[1], &h.b[1]};
+    for (int k = 1; k < 4; ++k)
+        for (int i = 0; i < Mh; ++i)
+            for (int j = 0; j < Mh; ++j) {
+                const double2 u = H0[(size_t)(*blk[0])[i] * M + (*blk[0])[j]];
+                const double2 v = H0[(size_t)(*blk[k])[i] * M + (*blk[k])[j]];
+                if (u.x != v.x || u.y != v.y) return false;
+            }
+    return true;
+}
+
+// the half-row system of `s` (M > 128), or nullptr when s does not split or
+// its leads act outside the end half-rows
+knit_system make_half_rows(knit_system s, const std::vector<double2> &H0, const std::vector<double2> &V,
+                           const std::vector<double> &sign, const std::vector<double> &onsite,
+                           const std::vector<double2> *C)
+{
+    const int M = s->M, L = s->L, Mh = M / 2;
+    HalfRows hr;
+    if (M <= 128 || !half_rows(H0, V, M, s->Vperiod, s->block, hr)) return nullptr;
+    auto nz = [](double2 v) { return v.x != 0.0 || v.y != 0.0; };
+    // left Sigma on the rows of its coupling, right Sigma on the columns
+    const std::vector<int> &aL = hr.a[0], &bR = hr.b[(L - 1) & 1];
+    std::vector<char> inL(M, 0), inR(M, 0);
+    for (int x : aL) inL[x] = 1;
+    for (int x : bR) inR[x] = 1;
+    for (int x = 0; x < M; ++x)
+        for (int y = 0; y < M; ++y) {
+            if (nz(C[0][(size_t)x * M + y]) && !inL[x]) return nullptr;
+            if (nz(C[1][(size_t)x * M + y]) && !inR[y]) return nullptr;
+        }
+    const size_t mm = (size_t)Mh * Mh, MM = (size_t)M * M;
+    std::vector<double2> Hh(mm), Vh(4 * mm);
+    const int P = s->Vperiod;
+    for (int i = 0; i < Mh; ++i)
+        for (int j = 0; j < Mh; ++j) {
+            Hh[(size_t)i * Mh + j] = H0[(size_t)hr.a[0][i] * M + hr.a[0][j]];
+            // slice m = 2n + h: m % 4 = 0 (n even) a_n <- b_{n-1}, 1 b_n <- a_n,
+            // 2 (n odd) a_n <- b_{n-1}, 3 b_n <- a_n
+            Vh[0 * mm + (size_t)i * Mh + j] = V[(size_t)(0 % P) * MM + (size_t)hr.a[0][i] * M + hr.b[1][j]];
+            Vh[1 * mm + (size_t)i * Mh + j] = H0[(size_t)hr.b[0][i] * M + hr.a[0][j]];
+            Vh[2 * mm + (size_t)i * Mh + j] = V[(size_t)(1 % P) * MM + (size_t)hr.a[1][i] * M + hr.b[0][j]];
+            Vh[3 * mm + (size_t)i * Mh + j] = H0[(size_t)hr.b[1][i] * M + hr.a[1][j]];
+        }
+    std::vector<double> on;
+    if (!onsite.empty()) {
+        on.resize((size_t)2 * L * Mh);
+        for (int n = 0; n < L; ++n)
+            for (int i = 0; i < Mh; ++i) {
+                on[(size_t)(2 * n) * Mh + i] = onsite[(size_t)n * M + hr.a[n & 1][i]];
+                on[(size_t)(2 * n + 1) * Mh + i] = onsite[(size_t)n * M + hr.b[n & 1][i]];
+            }
+    }
+    knit_system_desc d{};
+    d.M = Mh;
+    d.L = 2 * L;
+    d.block = 1;
+    d.onsite_sign = sign.data();
+    d.H0 = (const knit_c128 *)Hh.data();
+    d.onsite = on.empty() ? nullptr : on.data();
+    d.V = (const knit_c128 *)Vh.data();
+    d.Vperiod = 4;
+    knit_system h = nullptr;
+    if (knit_system_create(&d, &h) != KNIT_OK) return nullptr;
+    std::vector<int> xm(4 * Mh), sup(2 * Mh);
+    for (int i = 0; i < Mh; ++i) {
+        xm[0 * Mh + i] = hr.a[0][i];
+        xm[1 * Mh + i] = hr.b[0][i];
+        xm[2 * Mh + i] = hr.a[1][i];
+        xm[3 * Mh + i] = hr.b[1][i];
+        sup[i] = aL[i];
+        sup[Mh + i] = bR[i];
+    }
+    if (to_device(&h->xmap, xm.data(), xm.size(), "half-row map") != KNIT_OK ||
+        to_device(&s->hsup, sup.data(), sup.size(), "half-row support") != KNIT_OK) {
+        knit_system_destroy(h);
+        return nullptr;
+    }
+    const SysDev sd = h->dev();
+    if (cudaMemcpy(h->d_sys, &sd, sizeof(SysDev), cudaMemcpyHostToDevice) != cudaSuccess) {
+        knit_system_destroy(h);
+        return nullptr;
+    }
+    return h;
 }
 
 knit_status ensure_modes(knit_system s, int p)
@@ -497,6 +806,28 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
         const double eta = (o && o->eta > 0) ? o->eta : 1e-12;
         const double tol = (o && o->tol > 0) ? o->tol : 1e-14;
         const int maxit = (o && o->maxit > 0) ? o->maxit : 200;
+        const Lead &ld = s->lead[p];
+        if (ld.nsec > 1) {
+            // block by block in the cell's eigenbasis (lead_modes_p2.cu), one
+            // thread per (block, energy), then Sigma from the surface blocks
+            const int ns = ld.nsec, N = 2 * ld.ms;
+            const size_t nn = (size_t)N * N;
+            CK(s->secg.ensure(sizeof(double2) * nn * nE * ns), "block g");
+            CK(s->secst.ensure(sizeof(int) * (size_t)nE * ns), "block status");
+            CK(s->secit.ensure(sizeof(int) * (size_t)nE * ns), "block iterations");
+            CK(s->p2t.ensure(sizeof(double2) * (size_t)ld.nnz * ns * ld.ms * grid), "block scratch");
+            CK(knit_launch_small_decimation(ld.sH0, ld.sV, ns, N, p, dE, nE, eta, tol, maxit,
+                                            s->secg.as<double2>(), s->secit.as<int>(),
+                                            s->secst.as<int>(), st),
+               "block decimation");
+            CK(knit_launch_p2_sector_sigma(ld.Cq, ld.nzr, ld.nnz, ns, ld.ms, s->secg.as<double2>(), M,
+                                           nE, s->p2t.as<double2>(), sig, grid, st),
+               "block self-energy");
+            CK(knit_launch_sector_status(s->secst.as<int>(), s->secit.as<int>(), ns, nE, lst, lit, st),
+               "block status");
+            (void)gout;
+            return KNIT_OK;
+        }
         CK(s->decw.ensure(sizeof(double2) * 8 * MMp * grid), "decimation workspace");
         CK(s->p2g.ensure(sizeof(double2) * MMp * nE), "supercell g");
         CK(s->p2s.ensure(sizeof(double2) * MMp * nE), "supercell sigma");
@@ -623,6 +954,50 @@ knit_status both_sigmas(knit_system s, const double *dE, int nE, const knit_lead
     return KNIT_OK;
 }
 
+// Sigma_L / Sigma_R (M x M per energy) restricted to the end half-rows
+// sup[0 .. Mh - 1] / sup[Mh .. 2 Mh - 1]; an energy whose self-energy has an
+// entry outside them (which the half-row chain cannot carry) gets status
+// KNIT_ERR_INVALID in lst (per energy, copied from lin or zero first).  One
+// CTA per energy (grid-stride).
+__global__ void __launch_bounds__(256)
+half_sigma_kernel(const double2 *SL, const double2 *SR, int M, const int *sup, int Mh, int nE,
+                  double2 *hL, double2 *hR, const int *lin, int *lst)
+{
+    __shared__ unsigned char inL[256], inR[256];
+    __shared__ int bad;
+    for (int x = threadIdx.x; x < M; x += blockDim.x) inL[x] = inR[x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < Mh; i += blockDim.x) {
+        inL[sup[i]] = 1;
+        inR[sup[Mh + i]] = 1;
+    }
+    __syncthreads();
+    const size_t MM = (size_t)M * M, mm = (size_t)Mh * Mh;
+    for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+        if (threadIdx.x == 0) bad = 0;
+        __syncthreads();
+        int b = 0;
+        for (size_t q = threadIdx.x; q < MM; q += blockDim.x) {
+            const int x = (int)(q / M), y = (int)(q % M);
+            const double2 l = SL[e * MM + q], r = SR[e * MM + q];
+            if ((l.x != 0.0 || l.y != 0.0) && !(inL[x] && inL[y])) b = 1;
+            if ((r.x != 0.0 || r.y != 0.0) && !(inR[x] && inR[y])) b = 1;
+        }
+        if (b) bad = 1;
+        for (size_t q = threadIdx.x; q < mm; q += blockDim.x) {
+            const int i = (int)(q / Mh), j = (int)(q % Mh);
+            hL[e * mm + q] = SL[e * MM + (size_t)sup[i] * M + sup[j]];
+            hR[e * mm + q] = SR[e * MM + (size_t)sup[Mh + i] * M + sup[Mh + j]];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int s0 = lin ? lin[e] : 0;
+            lst[e] = s0 != 0 ? s0 : (bad ? (int)KNIT_ERR_INVALID : 0);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void combine_status(int *a, const int *b, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -630,18 +1005,24 @@ __global__ void combine_status(int *a, const int *b, int n)
 }
 
 // which sweep kernel serves a system at a given precision
-enum SweepKind { SWEEP_FP64 = 0, SWEEP_MIXED = 1, SWEEP_WIDE = 2, SWEEP_TC128 = 3 };
+enum SweepKind { SWEEP_FP64 = 0, SWEEP_MIXED = 1, SWEEP_WIDE = 2, SWEEP_TC128 = 3, SWEEP_HALF = 4 };
 
 // KNIT_MIXED: widths <= 64 with diagonal couplings on sweep_mixed(_tc).cu,
-// everything else up to 128 (diagonal or 4 x 4 block couplings) on the
-// tensor-core kernel of sweep_mixed_tc128.cu; KNIT_MIXED_CUDACORE keeps the
-// CUDA-core residual kernels (sweep_mixed.cu, sweep_mixed_wide.cu)
-int sweep_kind(const knit_system_s *s, int precision)
+// everything else up to 128 (diagonal, 4 x 4 block or tridiagonal couplings)
+// on the tensor-core kernel of sweep_mixed_tc128.cu; KNIT_MIXED_CUDACORE
+// keeps the CUDA-core residual kernels (sweep_mixed.cu, sweep_mixed_wide.cu),
+// which take diagonal and 4 x 4 block couplings
+// SWEEP_HALF (only where half_ok: an energy x seed grid without G_LL):
+// KNIT_MIXED on a system wider than 128 that splits into half-rows runs the
+// tensor-core kernel on the half-row chain
+int sweep_kind(const knit_system_s *s, int precision, bool half_ok = false)
 {
     if (precision == KNIT_FP64) return SWEEP_FP64;
+    if (half_ok && precision == KNIT_MIXED && s->half) return SWEEP_HALF;
     if (s->vb == 1 && s->M <= knit_mixed_max_M()) return SWEEP_MIXED;
-    if ((s->vb == 1 || s->vb == 4) && s->M <= 128)
-        return precision == KNIT_MIXED ? SWEEP_TC128 : SWEEP_WIDE;
+    if (s->M > 128) return SWEEP_FP64;
+    if (precision == KNIT_MIXED && (s->vb == 1 || s->vb == 4 || s->vtri)) return SWEEP_TC128;
+    if (precision == KNIT_MIXED_CUDACORE && (s->vb == 1 || s->vb == 4)) return SWEEP_WIDE;
     return SWEEP_FP64;
 }
 
@@ -652,7 +1033,30 @@ knit_status run_sweep(knit_system s, InstDev in, int precision, cudaStream_t st)
     in.queue = s->queue.as<int>();
     CK(cudaMemsetAsync(in.queue, 0, sizeof(int), st), "queue reset");
     const int grid = std::max(1, std::min(in.n, s->nsm));
-    const int kind = sweep_kind(s, precision);
+    const int kind = sweep_kind(s, precision, !in.per_instance && !in.GLL);
+    if (kind == SWEEP_HALF) {
+        knit_system h = s->half;
+        const int nE = in.n / in.nS, Mh = h->M;
+        const size_t mm = (size_t)Mh * Mh;
+        CK(h->sigL.ensure(sizeof(double2) * mm * nE), "half-row sigma");
+        CK(h->sigR.ensure(sizeof(double2) * mm * nE), "half-row sigma");
+        CK(h->lst.ensure(sizeof(int) * nE), "half-row lead status");
+        CK(h->queue.ensure(sizeof(int)), "queue");
+        half_sigma_kernel<<<std::max(1, std::min(nE, 4 * s->nsm)), 256, 0, st>>>(
+            in.sigL, in.sigR, s->M, s->hsup, Mh, nE, h->sigL.as<double2>(), h->sigR.as<double2>(),
+            in.lstatus, h->lst.as<int>());
+        CK(cudaGetLastError(), "half-row sigma");
+        InstDev hi = in;
+        hi.sys = h->d_sys;
+        hi.sigL = h->sigL.as<double2>();
+        hi.sigR = h->sigR.as<double2>();
+        hi.lstatus = h->lst.as<int>();
+        hi.queue = h->queue.as<int>();
+        CK(cudaMemsetAsync(hi.queue, 0, sizeof(int), st), "queue reset");
+        CK(h->work.ensure(knit_mixed_tc128_work_bytes() * grid), "tensor-core sweep workspace");
+        CK(knit_launch_mixed_tc128(&hi, grid, h->work.p, st), "half-row sweep launch");
+        return KNIT_OK;
+    }
     if (kind == SWEEP_MIXED) {
         CK(knit_launch_mixed_impl(&in, s->M, grid, precision == KNIT_MIXED, st), "mixed sweep launch");
         return KNIT_OK;
@@ -778,7 +1182,7 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
     if (L < 1) return fail(KNIT_ERR_INVALID, "L = %d must be >= 1", L);
     if (B != 1 && B != 2 && B != 4) return fail(KNIT_ERR_INVALID, "block must be 1, 2 or 4");
     if (M % B) return fail(KNIT_ERR_INVALID, "M must be a multiple of block");
-    if (P != 1 && P != 2) return fail(KNIT_ERR_INVALID, "Vperiod must be 1 or 2");
+    if (P != 1 && P != 2 && P != 4) return fail(KNIT_ERR_INVALID, "Vperiod must be 1, 2 or 4");
     if (!d->H0 || !d->V) return fail(KNIT_ERR_INVALID, "H0 and V are required");
     const size_t MM = (size_t)M * M;
     std::vector<double2> H0, V, sign, onsite_dummy;
@@ -787,10 +1191,16 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
     if ((r = to_host(H0, d->H0, MM, "H0")) != KNIT_OK) return r;
     if ((r = to_host(V, d->V, MM * P, "V")) != KNIT_OK) return r;
     if (!hermitian(H0.data(), M)) return fail(KNIT_ERR_INVALID, "H0 is not Hermitian");
-    int vb = 1;
+    int vb = 1, vtri = 0;
     for (int q = 0; q < P; ++q) {
         int b = block_structure(V.data() + q * MM, M, B);
-        if (b == 0) return fail(KNIT_ERR_INVALID, "V[%d] is not block-diagonal with %dx%d blocks", q, B, B);
+        if (b == 0 && tridiagonal(V.data() + q * MM, M)) {
+            vtri = 1;
+            b = M;   // the FP64 paths treat it as a dense coupling
+        }
+        if (b == 0)
+            return fail(KNIT_ERR_INVALID, "V[%d] is neither block-diagonal with %dx%d blocks nor tridiagonal",
+                        q, B, B);
         vb = std::max(vb, b);
     }
     hs.assign(B, 1.0);
@@ -806,6 +1216,7 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
     s->block = B;
     s->Vperiod = P;
     s->vb = vb;
+    s->vtri = vtri;
     cudaGetDevice(&s->device);
     cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->device);
     // sparse rows of H0 for the mixed residual
@@ -821,7 +1232,7 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
         }
         rp[i + 1] = (int)cols.size();
     }
-    std::vector<double2> hC[2];
+    std::vector<double2> hC[2], cellH[2], cellA[2];   // period-2 leads: C = V_first, H0, V_second
     for (int p = 0; p < 2; ++p) {
         Lead &ld = s->lead[p];
         const int per = d->lead_Vperiod[p] <= 1 ? 1 : d->lead_Vperiod[p];
@@ -863,6 +1274,8 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
             vv.insert(vv.end(), V.begin() + (size_t)n1 * MM, V.begin() + (size_t)(n1 + 1) * MM);
         }
         const double2 *Vf = vv.data(), *Vs = vv.data() + MM;
+        cellH[p] = ld.hH0;
+        cellA[p].assign(Vs, Vs + MM);
         // supercell (surface slice first): left  H0c = [[H0, A], [A^+, H0]], coupling to the
         // next cell outward [[0, 0], [B, 0]]; right H0c = [[H0, A^+], [A, H0]], coupling
         // [[0, B], [0, 0]] (slice-forward orientation); A = V_second, B = V_first
@@ -948,7 +1361,12 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
             knit_system_destroy(s);
             return r;
         }
-        if (ld.Mp == M && !ld.scalar) {
+        if (ld.Mp != M) {
+            if ((r = p2_mode_sectors(ld, M, p, cellH[p], cellA[p].data(), hC[p].data())) != KNIT_OK) {
+                knit_system_destroy(s);
+                return r;
+            }
+        } else if (!ld.scalar) {
             std::vector<double2> bH0, bV;
             std::vector<int> idx;
             lead_sectors(ld, M, bH0, bV, idx);
@@ -968,6 +1386,13 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
             return r;
         }
     }
+    if (M > 128) {
+        const std::vector<double2> C[2] = {s->lead[0].Mp == M ? s->lead[0].hV : hC[0],
+                                           s->lead[1].Mp == M ? s->lead[1].hV : hC[1]};
+        const std::string keep = g_err;   // a system that does not split is no error
+        s->half = make_half_rows(s, H0, V, hs, hon, C);
+        g_err = keep;
+    }
     *out = s;
     return KNIT_OK;
 }
@@ -976,6 +1401,9 @@ knit_status knit_system_destroy(knit_system s)
 {
     if (!s) return KNIT_OK;
     cudaSetDevice(s->device);
+    knit_system_destroy(s->half);
+    cudaFree(s->hsup);
+    cudaFree(s->xmap);
     cudaFree(s->H0);
     cudaFree(s->V);
     cudaFree(s->sign);
@@ -996,6 +1424,8 @@ knit_status knit_system_destroy(knit_system s)
         cudaFree(s->lead[p].sH0);
         cudaFree(s->lead[p].sV);
         cudaFree(s->lead[p].sidx);
+        cudaFree(s->lead[p].Cq);
+        cudaFree(s->lead[p].nzr);
     }
     DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
                       &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
@@ -1041,6 +1471,12 @@ knit_status knit_lead_selfenergy(knit_system s, int32_t lead, const double *E, i
         const int grid = std::min(nE, s->nsm * 4);
         const Lead &ld = s->lead[lead];
         const bool cell2 = ld.Mp != s->M;   // residual of the supercell's g
+        if (cell2 && ld.nsec > 1) {
+            CK(s->p2g.ensure(sizeof(double2) * (size_t)ld.Mp * ld.Mp * nE), "supercell g");
+            CK(knit_launch_p2_sector_cell(ld.U, ld.sidx, ld.nsec, ld.ms, s->secg.as<double2>(), s->M, nE,
+                                          s->p2g.as<double2>(), s->nsm * 8, st),
+               "supercell g from blocks");
+        }
         CK(s->decw.ensure(sizeof(double2) * 3 * (size_t)ld.Mp * ld.Mp * grid), "residual workspace");
         CK(s->lres.ensure(sizeof(double) * nE), "residual");
         CK(knit_launch_lead_residual(ld.H0, ld.V, ld.Mp, ld.vb, lead, dE, nE,
@@ -1515,6 +1951,22 @@ knit_status knit_graph_transmission(knit_graph g, const double *E, int32_t nE,
     if (hT) CK(cudaMemcpyAsync(T, dT, sizeof(double) * nE, cudaMemcpyDeviceToHost, st), "T out");
     if (hSt) CK(cudaMemcpyAsync(status, dSt, sizeof(int) * nE, cudaMemcpyDeviceToHost, st), "status out");
     return finish(st, hT || hSt, "knit_graph_transmission");
+}
+
+knit_status knit_system_info(knit_system s, int32_t precision, int32_t *sweep, int32_t *lead_blocks)
+{
+    knit_status r = check_system(s);
+    if (r != KNIT_OK) return r;
+    if (!sweep || !lead_blocks) return fail(KNIT_ERR_INVALID, "sweep and lead_blocks are required");
+    if (precision != KNIT_FP64 && precision != KNIT_MIXED && precision != KNIT_MIXED_CUDACORE)
+        return fail(KNIT_ERR_INVALID, "unknown precision %d", precision);
+    static_assert(SWEEP_FP64 == KNIT_SWEEP_FP64 && SWEEP_MIXED == KNIT_SWEEP_MIXED_NARROW &&
+                      SWEEP_WIDE == KNIT_SWEEP_MIXED_CUDACORE && SWEEP_TC128 == KNIT_SWEEP_MIXED_TC128 &&
+                      SWEEP_HALF == KNIT_SWEEP_MIXED_HALF_ROWS,
+                  "sweep kinds");
+    *sweep = sweep_kind(s, precision, true);
+    for (int p = 0; p < 2; ++p) lead_blocks[p] = s->lead[p].nsec;
+    return KNIT_OK;
 }
 
 knit_status knit_system_num_edges(knit_system s, int32_t *count)

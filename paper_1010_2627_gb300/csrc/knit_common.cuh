@@ -183,7 +183,8 @@ enum {
 struct SysDev {
     int M, L, block, Vperiod;
     int vdiag;                 // 1: every V is diagonal (block-diagonal with 1 x 1 blocks)
-    int vb;                    // block size of the block-diagonal V
+    int vb;                    // block size of the block-diagonal V (M for a tridiagonal V)
+    int vband;                 // nonzeros of V within this distance of the diagonal (>= vb: any)
     const double2 *H0;         // M*M
     const double2 *V;          // Vperiod*M*M
     const double *sign;        // block
@@ -195,6 +196,10 @@ struct SysDev {
     // H0 as double-float (hi, lo) in the width-128 layout: column pair jp,
     // row i at float4 jp * 128 + i; zero outside M x M (M <= 128, else null)
     const float4 *h0_dfh, *h0_dfl;
+    // a honeycomb-type system run by half-rows: orbital i of slice m is the
+    // site xmap[((((m >> 1) & 1) << 1) | (m & 1)) * M + i] of row m >> 1, whose
+    // disorder it draws (block 1); nullptr for every other system
+    const int *xmap;
 };
 
 struct InstDev {

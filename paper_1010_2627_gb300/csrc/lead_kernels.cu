@@ -81,13 +81,6 @@ static __device__ int psd_check64(double2 *A, int M, double *red)
     return 1;
 }
 
-// decimation retries: eta, 100 eta, 1e4 eta, 1e6 eta; a surface g counts as
-// converged when it satisfies its fixed point at its own eta to this relative
-// max-norm and lies on the retarded branch (i(g - g^dagger) positive
-// semidefinite): at eta ~ 1e-12 the doubling can lose enough precision on wide
-// leads to land on another solution of the fixed-point equation
-constexpr int DEC_ATTEMPTS = 4;
-constexpr double DEC_SELF_TOL = 1e-5;
 
 // ---------------------------------------------------------------------------
 // A (M x M, Hermitian) -> diag in A, eigenvectors in U (global memory).

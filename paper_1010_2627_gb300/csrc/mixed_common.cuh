@@ -75,6 +75,8 @@ __device__ void slice_diag(double *eps, const SysDev &s, uint64_t ms, double W, 
         if (i < s.M) {
             double o = 0.0;
             if (s.onsite) o = s.onsite[(size_t)n * s.M + i];
+            else if (W != 0.0 && s.xmap)
+                o = s.sign[0] * knit_disorder(ms, n >> 1, s.xmap[((((n >> 1) & 1) << 1) | (n & 1)) * s.M + i], W);
             else if (W != 0.0) o = s.sign[i % s.block] * knit_disorder(ms, n, i / s.block, W);
             d = E - o;
         }

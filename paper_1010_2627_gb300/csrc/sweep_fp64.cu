@@ -98,7 +98,8 @@ __device__ void copy_mat(const double2 *src, double2 *dst, int M)
 
 // C = (A V^dagger) B; for a diagonal V the columns of A are scaled in place
 // first (A is the previous G_{0,n-1}, dead after this product)
-__device__ void g1_update(double2 *A, const double2 *V, int vb, const double2 *B, double2 *C, int M)
+__device__ void g1_update(double2 *A, const double2 *V, int vb, int band, const double2 *B, double2 *C,
+                          int M)
 {
     if (vb == 1) {
         for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
@@ -108,7 +109,7 @@ __device__ void g1_update(double2 *A, const double2 *V, int vb, const double2 *B
         __syncthreads();
         gemm64(A, B, C, M);
     } else {
-        gemm64_avd_b(A, V, vb, B, C, M);
+        gemm64_avd_b(A, V, vb, band, B, C, M);
     }
 }
 
@@ -141,7 +142,7 @@ __device__ int forward(const SysDev &s, const InstParams &ip, Bufs &b, double2 *
             copy_mat(F, Q, M);
         } else {
             const double2 *Vn = s.V + (size_t)(n % s.Vperiod) * MM;
-            g1_update(Q, Vn, s.vb, F, P, M);   // G_{0,n} = G_{0,n-1} V_n^dagger g_n
+            g1_update(Q, Vn, s.vb, s.vband, F, P, M);   // G_{0,n} = G_{0,n-1} V_n^dagger g_n
             double2 *t = Q;
             Q = P;
             P = t;

@@ -104,8 +104,9 @@ struct Tc128Smem {
         } va;
     } u;
     double eps[MP];
-    int vuni[2];
-    float vch[2], vcl[2];
+    int vkind[4];                  // per coupling V[q]: 0 diagonal, 1 4 x 4 blocks, 2 tridiagonal
+    int vuni[4];
+    float vch[4], vcl[4];
     int rexp[MP];                  // Gv' row exponents (one bit of headroom included)
     int cexp[MP];                  // X' column exponents, by true column
     unsigned rmaxu[MP];            // row maxima of |Gv'| (float bits)
@@ -342,6 +343,86 @@ __device__ void gv_blocks4(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, int M,
     }
 }
 
+// V g V^dagger for a tridiagonal V (coupling q) in two passes through the
+// workspace: U = g V^dagger into S1 / S2, then V U back into the state
+// buffers (g is no longer needed); V's three diagonals staged in shared
+// memory (row r: V[r][r - 1], V[r][r], V[r][r + 1] at r, 128 + r, 256 + r)
+__device__ void gv_tridiag(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, int M, int q)
+{
+    const size_t MM = (size_t)M * M;
+    const double2 *Vq = s.V + (size_t)(q % s.Vperiod) * MM;
+    for (int e = threadIdx.x; e < 3 * MP; e += NTH) {
+        const int k = e / MP - 1, r = e % MP, c = r + k;
+        const double2 v = (r < M && c >= 0 && c < M) ? Vq[(size_t)r * M + c] : make_double2(0.0, 0.0);
+        float2 h, l;
+        to_df(v.x, h.x, l.x);
+        to_df(v.y, h.y, l.y);
+        sm.u.va.vh[e] = h;
+        sm.u.va.vl[e] = l;
+    }
+    __syncthreads();
+    float4 *const uh = reinterpret_cast<float4 *>(wk.S1);
+    float4 *const ul = reinterpret_cast<float4 *>(wk.S2);
+    // U[a][j] = sum_{b = j-1 .. j+1} g[a][b] conj(V[j][b])
+    for (int e = threadIdx.x; e < (MP / 2) * MP; e += NTH) {
+        const int a = e % MP, jp = e / MP;
+        float2 gh[4], gl[4];   // g[a][2jp - 1 .. 2jp + 2]
+        {
+            const float4 h0 = jp > 0 ? wk.Gh[(jp - 1) * MP + a] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 l0 = jp > 0 ? wk.Gl[(jp - 1) * MP + a] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 h1 = wk.Gh[jp * MP + a], l1 = wk.Gl[jp * MP + a];
+            const float4 h2 = jp + 1 < MP / 2 ? wk.Gh[(jp + 1) * MP + a] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 l2 = jp + 1 < MP / 2 ? wk.Gl[(jp + 1) * MP + a] : make_float4(0.f, 0.f, 0.f, 0.f);
+            gh[0] = make_float2(h0.z, h0.w); gl[0] = make_float2(l0.z, l0.w);
+            gh[1] = make_float2(h1.x, h1.y); gl[1] = make_float2(l1.x, l1.y);
+            gh[2] = make_float2(h1.z, h1.w); gl[2] = make_float2(l1.z, l1.w);
+            gh[3] = make_float2(h2.x, h2.y); gl[3] = make_float2(l2.x, l2.y);
+        }
+        float2 oh[2], ol[2];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int j = 2 * jp + s2;
+            float2 sh = make_float2(0.f, 0.f), sl = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = -1; k <= 1; ++k) {
+                float2 vh = sm.u.va.vh[(k + 1) * MP + j], vl = sm.u.va.vl[(k + 1) * MP + j];
+                if (vh.x == 0.f && vh.y == 0.f) continue;
+                vh.y = -vh.y;
+                vl.y = -vl.y;
+                float2 ph, pl;
+                cdf_mul(gh[s2 + k + 1], gl[s2 + k + 1], vh, vl, ph, pl);
+                cdf_add(sh, sl, ph, pl);
+            }
+            oh[s2] = sh;
+            ol[s2] = sl;
+        }
+        uh[e] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
+        ul[e] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
+    }
+    __syncthreads();
+    // Gv[i][j] = sum_{a = i-1 .. i+1} V[i][a] U[a][j]
+    for (int e = threadIdx.x; e < (MP / 2) * MP; e += NTH) {
+        const int i = e % MP, jp = e / MP;
+        float2 oh[2] = {}, ol[2] = {};
+#pragma unroll
+        for (int k = -1; k <= 1; ++k) {
+            const int a = i + k;
+            const float2 vh = sm.u.va.vh[(k + 1) * MP + i], vl = sm.u.va.vl[(k + 1) * MP + i];
+            if (a < 0 || a >= MP || (vh.x == 0.f && vh.y == 0.f)) continue;
+            const float4 h = uh[jp * MP + a], l = ul[jp * MP + a];
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                float2 ph, pl;
+                cdf_mul(vh, vl, s2 ? make_float2(h.z, h.w) : make_float2(h.x, h.y),
+                        s2 ? make_float2(l.z, l.w) : make_float2(l.x, l.y), ph, pl);
+                cdf_add(oh[s2], ol[s2], ph, pl);
+            }
+        }
+        wk.Gh[e] = make_float4(oh[0].x, oh[0].y, oh[1].x, oh[1].y);
+        wk.Gl[e] = make_float4(ol[0].x, ol[0].y, ol[1].x, ol[1].y);
+    }
+}
+
 // Gv' = (V g V^dagger or Sigma_L) + Sigma_R + H0 - diag(E - onsite) in
 // double-float, elementwise into the state buffers; zero in the padding.
 // vmode: 0 general diagonal V, 1 V g V^dagger already formed (4 x 4 block
@@ -349,7 +430,7 @@ __device__ void gv_blocks4(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, int M,
 __device__ void gv_elementwise(Tc128Work &wk, Tc128Smem &sm, const SysDev &s, int M, int n, int L,
                                int vmode, bool from_s, const double2 *SL, const double2 *SR)
 {
-    const int q = n & 1;
+    const int q = n % s.Vperiod;
     const double2 *Vd = s.V + (size_t)(q % s.Vperiod) * M * M;   // diagonal at stride M + 1
     const float4 *srch = from_s ? reinterpret_cast<const float4 *>(wk.S1) : wk.Gh;
     const float4 *srcl = from_s ? reinterpret_cast<const float4 *>(wk.S2) : wk.Gl;
@@ -1250,12 +1331,22 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
         const int M = s.M, L = s.L, vb = s.vb;
         const size_t MM = (size_t)M * M;
         if (reload) {
-            if (tid < 2) {
-                if (vb == 1)
-                    classify_vdiag(s.V + (size_t)(tid % s.Vperiod) * MM, M + 1, M, sm.vuni[tid],
-                                   sm.vch[tid], sm.vcl[tid]);
-                else
-                    sm.vuni[tid] = 1;   // V g V^dagger formed by the block pass
+            // the kind of each coupling: diagonal (scalar when uniform), 4 x 4
+            // blocks, or tridiagonal (the host admits nothing else); every
+            // thread that sees an off-diagonal entry writes the same kind
+            if (tid < 4) sm.vkind[tid] = 0;
+            __syncthreads();
+            if (vb != 1)
+                for (int q = 0; q < s.Vperiod; ++q)
+                    for (int e = tid; e < M * M; e += NTH) {
+                        const double2 v = s.V[(size_t)q * MM + e];
+                        if (e / M != e % M && (v.x != 0.0 || v.y != 0.0)) sm.vkind[q] = vb == 4 ? 1 : 2;
+                    }
+            __syncthreads();
+            if (tid < s.Vperiod) {
+                sm.vuni[tid] = 1;
+                if (sm.vkind[tid] == 0)
+                    classify_vdiag(s.V + (size_t)tid * MM, M + 1, M, sm.vuni[tid], sm.vch[tid], sm.vcl[tid]);
             }
             if (tid == 0) sm.cur_sys = si;
             __syncthreads();
@@ -1267,11 +1358,12 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             // ---- A
             slice_diag<MP, NTH>(sm.eps, s, ip.ms, ip.W, ip.E, n);
             for (int i = tid; i < MP; i += NTH) sm.rmaxu[i] = 0u;
-            if (vb == 4 && n > 0) gv_blocks4(wk, sm, s, M, n & 1);
-            __syncthreads();   // eps (and the block pass's output) complete
-            const int q = n & 1;
-            const int vmode = vb == 4 ? 1 : (sm.vuni[q] == 1 ? 1 : (sm.vuni[q] == 2 ? 2 : 0));
-            gv_elementwise(wk, sm, s, M, n, L, vmode, vb == 4 && n > 0, ip.SL, ip.SR);
+            const int q = n % s.Vperiod, vk = sm.vkind[q];
+            if (vk == 1 && n > 0) gv_blocks4(wk, sm, s, M, q);
+            if (vk == 2 && n > 0) gv_tridiag(wk, sm, s, M, q);
+            __syncthreads();   // eps (and the block passes' output) complete
+            const int vmode = vk != 0 ? 1 : (sm.vuni[q] == 1 ? 1 : (sm.vuni[q] == 2 ? 2 : 0));
+            gv_elementwise(wk, sm, s, M, n, L, vmode, vk == 1 && n > 0, ip.SL, ip.SR);
             __syncthreads();
             fence_after();
             x_to_tmem(wk, sm, tmem, M);

@@ -95,6 +95,63 @@ def armchair(M: int, L: int, t: float = 2.7) -> SliceSystem:
     return SliceSystem(M, L, H0, V, lead_V=(left, right), name=f"armchair M={M} L={L} t={t}")
 
 
+def armchair_half_sites(M: int, n: int):
+    """Sites x of brick-wall row n split as (a_n, b_n): a_n couples to row
+    n - 1 ((x + n) even), b_n to row n + 1 (the others), each in increasing
+    x (M even)."""
+    x = np.arange(M)
+    a = x[(x + n) % 2 == 0]
+    b = x[(x + n) % 2 == 1]
+    return a, b
+
+
+def armchair_halfslices(M: int, L: int, t: float = 2.7) -> SliceSystem:
+    """The armchair ribbon of ``armchair(M, L, t)`` sliced by half-rows: row n
+    splits into a_n (the sites coupled to row n - 1) and b_n (the rest), and
+    the chain a_0, b_0, a_1, b_1, ... is block tridiagonal with blocks of
+    M / 2 orbitals and no hopping inside a block.  Couplings (H_{m, m-1} =
+    V[m % 4]): t I between b_{n-1} and a_n (the same x), and the in-row chain
+    bonds between a_n and b_n, bidiagonal with a shape set by the parity of
+    n.  The same physical system, so the same transmission; disorder must be
+    given per half-row (``armchair_halfslice_onsite``), and the lead
+    self-energies are the row picture's restricted to a_0 (left) and
+    b_{L-1} (right) (``armchair_halfslice_sigma``)."""
+    assert M % 2 == 0
+    h = M // 2
+    V = np.zeros((4, h, h), np.complex128)
+    V[0] = t * np.eye(h)
+    V[2] = t * np.eye(h)
+    for n, q in ((0, 1), (1, 3)):
+        a, b = armchair_half_sites(M, n)
+        for i, xa in enumerate(a):
+            for j, xb in enumerate(b):
+                if abs(int(xa) - int(xb)) == 1:
+                    V[q][j, i] = t          # H_{b_n, a_n}
+    return SliceSystem(h, 2 * L, np.zeros((h, h), np.complex128), V,
+                       name=f"armchair half-rows M={M} L={L} t={t}")
+
+
+def armchair_halfslice_onsite(eps: np.ndarray) -> np.ndarray:
+    """(2L, M / 2) on-site energies of the half-row slicing from the row
+    picture's (L, M)."""
+    L, M = eps.shape
+    out = np.empty((2 * L, M // 2))
+    for n in range(L):
+        a, b = armchair_half_sites(M, n)
+        out[2 * n] = eps[n, a]
+        out[2 * n + 1] = eps[n, b]
+    return out
+
+
+def armchair_halfslice_sigma(SL: np.ndarray, SR: np.ndarray, M: int, L: int):
+    """The row picture's self-energies (..., M, M) restricted to the half-rows
+    they act on: a_0 (left lead) and b_{L-1} (right lead)."""
+    a0, _ = armchair_half_sites(M, 0)
+    _, bl = armchair_half_sites(M, L - 1)
+    return (np.ascontiguousarray(SL[..., a0[:, None], a0[None, :]]),
+            np.ascontiguousarray(SR[..., bl[:, None], bl[None, :]]))
+
+
 _s0 = np.eye(2, dtype=np.complex128)
 _sx = np.array([[0, 1], [1, 0]], np.complex128)
 _sy = np.array([[0, -1j], [1j, 0]], np.complex128)

@@ -26,6 +26,8 @@ KNIT_LEAD_AUTO, KNIT_LEAD_MODES, KNIT_LEAD_DECIMATION, KNIT_LEAD_LEARNED = 0, 1,
 KNIT_PEAK_MMA_BF16, KNIT_PEAK_MMA_TF32, KNIT_PEAK_DFMA, KNIT_PEAK_FFMA = 0, 1, 2, 3
 KNIT_PEAK_MMA_N64, KNIT_PEAK_MMA_N16, KNIT_PEAK_MMA_RESIDUAL = 4, 5, 6
 KNIT_PEAK_MMA_RESIDUAL_TF32 = 7
+KNIT_SWEEP_FP64, KNIT_SWEEP_MIXED_NARROW, KNIT_SWEEP_MIXED_CUDACORE = 0, 1, 2
+KNIT_SWEEP_MIXED_TC128, KNIT_SWEEP_MIXED_HALF_ROWS = 3, 4
 
 P = ctypes.c_void_p
 i32, f64 = ctypes.c_int32, ctypes.c_double
@@ -68,6 +70,7 @@ _SIGS = {
     "knit_transmission_eigenvalues": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P, P]),
     "knit_lesser": (i32, [P, P, i32, P, i32, f64, i32, P, P, P, P, P, P, P, P]),
     "knit_system_num_edges": (i32, [P, P]),
+    "knit_system_info": (i32, [P, i32, P, P]),
     "knit_graph_create": (i32, [P, P]),
     "knit_graph_destroy": (i32, [P]),
     "knit_graph_slices": (i32, [P, P, P, P]),
@@ -342,6 +345,10 @@ class Graph:
             self.handle = knit_graph_create_multi(H, leads)
             self.P = len(leads)
 
+    def info(self, precision=KNIT_MIXED):
+        """(sweep kernel KNIT_SWEEP_*, [lead blocks left, right])"""
+        return knit_system_info(self.handle, precision)
+
     def close(self):
         if self.handle:
             knit_graph_destroy(self.handle)
@@ -371,6 +378,14 @@ class Graph:
         sig = [_c128(s) for s in sigmas]
         knit_graph_conductance(self.handle, E, sig, Tm, st)
         return Tm, st
+
+
+def knit_system_info(handle, precision):
+    """(sweep kernel KNIT_SWEEP_*, [lead blocks left, right]) of a system."""
+    sw = ctypes.c_int32()
+    lb = (ctypes.c_int32 * 2)()
+    _check(load().knit_system_info(P(handle), int(precision), ctypes.byref(sw), lb))
+    return sw.value, [lb[0], lb[1]]
 
 
 def knit_system_num_edges(handle) -> int:

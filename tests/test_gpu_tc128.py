@@ -155,3 +155,29 @@ def test_batch_with_wide_instances(knit):
         assert abs(T[p] - To) / max(1, nch_square(ss.M, E[p])) <= TOL_MIXED, (p, ss.M, T[p], To)
     for h in handles:
         h.close()
+
+
+@pytest.mark.parametrize("Mrow,Lrow", [(40, 3), (100, 4), (256, 2)])
+def test_armchair_halfslices_tridiagonal(knit, Mrow, Lrow):
+    """the honeycomb ribbon sliced by half-rows by the caller (width Mrow / 2,
+    no hopping inside a half-row, tridiagonal couplings of period 4) against
+    the oracle's row picture with the same disorder and lead self-energies
+    (the GPU's, restricted to the end half-rows), mixed and FP64"""
+    rows = inputs.armchair(Mrow, Lrow)
+    half = inputs.armchair_halfslices(Mrow, Lrow)
+    E = np.array([-1.3, 0.21, 0.9])
+    eps = oracle.onsite(5, Lrow, Mrow, 0.5)
+    rsys = knit.System(rows)
+    SL = rsys.lead_selfenergy(0, E)[0]
+    SR = rsys.lead_selfenergy(1, E)[0]
+    rsys.close()
+    To = np.array([oracle.rgf(rows.H0, rows.V, eps, Lrow, e, SL[k], SR[k])["T"]
+                   for k, e in enumerate(E)])
+    hSL, hSR = inputs.armchair_halfslice_sigma(SL, SR, Mrow, Lrow)
+    sysk = knit.System(half, onsite=inputs.armchair_halfslice_onsite(eps))
+    assert sysk.info(knit.KNIT_MIXED)[0] == knit.KNIT_SWEEP_MIXED_TC128
+    for precision, tol in ((knit.KNIT_MIXED, TOL_MIXED), (knit.KNIT_FP64, TOL_FP64)):
+        T, st = sysk.transmission_sigma(E, hSL, hSR, precision=precision)
+        assert (st == 0).all()
+        assert np.abs(T[:, 0] - To).max() <= tol * Mrow, (precision, T[:, 0], To)
+    sysk.close()

@@ -4,6 +4,7 @@ of each lattice (square: t I; graphene brick wall: alternating bond masks;
 BdG: 4 x 4 spin x Nambu blocks with particle-hole structure), the uneven
 batch's distributions, and the L-shaped example's geometry.  CPU only."""
 import numpy as np
+import pytest
 
 from paper_1010_2627_gb300 import inputs
 
@@ -84,3 +85,25 @@ def test_lshape_example_geometry():
     assert len(i0) == 4 and len(i1) == 3 and not set(i0) & set(i1)
     deg = (np.abs(H) > 0).sum(axis=1)
     assert deg.max() == 4 and deg.min() == 2
+
+
+def test_armchair_halfslices_same_transmission_as_rows():
+    """The half-row slicing of an armchair ribbon is the same system: the
+    oracle's slice sweep gives the row picture's T, with the same disorder
+    and the row picture's lead self-energies restricted to a_0 and b_{L-1}."""
+    import oracle
+    from paper_1010_2627_gb300 import inputs
+    for M, L in ((6, 3), (12, 5), (10, 4)):
+        ss = inputs.armchair(M, L)
+        hs = inputs.armchair_halfslices(M, L)
+        eps = oracle.onsite(7, L, M, 0.8)
+        for E in (-1.7, 0.3, 2.1):
+            SL = oracle.decimation_period2(ss.H0, *ss.lead_V[0], E, 0)
+            SR = oracle.decimation_period2(ss.H0, *ss.lead_V[1], E, 1)
+            Tr = oracle.dense(ss.H0, ss.V, eps, L, E, SL, SR)["T_LR"]
+            hl, hr = inputs.armchair_halfslice_sigma(SL, SR, M, L)
+            # the row picture's Sigma lives on those half-rows only
+            a0, _ = inputs.armchair_half_sites(M, 0)
+            assert np.abs(SL).sum() == pytest.approx(np.abs(hl).sum(), rel=1e-14)
+            Th = oracle.rgf(hs.H0, hs.V, inputs.armchair_halfslice_onsite(eps), 2 * L, E, hl, hr)["T"]
+            assert abs(Th - Tr) < 1e-10, (M, L, E, Th, Tr)
