@@ -448,6 +448,12 @@ def run_uneven(args):
     dT = torch.empty(n, dtype=torch.float64, device="cuda")
     dst = torch.empty(n, dtype=torch.int32, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    # CTAs per SM per kernel variant: own CUDA-event timings, cached as JSON
+    cache = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1010_2627_gb300",
+                         "_build", "autotune_uneven.json")
+    t0 = time.perf_counter()
+    tuned = batch.autotune(inst["E"], inst["seeds"], inst["W"], cache=cache)
+    tune_s = time.perf_counter() - t0
 
     def step():
         knit.knit_batch_transmission(batch.handle, dE, ds, dW, dT, dst, stream=stream)
@@ -471,6 +477,27 @@ def run_uneven(args):
     clk = _clock_summary(clocks, torch.cuda.current_device())
     T = dT.cpu().numpy()
     st = dst.cpu().numpy()
+    # the same step captured once in a CUDA graph and replayed (the plan only
+    # enqueues kernels once its buffers exist)
+    graph = {}
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            step()
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                gev[k][0].record(stream)
+                g.replay()
+                gev[k][1].record(stream)
+        torch.cuda.synchronize()
+        gms = statistics.mean(a.elapsed_time(b) for a, b in gev)
+        graph = {"ms_per_step": gms, "value": n / (gms / 1e3),
+                 "same_T": bool(np.array_equal(dT.cpu().numpy(), T))}
+    except Exception as exc:   # capture refused: report, keep the stream numbers
+        graph = {"error": str(exc)[:200]}
     slices = int(inst["L"].sum())
     flop = float((16.0 * inst["M"].astype(np.float64) ** 3 * inst["L"]).sum())
     achieved = flop / (ms / 1e3) / 1e12
@@ -494,6 +521,9 @@ def run_uneven(args):
                      "note": "sum of 16 M^3 L over the batch / step time (leads included) over "
                              "the measured dense TF32 tensor peak (own loop)"},
         "clocks": clk, "peaks_measured": pk,
+        "kernel_variants": [{"kind": k, "Mmax": m, "instances": c, "max_ctas_per_sm": x,
+                             "ctas_per_sm": tuned[q]} for q, (k, m, c, x) in enumerate(batch.buckets())],
+        "autotune_s": tune_s, "cuda_graph": graph,
         "status_nonzero": int((st != 0).sum())}
     # stratified subset: the 13 (12 for the last width) shortest instances of each width
     import oracle

@@ -389,7 +389,10 @@ knit_status knit_lead_model_gradient(knit_lead_model model, const double *E, con
  * calls while the plan runs).  The plan groups instances per system for the
  * lead solvers and per sweep kernel for the sweep, and orders each kernel's
  * queue by decreasing cost M^3 L (longest processing time first), so each
- * kernel variant is one persistent launch.  KNIT_MIXED instances whose
+ * kernel variant is one persistent launch.  The variants' launches run at
+ * once on streams of the plan (forked from and joined back into the caller's
+ * stream), issued heaviest first, so that the SMs one variant's tail leaves
+ * idle take the next variant's CTAs.  KNIT_MIXED instances whose
  * system the mixed kernels do not cover run in the FP64 sweep.  Lead
  * eigen-decompositions are done here, so that a run with device pointers
  * only enqueues kernels and can be captured in a CUDA graph. */
@@ -411,6 +414,31 @@ knit_status knit_batch_destroy(knit_batch batch);
 knit_status knit_batch_transmission(knit_batch batch, const double *E, const uint64_t *seeds,
                                     const double *W, const knit_lead_opts *opts, double *T,
                                     int32_t *status, void *stream);
+
+/* The plan's kernel variants ("buckets", in launch order): *nb of them; per
+ * variant q (arrays of *nb, each optional) its kind (0 FP64 sweep, 1 mixed
+ * M <= 64, 2 mixed CUDA-core M <= 128, 3 tensor-core M <= 128), widest M,
+ * instance count and the most CTAs per SM its kernel can hold.
+ * KNIT_ERR_INVALID for a NULL batch or nb. */
+knit_status knit_batch_buckets(knit_batch batch, int32_t *nb, int32_t *kind, int32_t *Mmax,
+                               int32_t *count, int32_t *max_ctas);
+
+/* Set the CTAs per SM of every variant's persistent launch (config: *nb
+ * values, clamped to 1 .. max_ctas), e.g. from a cache of
+ * knit_batch_autotune results.  KNIT_ERR_INVALID for NULL arguments. */
+knit_status knit_batch_configure(knit_batch batch, const int32_t *config);
+
+/* Tune the launch shapes on the plan's own instances (inputs as in
+ * knit_batch_transmission, host or device): the lead self-energies once,
+ * then for every variant whose CTAs can share an SM each CTA count per SM
+ * from 1 to max_ctas timed with CUDA events (that variant's sweep launch
+ * alone) and the fastest kept in the plan.  config, ms (optional, *nb
+ * values): the chosen CTAs per SM and its time (-1 where nothing was
+ * tried).  Synchronous; on its own stream.  KNIT_ERR_INVALID for a NULL
+ * batch or E; KNIT_ERR_CUDA / KNIT_ERR_OOM for device failures. */
+knit_status knit_batch_autotune(knit_batch batch, const double *E, const uint64_t *seeds,
+                                const double *W, const knit_lead_opts *opts, int32_t *config,
+                                float *ms);
 
 /* Lead self-energy by Sancho-Rubio decimation without any allocation (the
  * paper has no counterpart; it exists for callers that cannot let a library

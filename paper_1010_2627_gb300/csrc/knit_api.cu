@@ -30,6 +30,7 @@ extern "C" cudaError_t knit_launch_lesser_fp64(const InstDev *, int, int, int, d
                                                int, const int2 *, int, double *, double *, double *,
                                                double *, cudaStream_t);
 extern "C" cudaError_t knit_launch_mixed_impl(const InstDev *, int, int, int, cudaStream_t);
+extern "C" int knit_mixed_ctas_per_sm(int, int);
 extern "C" int knit_mixed_max_M(void);
 extern "C" size_t knit_ldos_mixed_work_bytes(int, int, int);
 extern "C" cudaError_t knit_launch_ldos_mixed(const InstDev *, int, int, int, int, void *, double *,
@@ -1127,12 +1128,18 @@ __global__ void fill_int(int *a, int n, int v)
 
 struct knit_batch_s {
     struct Bucket {
-        int kind = 0;          // 0 FP64 sweep, 1 mixed M <= 64, 2 mixed wide (M <= 128)
+        int kind = 0;          // 0 FP64 sweep, 1 mixed M <= 64, 2 mixed wide, 3 tensor-core M <= 128
         int use_tc = 0;
         int Mmax = 0, Lmax = 0;
+        int ctas = 1, max_ctas = 1;   // CTAs per SM of its persistent launch
+        double cost0 = 0.0;           // M^3 L of its heaviest instance
+        size_t work_off = 0;          // its part of the workspace (bytes)
         std::vector<int> order;   // plan positions in cost order
         DevBuf d_order;
+        cudaStream_t stream = nullptr;
+        cudaEvent_t done = nullptr;
     };
+    cudaEvent_t ready = nullptr;
     int nInst = 0, precision = 0, device = 0, nsm = 1;
     std::vector<knit_system> sys;            // distinct systems (not owned)
     std::vector<int> perm;                   // plan position -> caller's instance
@@ -1152,7 +1159,15 @@ knit_status batch_release(knit_batch b)
                       &b->W, &b->Ep, &b->Sp, &b->Wp, &b->sigL, &b->sigR, &b->gbuf, &b->lst,
                       &b->T, &b->status, &b->queue, &b->work};
     for (DevBuf *x : bufs) x->release();
-    for (auto &bk : b->buckets) bk.d_order.release();
+    for (auto &bk : b->buckets) {
+        bk.d_order.release();
+        if (bk.stream) cudaStreamDestroy(bk.stream);
+        if (bk.done) cudaEventDestroy(bk.done);
+        bk.stream = nullptr;
+        bk.done = nullptr;
+    }
+    if (b->ready) cudaEventDestroy(b->ready);
+    b->ready = nullptr;
     return KNIT_OK;
 }
 
@@ -1960,9 +1975,10 @@ knit_status knit_system_info(knit_system s, int32_t precision, int32_t *sweep, i
     if (!sweep || !lead_blocks) return fail(KNIT_ERR_INVALID, "sweep and lead_blocks are required");
     if (precision != KNIT_FP64 && precision != KNIT_MIXED && precision != KNIT_MIXED_CUDACORE)
         return fail(KNIT_ERR_INVALID, "unknown precision %d", precision);
-    static_assert(SWEEP_FP64 == KNIT_SWEEP_FP64 && SWEEP_MIXED == KNIT_SWEEP_MIXED_NARROW &&
-                      SWEEP_WIDE == KNIT_SWEEP_MIXED_CUDACORE && SWEEP_TC128 == KNIT_SWEEP_MIXED_TC128 &&
-                      SWEEP_HALF == KNIT_SWEEP_MIXED_HALF_ROWS,
+    static_assert((int)SWEEP_FP64 == (int)KNIT_SWEEP_FP64 && (int)SWEEP_MIXED == (int)KNIT_SWEEP_MIXED_NARROW &&
+                      (int)SWEEP_WIDE == (int)KNIT_SWEEP_MIXED_CUDACORE &&
+                      (int)SWEEP_TC128 == (int)KNIT_SWEEP_MIXED_TC128 &&
+                      (int)SWEEP_HALF == (int)KNIT_SWEEP_MIXED_HALF_ROWS,
                   "sweep kinds");
     *sweep = sweep_kind(s, precision, true);
     for (int p = 0; p < 2; ++p) lead_blocks[p] = s->lead[p].nsec;
@@ -2170,13 +2186,19 @@ knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const in
         bk.Mmax = std::max(bk.Mmax, s->M);
         bk.Lmax = std::max(bk.Lmax, s->L);
     }
-    for (auto &bk : b->buckets)
-        std::stable_sort(bk.order.begin(), bk.order.end(), [&](int a, int c) {
-            knit_system sa = b->sys[sys_of[a]], sc = b->sys[sys_of[c]];
-            double ca = (double)sa->M * sa->M * sa->M * sa->L;
-            double cc = (double)sc->M * sc->M * sc->M * sc->L;
-            return ca > cc;
-        });
+    auto cost = [&](int p) {
+        knit_system sp = b->sys[sys_of[p]];
+        return (double)sp->M * sp->M * sp->M * sp->L;
+    };
+    for (auto &bk : b->buckets) {
+        std::stable_sort(bk.order.begin(), bk.order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+        bk.cost0 = cost(bk.order[0]);
+        if (bk.kind == 1 && !bk.use_tc) bk.max_ctas = knit_mixed_ctas_per_sm(bk.Mmax, 0);
+    }
+    // all variants run at once on their own streams, launched heaviest first:
+    // the SMs a variant's tail leaves idle take the next variant's CTAs
+    std::stable_sort(b->buckets.begin(), b->buckets.end(),
+                     [](const knit_batch_s::Bucket &x, const knit_batch_s::Bucket &y) { return x.cost0 > y.cost0; });
     // device tables
     std::vector<SysDev> tab(nSys);
     for (int k = 0; k < nSys; ++k) tab[k] = b->sys[k]->dev();
@@ -2202,18 +2224,28 @@ knit_status knit_batch_create(const knit_system *systems, int32_t nSys, const in
         return cuda_fail(e, "knit_batch_create");
     }
     size_t work = 0;
+    if ((e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming)) != cudaSuccess) {
+        batch_release(b);
+        delete b;
+        return cuda_fail(e, "knit_batch_create");
+    }
     for (auto &bk : b->buckets) {
         if ((e = bk.d_order.ensure(sizeof(int) * bk.order.size())) != cudaSuccess ||
             (e = cudaMemcpy(bk.d_order.p, bk.order.data(), sizeof(int) * bk.order.size(),
-                            cudaMemcpyHostToDevice)) != cudaSuccess) {
+                            cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&bk.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&bk.done, cudaEventDisableTiming)) != cudaSuccess) {
             batch_release(b);
             delete b;
             return cuda_fail(e, "knit_batch_create");
         }
+        // each variant its own workspace, since they run concurrently
+        work = (work + 255) & ~(size_t)255;
+        bk.work_off = work;
         if (bk.kind == 0 && knit_fp64_smem_bytes(bk.Mmax, 1, 3) > 220 * 1024)
-            work = std::max(work, sizeof(double2) * 3 * (size_t)bk.Mmax * bk.Mmax * b->nsm);
-        if (bk.kind == 2) work = std::max(work, knit_mixed_wide_work_bytes(bk.Mmax) * b->nsm);
-        if (bk.kind == 3) work = std::max(work, knit_mixed_tc128_work_bytes() * b->nsm);
+            work += sizeof(double2) * 3 * (size_t)bk.Mmax * bk.Mmax * b->nsm;
+        if (bk.kind == 2) work += knit_mixed_wide_work_bytes(bk.Mmax) * b->nsm;
+        if (bk.kind == 3) work += knit_mixed_tc128_work_bytes() * b->nsm;
     }
     if (work && (e = b->work.ensure(work)) != cudaSuccess) {
         batch_release(b);
@@ -2241,13 +2273,15 @@ knit_status knit_batch_destroy(knit_batch b)
     return KNIT_OK;
 }
 
-knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_t *seeds,
-                                    const double *W, const knit_lead_opts *opts, double *T,
-                                    int32_t *status, void *stream)
+}  // extern "C"
+
+namespace {
+
+// instance parameters gathered into plan order, both leads' self-energies per
+// system, lead status combined (all on st)
+knit_status batch_prepare(knit_batch b, const double *E, const uint64_t *seeds, const double *W,
+                          const knit_lead_opts *opts, cudaStream_t st)
 {
-    if (!b || !E || !T) return fail(KNIT_ERR_INVALID, "knit_batch_transmission: bad arguments");
-    CK(cudaSetDevice(b->device), "cudaSetDevice");
-    cudaStream_t st = (cudaStream_t)stream;
     const int n = b->nInst;
     knit_status r;
     const double *dE, *dW;
@@ -2260,7 +2294,6 @@ knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_
     uint64_t *Sp = b->Sp.as<uint64_t>();
     gather_instances<<<(n + 255) / 256, 256, 0, st>>>(dE, dS, dW, b->d_perm.as<int>(), n, Ep, Sp, Wp);
     CK(cudaGetLastError(), "gather");
-    // lead self-energies per system, for its instances' energies
     int *lst = b->lst.as<int>();
     for (size_t k = 0; k < b->sys.size(); ++k) {
         if (!b->count[k]) continue;
@@ -2274,6 +2307,63 @@ knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_
             return r;
     }
     combine_status<<<(n + 255) / 256, 256, 0, st>>>(lst, lst + n, n);
+    CK(cudaGetLastError(), "status combine");
+    return KNIT_OK;
+}
+
+// the persistent sweep launch of variant q on stream st (its queue counter
+// already zeroed), with `ctas` CTAs per SM
+knit_status batch_launch(knit_batch b, size_t q, int ctas, double *dT, int *dSt, cudaStream_t st)
+{
+    auto &bk = b->buckets[q];
+    InstDev in{};
+    in.n = (int)bk.order.size();
+    in.nS = 1;
+    in.per_instance = 1;
+    in.sys = b->d_systab.as<SysDev>();
+    in.sys_of = b->d_sys_of.as<int>();
+    in.order = bk.d_order.as<int>();
+    in.E = b->Ep.as<double>();
+    in.seeds = b->Sp.as<uint64_t>();
+    in.Wi = b->Wp.as<double>();
+    in.sigL = b->sigL.as<double2>();
+    in.sigR = b->sigR.as<double2>();
+    in.sig_off = b->d_sig_off.as<long long>();
+    in.T = dT;
+    in.status = dSt;
+    in.out_index = b->d_perm.as<int>();
+    in.lstatus = b->lst.as<int>();
+    in.queue = b->queue.as<int>() + q;
+    const int grid = std::max(1, std::min(in.n, b->nsm * std::max(1, ctas)));
+    void *work = static_cast<char *>(b->work.p) + bk.work_off;
+    if (bk.kind == 1) {
+        CK(knit_launch_mixed_impl(&in, bk.Mmax, grid, bk.use_tc, st), "mixed sweep launch");
+    } else if (bk.kind == 2) {
+        CK(knit_launch_mixed_wide(&in, bk.Mmax, grid, work, st), "wide mixed sweep launch");
+    } else if (bk.kind == 3) {
+        CK(knit_launch_mixed_tc128(&in, grid, work, st), "tensor-core wide sweep launch");
+    } else {
+        const int use_smem = knit_fp64_smem_bytes(bk.Mmax, 1, 3) <= 220 * 1024;
+        CK(knit_launch_sweep_fp64(&in, bk.Mmax, grid, static_cast<double2 *>(work), use_smem, st),
+           "fp64 sweep launch");
+    }
+    return KNIT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_t *seeds,
+                                    const double *W, const knit_lead_opts *opts, double *T,
+                                    int32_t *status, void *stream)
+{
+    if (!b || !E || !T) return fail(KNIT_ERR_INVALID, "knit_batch_transmission: bad arguments");
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = b->nInst;
+    knit_status r;
+    if ((r = batch_prepare(b, E, seeds, W, opts, st)) != KNIT_OK) return r;
     bool hT, hSt = false;
     double *dT;
     int *dSt;
@@ -2282,42 +2372,98 @@ knit_status knit_batch_transmission(knit_batch b, const double *E, const uint64_
         return r;
     if (dSt) fill_int<<<(n + 255) / 256, 256, 0, st>>>(dSt, n, ST_TIMEOUT);
     CK(cudaMemsetAsync(b->queue.p, 0, sizeof(int) * b->buckets.size(), st), "queue reset");
+    // fork: every variant on its own stream after the work above, heaviest
+    // first; join back into st
+    CK(cudaEventRecord(b->ready, st), "fork");
     for (size_t q = 0; q < b->buckets.size(); ++q) {
         auto &bk = b->buckets[q];
-        InstDev in{};
-        in.n = (int)bk.order.size();
-        in.nS = 1;
-        in.per_instance = 1;
-        in.sys = b->d_systab.as<SysDev>();
-        in.sys_of = b->d_sys_of.as<int>();
-        in.order = bk.d_order.as<int>();
-        in.E = Ep;
-        in.seeds = Sp;
-        in.Wi = Wp;
-        in.sigL = b->sigL.as<double2>();
-        in.sigR = b->sigR.as<double2>();
-        in.sig_off = b->d_sig_off.as<long long>();
-        in.T = dT;
-        in.status = dSt;
-        in.out_index = b->d_perm.as<int>();
-        in.lstatus = lst;
-        in.queue = b->queue.as<int>() + q;
-        const int grid = std::max(1, std::min(in.n, b->nsm));
-        if (bk.kind == 1) {
-            CK(knit_launch_mixed_impl(&in, bk.Mmax, grid, bk.use_tc, st), "mixed sweep launch");
-        } else if (bk.kind == 2) {
-            CK(knit_launch_mixed_wide(&in, bk.Mmax, grid, b->work.p, st), "wide mixed sweep launch");
-        } else if (bk.kind == 3) {
-            CK(knit_launch_mixed_tc128(&in, grid, b->work.p, st), "tensor-core wide sweep launch");
-        } else {
-            const int use_smem = knit_fp64_smem_bytes(bk.Mmax, 1, 3) <= 220 * 1024;
-            CK(knit_launch_sweep_fp64(&in, bk.Mmax, grid, b->work.as<double2>(), use_smem, st),
-               "fp64 sweep launch");
-        }
+        CK(cudaStreamWaitEvent(bk.stream, b->ready, 0), "fork");
+        if ((r = batch_launch(b, q, bk.ctas, dT, dSt, bk.stream)) != KNIT_OK) return r;
+        CK(cudaEventRecord(bk.done, bk.stream), "join");
+        CK(cudaStreamWaitEvent(st, bk.done, 0), "join");
     }
     if (hT) CK(cudaMemcpyAsync(T, dT, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "T out");
     if (hSt) CK(cudaMemcpyAsync(status, dSt, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "status out");
     return finish(st, hT || hSt, "knit_batch_transmission");
+}
+
+knit_status knit_batch_buckets(knit_batch b, int32_t *nb, int32_t *kind, int32_t *Mmax, int32_t *count,
+                               int32_t *max_ctas)
+{
+    if (!b || !nb) return fail(KNIT_ERR_INVALID, "knit_batch_buckets: bad arguments");
+    *nb = (int32_t)b->buckets.size();
+    for (size_t q = 0; q < b->buckets.size(); ++q) {
+        const auto &bk = b->buckets[q];
+        if (kind) kind[q] = bk.kind;
+        if (Mmax) Mmax[q] = bk.Mmax;
+        if (count) count[q] = (int32_t)bk.order.size();
+        if (max_ctas) max_ctas[q] = bk.max_ctas;
+    }
+    return KNIT_OK;
+}
+
+knit_status knit_batch_configure(knit_batch b, const int32_t *config)
+{
+    if (!b || !config) return fail(KNIT_ERR_INVALID, "knit_batch_configure: bad arguments");
+    for (size_t q = 0; q < b->buckets.size(); ++q) {
+        auto &bk = b->buckets[q];
+        bk.ctas = std::max(1, std::min((int)config[q], bk.max_ctas));
+    }
+    return KNIT_OK;
+}
+
+knit_status knit_batch_autotune(knit_batch b, const double *E, const uint64_t *seeds, const double *W,
+                                const knit_lead_opts *opts, int32_t *config, float *ms)
+{
+    if (!b || !E) return fail(KNIT_ERR_INVALID, "knit_batch_autotune: bad arguments");
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    cudaStream_t st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "autotune stream");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    };
+    knit_status r = KNIT_OK;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cleanup();
+        return cuda_fail(ce, "autotune events");
+    }
+    const int n = b->nInst;
+    if ((r = batch_prepare(b, E, seeds, W, opts, st)) != KNIT_OK ||
+        (ce = b->T.ensure(sizeof(double) * n)) != cudaSuccess ||
+        (ce = b->status.ensure(sizeof(int) * n)) != cudaSuccess) {
+        cleanup();
+        return r != KNIT_OK ? r : cuda_fail(ce, "autotune buffers");
+    }
+    for (size_t q = 0; q < b->buckets.size() && r == KNIT_OK; ++q) {
+        auto &bk = b->buckets[q];
+        float best = -1.0f;
+        int best_k = bk.ctas;
+        for (int k = 1; k <= bk.max_ctas && bk.max_ctas > 1; ++k) {
+            float t = 0.0f;
+            if ((ce = cudaMemsetAsync(b->queue.as<int>() + q, 0, sizeof(int), st)) != cudaSuccess ||
+                (ce = cudaEventRecord(e0, st)) != cudaSuccess) break;
+            if ((r = batch_launch(b, q, k, b->T.as<double>(), b->status.as<int>(), st)) != KNIT_OK) break;
+            if ((ce = cudaEventRecord(e1, st)) != cudaSuccess || (ce = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (ce = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess)
+                break;
+            if (best < 0.0f || t < best) {
+                best = t;
+                best_k = k;
+            }
+        }
+        if (r == KNIT_OK && ce != cudaSuccess) r = cuda_fail(ce, "autotune launch");
+        bk.ctas = best_k;
+        if (config) config[q] = best_k;
+        if (ms) ms[q] = best;
+    }
+    cleanup();
+    return r;
 }
 
 

@@ -577,3 +577,24 @@ extern "C" cudaError_t knit_launch_mixed_impl(const InstDev *in, int Mmax, int g
 }
 
 extern "C" int knit_mixed_max_M(void) { return 64; }
+
+// CTAs of the CUDA-core mixed sweep for widths up to Mmax that fit on one SM
+// at once (1 for the tensor-core variant, which takes all tensor memory)
+extern "C" int knit_mixed_ctas_per_sm(int Mmax, int use_tc)
+{
+    int n = 1;
+    if (Mmax <= 16) {
+        const size_t sm = sizeof(MixedSmem<16>);
+        cudaFuncSetAttribute(knit_sweep_mixed_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, knit_sweep_mixed_kernel<16>, NT, sm);
+    } else if (Mmax <= 32) {
+        const size_t sm = sizeof(MixedSmem<32>);
+        cudaFuncSetAttribute(knit_sweep_mixed_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, knit_sweep_mixed_kernel<32>, NT, sm);
+    } else if (Mmax <= 64 && !use_tc) {
+        const size_t sm = sizeof(MixedSmem<64>);
+        cudaFuncSetAttribute(knit_sweep_mixed_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, knit_sweep_mixed_kernel<64>, NT, sm);
+    }
+    return n < 1 ? 1 : n;
+}

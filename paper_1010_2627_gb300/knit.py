@@ -91,6 +91,9 @@ _SIGS = {
     "knit_lead_model_gradient": (i32, [P, P, P, i32, P, P, P]),
     "knit_batch_destroy": (i32, [P]),
     "knit_batch_transmission": (i32, [P, P, P, P, P, P, P, P]),
+    "knit_batch_buckets": (i32, [P, P, P, P, P, P]),
+    "knit_batch_configure": (i32, [P, P]),
+    "knit_batch_autotune": (i32, [P, P, P, P, P, P, P]),
     "knit_peak_probe": (i32, [i32, ctypes.c_int64, i32, P, P, P]),
     "knit_debug_wait_probe": (i32, [ctypes.c_int64, P, P]),
     "knit_last_error": (ctypes.c_char_p, []),
@@ -345,10 +348,6 @@ class Graph:
             self.handle = knit_graph_create_multi(H, leads)
             self.P = len(leads)
 
-    def info(self, precision=KNIT_MIXED):
-        """(sweep kernel KNIT_SWEEP_*, [lead blocks left, right])"""
-        return knit_system_info(self.handle, precision)
-
     def close(self):
         if self.handle:
             knit_graph_destroy(self.handle)
@@ -456,6 +455,31 @@ def knit_batch_transmission(plan, E, seeds, W, T, status=None, opts=None, stream
                                           _ptr(status), _stream(stream)))
 
 
+def knit_batch_buckets(plan):
+    """[(kind, Mmax, count, max_ctas)] per kernel variant, in launch order."""
+    nb = ctypes.c_int32()
+    _check(load().knit_batch_buckets(P(plan), ctypes.byref(nb), None, None, None, None))
+    a = [np.zeros(nb.value, np.int32) for _ in range(4)]
+    _check(load().knit_batch_buckets(P(plan), ctypes.byref(nb), *[_ptr(x) for x in a]))
+    return [tuple(int(x[q]) for x in a) for q in range(nb.value)]
+
+
+def knit_batch_configure(plan, config):
+    c = np.ascontiguousarray(config, dtype=np.int32)
+    _check(load().knit_batch_configure(P(plan), _ptr(c)))
+
+
+def knit_batch_autotune(plan, E, seeds, W, opts=None):
+    """(CTAs per SM, ms) chosen per kernel variant."""
+    nb = len(knit_batch_buckets(plan))
+    cfg = np.zeros(nb, np.int32)
+    ms = np.zeros(nb, np.float32)
+    _check(load().knit_batch_autotune(P(plan), _ptr(E), _ptr(seeds), _ptr(W),
+                                      None if opts is None else ctypes.byref(opts), _ptr(cfg),
+                                      _ptr(ms)))
+    return cfg, ms
+
+
 class LeadModel:
     """A learned warm start for one lead of a System (see include/knit.h)."""
 
@@ -521,6 +545,35 @@ class Batch:
         self.n = len(sys_index)
         self.handle = knit_batch_create([s.handle for s in self.systems], sys_index, precision)
 
+    def buckets(self):
+        return knit_batch_buckets(self.handle)
+
+    def autotune(self, E, seeds=None, W=None, cache=None):
+        """Tune CTAs per SM per kernel variant (knit_batch_autotune), or take
+        them from the JSON file `cache`, whose entries are keyed by the
+        variants' (kind, Mmax, count, max_ctas) and the instance count;
+        returns the configuration."""
+        import json
+        key = repr((self.n, self.buckets()))
+        table = {}
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                cfg = table[key]["ctas_per_sm"]
+                knit_batch_configure(self.handle, cfg)
+                return cfg
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.uint64)
+        Wv = None if W is None else np.ascontiguousarray(np.broadcast_to(W, (self.n,)),
+                                                          dtype=np.float64)
+        cfg, ms = knit_batch_autotune(self.handle, E, sd, Wv)
+        if cache is not None:
+            table[key] = {"ctas_per_sm": [int(c) for c in cfg], "ms": [float(m) for m in ms]}
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1)
+        return [int(c) for c in cfg]
+
     def close(self):
         if self.handle:
             knit_batch_destroy(self.handle)
@@ -554,6 +607,10 @@ class System:
         self.handle = knit_system_create(ss.M, ss.L, ss.H0, ss.V, block=ss.block,
                                          onsite_sign=ss.sign, onsite=onsite,
                                          lead_H0=ss.lead_H0, lead_V=ss.lead_V)
+
+    def info(self, precision=KNIT_MIXED):
+        """(sweep kernel KNIT_SWEEP_*, [lead blocks left, right])"""
+        return knit_system_info(self.handle, precision)
 
     def close(self):
         if self.handle:
