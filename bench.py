@@ -320,27 +320,28 @@ def run_knit(args):
     dEs = torch.tensor(E[sub], device="cuda")
     dTs = torch.empty(nsub_e * NS, dtype=torch.float64, device="cuda")
     dsts = torch.empty(nsub_e * NS, dtype=torch.int32, device="cuda")
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        knit.knit_transmission(sysk.handle, dEs, ds, W, knit.KNIT_FP64, dTs, dsts, nE=nsub_e,
-                               nS=NS, stream=stream)   # warm-up (lead modes cached)
-        a.record(stream)
-        knit.knit_transmission(sysk.handle, dEs, ds, W, knit.KNIT_FP64, dTs, dsts, nE=nsub_e,
-                               nS=NS, stream=stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = a.elapsed_time(b)
+    REPS = 5   # each side timed as the median of 5 launches after a warm-up
+
+    def median_ms(precision, out):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(REPS)]
+        with torch.cuda.stream(stream):
+            knit.knit_transmission(sysk.handle, dEs, ds, W, precision, out, dsts, nE=nsub_e,
+                                   nS=NS, stream=stream)   # warm-up (lead modes cached)
+            for a, b in evs:
+                a.record(stream)
+                knit.knit_transmission(sysk.handle, dEs, ds, W, precision, out, dsts, nE=nsub_e,
+                                       nS=NS, stream=stream)
+                b.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    fp64_ms = median_ms(knit.KNIT_FP64, dTs)
     fp64_rate = nsub_e * NS / (fp64_ms / 1e3)
     fp64_tflops = 16.0 * M ** 3 * L * nsub_e * NS / (fp64_ms / 1e3) / 1e12
     # the same subset through the CUDA-core residual path of the mixed sweep
     dTc = torch.empty(nsub_e * NS, dtype=torch.float64, device="cuda")
-    with torch.cuda.stream(stream):
-        a.record(stream)
-        knit.knit_transmission(sysk.handle, dEs, ds, W, knit.KNIT_MIXED_CUDACORE, dTc, dsts,
-                               nE=nsub_e, nS=NS, stream=stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    cc_rate = nsub_e * NS / (a.elapsed_time(b) / 1e3)
+    cc_rate = nsub_e * NS / (median_ms(knit.KNIT_MIXED_CUDACORE, dTc) / 1e3)
     T64 = dTs.cpu().numpy().reshape(nsub_e, NS)
     ek = 2 * np.cos(np.arange(1, M + 1) * np.pi / (M + 1))
     nch = np.array([max(1, int(np.sum(np.abs(e - ek) < 2))) for e in E[sub]])
@@ -370,7 +371,8 @@ def run_knit(args):
                    "flush": "L2 flushed before every timed step (252 MB write)"},
         "slice_updates_per_s": value * L,
         "fp64_sweep": {"value": fp64_rate, "unit": "T(E) points/s",
-                       "sample": f"{nsub_e} energies x {NS} seeds, one wave", "ms": fp64_ms,
+                       "sample": f"{nsub_e} energies x {NS} seeds, one wave, median of {REPS} "
+                                 f"launches", "ms": fp64_ms,
                        "mixed_speedup": value / ws / fp64_rate,
                        "roofline": {"bound": "fp64", "achieved": fp64_tflops,
                                     "peak": pk["dfma_tflops"], "unit": "TFLOP/s",
