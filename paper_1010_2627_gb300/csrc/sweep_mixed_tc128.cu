@@ -102,6 +102,13 @@ struct Tc128Smem {
         struct {                                       // slice set-up: V's 4 x 4 block rows
             float2 vh[MP * 4], vl[MP * 4];             // row r: V[r][4 (r / 4) + b], b = 0 .. 3
         } va;
+        struct {                                       // double-float inversion of a slice
+            float4 col[MP];                            // column k before the step
+            float4 row[MP];                            // row k after scaling
+            float4 inv;                                // 1 / pivot
+            float key[4];                              // per warp: best pivot key and its row
+            int idx[4];
+        } fb;
     } u;
     double eps[MP];
     int vkind[4];                  // per coupling V[q]: 0 diagonal, 1 4 x 4 blocks, 2 tridiagonal
@@ -1213,6 +1220,135 @@ __device__ int fallback64(Tc128Work &wk, int M)
     return ST_OK;
 }
 
+// near-singular A_n: this slice inverted by Gauss-Jordan with partial
+// pivoting in double-float on the CUDA cores (entries as (hi, lo) float
+// pairs, ~2^-47 relative per operation, about six times the speed of the
+// FP64 pipe's Gauss-Jordan at this width), from Gv' in the state; rows are
+// swapped in place and the swaps undone on the columns at the end
+__device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
+{
+    float4 *const a = reinterpret_cast<float4 *>(wk.A64);   // row-major MP x MP: hi.re, hi.im, lo.re, lo.im
+    const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
+    const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < MP * MP; e += NTH) {
+        const int i = e >> 7, j = e & (MP - 1);
+        if (i >= M || j >= M) continue;
+        const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+        a[e] = make_float4(-gh[f].x, -gh[f].y, -gl[f].x, -gl[f].y);
+    }
+    __syncthreads();
+    for (int k = 0; k < M; ++k) {
+        // pivot: the largest |Re| + |Im| of column k in rows k .. M - 1
+        if (warp < 4) {
+            const int i = 32 * warp + lane;
+            float v = -1.f;
+            if (i >= k && i < M) {
+                const float4 x = a[i * MP + k];
+                v = fabsf(x.x) + fabsf(x.y);
+            }
+            int bi = i;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > v || (ov == v && oi < bi)) {
+                    v = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                sm.u.fb.key[warp] = v;
+                sm.u.fb.idx[warp] = bi;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float v = sm.u.fb.key[0];
+            int r = sm.u.fb.idx[0];
+            for (int w = 1; w < 4; ++w)
+                if (sm.u.fb.key[w] > v) {
+                    v = sm.u.fb.key[w];
+                    r = sm.u.fb.idx[w];
+                }
+            sm.perm[k] = r;
+            sm.flag = (v > 0.f && isfinite(v)) ? r : -1;
+        }
+        __syncthreads();
+        const int r = sm.flag;
+        if (r < 0) return ST_SINGULAR;
+        if (r != k)
+            for (int j = tid; j < M; j += NTH) {
+                const float4 t = a[k * MP + j];
+                a[k * MP + j] = a[r * MP + j];
+                a[r * MP + j] = t;
+            }
+        __syncthreads();
+        for (int i = tid; i < M; i += NTH) sm.u.fb.col[i] = a[i * MP + k];
+        __syncthreads();
+        if (tid == 0) {
+            const float4 pv = sm.u.fb.col[k];
+            const double pr = (double)pv.x + (double)pv.z, pi = (double)pv.y + (double)pv.w;
+            const double d = 1.0 / (pr * pr + pi * pi);
+            float4 inv;
+            to_df(pr * d, inv.x, inv.z);
+            to_df(-pi * d, inv.y, inv.w);
+            sm.u.fb.inv = inv;
+        }
+        __syncthreads();
+        const float4 inv = sm.u.fb.inv;
+        for (int j = tid; j < M; j += NTH) {
+            const float4 x = j == k ? make_float4(1.f, 0.f, 0.f, 0.f) : a[k * MP + j];
+            float2 h, l;
+            cdf_mul(make_float2(x.x, x.y), make_float2(x.z, x.w), make_float2(inv.x, inv.y),
+                    make_float2(inv.z, inv.w), h, l);
+            const float4 y = make_float4(h.x, h.y, l.x, l.y);
+            a[k * MP + j] = y;
+            sm.u.fb.row[j] = y;
+        }
+        __syncthreads();
+        for (int e = tid; e < MP * MP; e += NTH) {
+            const int i = e >> 7, j = e & (MP - 1);
+            if (i >= M || j >= M || i == k) continue;
+            const float4 c = sm.u.fb.col[i], rw = sm.u.fb.row[j];
+            const float4 x = j == k ? make_float4(0.f, 0.f, 0.f, 0.f) : a[e];
+            float2 ph, pl, h = make_float2(x.x, x.y), l = make_float2(x.z, x.w);
+            cdf_mul(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(rw.x, rw.y),
+                    make_float2(rw.z, rw.w), ph, pl);
+            cdf_add(h, l, make_float2(-ph.x, -ph.y), make_float2(-pl.x, -pl.y));
+            a[e] = make_float4(h.x, h.y, l.x, l.y);
+        }
+        __syncthreads();
+    }
+    // the row swaps, undone on the columns in reverse order
+    for (int k = M - 1; k >= 0; --k) {
+        const int r = sm.perm[k];
+        if (r != k)
+            for (int i = tid; i < M; i += NTH) {
+                const float4 t = a[i * MP + k];
+                a[i * MP + k] = a[i * MP + r];
+                a[i * MP + r] = t;
+            }
+        __syncthreads();
+    }
+    float2 *const oh = reinterpret_cast<float2 *>(wk.Gh);
+    float2 *const ol = reinterpret_cast<float2 *>(wk.Gl);
+    for (int e = tid; e < MP * MP; e += NTH) {
+        const int i = e & (MP - 1), j = e >> 7;
+        const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+        if (i < M && j < M) {
+            const float4 v = a[i * MP + j];
+            oh[f] = make_float2(v.x, v.y);
+            ol[f] = make_float2(v.z, v.w);
+        } else {
+            oh[f] = make_float2(i == j ? 1.f : 0.f, 0.f);
+            ol[f] = make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    return ST_OK;
+}
+
 // T from G_LL = Gh + Gl by the unitarity identity (as ward_T of
 // mixed_common.cuh), in double-float on the CUDA cores (GB300's FP64 rate
 // is 1/72 of its FP32 rate; an FP64 trace would cost as much as ~20 slices):
@@ -1441,7 +1577,9 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             // ---- E
             const float rmax = block_max_nonneg<NTH>(rloc, sm.redu);
             if (refinement_fails(rmax, M)) {
-                st = fallback64(wk, M);
+                // double-float Gauss-Jordan; FP64 if it meets an exact zero pivot
+                st = fallback_df(wk, sm, M);
+                if (st != ST_OK) st = fallback64(wk, M);
                 __syncthreads();
                 continue;
             }
