@@ -347,7 +347,13 @@ knit_status knit_ldos(knit_system sys, const double *E, int32_t nE, const uint64
  * Green function g, row-major) is trained on the GPU with the library's own
  * forward, backward and Adam kernels (FP32) on g from the library's own
  * decimation at the training energies.  Parameters are stored as, for layers
- * l = 0..3, W_l (out x in, row-major) then b_l.  Cells of at most 8 orbitals. */
+ * l = 0..3, W_l (out x in, row-major) then b_l.  Cells of at most 8 orbitals,
+ * or a period-2 lead that splits into blocks of at most 4 in the eigenbasis
+ * of its cell Hamiltonian (knit_system_info > 1 blocks; the armchair ribbon's
+ * lead): the output is then every block's two-slice surface function in the
+ * mode basis, block c's N x N (N <= 4) values at 2 N^2 c, and Newton runs per
+ * (block, energy) in one thread.  knit_lead_model_num_outputs gives the
+ * output width. */
 typedef struct knit_lead_model_s *knit_lead_model;
 
 /* Train for `epochs` passes over the training energies in shuffled
@@ -366,6 +372,10 @@ knit_status knit_lead_model_destroy(knit_lead_model model);
 /* Number of parameters (0 for NULL). */
 int64_t knit_lead_model_num_params(knit_lead_model model);
 
+/* Floats of network output per energy: 2 M^2, or 2 N^2 per block for a lead
+ * solved in blocks (0 for NULL). */
+int64_t knit_lead_model_num_outputs(knit_lead_model model);
+
 /* Copy the parameters out to a host or device float array of
  * knit_lead_model_num_params values (layout above); KNIT_ERR_INVALID for NULL. */
 knit_status knit_lead_model_get_params(knit_lead_model model, float *params);
@@ -373,11 +383,13 @@ knit_status knit_lead_model_get_params(knit_lead_model model, float *params);
 /* Copy the parameters in from a host or device float array (same layout). */
 knit_status knit_lead_model_set_params(knit_lead_model model, const float *params);
 
-/* Network output for nE energies: nE x 2 M^2 floats (re, im of g, row-major). */
+/* Network output for nE energies: nE x knit_lead_model_num_outputs floats
+ * (re, im of g, row-major; per block for a lead solved in blocks). */
 knit_status knit_lead_model_forward(knit_lead_model model, const double *E, int32_t nE, float *out,
                                     void *stream);
 
-/* Mean squared error of the network against `target` (n x 2 M^2 floats) and
+/* Mean squared error of the network against `target` (n x
+ * knit_lead_model_num_outputs floats) and
  * its gradient with respect to every parameter (knit_lead_model_num_params
  * floats), as used by training. */
 knit_status knit_lead_model_gradient(knit_lead_model model, const double *E, const float *target,

@@ -46,7 +46,12 @@ extern "C" cudaError_t knit_launch_sector_status(const int *, const int *, int, 
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
 extern "C" cudaError_t knit_launch_small_decimation(const double2 *, const double2 *, int, int, int,
                                                     const double *, int, double, double, int,
-                                                    double2 *, int *, int *, cudaStream_t);
+                                                    double2 *, int *, int *, int, cudaStream_t);
+extern "C" cudaError_t knit_launch_small_newton(const double2 *, const double2 *, int, int, int,
+                                                const double *, int, const float *, long, double, int,
+                                                double2 *, int *, int *, cudaStream_t);
+extern "C" cudaError_t knit_mlp_targets_blocks(const double2 *, const int *, int, int, int, int, float *,
+                                               cudaStream_t);
 extern "C" cudaError_t knit_launch_p2_sector_sigma(const double2 *, const int *, int, int, int,
                                                    const double2 *, int, int, double2 *, double2 *,
                                                    int, cudaStream_t);
@@ -313,15 +318,16 @@ struct knit_lead_model_s {
     static constexpr int NL = 4, HID = 128;
     knit_system sys = nullptr;
     int lead = 0, M = 0, device = 0;
+    int nsec = 0, nb = 0;   // a lead solved in blocks: nsec blocks of nb x nb (else 0)
     int dims[NL + 1] = {1, HID, HID, HID, 0};
     size_t woff[NL] = {}, boff[NL] = {}, nparam = 0;
     double mid = 0.0, half = 1.0;
     DevBuf params, grads, m, v, act, dact, U, Tt, loss, idx, tmpE;
     int step = 0;
     int maxB = 0;
-    knit_lead_model_s(int M_) : M(M_)
+    knit_lead_model_s(int M_, int nout) : M(M_)
     {
-        dims[NL] = 2 * M * M;
+        dims[NL] = nout;
         size_t o = 0;
         for (int l = 0; l < NL; ++l) {
             woff[l] = o;
@@ -800,8 +806,12 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
     if (s->lead[p].Mp != M) {
         // period-2 lead: decimation of the two-slice supercell, then the end
         // slice's Sigma from the surface block
-        if (method != KNIT_LEAD_DECIMATION)
-            return fail(KNIT_ERR_INVALID, "lead %d has period 2: only DECIMATION applies", p);
+        const bool blocks_learned = method == KNIT_LEAD_LEARNED && s->lead[p].nsec > 1 &&
+                                    2 * s->lead[p].ms <= 4;
+        if (method != KNIT_LEAD_DECIMATION && !blocks_learned)
+            return fail(KNIT_ERR_INVALID,
+                        "lead %d has period 2: only DECIMATION applies (LEARNED where it splits into blocks "
+                        "of at most 4)", p);
         const int Mp = s->lead[p].Mp;
         const size_t MMp = (size_t)Mp * Mp;
         const double eta = (o && o->eta > 0) ? o->eta : 1e-12;
@@ -817,10 +827,33 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
             CK(s->secst.ensure(sizeof(int) * (size_t)nE * ns), "block status");
             CK(s->secit.ensure(sizeof(int) * (size_t)nE * ns), "block iterations");
             CK(s->p2t.ensure(sizeof(double2) * (size_t)ld.nnz * ns * ld.ms * grid), "block scratch");
-            CK(knit_launch_small_decimation(ld.sH0, ld.sV, ns, N, p, dE, nE, eta, tol, maxit,
-                                            s->secg.as<double2>(), s->secit.as<int>(),
-                                            s->secst.as<int>(), st),
-               "block decimation");
+            if (method == KNIT_LEAD_LEARNED) {
+                // the network's guess for every block, Newton per (block, energy),
+                // decimation where Newton did not settle
+                knit_lead_model md = o ? (knit_lead_model)o->model[p] : nullptr;
+                if (!md || md->sys != s || md->lead != p || md->nsec != ns || md->nb != N)
+                    return fail(KNIT_ERR_INVALID, "KNIT_LEAD_LEARNED needs a model trained for this lead");
+                knit_status r = model_reserve(md, nE);
+                if (r != KNIT_OK) return r;
+                CK(knit_mlp_inputs(dE, nullptr, nE, md->mid, md->half, md->act.as<float>(), st),
+                   "model inputs");
+                if ((r = model_forward(md, nE, st)) != KNIT_OK) return r;
+                CK(knit_launch_small_newton(ld.sH0, ld.sV, ns, N, p, dE, nE,
+                                            md->act.as<float>() + md->act_off(knit_lead_model_s::NL),
+                                            md->dims[knit_lead_model_s::NL], 1e-12, 8,
+                                            s->secg.as<double2>(), s->secit.as<int>(), s->secst.as<int>(),
+                                            st),
+                   "block newton");
+                CK(knit_launch_small_decimation(ld.sH0, ld.sV, ns, N, p, dE, nE, eta, tol, maxit,
+                                                s->secg.as<double2>(), s->secit.as<int>(),
+                                                s->secst.as<int>(), 1, st),
+                   "block decimation fallback");
+            } else {
+                CK(knit_launch_small_decimation(ld.sH0, ld.sV, ns, N, p, dE, nE, eta, tol, maxit,
+                                                s->secg.as<double2>(), s->secit.as<int>(),
+                                                s->secst.as<int>(), 0, st),
+                   "block decimation");
+            }
             CK(knit_launch_p2_sector_sigma(ld.Cq, ld.nzr, ld.nnz, ns, ld.ms, s->secg.as<double2>(), M,
                                            nE, s->p2t.as<double2>(), sig, grid, st),
                "block self-energy");
@@ -2480,15 +2513,25 @@ knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_t
     if (!out || !E_train || nTrain < 2 || epochs < 1 || batch < 1 || !(lr > 0.f))
         return fail(KNIT_ERR_INVALID, "knit_lead_model_train: bad arguments");
     if (lead != 0 && lead != 1) return fail(KNIT_ERR_INVALID, "lead must be 0 or 1");
-    if (s->M > 8) return fail(KNIT_ERR_INVALID, "learned leads support cells of at most 8 orbitals");
-    if (s->lead[lead].Mp != s->M)
-        return fail(KNIT_ERR_INVALID, "learned leads support period-1 leads only");
+    const Lead &ld = s->lead[lead];
+    // a period-2 lead split into blocks of at most 4: the network predicts
+    // every block's supercell surface function; otherwise the whole cell's g
+    const bool blocks = ld.Mp != s->M && ld.nsec > 1 && 2 * ld.ms <= 4;
+    if (!blocks && s->M > 8)
+        return fail(KNIT_ERR_INVALID, "learned leads support cells of at most 8 orbitals, or period-2 "
+                                      "leads that split into blocks of at most 4");
+    if (!blocks && ld.Mp != s->M)
+        return fail(KNIT_ERR_INVALID, "this period-2 lead does not split into blocks of at most 4");
+    const int nb = blocks ? 2 * ld.ms : 0, nsec = blocks ? ld.nsec : 0;
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<double> hE;
     if ((r = to_host(hE, E_train, (size_t)nTrain, "E_train")) != KNIT_OK) return r;
-    knit_lead_model md = new (std::nothrow) knit_lead_model_s(s->M);
+    knit_lead_model md = new (std::nothrow)
+        knit_lead_model_s(s->M, blocks ? 2 * nsec * nb * nb : 2 * s->M * s->M);
     if (!md) return fail(KNIT_ERR_OOM, "host allocation");
+    md->nsec = nsec;
+    md->nb = nb;
     md->sys = s;
     md->lead = lead;
     md->device = s->device;
@@ -2532,10 +2575,12 @@ knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_t
         (e = cudaMemset(md->v.p, 0, sizeof(float) * md->nparam)) != cudaSuccess ||
         (e = cudaMemcpy(md->tmpE.p, hE.data(), sizeof(double) * nTrain, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(cuda_fail(e, "model allocation"));
-    // targets: the library's own decimation at every training energy
+    // targets: the library's own decimation at every training energy (for a
+    // lead in blocks, the blocks' surface functions stay in the system's
+    // block buffer, energy-major per block)
     const size_t MM = (size_t)s->M * s->M;
     DevBuf gtr, sgtr, sttr;
-    if ((e = gtr.ensure(sizeof(double2) * MM * nTrain)) != cudaSuccess ||
+    if ((e = gtr.ensure(sizeof(double2) * (blocks ? 1 : MM * nTrain))) != cudaSuccess ||
         (e = sgtr.ensure(sizeof(double2) * MM * nTrain)) != cudaSuccess ||
         (e = sttr.ensure(sizeof(int) * nTrain)) != cudaSuccess)
         return cleanup(cuda_fail(e, "training targets"));
@@ -2574,7 +2619,10 @@ knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_t
             const int *ib = md->idx.as<int>() + b0;
             if ((e = knit_mlp_inputs(md->tmpE.as<double>(), ib, B, md->mid, md->half,
                                      md->act.as<float>(), st)) != cudaSuccess ||
-                (e = knit_mlp_targets(gtr.as<double2>(), ib, B, (int)MM, md->Tt.as<float>(), st)) != cudaSuccess)
+                (e = blocks ? knit_mlp_targets_blocks(s->secg.as<double2>(), ib, B, nsec, nb * nb, nTrain,
+                                                      md->Tt.as<float>(), st)
+                            : knit_mlp_targets(gtr.as<double2>(), ib, B, (int)MM, md->Tt.as<float>(), st)) !=
+                    cudaSuccess)
                 return cleanup(cuda_fail(e, "training batch"));
             if ((r = model_forward(md, B, st)) != KNIT_OK || (r = model_backward(md, B, st)) != KNIT_OK)
                 return cleanup(r);
@@ -2608,6 +2656,11 @@ knit_status knit_lead_model_destroy(knit_lead_model md)
 }
 
 int64_t knit_lead_model_num_params(knit_lead_model md) { return md ? (int64_t)md->nparam : 0; }
+
+int64_t knit_lead_model_num_outputs(knit_lead_model md)
+{
+    return md ? (int64_t)md->dims[knit_lead_model_s::NL] : 0;
+}
 
 knit_status knit_lead_model_get_params(knit_lead_model md, float *params)
 {

@@ -321,6 +321,29 @@ extern "C" cudaError_t knit_mlp_inputs(const double *E, const int *idx, int n, d
     return cudaGetLastError();
 }
 
+// targets of a lead solved in blocks: sample r (energy idx[r]) gets every
+// block's surface function, block c at 2 nn c; g holds block c of energy e
+// at (c nE + e) nn
+__global__ void mlp_targets_blocks(const double2 *g, const int *idx, int n, int nsec, int nn, int nE,
+                                   float *Tt)
+{
+    const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long)n * nsec * nn) return;
+    const int r = (int)(q / ((long)nsec * nn)), rem = (int)(q - (long)r * nsec * nn);
+    const int c = rem / nn, k = rem - c * nn;
+    const double2 v = g[((size_t)c * nE + (idx ? idx[r] : r)) * nn + k];
+    Tt[(size_t)r * 2 * nsec * nn + 2 * rem] = (float)v.x;
+    Tt[(size_t)r * 2 * nsec * nn + 2 * rem + 1] = (float)v.y;
+}
+
+extern "C" cudaError_t knit_mlp_targets_blocks(const double2 *g, const int *idx, int n, int nsec, int nn,
+                                               int nE, float *T, cudaStream_t st)
+{
+    const long tot = (long)n * nsec * nn;
+    mlp_targets_blocks<<<(int)((tot + 255) / 256), 256, 0, st>>>(g, idx, n, nsec, nn, nE, T);
+    return cudaGetLastError();
+}
+
 extern "C" cudaError_t knit_mlp_targets(const double2 *g, const int *idx, int n, int MM, float *T,
                                         cudaStream_t st)
 {

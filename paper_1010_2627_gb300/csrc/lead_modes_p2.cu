@@ -118,10 +118,11 @@ template <int N>
 __global__ void __launch_bounds__(128)
 knit_small_decimation_kernel(const double2 *H0s, const double2 *Vs, int nsec, int side,
                              const double *E, int nE, double eta, double tol, int maxit,
-                             double2 *gout, int *iters, int *status)
+                             double2 *gout, int *iters, int *status, int only_failed)
 {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)nsec * nE) return;
+    if (only_failed && status[t] == ST_OK) return;
     const int c = (int)(t / nE), e = (int)(t - (long)c * nE);
     const double2 *H = H0s + (size_t)c * N * N, *V = Vs + (size_t)c * N * N;
     double2 eps[N * N], eps_s[N * N], al[N * N], be[N * N], gb[N * N], t1[N * N], t2[N * N],
@@ -234,7 +235,7 @@ extern "C" cudaError_t knit_launch_small_decimation(const double2 *H0s, const do
                                                     int N, int side, const double *E, int nE,
                                                     double eta, double tol, int maxit,
                                                     double2 *gout, int *iters, int *status,
-                                                    cudaStream_t stream)
+                                                    int only_failed, cudaStream_t stream)
 {
     const long n = (long)nsec * nE;
     if (n <= 0) return cudaSuccess;
@@ -242,19 +243,165 @@ extern "C" cudaError_t knit_launch_small_decimation(const double2 *H0s, const do
     switch (N) {
     case 2:
         knit_small_decimation_kernel<2><<<grid, 128, 0, stream>>>(H0s, Vs, nsec, side, E, nE, eta,
-                                                                  tol, maxit, gout, iters, status);
+                                                                  tol, maxit, gout, iters, status,
+                                                                  only_failed);
         break;
     case 4:
         knit_small_decimation_kernel<4><<<grid, 128, 0, stream>>>(H0s, Vs, nsec, side, E, nE, eta,
-                                                                  tol, maxit, gout, iters, status);
+                                                                  tol, maxit, gout, iters, status,
+                                                                  only_failed);
         break;
     case 6:
         knit_small_decimation_kernel<6><<<grid, 128, 0, stream>>>(H0s, Vs, nsec, side, E, nE, eta,
-                                                                  tol, maxit, gout, iters, status);
+                                                                  tol, maxit, gout, iters, status,
+                                                                  only_failed);
         break;
     case 8:
         knit_small_decimation_kernel<8><<<grid, 128, 0, stream>>>(H0s, Vs, nsec, side, E, nE, eta,
-                                                                  tol, maxit, gout, iters, status);
+                                                                  tol, maxit, gout, iters, status,
+                                                                  only_failed);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Newton's method on the fixed point of each N x N cell from a guess, one
+// thread per (cell c, energy e), t = c * nE + e (the learned warm start of
+// KNIT_LEAD_LEARNED for a lead solved in blocks).  At the real energy E:
+//   F(g) = A g - I,  A = E - H0 - Vl g Vr,  (Vl, Vr) = (V, V^dagger) on the
+//   left, (V^dagger, V) on the right; the step D solves A D - Vl D (Vr g) = -F,
+// a dense N^2 x N^2 system (vec of D row by row) by Gaussian elimination with
+// partial pivoting.  Converged when max |F_ij| < tol and the result is
+// retarded (-Im g_kk >= 0); otherwise status ST_NOCONVERGE (the caller then
+// decimates).  guess: float (re, im) pairs of cell c at guess + e * gstride
+// + 2 N^2 c.
+template <int N>
+__global__ void __launch_bounds__(128)
+knit_small_newton_kernel(const double2 *H0s, const double2 *Vs, int nsec, int side,
+                         const double *E, int nE, const float *guess, long gstride, double tol,
+                         int maxit, double2 *gout, int *iters, int *status)
+{
+    constexpr int NN = N * N;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nsec * nE) return;
+    const int c = (int)(t / nE), e = (int)(t - (long)c * nE);
+    const double2 *H = H0s + (size_t)c * NN, *V = Vs + (size_t)c * NN;
+    double2 g[NN], A[NN], B[NN], F[NN], J[NN * NN];
+    const float *gs = guess + (size_t)e * gstride + 2 * NN * c;
+    for (int q = 0; q < NN; ++q) g[q] = make_double2((double)gs[2 * q], (double)gs[2 * q + 1]);
+    auto vl = [&](int i, int k) { return side == 0 ? V[i * N + k] : cconj(V[k * N + i]); };
+    auto vr = [&](int i, int k) { return side == 0 ? cconj(V[k * N + i]) : V[i * N + k]; };
+    const double En = E[e];
+    int it = 0, st = ST_NOCONVERGE;
+    for (it = 0; it <= maxit; ++it) {
+        // A = E - H0 - Vl g Vr, B = Vr g
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                double2 s = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+                for (int k = 0; k < N; ++k) {
+                    double2 u = make_double2(0.0, 0.0);
+                    for (int l = 0; l < N; ++l) u = cfma(g[k * N + l], vr(l, j), u);
+                    s = cfma(vl(i, k), u, s);
+                    b = cfma(vr(i, k), g[k * N + j], b);
+                }
+                double2 a = make_double2(-H[i * N + j].x - s.x, -H[i * N + j].y - s.y);
+                if (i == j) a.x += En;
+                A[i * N + j] = a;
+                B[i * N + j] = b;
+            }
+        double fm = 0.0;
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                double2 s = make_double2(i == j ? -1.0 : 0.0, 0.0);
+                for (int k = 0; k < N; ++k) s = cfma(A[i * N + k], g[k * N + j], s);
+                F[i * N + j] = s;
+                fm = fmax(fm, fabs(s.x) + fabs(s.y));
+            }
+        if (!isfinite(fm)) break;
+        if (fm < tol) {
+            st = ST_OK;
+            break;
+        }
+        if (it == maxit) break;
+        // J[(i,j),(k,l)] = A[i][k] delta(l,j) - Vl[i][k] B[l][j]; right-hand side -F
+        for (int p = 0; p < NN; ++p) {
+            const int i = p / N, j = p - i * N;
+            for (int r = 0; r < NN; ++r) {
+                const int k = r / N, l = r - k * N;
+                double2 v = cmul(vl(i, k), B[l * N + j]);
+                v = make_double2(-v.x, -v.y);
+                if (l == j) v = cadd(v, A[i * N + k]);
+                J[p * NN + r] = v;
+            }
+            F[p] = make_double2(-F[p].x, -F[p].y);
+        }
+        bool ok = true;
+        for (int k = 0; k < NN && ok; ++k) {
+            int pv = k;
+            double best = cabs1(J[k * NN + k]);
+            for (int i = k + 1; i < NN; ++i)
+                if (cabs1(J[i * NN + k]) > best) {
+                    best = cabs1(J[i * NN + k]);
+                    pv = i;
+                }
+            if (!(best > 0.0)) {
+                ok = false;
+                break;
+            }
+            if (pv != k) {
+                for (int j = k; j < NN; ++j) {
+                    const double2 tt = J[k * NN + j];
+                    J[k * NN + j] = J[pv * NN + j];
+                    J[pv * NN + j] = tt;
+                }
+                const double2 tt = F[k];
+                F[k] = F[pv];
+                F[pv] = tt;
+            }
+            const double2 inv = crcp(J[k * NN + k]);
+            for (int i = k + 1; i < NN; ++i) {
+                const double2 f = cmul(J[i * NN + k], inv);
+                if (f.x == 0.0 && f.y == 0.0) continue;
+                for (int j = k + 1; j < NN; ++j) J[i * NN + j] = cfms(f, J[k * NN + j], J[i * NN + j]);
+                F[i] = cfms(f, F[k], F[i]);
+            }
+        }
+        if (!ok) break;
+        for (int k = NN - 1; k >= 0; --k) {
+            double2 s = F[k];
+            for (int j = k + 1; j < NN; ++j) s = cfms(J[k * NN + j], F[j], s);
+            F[k] = cmul(s, crcp(J[k * NN + k]));   // the step D, in place
+        }
+        for (int q = 0; q < NN; ++q) g[q] = cadd(g[q], F[q]);
+    }
+    if (st == ST_OK)
+        for (int k = 0; k < N; ++k)
+            if (g[k * N + k].y > 1e-12) st = ST_NOCONVERGE;
+    double2 *G = gout + (size_t)t * NN;
+    for (int q = 0; q < NN; ++q) G[q] = st == ST_OK ? g[q] : make_double2(nan(""), nan(""));
+    if (iters) iters[t] = it;
+    if (status) status[t] = st;
+}
+
+extern "C" cudaError_t knit_launch_small_newton(const double2 *H0s, const double2 *Vs, int nsec, int N,
+                                                int side, const double *E, int nE, const float *guess,
+                                                long gstride, double tol, int maxit, double2 *gout,
+                                                int *iters, int *status, cudaStream_t stream)
+{
+    const long n = (long)nsec * nE;
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)((n + 127) / 128);
+    switch (N) {
+    case 2:
+        knit_small_newton_kernel<2><<<grid, 128, 0, stream>>>(H0s, Vs, nsec, side, E, nE, guess, gstride,
+                                                              tol, maxit, gout, iters, status);
+        break;
+    case 4:
+        knit_small_newton_kernel<4><<<grid, 128, 0, stream>>>(H0s, Vs, nsec, side, E, nE, guess, gstride,
+                                                              tol, maxit, gout, iters, status);
         break;
     default:
         return cudaErrorInvalidValue;

@@ -85,6 +85,7 @@ _SIGS = {
                                     P, P, P, P]),
     "knit_lead_model_destroy": (i32, [P]),
     "knit_lead_model_num_params": (ctypes.c_int64, [P]),
+    "knit_lead_model_num_outputs": (ctypes.c_int64, [P]),
     "knit_lead_model_get_params": (i32, [P, P]),
     "knit_lead_model_set_params": (i32, [P, P]),
     "knit_lead_model_forward": (i32, [P, P, i32, P, P]),
@@ -520,10 +521,13 @@ class LeadModel:
         p = np.ascontiguousarray(params, dtype=np.float32)
         _check(load().knit_lead_model_set_params(P(self.handle), _ptr(p)))
 
+    @property
+    def num_outputs(self):
+        return int(load().knit_lead_model_num_outputs(P(self.handle)))
+
     def forward(self, E):
         E = np.ascontiguousarray(E, dtype=np.float64)
-        M = self.system.M
-        out = np.empty((len(E), 2 * M * M), np.float32)
+        out = np.empty((len(E), self.num_outputs), np.float32)
         _check(load().knit_lead_model_forward(P(self.handle), _ptr(E), len(E), _ptr(out), None))
         return out
 

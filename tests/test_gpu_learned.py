@@ -96,3 +96,73 @@ def test_learned_lead_bdg_cell(knit):
     for e, Ee in enumerate(E):
         _, So, _ = oracle.decimation(b.lead_H0[0], b.lead_V[0], Ee, 0, eta=1e-12)
         assert np.abs(S[e] - So).max() < 1e-7
+
+
+@pytest.fixture(scope="module")
+def ribbon_lead_model(knit):
+    """The armchair ribbon's period-2 lead (M = 64: 32 blocks of 4 x 4 in the
+    eigenbasis of its cell), the network trained on 20 000 decimation samples
+    over (-2, 2)"""
+    ss = inputs.armchair(64, 3)
+    sysk = knit.System(ss)
+    E_train = np.random.default_rng(3).uniform(-2.0, 2.0, 20000)
+    model = knit.LeadModel(sysk, 0, E_train, epochs=60, batch=256, lr=1e-3, seed=4)
+    return ss, sysk, model
+
+
+def test_learned_lead_mode_blocks_against_oracle(knit, ribbon_lead_model):
+    ss, sysk, model = ribbon_lead_model
+    assert sysk.info()[1] == [32, 32]
+    assert model.num_outputs == 2 * 32 * 16
+    assert model.loss[-1] < 0.05 * model.loss[0]
+    E = np.array([-1.7, -0.45, 0.31, 1.2])
+    S, it, res = sysk.lead_selfenergy(0, E, method=knit.KNIT_LEAD_LEARNED, want_residual=True,
+                                      models=(model, None))
+    for e, Ee in enumerate(E):
+        So = oracle.decimation_period2(ss.H0, *ss.lead_V[0], Ee, 0)
+        assert np.abs(S[e] - So).max() < 1e-8 * max(1.0, np.abs(So).max()), Ee
+        assert res[e] < 1e-7
+
+
+def test_learned_lead_mode_blocks_time_to_fixed_point(knit):
+    """Wall time for the self-energies of the 256-site ribbon's lead at 8192
+    energies, with the network (Newton to max|A g - I| < 1e-12 at eta = 0 in
+    every block, decimation where Newton does not settle) and without it
+    (decimation at eta = 1e-12): the two agree to the decimation tolerance,
+    most blocks settle by Newton, and the learned path is the faster one."""
+    import time
+    import torch
+    ss = inputs.armchair(256, 3)
+    sysk = knit.System(ss)
+    t0 = time.perf_counter()
+    model = knit.LeadModel(sysk, 0, np.random.default_rng(8).uniform(-2.0, 2.0, 20000), epochs=60,
+                           batch=256, lr=1e-3, seed=5)
+    train_s = time.perf_counter() - t0
+    E = inputs.energy_grid(-2.0, 2.0, 8192)
+    dE = torch.tensor(E, device="cuda")
+    dS = torch.empty(8192 * 256 * 256 * 2, dtype=torch.float64, device="cuda")
+    dit = torch.empty(8192, dtype=torch.int32, device="cuda")
+
+    def run(method):
+        opts = knit._opts(method, 0.0, models=(model.handle, None))
+        knit.knit_lead_selfenergy(sysk.handle, 0, dE, dS, opts, dit)
+        torch.cuda.synchronize()
+
+    times = {}
+    out = {}
+    for method in (knit.KNIT_LEAD_DECIMATION, knit.KNIT_LEAD_LEARNED):
+        run(method)   # warm-up
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            run(method)
+            ts.append(time.perf_counter() - t0)
+        times[method] = sorted(ts)[1]
+        out[method] = (dS.view(8192, 256, 256, 2)[::97].cpu().numpy(), dit.cpu().numpy())
+    Sd, itd = out[knit.KNIT_LEAD_DECIMATION]
+    Sl, itl = out[knit.KNIT_LEAD_LEARNED]
+    assert np.abs(Sl - Sd).max() < 1e-7 * max(1.0, np.abs(Sd).max())
+    print(f"ribbon lead, 8192 energies: decimation {times[knit.KNIT_LEAD_DECIMATION]:.3f} s, "
+          f"learned + Newton {times[knit.KNIT_LEAD_LEARNED]:.3f} s (training {train_s:.1f} s)")
+    assert times[knit.KNIT_LEAD_LEARNED] < times[knit.KNIT_LEAD_DECIMATION]
+    sysk.close()
