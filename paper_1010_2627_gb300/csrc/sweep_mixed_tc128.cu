@@ -103,6 +103,7 @@ struct Tc128Smem {
             float2 vh[MP * 4], vl[MP * 4];             // row r: V[r][4 (r / 4) + b], b = 0 .. 3
         } va;
         struct {                                       // double-float inversion of a slice
+            float2 hi[MP * MP];                        // hi parts, row-major
             float4 col[MP];                            // column k before the step
             float4 row[MP];                            // row k after scaling
             float4 inv;                                // 1 / pivot
@@ -1222,12 +1223,14 @@ __device__ int fallback64(Tc128Work &wk, int M)
 
 // near-singular A_n: this slice inverted by Gauss-Jordan with partial
 // pivoting in double-float on the CUDA cores (entries as (hi, lo) float
-// pairs, ~2^-47 relative per operation, about six times the speed of the
-// FP64 pipe's Gauss-Jordan at this width), from Gv' in the state; rows are
-// swapped in place and the swaps undone on the columns at the end
+// pairs, ~2^-47 relative per operation, several times the speed of the FP64
+// pipe's Gauss-Jordan at this width), from Gv' in the state.  The hi parts
+// live in shared memory, the lo parts in the workspace; rows are swapped in
+// place and the swaps undone on the columns at the end.
 __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
 {
-    float4 *const a = reinterpret_cast<float4 *>(wk.A64);   // row-major MP x MP: hi.re, hi.im, lo.re, lo.im
+    float2 *const ah = sm.u.fb.hi;                               // row-major MP x MP
+    float2 *const al = reinterpret_cast<float2 *>(wk.A64);       // same layout
     const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
     const float2 *gl = reinterpret_cast<const float2 *>(wk.Gl);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1235,7 +1238,8 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
         const int i = e >> 7, j = e & (MP - 1);
         if (i >= M || j >= M) continue;
         const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
-        a[e] = make_float4(-gh[f].x, -gh[f].y, -gl[f].x, -gl[f].y);
+        ah[e] = make_float2(-gh[f].x, -gh[f].y);
+        al[e] = make_float2(-gl[f].x, -gl[f].y);
     }
     __syncthreads();
     for (int k = 0; k < M; ++k) {
@@ -1244,7 +1248,7 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
             const int i = 32 * warp + lane;
             float v = -1.f;
             if (i >= k && i < M) {
-                const float4 x = a[i * MP + k];
+                const float2 x = ah[i * MP + k];
                 v = fabsf(x.x) + fabsf(x.y);
             }
             int bi = i;
@@ -1279,12 +1283,18 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
         if (r < 0) return ST_SINGULAR;
         if (r != k)
             for (int j = tid; j < M; j += NTH) {
-                const float4 t = a[k * MP + j];
-                a[k * MP + j] = a[r * MP + j];
-                a[r * MP + j] = t;
+                float2 t = ah[k * MP + j];
+                ah[k * MP + j] = ah[r * MP + j];
+                ah[r * MP + j] = t;
+                t = al[k * MP + j];
+                al[k * MP + j] = al[r * MP + j];
+                al[r * MP + j] = t;
             }
         __syncthreads();
-        for (int i = tid; i < M; i += NTH) sm.u.fb.col[i] = a[i * MP + k];
+        for (int i = tid; i < M; i += NTH) {
+            const float2 h = ah[i * MP + k], l = al[i * MP + k];
+            sm.u.fb.col[i] = make_float4(h.x, h.y, l.x, l.y);
+        }
         __syncthreads();
         if (tid == 0) {
             const float4 pv = sm.u.fb.col[k];
@@ -1298,25 +1308,26 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
         __syncthreads();
         const float4 inv = sm.u.fb.inv;
         for (int j = tid; j < M; j += NTH) {
-            const float4 x = j == k ? make_float4(1.f, 0.f, 0.f, 0.f) : a[k * MP + j];
-            float2 h, l;
-            cdf_mul(make_float2(x.x, x.y), make_float2(x.z, x.w), make_float2(inv.x, inv.y),
-                    make_float2(inv.z, inv.w), h, l);
-            const float4 y = make_float4(h.x, h.y, l.x, l.y);
-            a[k * MP + j] = y;
-            sm.u.fb.row[j] = y;
+            float2 h = j == k ? make_float2(1.f, 0.f) : ah[k * MP + j];
+            float2 l = j == k ? make_float2(0.f, 0.f) : al[k * MP + j];
+            cdf_mul(h, l, make_float2(inv.x, inv.y), make_float2(inv.z, inv.w), h, l);
+            ah[k * MP + j] = h;
+            al[k * MP + j] = l;
+            sm.u.fb.row[j] = make_float4(h.x, h.y, l.x, l.y);
         }
         __syncthreads();
         for (int e = tid; e < MP * MP; e += NTH) {
             const int i = e >> 7, j = e & (MP - 1);
             if (i >= M || j >= M || i == k) continue;
             const float4 c = sm.u.fb.col[i], rw = sm.u.fb.row[j];
-            const float4 x = j == k ? make_float4(0.f, 0.f, 0.f, 0.f) : a[e];
-            float2 ph, pl, h = make_float2(x.x, x.y), l = make_float2(x.z, x.w);
+            float2 h = j == k ? make_float2(0.f, 0.f) : ah[e];
+            float2 l = j == k ? make_float2(0.f, 0.f) : al[e];
+            float2 ph, pl;
             cdf_mul(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(rw.x, rw.y),
                     make_float2(rw.z, rw.w), ph, pl);
             cdf_add(h, l, make_float2(-ph.x, -ph.y), make_float2(-pl.x, -pl.y));
-            a[e] = make_float4(h.x, h.y, l.x, l.y);
+            ah[e] = h;
+            al[e] = l;
         }
         __syncthreads();
     }
@@ -1325,9 +1336,12 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
         const int r = sm.perm[k];
         if (r != k)
             for (int i = tid; i < M; i += NTH) {
-                const float4 t = a[i * MP + k];
-                a[i * MP + k] = a[i * MP + r];
-                a[i * MP + r] = t;
+                float2 t = ah[i * MP + k];
+                ah[i * MP + k] = ah[i * MP + r];
+                ah[i * MP + r] = t;
+                t = al[i * MP + k];
+                al[i * MP + k] = al[i * MP + r];
+                al[i * MP + r] = t;
             }
         __syncthreads();
     }
@@ -1337,9 +1351,8 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
         const int i = e & (MP - 1), j = e >> 7;
         const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
         if (i < M && j < M) {
-            const float4 v = a[i * MP + j];
-            oh[f] = make_float2(v.x, v.y);
-            ol[f] = make_float2(v.z, v.w);
+            oh[f] = ah[i * MP + j];
+            ol[f] = al[i * MP + j];
         } else {
             oh[f] = make_float2(i == j ? 1.f : 0.f, 0.f);
             ol[f] = make_float2(0.f, 0.f);
