@@ -287,6 +287,16 @@ def run_knit(args):
     clk = _clock_summary(clocks, dev)
     T_mixed = dT.cpu().numpy().reshape(NE, NS).copy()
     st = dst.cpu().numpy()
+    gathered = None
+    if ws > 1:
+        # every rank's T in the global (energy, seed) order, once, on the host
+        def agather(obj):
+            out = [None] * ws
+            torch.distributed.all_gather_object(out, obj)
+            return out
+        rows = shard.interleave(NE * ws, ws, rank)
+        idx = (rows[:, None] * NS + np.arange(NS)[None, :]).ravel()
+        gathered = int(len(shard.gather(T_mixed.ravel(), idx, NE * ws * NS, agather)))
     ms_per_step = total_ms / args.steps
     value = ws * n / (ms_per_step / 1e3)
 
@@ -412,6 +422,8 @@ def run_knit(args):
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
         "status_nonzero": int((st != 0).sum()),
     }
+    if gathered is not None:
+        line["results_gathered"] = gathered
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(E, seeds) if ws == 1 else None
     if rank == 0:
@@ -432,12 +444,23 @@ def run_uneven(args):
     instances (the shortest of each width) checked against the oracle, and
     the oracle's rate on that subset."""
     import torch
-    from paper_1010_2627_gb300 import build, inputs, knit
+    from paper_1010_2627_gb300 import build, inputs, knit, shard
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        dist.init_process_group("nccl")
     build.build()
     knit.load()
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     pk = measure_peaks(knit, torch, torch.cuda.current_stream(), nsm)
-    inst = inputs.uneven_instances(4096)
+    inst_all = inputs.uneven_instances(4096)
+    n_all = len(inst_all["M"])
+    # several GPUs: the fixed batch split by cost M^3 L, longest first
+    # (strong scaling), each rank one plan over its share
+    owner = shard.lpt(inst_all["M"].astype(np.float64) ** 3 * inst_all["L"], ws)
+    mine = np.flatnonzero(owner == rank)
+    inst = {k: v[mine] for k, v in inst_all.items()}
     keys = sorted(set(zip(inst["M"].tolist(), inst["L"].tolist())))
     systems = [knit.System(inputs.square(m, l)) for m, l in keys]
     sys_index = np.array([keys.index((m, l)) for m, l in zip(inst["M"], inst["L"])], np.int32)
@@ -465,6 +488,9 @@ def run_uneven(args):
             flush.fill_(1.0)
             step()
     torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     clocks = _clock_sampler()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -476,9 +502,24 @@ def run_uneven(args):
             ev[k][1].record(stream)
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
     clk = _clock_summary(clocks, torch.cuda.current_device())
-    T = dT.cpu().numpy()
-    st = dst.cpu().numpy()
+    T_mine = dT.cpu().numpy()
+    st_mine = dst.cpu().numpy()
+    if ws > 1:
+        # every rank's results in the caller's instance order, once, on the host
+        def agather(obj):
+            out = [None] * ws
+            torch.distributed.all_gather_object(out, obj)
+            return out
+        T = shard.gather(T_mine, mine, n_all, agather)
+        st = shard.gather(st_mine, mine, n_all, agather)
+    else:
+        T, st = T_mine, st_mine
+    inst, n = inst_all, n_all
     # the same step captured once in a CUDA graph and replayed (the plan only
     # enqueues kernels once its buffers exist)
     graph = {}
@@ -497,7 +538,7 @@ def run_uneven(args):
         torch.cuda.synchronize()
         gms = statistics.mean(a.elapsed_time(b) for a, b in gev)
         graph = {"ms_per_step": gms, "value": n / (gms / 1e3),
-                 "same_T": bool(np.array_equal(dT.cpu().numpy(), T))}
+                 "same_T": bool(np.array_equal(dT.cpu().numpy(), T_mine))}
     except Exception as exc:   # capture refused: report, keep the stream numbers
         graph = {"error": str(exc)[:200]}
     slices = int(inst["L"].sum())
@@ -506,8 +547,8 @@ def run_uneven(args):
     Ms = inst["M"]
     line = {
         "metric": "T(E) points/s (uneven batch)", "value": n / (ms / 1e3),
-        "unit": "T(E) points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "unit": "T(E) points/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "c64 inversion + bf16-digit tensor-core residual (f32 accumulate)",
         "data": "synthetic",
         "config": {"workload": "uneven square batch, 4096 instances, M in {32..128}, "
@@ -527,6 +568,12 @@ def run_uneven(args):
                              "ctas_per_sm": tuned[q]} for q, (k, m, c, x) in enumerate(batch.buckets())],
         "autotune_s": tune_s, "cuda_graph": graph,
         "status_nonzero": int((st != 0).sum())}
+    if ws > 1:
+        line["sharding"] = "LPT by M^3 L over ranks, results gathered to rank 0"
+    if rank != 0:
+        batch.close()
+        torch.distributed.destroy_process_group()
+        return
     # stratified subset: the 13 (12 for the last width) shortest instances of each width
     import oracle
     sub = []
@@ -560,6 +607,8 @@ def run_uneven(args):
                                           f"OpenMP over instances, {dt:.1f} s"}
     print(json.dumps(line), flush=True)
     batch.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def run_profile_case(args):
