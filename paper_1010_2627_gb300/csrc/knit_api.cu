@@ -2522,16 +2522,16 @@ knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_t
                                       "leads that split into blocks of at most 4");
     if (!blocks && ld.Mp != s->M)
         return fail(KNIT_ERR_INVALID, "this period-2 lead does not split into blocks of at most 4");
-    const int nb = blocks ? 2 * ld.ms : 0, nsec = blocks ? ld.nsec : 0;
+    const int bsz = blocks ? 2 * ld.ms : 0, nsec = blocks ? ld.nsec : 0;
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<double> hE;
     if ((r = to_host(hE, E_train, (size_t)nTrain, "E_train")) != KNIT_OK) return r;
     knit_lead_model md = new (std::nothrow)
-        knit_lead_model_s(s->M, blocks ? 2 * nsec * nb * nb : 2 * s->M * s->M);
+        knit_lead_model_s(s->M, blocks ? 2 * nsec * bsz * bsz : 2 * s->M * s->M);
     if (!md) return fail(KNIT_ERR_OOM, "host allocation");
     md->nsec = nsec;
-    md->nb = nb;
+    md->nb = bsz;
     md->sys = s;
     md->lead = lead;
     md->device = s->device;
@@ -2619,7 +2619,7 @@ knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_t
             const int *ib = md->idx.as<int>() + b0;
             if ((e = knit_mlp_inputs(md->tmpE.as<double>(), ib, B, md->mid, md->half,
                                      md->act.as<float>(), st)) != cudaSuccess ||
-                (e = blocks ? knit_mlp_targets_blocks(s->secg.as<double2>(), ib, B, nsec, nb * nb, nTrain,
+                (e = blocks ? knit_mlp_targets_blocks(s->secg.as<double2>(), ib, B, nsec, bsz * bsz, nTrain,
                                                       md->Tt.as<float>(), st)
                             : knit_mlp_targets(gtr.as<double2>(), ib, B, (int)MM, md->Tt.as<float>(), st)) !=
                     cudaSuccess)
