@@ -53,6 +53,7 @@ extern "C" cudaError_t knit_launch_decimation_df(const double2 *, const double2 
 extern "C" cudaError_t knit_launch_small_newton(const double2 *, const double2 *, int, int, int,
                                                 const double *, int, const float *, long, double, int,
                                                 double2 *, int *, int *, cudaStream_t);
+extern "C" cudaError_t knit_mlp_block_gmax(const double2 *, int, int, int, float *, cudaStream_t);
 extern "C" cudaError_t knit_mlp_targets_blocks(const double2 *, const int *, int, int, int, int, float *,
                                                cudaStream_t);
 extern "C" cudaError_t knit_launch_p2_sector_sigma(const double2 *, const int *, int, int, int,
@@ -2606,6 +2607,29 @@ knit_status knit_lead_model_train(knit_system s, int32_t lead, const double *E_t
     std::vector<int> valid;
     for (int i = 0; i < nTrain; ++i)
         if (hst[i] == ST_OK) valid.push_back(i);
+    if (blocks && valid.size() > 16) {
+        // a lead in blocks: leave out the energies next to a band edge of some
+        // block (largest |g| above 8x the median), where g diverges like
+        // 1/sqrt(E - E_edge) and would dominate the squared error; Newton falls
+        // back to decimation there anyway
+        DevBuf gm;
+        std::vector<float> hg(nTrain);
+        if ((e = gm.ensure(sizeof(float) * nTrain)) != cudaSuccess ||
+            (e = knit_mlp_block_gmax(s->secg.as<double2>(), nsec, bsz * bsz, nTrain, gm.as<float>(), st)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(hg.data(), gm.p, sizeof(float) * nTrain, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cleanup(cuda_fail(e, "training targets"));
+        std::vector<float> v;
+        for (int i : valid) v.push_back(hg[i]);
+        std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+        const float cap = 8.f * v[v.size() / 2];
+        std::vector<int> kept;
+        for (int i : valid)
+            if (hg[i] <= cap) kept.push_back(i);
+        valid.swap(kept);
+    }
     if (valid.size() < 2) return cleanup(fail(KNIT_ERR_NOCONVERGE, "decimation failed on the training set"));
     const int nv = (int)valid.size();
     const int B = std::min(batch, nv);

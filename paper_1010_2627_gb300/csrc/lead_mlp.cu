@@ -336,6 +336,28 @@ __global__ void mlp_targets_blocks(const double2 *g, const int *idx, int n, int 
     Tt[(size_t)r * 2 * nsec * nn + 2 * rem + 1] = (float)v.y;
 }
 
+// largest |g_ij| over every block of each energy (the training set leaves out
+// energies next to a band edge, where g diverges)
+__global__ void mlp_block_gmax(const double2 *g, int nsec, int nn, int nE, float *gmax)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    float m = 0.f;
+    for (int c = 0; c < nsec; ++c)
+        for (int k = 0; k < nn; ++k) {
+            const double2 v = g[((size_t)c * nE + e) * nn + k];
+            m = fmaxf(m, (float)(fabs(v.x) + fabs(v.y)));
+        }
+    gmax[e] = m;
+}
+
+extern "C" cudaError_t knit_mlp_block_gmax(const double2 *g, int nsec, int nn, int nE, float *gmax,
+                                           cudaStream_t st)
+{
+    mlp_block_gmax<<<(nE + 127) / 128, 128, 0, st>>>(g, nsec, nn, nE, gmax);
+    return cudaGetLastError();
+}
+
 extern "C" cudaError_t knit_mlp_targets_blocks(const double2 *g, const int *idx, int n, int nsec, int nn,
                                                int nE, float *T, cudaStream_t st)
 {
