@@ -47,9 +47,6 @@ extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cuda
 extern "C" cudaError_t knit_launch_small_decimation(const double2 *, const double2 *, int, int, int,
                                                     const double *, int, double, double, int,
                                                     double2 *, int *, int *, int, cudaStream_t);
-extern "C" cudaError_t knit_launch_decimation_df(const double2 *, const double2 *, int, int, int,
-                                                 const double *, int, double, double, int, double2 *,
-                                                 double2 *, double2 *, int *, int *, int, cudaStream_t);
 extern "C" cudaError_t knit_launch_small_newton(const double2 *, const double2 *, int, int, int,
                                                 const double *, int, const float *, long, double, int,
                                                 double2 *, int *, int *, cudaStream_t);
@@ -932,15 +929,13 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
         CK(s->secg.ensure(sizeof(double2) * mm * nE * ns), "sector g");
         CK(s->secst.ensure(sizeof(int) * (size_t)nE * ns), "sector status");
         CK(s->secit.ensure(sizeof(int) * (size_t)nE * ns), "sector iterations");
-        // the doubling steps in double-float on the CUDA cores for sectors of
-        // up to 64 orbitals (GB300's FP64 rate is 1/72 of FP32), the converged
-        // surface function accepted in FP64
         for (int q = 0; q < ns; ++q)
-            CK((ms <= 64 ? knit_launch_decimation_df : knit_launch_decimation)(
-                   ld.sH0 + q * mm, ld.sV + q * mm, ms, ms, p, dE, nE, eta, tol, maxit,
-                   s->decw.as<double2>(), s->secs.as<double2>() + q * mm * nE,
-                   s->secg.as<double2>() + q * mm * nE, s->secit.as<int>() + (size_t)q * nE,
-                   s->secst.as<int>() + (size_t)q * nE, grid, st),
+            CK(knit_launch_decimation(ld.sH0 + q * mm, ld.sV + q * mm, ms, ms, p, dE, nE, eta, tol,
+                                      maxit, s->decw.as<double2>(),
+                                      s->secs.as<double2>() + q * mm * nE,
+                                      s->secg.as<double2>() + q * mm * nE,
+                                      s->secit.as<int>() + (size_t)q * nE,
+                                      s->secst.as<int>() + (size_t)q * nE, grid, st),
                "sector decimation");
         CK(knit_launch_sector_assemble(s->secs.as<double2>(), ld.sidx, ns, ms, M, nE, sig, st),
            "sector sigma assembly");

@@ -17,7 +17,6 @@
 
 #include <algorithm>
 #include "dense_fp64.cuh"
-#include "mixed_common.cuh"
 
 // W = V G V^dagger (side 0) or V^dagger G V (side 1): elementwise for
 // block-diagonal V (blocks up to 4), as two products for a dense V (a
@@ -221,268 +220,13 @@ knit_modes_sigma_kernel(const double2 *U, const double2 *Adiag, int M, double t2
 }
 
 // ---------------------------------------------------------------------------
-// The decimation's doubling steps in double-float (hi + lo floats on the CUDA
-// cores, ~2^-47 per operation; GB300 runs FP64 at 1/72 of its FP32 rate), for
-// cells of at most 64 orbitals.  Matrices: float4 (hi.re, hi.im, lo.re,
-// lo.im) row-major, leading dimension M, in the same workspace slots as the
-// FP64 path's double2 matrices.
-
-// C = A B (all threads; ends with a barrier): products of the hi parts exact
-// (TwoProduct), the cross terms in fp32, the running sums compensated
-static __device__ void gemm_df(const float4 *A, const float4 *B, float4 *C, int M)
-{
-    for (int q = threadIdx.x; q < M * M; q += blockDim.x) {
-        const int i = q / M, j = q - i * M;
-        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
-        for (int k = 0; k < M; ++k) {
-            const float4 a = A[i * M + k], b = B[k * M + j];
-            // re: a.re b.re - a.im b.im; im: a.re b.im + a.im b.re
-            float p, e, t, u;
-            p = a.x * b.x;
-            e = fmaf(a.x, b.x, -p);
-            e = fmaf(a.x, b.z, fmaf(a.z, b.x, e));
-            two_sum(sr, p, t, u);
-            sr = t;
-            cr += u + e;
-            p = -a.y * b.y;
-            e = fmaf(-a.y, b.y, -p);
-            e = fmaf(-a.y, b.w, fmaf(-a.w, b.y, e));
-            two_sum(sr, p, t, u);
-            sr = t;
-            cr += u + e;
-            p = a.x * b.y;
-            e = fmaf(a.x, b.y, -p);
-            e = fmaf(a.x, b.w, fmaf(a.z, b.y, e));
-            two_sum(si, p, t, u);
-            si = t;
-            ci += u + e;
-            p = a.y * b.x;
-            e = fmaf(a.y, b.x, -p);
-            e = fmaf(a.y, b.z, fmaf(a.w, b.x, e));
-            two_sum(si, p, t, u);
-            si = t;
-            ci += u + e;
-        }
-        float hr, lr, hi, li;
-        two_sum(sr, cr, hr, lr);
-        two_sum(si, ci, hi, li);
-        C[q] = make_float4(hr, hi, lr, li);
-    }
-    __syncthreads();
-}
-
-// X += Y (DF, elementwise; all threads, ends with a barrier)
-static __device__ void add_df(float4 *X, const float4 *Y, int n)
-{
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        const float4 x = X[q], y = Y[q];
-        float2 h = make_float2(x.x, x.y), l = make_float2(x.z, x.w);
-        mixed::cdf_add(h, l, make_float2(y.x, y.y), make_float2(y.z, y.w));
-        X[q] = make_float4(h.x, h.y, l.x, l.y);
-    }
-    __syncthreads();
-}
-
-// in-place inverse of A (M <= 64) by Gauss-Jordan with partial pivoting in
-// double-float; rows swapped in place, the swaps undone on the columns; the
-// scratch of the FP64 routine reused (row / col as float4, red for the
-// per-warp pivot keys)
-static __device__ int inverse_df(float4 *a, int M, GJScratch64 &sc, double *red)
-{
-    float4 *const colk = reinterpret_cast<float4 *>(sc.col);
-    float4 *const rowk = reinterpret_cast<float4 *>(sc.row);
-    float4 *const inv = reinterpret_cast<float4 *>(sc.pval);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int k = 0; k < M; ++k) {
-        if (warp < 2) {
-            const int i = 32 * warp + lane;
-            float v = -1.f;
-            if (i >= k && i < M) {
-                const float4 x = a[i * M + k];
-                v = fabsf(x.x) + fabsf(x.y);
-            }
-            int bi = i;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > v || (ov == v && oi < bi)) {
-                    v = ov;
-                    bi = oi;
-                }
-            }
-            if (lane == 0) {
-                red[warp] = v;
-                red[16 + warp] = bi;
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double v = red[0];
-            int r = (int)red[16];
-            if (red[1] > v) {
-                v = red[1];
-                r = (int)red[17];
-            }
-            sc.perm[k] = r;
-            *sc.flag = (v > 0.0 && isfinite(v)) ? r : -1;
-        }
-        __syncthreads();
-        const int r = *sc.flag;
-        if (r < 0) return ST_SINGULAR;
-        if (r != k)
-            for (int j = tid; j < M; j += blockDim.x) {
-                const float4 t = a[k * M + j];
-                a[k * M + j] = a[r * M + j];
-                a[r * M + j] = t;
-            }
-        __syncthreads();
-        for (int i = tid; i < M; i += blockDim.x) colk[i] = a[i * M + k];
-        __syncthreads();
-        if (tid == 0) {
-            const float4 pv = colk[k];
-            const double pr = (double)pv.x + (double)pv.z, pi = (double)pv.y + (double)pv.w;
-            const double d = 1.0 / (pr * pr + pi * pi);
-            float4 w;
-            mixed::to_df(pr * d, w.x, w.z);
-            mixed::to_df(-pi * d, w.y, w.w);
-            *inv = w;
-        }
-        __syncthreads();
-        const float4 iv = *inv;
-        for (int j = tid; j < M; j += blockDim.x) {
-            float2 h = j == k ? make_float2(1.f, 0.f) : make_float2(a[k * M + j].x, a[k * M + j].y);
-            float2 l = j == k ? make_float2(0.f, 0.f) : make_float2(a[k * M + j].z, a[k * M + j].w);
-            mixed::cdf_mul(h, l, make_float2(iv.x, iv.y), make_float2(iv.z, iv.w), h, l);
-            a[k * M + j] = make_float4(h.x, h.y, l.x, l.y);
-            rowk[j] = a[k * M + j];
-        }
-        __syncthreads();
-        for (int q = tid; q < M * M; q += blockDim.x) {
-            const int i = q / M, j = q - i * M;
-            if (i == k) continue;
-            const float4 c = colk[i], rw = rowk[j];
-            const float4 x = j == k ? make_float4(0.f, 0.f, 0.f, 0.f) : a[q];
-            float2 h = make_float2(x.x, x.y), l = make_float2(x.z, x.w), ph, pl;
-            mixed::cdf_mul(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(rw.x, rw.y),
-                           make_float2(rw.z, rw.w), ph, pl);
-            mixed::cdf_add(h, l, make_float2(-ph.x, -ph.y), make_float2(-pl.x, -pl.y));
-            a[q] = make_float4(h.x, h.y, l.x, l.y);
-        }
-        __syncthreads();
-    }
-    for (int k = M - 1; k >= 0; --k) {
-        const int r = sc.perm[k];
-        if (r != k)
-            for (int i = tid; i < M; i += blockDim.x) {
-                const float4 t = a[i * M + k];
-                a[i * M + k] = a[i * M + r];
-                a[i * M + r] = t;
-            }
-        __syncthreads();
-    }
-    return ST_OK;
-}
-
-// the doubling of the decimation below in double-float; on return the
-// workspace slot of eps_s holds eps_s as double2 (FP64) for the acceptance
-// tests, `it` the iterations taken; status as in the FP64 loop
-static __device__ int doubling_df(const double2 *H0, const double2 *V, int M, int side, double2 z,
-                                  double tol, int maxit, double2 *w, GJScratch64 &sc, double *red,
-                                  int &it)
-{
-    const int MM = M * M;
-    float4 *const f = reinterpret_cast<float4 *>(w);
-    float4 *eps = f, *eps_s = f + MM, *al = f + 2 * MM, *be = f + 3 * MM;
-    float4 *gb = f + 4 * MM, *t1 = f + 5 * MM, *t2 = f + 6 * MM, *t3 = f + 7 * MM;
-    auto df4 = [](double2 v) {
-        float4 r;
-        mixed::to_df(v.x, r.x, r.z);
-        mixed::to_df(v.y, r.y, r.w);
-        return r;
-    };
-    for (int q = threadIdx.x; q < MM; q += blockDim.x) {
-        const int i = q / M, j = q - i * M;
-        const double2 v = V[q], vd = cconj(V[(size_t)j * M + i]);
-        eps[q] = eps_s[q] = df4(H0[q]);
-        al[q] = df4(side == 0 ? v : vd);
-        be[q] = df4(side == 0 ? vd : v);
-    }
-    __syncthreads();
-    const float4 zf = df4(z);
-    int st = ST_NOCONVERGE;
-    for (it = 0; it < maxit; ++it) {
-        float na = 0.f, nb = 0.f;
-        for (int q = threadIdx.x; q < MM; q += blockDim.x) {
-            na = fmaxf(na, hypotf(al[q].x, al[q].y));
-            nb = fmaxf(nb, hypotf(be[q].x, be[q].y));
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            na = fmaxf(na, __shfl_xor_sync(0xffffffffu, na, o));
-            nb = fmaxf(nb, __shfl_xor_sync(0xffffffffu, nb, o));
-        }
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) {
-            red[threadIdx.x >> 5] = na;
-            red[16 + (threadIdx.x >> 5)] = nb;
-        }
-        __syncthreads();
-        double mna = 0.0, mnb = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-            mna = fmax(mna, red[q]);
-            mnb = fmax(mnb, red[16 + q]);
-        }
-        __syncthreads();
-        if (mna + mnb < tol) {
-            st = ST_OK;
-            break;
-        }
-        if (!isfinite(mna + mnb)) break;
-        // gb = (z - eps)^{-1}
-        for (int q = threadIdx.x; q < MM; q += blockDim.x) {
-            const int i = q / M, j = q - i * M;
-            const float4 x = eps[q];
-            float2 h = make_float2(-x.x, -x.y), l = make_float2(-x.z, -x.w);
-            if (i == j) mixed::cdf_add(h, l, make_float2(zf.x, zf.y), make_float2(zf.z, zf.w));
-            gb[q] = make_float4(h.x, h.y, l.x, l.y);
-        }
-        __syncthreads();
-        if (inverse_df(gb, M, sc, red) != ST_OK) {
-            st = ST_SINGULAR;
-            break;
-        }
-        gemm_df(gb, be, t1, M);    // gb beta
-        gemm_df(gb, al, t2, M);    // gb alpha
-        gemm_df(al, t1, t3, M);    // alpha gb beta
-        add_df(eps_s, t3, MM);
-        add_df(eps, t3, MM);
-        gemm_df(be, t2, t3, M);    // beta gb alpha
-        add_df(eps, t3, MM);
-        gemm_df(al, t2, t3, M);    // alpha gb alpha: the next alpha
-        gemm_df(be, t1, t2, M);    // beta gb beta: the next beta
-        for (int q = threadIdx.x; q < MM; q += blockDim.x) {
-            al[q] = t3[q];
-            be[q] = t2[q];
-        }
-        __syncthreads();
-    }
-    // eps_s to FP64 in place (same 16 bytes per entry, each thread its own)
-    for (int q = threadIdx.x; q < MM; q += blockDim.x) {
-        const float4 x = eps_s[q];
-        w[MM + q] = make_double2((double)x.x + (double)x.z, (double)x.y + (double)x.w);
-    }
-    __syncthreads();
-    return st;
-}
-
-// ---------------------------------------------------------------------------
 // Sancho-Rubio decimation, one CTA per energy (grid-stride).  side 0: alpha = V
 // (surface -> next cell outward), beta = V^dagger; side 1: the reverse.
 // work: per CTA 8 M*M complex.  Outputs Sigma, g, iterations, status.
 extern "C" __global__ void __launch_bounds__(256)
 knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int side, const double *E,
                        int nE, double eta, double tol, int maxit, double2 *work, double2 *sigma,
-                       double2 *gout, int *iters, int *status, int only_failed, int df)
+                       double2 *gout, int *iters, int *status, int only_failed)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GJScratch64 sc;
@@ -516,8 +260,6 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
         double eta_k = eta;
         for (int attempt = 0; attempt < DEC_ATTEMPTS; ++attempt, eta_k *= 100.0) {
         const double2 z = make_double2(E[e], eta_k);
-        if (df) st = doubling_df(H0, V, M, side, z, tol, maxit, w, sc, red, it);
-        if (!df) {
         for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
             int i = q / M, j = q - i * M;
             double2 v = V[q], vd = cconj(V[(size_t)j * M + i]);
@@ -577,7 +319,6 @@ knit_decimation_kernel(const double2 *H0, const double2 *V, int M, int vb, int s
                 be[q] = t2[q];
             }
             __syncthreads();
-        }
         }
         if (st == ST_OK) {
             for (int q = threadIdx.x; q < (int)MM; q += blockDim.x) {
@@ -746,21 +487,7 @@ extern "C" cudaError_t knit_launch_decimation(const double2 *H0, const double2 *
                                               int *status, int grid, cudaStream_t stream)
 {
     knit_decimation_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(
-        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status, 0, 0);
-    return cudaGetLastError();
-}
-
-// the same with the doubling steps in double-float (M <= 64); the converged
-// surface function and its acceptance tests in FP64 as above
-extern "C" cudaError_t knit_launch_decimation_df(const double2 *H0, const double2 *V, int M, int vb,
-                                                 int side, const double *E, int nE, double eta,
-                                                 double tol, int maxit, double2 *work,
-                                                 double2 *sigma, double2 *g, int *iters,
-                                                 int *status, int grid, cudaStream_t stream)
-{
-    if (M > 64) return cudaErrorInvalidValue;
-    knit_decimation_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(
-        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status, 0, 1);
+        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status, 0);
     return cudaGetLastError();
 }
 
@@ -774,7 +501,7 @@ extern "C" cudaError_t knit_launch_decimation_failed(const double2 *H0, const do
                                                      cudaStream_t stream)
 {
     knit_decimation_kernel<<<grid, 256, knit_gj_smem_bytes(M), stream>>>(
-        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status, 1, 0);
+        H0, V, M, vb, side, E, nE, eta, tol, maxit, work, sigma, g, iters, status, 1);
     return cudaGetLastError();
 }
 
