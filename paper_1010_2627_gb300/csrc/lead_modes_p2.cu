@@ -274,9 +274,12 @@ extern "C" cudaError_t knit_launch_small_decimation(const double2 *H0s, const do
 //   F(g) = A g - I,  A = E - H0 - Vl g Vr,  (Vl, Vr) = (V, V^dagger) on the
 //   left, (V^dagger, V) on the right; the step D solves A D - Vl D (Vr g) = -F,
 // a dense N^2 x N^2 system (vec of D row by row) by Gaussian elimination with
-// partial pivoting.  Converged when max |F_ij| < tol and the result is
-// retarded (-Im g_kk >= 0); otherwise status ST_NOCONVERGE (the caller then
-// decimates).  guess: float (re, im) pairs of cell c at guess + e * gstride
+// partial pivoting.  Accepted when max |F_ij| < tol, the result is retarded
+// (i(g - g^dagger) positive semidefinite, the test of the decimation) and it
+// lies within a tenth of the guess's size of the guess: the fixed-point
+// equation has other solutions (at a real energy in a gap they are real
+// too), and only a root near a good guess is taken to be the physical one;
+// otherwise status ST_NOCONVERGE (the caller then decimates).  guess: float (re, im) pairs of cell c at guess + e * gstride
 // + 2 N^2 c.
 template <int N>
 __global__ void __launch_bounds__(128)
@@ -291,7 +294,11 @@ knit_small_newton_kernel(const double2 *H0s, const double2 *Vs, int nsec, int si
     const double2 *H = H0s + (size_t)c * NN, *V = Vs + (size_t)c * NN;
     double2 g[NN], A[NN], B[NN], F[NN], J[NN * NN];
     const float *gs = guess + (size_t)e * gstride + 2 * NN * c;
-    for (int q = 0; q < NN; ++q) g[q] = make_double2((double)gs[2 * q], (double)gs[2 * q + 1]);
+    double gsz = 0.0;
+    for (int q = 0; q < NN; ++q) {
+        g[q] = make_double2((double)gs[2 * q], (double)gs[2 * q + 1]);
+        gsz = fmax(gsz, cabs1(g[q]));
+    }
     auto vl = [&](int i, int k) { return side == 0 ? V[i * N + k] : cconj(V[k * N + i]); };
     auto vr = [&](int i, int k) { return side == 0 ? cconj(V[k * N + i]) : V[i * N + k]; };
     const double En = E[e];
@@ -377,9 +384,20 @@ knit_small_newton_kernel(const double2 *H0s, const double2 *Vs, int nsec, int si
         }
         for (int q = 0; q < NN; ++q) g[q] = cadd(g[q], F[q]);
     }
-    if (st == ST_OK)
-        for (int k = 0; k < N; ++k)
-            if (g[k * N + k].y > 1e-12) st = ST_NOCONVERGE;
+    if (st == ST_OK) {
+        double moved = 0.0;
+        for (int q = 0; q < NN; ++q)
+            moved = fmax(moved, cabs1(csub(g[q], make_double2((double)gs[2 * q], (double)gs[2 * q + 1]))));
+        if (!(moved <= 0.1 * gsz)) st = ST_NOCONVERGE;
+    }
+    if (st == ST_OK) {
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                const double2 a = g[i * N + j], b = cconj(g[j * N + i]);
+                A[i * N + j] = make_double2(-(a.y - b.y), a.x - b.x);   // i (g - g^dagger)
+            }
+        if (!small_psd<N>(A)) st = ST_NOCONVERGE;
+    }
     double2 *G = gout + (size_t)t * NN;
     for (int q = 0; q < NN; ++q) G[q] = st == ST_OK ? g[q] : make_double2(nan(""), nan(""));
     if (iters) iters[t] = it;
