@@ -1502,6 +1502,7 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
         }
         const InstParams ip = inst_params(in, inst, M);
         int st = ip.st;
+        int dfrun = 0;   // consecutive slices that needed the double-float inversion
 
         for (int n = 0; n < L && st == ST_OK; ++n) {
             // ---- A
@@ -1514,6 +1515,16 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             const int vmode = vk != 0 ? 1 : (sm.vuni[q] == 1 ? 1 : (sm.vuni[q] == 2 ? 2 : 0));
             gv_elementwise(wk, sm, s, M, n, L, vmode, vk == 1 && n > 0, ip.SL, ip.SR);
             __syncthreads();
+            if (dfrun > 0 && (dfrun & 7) != 0) {
+                // the slice before needed the double-float inversion; this one,
+                // next to the same resonance, goes there directly (every eighth
+                // slice of such a run tries the complex64 path again)
+                st = fallback_df(wk, sm, M);
+                if (st != ST_OK) st = fallback64(wk, M);
+                ++dfrun;
+                __syncthreads();
+                continue;
+            }
             fence_after();
             x_to_tmem(wk, sm, tmem, M);
             fence_before();
@@ -1593,9 +1604,11 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                 // double-float Gauss-Jordan; FP64 if it meets an exact zero pivot
                 st = fallback_df(wk, sm, M);
                 if (st != ST_OK) st = fallback64(wk, M);
+                ++dfrun;
                 __syncthreads();
                 continue;
             }
+            dfrun = 0;
             const int nx = neumann_terms(rmax, M);
             const float2 *S = wk.R;
             for (int t = 0; t < nx && !timed_out; ++t) {
