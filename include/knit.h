@@ -78,8 +78,10 @@ enum {
                        65..128, and any width up to 128 with 4 x 4 block or
                        tridiagonal couplings, use a 512-thread tensor-core
                        variant (tcgen05, accumulators in tensor memory) with
-                       the state in device memory; M > 128 runs the
-                       KNIT_FP64 sweep instead. */
+                       the state in device memory.  Above 128, a system
+                       whose rows split into half-rows (knit_system_create)
+                       runs that variant on its half-row chain; any other
+                       M > 128 runs the KNIT_FP64 sweep instead. */
     KNIT_MIXED_CUDACORE = 2  /* KNIT_MIXED with the residual always accumulated
                                 in double-float arithmetic on CUDA cores
                                 (diagonal and 4 x 4 block couplings; other
