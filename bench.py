@@ -33,10 +33,12 @@ NE, NS = 1024, 8
 METRIC = "T(E) points/s (mixed sweep, |dT| <= 1e-6 vs FP64)"
 WORKLOAD = "square M=64 L=512 W=2, 1024 energies x 8 seeds, two clean leads"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu pass) of one
-# launch of the sweep kernel on exactly this workload, for the kernel as it
-# stands; set to None whenever the kernel changes until it is measured again
-SWEEP_TRAFFIC_BYTES = 69.85e6
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the sweep kernel on this workload, for the kernel as it stands: taken on the
+# 152-instance profile case (one kernel, one launch: 1.3914 MB) and scaled by
+# instances to 8192 (the traffic is per instance: parameters and self-energy
+# blocks); set to None whenever the kernel changes until it is measured again
+SWEEP_TRAFFIC_BYTES = 1.3914e6 * 8192 / 152
 L2_BYTES = 126 * 1024 * 1024
 
 
