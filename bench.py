@@ -617,19 +617,23 @@ def run_profile_case(args):
     """Small case for ncu captures: square lattice of width --profile-M
     (default 64), L = --profile-L (default 64), W = 2, 19 energies x 8 seeds
     (one wave of 152 instances), two mixed sweeps and one FP64 sweep (FP64
-    skipped above width 64, where it takes seconds)."""
+    skipped above width 64, where it takes seconds).  --profile-lattice
+    armchair: the graphene ribbon of the same row width and length instead
+    (t = 2.7, W = 1, 19 energies in (-2, 2)), above width 128 run by
+    half-rows."""
     import torch
     from paper_1010_2627_gb300 import build, inputs, knit
     build.build()
     knit.load()
     Lp, Mp = args.profile_L, args.profile_M
-    ss = inputs.square(Mp, Lp)
-    E = inputs.energy_grid(-3.9, 3.9, 19)
+    honeycomb = args.profile_lattice == "armchair"
+    ss = inputs.armchair(Mp, Lp) if honeycomb else inputs.square(Mp, Lp)
+    E = inputs.energy_grid(-2.0, 2.0, 19) if honeycomb else inputs.energy_grid(-3.9, 3.9, 19)
     seeds = np.arange(NS, dtype=np.uint64)
     sysk = knit.System(ss)
     runs = (knit.KNIT_MIXED, knit.KNIT_MIXED) + ((knit.KNIT_FP64,) if Mp <= 64 else ())
     for precision in runs:
-        T, st = sysk.transmission(E, seeds, W=W, precision=precision)
+        T, st = sysk.transmission(E, seeds, W=1.0 if honeycomb else W, precision=precision)
         assert (st == 0).all()
     torch.cuda.synchronize()
     print(json.dumps({"case": "profile", "M": Mp, "L": Lp, "instances": 19 * NS,
@@ -1228,6 +1232,8 @@ def main():
     ap.add_argument("--graphene-L", dest="graphene_L", type=int, default=1024)
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--profile-M", dest="profile_M", type=int, default=64)
+    ap.add_argument("--profile-lattice", dest="profile_lattice", default="square",
+                    choices=["square", "armchair"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
