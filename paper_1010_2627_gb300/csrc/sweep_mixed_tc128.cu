@@ -1320,14 +1320,35 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
             const int i = e >> 7, j = e & (MP - 1);
             if (i >= M || j >= M || i == k) continue;
             const float4 c = sm.u.fb.col[i], rw = sm.u.fb.row[j];
-            float2 h = j == k ? make_float2(0.f, 0.f) : ah[e];
-            float2 l = j == k ? make_float2(0.f, 0.f) : al[e];
-            float2 ph, pl;
-            cdf_mul(make_float2(c.x, c.y), make_float2(c.z, c.w), make_float2(rw.x, rw.y),
-                    make_float2(rw.z, rw.w), ph, pl);
-            cdf_add(h, l, make_float2(-ph.x, -ph.y), make_float2(-pl.x, -pl.y));
-            ah[e] = h;
-            al[e] = l;
+            const float2 h = j == k ? make_float2(0.f, 0.f) : ah[e];
+            const float2 l = j == k ? make_float2(0.f, 0.f) : al[e];
+            // a - c r in one compensated pass: the products of the hi parts
+            // exact (TwoProduct), the hi-lo cross terms in fp32, the sums
+            // compensated (TwoSum), normalised once per part
+            float p, pe, s1, t, er, ei;
+            p = c.x * rw.x;
+            pe = fmaf(c.x, rw.x, -p);
+            two_sum(h.x, -p, s1, t);
+            er = (l.x + t) - pe;
+            p = c.y * rw.y;
+            pe = fmaf(c.y, rw.y, -p);
+            two_sum(s1, p, s1, t);
+            er += t + pe;
+            er -= fmaf(c.x, rw.z, fmaf(c.z, rw.x, -fmaf(c.y, rw.w, c.w * rw.y)));
+            float2 oh, ol;
+            two_sum(s1, er, oh.x, ol.x);
+            p = c.x * rw.y;
+            pe = fmaf(c.x, rw.y, -p);
+            two_sum(h.y, -p, s1, t);
+            ei = (l.y + t) - pe;
+            p = c.y * rw.x;
+            pe = fmaf(c.y, rw.x, -p);
+            two_sum(s1, -p, s1, t);
+            ei += t - pe;
+            ei -= fmaf(c.x, rw.w, fmaf(c.z, rw.y, fmaf(c.y, rw.z, c.w * rw.x)));
+            two_sum(s1, ei, oh.y, ol.y);
+            ah[e] = oh;
+            al[e] = ol;
         }
         __syncthreads();
     }
