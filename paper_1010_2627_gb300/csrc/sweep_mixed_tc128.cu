@@ -1316,12 +1316,22 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
             sm.u.fb.row[j] = make_float4(h.x, h.y, l.x, l.y);
         }
         __syncthreads();
-        for (int e = tid; e < MP * MP; e += NTH) {
+        // eight elements per batch, their lo parts loaded first so that the
+        // workspace latency is paid once per batch, not once per element
+        constexpr int FB = 8;
+#pragma unroll 1
+        for (int e0 = tid; e0 < MP * MP; e0 += FB * NTH) {
+            float2 lb[FB];
+#pragma unroll
+            for (int b = 0; b < FB; ++b) lb[b] = al[e0 + b * NTH];
+#pragma unroll
+            for (int b = 0; b < FB; ++b) {
+            const int e = e0 + b * NTH;
             const int i = e >> 7, j = e & (MP - 1);
             if (i >= M || j >= M || i == k) continue;
             const float4 c = sm.u.fb.col[i], rw = sm.u.fb.row[j];
             const float2 h = j == k ? make_float2(0.f, 0.f) : ah[e];
-            const float2 l = j == k ? make_float2(0.f, 0.f) : al[e];
+            const float2 l = j == k ? make_float2(0.f, 0.f) : lb[b];
             // a - c r in one compensated pass: the products of the hi parts
             // exact (TwoProduct), the hi-lo cross terms in fp32, the sums
             // compensated (TwoSum), normalised once per part
@@ -1349,6 +1359,7 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
             two_sum(s1, ei, oh.y, ol.y);
             ah[e] = oh;
             al[e] = ol;
+            }
         }
         __syncthreads();
     }
