@@ -103,12 +103,14 @@ struct Tc128Smem {
             float2 vh[MP * 4], vl[MP * 4];             // row r: V[r][4 (r / 4) + b], b = 0 .. 3
         } va;
         struct {                                       // double-float inversion of a slice
-            float2 hi[MP * MP];                        // hi parts, row-major
-            float4 col[MP];                            // column k before the step
-            float4 row[MP];                            // row k after scaling
-            float4 inv;                                // 1 / pivot
+            float2 hi[MP * MP];                        // hi parts of X, row-major
+            float4 U[MP * 8];                          // u vectors of the panel, row i at 8 i
+            float4 V[8 * MP];                          // v vectors of the panel, step c at c MP
+            float4 prow[8];                            // the pivot row's panel entries
+            float4 rinv[8];                            // 1 / pivot of each step
             float key[4];                              // per warp: best pivot key and its row
             int idx[4];
+            int pinv[MP];                              // row of the inverse that column j is
         } fb;
     } u;
     double eps[MP];
@@ -1221,14 +1223,70 @@ __device__ int fallback64(Tc128Work &wk, int M)
     return ST_OK;
 }
 
-// near-singular A_n: this slice inverted by Gauss-Jordan with partial
-// pivoting in double-float on the CUDA cores (entries as (hi, lo) float
-// pairs, ~2^-47 relative per operation, several times the speed of the FP64
-// pipe's Gauss-Jordan at this width), from Gv' in the state.  The hi parts
-// live in shared memory, the lo parts in the workspace; rows are swapped in
-// place and the swaps undone on the columns at the end.
+// double-float complex values as float4 (hi.re, hi.im, lo.re, lo.im)
+__device__ __forceinline__ float4 df4_mul(float4 a, float4 b)
+{
+    float2 h, l;
+    cdf_mul(make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w), h,
+            l);
+    return make_float4(h.x, h.y, l.x, l.y);
+}
+
+// x - c r in one compensated pass: the products of the hi parts exact
+// (TwoProduct), the hi-lo cross terms in fp32, the sums compensated (TwoSum),
+// normalised once per part (~2^-46 relative to |x| + |c| |r|)
+__device__ __forceinline__ float4 df4_fms(float4 x, float4 c, float4 r)
+{
+    float p, pe, s1, t, er, ei;
+    p = c.x * r.x;
+    pe = fmaf(c.x, r.x, -p);
+    two_sum(x.x, -p, s1, t);
+    er = (x.z + t) - pe;
+    p = c.y * r.y;
+    pe = fmaf(c.y, r.y, -p);
+    two_sum(s1, p, s1, t);
+    er += t + pe;
+    er -= fmaf(c.x, r.z, fmaf(c.z, r.x, -fmaf(c.y, r.w, c.w * r.y)));
+    float4 o;
+    two_sum(s1, er, o.x, o.z);
+    p = c.x * r.y;
+    pe = fmaf(c.x, r.y, -p);
+    two_sum(x.y, -p, s1, t);
+    ei = (x.w + t) - pe;
+    p = c.y * r.x;
+    pe = fmaf(c.y, r.x, -p);
+    two_sum(s1, -p, s1, t);
+    ei += t - pe;
+    ei -= fmaf(c.x, r.w, fmaf(c.z, r.y, fmaf(c.y, r.z, c.w * r.x)));
+    two_sum(s1, ei, o.y, o.w);
+    return o;
+}
+
+// x + d for a real float d
+__device__ __forceinline__ float4 df4_add_real(float4 x, float d)
+{
+    float s1, t;
+    two_sum(x.x, d, s1, t);
+    t += x.z;
+    two_sum(s1, t, x.x, x.z);
+    return x;
+}
+
+// near-singular A_n: this slice inverted in double-float on the CUDA cores
+// (entries as (hi, lo) float pairs, ~2^-46 relative per operation), from
+// Gv' in the state.  The in-place Gauss-Jordan elimination with implicit
+// partial pivoting and deferred panel updates of the width-64 kernel
+// (gj_blocked in mixed_common.cuh), in double-float: per panel of 8 columns
+// four warps (one row per thread) take the pivot steps on the panel columns
+// in registers and keep u = column - e_p; one thread per column forms the v
+// vectors by forward substitution from the pivot rows at the start of the
+// panel; then every thread applies X -= U V to its elements.  With p_k the
+// pivot row of step k, the inverse is g[r][c] = X[p_r][q_c] for q the
+// inverse permutation.  X's hi parts live in shared memory, the lo parts in
+// the workspace.
 __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
 {
+    constexpr int NBK = 8;
     float2 *const ah = sm.u.fb.hi;                               // row-major MP x MP
     float2 *const al = reinterpret_cast<float2 *>(wk.A64);       // same layout
     const float2 *gh = reinterpret_cast<const float2 *>(wk.Gh);
@@ -1236,88 +1294,109 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int e = tid; e < MP * MP; e += NTH) {
         const int i = e >> 7, j = e & (MP - 1);
-        if (i >= M || j >= M) continue;
-        const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
-        ah[e] = make_float2(-gh[f].x, -gh[f].y);
-        al[e] = make_float2(-gl[f].x, -gl[f].y);
+        float2 h = make_float2(0.f, 0.f), l = h;
+        if (i < M && j < M) {
+            const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
+            h = make_float2(-gh[f].x, -gh[f].y);
+            l = make_float2(-gl[f].x, -gl[f].y);
+        }
+        ah[e] = h;
+        al[e] = l;
     }
+    if (tid == 0) sm.flag = 0;
     __syncthreads();
-    for (int k = 0; k < M; ++k) {
-        // pivot: the largest |Re| + |Im| of column k in rows k .. M - 1
-        if (warp < 4) {
-            const int i = 32 * warp + lane;
-            float v = -1.f;
-            if (i >= k && i < M) {
-                const float2 x = ah[i * MP + k];
-                v = fabsf(x.x) + fabsf(x.y);
-            }
-            int bi = i;
+    bool open = tid < M;   // threads 0 .. 127: row tid may still become a pivot row
+    for (int K = 0; K < M; K += NBK) {
+        const int nk = min(NBK, M - K);
+        // ---- the pivot steps on the panel columns, one row per thread
+        if (tid < MP) {
+            float4 pc[NBK];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > v || (ov == v && oi < bi)) {
-                    v = ov;
-                    bi = oi;
+            for (int c = 0; c < NBK; ++c) {
+                const int e = tid * MP + K + c;
+                pc[c] = K + c < M ? make_float4(ah[e].x, ah[e].y, al[e].x, al[e].y)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int kk = 0; kk < NBK; ++kk) {
+                if (kk < nk) {
+                    float v = open ? fabsf(pc[kk].x) + fabsf(pc[kk].y) : -1.f;
+                    int bi = tid;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                        if (ov > v || (ov == v && oi < bi)) {
+                            v = ov;
+                            bi = oi;
+                        }
+                    }
+                    if (lane == 0) {
+                        sm.u.fb.key[warp] = v;
+                        sm.u.fb.idx[warp] = bi;
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    float bv = sm.u.fb.key[0];
+                    int p = sm.u.fb.idx[0];
+#pragma unroll
+                    for (int w = 1; w < 4; ++w)
+                        if (sm.u.fb.key[w] > bv) {
+                            bv = sm.u.fb.key[w];
+                            p = sm.u.fb.idx[w];
+                        }
+                    const bool ok = bv > 0.f && isfinite(bv);
+                    if (!ok) p = 0;
+                    if (tid == p) {
+                        if (!ok) sm.flag = 1;
+                        sm.perm[K + kk] = p;
+#pragma unroll
+                        for (int c = 0; c < NBK; ++c) sm.u.fb.prow[c] = pc[c];
+                        const double pr = (double)pc[kk].x + (double)pc[kk].z;
+                        const double pi = (double)pc[kk].y + (double)pc[kk].w;
+                        const double d = 1.0 / (pr * pr + pi * pi);
+                        float4 ri;
+                        to_df(pr * d, ri.x, ri.z);
+                        to_df(-pi * d, ri.y, ri.w);
+                        sm.u.fb.rinv[kk] = ri;
+                    }
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    const float4 ri = sm.u.fb.rinv[kk];
+                    const float4 u = tid == p ? df4_add_real(pc[kk], -1.f) : pc[kk];
+                    sm.u.fb.U[tid * NBK + kk] = u;
+#pragma unroll
+                    for (int c = kk + 1; c < NBK; ++c)
+                        pc[c] = df4_fms(pc[c], u, df4_mul(sm.u.fb.prow[c], ri));
+                    open = open && tid != p;
+                } else {
+                    sm.u.fb.U[tid * NBK + kk] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
-            if (lane == 0) {
-                sm.u.fb.key[warp] = v;
-                sm.u.fb.idx[warp] = bi;
-            }
         }
         __syncthreads();
-        if (tid == 0) {
-            float v = sm.u.fb.key[0];
-            int r = sm.u.fb.idx[0];
-            for (int w = 1; w < 4; ++w)
-                if (sm.u.fb.key[w] > v) {
-                    v = sm.u.fb.key[w];
-                    r = sm.u.fb.idx[w];
+        if (sm.flag) return ST_SINGULAR;
+        // ---- v vectors: one thread per column j, forward substitution from the
+        // pivot rows of X at the start of the panel
+        if (tid < MP) {
+            const int j = tid;
+            float4 v[NBK];
+#pragma unroll
+            for (int kk = 0; kk < NBK; ++kk) {
+                v[kk] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (kk < nk && j < M) {
+                    const int p = sm.perm[K + kk];
+                    float4 r = make_float4(ah[p * MP + j].x, ah[p * MP + j].y, al[p * MP + j].x,
+                                           al[p * MP + j].y);
+                    if (j == K + kk) r = df4_add_real(r, 1.f);
+#pragma unroll
+                    for (int c = 0; c < kk; ++c) r = df4_fms(r, sm.u.fb.U[p * NBK + c], v[c]);
+                    v[kk] = df4_mul(r, sm.u.fb.rinv[kk]);
                 }
-            sm.perm[k] = r;
-            sm.flag = (v > 0.f && isfinite(v)) ? r : -1;
-        }
-        __syncthreads();
-        const int r = sm.flag;
-        if (r < 0) return ST_SINGULAR;
-        if (r != k)
-            for (int j = tid; j < M; j += NTH) {
-                float2 t = ah[k * MP + j];
-                ah[k * MP + j] = ah[r * MP + j];
-                ah[r * MP + j] = t;
-                t = al[k * MP + j];
-                al[k * MP + j] = al[r * MP + j];
-                al[r * MP + j] = t;
             }
-        __syncthreads();
-        for (int i = tid; i < M; i += NTH) {
-            const float2 h = ah[i * MP + k], l = al[i * MP + k];
-            sm.u.fb.col[i] = make_float4(h.x, h.y, l.x, l.y);
+#pragma unroll
+            for (int kk = 0; kk < NBK; ++kk) sm.u.fb.V[kk * MP + j] = v[kk];
         }
         __syncthreads();
-        if (tid == 0) {
-            const float4 pv = sm.u.fb.col[k];
-            const double pr = (double)pv.x + (double)pv.z, pi = (double)pv.y + (double)pv.w;
-            const double d = 1.0 / (pr * pr + pi * pi);
-            float4 inv;
-            to_df(pr * d, inv.x, inv.z);
-            to_df(-pi * d, inv.y, inv.w);
-            sm.u.fb.inv = inv;
-        }
-        __syncthreads();
-        const float4 inv = sm.u.fb.inv;
-        for (int j = tid; j < M; j += NTH) {
-            float2 h = j == k ? make_float2(1.f, 0.f) : ah[k * MP + j];
-            float2 l = j == k ? make_float2(0.f, 0.f) : al[k * MP + j];
-            cdf_mul(h, l, make_float2(inv.x, inv.y), make_float2(inv.z, inv.w), h, l);
-            ah[k * MP + j] = h;
-            al[k * MP + j] = l;
-            sm.u.fb.row[j] = make_float4(h.x, h.y, l.x, l.y);
-        }
-        __syncthreads();
-        // eight elements per batch, their lo parts loaded first so that the
-        // workspace latency is paid once per batch, not once per element
+        // ---- X -= U V over the whole matrix (lo parts loaded eight at a time)
         constexpr int FB = 8;
 #pragma unroll 1
         for (int e0 = tid; e0 < MP * MP; e0 += FB * NTH) {
@@ -1326,67 +1405,33 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
             for (int b = 0; b < FB; ++b) lb[b] = al[e0 + b * NTH];
 #pragma unroll
             for (int b = 0; b < FB; ++b) {
-            const int e = e0 + b * NTH;
-            const int i = e >> 7, j = e & (MP - 1);
-            if (i >= M || j >= M || i == k) continue;
-            const float4 c = sm.u.fb.col[i], rw = sm.u.fb.row[j];
-            const float2 h = j == k ? make_float2(0.f, 0.f) : ah[e];
-            const float2 l = j == k ? make_float2(0.f, 0.f) : lb[b];
-            // a - c r in one compensated pass: the products of the hi parts
-            // exact (TwoProduct), the hi-lo cross terms in fp32, the sums
-            // compensated (TwoSum), normalised once per part
-            float p, pe, s1, t, er, ei;
-            p = c.x * rw.x;
-            pe = fmaf(c.x, rw.x, -p);
-            two_sum(h.x, -p, s1, t);
-            er = (l.x + t) - pe;
-            p = c.y * rw.y;
-            pe = fmaf(c.y, rw.y, -p);
-            two_sum(s1, p, s1, t);
-            er += t + pe;
-            er -= fmaf(c.x, rw.z, fmaf(c.z, rw.x, -fmaf(c.y, rw.w, c.w * rw.y)));
-            float2 oh, ol;
-            two_sum(s1, er, oh.x, ol.x);
-            p = c.x * rw.y;
-            pe = fmaf(c.x, rw.y, -p);
-            two_sum(h.y, -p, s1, t);
-            ei = (l.y + t) - pe;
-            p = c.y * rw.x;
-            pe = fmaf(c.y, rw.x, -p);
-            two_sum(s1, -p, s1, t);
-            ei += t - pe;
-            ei -= fmaf(c.x, rw.w, fmaf(c.z, rw.y, fmaf(c.y, rw.z, c.w * rw.x)));
-            two_sum(s1, ei, oh.y, ol.y);
-            ah[e] = oh;
-            al[e] = ol;
+                const int e = e0 + b * NTH, i = e >> 7, j = e & (MP - 1);
+                float4 x = make_float4(ah[e].x, ah[e].y, lb[b].x, lb[b].y);
+#pragma unroll
+                for (int c = 0; c < NBK; ++c)
+                    if (c < nk) x = df4_fms(x, sm.u.fb.U[i * NBK + c], sm.u.fb.V[c * MP + j]);
+                if (i < M && j < M) {
+                    ah[e] = make_float2(x.x, x.y);
+                    al[e] = make_float2(x.z, x.w);
+                }
             }
         }
         __syncthreads();
     }
-    // the row swaps, undone on the columns in reverse order
-    for (int k = M - 1; k >= 0; --k) {
-        const int r = sm.perm[k];
-        if (r != k)
-            for (int i = tid; i < M; i += NTH) {
-                float2 t = ah[i * MP + k];
-                ah[i * MP + k] = ah[i * MP + r];
-                ah[i * MP + r] = t;
-                t = al[i * MP + k];
-                al[i * MP + k] = al[i * MP + r];
-                al[i * MP + r] = t;
-            }
-        __syncthreads();
-    }
+    // g[r][c] = X[p_r][q_c], q the inverse of the pivot permutation
+    for (int j = tid; j < M; j += NTH) sm.u.fb.pinv[sm.perm[j]] = j;
+    __syncthreads();
     float2 *const oh = reinterpret_cast<float2 *>(wk.Gh);
     float2 *const ol = reinterpret_cast<float2 *>(wk.Gl);
     for (int e = tid; e < MP * MP; e += NTH) {
-        const int i = e & (MP - 1), j = e >> 7;
-        const int f = ((j >> 1) * MP + i) * 2 + (j & 1);
-        if (i < M && j < M) {
-            oh[f] = ah[i * MP + j];
-            ol[f] = al[i * MP + j];
+        const int r = e & (MP - 1), c = e >> 7;
+        const int f = ((c >> 1) * MP + r) * 2 + (c & 1);
+        if (r < M && c < M) {
+            const int src = sm.perm[r] * MP + sm.u.fb.pinv[c];
+            oh[f] = ah[src];
+            ol[f] = al[src];
         } else {
-            oh[f] = make_float2(i == j ? 1.f : 0.f, 0.f);
+            oh[f] = make_float2(r == c ? 1.f : 0.f, 0.f);
             ol[f] = make_float2(0.f, 0.f);
         }
     }
