@@ -111,10 +111,6 @@ struct Tc128Smem {
             float key[4];                              // per warp: best pivot key and its row
             int idx[4];
             int pinv[MP];                              // row of the inverse that column j is
-            int uexp[MP];                              // exponent of row i of U (real form)
-            int vexp[32];                              // exponent of the pass's columns of V
-            alignas(128) unsigned char ad[6 * A_TILE]; // digits of U in real form, 128 x 16
-            alignas(128) unsigned char bd[6 * 32 * 32]; // digits of 32 real columns of V, 6 x 32 x 16
         } fb;
     } u;
     double eps[MP];
@@ -1288,7 +1284,7 @@ __device__ __forceinline__ float4 df4_add_real(float4 x, float d)
 // pivot row of step k, the inverse is g[r][c] = X[p_r][q_c] for q the
 // inverse permutation.  X's hi parts live in shared memory, the lo parts in
 // the workspace.
-__device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M, uint32_t tmem, Bars &br)
+__device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M)
 {
     constexpr int NBK = 8;
     float2 *const ah = sm.u.fb.hi;                               // row-major MP x MP
@@ -1400,125 +1396,27 @@ __device__ __noinline__ int fallback_df(Tc128Work &wk, Tc128Smem &sm, int M, uin
             for (int kk = 0; kk < NBK; ++kk) sm.u.fb.V[kk * MP + j] = v[kk];
         }
         __syncthreads();
-        // ---- X -= U V on the tensor cores.  In real form, D = U V is the
-        // 128 x 256 product of A (row i: Re U[i][0..7], Im U[i][0..7]) and B
-        // (column 2j: Re V[., j], -Im V[., j]; column 2j + 1: Im V[., j],
-        // Re V[., j]).  Every row of A and column of B is cut into six bf16
-        // digits of 8 bits below its own exponent (integers of at most 128
-        // in magnitude), so a digit product summed over K = 16 is an exact
-        // integer in fp32; digit t of A against digits s = 0 .. 5 - t of B
-        // side by side lands in accumulator d = t + s (six accumulators, the
-        // first MMA initialising all of them), and D = 2^(e_i + f_n) sum_d
-        // acc_d 2^-8(d + 2) is put together in double-float: products below
-        // 2^-48 of the largest are left out.  Eight passes of 32 real columns.
-        if (tid < MP) {
-            float m = 0.f;
+        // ---- X -= U V over the whole matrix (lo parts loaded eight at a time)
+        constexpr int FB = 8;
+#pragma unroll 1
+        for (int e0 = tid; e0 < MP * MP; e0 += FB * NTH) {
+            float2 lb[FB];
 #pragma unroll
-            for (int c = 0; c < NBK; ++c) {
-                const float4 u = sm.u.fb.U[tid * NBK + c];
-                m = fmaxf(m, fmaxf(fabsf(u.x), fabsf(u.y)));
+            for (int b = 0; b < FB; ++b) lb[b] = al[e0 + b * NTH];
+#pragma unroll
+            for (int b = 0; b < FB; ++b) {
+                const int e = e0 + b * NTH, i = e >> 7, j = e & (MP - 1);
+                float4 x = make_float4(ah[e].x, ah[e].y, lb[b].x, lb[b].y);
+#pragma unroll
+                for (int c = 0; c < NBK; ++c)
+                    if (c < nk) x = df4_fms(x, sm.u.fb.U[i * NBK + c], sm.u.fb.V[c * MP + j]);
+                if (i < M && j < M) {
+                    ah[e] = make_float2(x.x, x.y);
+                    al[e] = make_float2(x.z, x.w);
+                }
             }
-            sm.u.fb.uexp[tid] = scale_exp(m) + 1;
         }
         __syncthreads();
-        for (int q = tid; q < MP * 16; q += NTH) {
-            const int i = q >> 4, k = q & 15;
-            const float4 u = sm.u.fb.U[i * NBK + (k & 7)];
-            const int e = sm.u.fb.uexp[i];
-            float yh = ldexpf(k < 8 ? u.x : u.y, -e), yl = ldexpf(k < 8 ? u.z : u.w, -e);
-#pragma unroll
-            for (int t = 0; t < 6; ++t) {
-                yh *= 256.f;
-                yl *= 256.f;
-                const float d = rintf(yh);
-                yh -= d;
-                two_sum(yh, yl, yh, yl);
-                *reinterpret_cast<__nv_bfloat16 *>(sm.u.fb.ad + t * A_TILE + tile_off(i, k)) =
-                    __float2bfloat16_rn(d);
-            }
-        }
-        for (int pass = 0; pass < 8; ++pass) {
-            // B digits of real columns n = 32 pass + nl: thread (nl, k)
-            if (tid < 32 * 16) {
-                const int nl = tid >> 4, k = tid & 15, n = 32 * pass + nl, j = n >> 1;
-                const float4 v = sm.u.fb.V[(k & 7) * MP + j];
-                float bh, bl;
-                if ((n & 1) == 0) {
-                    bh = k < 8 ? v.x : -v.y;
-                    bl = k < 8 ? v.z : -v.w;
-                } else {
-                    bh = k < 8 ? v.y : v.x;
-                    bl = k < 8 ? v.w : v.z;
-                }
-                float m = fabsf(bh);
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                const int f = scale_exp(m) + 1;
-                if (k == 0) sm.u.fb.vexp[nl] = f;
-                float yh = ldexpf(bh, -f), yl = ldexpf(bl, -f);
-#pragma unroll
-                for (int t = 0; t < 6; ++t) {
-                    yh *= 256.f;
-                    yl *= 256.f;
-                    const float d = rintf(yh);
-                    yh -= d;
-                    two_sum(yh, yl, yh, yl);
-                    *reinterpret_cast<__nv_bfloat16 *>(sm.u.fb.bd + tile_off(32 * t + nl, k)) =
-                        __float2bfloat16_rn(d);
-                }
-            }
-            async_proxy_fence();
-            fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                fence_after();
-#pragma unroll
-                for (int t = 0; t < 6; ++t)
-                    mma_bf16(tmem + 32 * t, smem_desc(smem_u32(sm.u.fb.ad + t * A_TILE)),
-                             smem_desc(smem_u32(sm.u.fb.bd)), idesc_bf16_m128(32 * (6 - t)),
-                             t ? 1u : 0u);
-                mma_commit(&sm.bar[0]);
-            }
-            br.pend[0] = 1u;
-            if (!bar_wait(sm, br, 0)) return ST_TIMEOUT;
-            fence_after();
-            {
-                // warp w: rows 32 (w & 3) + lane, real columns 8 (w >> 2) .. + 7
-                const int qd = warp & 3, g = warp >> 2, i = 32 * qd + lane;
-                const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + 8 * g;
-                uint32_t acc[6][8];
-#pragma unroll
-                for (int d = 0; d < 6; ++d) tmem_ld8(ta + 32 * d, acc[d]);
-                wait_ld();
-                const int e = sm.u.fb.uexp[i];
-#pragma unroll
-                for (int c = 0; c < 8; c += 2) {
-                    const int nl = 8 * g + c, j = (32 * pass + nl) >> 1;
-                    float dh[2], dl[2];
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        const int sc = e + sm.u.fb.vexp[nl + r] - 16;
-                        float h = 0.f, l = 0.f;
-#pragma unroll
-                        for (int d = 5; d >= 0; --d) {
-                            const float term = ldexpf(__uint_as_float(acc[d][c + r]), sc - 8 * d);
-                            float t2;
-                            two_sum(h, term, h, t2);
-                            l += t2;
-                        }
-                        two_sum(h, l, dh[r], dl[r]);
-                    }
-                    if (i < M && j < M) {
-                        float2 h = ah[i * MP + j], l = al[i * MP + j];
-                        cdf_add(h, l, make_float2(-dh[0], -dh[1]), make_float2(-dl[0], -dl[1]));
-                        ah[i * MP + j] = h;
-                        al[i * MP + j] = l;
-                    }
-                }
-            }
-            fence_before();
-            __syncthreads();
-        }
     }
     // g[r][c] = X[p_r][q_c], q the inverse of the pivot permutation
     for (int j = tid; j < M; j += NTH) sm.u.fb.pinv[sm.perm[j]] = j;
@@ -1698,11 +1596,7 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
                 // the slice before needed the double-float inversion; this one,
                 // next to the same resonance, goes there directly (every eighth
                 // slice of such a run tries the complex64 path again)
-                st = fallback_df(wk, sm, M, tmem, br);
-                if (st == ST_TIMEOUT) {
-                    timed_out = true;
-                    break;
-                }
+                st = fallback_df(wk, sm, M);
                 if (st != ST_OK) st = fallback64(wk, M);
                 ++dfrun;
                 __syncthreads();
@@ -1785,11 +1679,7 @@ knit_sweep_mixed_tc128_kernel(InstDev in, Tc128Work *work)
             const float rmax = block_max_nonneg<NTH>(rloc, sm.redu);
             if (refinement_fails(rmax, M)) {
                 // double-float Gauss-Jordan; FP64 if it meets an exact zero pivot
-                st = fallback_df(wk, sm, M, tmem, br);
-                if (st == ST_TIMEOUT) {
-                    timed_out = true;
-                    break;
-                }
+                st = fallback_df(wk, sm, M);
                 if (st != ST_OK) st = fallback64(wk, M);
                 ++dfrun;
                 __syncthreads();
