@@ -47,6 +47,9 @@ extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cuda
 extern "C" cudaError_t knit_launch_small_decimation(const double2 *, const double2 *, int, int, int,
                                                     const double *, int, double, double, int,
                                                     double2 *, int *, int *, int, cudaStream_t);
+extern "C" cudaError_t knit_launch_sector_ph(const double2 *, const int *, int, int, double2 *, cudaStream_t);
+extern "C" cudaError_t knit_launch_sector_ph_status(const int *, const int *, const int *, int, int *, int *,
+                                                    cudaStream_t);
 extern "C" cudaError_t knit_launch_small_newton(const double2 *, const double2 *, int, int, int,
                                                 const double *, int, const float *, long, double, int,
                                                 double2 *, int *, int *, cudaStream_t);
@@ -199,6 +202,10 @@ struct Lead {
     double2 *Cq = nullptr;
     int *nzr = nullptr;
     int nnz = 0;
+    // two sectors, the second the particle-hole image of the first:
+    // X1 = -S conj(X0) S^dagger for H0 and V, S = 1 (x) i sigma_y on
+    // consecutive orbital pairs, so that g1(E) = -S conj(g0(-E)) S^dagger
+    int ph = 0;
 };
 
 // Split a lead cell into the connected components of the orbital graph with
@@ -250,6 +257,26 @@ void lead_sectors(Lead &ld, int M, std::vector<double2> &bH0, std::vector<double
             }
         }
     }
+    // the Nambu structure of a normal BdG lead (Sec. 6.2; basis c_up, c_dn,
+    // c_dn^+, -c_up^+): the hole sector is the particle-hole image of the
+    // electron sector, X1[a][b] = -(-1)^(a + b) conj(X0[a ^ 1][b ^ 1])
+    ld.ph = 0;
+    if (comp.size() == 2 && ms % 2 == 0) {
+        double scale = 0.0;
+        for (size_t q = 0; q < ms * ms; ++q)
+            scale = std::max({scale, std::fabs(bH0[q].x) + std::fabs(bH0[q].y), std::fabs(bV[q].x) + std::fabs(bV[q].y)});
+        bool ok = true;
+        for (size_t a = 0; a < ms && ok; ++a)
+            for (size_t b = 0; b < ms && ok; ++b) {
+                const double sg = ((a + b) & 1) ? 1.0 : -1.0;
+                for (int w = 0; w < 2 && ok; ++w) {
+                    const std::vector<double2> &X = w ? bV : bH0;
+                    const double2 x0 = X[(a ^ 1) * ms + (b ^ 1)], x1 = X[(ms + a) * ms + b];
+                    ok = std::fabs(x1.x - sg * x0.x) + std::fabs(x1.y + sg * x0.y) <= 1e-13 * std::max(scale, 1e-300);
+                }
+            }
+        ld.ph = ok ? 1 : 0;
+    }
 }
 
 }  // namespace
@@ -277,6 +304,7 @@ struct knit_system_s {
     DevBuf E, seeds, T, status, queue, sigL, sigR, gL, gR, lst, lit, lres, work, ckpt, decw, ldos;
     DevBuf p2g, p2s, p2t;   // period-2 leads: supercell g and Sigma, block-product scratch
     DevBuf secs, secg, secst, secit;   // sector leads: per-sector Sigma, g, status, iterations
+    DevBuf phE, phmap, phs, phg, phst, phit;   // particle-hole sector pairs: energies, map, first sector
     DevBuf gll, tw, ts, tg, trk, tau, noise;   // transmission eigenvalues: G_LL, scratch, W, rank, out
     DevBuf lrl, lrr, ljx, ljt;                 // lesser function outputs staged for host pointers
 
@@ -929,6 +957,53 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
         CK(s->secg.ensure(sizeof(double2) * mm * nE * ns), "sector g");
         CK(s->secst.ensure(sizeof(int) * (size_t)nE * ns), "sector status");
         CK(s->secit.ensure(sizeof(int) * (size_t)nE * ns), "sector iterations");
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(st, &cap), "capture status");
+        if (ld.ph && cap == cudaStreamCaptureStatusNone) {
+            // particle-hole pair: the electron sector at E and at -E (energies
+            // of the list reused where -E is in it, to 1e-12), the hole sector
+            // from it; halves the work on a grid symmetric about zero
+            std::vector<double> hE(nE);
+            CK(cudaMemcpyAsync(hE.data(), dE, sizeof(double) * nE, cudaMemcpyDeviceToHost, st), "energies");
+            CK(cudaStreamSynchronize(st), "energies");
+            std::vector<int> order(nE), map(nE);
+            for (int e = 0; e < nE; ++e) order[e] = e;
+            std::sort(order.begin(), order.end(), [&](int a, int b) { return hE[a] < hE[b]; });
+            std::vector<double> ext(hE);
+            for (int e = 0; e < nE; ++e) {
+                const double t = -hE[e], tol = 1e-12 * std::max(1.0, std::fabs(t));
+                auto it = std::lower_bound(order.begin(), order.end(), t - tol,
+                                           [&](int a, double v) { return hE[a] < v; });
+                if (it != order.end() && std::fabs(hE[*it] - t) <= tol) {
+                    map[e] = *it;
+                } else {
+                    map[e] = (int)ext.size();
+                    ext.push_back(t);
+                }
+            }
+            const int nX = (int)ext.size();
+            CK(s->phE.ensure(sizeof(double) * nX), "particle-hole energies");
+            CK(s->phmap.ensure(sizeof(int) * nE), "particle-hole map");
+            CK(s->phs.ensure(sizeof(double2) * mm * nX), "particle-hole sector");
+            CK(s->phg.ensure(sizeof(double2) * mm * nX), "particle-hole sector");
+            CK(s->phst.ensure(sizeof(int) * nX), "particle-hole sector");
+            CK(s->phit.ensure(sizeof(int) * nX), "particle-hole sector");
+            CK(cudaMemcpy(s->phE.p, ext.data(), sizeof(double) * nX, cudaMemcpyHostToDevice), "energies");
+            CK(cudaMemcpy(s->phmap.p, map.data(), sizeof(int) * nE, cudaMemcpyHostToDevice), "map");
+            const int gx = std::min(nX, s->nsm * 4);
+            CK(s->decw.ensure(sizeof(double2) * 8 * mm * gx), "decimation workspace");
+            CK(knit_launch_decimation(ld.sH0, ld.sV, ms, ms, p, s->phE.as<double>(), nX, eta, tol, maxit,
+                                      s->decw.as<double2>(), s->phs.as<double2>(), s->phg.as<double2>(),
+                                      s->phit.as<int>(), s->phst.as<int>(), gx, st),
+               "sector decimation");
+            CK(knit_launch_sector_ph(s->phs.as<double2>(), s->phmap.as<int>(), ms, nE, s->secs.as<double2>(), st),
+               "particle-hole sector");
+            CK(knit_launch_sector_ph(s->phg.as<double2>(), s->phmap.as<int>(), ms, nE, s->secg.as<double2>(), st),
+               "particle-hole sector");
+            CK(knit_launch_sector_ph_status(s->phst.as<int>(), s->phit.as<int>(), s->phmap.as<int>(), nE,
+                                            s->secst.as<int>(), s->secit.as<int>(), st),
+               "particle-hole sector");
+        } else
         for (int q = 0; q < ns; ++q)
             CK(knit_launch_decimation(ld.sH0 + q * mm, ld.sV + q * mm, ms, ms, p, dE, nE, eta, tol,
                                       maxit, s->decw.as<double2>(),
@@ -1480,7 +1555,8 @@ knit_status knit_system_destroy(knit_system s)
                       &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
                       &s->p2g, &s->p2s, &s->p2t, &s->gll, &s->tw, &s->ts, &s->tg, &s->trk,
                       &s->tau, &s->noise, &s->lrl, &s->lrr, &s->ljx, &s->ljt, &s->secs,
-                      &s->secg, &s->secst, &s->secit};
+                      &s->secg, &s->secst, &s->secit, &s->phE, &s->phmap, &s->phs, &s->phg,
+                      &s->phst, &s->phit};
     for (DevBuf *b : bufs) b->release();
     delete s;
     return KNIT_OK;

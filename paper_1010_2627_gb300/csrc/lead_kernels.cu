@@ -609,6 +609,52 @@ __global__ void sector_status_kernel(const int *st, const int *it, int nsec, int
     if (it_out) it_out[e] = i0;
 }
 
+// a particle-hole pair of sectors from the first sector alone: src holds the
+// first sector at nE + nX energies (the caller's nE first, then the extra
+// energies -E that the list lacks), map[e] the index of -E_e there; out gets
+// both sectors at the caller's energies, block 0 = src[e], block 1 =
+// -S conj(src[map[e]]) S^dagger, S = 1 (x) i sigma_y on orbital pairs:
+// X1[a][b] = -(-1)^(a + b) conj(X0[a ^ 1][b ^ 1])
+__global__ void sector_ph_kernel(const double2 *src, const int *map, int ms, int nE, double2 *out)
+{
+    const size_t mm = (size_t)ms * ms, total = (size_t)nE * mm;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(q / mm), ab = (int)(q - (size_t)e * mm), a = ab / ms, b = ab - a * ms;
+        out[q] = src[q];
+        const double2 x = src[(size_t)map[e] * mm + (size_t)(a ^ 1) * ms + (b ^ 1)];
+        const double sg = ((a + b) & 1) ? 1.0 : -1.0;
+        out[total + q] = make_double2(sg * x.x, -sg * x.y);
+    }
+}
+
+__global__ void sector_ph_status_kernel(const int *st, const int *it, const int *map, int nE, int *st_out,
+                                        int *it_out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    st_out[e] = st[e];
+    it_out[e] = it[e];
+    st_out[nE + e] = st[map[e]];
+    it_out[nE + e] = it[map[e]];
+}
+
+extern "C" cudaError_t knit_launch_sector_ph(const double2 *src, const int *map, int ms, int nE,
+                                             double2 *out, cudaStream_t stream)
+{
+    const size_t total = (size_t)nE * ms * ms;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, 65535);
+    sector_ph_kernel<<<grid, 256, 0, stream>>>(src, map, ms, nE, out);
+    return cudaGetLastError();
+}
+
+extern "C" cudaError_t knit_launch_sector_ph_status(const int *st, const int *it, const int *map, int nE,
+                                                    int *st_out, int *it_out, cudaStream_t stream)
+{
+    sector_ph_status_kernel<<<(nE + 255) / 256, 256, 0, stream>>>(st, it, map, nE, st_out, it_out);
+    return cudaGetLastError();
+}
+
 extern "C" cudaError_t knit_launch_sector_assemble(const double2 *blk, const int *idx, int nsec,
                                                    int ms, int M, int nE, double2 *out,
                                                    cudaStream_t stream)
