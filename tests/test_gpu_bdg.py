@@ -111,3 +111,27 @@ def test_bdg_lead_sectors_against_oracle(knit, Ns, lead_delta):
             assert np.abs(S[e] - So).max() < 1e-8, (Ns, lead_delta, lead, Ee)
             assert res[e] < 1e-5
     sysk.close()
+
+
+def test_bdg_lead_particle_hole_pairs_symmetric_grid(knit):
+    """Normal Nambu leads: the hole sector is the particle-hole image of the
+    electron sector, so on a grid symmetric about zero every hole block comes
+    from the electron block at -E of the same list; both against the
+    oracle's decimation of the whole cell (1e-8), and the end-to-end T with
+    the mirror symmetry T(E) = T(-E) of a bar without disorder"""
+    b = inputs.bdg(6, 4, mu=-1.0, delta=0.1, alpha=0.2)
+    E = inputs.energy_grid(-0.16, 0.16, 6)
+    assert np.array_equal(E, -E[::-1]) or np.abs(E + E[::-1]).max() < 1e-15
+    sysk = knit.System(b)
+    assert sysk.info()[1] == [2, 2]
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION, eta=1e-12,
+                                          want_residual=True)
+        for e, Ee in enumerate(E):
+            So = oracle.decimation(b.lead_H0[lead], b.lead_V[lead], Ee, lead, eta=1e-12)[1]
+            assert np.abs(S[e] - So).max() < 1e-8, (lead, Ee)
+            assert res[e] < 1e-5
+    T, st = sysk.transmission(E, precision=knit.KNIT_FP64)
+    sysk.close()
+    assert (st == 0).all()
+    assert np.abs(T[:, 0] - T[::-1, 0]).max() < 1e-8
