@@ -1223,55 +1223,6 @@ __device__ int fallback64(Tc128Work &wk, int M)
     return ST_OK;
 }
 
-// double-float complex values as float4 (hi.re, hi.im, lo.re, lo.im)
-__device__ __forceinline__ float4 df4_mul(float4 a, float4 b)
-{
-    float2 h, l;
-    cdf_mul(make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w), h,
-            l);
-    return make_float4(h.x, h.y, l.x, l.y);
-}
-
-// x - c r in one compensated pass: the products of the hi parts exact
-// (TwoProduct), the hi-lo cross terms in fp32, the sums compensated (TwoSum),
-// normalised once per part (~2^-46 relative to |x| + |c| |r|)
-__device__ __forceinline__ float4 df4_fms(float4 x, float4 c, float4 r)
-{
-    float p, pe, s1, t, er, ei;
-    p = c.x * r.x;
-    pe = fmaf(c.x, r.x, -p);
-    two_sum(x.x, -p, s1, t);
-    er = (x.z + t) - pe;
-    p = c.y * r.y;
-    pe = fmaf(c.y, r.y, -p);
-    two_sum(s1, p, s1, t);
-    er += t + pe;
-    er -= fmaf(c.x, r.z, fmaf(c.z, r.x, -fmaf(c.y, r.w, c.w * r.y)));
-    float4 o;
-    two_sum(s1, er, o.x, o.z);
-    p = c.x * r.y;
-    pe = fmaf(c.x, r.y, -p);
-    two_sum(x.y, -p, s1, t);
-    ei = (x.w + t) - pe;
-    p = c.y * r.x;
-    pe = fmaf(c.y, r.x, -p);
-    two_sum(s1, -p, s1, t);
-    ei += t - pe;
-    ei -= fmaf(c.x, r.w, fmaf(c.z, r.y, fmaf(c.y, r.z, c.w * r.x)));
-    two_sum(s1, ei, o.y, o.w);
-    return o;
-}
-
-// x + d for a real float d
-__device__ __forceinline__ float4 df4_add_real(float4 x, float d)
-{
-    float s1, t;
-    two_sum(x.x, d, s1, t);
-    t += x.z;
-    two_sum(s1, t, x.x, x.z);
-    return x;
-}
-
 // near-singular A_n: this slice inverted in double-float on the CUDA cores
 // (entries as (hi, lo) float pairs, ~2^-46 relative per operation), from
 // Gv' in the state.  The in-place Gauss-Jordan elimination with implicit
