@@ -38,7 +38,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 152-instance profile case (one kernel, one launch: 1.3914 MB) and scaled by
 # instances to 8192 (the traffic is per instance: parameters and self-energy
 # blocks); set to None whenever the kernel changes until it is measured again
-SWEEP_TRAFFIC_BYTES = 1.3914e6 * 8192 / 152
+SWEEP_TRAFFIC_BYTES = None
 L2_BYTES = 126 * 1024 * 1024
 
 
