@@ -1034,6 +1034,66 @@ __device__ double ward_T(const float2 *Gh, const float2 *Gl, double2 *G, const d
     return block_sum(t, red);
 }
 
+// ward_T in double-float on the CUDA cores: its two M^3 complex products in
+// FP64 take ~M^3 FP64 FMAs per instance on a part whose FP64 rate is 1/64 of
+// FP32.  Gamma_R = i(Sigma_R - Sigma_R^dagger) is staged in double-float in
+// Gam (MPT x MPT float4, a buffer the caller no longer needs); (Gamma G) and
+// (G Gamma) are accumulated in double-float, the traces in FP64.  Gh, Gl:
+// G_LL row-major with leading dimension MPT.
+template <int MPT, int NTT>
+__device__ __noinline__ double ward_T_df(const float2 *Gh, const float2 *Gl, float4 *Gam,
+                                         const double2 *SR, int M, double *red)
+{
+    const int tid = threadIdx.x;
+    for (int e = tid; e < MPT * MPT; e += NTT) {
+        const int i = e / MPT, j = e - i * MPT;
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < M && j < M) {
+            const double2 d = csub(SR[(size_t)i * M + j], cconj(SR[(size_t)j * M + i]));
+            to_df(-d.y, g.x, g.z);
+            to_df(d.x, g.y, g.w);
+        }
+        Gam[e] = g;
+    }
+    __syncthreads();
+    double t = 0.0;
+    for (int e = tid; e < M * M; e += NTT) {
+        const int i = e / M, j = e - i * M;
+        const float4 gij = Gam[i * MPT + j];
+        const double gr = (double)gij.x + (double)gij.z, gi = (double)gij.y + (double)gij.w;
+        const double2 gji = make_double2((double)Gh[j * MPT + i].x + (double)Gl[j * MPT + i].x,
+                                         (double)Gh[j * MPT + i].y + (double)Gl[j * MPT + i].y);
+        const double2 gijc = make_double2((double)Gh[i * MPT + j].x + (double)Gl[i * MPT + j].x,
+                                          (double)Gh[i * MPT + j].y + (double)Gl[i * MPT + j].y);
+        // a = i (G_ji - conj(G_ij)); t += Re(Gamma_ij a)
+        const double ux = gji.x - gijc.x, uy = gji.y + gijc.y;
+        t += gr * (-uy) - gi * ux;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f), z = y;
+        for (int k = 0; k < M; ++k) {
+            const float4 gik = Gam[i * MPT + k], gkj = Gam[k * MPT + j];
+            const float2 ah = Gh[k * MPT + j], al = Gl[k * MPT + j], bh = Gh[i * MPT + k], bl = Gl[i * MPT + k];
+            y = df4_fms(y, make_float4(-gik.x, -gik.y, -gik.z, -gik.w), make_float4(ah.x, ah.y, al.x, al.y));
+            z = df4_fms(z, make_float4(-bh.x, -bh.y, -bl.x, -bl.y), gkj);
+        }
+        // t -= Re(y conj(z))
+        const double yr = (double)y.x + (double)y.z, yi = (double)y.y + (double)y.w;
+        const double zr = (double)z.x + (double)z.z, zi = (double)z.y + (double)z.w;
+        t -= yr * zr + yi * zi;
+    }
+    return block_sum(t, red);
+}
+
+// G_LL = Gh + Gl (row-major, leading dimension MP) into dst (M x M, complex128)
+template <int MP, int NTH = NT>
+__device__ void store_gll_df(const float2 *Gh, const float2 *Gl, int M, double2 *dst)
+{
+    for (int e = threadIdx.x; e < M * M; e += NTH) {
+        const int i = e / M, j = e - i * M;
+        dst[e] = make_double2((double)Gh[i * MP + j].x + (double)Gl[i * MP + j].x,
+                              (double)Gh[i * MP + j].y + (double)Gl[i * MP + j].y);
+    }
+}
+
 // G_LL from ward_T's scratch G (MP x MP, row-major) into dst (M x M)
 template <int MP, int NTH = NT>
 __device__ void store_gll(const double2 *G, int M, double2 *dst)

@@ -276,9 +276,8 @@ knit_sweep_mixed_kernel(InstDev in)
 
         double T = 0.0;
         if (st == ST_OK) {
-            T = ward_T<MP>(sm.Gh, sm.Gl, reinterpret_cast<double2 *>(sm.X), ip.SR, M, sm.red);
-            if (in.GLL)
-                store_gll<MP>(reinterpret_cast<double2 *>(sm.X), M, in.GLL + (size_t)ip.out * M * M);
+            T = ward_T_df<MP, NT>(sm.Gh, sm.Gl, reinterpret_cast<float4 *>(sm.X), ip.SR, M, sm.red);
+            if (in.GLL) store_gll_df<MP>(sm.Gh, sm.Gl, M, in.GLL + (size_t)ip.out * M * M);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {
@@ -421,7 +420,7 @@ knit_ldos_mixed_kernel(InstDev in, int Lmax, int save, float2 *work, double *ldo
             for (int x = tid; x < M; x += NT)
                 out[(size_t)(L - 1) * M + x] =
                     -((double)sm.Gh[x * MP + x].y + (double)sm.Gl[x * MP + x].y) / 3.141592653589793;
-            T = ward_T<MP>(sm.Gh, sm.Gl, reinterpret_cast<double2 *>(sm.X), ip.SR, M, sm.red);
+            T = ward_T_df<MP, NT>(sm.Gh, sm.Gl, reinterpret_cast<float4 *>(sm.X), ip.SR, M, sm.red);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         int seg_lo = -1;   // checkpoint slice whose segment the slots hold

@@ -102,54 +102,6 @@ struct TcSmem {
     int h0_cached;
 };
 
-// T from G_LL = Gh + Gl by the unitarity identity (the formula of ward_T in
-// mixed_common.cuh), in double-float on the CUDA cores: its two M^3 complex
-// products in FP64 would take ~1M FP64 FMAs per instance on a part whose FP64
-// rate is 1/64 of FP32.  Gamma_R = i(Sigma_R - Sigma_R^dagger) is staged in
-// double-float in Gam (MPT x MPT float4, free at this point); (Gamma G) and
-// (G Gamma) are accumulated in double-float, the traces in FP64.
-__device__ __noinline__ double ward_T_df(const float2 *Gh, const float2 *Gl, float4 *Gam, const double2 *SR, int M,
-                            double *red)
-{
-    const int tid = threadIdx.x;
-    for (int e = tid; e < MPT * MPT; e += NTT) {
-        const int i = e / MPT, j = e - i * MPT;
-        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < M && j < M) {
-            const double2 d = csub(SR[(size_t)i * M + j], cconj(SR[(size_t)j * M + i]));
-            to_df(-d.y, g.x, g.z);
-            to_df(d.x, g.y, g.w);
-        }
-        Gam[e] = g;
-    }
-    __syncthreads();
-    double t = 0.0;
-    for (int e = tid; e < M * M; e += NTT) {
-        const int i = e / M, j = e - i * M;
-        const float4 gij = Gam[i * MPT + j];
-        const double gr = (double)gij.x + (double)gij.z, gi = (double)gij.y + (double)gij.w;
-        const double2 gji = make_double2((double)Gh[j * MPT + i].x + (double)Gl[j * MPT + i].x,
-                                         (double)Gh[j * MPT + i].y + (double)Gl[j * MPT + i].y);
-        const double2 gijc = make_double2((double)Gh[i * MPT + j].x + (double)Gl[i * MPT + j].x,
-                                          (double)Gh[i * MPT + j].y + (double)Gl[i * MPT + j].y);
-        // a = i (G_ji - conj(G_ij)); t += Re(Gamma_ij a)
-        const double ux = gji.x - gijc.x, uy = gji.y + gijc.y;
-        t += gr * (-uy) - gi * ux;
-        float4 y = make_float4(0.f, 0.f, 0.f, 0.f), z = y;
-        for (int k = 0; k < M; ++k) {
-            const float4 gik = Gam[i * MPT + k], gkj = Gam[k * MPT + j];
-            const float2 ah = Gh[k * MPT + j], al = Gl[k * MPT + j], bh = Gh[i * MPT + k], bl = Gl[i * MPT + k];
-            y = df4_fms(y, make_float4(-gik.x, -gik.y, -gik.z, -gik.w), make_float4(ah.x, ah.y, al.x, al.y));
-            z = df4_fms(z, make_float4(-bh.x, -bh.y, -bl.x, -bl.y), gkj);
-        }
-        // t -= Re(y conj(z))
-        const double yr = (double)y.x + (double)y.z, yi = (double)y.y + (double)y.w;
-        const double zr = (double)z.x + (double)z.z, zi = (double)z.y + (double)z.w;
-        t -= yr * zr + yi * zi;
-    }
-    return block_sum(t, red);
-}
-
 // 2^e as a float for |e| <= 126 (exact power of two)
 KNIT_DEV float pow2f(int e) { return __int_as_float((127 + e) << 23); }
 
@@ -556,15 +508,8 @@ knit_sweep_mixed_tc_kernel(InstDev in)
 
         double T = 0.0;
         if (st == ST_OK) {
-            T = ward_T_df(Gh, Gl, reinterpret_cast<float4 *>(sm.X), SR, M, sm.red);
-            if (in.GLL) {
-                double2 *dst = in.GLL + (size_t)ip.out * M * M;
-                for (int e = tid; e < M * M; e += NTT) {
-                    const int i = e / M, j = e - i * M;
-                    dst[e] = make_double2((double)Gh[i * MPT + j].x + (double)Gl[i * MPT + j].x,
-                                          (double)Gh[i * MPT + j].y + (double)Gl[i * MPT + j].y);
-                }
-            }
+            T = ward_T_df<MPT, NTT>(Gh, Gl, reinterpret_cast<float4 *>(sm.X), SR, M, sm.red);
+            if (in.GLL) store_gll_df<MPT, NTT>(Gh, Gl, M, in.GLL + (size_t)ip.out * M * M);
             if (!isfinite(T)) st = ST_NONFINITE;
         }
         if (tid == 0) {
