@@ -707,9 +707,9 @@ def run_bdg_case(args):
     """Spinful BdG bar: 32 sites x 4 (spin x Nambu) = 128 orbitals per slice,
     L = 2048, mu = -1, t = 1, Delta = 0.1 in the system, Rashba alpha = 0.2,
     normal leads, W = 1 seed 0, 2048 midpoint energies in (-0.2, 0.2).  One
-    step = lead self-energies (FP64 decimation of the leads' electron and hole
-    sectors) + mixed sweep (tensor-core kernel, 4 x 4 block couplings) for all
-    energies.  Beside it: the lead solve and the sweep timed apart (the
+    step = lead self-energies (FP64 decimation of the leads' electron sector
+    in its two mode blocks, the hole sector its particle-hole image) + mixed
+    sweep (tensor-core kernel, 4 x 4 block couplings) for all energies.  Beside it: the lead solve and the sweep timed apart (the
     sweep's roofline over the measured TF32 peak), the FP64 sweep on 16
     energies, particle-hole symmetry of the total transmission T(E) = T(-E)
     for one disorder realisation, and the oracle on a bounded sample."""
@@ -770,6 +770,7 @@ def run_bdg_case(args):
                                f"seed 0, {ne} energies in (-0.2, 0.2), normal leads"},
         "slice_updates_per_s": ne * Lb / sec,
         "lead_selfenergies_s": lead_sec, "sweep_s": sweep_ms / 1e3,
+        "lead_blocks": sysk.info()[1],
         "roofline": {"bound": "tensor", "kernel": "knit_sweep_mixed_tc128_kernel",
                      "achieved": achieved, "peak": pk["mma_tf32_tflops"], "unit": "TFLOP/s",
                      "frac": achieved / pk["mma_tf32_tflops"], "traffic": None,

@@ -140,7 +140,14 @@ typedef struct {
  * (width M / 2, 2L slices, couplings of period 4), on which KNIT_MIXED
  * transmissions then run; a period-2 lead whose supercell splits into
  * blocks of at most 4 modes in the eigenbasis of its cell Hamiltonian is
- * solved block by block (knit_system_info reports both). */
+ * solved block by block.  A lead whose orbitals fall into decoupled sectors
+ * of one size (a normal BdG lead: electrons and holes) is decimated sector
+ * by sector, the hole sector taken as the particle-hole image of the
+ * electron sector where it is one; a sector that splits again in the
+ * eigenbasis of H0 + a (V + V^dagger) + i b (V - V^dagger) (any symmetry
+ * of the lead, e.g. a mirror of a Rashba strip) into blocks of one size is
+ * decimated block by block, Sigma = U diag(Sigma_r) U^dagger
+ * (knit_system_info reports the half-row chain and the block counts). */
 knit_status knit_system_create(const knit_system_desc *desc, knit_system *out);
 
 /* Free a system and its device workspace (NULL is accepted). */
@@ -246,8 +253,9 @@ enum {
 
 /* Which sweep kernel knit_transmission (energy x seed grid) runs for this
  * system at `precision` (*sweep, a KNIT_SWEEP_* value), and into how many
- * independent blocks the decimation of each lead splits (lead_blocks[2];
- * 1 = the whole cell or two-slice supercell).  Host only, no device work.
+ * independent blocks the decimation of each lead splits (lead_blocks[2]:
+ * sectors x mode blocks per sector, or the two-slice supercell's mode
+ * blocks; 1 = the whole cell or supercell).  Host only, no device work.
  * KNIT_ERR_INVALID for NULL arguments or an unknown precision. */
 knit_status knit_system_info(knit_system sys, int32_t precision, int32_t *sweep,
                              int32_t *lead_blocks);

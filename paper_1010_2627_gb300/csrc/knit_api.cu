@@ -44,6 +44,8 @@ extern "C" cudaError_t knit_launch_sector_assemble(const double2 *, const int *,
 extern "C" cudaError_t knit_launch_sector_status(const int *, const int *, int, int, int *, int *,
                                                  cudaStream_t);
 extern "C" cudaError_t knit_launch_jacobi(double2 *, double2 *, int, int *, cudaStream_t);
+extern "C" cudaError_t knit_launch_sector_unmode(const double2 *, const double2 *, int, int, int, double2 *,
+                                                 double2 *, int, cudaStream_t);
 extern "C" cudaError_t knit_launch_small_decimation(const double2 *, const double2 *, int, int, int,
                                                     const double *, int, double, double, int,
                                                     double2 *, int *, int *, int, cudaStream_t);
@@ -206,7 +208,74 @@ struct Lead {
     // X1 = -S conj(X0) S^dagger for H0 and V, S = 1 (x) i sigma_y on
     // consecutive orbital pairs, so that g1(E) = -S conj(g0(-E)) S^dagger
     int ph = 0;
+    // orbital sectors that split further in a mode basis: sector q is
+    // Uq diag(block q nsub + r) Uq^dagger with nsub blocks of mu modes each
+    // (uU: nsec unitaries of ms x ms, columns grouped by block; uH0 / uV:
+    // nsec nsub blocks of mu x mu)
+    int nsub = 1, mu = 0;
+    double2 *uU = nullptr, *uH0 = nullptr, *uV = nullptr;
 };
+
+// U^dagger X U for M x M row-major matrices (host, FP64)
+std::vector<double2> unitary_sandwich(const std::vector<double2> &U, const double2 *X, int M)
+{
+    auto cm = [](double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); };
+    const size_t MM = (size_t)M * M;
+    std::vector<double2> T(MM), R(MM);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < M; ++k) {
+                const double2 t = cm(X[(size_t)i * M + k], U[(size_t)k * M + j]);
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+            T[(size_t)i * M + j] = acc;
+        }
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < M; ++k) {
+                const double2 u = U[(size_t)k * M + i];
+                const double2 t = cm(make_double2(u.x, -u.y), T[(size_t)k * M + j]);
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+            R[(size_t)i * M + j] = acc;
+        }
+    return R;
+}
+
+// connected components of the graph on 0 .. n-1 with an edge (i, j) where
+// linked(i, j); components in order of their smallest member, members
+// increasing
+template <typename F>
+std::vector<std::vector<int>> graph_components(int n, F linked)
+{
+    std::vector<int> par(n);
+    for (int i = 0; i < n; ++i) par[i] = i;
+    auto find = [&](int x) {
+        while (par[x] != x) x = par[x] = par[par[x]];
+        return x;
+    };
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (linked(i, j)) {
+                const int a = find(i), b = find(j);
+                if (a != b) par[a] = b;
+            }
+    std::vector<std::vector<int>> comp;
+    std::vector<int> slot(n, -1);
+    for (int i = 0; i < n; ++i) {
+        const int r = find(i);
+        if (slot[r] < 0) {
+            slot[r] = (int)comp.size();
+            comp.emplace_back();
+        }
+        comp[slot[r]].push_back(i);
+    }
+    return comp;
+}
 
 // Split a lead cell into the connected components of the orbital graph with
 // an edge wherever H0 or V (either direction) is non-zero.  Sets ld.nsec and
@@ -305,6 +374,7 @@ struct knit_system_s {
     DevBuf p2g, p2s, p2t;   // period-2 leads: supercell g and Sigma, block-product scratch
     DevBuf secs, secg, secst, secit;   // sector leads: per-sector Sigma, g, status, iterations
     DevBuf phE, phmap, phs, phg, phst, phit;   // particle-hole sector pairs: energies, map, first sector
+    DevBuf subs, subg, subst, subit, subt;     // mode blocks of a sector: Sigma, g, status, iterations, scratch
     DevBuf gll, tw, ts, tg, trk, tau, noise;   // transmission eigenvalues: G_LL, scratch, W, rank, out
     DevBuf lrl, lrr, ljx, ljt;                 // lesser function outputs staged for host pointers
 
@@ -489,6 +559,114 @@ knit_status stage_out(DevBuf &buf, T *dst, size_t count, T **out, bool *host, co
     return KNIT_OK;
 }
 
+// Hermitian eigenbasis of an M x M matrix on the device (Jacobi); false when
+// the rotations leave an off-diagonal entry above tol (U, D then unset)
+knit_status device_eigenbasis(const std::vector<double2> &K, int M, double tol,
+                              std::vector<double2> &U, std::vector<double2> &D, bool *ok)
+{
+    const size_t MM = (size_t)M * M;
+    U.assign(MM, make_double2(0.0, 0.0));
+    D = U;
+    double2 *dA = nullptr, *dU = nullptr;
+    CK(dev_alloc((void **)&dA, sizeof(double2) * MM), "lead eigenbasis");
+    cudaError_t e = dev_alloc((void **)&dU, sizeof(double2) * MM);
+    if (e == cudaSuccess) e = cudaMemcpy(dA, K.data(), sizeof(double2) * MM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = knit_launch_jacobi(dA, dU, M, nullptr, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e == cudaSuccess) e = cudaMemcpy(U.data(), dU, sizeof(double2) * MM, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(D.data(), dA, sizeof(double2) * MM, cudaMemcpyDeviceToHost);
+    cudaFree(dA);
+    cudaFree(dU);
+    CK(e, "lead eigenbasis");
+    double off = 0.0;
+    for (size_t q = 0; q < MM; ++q)
+        if (q / M != q % M) off = std::max(off, std::fabs(D[q].x) + std::fabs(D[q].y));
+    *ok = off <= tol;
+    return KNIT_OK;
+}
+
+// Orbital sectors that split further in a mode basis.  Every unitary
+// symmetry of a sector's lead (for the Rashba bar: the transverse mirror
+// combined with a spin rotation) commutes with its cell H0 and coupling V,
+// hence with K = H0 + a (V + V^dagger) + i b (V - V^dagger), a Hermitian
+// element of the algebra they generate.  With b != 0, K is odd under time
+// reversal, which lifts the Kramers pairs of a time-reversal invariant lead,
+// so its eigenvectors are generically non-degenerate and each carries one
+// symmetry label; in that eigenbasis U, U^dagger H0 U and U^dagger V U are
+// block-diagonal and every block is a lead of its own: g = U diag(g_r)
+// U^dagger, Sigma = U diag(Sigma_r) U^dagger (the fixed point of Sec. 5.3 B
+// is covariant under a unitary change of basis).  Entries below 1e-11 of the
+// largest |H0|, |V| count as zero (the eigenbasis is exact to ~1e-14).
+// Leaves ld.nsub = 1 unless every sector splits into blocks of one common
+// size.  bH0 / bV: the nsec sector blocks of ms x ms.
+knit_status mode_subsectors(Lead &ld, const std::vector<double2> &bH0, const std::vector<double2> &bV)
+{
+    ld.nsub = 1;
+    const int ns = ld.nsec, ms = ld.ms;
+    if (ns < 2 || ms < 2) return KNIT_OK;
+    const size_t mm = (size_t)ms * ms;
+    constexpr double KA = 0.3711, KB = 0.6180;   // any values with KB != 0 will do
+    auto cab = [](double2 v) { return std::fabs(v.x) + std::fabs(v.y); };
+    std::vector<double2> uU((size_t)ns * mm), uH, uV;
+    int nsub = 0, mu = 0;
+    for (int q = 0; q < ns; ++q) {
+        const double2 *H = bH0.data() + q * mm, *V = bV.data() + q * mm;
+        std::vector<double2> K(mm);
+        double scale = 0.0;
+        for (int i = 0; i < ms; ++i)
+            for (int j = 0; j < ms; ++j) {
+                const double2 h = H[(size_t)i * ms + j], v = V[(size_t)i * ms + j];
+                const double2 vt = make_double2(V[(size_t)j * ms + i].x, -V[(size_t)j * ms + i].y);   // (V^dagger)_ij
+                // a (V + V^dagger) + i b (V - V^dagger)
+                K[(size_t)i * ms + j] = make_double2(h.x + KA * (v.x + vt.x) - KB * (v.y - vt.y),
+                                                     h.y + KA * (v.y + vt.y) + KB * (v.x - vt.x));
+                scale = std::max({scale, cab(h), cab(v)});
+            }
+        const double tol = 1e-11 * std::max(scale, 1e-300);
+        std::vector<double2> U, D;
+        bool ok = false;
+        knit_status r = device_eigenbasis(K, ms, tol, U, D, &ok);
+        if (r != KNIT_OK) return r;
+        if (!ok) return KNIT_OK;
+        const std::vector<double2> Hh = unitary_sandwich(U, H, ms), Vh = unitary_sandwich(U, V, ms);
+        const auto comp = graph_components(ms, [&](int i, int j) {
+            return cab(Hh[(size_t)i * ms + j]) > tol || cab(Vh[(size_t)i * ms + j]) > tol;
+        });
+        const int n = (int)comp.size(), m = (int)comp[0].size();
+        if (n < 2) return KNIT_OK;
+        for (auto &c : comp)
+            if ((int)c.size() != m) return KNIT_OK;
+        if (q == 0) {
+            nsub = n;
+            mu = m;
+            uH.assign((size_t)ns * n * m * m, make_double2(0.0, 0.0));
+            uV = uH;
+        } else if (n != nsub || m != mu) {
+            return KNIT_OK;
+        }
+        // columns of Uq grouped by block; the blocks of H^, V^ (entries
+        // between blocks are below tol and dropped)
+        for (int c = 0; c < n; ++c)
+            for (int a = 0; a < m; ++a) {
+                for (int i = 0; i < ms; ++i) uU[q * mm + (size_t)i * ms + c * m + a] = U[(size_t)i * ms + comp[c][a]];
+                for (int b = 0; b < m; ++b) {
+                    const size_t src = (size_t)comp[c][a] * ms + comp[c][b];
+                    const size_t dst = (((size_t)q * n + c) * m + a) * m + b;
+                    uH[dst] = Hh[src];
+                    uV[dst] = Vh[src];
+                }
+            }
+    }
+    knit_status r;
+    if ((r = to_device(&ld.uU, uU.data(), uU.size(), "lead mode blocks")) != KNIT_OK ||
+        (r = to_device(&ld.uH0, uH.data(), uH.size(), "lead mode blocks")) != KNIT_OK ||
+        (r = to_device(&ld.uV, uV.data(), uV.size(), "lead mode blocks")) != KNIT_OK)
+        return r;
+    ld.nsub = nsub;
+    ld.mu = mu;
+    return KNIT_OK;
+}
+
 // A period-2 lead (cell H0, couplings A inside the two-slice supercell and B
 // between supercells, C = B to the system) in the eigenbasis U of H0: the
 // supercell blocks that U^dagger A U and U^dagger B U leave decoupled (entries
@@ -527,55 +705,10 @@ knit_status p2_mode_sectors(Lead &ld, int M, int side, const std::vector<double2
     }
     const double tol = 1e-11 * std::max(scale, 1e-300);
     if (!(off <= tol)) return KNIT_OK;   // the eigensolver did not settle: keep the supercell
-    // X^ = U^dagger X U
-    auto sandwich = [&](const double2 *X) {
-        std::vector<double2> T(MM), R(MM);
-        for (int i = 0; i < M; ++i)
-            for (int j = 0; j < M; ++j) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int k = 0; k < M; ++k) {
-                    const double2 t = cm(X[(size_t)i * M + k], U[(size_t)k * M + j]);
-                    acc.x += t.x;
-                    acc.y += t.y;
-                }
-                T[(size_t)i * M + j] = acc;
-            }
-        for (int i = 0; i < M; ++i)
-            for (int j = 0; j < M; ++j) {
-                double2 acc = make_double2(0.0, 0.0);
-                for (int k = 0; k < M; ++k) {
-                    const double2 u = U[(size_t)k * M + i];
-                    const double2 t = cm(make_double2(u.x, -u.y), T[(size_t)k * M + j]);
-                    acc.x += t.x;
-                    acc.y += t.y;
-                }
-                R[(size_t)i * M + j] = acc;
-            }
-        return R;
-    };
-    const std::vector<double2> Ah = sandwich(A), Bh = sandwich(B);
-    std::vector<int> par(M);
-    for (int i = 0; i < M; ++i) par[i] = i;
-    auto find = [&](int x) {
-        while (par[x] != x) x = par[x] = par[par[x]];
-        return x;
-    };
-    for (int i = 0; i < M; ++i)
-        for (int j = 0; j < M; ++j)
-            if (cab(Ah[(size_t)i * M + j]) > tol || cab(Bh[(size_t)i * M + j]) > tol) {
-                const int a = find(i), b = find(j);
-                if (a != b) par[a] = b;
-            }
-    std::vector<std::vector<int>> comp;
-    std::vector<int> slot(M, -1);
-    for (int i = 0; i < M; ++i) {
-        const int r = find(i);
-        if (slot[r] < 0) {
-            slot[r] = (int)comp.size();
-            comp.emplace_back();
-        }
-        comp[slot[r]].push_back(i);
-    }
+    const std::vector<double2> Ah = unitary_sandwich(U, A, M), Bh = unitary_sandwich(U, B, M);
+    const auto comp = graph_components(M, [&](int i, int j) {
+        return cab(Ah[(size_t)i * M + j]) > tol || cab(Bh[(size_t)i * M + j]) > tol;
+    });
     const int ms = (int)comp[0].size(), ns = (int)comp.size();
     if (ns < 2 || ms > 4) return KNIT_OK;
     for (auto &c : comp)
@@ -957,6 +1090,43 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
         CK(s->secg.ensure(sizeof(double2) * mm * nE * ns), "sector g");
         CK(s->secst.ensure(sizeof(int) * (size_t)nE * ns), "sector status");
         CK(s->secit.ensure(sizeof(int) * (size_t)nE * ns), "sector iterations");
+        // sector q at n energies into Sigma / g blocks (ms x ms per energy),
+        // status and iterations per energy: the block as a whole, or its mode
+        // blocks one by one put back as Uq diag(.) Uq^dagger
+        auto sector_decimation = [&](int q, const double *Eq, int n, int gq, double2 *so, double2 *go,
+                                     int *ito, int *sto) -> knit_status {
+            if (ld.nsub == 1) {
+                CK(knit_launch_decimation(ld.sH0 + q * mm, ld.sV + q * mm, ms, ms, p, Eq, n, eta, tol,
+                                          maxit, s->decw.as<double2>(), so, go, ito, sto, gq, st),
+                   "sector decimation");
+                return KNIT_OK;
+            }
+            const int nb = ld.nsub, mu = ld.mu;
+            const size_t uu = (size_t)mu * mu;
+            CK(s->subs.ensure(sizeof(double2) * uu * n * nb), "mode blocks");
+            CK(s->subg.ensure(sizeof(double2) * uu * n * nb), "mode blocks");
+            CK(s->subst.ensure(sizeof(int) * (size_t)n * nb), "mode blocks");
+            CK(s->subit.ensure(sizeof(int) * (size_t)n * nb), "mode blocks");
+            CK(s->subt.ensure(sizeof(double2) * mm * gq), "mode blocks");
+            for (int r = 0; r < nb; ++r) {
+                const size_t b = (size_t)q * nb + r;
+                CK(knit_launch_decimation(ld.uH0 + b * uu, ld.uV + b * uu, mu, mu, p, Eq, n, eta, tol,
+                                          maxit, s->decw.as<double2>(), s->subs.as<double2>() + r * uu * n,
+                                          s->subg.as<double2>() + r * uu * n, s->subit.as<int>() + (size_t)r * n,
+                                          s->subst.as<int>() + (size_t)r * n, gq, st),
+                   "mode block decimation");
+            }
+            CK(knit_launch_sector_unmode(s->subs.as<double2>(), ld.uU + q * mm, nb, mu, n,
+                                         s->subt.as<double2>(), so, gq, st),
+               "mode blocks");
+            CK(knit_launch_sector_unmode(s->subg.as<double2>(), ld.uU + q * mm, nb, mu, n,
+                                         s->subt.as<double2>(), go, gq, st),
+               "mode blocks");
+            CK(knit_launch_sector_status(s->subst.as<int>(), s->subit.as<int>(), nb, n, sto, ito, st),
+               "mode blocks");
+            return KNIT_OK;
+        };
+        knit_status rs;
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         CK(cudaStreamIsCapturing(st, &cap), "capture status");
         if (ld.ph && cap == cudaStreamCaptureStatusNone) {
@@ -992,10 +1162,9 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
             CK(cudaMemcpy(s->phmap.p, map.data(), sizeof(int) * nE, cudaMemcpyHostToDevice), "map");
             const int gx = std::min(nX, s->nsm * 4);
             CK(s->decw.ensure(sizeof(double2) * 8 * mm * gx), "decimation workspace");
-            CK(knit_launch_decimation(ld.sH0, ld.sV, ms, ms, p, s->phE.as<double>(), nX, eta, tol, maxit,
-                                      s->decw.as<double2>(), s->phs.as<double2>(), s->phg.as<double2>(),
-                                      s->phit.as<int>(), s->phst.as<int>(), gx, st),
-               "sector decimation");
+            if ((rs = sector_decimation(0, s->phE.as<double>(), nX, gx, s->phs.as<double2>(),
+                                        s->phg.as<double2>(), s->phit.as<int>(), s->phst.as<int>())) != KNIT_OK)
+                return rs;
             CK(knit_launch_sector_ph(s->phs.as<double2>(), s->phmap.as<int>(), ms, nE, s->secs.as<double2>(), st),
                "particle-hole sector");
             CK(knit_launch_sector_ph(s->phg.as<double2>(), s->phmap.as<int>(), ms, nE, s->secg.as<double2>(), st),
@@ -1003,15 +1172,14 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
             CK(knit_launch_sector_ph_status(s->phst.as<int>(), s->phit.as<int>(), s->phmap.as<int>(), nE,
                                             s->secst.as<int>(), s->secit.as<int>(), st),
                "particle-hole sector");
-        } else
-        for (int q = 0; q < ns; ++q)
-            CK(knit_launch_decimation(ld.sH0 + q * mm, ld.sV + q * mm, ms, ms, p, dE, nE, eta, tol,
-                                      maxit, s->decw.as<double2>(),
-                                      s->secs.as<double2>() + q * mm * nE,
-                                      s->secg.as<double2>() + q * mm * nE,
-                                      s->secit.as<int>() + (size_t)q * nE,
-                                      s->secst.as<int>() + (size_t)q * nE, grid, st),
-               "sector decimation");
+        } else {
+            for (int q = 0; q < ns; ++q)
+                if ((rs = sector_decimation(q, dE, nE, grid, s->secs.as<double2>() + q * mm * nE,
+                                            s->secg.as<double2>() + q * mm * nE,
+                                            s->secit.as<int>() + (size_t)q * nE,
+                                            s->secst.as<int>() + (size_t)q * nE)) != KNIT_OK)
+                    return rs;
+        }
         CK(knit_launch_sector_assemble(s->secs.as<double2>(), ld.sidx, ns, ms, M, nE, sig, st),
            "sector sigma assembly");
         if (gout)
@@ -1497,7 +1665,8 @@ knit_status knit_system_create(const knit_system_desc *d, knit_system *out)
             if (ld.nsec > 1 &&
                 ((r = to_device(&ld.sH0, bH0.data(), bH0.size(), "lead sectors")) != KNIT_OK ||
                  (r = to_device(&ld.sV, bV.data(), bV.size(), "lead sectors")) != KNIT_OK ||
-                 (r = to_device(&ld.sidx, idx.data(), idx.size(), "lead sectors")) != KNIT_OK)) {
+                 (r = to_device(&ld.sidx, idx.data(), idx.size(), "lead sectors")) != KNIT_OK ||
+                 (r = mode_subsectors(ld, bH0, bV)) != KNIT_OK)) {
                 knit_system_destroy(s);
                 return r;
             }
@@ -1550,13 +1719,16 @@ knit_status knit_system_destroy(knit_system s)
         cudaFree(s->lead[p].sidx);
         cudaFree(s->lead[p].Cq);
         cudaFree(s->lead[p].nzr);
+        cudaFree(s->lead[p].uU);
+        cudaFree(s->lead[p].uH0);
+        cudaFree(s->lead[p].uV);
     }
     DevBuf *bufs[] = {&s->E, &s->seeds, &s->T, &s->status, &s->queue, &s->sigL, &s->sigR, &s->gL,
                       &s->gR, &s->lst, &s->lit, &s->lres, &s->work, &s->ckpt, &s->decw, &s->ldos,
                       &s->p2g, &s->p2s, &s->p2t, &s->gll, &s->tw, &s->ts, &s->tg, &s->trk,
                       &s->tau, &s->noise, &s->lrl, &s->lrr, &s->ljx, &s->ljt, &s->secs,
                       &s->secg, &s->secst, &s->secit, &s->phE, &s->phmap, &s->phs, &s->phg,
-                      &s->phst, &s->phit};
+                      &s->phst, &s->phit, &s->subs, &s->subg, &s->subst, &s->subit, &s->subt};
     for (DevBuf *b : bufs) b->release();
     delete s;
     return KNIT_OK;
@@ -2091,7 +2263,7 @@ knit_status knit_system_info(knit_system s, int32_t precision, int32_t *sweep, i
                       (int)SWEEP_HALF == (int)KNIT_SWEEP_MIXED_HALF_ROWS,
                   "sweep kinds");
     *sweep = sweep_kind(s, precision, true);
-    for (int p = 0; p < 2; ++p) lead_blocks[p] = s->lead[p].nsec;
+    for (int p = 0; p < 2; ++p) lead_blocks[p] = s->lead[p].nsec * s->lead[p].nsub;
     return KNIT_OK;
 }
 

@@ -609,6 +609,40 @@ __global__ void sector_status_kernel(const int *st, const int *it, int nsec, int
     if (it_out) it_out[e] = i0;
 }
 
+// a sector's Sigma or g from its mode blocks: out[e] = U diag(blk_0[e], ..,
+// blk_{nb-1}[e]) U^dagger, ms = nb mu, block r of energy e at blk + (r nE +
+// e) mu^2, U (ms x ms) with the modes of block r in columns r mu .. r mu +
+// mu - 1; one CTA per energy (grid-stride), T = U diag(.) in a per-CTA
+// scratch of ms^2
+__global__ void __launch_bounds__(256)
+sector_unmode_kernel(const double2 *blk, const double2 *U, int nb, int mu, int nE, double2 *scratch,
+                     double2 *out)
+{
+    const int ms = nb * mu;
+    const size_t mm = (size_t)ms * ms, uu = (size_t)mu * mu;
+    double2 *T = scratch + (size_t)blockIdx.x * mm;
+    for (int e = blockIdx.x; e < nE; e += gridDim.x) {
+        for (int q = threadIdx.x; q < (int)mm; q += blockDim.x) {
+            const int i = q / ms, c = q - i * ms, r = c / mu, b = c - r * mu;
+            const double2 *B = blk + ((size_t)r * nE + e) * uu;
+            const double2 *Ui = U + (size_t)i * ms + r * mu;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int a = 0; a < mu; ++a) acc = cfma(Ui[a], B[(size_t)a * mu + b], acc);
+            T[q] = acc;
+        }
+        __syncthreads();
+        double2 *O = out + (size_t)e * mm;
+        for (int q = threadIdx.x; q < (int)mm; q += blockDim.x) {
+            const int i = q / ms, j = q - i * ms;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int c = 0; c < ms; ++c)
+                acc = cfma(T[(size_t)i * ms + c], cconj(U[(size_t)j * ms + c]), acc);
+            O[q] = acc;
+        }
+        __syncthreads();
+    }
+}
+
 // a particle-hole pair of sectors from the first sector alone: src holds the
 // first sector at nE + nX energies (the caller's nE first, then the extra
 // energies -E that the list lacks), map[e] the index of -E_e there; out gets
@@ -672,5 +706,15 @@ extern "C" cudaError_t knit_launch_sector_status(const int *st, const int *it, i
                                                  int *st_out, int *it_out, cudaStream_t stream)
 {
     sector_status_kernel<<<(nE + 255) / 256, 256, 0, stream>>>(st, it, nsec, nE, st_out, it_out);
+    return cudaGetLastError();
+}
+
+// scratch: ms^2 complex per CTA, for min(grid, nE) CTAs
+extern "C" cudaError_t knit_launch_sector_unmode(const double2 *blk, const double2 *U, int nb, int mu,
+                                                 int nE, double2 *scratch, double2 *out, int grid,
+                                                 cudaStream_t stream)
+{
+    if (nE <= 0) return cudaSuccess;
+    sector_unmode_kernel<<<std::min(grid, nE), 256, 0, stream>>>(blk, U, nb, mu, nE, scratch, out);
     return cudaGetLastError();
 }

@@ -96,13 +96,16 @@ def test_bdg3_sweep_fp64_with_oracle_leads(knit):
 
 @pytest.mark.parametrize("Ns,lead_delta", [(32, 0.0), (6, 0.0), (6, 0.05)])
 def test_bdg_lead_sectors_against_oracle(knit, Ns, lead_delta):
-    """Normal Nambu leads split into electron and hole sectors that the GPU
-    decimates one by one (Sec. 5.3 B on each decoupled block); a lead with
-    pairing does not split.  Either way Sigma equals the oracle's decimation
-    of the whole cell to the decimation tolerance (1e-8)."""
+    """Normal Nambu leads split into electron and hole sectors, and each of
+    those into two blocks in a mode basis (the transverse mirror combined
+    with a spin rotation commutes with the Rashba lead's H0 and V), which the
+    GPU decimates one by one (Sec. 5.3 B on each decoupled block); a lead
+    with pairing does not split.  Either way Sigma equals the oracle's
+    decimation of the whole cell to the decimation tolerance (1e-8)."""
     b = inputs.bdg(Ns, 3, mu=-1.0, delta=0.1, alpha=0.2, lead_delta=lead_delta)
     E = np.array([-0.17, 0.04]) if Ns == 32 else np.array([-0.17, 0.04, 0.11])
     sysk = knit.System(b)
+    assert sysk.info()[1] == ([1, 1] if lead_delta else [4, 4])
     for lead in (0, 1):
         S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION, eta=1e-12,
                                           want_residual=True)
@@ -123,7 +126,8 @@ def test_bdg_lead_particle_hole_pairs_symmetric_grid(knit):
     E = inputs.energy_grid(-0.16, 0.16, 6)
     assert np.array_equal(E, -E[::-1]) or np.abs(E + E[::-1]).max() < 1e-15
     sysk = knit.System(b)
-    assert sysk.info()[1] == [2, 2]
+    # electron and hole sectors, each two mode blocks (mirror x spin rotation)
+    assert sysk.info()[1] == [4, 4]
     for lead in (0, 1):
         S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION, eta=1e-12,
                                           want_residual=True)
@@ -135,3 +139,46 @@ def test_bdg_lead_particle_hole_pairs_symmetric_grid(knit):
     sysk.close()
     assert (st == 0).all()
     assert np.abs(T[:, 0] - T[::-1, 0]).max() < 1e-8
+
+
+def _rashba_electron_cell(Ns, mu, alpha):
+    """the electron sector (c_up, c_dn per site) of the normal BdG lead"""
+    b = inputs.bdg(Ns, 1, mu=mu, delta=0.0, alpha=alpha)
+    e = [i for i in range(b.M) if i % 4 < 2]
+    return b.lead_H0[0][np.ix_(e, e)], b.lead_V[0][np.ix_(e, e)]
+
+
+def test_two_unrelated_sectors_split_in_mode_basis(knit):
+    """A lead of two decoupled Rashba strips with different mu and alpha: two
+    orbital sectors that are not particle-hole images of each other, so each
+    is decimated by itself, and each splits again into two mode blocks.
+    Sigma of both leads against the oracle's decimation of the whole cell
+    (1e-8), and the FP64 transmission of a short bar against the oracle's
+    dense solve with the oracle's self-energies."""
+    Ns = 5
+    ha, va = _rashba_electron_cell(Ns, -1.0, 0.2)
+    hb, vb = _rashba_electron_cell(Ns, -0.7, 0.35)
+    m = ha.shape[0]
+    Z = np.zeros((m, m), np.complex128)
+    H0 = np.block([[ha, Z], [Z, hb]])
+    V = np.block([[va, Z], [Z, vb]])
+    b = inputs.SliceSystem(2 * m, 3, H0, V, name="two Rashba strips")
+    E = np.array([-0.9, 0.3, 1.7])
+    sysk = knit.System(b)
+    assert sysk.info()[1] == [4, 4]
+    S_or = []
+    for lead in (0, 1):
+        S, it, res = sysk.lead_selfenergy(lead, E, method=knit.KNIT_LEAD_DECIMATION, eta=1e-12,
+                                          want_residual=True)
+        So = np.stack([oracle.decimation(b.lead_H0[lead], b.lead_V[lead], e, lead, eta=1e-12)[1]
+                       for e in E])
+        S_or.append(So)
+        assert np.abs(S - So).max() < 1e-8, lead
+        assert (res < 1e-5).all()
+    T, st = sysk.transmission(E, precision=knit.KNIT_FP64)
+    sysk.close()
+    assert (st == 0).all()
+    eps = np.zeros((b.L, b.M))
+    To = np.array([oracle.dense(b.H0, b.V, eps, b.L, e, S_or[0][k], S_or[1][k])["T_LR"]
+                   for k, e in enumerate(E)])
+    assert np.abs(T[:, 0] - To).max() < 1e-8
