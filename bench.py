@@ -38,7 +38,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 152-instance profile case (one kernel, one launch: 1.3878 MB) and scaled by
 # instances to 8192 (the traffic is per instance: parameters and self-energy
 # blocks); set to None whenever the kernel changes until it is measured again
-SWEEP_TRAFFIC_BYTES = 1.3878e6 * 8192 / 152
+SWEEP_TRAFFIC_BYTES = None
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -321,9 +321,11 @@ def run_knit(args):
     alg_flop = 16.0 * M ** 3 * L * n          # 16 M^3 real flop per slice-update
     achieved_tflops = alg_flop / (sweep_ms / 1e3) / 1e12
     # executed tensor-core work per slice, in 128 x 64 x 16 MMA units: the
-    # residual's 18 digit products x 8 K-chunks and the Gauss-Jordan's 9 term
-    # products x 8 panels (M / 8 panels of 8 columns)
-    tc_flop = (18 * 8 + 9 * (M // 8)) * 2.0 * 128 * 64 * 16 * L * n
+    # residual's 18 digit products x 8 K-chunks, the Gauss-Jordan's 9 term
+    # products x 8 panels (M / 8 panels of 8 columns) and the refinement
+    # product's 6 term products x 4 K-chunks at N = 128 (every slice but the
+    # ~0.07 % that take the error-free CUDA-core product)
+    tc_flop = (18 * 8 + 9 * (M // 8) + 6 * 4 * 2) * 2.0 * 128 * 64 * 16 * L * n
     tc_tflops = tc_flop / (sweep_ms / 1e3) / 1e12
 
     # ---- plain FP64 GPU sweep on a one-wave subset (same energies/seeds grid)
@@ -412,10 +414,11 @@ def run_knit(args):
                                      "peak": pk["mma_bf16_tflops"],
                                      "frac": tc_tflops / pk["mma_bf16_tflops"],
                                      "note": "bf16 products per slice: the residual's 18 digit "
-                                             "products x 8 K-chunks and the Gauss-Jordan panel "
-                                             "updates' 9 term products x 8 panels, each a "
-                                             "128 x 64 x 16 MMA, over the measured bf16 MMA "
-                                             "peak (own loop)"}},
+                                             "products x 8 K-chunks, the Gauss-Jordan panel "
+                                             "updates' 9 term products x 8 panels and the "
+                                             "refinement product's 6 term products x 4 K-chunks "
+                                             "(N = 128), in units of a 128 x 64 x 16 MMA, over "
+                                             "the measured bf16 MMA peak (own loop)"}},
         "peaks_measured": pk,
         "e2e": {"value": e2e_val, "unit": "T(E) points/s", "h2d_bytes_per_step": 8 * NE + 8 * NS,
                 "d2h_bytes_per_step": 12 * n, "ms": statistics.mean(e2e_ms)},

@@ -1124,6 +1124,13 @@ knit_status compute_sigma(knit_system s, int p, const double *dE, int nE,
                "mode blocks");
             CK(knit_launch_sector_status(s->subst.as<int>(), s->subit.as<int>(), nb, n, sto, ito, st),
                "mode blocks");
+            // near a subband edge the doubling can end off its fixed point in
+            // one basis and not in the other (the acceptance sits at a 1e-5
+            // mismatch there): the energies a block failed, once more on the
+            // whole sector
+            CK(knit_launch_decimation_failed(ld.sH0 + q * mm, ld.sV + q * mm, ms, ms, p, Eq, n, eta, tol,
+                                             maxit, s->decw.as<double2>(), so, go, ito, sto, gq, st),
+               "sector decimation of failed energies");
             return KNIT_OK;
         };
         knit_status rs;

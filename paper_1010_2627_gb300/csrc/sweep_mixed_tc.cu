@@ -113,6 +113,132 @@ KNIT_DEV int scale_exp(float mx)
     return e;
 }
 
+// x = h + m + l exactly, three bf16 values (bit patterns in the upper
+// halves), each cut at round to nearest: h takes the leading 8 significant
+// bits of the 24, r = x - h and l = r - m are exact (Sterbenz), and
+// |m| <= 2^-8 |x|, |l| <= 2^-16 |x| up to the half-ulp of each cut
+KNIT_DEV void bf16_split3_rn(float x, uint32_t &h, uint32_t &m, uint32_t &l)
+{
+    h = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)) << 16;
+    const float r = x - __uint_as_float(h);
+    m = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(r)) << 16;
+    l = __float_as_uint(r - __uint_as_float(m));
+}
+
+// two terms (upper halves) into one word, a at the lower address
+KNIT_DEV uint32_t pack_hi(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
+
+// g = X' + X' S on the tensor cores, X' in sm.X, S (row stride RS, zero
+// outside M x M) in sm.u.R, result as double-float in (Gh, Gl).  X' S is
+// formed as its transpose S^T X'^T in a split real form: A row 2n + r holds
+// column n of S, real (r = 0) or imaginary (r = 1) parts, along K = k (64:
+// four K-chunks); B row j holds row j of X' (real parts) and B row 64 + j
+// its imaginary parts (N = 128).  Accumulator lane 2n + r, column j then
+// holds (X'_re S_r)[j][n] and column 64 + j (X'_im S_r)[j][n]; with
+// Re (X'S) = X'_re S_re - X'_im S_im and Im (X'S) = X'_re S_im + X'_im S_re
+// one exchange between the lanes 2n and 2n + 1 completes the entry.  Every
+// value is cut into three bf16 terms (bf16_split3_rn, exact); the six term
+// products with p + q <= 2 run (those left out are ~2^-24 of the product
+// and below), the leading one into accumulator 0 (columns 0 .. 127), the
+// other five into accumulator 1 (128 .. 255), summed smallest first.
+// A terms: 12 tiles of 128 x 16 in the B-digit buffer; B terms: 12 tiles
+// over Gh / Gl, which hold nothing until the result is written there.
+// Returns 0 when the wait on the tensor cores runs out (phase flipped as
+// for a completed wait).
+KNIT_DEV int refine_tc(TcSmem &sm, uint32_t tmem, uint32_t &phase)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned char *const at = sm.w.s.bdig;
+    unsigned char *const bt = reinterpret_cast<unsigned char *>(sm.w.s.Gh);
+    static_assert(sizeof(sm.w.s.bdig) >= 12 * A_TILE, "A terms of S");
+    static_assert(sizeof(sm.w.s.Gh) + sizeof(sm.w.s.Gl) >= 12 * A_TILE, "B terms of X'");
+    const float2 *const S = sm.u.R;
+    // item e: chunk c = e / 512, row n (A) or j (B) = (e / 8) % 64, K pair
+    // 2 (e % 8) of the chunk; eight lanes share a row (conflict-free loads)
+    for (int e = tid; e < 4 * MPT * 8; e += NTT) {
+        const int kp = e & 7, rI = (e >> 3) & 63, c = e >> 9, k = 16 * c + 2 * kp;
+        uint32_t t[2][2][3];   // [re / im][k / k+1][term]
+        {
+            const float2 s0 = S[k * RS + rI], s1 = S[(k + 1) * RS + rI];
+            bf16_split3_rn(s0.x, t[0][0][0], t[0][0][1], t[0][0][2]);
+            bf16_split3_rn(s1.x, t[0][1][0], t[0][1][1], t[0][1][2]);
+            bf16_split3_rn(s0.y, t[1][0][0], t[1][0][1], t[1][0][2]);
+            bf16_split3_rn(s1.y, t[1][1][0], t[1][1][1], t[1][1][2]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    *reinterpret_cast<uint32_t *>(at + (c * 3 + q) * A_TILE + tile_off(2 * rI + r, 2 * kp)) =
+                        pack_hi(t[r][0][q], t[r][1][q]);
+        }
+        {
+            const float4 x = *reinterpret_cast<const float4 *>(sm.X + rI * MPT + k);
+            bf16_split3_rn(x.x, t[0][0][0], t[0][0][1], t[0][0][2]);
+            bf16_split3_rn(x.z, t[0][1][0], t[0][1][1], t[0][1][2]);
+            bf16_split3_rn(x.y, t[1][0][0], t[1][0][1], t[1][0][2]);
+            bf16_split3_rn(x.w, t[1][1][0], t[1][1][1], t[1][1][2]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    *reinterpret_cast<uint32_t *>(bt + (c * 3 + q) * A_TILE + tile_off(64 * r + rI, 2 * kp)) =
+                        pack_hi(t[r][0][q], t[r][1][q]);
+        }
+    }
+    async_proxy_fence();
+    fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        fence_after();
+        const uint32_t idesc = idesc_bf16_m128(128);
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3 - p; ++q) {
+                    const bool lead = p + q == 0;
+                    const uint32_t acc = lead ? (c > 0) : !(c == 0 && p == 0 && q == 1);
+                    mma_bf16(tmem + (lead ? 0u : 128u), smem_desc(smem_u32(at + (c * 3 + p) * A_TILE)),
+                             smem_desc(smem_u32(bt + (c * 3 + q) * A_TILE)), idesc, acc);
+                }
+        mma_commit(&sm.mbar);
+    }
+    const int ok = tid == 0 ? mbar_wait(&sm.mbar, phase) : 1;
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) return 0;
+    fence_after();
+    {
+        // warp w: lanes 32 (w % 4) .. (columns n = 16 (w % 4) + lane / 2,
+        // part r = lane % 2), rows j = 16 (w / 4) ..
+        const int qd = warp & 3, j0 = 16 * (warp >> 2);
+        const int n = 16 * qd + (lane >> 1), r = lane & 1;
+        const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + j0;
+        uint32_t a0[16], b0[16], a1[16], b1[16];
+        tmem_ld16(ta, a0);
+        tmem_ld16(ta + 64, b0);
+        tmem_ld16(ta + 128, a1);
+        tmem_ld16(ta + 192, b1);
+        wait_ld();
+        float *const Xf = reinterpret_cast<float *>(sm.X);
+        float *const Ghf = reinterpret_cast<float *>(sm.w.s.Gh);
+        float *const Glf = reinterpret_cast<float *>(sm.w.s.Gl);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const float d1 = __uint_as_float(a1[jj]) + __uint_as_float(a0[jj]);
+            const float d2 = __uint_as_float(b1[jj]) + __uint_as_float(b0[jj]);
+            const float o = __shfl_xor_sync(0xffffffffu, d2, 1);
+            const float v = r ? d1 + o : d1 - o;
+            const int e = 2 * ((j0 + jj) * MPT + n) + r;
+            float h, l;
+            two_sum(Xf[e], v, h, l);
+            Ghf[e] = h;
+            Glf[e] = l;
+        }
+    }
+    fence_before();
+    return 1;
+}
+
 __global__ void fill_status(int *st, int n, int v)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -499,10 +625,21 @@ knit_sweep_mixed_tc_kernel(InstDev in)
             const int nx = neumann_terms(rmax, M);
             float2 *const S = nx ? reinterpret_cast<float2 *>(sm.w.s.bdig) : sm.u.R;
             neumann_inplace<MPT, RS, TYT, TXT>(sm.u.R, S, M, nx);
-            if (rmax > EXACT_RMAX)
+            if (rmax > EXACT_RMAX) {
                 refine_exact<MPT, RS, TYT, TXT>(sm.X, S, Gh, Gl, M);
-            else
-                refine<MPT, RS, TYT, TXT>(sm.X, S, Gh, Gl, M);
+            } else {
+                if (nx) {
+                    // the series into the residual's place: the B-digit
+                    // buffer takes the operand terms
+                    for (int e = tid; e < MPT * RS; e += NTT) sm.u.R[e] = S[e];
+                    __syncthreads();
+                }
+                if (!refine_tc(sm, tmem, phase)) {
+                    st = ST_TIMEOUT;
+                    timed_out = true;
+                    break;
+                }
+            }
             __syncthreads();
         }
 
