@@ -35,10 +35,10 @@ WORKLOAD = "square M=64 L=512 W=2, 1024 energies x 8 seeds, two clean leads"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the sweep kernel on this workload, for the kernel as it stands: taken on the
-# 152-instance profile case (one kernel, one launch: 1.3878 MB) and scaled by
+# 152-instance profile case (one kernel, one launch: 1.387 MB) and scaled by
 # instances to 8192 (the traffic is per instance: parameters and self-energy
 # blocks); set to None whenever the kernel changes until it is measured again
-SWEEP_TRAFFIC_BYTES = None
+SWEEP_TRAFFIC_BYTES = 1.387008e6 * 8192 / 152
 L2_BYTES = 126 * 1024 * 1024
 
 
