@@ -30,9 +30,10 @@
 //  * the seven accumulators are summed -- 3 .. 6 (below 2^-24 of the
 //    leading one) in fp32, then with 0 .. 2 in double-float -- scaled by
 //    sigma_i tau_n 2^-16, the identity added, and R rounded once to fp32;
-//  * g = X' (I + R + R^2 + ...) with as many terms as max|R_ij| asks for,
-//    the product X' S accumulated error-free where max|R_ij| is large
-//    (mixed_common.cuh: neumann_terms, refine_exact).
+//  * g = X' (I + R + R^2 + ...) with as many terms as max|R_ij| asks for
+//    (mixed_common.cuh: neumann_terms), the product X' S on the tensor cores
+//    as six bf16-term MMAs per K-chunk (refine_tc), or accumulated
+//    error-free on the CUDA cores where max|R_ij| is large (refine_exact).
 // The digit products are the Ozaki splitting (Ozaki, Ogita, Oishi & Rump
 // 2012) with bf16 slices, specialised to the residual of an approximate
 // inverse.
