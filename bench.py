@@ -623,26 +623,34 @@ def run_profile_case(args):
     skipped above width 64, where it takes seconds).  --profile-lattice
     armchair: the graphene ribbon of the same row width and length instead
     (t = 2.7, W = 1, 19 energies in (-2, 2)), above width 128 run by
-    half-rows."""
+    half-rows; --profile-lattice bdg: the spinful BdG bar of --profile-M / 4
+    sites (mu = -1, Delta = 0.1, alpha = 0.2, W = 1, 19 energies in
+    (-0.2, 0.2), normal leads)."""
     import torch
     from paper_1010_2627_gb300 import build, inputs, knit
     build.build()
     knit.load()
     Lp, Mp = args.profile_L, args.profile_M
     honeycomb = args.profile_lattice == "armchair"
-    ss = inputs.armchair(Mp, Lp) if honeycomb else inputs.square(Mp, Lp)
-    E = inputs.energy_grid(-2.0, 2.0, 19) if honeycomb else inputs.energy_grid(-3.9, 3.9, 19)
+    nambu = args.profile_lattice == "bdg"
+    if honeycomb:
+        ss, E, Wp = inputs.armchair(Mp, Lp), inputs.energy_grid(-2.0, 2.0, 19), 1.0
+    elif nambu:
+        ss = inputs.bdg(Mp // 4, Lp, mu=-1.0, delta=0.1, alpha=0.2)
+        E, Wp = inputs.energy_grid(-0.2, 0.2, 19), 1.0
+    else:
+        ss, E, Wp = inputs.square(Mp, Lp), inputs.energy_grid(-3.9, 3.9, 19), W
     seeds = np.arange(NS, dtype=np.uint64)
     sysk = knit.System(ss)
     runs = (knit.KNIT_MIXED, knit.KNIT_MIXED) + ((knit.KNIT_FP64,) if Mp <= 64 else ())
     for precision in runs:
-        T, st = sysk.transmission(E, seeds, W=1.0 if honeycomb else W, precision=precision)
+        T, st = sysk.transmission(E, seeds, W=Wp, precision=precision)
         if (st != 0).any():
             bad = np.argwhere(st != 0)
             print(json.dumps({"case": "profile", "status": {int(c): int((st == c).sum()) for c in np.unique(st)
                                                             if c != 0},
                               "energies": sorted({float(E[e]) for e, _ in bad})}), flush=True)
-        assert honeycomb or (st == 0).all()
+        assert honeycomb or nambu or (st == 0).all()
     torch.cuda.synchronize()
     print(json.dumps({"case": "profile", "M": Mp, "L": Lp, "instances": 19 * NS,
                       "T_mean": float(T.mean())}))
@@ -1242,7 +1250,7 @@ def main():
     ap.add_argument("--profile-L", dest="profile_L", type=int, default=64)
     ap.add_argument("--profile-M", dest="profile_M", type=int, default=64)
     ap.add_argument("--profile-lattice", dest="profile_lattice", default="square",
-                    choices=["square", "armchair"])
+                    choices=["square", "armchair", "bdg"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
