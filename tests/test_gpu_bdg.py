@@ -1,5 +1,6 @@
-"""GPU parity at the spinful BdG bar's width (32 sites x 4 = 128 orbitals,
-configuration 5's slice) against the oracle's dense solve (Eq. 2, Sec. 2.3).
+"""GPU parity at the spinful BdG bar's width (32 sites x 4 = 128 orbitals
+per slice, the Rashba bar of the BdG workload) against the oracle's dense
+solve (Eq. 2, Sec. 2.3).
 
 The sweep is checked on its own by giving the GPU the oracle's self-energies
 (knit_transmission_sigma): |dT| / max(1, N_ch) <= 1e-8 in FP64 and <= 1e-6 in
