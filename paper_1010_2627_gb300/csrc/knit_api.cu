@@ -1816,7 +1816,7 @@ static knit_status transmission_impl(knit_system s, const double *E, int32_t nE,
     if ((r = stage_in(s->E, E, (size_t)nE, st, &in.E, "E")) != KNIT_OK) return r;
     if ((r = stage_in(s->seeds, seeds, (size_t)nS, st, &in.seeds, "seeds")) != KNIT_OK) return r;
     if (sigmaL) {
-        const double2 *a, *b;
+        const double2 *a = nullptr, *b = nullptr;
         if ((r = stage_in(s->sigL, (const double2 *)sigmaL, MM * nE, st, &a, "sigmaL")) != KNIT_OK ||
             (r = stage_in(s->sigR, (const double2 *)sigmaR, MM * nE, st, &b, "sigmaR")) != KNIT_OK)
             return r;
